@@ -1,0 +1,506 @@
+"""Plain FP64 CPU oracle of the preconditioned modified linearized Bregman
+algorithm (MLBA) for frame-based deblurring with boundary treatment.
+
+TEST INFRASTRUCTURE ONLY.  This module exists to check the CUDA library
+against the paper.  Only the test suite, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+It shares no code with the CUDA path and never imports it.
+
+Everything is float64 numpy, written for readability, not speed: direct
+convolution by a loop over PSF taps, the framelet as explicit sparse 1-D filter
+matrices applied level by level, library FFT/DCT as the transform step, the
+textbook PCG, and a bracketing root finder for the nonstationary parameter.
+Where the paper is silent or garbled the reading taken is stated in the
+function's docstring (readings c1..c19 of the design notes).
+
+Pins (tests/test_oracle_*.py): dense-matrix brute force of A and A^T built
+from the padding definitions of Table 1, the adjoint identity, W^T W = I and
+the printed 1-D framelet matrices of Section 6.1, BCCB eigenvalues against the
+dense periodic matrix, the DCT diagonalisation of the reflective matrix for a
+symmetric PSF, the closed-form soft threshold, the closed-form iterated
+Tikhonov sequence (mu = 0, periodic BC), the closed-form first iterate, the
+PCG against a dense solve, and the defining equation of alpha_n.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.fft as sfft
+import scipy.sparse as sp
+
+BCS = ("zero", "periodic", "reflective", "rect")
+PRECONDS = ("none", "bccb", "krylov", "sym", "tikh", "tikh_ns")
+
+
+# ---------------------------------------------------------------------------
+# Section 2: the blurring matrix
+# ---------------------------------------------------------------------------
+
+def psf_centre(h: np.ndarray) -> int:
+    """Centre index of an odd p x p PSF (reading c17: only odd p)."""
+    p = h.shape[0]
+    if h.shape != (p, p) or p % 2 == 0:
+        raise ValueError("PSF must be square with odd size")
+    return (p - 1) // 2
+
+
+def bc_index(e: np.ndarray, n: int, bc: str) -> np.ndarray:
+    """Field-of-view index that the extended index ``e`` copies (Table 1).
+
+    zero: outside pixels are 0 (returned as -1); periodic: e mod n;
+    reflective: fliplr/flipud mirror, i.e. e = -1 copies 0, e = n copies n-1,
+    repeated with period 2n.
+    """
+    e = np.asarray(e)
+    if bc == "zero":
+        return np.where((e >= 0) & (e < n), e, -1)
+    if bc == "periodic":
+        return np.mod(e, n)
+    if bc == "reflective":
+        q = np.mod(e, 2 * n)
+        return np.where(q < n, q, 2 * n - 1 - q)
+    raise ValueError(bc)
+
+
+def extend(f: np.ndarray, c: int, bc: str) -> np.ndarray:
+    """Pad the n x n image by c pixels on every side as in Table 1."""
+    n = f.shape[0]
+    idx = bc_index(np.arange(-c, n + c), n, bc)
+    ok = idx >= 0
+    out = np.zeros((n + 2 * c, n + 2 * c))
+    sel = np.where(ok, idx, 0)
+    out[:, :] = f[np.ix_(sel, sel)]
+    out[~ok, :] = 0.0
+    out[:, ~ok] = 0.0
+    return out
+
+
+def blur(f: np.ndarray, h: np.ndarray, bc: str) -> np.ndarray:
+    """A f for the model g = A f + eta (Eq. model2 / modeld).
+
+    True convolution (reading c10): (A f)(i, j) = sum_{a,b} H[a,b]
+    f_ext(i + c - (a - c) - c, ...) i.e. the PSF entry at offset (dy, dx) from
+    its centre multiplies f at (i - dy, j - dx).  ``bc == 'rect'``: f is
+    m x m and A is the rectangular n^2 x m^2 'valid' operator A = M A_big of
+    Eq. Arect (n = m - p + 1).  Otherwise f is n x n and is first padded by the
+    boundary condition of Table 1 (zero / periodic / reflective).
+    """
+    p = h.shape[0]
+    c = psf_centre(h)
+    if bc == "rect":
+        fe = f
+        n = f.shape[0] - p + 1
+    else:
+        fe = extend(f, c, bc)
+        n = f.shape[0]
+    out = np.zeros((n, n))
+    for a in range(p):
+        for b in range(p):
+            if h[a, b] != 0.0:
+                out += h[a, b] * fe[p - 1 - a:p - 1 - a + n, p - 1 - b:p - 1 - b + n]
+    return out
+
+
+def blur_adjoint(t: np.ndarray, h: np.ndarray, bc: str) -> np.ndarray:
+    """A^T t, the exact transpose of :func:`blur` (reading c11).
+
+    The transpose of the tap loop scatters every tap onto the extended
+    (n + p - 1)^2 domain (zero padding then full correlation, Section 2.1);
+    for a boundary condition the extended domain is then folded back onto the
+    field of view by the transpose of the Table 1 padding (each padded pixel
+    adds into the pixel it copied; zero-BC padding is dropped).
+    """
+    n = t.shape[0]
+    p = h.shape[0]
+    c = psf_centre(h)
+    v = np.zeros((n + p - 1, n + p - 1))
+    for a in range(p):
+        for b in range(p):
+            if h[a, b] != 0.0:
+                v[p - 1 - a:p - 1 - a + n, p - 1 - b:p - 1 - b + n] += h[a, b] * t
+    if bc == "rect":
+        return v
+    idx = bc_index(np.arange(-c, n + c), n, bc)
+    ok = idx >= 0
+    rows = np.zeros((n, n + 2 * c))
+    np.add.at(rows, idx[ok], v[ok, :])
+    u = np.zeros((n, n))
+    np.add.at(u.T, idx[ok], rows.T[ok, :])
+    return u
+
+
+# ---------------------------------------------------------------------------
+# Section 6.1: piecewise-linear B-spline tight framelets
+# ---------------------------------------------------------------------------
+
+# masks b0, b1, b2 of Section 6.1 as taps at offsets -1, 0, +1 (reading c1)
+MASKS = (
+    (0.25, 0.5, 0.25),
+    (math.sqrt(2.0) / 4.0, 0.0, -math.sqrt(2.0) / 4.0),
+    (-0.25, 0.5, -0.25),
+)
+# band order within a level: (i, j) != (0, 0) lexicographically (reading c2)
+HIGH_BANDS = tuple((i, j) for i in range(3) for j in range(3) if (i, j) != (0, 0))
+
+
+def reflect_half(e: np.ndarray, n: int) -> np.ndarray:
+    """Half-sample symmetric extension index (x[-1] = x[0], x[n] = x[n-1])."""
+    q = np.mod(e, 2 * n)
+    return np.where(q < n, q, 2 * n - 1 - q)
+
+
+def filter_matrix(k: int, n: int, dilation: int = 1) -> sp.csr_matrix:
+    """n x n matrix of mask b_k dilated by ``dilation`` under the reflective
+    boundary of Section 6.1: row i holds b_k[t] at column refl(i + t*dilation).
+    For dilation 1 this gives the printed B_0 and the printed [-1, 2, -1]
+    matrix exactly (reading c1)."""
+    rows, cols, vals = [], [], []
+    i = np.arange(n)
+    for t, w in zip((-1, 0, 1), MASKS[k]):
+        if w == 0.0:
+            continue
+        rows.append(i)
+        cols.append(reflect_half(i + t * dilation, n))
+        vals.append(np.full(n, w))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n, n))
+
+
+def n_bands(levels: int) -> int:
+    return 8 * levels + 1
+
+
+def framelet_analysis(u: np.ndarray, levels: int) -> np.ndarray:
+    """W u: the undecimated multilevel framelet transform (reading c2).
+
+    Level l uses the masks dilated by 2^(l-1) on the level-(l-1) low-pass;
+    the nine 2-D filters are B_i (rows) x B_j (columns), i.e. B_i X B_j^T.
+    Output: (8*levels + 1, N, N) with the eight high-pass bands of level 1,
+    then level 2, ..., and the final low-pass band last.
+    """
+    n = u.shape[0]
+    bands = []
+    cur = u
+    for lev in range(1, levels + 1):
+        d = 2 ** (lev - 1)
+        b = [filter_matrix(k, n, d) for k in range(3)]
+        for i, j in HIGH_BANDS:
+            bands.append(np.asarray(b[i] @ cur @ b[j].T))
+        cur = np.asarray(b[0] @ cur @ b[0].T)
+    bands.append(cur)
+    return np.stack(bands)
+
+
+def framelet_synthesis(x: np.ndarray, levels: int) -> np.ndarray:
+    """W^T x, the transpose of :func:`framelet_analysis`."""
+    n = x.shape[-1]
+    s = x[-1]
+    for lev in range(levels, 0, -1):
+        d = 2 ** (lev - 1)
+        b = [filter_matrix(k, n, d) for k in range(3)]
+        acc = np.asarray(b[0].T @ s @ b[0])
+        for k, (i, j) in enumerate(HIGH_BANDS):
+            acc = acc + np.asarray(b[i].T @ x[(lev - 1) * 8 + k] @ b[j])
+        s = acc
+    return s
+
+
+def soft(x: np.ndarray, mu: float) -> np.ndarray:
+    """S_mu of Eq. soft: sgn(x) max(|x| - mu, 0), componentwise."""
+    return np.sign(x) * np.maximum(np.abs(x) - mu, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Section 4: preconditioners
+# ---------------------------------------------------------------------------
+
+def quadrantally_symmetric(h: np.ndarray, tol: float = 1e-14) -> bool:
+    """True when H equals its left-right and up-down flips (Section 4.1)."""
+    s = np.abs(h).max()
+    return (np.abs(h - h[::-1, :]).max() <= tol * s) and (np.abs(h - h[:, ::-1]).max() <= tol * s)
+
+
+def symmetrize(h: np.ndarray) -> np.ndarray:
+    """H~ of Section 4.3: mean over the four sign flips of the offsets from
+    the PSF centre (reading c8)."""
+    return 0.25 * (h + h[::-1, :] + h[:, ::-1] + h[::-1, ::-1])
+
+
+def spectrum_dft(h: np.ndarray, n: int) -> np.ndarray:
+    """Eigenvalues of the periodic-BC (BCCB, Strang) matrix C of Section 4.1:
+    2-D DFT of the PSF zero-padded to n x n with its centre moved to (0, 0)."""
+    c = psf_centre(h)
+    p = h.shape[0]
+    pad = np.zeros((n, n))
+    for a in range(p):
+        for b in range(p):
+            pad[(a - c) % n, (b - c) % n] += h[a, b]
+    return np.fft.fft2(pad)
+
+
+def spectrum_dct(h: np.ndarray, n: int) -> np.ndarray:
+    """Eigenvalues of the reflective-BC matrix of a quadrantally symmetric PSF
+    (Section 2.2, Section 4.1): dct2(A e_1) ./ dct2(e_1) with the orthonormal
+    2-D DCT-II (reading c9)."""
+    e1 = np.zeros((n, n))
+    e1[0, 0] = 1.0
+    a_e1 = blur(e1, h, "reflective")
+    return sfft.dctn(a_e1, type=2, norm="ortho") / sfft.dctn(e1, type=2, norm="ortho")
+
+
+class SpectralPrecond:
+    """(CC^T + alpha I)^{-1} and C^T (CC^T + alpha I)^{-1} for a C diagonalised
+    by the DFT (periodic BC) or the DCT (reflective BC, symmetric PSF)."""
+
+    def __init__(self, h: np.ndarray, n: int, transform: str):
+        self.transform = transform
+        self.n = n
+        if transform == "dft":
+            self.lam = spectrum_dft(h, n)
+        elif transform == "dct":
+            self.lam = spectrum_dct(h, n)
+        else:
+            raise ValueError(transform)
+        self.sigma = np.abs(self.lam) ** 2
+
+    def forward(self, r):
+        if self.transform == "dft":
+            return np.fft.fft2(r) / self.n       # unitary scaling
+        return sfft.dctn(r, type=2, norm="ortho")
+
+    def inverse(self, rhat):
+        if self.transform == "dft":
+            return np.real(np.fft.ifft2(rhat * self.n))
+        return sfft.idctn(rhat, type=2, norm="ortho")
+
+    def inv(self, r, alpha):
+        """(CC^T + alpha I)^{-1} r (Eq. Alg1, Alg3)."""
+        return self.inverse(self.forward(r) / (self.sigma + alpha))
+
+    def tikh(self, r, alpha):
+        """C^T (CC^T + alpha I)^{-1} r (Eq. Alg4)."""
+        return self.inverse(self.forward(r) * np.conj(self.lam) / (self.sigma + alpha))
+
+    def apply_C(self, f):
+        return self.inverse(self.forward(f) * self.lam)
+
+
+def pcg(r, apply_aat, apply_m, alpha, tol=1e-3, max_steps=5):
+    """Algorithm 2 inner solve (Section 4.2, Eqs. syscg, psys, bet).
+
+    Preconditioned CG for (A A^T + alpha I) t = r with preconditioner
+    M = (CC^T + alpha I)^{-1} and zero initial guess.  Stops after
+    beta_n = min(5, beta_tol) steps, beta_tol being the first step at which
+    the relative residual of the symmetric system (psys),
+    sqrt(r_k^T M r_k / r_0^T M r_0), is <= tol (reading c12).
+    Returns (t, beta_n).
+    """
+    x = np.zeros_like(r)
+    res = r.copy()
+    zz = apply_m(res)
+    rho = float(np.vdot(res, zz))
+    rho0 = rho
+    if rho0 == 0.0:
+        return x, 0
+    p = zz.copy()
+    steps = 0
+    for k in range(1, max_steps + 1):
+        q = apply_aat(p) + alpha * p
+        a = rho / float(np.vdot(p, q))
+        x = x + a * p
+        res = res - a * q
+        steps = k
+        zz = apply_m(res)
+        rho_new = float(np.vdot(res, zz))
+        if math.sqrt(max(rho_new, 0.0) / rho0) <= tol:
+            break
+        p = zz + (rho_new / rho) * p
+        rho = rho_new
+    return x, steps
+
+
+def ns_qn(resnorm: float, delta: float, q: float, rho: float) -> float:
+    """q_n = max{q, 2 rho + (1 + rho)/tau_n}, tau_n = ||r^n|| / delta (Eq. Alg4_rev_7)."""
+    tau_n = resnorm / delta
+    return max(q, 2.0 * rho + (1.0 + rho) / tau_n)
+
+
+def ns_tau(rho: float) -> float:
+    """tau = (1 + 2 rho)/(1 - 2 rho) of Algorithm 4-NS."""
+    return (1.0 + 2.0 * rho) / (1.0 - 2.0 * rho)
+
+
+ALPHA_FLOOR = 1e-14
+
+
+def ns_alpha(rhat2: np.ndarray, sigma: np.ndarray, qn: float) -> float:
+    """alpha_n solving alpha ||(CC^T + alpha I)^{-1} r|| = q_n ||r||
+    (Eq. Alg4_rev_7, reading c13).
+
+    With a unitary transform, ||(CC^T + a I)^{-1} r||^2 = sum |r^_k|^2/(s_k+a)^2
+    and ||r||^2 = sum |r^_k|^2, so the equation is
+    psi(a) = sum |r^_k|^2 a^2/(s_k+a)^2 = q_n^2 sum |r^_k|^2.  psi increases
+    with a, so the root is unique (Remark after Algorithm 4-NS).  It is found
+    by bisection on log(a) to a relative bracket of 1e-3 and then by
+    safeguarded Newton steps to a relative change below 1e-15.  If even
+    a = ALPHA_FLOOR over-shoots the target, ALPHA_FLOOR is returned.
+    """
+    total = float(rhat2.sum())
+    target = qn * qn * total
+
+    def psi(a):
+        w = a / (sigma + a)
+        return float((rhat2 * w * w).sum())
+
+    def dpsi(a):
+        # d psi / d a = sum 2 |r^|^2 a s /(s + a)^3
+        return float((rhat2 * 2.0 * a * sigma / (sigma + a) ** 3).sum())
+
+    lo, hi = ALPHA_FLOOR, 1.0
+    if psi(lo) >= target:
+        return lo
+    while psi(hi) < target:
+        lo, hi = hi, hi * 16.0
+        if hi > 1e30:
+            return hi
+    while hi / lo > 1.001:
+        mid = math.sqrt(lo * hi)
+        if psi(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    a = math.sqrt(lo * hi)
+    for _ in range(100):
+        fa = psi(a) - target
+        da = dpsi(a)
+        step = fa / da if da > 0 else 0.0
+        a_new = a - step
+        if not (lo < a_new < hi):
+            a_new = 0.5 * (lo + hi)
+        if fa < 0:
+            lo = max(lo, a)
+        else:
+            hi = min(hi, a)
+        if abs(a_new - a) <= 1e-15 * a:
+            a = a_new
+            break
+        a = a_new
+    return a
+
+
+# ---------------------------------------------------------------------------
+# Section 3 / 4 / 5: the iteration
+# ---------------------------------------------------------------------------
+
+def choose_transform(h: np.ndarray, precond: str, transform: str) -> str:
+    """DCT for a quadrantally symmetric PSF (Section 4.1) or always for the
+    symmetrised Algorithm 3; DFT otherwise; an explicit choice wins for
+    Algorithms 1, 2 and 4."""
+    if precond == "sym":
+        return "dct"
+    if transform in ("dft", "dct"):
+        return transform
+    return "dct" if quadrantally_symmetric(h) else "dft"
+
+
+def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
+         stop=True, gamma=1.0 + 1e-15, q=0.5, rho=1e-4, transform="auto",
+         rect_ns_hybrid=False, pcg_tol=1e-3, pcg_max=5):
+    """Run the preconditioned MLBA of Eq. MLBA2 in the variant ``precond``.
+
+    - 'none'   : P = I (linearized Bregman, Eq. iterLinBreg with lambda = 1)
+    - 'bccb'   : Algorithm 1, z += W A^T (CC^T + alpha I)^{-1} r
+    - 'krylov' : Algorithm 2, t from :func:`pcg`, z += W A^T t
+    - 'sym'    : Algorithm 3, Q = reflective BC of H~, z += W A^T (QQ^T+alpha I)^{-1} r
+    - 'tikh'   : Algorithm 4, z += W C^T (CC^T + alpha I)^{-1} r (BC only)
+    - 'tikh_ns': Algorithm 4-NS with alpha_n from Eq. Alg4_rev_7; with
+                 ``bc == 'rect'`` (only if ``rect_ns_hybrid``) the Algorithm-1
+                 form z += W A^T (CC^T + alpha_n I)^{-1} r with alpha_n floored
+                 at ``alpha``, which must satisfy Eq. condconvalg1 (reading c14).
+
+    with x = S_mu(z), f = W^T x, z^0 = x^0 = 0 and r^n = g - A f^n.
+    Stopping (Eq. discrpr, Eq. Alg4_rev_12): the first n > 0 with
+    ||r^n|| <= gamma delta (Algorithms 1-4), or the first n >= 0 with
+    ||r^n|| <= tau delta (4-NS) (readings c4, c16).  With ``stop=False``
+    exactly ``max_iter`` updates run and the iteration at which the rule would
+    have fired is recorded (reading c15); past that point 4-NS keeps alpha_n
+    at its last value.
+
+    Returns a dict: f (restoration), z, iters (updates done), stop_iter,
+    resnorms (||r^0|| .. ||r^iters||), alphas, betas.
+    """
+    if bc not in BCS or precond not in PRECONDS:
+        raise ValueError((bc, precond))
+    n = g.shape[0]
+    p = h.shape[0]
+    nf = n + p - 1 if bc == "rect" else n
+    if precond in ("tikh", "tikh_ns") and bc == "rect" and not (precond == "tikh_ns" and rect_ns_hybrid):
+        raise ValueError("Algorithm 4 needs a square A (Section 5)")
+    ns = precond == "tikh_ns"
+    tr = choose_transform(h, precond, transform)
+    pre = None
+    if precond in ("bccb", "krylov", "tikh", "tikh_ns"):
+        pre = SpectralPrecond(h, n, tr)
+    elif precond == "sym":
+        pre = SpectralPrecond(symmetrize(h), n, "dct")
+    tau = ns_tau(rho)
+
+    B = n_bands(levels)
+    z = np.zeros((B, nf, nf))
+    f = np.zeros((nf, nf))
+    resnorms, alphas, betas = [], [], []
+    stop_iter = None
+    alpha_n = alpha
+    it = 0
+    while True:
+        r = g - blur(f, h, bc)
+        rn = float(np.linalg.norm(r))
+        resnorms.append(rn)
+        crossed = (rn <= tau * delta) if ns else (it > 0 and rn <= gamma * delta)
+        if crossed and stop_iter is None:
+            stop_iter = it
+        if stop and crossed:
+            break
+        if it >= max_iter:
+            break
+        if precond == "none":
+            u = blur_adjoint(r, h, bc)
+        elif precond in ("bccb", "sym"):
+            u = blur_adjoint(pre.inv(r, alpha), h, bc)
+        elif precond == "krylov":
+            t, beta = pcg(r, lambda v: blur(blur_adjoint(v, h, bc), h, bc),
+                          lambda v: pre.inv(v, alpha), alpha, pcg_tol, pcg_max)
+            betas.append(beta)
+            u = blur_adjoint(t, h, bc)
+        elif precond == "tikh":
+            u = pre.tikh(r, alpha)
+        else:  # tikh_ns
+            if not (rn <= tau * delta):
+                qn = ns_qn(rn, delta, q, rho)
+                rhat = pre.forward(r)
+                alpha_n = ns_alpha(np.abs(rhat) ** 2, pre.sigma, qn)
+                if bc == "rect":
+                    alpha_n = max(alpha_n, alpha)
+            alphas.append(alpha_n)
+            if bc == "rect":
+                u = blur_adjoint(pre.inv(r, alpha_n), h, bc)
+            else:
+                u = pre.tikh(r, alpha_n)
+        z = z + framelet_analysis(u, levels)
+        f = framelet_synthesis(soft(z, mu), levels)
+        it += 1
+    return {"f": f, "z": z, "iters": it, "stop_iter": stop_iter,
+            "resnorms": resnorms, "alphas": alphas, "betas": betas}
+
+
+def rre(f_est: np.ndarray, f_true: np.ndarray) -> float:
+    """Relative restoration error ||f - f~|| / ||f||."""
+    return float(np.linalg.norm(f_est - f_true) / np.linalg.norm(f_true))
+
+
+def psnr(f_est: np.ndarray, f_true: np.ndarray) -> float:
+    """PSNR of Section 6 with peak 1 instead of 255 (reading c6):
+    20 log10(N / ||f - f~||) for N x N images."""
+    nn = f_true.shape[0]
+    return 20.0 * math.log10(nn / np.linalg.norm(f_est - f_true))

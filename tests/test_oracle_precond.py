@@ -1,0 +1,171 @@
+"""Pins of the oracle's preconditioners (Sections 4 and 5)."""
+import math
+
+import numpy as np
+import pytest
+
+import mlba_inputs as I
+from oracle import mlba_oracle as O
+from test_oracle_blur import dense_blur_matrix
+
+
+def dct_matrix(n):
+    """Orthonormal DCT-II from its cosine definition."""
+    k = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    d = np.sqrt(2.0 / n) * np.cos(np.pi * k * (2 * j + 1) / (2 * n))
+    d[0] /= np.sqrt(2.0)
+    return d
+
+
+def test_bccb_eigenvalues_are_dft_of_padded_psf():
+    """Section 2.2 / 4.1: the periodic-BC matrix is diagonalised by the 2-D
+    DFT; its eigenvalue for the Fourier mode k is the spectrum entry."""
+    h = I.psf_motion(5, 0.9)
+    n = 8
+    c = dense_blur_matrix(h, n, "periodic")
+    lam = O.spectrum_dft(h, n)
+    yy, xx = np.mgrid[0:n, 0:n]
+    for k1 in range(n):
+        for k2 in range(n):
+            v = np.exp(2j * np.pi * (k1 * yy + k2 * xx) / n).ravel()
+            np.testing.assert_allclose(c @ v, lam[k1, k2] * v, atol=1e-13)
+
+
+def test_reflective_matrix_diagonalised_by_dct():
+    """Section 2.2: reflective BC with a quadrantally symmetric PSF is
+    D^T diag(Lambda) D with D the orthonormal 2-D DCT-II."""
+    h = I.psf_disk(2)
+    n = 9
+    a = dense_blur_matrix(h, n, "reflective")
+    d1 = dct_matrix(n)
+    d = np.kron(d1, d1)
+    diag = d @ a @ d.T
+    lam = O.spectrum_dct(h, n)
+    np.testing.assert_allclose(diag, np.diag(lam.ravel()), atol=1e-13)
+    # closed form: Lambda(k1,k2) = sum_h h(dy,dx) cos(pi k1 dy/n) cos(pi k2 dx/n)
+    p = h.shape[0]
+    cc = (p - 1) // 2
+    k = np.arange(n)
+    closed = np.zeros((n, n))
+    for a_ in range(p):
+        for b_ in range(p):
+            closed += h[a_, b_] * np.outer(np.cos(np.pi * k * (a_ - cc) / n),
+                                           np.cos(np.pi * k * (b_ - cc) / n))
+    np.testing.assert_allclose(lam, closed, atol=1e-13)
+
+
+@pytest.mark.parametrize("transform,bc,psf", [
+    ("dft", "periodic", I.psf_motion(5, 0.3)),
+    ("dct", "reflective", I.psf_gaussian(1.1, 5)),
+])
+def test_spectral_precond_matches_dense(transform, bc, psf):
+    n = 8
+    c = dense_blur_matrix(psf, n, bc)
+    pre = O.SpectralPrecond(psf, n, transform)
+    alpha = 0.07
+    rng = np.random.default_rng(2)
+    r = rng.standard_normal((n, n))
+    m = np.linalg.inv(c @ c.T + alpha * np.eye(n * n))
+    np.testing.assert_allclose(pre.inv(r, alpha).ravel(), m @ r.ravel(), atol=1e-12)
+    np.testing.assert_allclose(pre.tikh(r, alpha).ravel(), c.T @ m @ r.ravel(), atol=1e-12)
+    np.testing.assert_allclose(pre.apply_C(r).ravel(), c @ r.ravel(), atol=1e-12)
+
+
+def test_symmetrize():
+    """Section 4.3: H~ is quadrantally symmetric, equals H for a symmetric H,
+    and is the Frobenius-nearest quadrantally symmetric PSF (orthogonal
+    projection: H - H~ is orthogonal to every symmetric S)."""
+    h = I.psf_motion(7, 0.4)
+    hs = O.symmetrize(h)
+    assert O.quadrantally_symmetric(hs)
+    assert not O.quadrantally_symmetric(h)
+    g = I.psf_gaussian(1.2, 7)
+    np.testing.assert_allclose(O.symmetrize(g), g, atol=1e-16)
+    rng = np.random.default_rng(0)
+    s = O.symmetrize(rng.standard_normal((7, 7)))
+    assert abs(np.vdot(h - hs, s)) < 1e-15
+    assert abs(hs.sum() - 1.0) < 1e-14
+
+
+def test_pcg_against_dense_solve():
+    """Section 4.2: PCG with enough steps solves (A A^T + alpha I) t = r."""
+    h = I.psf_motion(5, 1.3)
+    n = 7
+    a = dense_blur_matrix(h, n, "rect")
+    alpha = 0.02
+    pre = O.SpectralPrecond(h, n, "dft")
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal((n, n))
+    t, steps = O.pcg(r, lambda v: O.blur(O.blur_adjoint(v, h, "rect"), h, "rect"),
+                     lambda v: pre.inv(v, alpha), alpha, tol=1e-14, max_steps=200)
+    exact = np.linalg.solve(a @ a.T + alpha * np.eye(n * n), r.ravel())
+    np.testing.assert_allclose(t.ravel(), exact, atol=1e-10)
+    assert 1 <= steps <= n * n
+    # the cap beta_n <= 5 of Eq. bet
+    _, capped = O.pcg(r, lambda v: O.blur(O.blur_adjoint(v, h, "rect"), h, "rect"),
+                      lambda v: pre.inv(v, alpha), alpha, tol=1e-14, max_steps=5)
+    assert capped == 5
+
+
+def test_pcg_one_step_when_preconditioner_exact():
+    """With periodic BC, A = C and the preconditioner is exact: one step."""
+    h = I.psf_motion(5, 1.3)
+    n = 10
+    alpha = 0.03
+    pre = O.SpectralPrecond(h, n, "dft")
+    rng = np.random.default_rng(6)
+    r = rng.standard_normal((n, n))
+    t, steps = O.pcg(r, lambda v: O.blur(O.blur_adjoint(v, h, "periodic"), h, "periodic"),
+                     lambda v: pre.inv(v, alpha), alpha)
+    assert steps == 1
+    np.testing.assert_allclose(t, pre.inv(r, alpha), atol=1e-12)
+
+
+def test_ns_parameters():
+    """Algorithm 4-NS: tau = (1+2rho)/(1-2rho); q_n in [q, 1) while
+    ||r|| > tau delta."""
+    rho, q = 1e-4, 0.5
+    tau = O.ns_tau(rho)
+    assert abs(tau - (1 + 2e-4) / (1 - 2e-4)) < 1e-16
+    for tn in (tau * 1.0000001, 1.01, 1.5, 2.0, 10.0, 1e6):
+        qn = O.ns_qn(tn * 3.0, 3.0, q, rho)
+        assert q <= qn < 1.0
+    assert O.ns_qn(1e9, 1.0, q, rho) == q
+
+
+@pytest.mark.parametrize("transform,bc", [("dft", "periodic"), ("dct", "reflective")])
+def test_ns_alpha_solves_defining_equation(transform, bc):
+    """Eq. Alg4_rev_7 in the image domain with the dense C:
+    alpha ||(CC^T + alpha I)^{-1} r|| = q_n ||r||."""
+    h = I.psf_gaussian(1.4, 5)
+    n = 8
+    c = dense_blur_matrix(h, n, bc)
+    pre = O.SpectralPrecond(h, n, transform)
+    rng = np.random.default_rng(8)
+    r = rng.standard_normal((n, n))
+    for qn in (0.5, 0.8, 0.99):
+        a = O.ns_alpha(np.abs(pre.forward(r)) ** 2, pre.sigma, qn)
+        m = np.linalg.inv(c @ c.T + a * np.eye(n * n))
+        lhs = a * np.linalg.norm(m @ r.ravel())
+        assert abs(lhs - qn * np.linalg.norm(r)) <= 1e-12 * np.linalg.norm(r)
+    # unique root, increasing in q_n
+    a1 = O.ns_alpha(np.abs(pre.forward(r)) ** 2, pre.sigma, 0.6)
+    a2 = O.ns_alpha(np.abs(pre.forward(r)) ** 2, pre.sigma, 0.7)
+    assert a2 > a1
+
+
+def test_convergence_condition_workload_1():
+    """Eq. condconvalg1: ||K^T (CC^T+alpha I)^{-1} K|| < 1 at the alpha used by
+    the 64x64 rectangular FP64 workload (W^T W = I so the norm is that of
+    A^T P A).  Power iteration."""
+    pr = I.config(1)
+    pre = O.SpectralPrecond(pr.psf, pr.n, "dft")
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal((pr.nf, pr.nf))
+    lam = 0.0
+    for _ in range(150):
+        w = O.blur_adjoint(pre.inv(O.blur(v, pr.psf, "rect"), pr.alpha), pr.psf, "rect")
+        lam = np.linalg.norm(w) / np.linalg.norm(v)
+        v = w / np.linalg.norm(w)
+    assert lam < 1.0
