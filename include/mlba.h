@@ -1,0 +1,217 @@
+/*
+ * mlba.h — C ABI of the GB300 (sm_103a) library for the preconditioned
+ * modified linearized Bregman algorithm (MLBA) for frame-based image
+ * deblurring with reduced boundary artifacts (Cai, Donatelli, Bianchi,
+ * Huang, arXiv 1504.07234).
+ *
+ * The model is g = A f + eta (Section 1, Eq. modeld): an n x n observed image
+ * g, a p x p PSF (p odd, centred at ((p-1)/2, (p-1)/2)), noise norm
+ * delta = ||eta||.  A is either the rectangular n^2 x m^2 "valid" operator
+ * (m = n + p - 1, Section 2.1, Eq. Arect) or the square operator obtained by
+ * imposing zero / periodic / reflective boundary conditions (Section 2.2,
+ * Table 1).  One iteration (Eq. MLBA2 and Algorithms 1-4, 4-NS) is
+ *
+ *     r  = g - A f                                   (residual, FP64 norm)
+ *     stop when ||r|| <= gamma*delta (n > 0)  or  ||r|| <= tau*delta (4-NS)
+ *     t  = P r                                       (preconditioner)
+ *     u  = A^T t      (Algorithms 1-3)   or  u = C^T (CC^T+alpha I)^{-1} r (4)
+ *     z <- z + W u;   x = S_mu(z);   f = W^T x      (framelets, Section 6.1)
+ *
+ * Conventions
+ *  - Images are dense row-major arrays without padding: g, r, t are n x n;
+ *    f is N_f x N_f with N_f = m (rectangular A) or n (boundary conditions).
+ *  - The element type of images is double (MLBA_F64) or float (MLBA_F32),
+ *    chosen by mlba_opts.dtype.  The Bregman variable z is stored as
+ *    (8*levels + 1) planes of N_f x N_f in mlba_opts.z_store precision, band
+ *    order: the 8 high-pass bands (i,j) != (0,0) of level 1 in lexicographic
+ *    order, then level 2, ..., then the final low-pass band.
+ *  - "on_device" arguments: 1 = the pointer is device memory valid on the
+ *    context's stream, 0 = host memory (the call then synchronises).
+ *  - Every function returns MLBA_OK (0) or a negative status; nothing throws.
+ *  - All work is queued on mlba_opts.stream (a cudaStream_t; NULL makes the
+ *    library create and own a non-blocking stream, because the legacy
+ *    default stream cannot be captured into a CUDA graph).  The library owns
+ *    the device memory it allocates at create time (cudaMalloc) and frees it
+ *    at destroy.
+ *  - Calls on one context or batch are not thread-safe; distinct contexts
+ *    are independent.
+ */
+#ifndef MLBA_H
+#define MLBA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define MLBA_OK            0
+#define MLBA_E_INVAL      (-1)  /* bad argument (p even, p > n, alpha <= 0, Algorithm 4 with rectangular A, ...) */
+#define MLBA_E_NOMEM      (-2)  /* device or host allocation failed */
+#define MLBA_E_CUDA       (-3)  /* a CUDA runtime call failed */
+#define MLBA_E_TIMEOUT    (-4)  /* a bounded device-side wait expired */
+#define MLBA_E_DIVERGED   (-5)  /* ||r|| became NaN or Inf */
+#define MLBA_E_STATE      (-6)  /* call out of order (e.g. iterate before set_data) */
+#define MLBA_E_UNSUPPORTED (-7) /* size not supported (FFT length must be 2^a 3^b 5^c) */
+
+/* ---- enumerations ---------------------------------------------------- */
+enum mlba_bc {                 /* Section 2, Table 1 */
+  MLBA_BC_ZERO = 0,            /* Dirichlet: zero outside the field of view */
+  MLBA_BC_PERIODIC = 1,        /* A is BCCB */
+  MLBA_BC_REFLECTIVE = 2,      /* fliplr / flipud mirror (Neumann) */
+  MLBA_RECT = 3                /* rectangular n^2 x m^2 valid operator, Eq. Arect */
+};
+
+enum mlba_precond {            /* Sections 3-5 */
+  MLBA_P_NONE = 0,             /* P = I: linearized Bregman, Eq. iterLinBreg (lambda = 1) */
+  MLBA_P_BCCB = 1,             /* Algorithm 1: P = (CC^T + alpha I)^{-1}, Eq. Alg1 */
+  MLBA_P_KRYLOV = 2,           /* Algorithm 2: PCG for (AA^T + alpha I) t = r, Eqs. syscg, psys, bet */
+  MLBA_P_SYM = 3,              /* Algorithm 3: Q from the symmetrised PSF, Eq. Alg3 */
+  MLBA_P_TIKH = 4,             /* Algorithm 4: z += W C^T (CC^T + alpha I)^{-1} r, Eq. Alg4 */
+  MLBA_P_TIKH_NS = 5           /* Algorithm 4-NS: alpha_n from Eq. Alg4_rev_7 */
+};
+
+enum mlba_dtype { MLBA_F32 = 0, MLBA_F64 = 1, MLBA_BF16 = 2 };
+
+enum mlba_transform {          /* diagonalising transform of C (Section 4.1) */
+  MLBA_TR_AUTO = 0,            /* DCT for a quadrantally symmetric PSF, else DFT */
+  MLBA_TR_DFT = 1,             /* C = periodic-BC (Strang) matrix */
+  MLBA_TR_DCT = 2              /* C = reflective-BC matrix; PSF must be quadrantally symmetric */
+};
+
+/* ---- options --------------------------------------------------------- */
+typedef struct mlba_opts {
+  double mu;          /* soft-threshold parameter, Eq. soft */
+  double alpha;       /* regularisation of P (Algorithms 1-4); floor of alpha_n for the rectangular 4-NS hybrid */
+  double gamma;       /* discrepancy factor of Eq. discrpr (default 1 + 1e-15) */
+  double q;           /* Algorithm 4-NS safeguard q in (2 rho, 1) (default 0.5) */
+  double rho;         /* Algorithm 4-NS rho in (0, 1/2) (default 1e-4) */
+  double pcg_tol;     /* Algorithm 2 relative tolerance (default 1e-3) */
+  int levels;         /* framelet levels L >= 1; z has 8L+1 bands */
+  int max_iter;       /* iteration budget */
+  int pcg_max;        /* Algorithm 2 cap on PCG steps (default 5, Eq. bet) */
+  int dtype;          /* MLBA_F32 or MLBA_F64 */
+  int z_store;        /* MLBA_F32 or MLBA_BF16 with F32; MLBA_F64 with F64 */
+  int transform;      /* enum mlba_transform */
+  int stop;           /* 1: stop on the discrepancy principle; 0: run max_iter iterations */
+  int rect_ns_hybrid; /* 1: allow MLBA_P_TIKH_NS with MLBA_RECT (A^T (CC^T + alpha_n I)^{-1}) */
+  void* stream;       /* cudaStream_t */
+} mlba_opts;
+
+/* Fill defaults: mu = 10/255, alpha = 0.05, gamma = 1 + 1e-15, q = 0.5,
+ * rho = 1e-4, pcg_tol = 1e-3, levels = 1, max_iter = 200, pcg_max = 5,
+ * dtype = F32, z_store = F32, transform = AUTO, stop = 1, hybrid = 0,
+ * stream = NULL. */
+void mlba_opts_default(mlba_opts* o);
+
+/* ---- statistics ------------------------------------------------------- */
+typedef struct mlba_stats {
+  int iter;           /* z-updates done; the current f is f^iter */
+  int stopped;        /* 1 once the context stopped (rule fired, budget used, or diverged) */
+  int stop_iter;      /* first n at which the discrepancy rule held, -1 if never */
+  int status;         /* MLBA_OK or MLBA_E_DIVERGED */
+  double resnorm;     /* ||r^k|| of the last residual computed */
+  double alpha_n;     /* last alpha used (alpha_n for 4-NS) */
+  int beta_n;         /* last PCG step count (Algorithm 2) */
+  int nres;           /* residuals computed so far (history length) */
+} mlba_stats;
+
+/* ---- single problem --------------------------------------------------- */
+typedef struct mlba_ctx mlba_ctx;
+
+/* Create a context for one problem.  psf: host, p*p doubles, row-major,
+ * nonnegative; the library copies it.  n: observed size (n >= p).
+ * Validates the combination (Algorithm 4 needs a square A, Section 5), builds
+ * the PSF tap list and its rank-one test, the FFT plans for length n and the
+ * spectrum of C / Q in FP64 on the device (Section 4.1, 4.3), allocates all
+ * device buffers and captures one iteration into a CUDA graph.
+ * Errors: MLBA_E_INVAL, MLBA_E_UNSUPPORTED, MLBA_E_NOMEM, MLBA_E_CUDA. */
+int mlba_create(const double* psf, int p, int n, int bc, int precond,
+                const mlba_opts* opts, mlba_ctx** out);
+
+/* Upload g (n x n, dtype of the context) and the noise level delta, and
+ * reset the iteration (z = 0, f = 0, counters cleared). */
+int mlba_set_data(mlba_ctx* ctx, const void* g, int g_on_device, double delta);
+
+/* Queue k steps on the stream.  A step computes r^n = g - A f^n and its FP64
+ * norm, applies the stop rule, and (unless stopped) performs the update to
+ * z^{n+1}, f^{n+1}.  Once stopped, further steps do nothing.  Asynchronous. */
+int mlba_iterate(mlba_ctx* ctx, int k);
+
+/* Copy f (N_f x N_f, dtype of the context) out.  Host destination: syncs. */
+int mlba_result(mlba_ctx* ctx, void* f_out, int on_device);
+
+/* Synchronise the stream and read the counters. */
+int mlba_stats_get(mlba_ctx* ctx, mlba_stats* st);
+
+/* Residual-norm (and alpha_n, beta_n) history, up to cap entries each (host
+ * arrays; any may be NULL).  Returns the number of entries written. */
+int mlba_history(mlba_ctx* ctx, double* resnorm, double* alpha, int* beta, int cap);
+
+/* Copy the Bregman variable z out / in ((8L+1) x N_f x N_f, z_store type). */
+int mlba_get_z(mlba_ctx* ctx, void* z_out, int on_device);
+
+void mlba_destroy(mlba_ctx* ctx);
+const char* mlba_strerror(int status);
+
+/* ---- operator entry points (one kernel pass each, on a context) ------------
+ * All arrays are in the context dtype; on_device as above. */
+/* out = A f   (f: N_f x N_f, out: n x n)  Section 2, Table 1, Eq. Arect. */
+int mlba_op_blur(mlba_ctx* ctx, const void* f, void* out, int on_device);
+/* out = A^T t (t: n x n, out: N_f x N_f)  exact transpose of mlba_op_blur. */
+int mlba_op_blur_adjoint(mlba_ctx* ctx, const void* t, void* out, int on_device);
+/* out = (CC^T + alpha I)^{-1} r (which = 0, Eq. Alg1/Alg3) or
+ * C^T (CC^T + alpha I)^{-1} r (which = 1, Eq. Alg4); r, out: n x n.
+ * Uses the context's C (DFT or DCT) through the batched transform kernels. */
+int mlba_op_precond(mlba_ctx* ctx, const void* r, void* out, double alpha, int which, int on_device);
+/* One fused framelet pass: z_out = z_in + W u, f = W^T S_mu(z_out)
+ * (Eq. MLBA2 second half; Section 6.1).  z_*: z_store type; u, f: N_f x N_f. */
+int mlba_op_frame(mlba_ctx* ctx, const void* z_in, const void* u, void* z_out,
+                  void* f, double mu, int on_device);
+/* alpha solving alpha ||(CC^T + alpha I)^{-1} r|| = qn ||r|| (Eq. Alg4_rev_7);
+ * r: n x n; result written to *alpha_out (host). */
+int mlba_op_ns_alpha(mlba_ctx* ctx, const void* r, double qn, double* alpha_out, int on_device);
+/* Spectrum of C (or Q) as the library stores it: DFT: n x (n/2+1) complex
+ * (interleaved re, im doubles), DCT: n x n doubles.  Host output. */
+int mlba_op_spectrum(mlba_ctx* ctx, double* out, int* rows, int* cols, int* is_complex);
+
+/* ---- batch of independent problems (one graph launch per step) ---------- */
+typedef struct mlba_problem {
+  const double* psf;  /* host p*p */
+  int p, n, bc, precond, transform, max_iter;
+  double mu, alpha, delta;
+  const void* g;      /* n x n in the batch dtype */
+  int g_on_device;
+} mlba_problem;
+
+typedef struct mlba_batch mlba_batch;
+
+/* Problems share opts.dtype, z_store, levels, stop, gamma, q, rho, pcg_*,
+ * stream; each has its own size, PSF, BC, preconditioner, mu, alpha, delta
+ * and budget.  Each problem stops on its own rule. */
+int mlba_batch_create(const mlba_problem* probs, int count, const mlba_opts* opts, mlba_batch** out);
+int mlba_batch_iterate(mlba_batch* b, int k);
+/* Number of problems not yet stopped (synchronises). */
+int mlba_batch_active(mlba_batch* b, int* n_active);
+int mlba_batch_result(mlba_batch* b, int i, void* f_out, int on_device);
+int mlba_batch_stats(mlba_batch* b, int i, mlba_stats* st);
+/* Re-arm every problem: z = 0, f = 0, counters cleared (data kept). */
+int mlba_batch_reset(mlba_batch* b);
+/* Replace problem i's observed image g (n x n, batch dtype) and delta; the
+ * iteration state is left as it is (call mlba_batch_reset to restart).
+ * Host source: synchronises. */
+int mlba_batch_set_data(mlba_batch* b, int i, const void* g, int g_on_device, double delta);
+/* Time one stage of the step on the batch stream with CUDA events: stage 0 =
+ * the whole captured step (graph launch), 1 = residual stencil, 2 =
+ * spectral preconditioner passes, 3 = adjoint correlation, 4 = fused
+ * framelet kernel.  Launches it `reps` times and writes the mean time per
+ * launch in milliseconds.  Stages 1-4 run outside the graph and advance the
+ * per-problem state arbitrarily: call mlba_batch_reset before using results. */
+int mlba_batch_profile(mlba_batch* b, int stage, int reps, float* ms_per_rep);
+/* Number of kernel nodes in the captured step graph. */
+int mlba_batch_graph_kernels(mlba_batch* b, int* n_kernels);
+void mlba_batch_destroy(mlba_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLBA_H */

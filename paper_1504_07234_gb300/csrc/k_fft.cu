@@ -1,0 +1,638 @@
+// k_fft.cu — the regularising preconditioners of Sections 4 and 5 applied
+// through batched two-pass 2-D transforms.
+//
+//   t = T^{-1} [ w(k) * T r ]      (T = 2-D DFT or 2-D DCT-II)
+//   w = 1/(sigma + alpha)          (Eq. Alg1, Alg3; M in Algorithm 2)
+//   w = conj(lambda)/(sigma+alpha) (Eq. Alg4, Algorithm 4-NS)
+//
+// Pass 1 (rows): two real rows are packed into one complex FFT; DFT keeps the
+// half spectrum, DCT-II uses the even/odd reordering of the input so that
+// X[k] = Re(exp(-i pi k / 2n) V[k]) with V the DFT of the reordered row.
+// Pass 2 (columns): forward, weight, inverse on columns held in shared memory
+// (for 4-NS the forward spectrum is kept for the alpha_n solve and the weight
+// and inverse run after it).  Pass 3 (rows): inverse.  The unnormalised
+// forward / inverse pair gives n^2 times the result; 1/n^2 is folded into the
+// weight.  Weights are formed with an FP64 denominator sigma + alpha.
+//
+// The 1-D FFT is a Stockham autosort FFT in shared memory with radix 2, 3,
+// 4 and 5 stages; each stage loads all butterfly inputs of a thread into
+// registers, synchronises, and stores in place.
+#include "mlba_internal.cuh"
+#include "mlba_launch.h"
+
+namespace mlba {
+
+// ---------------------------------------------------------------------------
+// small DFTs (forward: exp(-2 pi i jk/R); INV: conjugate)
+template <typename T2, bool INV>
+__device__ __forceinline__ void dft2(T2* v) {
+  T2 a = v[0], b = v[1];
+  v[0] = cadd(a, b); v[1] = csub(a, b);
+}
+template <typename T2, bool INV>
+__device__ __forceinline__ void dft4(T2* v) {
+  T2 a = v[0], b = v[1], c = v[2], d = v[3];
+  T2 s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(b, d), s3 = csub(b, d);
+  // -i * s3 (forward) or +i * s3 (inverse)
+  T2 js3;
+  if (INV) { js3.x = -s3.y; js3.y = s3.x; } else { js3.x = s3.y; js3.y = -s3.x; }
+  v[0] = cadd(s0, s2); v[2] = csub(s0, s2);
+  v[1] = cadd(s1, js3); v[3] = csub(s1, js3);
+}
+template <typename T2, bool INV>
+__device__ __forceinline__ void dft3(T2* v) {
+  using T = decltype(v[0].x);
+  const T h = T(0.86602540378443864676);   // sin(2 pi / 3)
+  T2 a = v[0], b = v[1], c = v[2];
+  T2 t1 = cadd(b, c), t2 = csub(b, c);
+  T2 m; m.x = a.x - T(0.5) * t1.x; m.y = a.y - T(0.5) * t1.y;
+  // forward: X1 = m - i h t2, X2 = m + i h t2
+  T2 ih; ih.x = -h * t2.y; ih.y = h * t2.x;   // i h t2
+  v[0] = cadd(a, t1);
+  if (INV) { v[1] = cadd(m, ih); v[2] = csub(m, ih); }
+  else { v[1] = csub(m, ih); v[2] = cadd(m, ih); }
+}
+template <typename T2, bool INV>
+__device__ __forceinline__ void dft5(T2* v) {
+  using T = decltype(v[0].x);
+  const T c1 = T(0.30901699437494742410);   // cos(2 pi/5)
+  const T c2 = T(-0.80901699437494742410);  // cos(4 pi/5)
+  const T s1 = T(0.95105651629515357212);   // sin(2 pi/5)
+  const T s2 = T(0.58778525229247312917);   // sin(4 pi/5)
+  T2 a = v[0];
+  T2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  T2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  T2 m1, m2, n1, n2;
+  m1.x = a.x + c1 * t1.x + c2 * t2.x; m1.y = a.y + c1 * t1.y + c2 * t2.y;
+  m2.x = a.x + c2 * t1.x + c1 * t2.x; m2.y = a.y + c2 * t1.y + c1 * t2.y;
+  // n1 = s1 t3 + s2 t4 ; n2 = s2 t3 - s1 t4
+  n1.x = s1 * t3.x + s2 * t4.x; n1.y = s1 * t3.y + s2 * t4.y;
+  n2.x = s2 * t3.x - s1 * t4.x; n2.y = s2 * t3.y - s1 * t4.y;
+  // i * n
+  T2 in1, in2; in1.x = -n1.y; in1.y = n1.x; in2.x = -n2.y; in2.y = n2.x;
+  v[0] = cadd(a, cadd(t1, t2));
+  if (INV) {
+    v[1] = cadd(m1, in1); v[4] = csub(m1, in1);
+    v[2] = cadd(m2, in2); v[3] = csub(m2, in2);
+  } else {
+    v[1] = csub(m1, in1); v[4] = cadd(m1, in1);
+    v[2] = csub(m2, in2); v[3] = cadd(m2, in2);
+  }
+}
+
+template <typename T2, int R, bool INV>
+__device__ __forceinline__ void dft_small(T2* v) {
+  if (R == 2) dft2<T2, INV>(v);
+  else if (R == 3) dft3<T2, INV>(v);
+  else if (R == 4) dft4<T2, INV>(v);
+  else dft5<T2, INV>(v);
+}
+
+// one Stockham stage over G transforms of length N stored back to back
+template <typename T2, int R, bool INV>
+__device__ __forceinline__ void fft_stage(T2* sm, int G, int N, int Ns, const T2* __restrict__ tw) {
+  constexpr int MAXV = (sizeof(T2) == 16) ? TR_MAXV_F64 : TR_MAXV;
+  constexpr int MAXB = (MAXV + R - 1) / R;
+  const int per = N / R;
+  const int nbf = G * per;
+  const int step = N / (Ns * R);
+  T2 v[MAXB][R];
+#pragma unroll
+  for (int q = 0; q < MAXB; ++q) {
+    const int b = threadIdx.x + q * TR_THREADS;
+    if (b < nbf) {
+      const int g = b / per, j = b - g * per;
+      const int k = j % Ns;
+      const T2* base = sm + g * N;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = base[j + r * per];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          T2 w = __ldg(&tw[r * k * step]);
+          if (INV) w.y = -w.y;
+          v[q][r] = cmul(v[q][r], w);
+        }
+      }
+      dft_small<T2, R, INV>(v[q]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < MAXB; ++q) {
+    const int b = threadIdx.x + q * TR_THREADS;
+    if (b < nbf) {
+      const int g = b / per, j = b - g * per;
+      const int k = j % Ns;
+      T2* base = sm + g * N + (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[r * Ns] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T2, bool INV>
+__device__ __forceinline__ void fft_smem(T2* sm, int G, const Prob& pd) {
+  const int N = pd.n;
+  const T2* tw = static_cast<const T2*>(pd.tw);
+  int Ns = 1;
+  for (int s = 0; s < pd.nstage; ++s) {
+    const int R = pd.radix[s];
+    if (R == 4) fft_stage<T2, 4, INV>(sm, G, N, Ns, tw);
+    else if (R == 2) fft_stage<T2, 2, INV>(sm, G, N, Ns, tw);
+    else if (R == 3) fft_stage<T2, 3, INV>(sm, G, N, Ns, tw);
+    else fft_stage<T2, 5, INV>(sm, G, N, Ns, tw);
+    Ns *= R;
+  }
+}
+
+// position of input sample y in the DCT reordering v[j] = x[2j], v[N-1-j] = x[2j+1]
+__device__ __forceinline__ int dct_pos(int y, int N) {
+  return (y & 1) ? N - 1 - (y >> 1) : (y >> 1);
+}
+// inverse: sample stored at position j of v
+__device__ __forceinline__ int dct_src(int j, int N) {
+  return (j < (N + 1) / 2) ? 2 * j : 2 * (N - 1 - j) + 1;
+}
+
+// After a forward FFT of (a + i b) (two reordered real sequences): DCT-II of
+// both, X[k] = Re(exp(-i pi k/2N) V[k]); results stored as (Xa, Xb) at k.
+// Positions k and N-k depend only on each other, so one thread owns the pair
+// and updates it in place.
+template <typename T, typename T2>
+__device__ __forceinline__ T2 split_one(T2 Z, T2 Zr, T2 d) {
+  // Va = (Z + conj Zr)/2, Vb = (Z - conj Zr)/(2i), X = Re(d V)
+  T2 va, vb, o;
+  va.x = T(0.5) * (Z.x + Zr.x); va.y = T(0.5) * (Z.y - Zr.y);
+  vb.x = T(0.5) * (Z.y + Zr.y); vb.y = T(-0.5) * (Z.x - Zr.x);
+  o.x = d.x * va.x - d.y * va.y;
+  o.y = d.x * vb.x - d.y * vb.y;
+  return o;
+}
+template <typename T, typename T2>
+__device__ __forceinline__ void dct_split(T2* sm, int G, int N, const T2* __restrict__ dtw) {
+  const int np = N / 2 + 1;
+  for (int e = threadIdx.x; e < G * np; e += TR_THREADS) {
+    const int g = e / np, k = e - g * np;
+    const int kr = (k == 0) ? 0 : N - k;
+    T2* b = sm + g * N;
+    const T2 Z = b[k], Zr = b[kr];
+    const T2 ok = split_one<T, T2>(Z, Zr, __ldg(&dtw[k]));
+    if (kr != k) b[kr] = split_one<T, T2>(Zr, Z, __ldg(&dtw[kr]));
+    b[k] = ok;
+  }
+  __syncthreads();
+}
+
+// Inverse of dct_split: from (Xa, Xb) at k build Z = Va + i Vb with
+// V[k] = exp(+i pi k/2N) (X[k] - i X[N-k]), X[N] = 0, ready for an inverse FFT.
+template <typename T, typename T2>
+__device__ __forceinline__ T2 merge_one(T2 X, T2 Xr, T2 d) {
+  d.y = -d.y;                               // exp(+i pi k/2N)
+  T2 wa, wb;
+  wa.x = X.x; wa.y = -Xr.x;
+  wb.x = X.y; wb.y = -Xr.y;
+  const T2 va = cmul(d, wa), vb = cmul(d, wb);
+  T2 o; o.x = va.x - vb.y; o.y = va.y + vb.x;   // Va + i Vb
+  return o;
+}
+template <typename T, typename T2>
+__device__ __forceinline__ void dct_merge(T2* sm, int G, int N, const T2* __restrict__ dtw) {
+  const int np = N / 2 + 1;
+  for (int e = threadIdx.x; e < G * np; e += TR_THREADS) {
+    const int g = e / np, k = e - g * np;
+    T2* b = sm + g * N;
+    const T2 X = b[k];
+    T2 Xr;
+    if (k == 0) { Xr.x = T(0); Xr.y = T(0); } else Xr = b[N - k];
+    const T2 ok = merge_one<T, T2>(X, Xr, __ldg(&dtw[k]));
+    if (k != 0 && N - k != k) b[N - k] = merge_one<T, T2>(Xr, X, __ldg(&dtw[N - k]));
+    b[k] = ok;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool tr_skip(const State& st, int pcg) {
+  return st.stopped || (pcg && st.pdone);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: forward transform of row pairs: src (n x n real) -> S
+template <typename T>
+__global__ void __launch_bounds__(TR_THREADS, 1)
+k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+           int src_slot, int pcg) {
+  using T2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  if (tr_skip(states[item.x], pcg)) return;
+  const int N = pd.n, G = pd.row_g;
+  const int pair0 = item.y * G;
+  const bool dct = (pd.transform == TR_DCT);
+  const T* src = static_cast<const T*>(pd.buf[src_slot]);
+  for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+    const int g = e / N, x = e - g * N;
+    const int ra = 2 * (pair0 + g), rb = ra + 1;
+    const int xs = dct ? dct_src(x, N) : x;
+    T2 v;
+    v.x = (ra < N) ? src[(size_t)ra * N + xs] : T(0);
+    v.y = (rb < N) ? src[(size_t)rb * N + xs] : T(0);
+    sm[e] = v;
+  }
+  __syncthreads();
+  fft_smem<T2, false>(sm, G, pd);
+  if (dct) {
+    dct_split<T, T2>(sm, G, N, static_cast<const T2*>(pd.dtw));
+    T* S = static_cast<T*>(pd.buf[SL_S]);
+    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+      const int g = e / N, k = e - g * N;
+      const int ra = 2 * (pair0 + g), rb = ra + 1;
+      const T2 X = sm[e];
+      if (ra < N) S[(size_t)ra * N + k] = X.x;
+      if (rb < N) S[(size_t)rb * N + k] = X.y;
+    }
+  } else {
+    const int H = pd.half;
+    T2* S = static_cast<T2*>(pd.buf[SL_S]);
+    for (int e = threadIdx.x; e < G * H; e += TR_THREADS) {
+      const int g = e / H, k = e - g * H;
+      const int ra = 2 * (pair0 + g), rb = ra + 1;
+      const T2 Z = sm[g * N + k];
+      const T2 Zr = sm[g * N + (k == 0 ? 0 : N - k)];
+      T2 xa, xb;
+      xa.x = T(0.5) * (Z.x + Zr.x); xa.y = T(0.5) * (Z.y - Zr.y);
+      xb.x = T(0.5) * (Z.y + Zr.y); xb.y = T(-0.5) * (Z.x - Zr.x);
+      if (ra < N) S[(size_t)ra * H + k] = xa;
+      if (rb < N) S[(size_t)rb * H + k] = xb;
+    }
+  }
+}
+
+// spectral weight at (k1, col); alpha and kind as given
+template <typename T, typename T2>
+__device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, double alpha, int kind) {
+  const double d = pd.sigma[idx] + alpha;                 // FP64 denominator
+  const double scale = 1.0 / ((double)pd.n * (double)pd.n);
+  T2 w;
+  if (sizeof(T) == 8) {
+    const double inv = scale / d;
+    if (kind == W_TIKH) {
+      const T2 l = static_cast<const T2*>(pd.lam)[idx];
+      w.x = T(l.x * inv); w.y = T(-l.y * inv);
+    } else { w.x = T(inv); w.y = T(0); }
+  } else {
+    const T inv = T(1) / T(d * ((double)pd.n * (double)pd.n));
+    if (kind == W_TIKH) {
+      const T2 l = static_cast<const T2*>(pd.lam)[idx];
+      w.x = l.x * inv; w.y = -l.y * inv;
+    } else { w.x = inv; w.y = T(0); }
+  }
+  return w;
+}
+template <typename T>
+__device__ __forceinline__ T weight_dct(const Prob& pd, size_t idx, double alpha, int kind) {
+  const double d = pd.sigma[idx] + alpha;
+  const double nn = (double)pd.n * (double)pd.n;
+  if (sizeof(T) == 8) {
+    const double inv = 1.0 / (d * nn);
+    return kind == W_TIKH ? T(static_cast<const T*>(pd.lam)[idx] * inv) : T(inv);
+  } else {
+    const T inv = T(1) / T(d * nn);
+    return kind == W_TIKH ? static_cast<const T*>(pd.lam)[idx] * inv : inv;
+  }
+}
+
+// Pass 2: columns.  DFT: G complex columns of S (n x half).  DCT: G pairs of
+// real columns of S (n x n).
+template <typename T>
+__global__ void __launch_bounds__(TR_THREADS, 1)
+k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+       int mode, int pcg, double op_alpha, int op_kind) {
+  using T2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  const State& st = states[item.x];
+  if (tr_skip(st, pcg)) return;
+  if (mode == COL_NS_INV && !pd.ns) return;
+  const int N = pd.n, G = pd.col_g;
+  const bool dct = (pd.transform == TR_DCT);
+  // weight parameters
+  double alpha = pd.alpha;
+  int kind = (pd.precond == P_TIKH || pd.precond == P_TIKH_NS) && pd.bc != BC_RECT ? W_TIKH : W_INV;
+  if (mode == COL_NS_INV) alpha = st.alpha_n;
+  if (mode == COL_OP) { alpha = op_alpha; kind = op_kind; }
+  if (pd.precond == P_KRYLOV) kind = W_INV;
+
+  if (!dct) {
+    const int H = pd.half;
+    const int k0 = item.y * G;
+    T2* S = static_cast<T2*>(pd.buf[SL_S]);
+    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+      const int y = e / G, g = e - y * G;
+      const int col = k0 + g;
+      T2 v; v.x = T(0); v.y = T(0);
+      if (col < H) v = S[(size_t)y * H + col];
+      sm[g * N + y] = v;
+    }
+    __syncthreads();
+    if (mode != COL_NS_INV) fft_smem<T2, false>(sm, G, pd);
+    if (mode == COL_FWD) {
+      for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+        const int y = e / G, g = e - y * G;
+        const int col = k0 + g;
+        if (col < H) S[(size_t)y * H + col] = sm[g * N + y];
+      }
+      return;
+    }
+    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+      const int g = e / N, k1 = e - g * N;
+      const int col = k0 + g;
+      if (col < H) sm[e] = cmul(sm[e], weight_dft<T, T2>(pd, (size_t)k1 * H + col, alpha, kind));
+    }
+    __syncthreads();
+    fft_smem<T2, true>(sm, G, pd);
+    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+      const int y = e / G, g = e - y * G;
+      const int col = k0 + g;
+      if (col < H) S[(size_t)y * H + col] = sm[g * N + y];
+    }
+  } else {
+    const int k0 = item.y * 2 * G;          // first real column
+    T* S = static_cast<T*>(pd.buf[SL_S]);
+    T* smr = reinterpret_cast<T*>(sm);
+    for (int e = threadIdx.x; e < 2 * G * N; e += TR_THREADS) {
+      const int y = e / (2 * G), cc = e - y * (2 * G);
+      const int col = k0 + cc;
+      const T v = (col < N) ? S[(size_t)y * N + col] : T(0);
+      const int g = cc >> 1;
+      const int pos = (mode == COL_NS_INV) ? y : dct_pos(y, N);
+      smr[2 * (g * N + pos) + (cc & 1)] = v;
+    }
+    __syncthreads();
+    const T2* dtw = static_cast<const T2*>(pd.dtw);
+    if (mode != COL_NS_INV) {
+      fft_smem<T2, false>(sm, G, pd);
+      dct_split<T, T2>(sm, G, N, dtw);
+    }
+    if (mode == COL_FWD) {
+      for (int e = threadIdx.x; e < 2 * G * N; e += TR_THREADS) {
+        const int y = e / (2 * G), cc = e - y * (2 * G);
+        const int col = k0 + cc;
+        if (col < N) S[(size_t)y * N + col] = smr[2 * ((cc >> 1) * N + y) + (cc & 1)];
+      }
+      return;
+    }
+    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+      const int g = e / N, k1 = e - g * N;
+      const int ca = k0 + 2 * g, cb = ca + 1;
+      T2 v = sm[e];
+      v.x *= (ca < N) ? weight_dct<T>(pd, (size_t)k1 * N + ca, alpha, kind) : T(0);
+      v.y *= (cb < N) ? weight_dct<T>(pd, (size_t)k1 * N + cb, alpha, kind) : T(0);
+      sm[e] = v;
+    }
+    __syncthreads();
+    dct_merge<T, T2>(sm, G, N, dtw);
+    fft_smem<T2, true>(sm, G, pd);
+    for (int e = threadIdx.x; e < 2 * G * N; e += TR_THREADS) {
+      const int y = e / (2 * G), cc = e - y * (2 * G);
+      const int col = k0 + cc;
+      if (col < N) S[(size_t)y * N + col] = smr[2 * ((cc >> 1) * N + dct_pos(y, N)) + (cc & 1)];
+    }
+  }
+}
+
+// Pass 3: inverse transform of row pairs: S -> dst (n x n real)
+template <typename T>
+__global__ void __launch_bounds__(TR_THREADS, 1)
+k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+           int dst_slot, int pcg) {
+  using T2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  if (tr_skip(states[item.x], pcg)) return;
+  const int N = pd.n, G = pd.row_g;
+  const int pair0 = item.y * G;
+  const bool dct = (pd.transform == TR_DCT);
+  if (dct) {
+    const T* S = static_cast<const T*>(pd.buf[SL_S]);
+    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+      const int g = e / N, k = e - g * N;
+      const int ra = 2 * (pair0 + g), rb = ra + 1;
+      T2 v;
+      v.x = (ra < N) ? S[(size_t)ra * N + k] : T(0);
+      v.y = (rb < N) ? S[(size_t)rb * N + k] : T(0);
+      sm[e] = v;
+    }
+    __syncthreads();
+    dct_merge<T, T2>(sm, G, N, static_cast<const T2*>(pd.dtw));
+  } else {
+    const int H = pd.half;
+    const T2* S = static_cast<const T2*>(pd.buf[SL_S]);
+    const bool even = (N & 1) == 0;
+    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+      const int g = e / N, k = e - g * N;
+      const int ra = 2 * (pair0 + g), rb = ra + 1;
+      T2 xa, xb;
+      xa.x = xa.y = xb.x = xb.y = T(0);
+      if (k < H) {
+        if (ra < N) xa = S[(size_t)ra * H + k];
+        if (rb < N) xb = S[(size_t)rb * H + k];
+      } else {
+        if (ra < N) xa = cconj(S[(size_t)ra * H + (N - k)]);
+        if (rb < N) xb = cconj(S[(size_t)rb * H + (N - k)]);
+      }
+      if (k == 0 || (even && k == N / 2)) { xa.y = T(0); xb.y = T(0); }
+      T2 z; z.x = xa.x - xb.y; z.y = xa.y + xb.x;   // Xa + i Xb
+      sm[e] = z;
+    }
+    __syncthreads();
+  }
+  fft_smem<T2, true>(sm, G, pd);
+  T* dst = static_cast<T*>(pd.buf[dst_slot]);
+  for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+    const int g = e / N, x = e - g * N;
+    const int ra = 2 * (pair0 + g), rb = ra + 1;
+    const T2 v = dct ? sm[g * N + dct_pos(x, N)] : sm[e];
+    if (ra < N) dst[(size_t)ra * N + x] = v.x;
+    if (rb < N) dst[(size_t)rb * N + x] = v.y;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 4-NS: one Newton pass for alpha_n on log(alpha).  With a unitary
+// transform, Eq. Alg4_rev_7 reads F(a)/P = q_n^2 with P = sum |r^|^2,
+// F(a) = sum |r^|^2 (a/(s+a))^2; d F / d log a = sum 2 |r^|^2 x^2 (1-x),
+// x = a/(s+a).  The spectrum in S is the unnormalised one; the ratio is
+// scale free once each coefficient carries its orthonormal weight.  Each block sums its share; the last block takes the step.
+template <typename T>
+__global__ void __launch_bounds__(SPEC_THREADS)
+k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items) {
+  using T2 = typename Vec2<T>::type;
+  __shared__ double red[32];
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  State& st = states[item.x];
+  if (st.stopped || !pd.ns || !st.ns_active || st.nconv) return;
+  const int N = pd.n;
+  const bool dct = (pd.transform == TR_DCT);
+  const int W = dct ? N : pd.half;
+  const size_t tot = (size_t)N * W;
+  const size_t chunk = (size_t)SPEC_THREADS * SPEC_PER_THREAD;
+  const size_t beg = (size_t)item.y * chunk;
+  const size_t end = beg + chunk < tot ? beg + chunk : tot;
+  const double alpha = exp(st.nb);
+  T sP = T(0), sF = T(0), sG = T(0);
+  for (size_t i = beg + threadIdx.x; i < end; i += SPEC_THREADS) {
+    T pw;
+    if (dct) {
+      // unnormalised DCT-II: |orthonormal coefficient|^2 = v^2 s_k1^2 s_k2^2
+      // with s_0^2 = 1/N and s_k^2 = 2/N; the common 1/N^2 cancels
+      const T v = static_cast<const T*>(pd.buf[SL_S])[i];
+      const int k1 = (int)(i / W), k2 = (int)(i - (size_t)k1 * W);
+      const T m = T((k1 == 0 ? 1 : 2) * (k2 == 0 ? 1 : 2));
+      pw = m * v * v;
+    } else {
+      const T2 v = static_cast<const T2*>(pd.buf[SL_S])[i];
+      const int k2 = (int)(i % W);
+      const T m = (k2 == 0 || ((N & 1) == 0 && k2 == N / 2)) ? T(1) : T(2);
+      pw = m * (v.x * v.x + v.y * v.y);
+    }
+    const double d = pd.sigma[i] + alpha;       // FP64 denominator
+    const T x = (sizeof(T) == 8) ? T(alpha / d) : T(alpha) / T(d);
+    const T x2 = x * x;
+    sP += pw;
+    sF += pw * x2;
+    sG += T(2) * pw * x2 * (T(1) - x);
+  }
+  double v3[3];
+  v3[0] = block_sum<SPEC_THREADS>((double)sP, red);
+  v3[1] = block_sum<SPEC_THREADS>((double)sF, red);
+  v3[2] = block_sum<SPEC_THREADS>((double)sG, red);
+  double t3[3];
+  if (last_block_reduce<SPEC_THREADS, 3>(pd, st, item.y, pd.nblk_spec, v3, t3, red) &&
+      threadIdx.x == 0) {
+    const double P = t3[0];
+    const double target = st.qn * st.qn;
+    const double h = (P > 0.0) ? t3[1] / P - target : 0.0;
+    const double hp = (P > 0.0) ? t3[2] / P : 0.0;
+    double nb = st.nb;
+    if (h < 0.0) st.nb_lo = nb; else st.nb_hi = nb;
+    double nn = (hp > 0.0) ? nb - h / hp : nb;
+    const bool lo_ok = isfinite(st.nb_lo), hi_ok = isfinite(st.nb_hi);
+    if (!(hp > 0.0) || !isfinite(nn)) {
+      nn = (h < 0.0) ? nb + 2.0 : nb - 2.0;
+    }
+    if (lo_ok && hi_ok) {
+      if (!(nn > st.nb_lo && nn < st.nb_hi)) nn = 0.5 * (st.nb_lo + st.nb_hi);
+    } else {
+      if (nn > nb + 4.0) nn = nb + 4.0;
+      if (nn < nb - 4.0) nn = nb - 4.0;
+    }
+    const double tol = (sizeof(T) == 8) ? 1e-13 : 2e-6;
+    st.npass += 1;
+    if (fabs(nn - nb) <= tol || st.npass >= 40) st.nconv = 1;
+    if (nn < -32.2) { nn = -32.2; }               // alpha floor 1e-14
+    st.nb = nn;
+    double a = exp(nn);
+    if (pd.bc == BC_RECT && a < pd.alpha) a = pd.alpha;   // rectangular hybrid floor
+    st.alpha_n = a;
+    const int it = st.iter - 1;
+    if (it >= 0 && it < pd.max_iter + 2) pd.hist_alpha[it] = a;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Set-up: eigenvalues of C in FP64 (Section 4.1).  Q(dy, k2) = sum_dx h
+// e^{-2 pi i k2 dx/n} (DFT) or sum_dx h cos(pi k2 dx/n) (DCT) comes from
+// the host; here lambda(k1,k2) = sum_dy e^{-2 pi i k1 dy / n} Q(dy, k2) or
+// sum_dy cos(pi k1 dy/n) Q(dy,k2), with tab the exact table of
+// e^{-2 pi i m/n} (DFT, m < n) or cos(pi m/n) (DCT, m < 2n).
+__global__ void k_spectrum(int transform, int n, int p, int half, const double* __restrict__ q,
+                           const double* __restrict__ tab, double* __restrict__ sigma,
+                           void* lam, int is_double) {
+  const int c = (p - 1) / 2;
+  const int W = (transform == TR_DCT) ? n : half;
+  const size_t tot = (size_t)n * W;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int k1 = (int)(i / W), k2 = (int)(i - (size_t)k1 * W);
+    if (transform == TR_DCT) {
+      double s = 0.0;
+      for (int a = 0; a < p; ++a) {
+        int m = (k1 * (a - c)) % (2 * n); if (m < 0) m += 2 * n;
+        s += tab[m] * q[(size_t)a * n + k2];
+      }
+      sigma[i] = s * s;
+      if (is_double) static_cast<double*>(lam)[i] = s; else static_cast<float*>(lam)[i] = (float)s;
+    } else {
+      double re = 0.0, im = 0.0;
+      for (int a = 0; a < p; ++a) {
+        int m = (k1 * (a - c)) % n; if (m < 0) m += n;
+        const double er = tab[2 * m], ei = tab[2 * m + 1];
+        const double qr = q[2 * ((size_t)a * half + k2)], qi = q[2 * ((size_t)a * half + k2) + 1];
+        re += er * qr - ei * qi;
+        im += er * qi + ei * qr;
+      }
+      sigma[i] = re * re + im * im;
+      if (is_double) { static_cast<double2*>(lam)[i] = make_double2(re, im); }
+      else { static_cast<float2*>(lam)[i] = make_float2((float)re, (float)im); }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_rows_fwd(const Prob* probs, State* states, const int2* items, int nitems, int src,
+                     int pcg, size_t smem, cudaStream_t s) {
+  if (nitems > 0) k_rows_fwd<T><<<nitems, TR_THREADS, smem, s>>>(probs, states, items, src, pcg);
+}
+template <typename T>
+void launch_cols(const Prob* probs, State* states, const int2* items, int nitems, int mode,
+                 int pcg, double op_alpha, int op_kind, size_t smem, cudaStream_t s) {
+  if (nitems > 0)
+    k_cols<T><<<nitems, TR_THREADS, smem, s>>>(probs, states, items, mode, pcg, op_alpha, op_kind);
+}
+template <typename T>
+void launch_rows_inv(const Prob* probs, State* states, const int2* items, int nitems, int dst,
+                     int pcg, size_t smem, cudaStream_t s) {
+  if (nitems > 0) k_rows_inv<T><<<nitems, TR_THREADS, smem, s>>>(probs, states, items, dst, pcg);
+}
+template <typename T>
+void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, cudaStream_t s) {
+  if (nitems > 0) k_spec<T><<<nitems, SPEC_THREADS, 0, s>>>(probs, states, items);
+}
+void launch_spectrum_setup(const Prob*, int, int transform, int n, int p, int half,
+                           const double* q_dev, const double* tab_dev, double* sigma,
+                           void* lam, int is_double, cudaStream_t s) {
+  const size_t tot = (size_t)n * (transform == TR_DCT ? n : half);
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_spectrum<<<blocks, 256, 0, s>>>(transform, n, p, half, q_dev, tab_dev, sigma, lam, is_double);
+}
+template <typename T>
+cudaError_t fft_set_smem(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define INST(T)                                                                                   \
+  template void launch_rows_fwd<T>(const Prob*, State*, const int2*, int, int, int, size_t, cudaStream_t); \
+  template void launch_cols<T>(const Prob*, State*, const int2*, int, int, int, double, int, size_t, cudaStream_t); \
+  template void launch_rows_inv<T>(const Prob*, State*, const int2*, int, int, int, size_t, cudaStream_t); \
+  template void launch_spec<T>(const Prob*, State*, const int2*, int, cudaStream_t);              \
+  template cudaError_t fft_set_smem<T>(size_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace mlba

@@ -1,0 +1,1038 @@
+// mlba_api.cu — host runtime and C ABI of the MLBA library (include/mlba.h).
+//
+// A batch owns: a table of problem descriptors (Prob) and states (State) in
+// device memory, one device arena holding every problem's buffers, and the
+// item lists that map CTAs to (problem, block).  One step of the algorithm is
+// a fixed sequence of batched launches captured once into a CUDA graph; each
+// replay advances every live problem by one iteration.  A context for a
+// single problem is a batch of one.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+#include <new>
+
+#include "../../include/mlba.h"
+#include "mlba_internal.cuh"
+#include "mlba_launch.h"
+
+using namespace mlba;
+
+namespace {
+
+constexpr int NEWTON_PASSES = 10;   // graph nodes per iteration for the alpha_n solve
+constexpr size_t ALIGN = 256;
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e__ = (call);                      \
+    if (e__ != cudaSuccess) return MLBA_E_CUDA;    \
+  } while (0)
+
+struct HostProb {
+  Prob pd;                       // host copy with device pointers filled in
+  std::vector<double> psf;       // p x p, the PSF used by A
+  std::vector<double> psf_pre;   // PSF of the preconditioner (H or H~)
+  std::vector<int> dy, dx;
+  std::vector<double> w;
+  std::vector<double> hy, hx;
+  size_t off[NSLOT + 16];
+};
+
+struct ItemList {
+  int2* dev = nullptr;
+  int count = 0;
+};
+
+}  // namespace
+
+struct mlba_batch {
+  int dtype = MLBA_F32, z_store = MLBA_F32, levels = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<HostProb> hp;
+  Prob* d_probs = nullptr;
+  State* d_states = nullptr;
+  State* d_opstates = nullptr;
+  unsigned char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // item lists
+  ItemList blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry, cols_kry,
+      vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all;
+  std::vector<int2*> allocs;
+  size_t smem_stencil = 0, smem_fft = 0, smem_frame = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool has_data = false;
+  int any_krylov = 0, any_spec = 0, any_ns = 0, any_stat = 0;
+};
+
+struct mlba_ctx {
+  mlba_batch* b;
+};
+
+namespace {
+
+size_t tsize(int dtype) { return dtype == MLBA_F64 ? 8 : 4; }
+size_t zsize(int zs) { return zs == MLBA_F64 ? 8 : (zs == MLBA_BF16 ? 2 : 4); }
+size_t al(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+bool fft_plan(int n, int* radix, int* nstage) {
+  int m = n, s = 0;
+  while (m % 4 == 0 && s < MAX_STAGES) { radix[s++] = 4; m /= 4; }
+  while (m % 2 == 0 && s < MAX_STAGES) { radix[s++] = 2; m /= 2; }
+  while (m % 3 == 0 && s < MAX_STAGES) { radix[s++] = 3; m /= 3; }
+  while (m % 5 == 0 && s < MAX_STAGES) { radix[s++] = 5; m /= 5; }
+  *nstage = s;
+  return m == 1;
+}
+
+bool quad_symmetric(const std::vector<double>& h, int p) {
+  double mx = 0;
+  for (double v : h) mx = std::max(mx, std::fabs(v));
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b < p; ++b) {
+      const double v = h[a * p + b];
+      if (std::fabs(v - h[(p - 1 - a) * p + b]) > 1e-14 * mx) return false;
+      if (std::fabs(v - h[a * p + (p - 1 - b)]) > 1e-14 * mx) return false;
+    }
+  return true;
+}
+
+// H~ of Section 4.3, each quadrant orbit computed once so the result is
+// exactly symmetric
+std::vector<double> symmetrized(const std::vector<double>& h, int p) {
+  std::vector<double> s(h.size());
+  for (int a = 0; a <= (p - 1) / 2; ++a)
+    for (int b = 0; b <= (p - 1) / 2; ++b) {
+      const int a2 = p - 1 - a, b2 = p - 1 - b;
+      const double v = 0.25 * (h[a * p + b] + h[a2 * p + b] + h[a * p + b2] + h[a2 * p + b2]);
+      s[a * p + b] = s[a2 * p + b] = s[a * p + b2] = s[a2 * p + b2] = v;
+    }
+  return s;
+}
+
+bool rank_one(const std::vector<double>& h, int p, std::vector<double>& u, std::vector<double>& v) {
+  int a0 = 0, b0 = 0;
+  double mx = 0;
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b < p; ++b)
+      if (std::fabs(h[a * p + b]) > mx) { mx = std::fabs(h[a * p + b]); a0 = a; b0 = b; }
+  if (mx == 0) return false;
+  u.assign(p, 0); v.assign(p, 0);
+  for (int a = 0; a < p; ++a) u[a] = h[a * p + b0];
+  for (int b = 0; b < p; ++b) v[b] = h[a0 * p + b] / h[a0 * p + b0];
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b < p; ++b)
+      if (std::fabs(h[a * p + b] - u[a] * v[b]) > 1e-14 * mx) return false;
+  return true;
+}
+
+template <typename T>
+void put(unsigned char* host, size_t off, const std::vector<double>& v) {
+  T* d = reinterpret_cast<T*>(host + off);
+  for (size_t i = 0; i < v.size(); ++i) d[i] = (T)v[i];
+}
+
+int build_list(mlba_batch* B, ItemList& L, const std::vector<int2>& items) {
+  L.count = (int)items.size();
+  if (L.count == 0) return MLBA_OK;
+  CK(cudaMalloc(&L.dev, items.size() * sizeof(int2)));
+  B->allocs.push_back(L.dev);
+  CK(cudaMemcpy(L.dev, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  return MLBA_OK;
+}
+
+State initial_state(const Prob& pd) {
+  State s;
+  std::memset(&s, 0, sizeof(s));
+  s.stop_iter = -1;
+  s.alpha_n = pd.alpha;
+  s.nb = 0.0;
+  return s;
+}
+
+template <typename T, typename TZ>
+void enqueue_step(mlba_batch* B, cudaStream_t s) {
+  const Prob* P = B->d_probs;
+  State* S = B->d_states;
+  // a2: r = g - A f with ||r||^2 and the stop rule
+  launch_stencil<T>(ST_FWD_RESID, P, S, B->blur.dev, B->blur.count, SL_F, SL_R, SL_G, 0,
+                    B->smem_stencil, s);
+  // a4: spectral preconditioners (Algorithms 1, 3, 4, 4-NS)
+  if (B->any_spec) {
+    launch_rows_fwd<T>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_R, 0, B->smem_fft, s);
+    launch_cols<T>(P, S, B->cols_stat.dev, B->cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
+    if (B->any_ns) {
+      launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
+      for (int k = 0; k < NEWTON_PASSES; ++k) launch_spec<T>(P, S, B->spec.dev, B->spec.count, s);
+      launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
+    }
+    launch_rows_inv<T>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
+  }
+  // a4': Algorithm 2, PCG on (A A^T + alpha I) t = r preconditioned by (CC^T + alpha I)^{-1}
+  if (B->any_krylov) {
+    const int maxs = B->hp.empty() ? 5 : B->hp[0].pd.pcg_max;
+    launch_vec<T>(VEC_PCG_INIT, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
+    launch_rows_fwd<T>(P, S, B->rows_kry.dev, B->rows_kry.count, SL_PRES, 1, B->smem_fft, s);
+    launch_cols<T>(P, S, B->cols_kry.dev, B->cols_kry.count, COL_FUSED, 1, 0.0, 0, B->smem_fft, s);
+    launch_rows_inv<T>(P, S, B->rows_kry.dev, B->rows_kry.count, SL_PZ, 1, B->smem_fft, s);
+    launch_vec<T>(VEC_PCG_RHO0, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
+    for (int k = 0; k < maxs; ++k) {
+      launch_stencil<T>(ST_CORR, P, S, B->corr_kry.dev, B->corr_kry.count, SL_PP, SL_V, SL_V, 1,
+                        B->smem_stencil, s);
+      launch_vec<T>(VEC_FOLD, P, S, B->vec_kry_bc.dev, B->vec_kry_bc.count, 1, s);
+      launch_stencil<T>(ST_FWD_PCGQ, P, S, B->blur_kry.dev, B->blur_kry.count, -1, SL_PQ, SL_PP, 1,
+                        B->smem_stencil, s);
+      launch_vec<T>(VEC_PCG_AXPY, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
+      launch_rows_fwd<T>(P, S, B->rows_kry.dev, B->rows_kry.count, SL_PRES, 1, B->smem_fft, s);
+      launch_cols<T>(P, S, B->cols_kry.dev, B->cols_kry.count, COL_FUSED, 1, 0.0, 0, B->smem_fft, s);
+      launch_rows_inv<T>(P, S, B->rows_kry.dev, B->rows_kry.count, SL_PZ, 1, B->smem_fft, s);
+      launch_vec<T>(VEC_PCG_RHO, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
+      launch_vec<T>(VEC_PCG_PUPD, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
+    }
+    launch_vec<T>(VEC_PCG_FINISH, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
+  }
+  // a6: full correlation of t (A^T up to the BC fold)
+  launch_stencil<T>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
+  // a1: z += W u, x = S_mu(z), f = W^T x
+  launch_frame<T, TZ>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0,
+                      B->smem_frame, s);
+}
+
+void enqueue_dispatch(mlba_batch* B, cudaStream_t s) {
+  if (B->dtype == MLBA_F64) enqueue_step<double, double>(B, s);
+  else if (B->z_store == MLBA_BF16) enqueue_step<float, __nv_bfloat16>(B, s);
+  else enqueue_step<float, float>(B, s);
+}
+
+int set_smem_attrs(mlba_batch* B) {
+  if (B->dtype == MLBA_F64) {
+    CK(stencil_set_smem<double>(B->smem_stencil));
+    CK(fft_set_smem<double>(B->smem_fft));
+    CK((frame_set_smem<double, double>(B->smem_frame)));
+  } else {
+    CK(stencil_set_smem<float>(B->smem_stencil));
+    CK(fft_set_smem<float>(B->smem_fft));
+    if (B->z_store == MLBA_BF16) CK((frame_set_smem<float, __nv_bfloat16>(B->smem_frame)));
+    else CK((frame_set_smem<float, float>(B->smem_frame)));
+  }
+  return MLBA_OK;
+}
+
+size_t frame_smem(int dtype, int zs, int L) {
+  if (dtype == MLBA_F64) return frame_smem_bytes<double, double>(L);
+  if (zs == MLBA_BF16) return frame_smem_bytes<float, __nv_bfloat16>(L);
+  return frame_smem_bytes<float, float>(L);
+}
+
+void destroy_batch(mlba_batch* B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (int2* p : B->allocs) cudaFree(p);
+  if (B->arena) cudaFree(B->arena);
+  if (B->d_probs) cudaFree(B->d_probs);
+  if (B->d_states) cudaFree(B->d_states);
+  if (B->d_opstates) cudaFree(B->d_opstates);
+  if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
+  delete B;
+}
+
+// Validate one problem and fill its host description (no device work).
+int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
+  const int p = in.p, n = in.n;
+  if (!in.psf || p < 1 || (p % 2) == 0 || n < p || n < 2) return MLBA_E_INVAL;
+  if (in.bc < 0 || in.bc > 3 || in.precond < 0 || in.precond > 5) return MLBA_E_INVAL;
+  if (o.levels < 1 || o.levels > 4) return MLBA_E_INVAL;
+  if (!(in.delta >= 0.0) || !(in.mu >= 0.0)) return MLBA_E_INVAL;
+  const bool ns = in.precond == MLBA_P_TIKH_NS;
+  if (in.bc == MLBA_RECT && (in.precond == MLBA_P_TIKH || (ns && !o.rect_ns_hybrid)))
+    return MLBA_E_INVAL;   // Section 5: Algorithm 4 needs a square A
+  if (!ns && in.precond != MLBA_P_NONE && !(in.alpha > 0.0)) return MLBA_E_INVAL;
+  if (ns && in.bc == MLBA_RECT && !(in.alpha > 0.0)) return MLBA_E_INVAL;
+  if (ns && !(in.delta > 0.0)) return MLBA_E_INVAL;
+  if (!(o.q > 2.0 * o.rho && o.q < 1.0 && o.rho > 0.0 && o.rho < 0.5) && ns) return MLBA_E_INVAL;
+  h.psf.assign(in.psf, in.psf + (size_t)p * p);
+  for (double v : h.psf)
+    if (!std::isfinite(v)) return MLBA_E_INVAL;
+  Prob& pd = h.pd;
+  std::memset(&pd, 0, sizeof(pd));
+  pd.n = n; pd.p = p; pd.c = (p - 1) / 2;
+  pd.nf = in.bc == MLBA_RECT ? n + p - 1 : n;
+  pd.ne = n + p - 1;
+  pd.half = n / 2 + 1;
+  pd.bc = in.bc; pd.precond = in.precond; pd.levels = o.levels; pd.nbands = 8 * o.levels + 1;
+  pd.ns = ns ? 1 : 0;
+  pd.use_adj = (in.precond == MLBA_P_TIKH || (ns && in.bc != MLBA_RECT)) ? 0 : 1;
+  pd.max_iter = in.max_iter > 0 ? in.max_iter : o.max_iter;
+  pd.stop = o.stop;
+  pd.pcg_max = o.pcg_max;
+  pd.mu = in.mu; pd.alpha = in.alpha; pd.gamma = o.gamma; pd.delta = in.delta;
+  pd.q = o.q; pd.rho = o.rho; pd.tau = (1.0 + 2.0 * o.rho) / (1.0 - 2.0 * o.rho);
+  pd.pcg_tol = o.pcg_tol;
+  // transform (Section 4.1 / 4.3)
+  if (in.precond == MLBA_P_NONE) {
+    pd.transform = TR_NONE;
+  } else if (in.precond == MLBA_P_SYM) {
+    pd.transform = TR_DCT;
+    h.psf_pre = symmetrized(h.psf, p);
+  } else {
+    const int tr = in.transform;
+    const bool sym = quad_symmetric(h.psf, p);
+    if (tr == MLBA_TR_DCT && !sym) return MLBA_E_INVAL;
+    pd.transform = (tr == MLBA_TR_DFT) ? TR_DFT : (tr == MLBA_TR_DCT ? TR_DCT : (sym ? TR_DCT : TR_DFT));
+    h.psf_pre = h.psf;
+  }
+  if (pd.transform != TR_NONE) {
+    if (!fft_plan(n, pd.radix, &pd.nstage)) return MLBA_E_UNSUPPORTED;
+    // one transform must fit the per-CTA value budget of the smem FFT
+    if (n > (o.dtype == MLBA_F64 ? TR_MAXV_F64 : TR_MAXV) * TR_THREADS) return MLBA_E_UNSUPPORTED;
+  }
+  // taps
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b < p; ++b)
+      if (h.psf[a * p + b] != 0.0) {
+        h.dy.push_back(a - pd.c); h.dx.push_back(b - pd.c); h.w.push_back(h.psf[a * p + b]);
+      }
+  if (h.w.empty()) return MLBA_E_INVAL;
+  pd.ntaps = (int)h.w.size();
+  pd.sep = rank_one(h.psf, p, h.hy, h.hx) && p > 1 ? 1 : 0;
+  // launch geometry
+  const int TS = FRAME_TILE;
+  pd.nblk_blur = ((n + 31) / 32) * ((n + 31) / 32);
+  pd.nblk_corr = ((pd.ne + 31) / 32) * ((pd.ne + 31) / 32);
+  pd.nblk_frame = ((pd.nf + TS - 1) / TS) * ((pd.nf + TS - 1) / TS);
+  const int cap = (o.dtype == MLBA_F64 ? TR_MAXV_F64 : TR_MAXV) * TR_THREADS / n;   // transforms per CTA
+  const int pairs = (n + 1) / 2;
+  pd.row_g = std::max(1, std::min(cap, pairs));
+  pd.nblk_rows = (pairs + pd.row_g - 1) / pd.row_g;
+  if (pd.transform == TR_DCT) {
+    pd.col_g = std::max(1, std::min(cap, pairs));
+    pd.nblk_cols = (n + 2 * pd.col_g - 1) / (2 * pd.col_g);
+  } else {
+    pd.col_g = std::max(1, std::min(cap, pd.half));
+    pd.nblk_cols = (pd.half + pd.col_g - 1) / pd.col_g;
+  }
+  const size_t specn = (size_t)n * (pd.transform == TR_DCT ? n : pd.half);
+  pd.nblk_spec = (int)((specn + SPEC_THREADS * SPEC_PER_THREAD - 1) / (SPEC_THREADS * SPEC_PER_THREAD));
+  pd.nblk_vec = (int)(((size_t)n * n + VEC_THREADS * VEC_PER_THREAD - 1) / (VEC_THREADS * VEC_PER_THREAD));
+  return MLBA_OK;
+}
+
+// Build the spectrum of C / Q in FP64 on the device (Section 4.1).
+int build_spectrum(mlba_batch* B, HostProb& h) {
+  Prob& pd = h.pd;
+  const int n = pd.n, p = pd.p, c = pd.c, half = pd.half;
+  const bool dct = pd.transform == TR_DCT;
+  const int W = dct ? n : half;
+  const std::vector<double>& H = h.psf_pre;
+  std::vector<double> q, tab;
+  if (dct) {
+    tab.resize(2 * n);
+    for (int m = 0; m < 2 * n; ++m) tab[m] = std::cos(M_PI * (double)m / (double)n);
+    q.assign((size_t)p * n, 0.0);
+    for (int a = 0; a < p; ++a)
+      for (int k2 = 0; k2 < n; ++k2) {
+        double s = 0;
+        for (int b = 0; b < p; ++b) {
+          int m = (k2 * (b - c)) % (2 * n); if (m < 0) m += 2 * n;
+          s += H[a * p + b] * tab[m];
+        }
+        q[(size_t)a * n + k2] = s;
+      }
+  } else {
+    tab.resize(2 * n);
+    for (int m = 0; m < n; ++m) {
+      const double ang = 2.0 * M_PI * (double)m / (double)n;
+      tab[2 * m] = std::cos(ang); tab[2 * m + 1] = -std::sin(ang);
+    }
+    q.assign((size_t)p * half * 2, 0.0);
+    for (int a = 0; a < p; ++a)
+      for (int k2 = 0; k2 < half; ++k2) {
+        double re = 0, im = 0;
+        for (int b = 0; b < p; ++b) {
+          int m = (k2 * (b - c)) % n; if (m < 0) m += n;
+          re += H[a * p + b] * tab[2 * m]; im += H[a * p + b] * tab[2 * m + 1];
+        }
+        q[2 * ((size_t)a * half + k2)] = re; q[2 * ((size_t)a * half + k2) + 1] = im;
+      }
+  }
+  double *dq = nullptr, *dtab = nullptr;
+  CK(cudaMalloc(&dq, q.size() * sizeof(double)));
+  CK(cudaMalloc(&dtab, tab.size() * sizeof(double)));
+  CK(cudaMemcpyAsync(dq, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+  CK(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+  launch_spectrum_setup(nullptr, 0, pd.transform, n, p, half, dq, dtab, pd.sigma, pd.lam,
+                        B->dtype == MLBA_F64 ? 1 : 0, B->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(B->stream));
+  cudaFree(dq);
+  cudaFree(dtab);
+  (void)W;
+  return MLBA_OK;
+}
+
+int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in, mlba_batch** out) {
+  if (!probs || count <= 0 || !out) return MLBA_E_INVAL;
+  mlba_opts o;
+  if (opts_in) o = *opts_in; else mlba_opts_default(&o);
+  if (o.dtype != MLBA_F32 && o.dtype != MLBA_F64) return MLBA_E_INVAL;
+  if (o.dtype == MLBA_F64 && o.z_store != MLBA_F64) o.z_store = MLBA_F64;
+  if (o.dtype == MLBA_F32 && o.z_store != MLBA_BF16) o.z_store = MLBA_F32;
+  if (o.pcg_max < 1 || o.pcg_max > 50) return MLBA_E_INVAL;
+  mlba_batch* B = new (std::nothrow) mlba_batch();
+  if (!B) return MLBA_E_NOMEM;
+  B->dtype = o.dtype; B->z_store = o.z_store; B->levels = o.levels;
+  B->hp.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const int rc = setup_problem(probs[i], o, B->hp[i]);
+    if (rc != MLBA_OK) { destroy_batch(B); return rc; }
+  }
+  if (o.stream) { B->stream = (cudaStream_t)o.stream; }
+  else {
+    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      destroy_batch(B); return MLBA_E_CUDA;
+    }
+    B->own_stream = true;
+  }
+  const size_t ts = tsize(o.dtype), zs = zsize(o.z_store);
+  // ---- arena layout
+  size_t total = 0;
+  std::vector<std::vector<size_t>> offs(count);
+  for (int i = 0; i < count; ++i) {
+    Prob& pd = B->hp[i].pd;
+    const size_t n2 = (size_t)pd.n * pd.n, nf2 = (size_t)pd.nf * pd.nf, ne2 = (size_t)pd.ne * pd.ne;
+    const bool spec = pd.transform != TR_NONE;
+    const bool kry = pd.precond == P_KRYLOV;
+    const size_t W = pd.transform == TR_DCT ? pd.n : pd.half;
+    const size_t nspec = (size_t)pd.n * W;
+    const size_t aux = std::max(nf2, ne2);
+    std::vector<size_t> sz = {
+        n2 * ts,                               // G
+        nf2 * ts,                              // F
+        n2 * ts,                               // R
+        n2 * ts,                               // T
+        ne2 * ts,                              // V
+        n2 * ts,                               // U
+        spec ? (size_t)pd.n * (pd.n + 2) * ts : ts,   // S
+        kry ? n2 * ts : ts, kry ? n2 * ts : ts, kry ? n2 * ts : ts, kry ? n2 * ts : ts,
+        kry ? n2 * ts : ts,                    // PCG vectors
+        aux * ts, aux * ts,                    // AUX0, AUX1
+        (size_t)pd.nbands * nf2 * zs,          // z0
+        (size_t)pd.nbands * nf2 * zs,          // z1
+        spec ? nspec * 8 : 8,                  // sigma
+        spec ? nspec * ts * (pd.transform == TR_DCT ? 1 : 2) : ts,   // lam
+        spec ? (size_t)pd.n * 2 * ts : ts,     // tw
+        spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
+        (size_t)pd.ntaps * 4, (size_t)pd.ntaps * 4, (size_t)pd.ntaps * ts,   // taps
+        (size_t)pd.p * ts, (size_t)pd.p * ts,  // hy, hx
+        3 * (size_t)std::max({pd.nblk_blur, pd.nblk_vec, pd.nblk_spec, 1}) * 8,  // partial
+        (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 4};
+    offs[i].resize(sz.size());
+    for (size_t k = 0; k < sz.size(); ++k) { offs[i][k] = total; total += al(sz[k]); }
+  }
+  B->arena_bytes = total;
+  if (cudaMalloc(&B->arena, total) != cudaSuccess) { destroy_batch(B); return MLBA_E_NOMEM; }
+  // ---- fill pointers and constant tables
+  std::vector<unsigned char> host_init;   // staged constant data
+  for (int i = 0; i < count; ++i) {
+    HostProb& h = B->hp[i];
+    Prob& pd = h.pd;
+    const std::vector<size_t>& of = offs[i];
+    unsigned char* base = B->arena;
+    for (int s = 0; s < NSLOT; ++s) pd.buf[s] = base + of[s];
+    int k = NSLOT;
+    pd.z[0] = base + of[k++];
+    pd.z[1] = base + of[k++];
+    pd.sigma = reinterpret_cast<double*>(base + of[k++]);
+    pd.lam = base + of[k++];
+    pd.tw = base + of[k++];
+    pd.dtw = base + of[k++];
+    pd.tap_dy = reinterpret_cast<int*>(base + of[k++]);
+    pd.tap_dx = reinterpret_cast<int*>(base + of[k++]);
+    pd.tap_w = base + of[k++];
+    pd.hy = base + of[k++];
+    pd.hx = base + of[k++];
+    pd.partial = reinterpret_cast<double*>(base + of[k++]);
+    pd.hist_res = reinterpret_cast<double*>(base + of[k++]);
+    pd.hist_alpha = reinterpret_cast<double*>(base + of[k++]);
+    pd.hist_beta = reinterpret_cast<int*>(base + of[k++]);
+    pd.w = nullptr;
+    // tables
+    CK(cudaMemcpy(pd.tap_dy, h.dy.data(), h.dy.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pd.tap_dx, h.dx.data(), h.dx.size() * 4, cudaMemcpyHostToDevice));
+    std::vector<unsigned char> tmp;
+    auto upload = [&](void* dst, const std::vector<double>& v) -> int {
+      tmp.assign(v.size() * ts, 0);
+      if (ts == 8) put<double>(tmp.data(), 0, v); else put<float>(tmp.data(), 0, v);
+      if (!v.empty()) CK(cudaMemcpy(dst, tmp.data(), tmp.size(), cudaMemcpyHostToDevice));
+      return MLBA_OK;
+    };
+    if (upload(pd.tap_w, h.w) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
+    if (pd.sep) {
+      if (upload(pd.hy, h.hy) != MLBA_OK || upload(pd.hx, h.hx) != MLBA_OK) {
+        destroy_batch(B); return MLBA_E_CUDA;
+      }
+    }
+    if (pd.transform != TR_NONE) {
+      std::vector<double> tw(2 * (size_t)pd.n), dtw(2 * (size_t)pd.n);
+      for (int m = 0; m < pd.n; ++m) {
+        const double a = 2.0 * M_PI * (double)m / (double)pd.n;
+        tw[2 * m] = std::cos(a); tw[2 * m + 1] = -std::sin(a);
+        const double b = M_PI * (double)m / (2.0 * (double)pd.n);
+        dtw[2 * m] = std::cos(b); dtw[2 * m + 1] = -std::sin(b);
+      }
+      if (upload(pd.tw, tw) != MLBA_OK || upload(pd.dtw, dtw) != MLBA_OK) {
+        destroy_batch(B); return MLBA_E_CUDA;
+      }
+      const int rc = build_spectrum(B, h);
+      if (rc != MLBA_OK) { destroy_batch(B); return rc; }
+    }
+  }
+  // ---- device tables
+  std::vector<Prob> probs_h(count);
+  std::vector<State> st_h(count);
+  for (int i = 0; i < count; ++i) { probs_h[i] = B->hp[i].pd; st_h[i] = initial_state(probs_h[i]); }
+  if (cudaMalloc(&B->d_probs, count * sizeof(Prob)) != cudaSuccess ||
+      cudaMalloc(&B->d_states, count * sizeof(State)) != cudaSuccess ||
+      cudaMalloc(&B->d_opstates, count * sizeof(State)) != cudaSuccess) {
+    destroy_batch(B); return MLBA_E_NOMEM;
+  }
+  CK(cudaMemcpy(B->d_probs, probs_h.data(), count * sizeof(Prob), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B->d_states, st_h.data(), count * sizeof(State), cudaMemcpyHostToDevice));
+  // ---- item lists
+  std::vector<int2> blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
+      cols_kry, vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all;
+  size_t smem_st = 0, smem_fft = 0;
+  for (int i = 0; i < count; ++i) {
+    const Prob& pd = B->hp[i].pd;
+    auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
+    add(blur, pd.nblk_blur);
+    add(frame, pd.nblk_frame);
+    add(corr_all, pd.nblk_corr);
+    add(vec_all, pd.nblk_vec);
+    if (pd.use_adj) add(corr, pd.nblk_corr);
+    const bool specp = pd.transform != TR_NONE;
+    if (specp) { add(rows_all, pd.nblk_rows); add(cols_all, pd.nblk_cols); add(spec_all, pd.nblk_spec); }
+    if (pd.precond == P_KRYLOV) {
+      add(corr_kry, pd.nblk_corr); add(blur_kry, pd.nblk_blur); add(rows_kry, pd.nblk_rows);
+      add(cols_kry, pd.nblk_cols); add(vec_kry, pd.nblk_vec);
+      if (pd.bc != BC_RECT) add(vec_kry_bc, pd.nblk_vec);
+      B->any_krylov = 1;
+    } else if (specp) {
+      add(rows_spec, pd.nblk_rows);
+      B->any_spec = 1;
+      if (pd.ns) { add(cols_ns, pd.nblk_cols); add(spec, pd.nblk_spec); B->any_ns = 1; }
+      else { add(cols_stat, pd.nblk_cols); B->any_stat = 1; }
+    }
+    const size_t R = 32 + pd.p - 1;
+    const size_t nw = pd.sep ? 2 * pd.p : pd.ntaps;
+    const size_t st_b = (((nw + 1) & ~(size_t)1) + R * R + (pd.sep ? R * 32 : 0)) * ts + (pd.sep ? 0 : pd.ntaps * 4);
+    smem_st = std::max(smem_st, st_b);
+    if (specp) {
+      const size_t fb = (size_t)std::max(pd.row_g, pd.col_g) * pd.n * 2 * ts;
+      smem_fft = std::max(smem_fft, fb);
+    }
+  }
+  B->smem_stencil = std::max<size_t>(smem_st, 16);
+  B->smem_fft = std::max<size_t>(smem_fft, 16);
+  B->smem_frame = frame_smem(o.dtype, o.z_store, o.levels);
+  int rc = MLBA_OK;
+  rc |= build_list(B, B->blur, blur); rc |= build_list(B, B->corr, corr);
+  rc |= build_list(B, B->corr_kry, corr_kry); rc |= build_list(B, B->blur_kry, blur_kry);
+  rc |= build_list(B, B->rows_spec, rows_spec); rc |= build_list(B, B->cols_stat, cols_stat);
+  rc |= build_list(B, B->cols_ns, cols_ns); rc |= build_list(B, B->spec, spec);
+  rc |= build_list(B, B->rows_kry, rows_kry); rc |= build_list(B, B->cols_kry, cols_kry);
+  rc |= build_list(B, B->vec_kry, vec_kry); rc |= build_list(B, B->vec_kry_bc, vec_kry_bc);
+  rc |= build_list(B, B->frame, frame); rc |= build_list(B, B->corr_all, corr_all);
+  rc |= build_list(B, B->rows_all, rows_all); rc |= build_list(B, B->cols_all, cols_all);
+  rc |= build_list(B, B->spec_all, spec_all); rc |= build_list(B, B->vec_all, vec_all);
+  if (rc != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
+  if (set_smem_attrs(B) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
+  // ---- capture one step
+  if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    destroy_batch(B); return MLBA_E_CUDA;
+  }
+  enqueue_dispatch(B, B->stream);
+  if (cudaStreamEndCapture(B->stream, &B->graph) != cudaSuccess ||
+      cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess) {
+    destroy_batch(B); return MLBA_E_CUDA;
+  }
+  *out = B;
+  return MLBA_OK;
+}
+
+int reset_batch(mlba_batch* B) {
+  std::vector<State> st_h(B->hp.size());
+  for (size_t i = 0; i < B->hp.size(); ++i) {
+    const Prob& pd = B->hp[i].pd;
+    CK(cudaMemsetAsync(pd.z[0], 0, (size_t)pd.nbands * pd.nf * pd.nf * zsize(B->z_store), B->stream));
+    CK(cudaMemsetAsync(pd.buf[SL_F], 0, (size_t)pd.nf * pd.nf * tsize(B->dtype), B->stream));
+    st_h[i] = initial_state(pd);
+  }
+  CK(cudaMemcpyAsync(B->d_states, st_h.data(), st_h.size() * sizeof(State), cudaMemcpyHostToDevice,
+                     B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  return MLBA_OK;
+}
+
+int set_g(mlba_batch* B, int i, const void* g, int on_device, double delta) {
+  HostProb& h = B->hp[i];
+  const size_t bytes = (size_t)h.pd.n * h.pd.n * tsize(B->dtype);
+  if (!g) return MLBA_E_INVAL;
+  CK(cudaMemcpyAsync(h.pd.buf[SL_G], g, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     B->stream));
+  if (delta != h.pd.delta) {
+    h.pd.delta = delta;
+    CK(cudaMemcpyAsync(&B->d_probs[i].delta, &h.pd.delta, sizeof(double), cudaMemcpyHostToDevice, B->stream));
+  }
+  CK(cudaStreamSynchronize(B->stream));
+  return MLBA_OK;
+}
+
+int copy_out(mlba_batch* B, void* dst, const void* src, size_t bytes, int on_device) {
+  if (!dst) return MLBA_E_INVAL;
+  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, B->stream));
+  if (!on_device) CK(cudaStreamSynchronize(B->stream));
+  return MLBA_OK;
+}
+
+int copy_in(mlba_batch* B, void* dst, const void* src, size_t bytes, int on_device) {
+  if (!src) return MLBA_E_INVAL;
+  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, B->stream));
+  return MLBA_OK;
+}
+
+int stats_of(mlba_batch* B, int i, mlba_stats* s) {
+  if (!s || i < 0 || i >= (int)B->hp.size()) return MLBA_E_INVAL;
+  State st;
+  CK(cudaMemcpyAsync(&st, &B->d_states[i], sizeof(State), cudaMemcpyDeviceToHost, B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  s->iter = st.iter;
+  s->stopped = st.stopped;
+  s->stop_iter = st.stop_iter;
+  s->status = st.status;
+  s->resnorm = st.resnorm;
+  s->alpha_n = st.alpha_n;
+  s->beta_n = st.beta_last;
+  s->nres = st.nres;
+  return MLBA_OK;
+}
+
+int reset_opstates(mlba_batch* B) {
+  CK(cudaMemsetAsync(B->d_opstates, 0, B->hp.size() * sizeof(State), B->stream));
+  return MLBA_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+extern "C" {
+
+void mlba_opts_default(mlba_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->mu = 10.0 / 255.0;
+  o->alpha = 0.05;
+  o->gamma = 1.0 + 1e-15;
+  o->q = 0.5;
+  o->rho = 1e-4;
+  o->pcg_tol = 1e-3;
+  o->levels = 1;
+  o->max_iter = 200;
+  o->pcg_max = 5;
+  o->dtype = MLBA_F32;
+  o->z_store = MLBA_F32;
+  o->transform = MLBA_TR_AUTO;
+  o->stop = 1;
+  o->rect_ns_hybrid = 0;
+  o->stream = nullptr;
+}
+
+const char* mlba_strerror(int s) {
+  switch (s) {
+    case MLBA_OK: return "ok";
+    case MLBA_E_INVAL: return "invalid argument";
+    case MLBA_E_NOMEM: return "out of memory";
+    case MLBA_E_CUDA: return "CUDA runtime error";
+    case MLBA_E_TIMEOUT: return "device wait timed out";
+    case MLBA_E_DIVERGED: return "residual norm not finite (diverged)";
+    case MLBA_E_STATE: return "call out of order";
+    case MLBA_E_UNSUPPORTED: return "unsupported size (FFT length must be 2^a 3^b 5^c)";
+    default: return "unknown status";
+  }
+}
+
+int mlba_batch_create(const mlba_problem* probs, int count, const mlba_opts* opts, mlba_batch** out) {
+  if (!out) return MLBA_E_INVAL;
+  *out = nullptr;
+  mlba_batch* B = nullptr;
+  int rc = create_batch(probs, count, opts, &B);
+  if (rc != MLBA_OK) return rc;
+  for (int i = 0; i < count; ++i) {
+    if (probs[i].g) {
+      rc = set_g(B, i, probs[i].g, probs[i].g_on_device, probs[i].delta);
+      if (rc != MLBA_OK) { destroy_batch(B); return rc; }
+    }
+  }
+  rc = reset_batch(B);
+  if (rc != MLBA_OK) { destroy_batch(B); return rc; }
+  B->has_data = true;
+  for (int i = 0; i < count; ++i) if (!probs[i].g) B->has_data = false;
+  *out = B;
+  return MLBA_OK;
+}
+
+int mlba_batch_iterate(mlba_batch* B, int k) {
+  if (!B || k < 0) return MLBA_E_INVAL;
+  if (!B->has_data) return MLBA_E_STATE;
+  for (int i = 0; i < k; ++i) CK(cudaGraphLaunch(B->exec, B->stream));
+  return MLBA_OK;
+}
+
+int mlba_batch_active(mlba_batch* B, int* n_active) {
+  if (!B || !n_active) return MLBA_E_INVAL;
+  std::vector<State> st(B->hp.size());
+  CK(cudaMemcpyAsync(st.data(), B->d_states, st.size() * sizeof(State), cudaMemcpyDeviceToHost, B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  int a = 0;
+  for (const State& s : st) a += s.stopped ? 0 : 1;
+  *n_active = a;
+  return MLBA_OK;
+}
+
+int mlba_batch_result(mlba_batch* B, int i, void* f_out, int on_device) {
+  if (!B || i < 0 || i >= (int)B->hp.size()) return MLBA_E_INVAL;
+  const Prob& pd = B->hp[i].pd;
+  return copy_out(B, f_out, pd.buf[SL_F], (size_t)pd.nf * pd.nf * tsize(B->dtype), on_device);
+}
+
+int mlba_batch_stats(mlba_batch* B, int i, mlba_stats* st) {
+  if (!B) return MLBA_E_INVAL;
+  return stats_of(B, i, st);
+}
+
+int mlba_batch_reset(mlba_batch* B) {
+  if (!B) return MLBA_E_INVAL;
+  return reset_batch(B);
+}
+
+int mlba_batch_set_data(mlba_batch* B, int i, const void* g, int on_device, double delta) {
+  if (!B || i < 0 || i >= (int)B->hp.size() || !g || !(delta >= 0.0)) return MLBA_E_INVAL;
+  if (B->hp[i].pd.ns && !(delta > 0.0)) return MLBA_E_INVAL;
+  return set_g(B, i, g, on_device, delta);
+}
+
+int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
+  if (!B || !ms || reps < 1 || stage < 0 || stage > 4) return MLBA_E_INVAL;
+  if (!B->has_data) return MLBA_E_STATE;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const Prob* P = B->d_probs;
+  State* S = B->d_states;
+  cudaStream_t s = B->stream;
+  CK(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) {
+    if (stage == 0) {
+      CK(cudaGraphLaunch(B->exec, s));
+    } else if (B->dtype == MLBA_F64) {
+      if (stage == 1) launch_stencil<double>(ST_FWD_RESID, P, S, B->blur.dev, B->blur.count, SL_F, SL_R, SL_G, 0, B->smem_stencil, s);
+      if (stage == 2) {
+        launch_rows_fwd<double>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_R, 0, B->smem_fft, s);
+        launch_cols<double>(P, S, B->cols_stat.dev, B->cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
+        launch_cols<double>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
+        launch_cols<double>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
+        launch_rows_inv<double>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
+      }
+      if (stage == 3) launch_stencil<double>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
+      if (stage == 4) launch_frame<double, double>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, s);
+    } else {
+      if (stage == 1) launch_stencil<float>(ST_FWD_RESID, P, S, B->blur.dev, B->blur.count, SL_F, SL_R, SL_G, 0, B->smem_stencil, s);
+      if (stage == 2) {
+        launch_rows_fwd<float>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_R, 0, B->smem_fft, s);
+        launch_cols<float>(P, S, B->cols_stat.dev, B->cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
+        launch_cols<float>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
+        launch_cols<float>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
+        launch_rows_inv<float>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
+      }
+      if (stage == 3) launch_stencil<float>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
+      if (stage == 4) {
+        if (B->z_store == MLBA_BF16)
+          launch_frame<float, __nv_bfloat16>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, s);
+        else
+          launch_frame<float, float>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, s);
+      }
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / (float)reps;
+  return MLBA_OK;
+}
+
+int mlba_batch_graph_kernels(mlba_batch* B, int* n) {
+  if (!B || !n || !B->graph) return MLBA_E_INVAL;
+  size_t cnt = 0;
+  CK(cudaGraphGetNodes(B->graph, nullptr, &cnt));
+  std::vector<cudaGraphNode_t> nodes(cnt);
+  CK(cudaGraphGetNodes(B->graph, nodes.data(), &cnt));
+  int k = 0;
+  for (size_t i = 0; i < cnt; ++i) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nodes[i], &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  *n = k;
+  return MLBA_OK;
+}
+
+void mlba_batch_destroy(mlba_batch* B) { destroy_batch(B); }
+
+// ---- single problem ---------------------------------------------------------
+int mlba_create(const double* psf, int p, int n, int bc, int precond, const mlba_opts* opts,
+                mlba_ctx** out) {
+  if (!out) return MLBA_E_INVAL;
+  *out = nullptr;
+  mlba_opts o;
+  if (opts) o = *opts; else mlba_opts_default(&o);
+  mlba_problem pr;
+  std::memset(&pr, 0, sizeof(pr));
+  pr.psf = psf; pr.p = p; pr.n = n; pr.bc = bc; pr.precond = precond; pr.transform = o.transform;
+  pr.max_iter = o.max_iter; pr.mu = o.mu; pr.alpha = o.alpha;
+  pr.delta = precond == MLBA_P_TIKH_NS ? 1.0 : 0.0;   // placeholder until set_data
+  pr.g = nullptr;
+  mlba_batch* B = nullptr;
+  int rc = create_batch(&pr, 1, &o, &B);
+  if (rc != MLBA_OK) return rc;
+  mlba_ctx* c = new (std::nothrow) mlba_ctx();
+  if (!c) { destroy_batch(B); return MLBA_E_NOMEM; }
+  c->b = B;
+  *out = c;
+  return MLBA_OK;
+}
+
+int mlba_set_data(mlba_ctx* c, const void* g, int on_device, double delta) {
+  if (!c || !g || !(delta >= 0.0)) return MLBA_E_INVAL;
+  if (c->b->hp[0].pd.ns && !(delta > 0.0)) return MLBA_E_INVAL;
+  int rc = set_g(c->b, 0, g, on_device, delta);
+  if (rc != MLBA_OK) return rc;
+  rc = reset_batch(c->b);
+  if (rc != MLBA_OK) return rc;
+  c->b->has_data = true;
+  return MLBA_OK;
+}
+
+int mlba_iterate(mlba_ctx* c, int k) {
+  if (!c) return MLBA_E_INVAL;
+  return mlba_batch_iterate(c->b, k);
+}
+
+int mlba_result(mlba_ctx* c, void* f_out, int on_device) {
+  if (!c) return MLBA_E_INVAL;
+  return mlba_batch_result(c->b, 0, f_out, on_device);
+}
+
+int mlba_stats_get(mlba_ctx* c, mlba_stats* st) {
+  if (!c) return MLBA_E_INVAL;
+  return stats_of(c->b, 0, st);
+}
+
+int mlba_history(mlba_ctx* c, double* res, double* alpha, int* beta, int cap) {
+  if (!c || cap < 0) return MLBA_E_INVAL;
+  mlba_stats s;
+  int rc = stats_of(c->b, 0, &s);
+  if (rc != MLBA_OK) return rc;
+  const Prob& pd = c->b->hp[0].pd;
+  const int nres = std::min(s.nres, std::min(cap, pd.max_iter + 2));
+  const int nit = std::min(s.iter, std::min(cap, pd.max_iter + 2));
+  if (res && nres > 0) CK(cudaMemcpy(res, pd.hist_res, nres * sizeof(double), cudaMemcpyDeviceToHost));
+  if (alpha && nit > 0) CK(cudaMemcpy(alpha, pd.hist_alpha, nit * sizeof(double), cudaMemcpyDeviceToHost));
+  if (beta && nit > 0) CK(cudaMemcpy(beta, pd.hist_beta, nit * sizeof(int), cudaMemcpyDeviceToHost));
+  return nres;
+}
+
+int mlba_get_z(mlba_ctx* c, void* z_out, int on_device) {
+  if (!c) return MLBA_E_INVAL;
+  mlba_stats s;
+  int rc = stats_of(c->b, 0, &s);
+  if (rc != MLBA_OK) return rc;
+  const Prob& pd = c->b->hp[0].pd;
+  return copy_out(c->b, z_out, pd.z[s.iter & 1],
+                  (size_t)pd.nbands * pd.nf * pd.nf * zsize(c->b->z_store), on_device);
+}
+
+void mlba_destroy(mlba_ctx* c) {
+  if (!c) return;
+  destroy_batch(c->b);
+  delete c;
+}
+
+// ---- operator entry points ---------------------------------------------------
+int mlba_op_blur(mlba_ctx* c, const void* f, void* out, int on_device) {
+  if (!c) return MLBA_E_INVAL;
+  mlba_batch* B = c->b;
+  const Prob& pd = B->hp[0].pd;
+  const size_t ts = tsize(B->dtype);
+  int rc = copy_in(B, pd.buf[SL_AUX0], f, (size_t)pd.nf * pd.nf * ts, on_device);
+  if (rc != MLBA_OK) return rc;
+  if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
+  if (B->dtype == MLBA_F64)
+    launch_stencil<double>(ST_FWD_STORE, B->d_probs, B->d_opstates, B->blur.dev, B->blur.count,
+                           SL_AUX0, SL_AUX1, SL_AUX1, 0, B->smem_stencil, B->stream);
+  else
+    launch_stencil<float>(ST_FWD_STORE, B->d_probs, B->d_opstates, B->blur.dev, B->blur.count,
+                          SL_AUX0, SL_AUX1, SL_AUX1, 0, B->smem_stencil, B->stream);
+  CK(cudaGetLastError());
+  return copy_out(B, out, pd.buf[SL_AUX1], (size_t)pd.n * pd.n * ts, on_device);
+}
+
+int mlba_op_blur_adjoint(mlba_ctx* c, const void* t, void* out, int on_device) {
+  if (!c) return MLBA_E_INVAL;
+  mlba_batch* B = c->b;
+  const Prob& pd = B->hp[0].pd;
+  const size_t ts = tsize(B->dtype);
+  int rc = copy_in(B, pd.buf[SL_AUX0], t, (size_t)pd.n * pd.n * ts, on_device);
+  if (rc != MLBA_OK) return rc;
+  if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
+  if (B->dtype == MLBA_F64) {
+    launch_stencil<double>(ST_CORR, B->d_probs, B->d_opstates, B->corr_all.dev, B->corr_all.count,
+                           SL_AUX0, SL_V, SL_V, 0, B->smem_stencil, B->stream);
+    if (pd.bc != BC_RECT) launch_vec<double>(VEC_FOLD, B->d_probs, B->d_opstates, B->vec_all.dev, B->vec_all.count, 0, B->stream);
+  } else {
+    launch_stencil<float>(ST_CORR, B->d_probs, B->d_opstates, B->corr_all.dev, B->corr_all.count,
+                          SL_AUX0, SL_V, SL_V, 0, B->smem_stencil, B->stream);
+    if (pd.bc != BC_RECT) launch_vec<float>(VEC_FOLD, B->d_probs, B->d_opstates, B->vec_all.dev, B->vec_all.count, 0, B->stream);
+  }
+  CK(cudaGetLastError());
+  const void* src = pd.bc == BC_RECT ? pd.buf[SL_V] : pd.buf[SL_U];
+  return copy_out(B, out, src, (size_t)pd.nf * pd.nf * ts, on_device);
+}
+
+int mlba_op_precond(mlba_ctx* c, const void* r, void* out, double alpha, int which, int on_device) {
+  if (!c || !(alpha > 0.0) || which < 0 || which > 1) return MLBA_E_INVAL;
+  mlba_batch* B = c->b;
+  const Prob& pd = B->hp[0].pd;
+  if (pd.transform == TR_NONE) return MLBA_E_INVAL;
+  const size_t ts = tsize(B->dtype);
+  int rc = copy_in(B, pd.buf[SL_AUX0], r, (size_t)pd.n * pd.n * ts, on_device);
+  if (rc != MLBA_OK) return rc;
+  if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
+  if (B->dtype == MLBA_F64) {
+    launch_rows_fwd<double>(B->d_probs, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX0, 0, B->smem_fft, B->stream);
+    launch_cols<double>(B->d_probs, B->d_opstates, B->cols_all.dev, B->cols_all.count, COL_OP, 0, alpha, which, B->smem_fft, B->stream);
+    launch_rows_inv<double>(B->d_probs, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX1, 0, B->smem_fft, B->stream);
+  } else {
+    launch_rows_fwd<float>(B->d_probs, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX0, 0, B->smem_fft, B->stream);
+    launch_cols<float>(B->d_probs, B->d_opstates, B->cols_all.dev, B->cols_all.count, COL_OP, 0, alpha, which, B->smem_fft, B->stream);
+    launch_rows_inv<float>(B->d_probs, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX1, 0, B->smem_fft, B->stream);
+  }
+  CK(cudaGetLastError());
+  return copy_out(B, out, pd.buf[SL_AUX1], (size_t)pd.n * pd.n * ts, on_device);
+}
+
+int mlba_op_frame(mlba_ctx* c, const void* z_in, const void* u, void* z_out, void* f, double mu,
+                  int on_device) {
+  if (!c || !z_in || !u || !z_out || !f || !(mu >= 0.0)) return MLBA_E_INVAL;
+  mlba_batch* B = c->b;
+  const Prob& pd = B->hp[0].pd;
+  const size_t ts = tsize(B->dtype);
+  const size_t zbytes = (size_t)pd.nbands * pd.nf * pd.nf * zsize(B->z_store);
+  const size_t fbytes = (size_t)pd.nf * pd.nf * ts;
+  void *dzi = nullptr, *dzo = nullptr;
+  if (on_device) { dzi = const_cast<void*>(z_in); dzo = z_out; }
+  else {
+    CK(cudaMalloc(&dzi, zbytes));
+    CK(cudaMalloc(&dzo, zbytes));
+    CK(cudaMemcpyAsync(dzi, z_in, zbytes, cudaMemcpyHostToDevice, B->stream));
+  }
+  int rc = copy_in(B, pd.buf[SL_AUX0], u, fbytes, on_device);
+  if (rc != MLBA_OK) return rc;
+  if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
+  if (B->dtype == MLBA_F64)
+    launch_frame<double, double>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->stream);
+  else if (B->z_store == MLBA_BF16)
+    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->stream);
+  else
+    launch_frame<float, float>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->stream);
+  CK(cudaGetLastError());
+  rc = copy_out(B, f, pd.buf[SL_AUX1], fbytes, on_device);
+  if (rc != MLBA_OK) return rc;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(z_out, dzo, zbytes, cudaMemcpyDeviceToHost, B->stream));
+    CK(cudaStreamSynchronize(B->stream));
+    cudaFree(dzi);
+    cudaFree(dzo);
+  }
+  return MLBA_OK;
+}
+
+int mlba_op_ns_alpha(mlba_ctx* c, const void* r, double qn, double* alpha_out, int on_device) {
+  if (!c || !alpha_out || !(qn > 0.0 && qn < 1.0)) return MLBA_E_INVAL;
+  mlba_batch* B = c->b;
+  const Prob& pd = B->hp[0].pd;
+  if (pd.transform == TR_NONE) return MLBA_E_INVAL;
+  const size_t ts = tsize(B->dtype);
+  int rc = copy_in(B, pd.buf[SL_AUX0], r, (size_t)pd.n * pd.n * ts, on_device);
+  if (rc != MLBA_OK) return rc;
+  // op state: Newton armed at log(alpha) = 0
+  State s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.ns_active = 1; s0.qn = qn; s0.nb = 0.0; s0.nb_lo = -INFINITY; s0.nb_hi = INFINITY;
+  s0.iter = 0; s0.stop_iter = -1;
+  CK(cudaMemcpyAsync(B->d_opstates, &s0, sizeof(State), cudaMemcpyHostToDevice, B->stream));
+  // a temporary descriptor with the nonstationary flag set and no floor
+  Prob tmp = pd;
+  tmp.ns = 1;
+  tmp.bc = (pd.bc == BC_RECT) ? BC_PERIODIC : pd.bc;   // no rectangular floor here
+  tmp.max_iter = -1;                                    // no history writes
+  Prob* dtmp = nullptr;
+  CK(cudaMalloc(&dtmp, sizeof(Prob)));
+  CK(cudaMemcpyAsync(dtmp, &tmp, sizeof(Prob), cudaMemcpyHostToDevice, B->stream));
+  if (B->dtype == MLBA_F64) {
+    launch_rows_fwd<double>(dtmp, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX0, 0, B->smem_fft, B->stream);
+    launch_cols<double>(dtmp, B->d_opstates, B->cols_all.dev, B->cols_all.count, COL_FWD, 0, 0.0, 0, B->smem_fft, B->stream);
+    for (int k = 0; k < 60; ++k) launch_spec<double>(dtmp, B->d_opstates, B->spec_all.dev, B->spec_all.count, B->stream);
+  } else {
+    launch_rows_fwd<float>(dtmp, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX0, 0, B->smem_fft, B->stream);
+    launch_cols<float>(dtmp, B->d_opstates, B->cols_all.dev, B->cols_all.count, COL_FWD, 0, 0.0, 0, B->smem_fft, B->stream);
+    for (int k = 0; k < 60; ++k) launch_spec<float>(dtmp, B->d_opstates, B->spec_all.dev, B->spec_all.count, B->stream);
+  }
+  CK(cudaGetLastError());
+  State s1;
+  CK(cudaMemcpyAsync(&s1, B->d_opstates, sizeof(State), cudaMemcpyDeviceToHost, B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  cudaFree(dtmp);
+  *alpha_out = s1.alpha_n;
+  return MLBA_OK;
+}
+
+int mlba_op_spectrum(mlba_ctx* c, double* out, int* rows, int* cols, int* is_complex) {
+  if (!c || !out) return MLBA_E_INVAL;
+  mlba_batch* B = c->b;
+  const Prob& pd = B->hp[0].pd;
+  if (pd.transform == TR_NONE) return MLBA_E_INVAL;
+  const bool dct = pd.transform == TR_DCT;
+  const size_t W = dct ? pd.n : pd.half;
+  const size_t cnt = (size_t)pd.n * W * (dct ? 1 : 2);
+  std::vector<unsigned char> tmp(cnt * tsize(B->dtype));
+  CK(cudaMemcpy(tmp.data(), pd.lam, tmp.size(), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < cnt; ++i)
+    out[i] = B->dtype == MLBA_F64 ? reinterpret_cast<double*>(tmp.data())[i]
+                                  : (double)reinterpret_cast<float*>(tmp.data())[i];
+  if (rows) *rows = pd.n;
+  if (cols) *cols = (int)W;
+  if (is_complex) *is_complex = dct ? 0 : 1;
+  return MLBA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// mlba_internal.cuh — device-side data model shared by the kernels and the
+// host runtime of the MLBA library.  Every kernel is batched: a launch walks
+// an item list of (problem, block) pairs so that one launch serves all
+// problems of a batch (a single problem is a batch of one).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace mlba {
+
+// ----------------------------------------------------------------------------
+// enumerations mirrored from include/mlba.h
+enum { BC_ZERO = 0, BC_PERIODIC = 1, BC_REFLECTIVE = 2, BC_RECT = 3 };
+enum { P_NONE = 0, P_BCCB = 1, P_KRYLOV = 2, P_SYM = 3, P_TIKH = 4, P_TIKH_NS = 5 };
+enum { TR_NONE = 0, TR_DFT = 1, TR_DCT = 2 };
+
+// per-problem buffer slots; kernels pick their operands by slot so that the
+// same kernel serves the main loop, the PCG of Algorithm 2 and the operator
+// entry points
+enum Slot {
+  SL_G = 0,   // observed image g (n x n)
+  SL_F,       // current image f (Nf x Nf)
+  SL_R,       // residual r (n x n)
+  SL_T,       // preconditioned residual t (n x n)
+  SL_V,       // full correlation of t on the extended (n+p-1)^2 domain
+  SL_U,       // BC-folded A^T t (n x n); PCG work
+  SL_S,       // transform work array (n x (n+2) reals)
+  SL_PX, SL_PRES, SL_PP, SL_PQ, SL_PZ,  // PCG vectors (n x n)
+  SL_AUX0, SL_AUX1,                     // operator entry-point scratch (Nf x Nf)
+  NSLOT
+};
+
+constexpr int MAX_STAGES = 24;
+constexpr int MAX_LEVELS = 6;
+
+// Constant description of one problem (device copy lives in a table).
+struct Prob {
+  int n, p, c, nf, ne, half;     // half = n/2+1
+  int bc, precond, transform, levels, nbands;
+  int ns;            // nonstationary alpha (4-NS)
+  int use_adj;       // 1: u = A^T t ; 0: u = t (Algorithm 4 forms)
+  int sep;           // rank-one PSF: separable stencils
+  int ntaps;         // nonzero taps of the PSF
+  int max_iter, stop, pcg_max;
+  int nstage;        // FFT plan of length n
+  int radix[MAX_STAGES];
+  // per-list block counts (reductions need them)
+  int nblk_blur, nblk_corr, nblk_frame, nblk_rows, nblk_cols, nblk_spec, nblk_vec;
+  int row_g, col_g;  // transforms per CTA in the row / column passes
+  double mu, alpha, gamma, delta, q, rho, tau, pcg_tol;
+  void* buf[NSLOT];
+  void* z[2];        // ping-pong Bregman variable
+  void* w;           // stationary spectral weight (includes 1/n^2)
+  void* lam;         // spectrum of C (real for DCT, complex half for DFT), T precision
+  double* sigma;     // |lambda|^2 in FP64
+  void* tw;          // exp(-2 pi i k/n), k < n   (T2)
+  void* dtw;         // exp(-i pi k/(2n)), k < n  (T2)
+  int* tap_dy; int* tap_dx; void* tap_w;   // nonzero taps (offsets from centre)
+  void* hy; void* hx;                      // separable factors (length p)
+  double* partial;   // reduction partials (capacity per problem)
+  double* hist_res; double* hist_alpha; int* hist_beta;  // history, max_iter+2
+};
+
+// Mutable per-problem state (device).
+struct State {
+  int iter;          // z-updates done (f = f^iter)
+  int stopped;       // no more updates
+  int stop_iter;     // first n with the rule satisfied, -1 if none
+  int status;        // 0 or MLBA_E_DIVERGED
+  int nres;          // residuals computed
+  unsigned int counter;  // last-block reduction counter
+  int ns_active;     // 4-NS: alpha_n being solved this iteration
+  int nconv;         // 4-NS Newton converged
+  int npass;
+  int pdone, psteps; // PCG
+  int beta_last;
+  double resnorm, alpha_n, qn;
+  double nb, nb_lo, nb_hi;     // Newton on log(alpha)
+  double prho, prho0, pa, pbeta;
+};
+
+// ----------------------------------------------------------------------------
+// small helpers
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <typename T2, typename T>
+__host__ __device__ __forceinline__ T2 mk2(T a, T b) { T2 r; r.x = a; r.y = b; return r; }
+
+template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { a.x += b.x; a.y += b.y; return a; }
+template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  T2 r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename T2> __device__ __forceinline__ T2 cconj(T2 a) { a.y = -a.y; return a; }
+
+// storage conversions for z
+__device__ __forceinline__ float ld_z(const float* p) { return *p; }
+__device__ __forceinline__ double ld_z(const double* p) { return *p; }
+__device__ __forceinline__ float ld_z(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void st_z(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_z(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st_z(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+// Table 1 boundary map: FOV index copied by extended index e, or -1 (zero).
+__device__ __forceinline__ int bc_map(int e, int n, int bc) {
+  if (e >= 0 && e < n) return e;
+  if (bc == BC_ZERO) return -1;
+  if (bc == BC_PERIODIC) { int q = e % n; return q < 0 ? q + n : q; }
+  int m2 = 2 * n;
+  int q = e % m2; if (q < 0) q += m2;
+  return q < n ? q : m2 - 1 - q;
+}
+
+// half-sample symmetric reflection used by the framelets; *odd tells whether
+// an odd number of mirrorings happened (antisymmetric bands flip sign)
+__device__ __forceinline__ int refl_half(int e, int n, int* odd) {
+  int m2 = 2 * n;
+  int q = e % m2; if (q < 0) q += m2;
+  // e = q + k*2n; each period contains two mirrorings, so parity is that of q >= n
+  if (q < n) { *odd = 0; return q; }
+  *odd = 1; return m2 - 1 - q;
+}
+
+// block-wide sum of a double (deterministic order); all threads must call
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = (threadIdx.x < NT / 32) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+// Last-block reduction: every block of problem `pi` calls this with its K
+// partial values (valid in thread 0); the block that arrives last returns
+// true with the K totals (summed in block order) in tot[] (valid in thread 0).
+template <int NT, int K>
+__device__ bool last_block_reduce(const Prob& pd, State& st, int blk, int nblk,
+                                  const double* vals, double* tot, double* sh) {
+  __shared__ int is_last;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < K; ++k) pd.partial[(size_t)k * nblk + blk] = vals[k];
+    __threadfence();
+    unsigned int prev = atomicAdd(&st.counter, 1u);
+    is_last = (prev == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += NT) s += __ldcg(&pd.partial[(size_t)k * nblk + i]);
+    s = block_sum<NT>(s, sh);
+    if (threadIdx.x == 0) tot[k] = s;
+  }
+  if (threadIdx.x == 0) st.counter = 0u;
+  return true;
+}
+
+// BC fold of the extended correlation: u(a,b) = sum over the padded positions
+// that copy (a,b) (transpose of the Table 1 padding).
+template <typename T>
+__device__ __forceinline__ T fold_fetch(const Prob& pd, const T* V, int a, int b) {
+  const int n = pd.n, c = pd.c, ne = pd.ne;
+  int cy[3], cx[3], ny = 1, nx = 1;
+  cy[0] = a; cx[0] = b;
+  if (pd.bc == BC_PERIODIC) {
+    if (a + n <= n - 1 + c) cy[ny++] = a + n;
+    if (a - n >= -c) cy[ny++] = a - n;
+    if (b + n <= n - 1 + c) cx[nx++] = b + n;
+    if (b - n >= -c) cx[nx++] = b - n;
+  } else if (pd.bc == BC_REFLECTIVE) {
+    if (-1 - a >= -c) cy[ny++] = -1 - a;
+    if (2 * n - 1 - a <= n - 1 + c) cy[ny++] = 2 * n - 1 - a;
+    if (-1 - b >= -c) cx[nx++] = -1 - b;
+    if (2 * n - 1 - b <= n - 1 + c) cx[nx++] = 2 * n - 1 - b;
+  }
+  T s = T(0);
+  for (int i = 0; i < ny; ++i)
+    for (int j = 0; j < nx; ++j) s += V[(size_t)(cy[i] + c) * ne + (cx[j] + c)];
+  return s;
+}
+
+}  // namespace mlba

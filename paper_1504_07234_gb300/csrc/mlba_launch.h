@@ -1,0 +1,78 @@
+// mlba_launch.h — host-side launchers of the batched MLBA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include "mlba_internal.cuh"
+
+namespace mlba {
+
+// stencil modes (k_stencil.cu)
+enum {
+  ST_FWD_RESID = 0,   // dst = g - A src ; ||dst||^2 -> iteration bookkeeping (stop rule)
+  ST_FWD_STORE = 1,   // dst = A src
+  ST_FWD_PCGQ = 2,    // dst = A src + alpha aux ; <aux, dst> -> PCG step length
+  ST_CORR = 3         // dst (ne x ne) = full correlation of src (n x n, zero padded)
+};
+// vector kernels (k_stencil.cu)
+enum {
+  VEC_FOLD = 0,       // U = BC fold of V
+  VEC_PCG_INIT = 1,   // PX = 0, PRES = R
+  VEC_PCG_RHO0 = 2,   // rho0 = <PRES, PZ>, PP = PZ
+  VEC_PCG_AXPY = 3,   // PX += a PP, PRES -= a PQ
+  VEC_PCG_RHO = 4,    // rho = <PRES, PZ>, convergence test
+  VEC_PCG_PUPD = 5,   // PP = PZ + beta PP
+  VEC_PCG_FINISH = 6  // T = PX
+};
+// column-pass modes (k_fft.cu)
+enum {
+  COL_FUSED = 0,      // forward, weight (stationary alpha), inverse
+  COL_FWD = 1,        // forward only, spectrum kept in S (4-NS)
+  COL_NS_INV = 2,     // weight with alpha_n, inverse (4-NS)
+  COL_OP = 3          // forward, weight with the operator's alpha / kind, inverse
+};
+enum { W_INV = 0, W_TIKH = 1 };
+
+constexpr int STENCIL_THREADS = 256;
+constexpr int VEC_THREADS = 256;
+constexpr int VEC_PER_THREAD = 8;
+constexpr int TR_THREADS = 512;
+constexpr int TR_MAXV = 16;           // complex values per thread in the smem FFT (FP32)
+constexpr int TR_MAXV_F64 = 8;        // the same for FP64
+constexpr int FRAME_THREADS = 256;
+constexpr int FRAME_TILE = 32;
+constexpr int SPEC_THREADS = 512;
+constexpr int SPEC_PER_THREAD = 16;
+
+template <typename T>
+void launch_stencil(int mode, const Prob* probs, State* states, const int2* items, int nitems,
+                    int src, int dst, int aux, int pcg, size_t smem, cudaStream_t s);
+template <typename T>
+void launch_vec(int mode, const Prob* probs, State* states, const int2* items, int nitems,
+                int pcg, cudaStream_t s);
+template <typename T>
+void launch_rows_fwd(const Prob* probs, State* states, const int2* items, int nitems, int src,
+                     int pcg, size_t smem, cudaStream_t s);
+template <typename T>
+void launch_cols(const Prob* probs, State* states, const int2* items, int nitems, int mode,
+                 int pcg, double op_alpha, int op_kind, size_t smem, cudaStream_t s);
+template <typename T>
+void launch_rows_inv(const Prob* probs, State* states, const int2* items, int nitems, int dst,
+                     int pcg, size_t smem, cudaStream_t s);
+template <typename T>
+void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, cudaStream_t s);
+void launch_spectrum_setup(const Prob* probs, int pi, int transform, int n, int p, int half,
+                           const double* q_dev, const double* tab_dev, double* sigma,
+                           void* lam, int is_double, cudaStream_t s);
+template <typename T, typename TZ>
+void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, int u_slot,
+                  int f_slot, const void* zin, void* zout, double op_mu, size_t smem,
+                  cudaStream_t s);
+template <typename T, typename TZ>
+size_t frame_smem_bytes(int levels);
+template <typename T, typename TZ>
+cudaError_t frame_set_smem(size_t bytes);
+template <typename T>
+cudaError_t stencil_set_smem(size_t bytes);
+template <typename T>
+cudaError_t fft_set_smem(size_t bytes);
+
+}  // namespace mlba

@@ -1,0 +1,196 @@
+"""GPU parity of whole MLBA runs (Eq. MLBA2, Algorithms 1-4, 4-NS) against the
+FP64 oracle, called through the C ABI.
+
+FP64 path: the restoration f, the residual-norm history, alpha_n and beta_n
+match the oracle to rounding (tolerances below).  FP32 path (FP64 norms,
+denominators and alpha_n): restoration-level bars — RRE within 1e-3, PSNR
+within 0.05 dB, the discrepancy stop within one iteration — plus a relative
+image difference bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mlba_inputs as I
+from oracle import mlba_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1504_07234_gb300.build import build
+    build()
+    import paper_1504_07234_gb300 as mod
+    return mod
+
+
+def run_gpu(M, pr, dtype="f64", z_store=None, iters=None, stop=None):
+    stop = pr.stop if stop is None else stop
+    max_iter = pr.max_iter if iters is None else iters
+    ctx = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype=dtype, z_store=z_store,
+                    mu=pr.mu, alpha=pr.alpha, levels=pr.levels, max_iter=max_iter, stop=stop,
+                    gamma=pr.gamma, q=pr.q, rho=pr.rho, transform=pr.transform,
+                    rect_ns_hybrid=pr.rect_ns_hybrid)
+    ctx.set_data(pr.g, pr.delta)
+    st = ctx.run(max_iter)
+    f = ctx.result()
+    res, al, be = ctx.history()
+    ctx.close()
+    return f, st, res, al, be
+
+
+def run_oracle(pr, iters=None, stop=None):
+    stop = pr.stop if stop is None else stop
+    return O.mlba(pr.g, pr.psf, pr.delta, pr.bc, pr.precond, pr.mu, pr.alpha, pr.levels,
+                  pr.max_iter if iters is None else iters, stop=stop, gamma=pr.gamma, q=pr.q,
+                  rho=pr.rho, transform=pr.transform, rect_ns_hybrid=pr.rect_ns_hybrid)
+
+
+def small(bc, precond, n=40, psf=None, levels=2, alpha=0.3, mu=10 / 255, iters=12,
+          transform="auto", nu=0.01, seed=21):
+    psf = I.psf_motion(7, 0.9) if psf is None else psf
+    p = psf.shape[0]
+    f = I.true_image(n + p - 1, seed)
+    g, delta = I.observe(f, psf, nu, seed)
+    return I.Problem(g=g, psf=psf, delta=delta, bc=bc, precond=precond, mu=mu, alpha=alpha,
+                     levels=levels, max_iter=iters, stop=False, transform=transform, f_true=f,
+                     rect_ns_hybrid=(bc == "rect" and precond == "tikh_ns"))
+
+
+CASES = [
+    ("rect", "none", "auto", I.psf_motion(7, 0.9), 0.3),
+    ("rect", "bccb", "dft", I.psf_motion(7, 0.9), 0.3),
+    ("rect", "bccb", "dct", I.psf_gaussian(1.5, 7), 0.1),
+    ("rect", "krylov", "dft", I.psf_motion(7, 0.9), 0.05),
+    ("rect", "sym", "auto", I.psf_motion(7, 0.9), 0.5),
+    ("rect", "tikh_ns", "dct", I.psf_gaussian(1.5, 7), 0.05),
+    ("zero", "bccb", "dft", I.psf_motion(7, 0.9), 0.3),
+    ("zero", "krylov", "dft", I.psf_motion(7, 0.9), 0.05),
+    ("zero", "tikh", "dft", I.psf_motion(7, 0.9), 0.05),
+    ("periodic", "bccb", "dft", I.psf_motion(7, 0.9), 0.05),
+    ("periodic", "tikh_ns", "dft", I.psf_motion(7, 0.9), 0.05),
+    ("reflective", "sym", "auto", I.psf_motion(7, 0.9), 0.3),
+    ("reflective", "tikh", "dct", I.psf_disk(3), 0.02),
+    ("reflective", "tikh_ns", "dct", I.psf_disk(3), 0.05),
+    ("reflective", "krylov", "dct", I.psf_disk(3), 0.02),
+]
+
+
+@pytest.mark.parametrize("bc,precond,transform,psf,alpha", CASES,
+                         ids=[f"{c[0]}-{c[1]}-{c[2]}" for c in CASES])
+def test_fp64_loop_matches_oracle(M, bc, precond, transform, psf, alpha):
+    n = 48 if bc != "rect" else 42       # several tiles, ragged tails, FFT radix 2 and 3
+    pr = small(bc, precond, n=n, psf=psf, alpha=alpha, transform=transform)
+    f, st, res, al, be = run_gpu(M, pr, "f64")
+    ref = run_oracle(pr)
+    assert st["iter"] == ref["iters"]
+    scale = np.abs(ref["f"]).max()
+    assert np.abs(f - ref["f"]).max() <= 1e-9 * scale
+    np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-9)
+    if precond == "tikh_ns":
+        np.testing.assert_allclose(al, ref["alphas"], rtol=1e-8)
+    if precond == "krylov":
+        assert list(be) == ref["betas"]
+
+
+def test_fp64_stop_rule_matches_oracle(M):
+    pr = I.config(2, n=64)
+    pr.precond, pr.transform = "tikh", "dct"
+    pr.alpha = 0.02
+    pr.max_iter = 300
+    f, st, res, al, be = run_gpu(M, pr, "f64", stop=True)
+    ref = run_oracle(pr, stop=True)
+    assert st["stopped"] == 1 and st["stop_iter"] == ref["stop_iter"] == st["iter"]
+    assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
+
+
+def test_config1_fp64_plain(M):
+    """Workload 1: 64x64 rectangular FP64, BCCB (DFT), L = 1, 200 iterations."""
+    pr = I.config(1)
+    f, st, res, al, be = run_gpu(M, pr, "f64")
+    ref = run_oracle(pr)
+    assert st["iter"] == 200
+    assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
+    np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-9)
+
+
+def restoration_bars(f_gpu, ref, pr):
+    t = pr.truth_in_fov()
+    rre_g, rre_o = O.rre(f_gpu, t), O.rre(ref["f"], t)
+    ps_g, ps_o = O.psnr(f_gpu, t), O.psnr(ref["f"], t)
+    assert abs(rre_g - rre_o) <= 1e-3, (rre_g, rre_o)
+    assert abs(ps_g - ps_o) <= 0.05, (ps_g, ps_o)
+    return rre_g, rre_o
+
+
+def test_config2_fp32_ns(M):
+    """Workload 2: reflective 256x256, 15x15 disk, Algorithm 4-NS (DCT), L = 2,
+    discrepancy stop at tau*delta; FP32 with FP64 norms / alpha_n."""
+    pr = I.config(2)
+    f, st, res, al, be = run_gpu(M, pr, "f32")
+    ref = run_oracle(pr)
+    assert abs(st["stop_iter"] - ref["stop_iter"]) <= 1
+    restoration_bars(f, ref, pr)
+    k = min(len(al), len(ref["alphas"]))
+    np.testing.assert_allclose(al[:k], ref["alphas"][:k], rtol=1e-3)
+
+
+def test_config2_fp64_ns(M):
+    pr = I.config(2)
+    f, st, res, al, be = run_gpu(M, pr, "f64")
+    ref = run_oracle(pr)
+    assert st["stop_iter"] == ref["stop_iter"]
+    assert np.abs(f - ref["f"]).max() <= 1e-8 * np.abs(ref["f"]).max()
+    np.testing.assert_allclose(al, ref["alphas"], rtol=1e-8)
+
+
+@pytest.mark.parametrize("variant", ["rect1", "rect2", "rect3"])
+def test_config3_reduced_fp32_bf16(M, variant):
+    """Workload 3 at 192x192 for 30 iterations: FP32 transforms and stencils
+    with the Bregman variable stored in bf16 (and in FP32 for comparison)."""
+    pr = I.config(3, variant=variant, n=192)
+    ref = run_oracle(pr, iters=30)
+    f32, st, *_ = run_gpu(M, pr, "f32", iters=30)
+    restoration_bars(f32, ref, pr)
+    fb, st, *_ = run_gpu(M, pr, "f32", z_store="bf16", iters=30)
+    t = pr.truth_in_fov()
+    assert abs(O.rre(fb, t) - O.rre(ref["f"], t)) <= 5e-3
+
+
+def test_batch_matches_single(M):
+    """Mixed batch (sizes, PSFs, BCs, preconditioners) advanced by one graph
+    launch per step equals the problems run one by one (FP64, bit-for-bit
+    identical kernels, so up to reduction order: same kernels, same order)."""
+    probs = [small("rect", "bccb", n=40, transform="dft", iters=10),
+             small("reflective", "tikh_ns", n=48, psf=I.psf_disk(3), transform="dct", iters=10, seed=3),
+             small("periodic", "tikh_ns", n=36, psf=I.psf_motion(5, 0.2), iters=10, seed=4),
+             small("rect", "bccb", n=60, psf=I.psf_gaussian(1.2, 7), transform="dct", iters=10, seed=5)]
+    descs = [dict(psf=p.psf, g=p.g, delta=p.delta, bc=p.bc, precond=p.precond, mu=p.mu,
+                  alpha=p.alpha, transform=p.transform, max_iter=p.max_iter) for p in probs]
+    b = M.Batch(descs, dtype="f64", levels=2, stop=False, max_iter=10, rect_ns_hybrid=True)
+    b.iterate(11)
+    for i, p in enumerate(probs):
+        ref = run_oracle(p)
+        fb = b.result(i)
+        assert b.stats(i)["iter"] == 10
+        assert np.abs(fb - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max(), i
+    b.close()
+
+
+def test_batch_own_stop_rules(M):
+    """Each problem of a batch stops on its own discrepancy rule."""
+    probs = I.batch_problems(count=6, sizes=(64, 96, 128), max_iter=300)
+    descs = [dict(psf=p.psf, g=p.g, delta=p.delta, bc=p.bc, precond=p.precond, mu=p.mu,
+                  alpha=p.alpha, max_iter=p.max_iter) for p in probs]
+    b = M.Batch(descs, dtype="f32", levels=2, stop=True, max_iter=300)
+    b.iterate(301)
+    assert b.active() == 0
+    for i, p in enumerate(probs):
+        ref = run_oracle(p)
+        st = b.stats(i)
+        if ref["stop_iter"] is not None:
+            assert abs(st["stop_iter"] - ref["stop_iter"]) <= 1, (i, st, ref["stop_iter"])
+        restoration_bars(b.result(i), ref, p)
+    b.close()
