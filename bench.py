@@ -131,7 +131,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]})
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
@@ -210,6 +210,8 @@ def main():
     ap.add_argument("--impl", default="mlba", choices=["mlba", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
+    ap.add_argument("--problems", type=int, default=64,
+                    help="first K problems of the batch (small cases for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -230,7 +232,7 @@ def main():
         dist.barrier()
     import paper_1504_07234_gb300 as M
 
-    probs = problems_for_rank(rank)
+    probs = problems_for_rank(rank)[: args.problems]
     mpix = sum(p.n * p.n for p in probs) / 1e6
     K, W = args.steps, args.warmup
     reps_prof = 20
@@ -316,7 +318,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
                 "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "problems": 64, "mpix_per_step_per_gpu": mpix,
+                "config": {"workload": WORKLOAD if len(probs) == 64 else f"first {len(probs)} problems of: " + WORKLOAD,
+                           "problems": len(probs), "mpix_per_step_per_gpu": mpix,
                            "l2": "inputs larger than L2 (Bregman variable ~2.7 GB)",
                            "parallelism": f"replicas x{ws}, problems sharded"},
                 "clocks": ck, "e2e": e2e, "gpu_launches": kernels * K, "roofline": roofline,

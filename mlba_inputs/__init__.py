@@ -208,7 +208,7 @@ def config(i: int, variant: str | None = None, n: int | None = None) -> Problem:
         ang = float(rng.uniform(0.0, math.pi))
         psf = psf_motion(21, ang)
         variant = variant or "rect1"
-        pc, al = {"rect1": ("bccb", 0.3), "rect2": ("krylov", 0.05),
+        pc, al = {"rect1": ("bccb", 0.5), "rect2": ("krylov", 0.05),
                   "rect3": ("sym", 0.5)}[variant]
         return _make(n or 1024, psf, 0.01, 3, bc="rect", precond=pc, mu=mu,
                      alpha=al, levels=2, max_iter=200, stop=False,
@@ -231,7 +231,9 @@ def batch_problems(count: int = 64, seed: int = 4, sizes=BATCH_SIZES,
     disk r~U{2..8}, motion length~U{5,7,..,21} at angle~U[0,pi); BC uniform
     over periodic / reflective / rectangular; noise nu~U[0.005, 0.03].  BC
     problems run the nonstationary Algorithm 4-NS, rectangular ones the
-    BCCB-preconditioned Algorithm 1; each stops on its own discrepancy rule.
+    BCCB-preconditioned Algorithm 1 with alpha = 0.5 (the smallest of
+    0.3 / 0.5 at which Eq. condconvalg1 holds for every PSF of the family);
+    each stops on its own discrepancy rule.
     """
     rng = np.random.default_rng([seed, 0xba7c])
     out = []
@@ -249,6 +251,6 @@ def batch_problems(count: int = 64, seed: int = 4, sizes=BATCH_SIZES,
         nu = float(rng.uniform(0.005, 0.03))
         pc = "bccb" if bc == "rect" else "tikh_ns"
         out.append(_make(n, psf, nu, 1000 + k, bc=bc, precond=pc,
-                         mu=10.0 / 255.0, alpha=0.3, levels=2,
+                         mu=10.0 / 255.0, alpha=0.5, levels=2,
                          max_iter=max_iter, stop=True, name=f"C4-{k}"))
     return out

@@ -466,11 +466,19 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 4-NS: one Newton pass for alpha_n on log(alpha).  With a unitary
-// transform, Eq. Alg4_rev_7 reads F(a)/P = q_n^2 with P = sum |r^|^2,
-// F(a) = sum |r^|^2 (a/(s+a))^2; d F / d log a = sum 2 |r^|^2 x^2 (1-x),
-// x = a/(s+a).  The spectrum in S is the unnormalised one; the ratio is
-// scale free once each coefficient carries its orthonormal weight.  Each block sums its share; the last block takes the step.
+// Algorithm 4-NS: alpha_n of Eq. Alg4_rev_7.  With a unitary transform the
+// equation reads h(b) = F(a)/P - q_n^2 = 0, a = exp(b), P = sum |r^|^2,
+// F(a) = sum |r^|^2 x^2, x = a/(s+a); h increases with b (unique root), and
+// dh/db = sum 2 |r^|^2 x^2 (1-x) / P.  The spectrum in S is the unnormalised
+// one; every coefficient carries its orthonormal weight, so the ratio is
+// exact.  Pass 1 evaluates h at NS_CAND points b_prev + (j - 15.5) * 0.8 and
+// brackets the root within a factor e^0.8; later passes take safeguarded
+// Newton steps inside the bracket until |step| <= tol.  Each block sums its
+// share in T precision (FP64 accumulation across blocks); the last block
+// updates the scalar state.
+constexpr int NS_CAND = 32;
+constexpr double NS_CAND_STEP = 0.8;
+
 template <typename T>
 __global__ void __launch_bounds__(SPEC_THREADS)
 k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items) {
@@ -487,8 +495,19 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   const size_t chunk = (size_t)SPEC_THREADS * SPEC_PER_THREAD;
   const size_t beg = (size_t)item.y * chunk;
   const size_t end = beg + chunk < tot ? beg + chunk : tot;
-  const double alpha = exp(st.nb);
+  const bool cand = (st.nphase == 0);
+  const double b0 = st.nb;
+  const double alpha = exp(b0);
+  // per-thread partial sums
   T sP = T(0), sF = T(0), sG = T(0);
+  float cF[NS_CAND];
+#pragma unroll
+  for (int j = 0; j < NS_CAND; ++j) cF[j] = 0.f;
+  float ca[NS_CAND];
+  if (cand) {
+#pragma unroll
+    for (int j = 0; j < NS_CAND; ++j) ca[j] = (float)exp(b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
+  }
   for (size_t i = beg + threadIdx.x; i < end; i += SPEC_THREADS) {
     T pw;
     if (dct) {
@@ -504,12 +523,53 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
       const T m = (k2 == 0 || ((N & 1) == 0 && k2 == N / 2)) ? T(1) : T(2);
       pw = m * (v.x * v.x + v.y * v.y);
     }
-    const double d = pd.sigma[i] + alpha;       // FP64 denominator
-    const T x = (sizeof(T) == 8) ? T(alpha / d) : T(alpha) / T(d);
-    const T x2 = x * x;
+    const double sg = pd.sigma[i];
     sP += pw;
-    sF += pw * x2;
-    sG += T(2) * pw * x2 * (T(1) - x);
+    if (cand) {
+      const float pf = (float)pw, sf = (float)sg;
+#pragma unroll
+      for (int j = 0; j < NS_CAND; ++j) {
+        const float x = __fdividef(ca[j], sf + ca[j]);
+        cF[j] += pf * x * x;
+      }
+    } else {
+      const double d = sg + alpha;                 // FP64 denominator
+      const T x = (sizeof(T) == 8) ? T(alpha / d) : T(alpha) / T(d);
+      const T x2 = x * x;
+      sF += pw * x2;
+      sG += T(2) * pw * x2 * (T(1) - x);
+    }
+  }
+  if (cand) {
+    double v[NS_CAND + 1], t[NS_CAND + 1];
+    v[0] = block_sum<SPEC_THREADS>((double)sP, red);
+#pragma unroll 1
+    for (int j = 0; j < NS_CAND; ++j) v[j + 1] = block_sum<SPEC_THREADS>((double)cF[j], red);
+    if (last_block_reduce<SPEC_THREADS, NS_CAND + 1>(pd, st, item.y, pd.nblk_spec, v, t, red) &&
+        threadIdx.x == 0) {
+      const double P = t[0], target = st.qn * st.qn;
+      int j = 0;
+      while (j < NS_CAND && !(P > 0.0 && t[j + 1] / P - target >= 0.0)) ++j;
+      const double bj = b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP;
+      double nb;
+      if (j == 0) { st.nb_lo = -INFINITY; st.nb_hi = bj; nb = bj - NS_CAND_STEP; }
+      else if (j == NS_CAND) { st.nb_lo = bj - NS_CAND_STEP; st.nb_hi = INFINITY; nb = bj; }
+      else {
+        const double hl = t[j] / P - target, hh = t[j + 1] / P - target;
+        st.nb_lo = bj - NS_CAND_STEP; st.nb_hi = bj;
+        nb = st.nb_lo + (hh > hl ? (-hl) / (hh - hl) : 0.5) * NS_CAND_STEP;
+      }
+      if (nb < -32.2) nb = -32.2;
+      st.nb = nb;
+      st.nphase = 1;
+      st.npass += 1;
+      double a = exp(nb);
+      if (pd.bc == BC_RECT && a < pd.alpha) a = pd.alpha;   // rectangular hybrid floor
+      st.alpha_n = a;
+      const int it = st.iter - 1;
+      if (it >= 0 && it < pd.max_iter + 2) pd.hist_alpha[it] = a;
+    }
+    return;
   }
   double v3[3];
   v3[0] = block_sum<SPEC_THREADS>((double)sP, red);
@@ -522,23 +582,30 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
     const double target = st.qn * st.qn;
     const double h = (P > 0.0) ? t3[1] / P - target : 0.0;
     const double hp = (P > 0.0) ? t3[2] / P : 0.0;
-    double nb = st.nb;
-    if (h < 0.0) st.nb_lo = nb; else st.nb_hi = nb;
-    double nn = (hp > 0.0) ? nb - h / hp : nb;
-    const bool lo_ok = isfinite(st.nb_lo), hi_ok = isfinite(st.nb_hi);
-    if (!(hp > 0.0) || !isfinite(nn)) {
+    const double tol = (sizeof(T) == 8) ? 1e-10 : 1e-5;
+    const double nb = b0;
+    if (h < 0.0) st.nb_lo = fmax(st.nb_lo, nb);
+    else if (h > 0.0) st.nb_hi = fmin(st.nb_hi, nb);
+    double nn;
+    bool conv = false;
+    if (hp > 0.0 && isfinite(h / hp)) {
+      const double step = h / hp;
+      nn = nb - step;
+      conv = fabs(step) <= tol;        // quadratic convergence: nn is accurate
+    } else {
       nn = (h < 0.0) ? nb + 2.0 : nb - 2.0;
     }
-    if (lo_ok && hi_ok) {
-      if (!(nn > st.nb_lo && nn < st.nb_hi)) nn = 0.5 * (st.nb_lo + st.nb_hi);
-    } else {
-      if (nn > nb + 4.0) nn = nb + 4.0;
-      if (nn < nb - 4.0) nn = nb - 4.0;
+    if (!conv) {
+      if (isfinite(st.nb_lo) && isfinite(st.nb_hi)) {
+        if (!(nn >= st.nb_lo && nn <= st.nb_hi)) nn = 0.5 * (st.nb_lo + st.nb_hi);
+      } else {
+        if (nn > nb + 4.0) nn = nb + 4.0;
+        if (nn < nb - 4.0) nn = nb - 4.0;
+      }
     }
-    const double tol = (sizeof(T) == 8) ? 1e-13 : 2e-6;
     st.npass += 1;
-    if (fabs(nn - nb) <= tol || st.npass >= 40) st.nconv = 1;
-    if (nn < -32.2) { nn = -32.2; }               // alpha floor 1e-14
+    if (conv || st.npass >= 40) st.nconv = 1;
+    if (nn < -32.2) nn = -32.2;                   // alpha floor 1e-14
     st.nb = nn;
     double a = exp(nn);
     if (pd.bc == BC_RECT && a < pd.alpha) a = pd.alpha;   // rectangular hybrid floor

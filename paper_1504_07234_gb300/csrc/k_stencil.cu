@@ -35,6 +35,7 @@ __device__ void finalize_residual(const Prob& pd, State& st, double sumsq) {
       st.ns_active = 1;
       st.nconv = 0;
       st.npass = 0;
+      st.nphase = 0;
       st.nb_lo = -INFINITY;
       st.nb_hi = INFINITY;
     } else {

@@ -22,7 +22,7 @@ using namespace mlba;
 
 namespace {
 
-constexpr int NEWTON_PASSES = 10;   // graph nodes per iteration for the alpha_n solve
+constexpr int NEWTON_PASSES = 8;    // graph nodes per iteration for the alpha_n solve (1 bracketing + Newton)
 constexpr size_t ALIGN = 256;
 
 #define CK(call)                                   \
@@ -429,7 +429,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
         (size_t)pd.ntaps * 4, (size_t)pd.ntaps * 4, (size_t)pd.ntaps * ts,   // taps
         (size_t)pd.p * ts, (size_t)pd.p * ts,  // hy, hx
-        3 * (size_t)std::max({pd.nblk_blur, pd.nblk_vec, pd.nblk_spec, 1}) * 8,  // partial
+        std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, 33 * (size_t)pd.nblk_spec, (size_t)1}) * 8,  // partial
         (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 4};
     offs[i].resize(sz.size());
     for (size_t k = 0; k < sz.size(); ++k) { offs[i][k] = total; total += al(sz[k]); }

@@ -74,6 +74,7 @@ struct State {
   int ns_active;     // 4-NS: alpha_n being solved this iteration
   int nconv;         // 4-NS Newton converged
   int npass;
+  int nphase;        // 4-NS: 0 = bracketing pass pending, 1 = Newton
   int pdone, psteps; // PCG
   int beta_last;
   double resnorm, alpha_n, qn;

@@ -169,3 +169,29 @@ def test_convergence_condition_workload_1():
         lam = np.linalg.norm(w) / np.linalg.norm(v)
         v = w / np.linalg.norm(w)
     assert lam < 1.0
+
+
+def test_convergence_condition_batch_workload():
+    """Eq. condconvalg1 at the alpha of the batched workload for every
+    rectangular problem's PSF (checked at n = 48: the norm depends on the PSF
+    and the transform, hardly on n)."""
+    probs = I.batch_problems()
+    rng = np.random.default_rng(1)
+    seen = set()
+    for p in probs:
+        if p.bc != "rect":
+            continue
+        key = (p.psf.shape[0], round(float(p.psf.sum() * 1e6 + p.psf[0, 0] * 1e9), 3))
+        if key in seen:
+            continue
+        seen.add(key)
+        tr = O.choose_transform(p.psf, "bccb", "auto")
+        pre = O.SpectralPrecond(p.psf, 48, tr)
+        m = 48 + p.psf.shape[0] - 1
+        v = rng.standard_normal((m, m))
+        lam = 0.0
+        for _ in range(40):
+            w = O.blur_adjoint(pre.inv(O.blur(v, p.psf, "rect"), p.alpha), p.psf, "rect")
+            lam = np.linalg.norm(w) / np.linalg.norm(v)
+            v = w / np.linalg.norm(w)
+        assert lam < 0.95, (p.name, lam)
