@@ -73,7 +73,7 @@ enum mlba_precond {            /* Sections 3-5 */
 enum mlba_dtype { MLBA_F32 = 0, MLBA_F64 = 1, MLBA_BF16 = 2 };
 
 enum mlba_transform {          /* diagonalising transform of C (Section 4.1) */
-  MLBA_TR_AUTO = 0,            /* DCT for a quadrantally symmetric PSF, else DFT */
+  MLBA_TR_AUTO = 0,            /* DFT for periodic BC (C = A); else DCT for a quadrantally symmetric PSF, else DFT */
   MLBA_TR_DFT = 1,             /* C = periodic-BC (Strang) matrix */
   MLBA_TR_DCT = 2              /* C = reflective-BC matrix; PSF must be quadrantally symmetric */
 };

@@ -20,6 +20,7 @@ import math
 from dataclasses import dataclass, field
 
 import numpy as np
+from scipy.ndimage import convolve as nd_convolve
 from scipy.signal import fftconvolve
 
 __all__ = [
@@ -123,6 +124,21 @@ def observe(f_true: np.ndarray, psf: np.ndarray, nu: float, seed: int):
     return blurred + eta, float(np.linalg.norm(eta))
 
 
+def observe_periodic(f_true: np.ndarray, psf: np.ndarray, nu: float, seed: int):
+    """Observed n x n image of an n x n truth under periodic boundary
+    conditions (the truth repeats outside the field of view), plus noise as
+    in :func:`observe`.  Uses SciPy's wrap-mode convolution."""
+    blurred = nd_convolve(f_true, psf, mode="wrap")
+    rng = np.random.default_rng([seed, 0x5eed])
+    e = rng.standard_normal(blurred.shape)
+    eta = nu * np.linalg.norm(blurred) * e / np.linalg.norm(e)
+    return blurred + eta, float(np.linalg.norm(eta))
+
+
+def quadrant_symmetric(psf: np.ndarray) -> bool:
+    return bool(np.array_equal(psf, psf[::-1, :]) and np.array_equal(psf, psf[:, ::-1]))
+
+
 # ---------------------------------------------------------------------------
 # problem descriptions of the measured workloads
 # ---------------------------------------------------------------------------
@@ -169,7 +185,7 @@ class Problem:
 
     def truth_in_fov(self) -> np.ndarray:
         """The part of the truth a restoration is compared with."""
-        if self.bc == "rect":
+        if self.f_true.shape[0] == self.nf:
             return self.f_true
         c = (self.p - 1) // 2
         return self.f_true[c:c + self.n, c:c + self.n]
@@ -230,10 +246,15 @@ def batch_problems(count: int = 64, seed: int = 4, sizes=BATCH_SIZES,
     Sizes uniform in ``sizes``; PSF family uniform over Gaussian sigma~U[1,4],
     disk r~U{2..8}, motion length~U{5,7,..,21} at angle~U[0,pi); BC uniform
     over periodic / reflective / rectangular; noise nu~U[0.005, 0.03].  BC
-    problems run the nonstationary Algorithm 4-NS, rectangular ones the
-    BCCB-preconditioned Algorithm 1 with alpha = 0.5 (the smallest of
-    0.3 / 0.5 at which Eq. condconvalg1 holds for every PSF of the family);
-    each stops on its own discrepancy rule.
+    problems run the nonstationary Algorithm 4-NS where C = A (periodic BC
+    with the DFT; reflective BC with a quadrantally symmetric PSF and the
+    DCT), reflective problems with a nonsymmetric PSF run Algorithm 3
+    (symmetrised PSF, alpha = 0.3), rectangular ones the BCCB-preconditioned
+    Algorithm 1 with alpha = 0.5 (the smallest of 0.3 / 0.5 at which
+    Eq. condconvalg1 holds for every PSF of the family).  Periodic problems
+    observe a periodic scene (the BC is the right model); the others observe
+    the field of view of a larger scene (Example 3's protocol).  Each problem
+    stops on its own discrepancy rule.
     """
     rng = np.random.default_rng([seed, 0xba7c])
     out = []
@@ -249,8 +270,16 @@ def batch_problems(count: int = 64, seed: int = 4, sizes=BATCH_SIZES,
                              float(rng.uniform(0.0, math.pi)))
         bc = ("periodic", "reflective", "rect")[int(rng.integers(0, 3))]
         nu = float(rng.uniform(0.005, 0.03))
-        pc = "bccb" if bc == "rect" else "tikh_ns"
-        out.append(_make(n, psf, nu, 1000 + k, bc=bc, precond=pc,
-                         mu=10.0 / 255.0, alpha=0.5, levels=2,
-                         max_iter=max_iter, stop=True, name=f"C4-{k}"))
+        kw = dict(mu=10.0 / 255.0, levels=2, max_iter=max_iter, stop=True, name=f"C4-{k}")
+        if bc == "rect":
+            out.append(_make(n, psf, nu, 1000 + k, bc=bc, precond="bccb", alpha=0.5, **kw))
+        elif bc == "periodic":
+            f = true_image(n, 1000 + k)
+            g, delta = observe_periodic(f, psf, nu, 1000 + k)
+            out.append(Problem(g=g, psf=psf, delta=delta, f_true=f, bc=bc, precond="tikh_ns",
+                               alpha=0.05, **kw))
+        elif quadrant_symmetric(psf):
+            out.append(_make(n, psf, nu, 1000 + k, bc=bc, precond="tikh_ns", alpha=0.05, **kw))
+        else:
+            out.append(_make(n, psf, nu, 1000 + k, bc=bc, precond="sym", alpha=0.3, **kw))
     return out

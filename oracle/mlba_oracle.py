@@ -393,14 +393,20 @@ def ns_alpha(rhat2: np.ndarray, sigma: np.ndarray, qn: float) -> float:
 # Section 3 / 4 / 5: the iteration
 # ---------------------------------------------------------------------------
 
-def choose_transform(h: np.ndarray, precond: str, transform: str) -> str:
-    """DCT for a quadrantally symmetric PSF (Section 4.1) or always for the
-    symmetrised Algorithm 3; DFT otherwise; an explicit choice wins for
-    Algorithms 1, 2 and 4."""
+def choose_transform(h: np.ndarray, precond: str, transform: str, bc: str = "rect") -> str:
+    """Diagonalising transform of C (Section 4.1).
+
+    Algorithm 3 always uses the DCT of the symmetrised PSF.  An explicit
+    choice wins otherwise.  'auto': with periodic BCs the periodic C equals A
+    and the DFT is used; otherwise the DCT when the PSF is quadrantally
+    symmetric (the reflective C approximates A better, Section 4.1) and the
+    DFT when it is not."""
     if precond == "sym":
         return "dct"
     if transform in ("dft", "dct"):
         return transform
+    if bc == "periodic":
+        return "dft"
     return "dct" if quadrantally_symmetric(h) else "dft"
 
 
@@ -438,7 +444,7 @@ def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
     if precond in ("tikh", "tikh_ns") and bc == "rect" and not (precond == "tikh_ns" and rect_ns_hybrid):
         raise ValueError("Algorithm 4 needs a square A (Section 5)")
     ns = precond == "tikh_ns"
-    tr = choose_transform(h, precond, transform)
+    tr = choose_transform(h, precond, transform, bc)
     pre = None
     if precond in ("bccb", "krylov", "tikh", "tikh_ns"):
         pre = SpectralPrecond(h, n, tr)

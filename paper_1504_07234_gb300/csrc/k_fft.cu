@@ -503,10 +503,15 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   float cF[NS_CAND];
 #pragma unroll
   for (int j = 0; j < NS_CAND; ++j) cF[j] = 0.f;
+  __shared__ float s_ca[NS_CAND];
   float ca[NS_CAND];
   if (cand) {
+    // candidate alphas once per block (FP64 exp is scarce on this part)
+    if (threadIdx.x < NS_CAND)
+      s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
+    __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NS_CAND; ++j) ca[j] = (float)exp(b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
+    for (int j = 0; j < NS_CAND; ++j) ca[j] = s_ca[j];
   }
   for (size_t i = beg + threadIdx.x; i < end; i += SPEC_THREADS) {
     T pw;

@@ -283,7 +283,10 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
     const int tr = in.transform;
     const bool sym = quad_symmetric(h.psf, p);
     if (tr == MLBA_TR_DCT && !sym) return MLBA_E_INVAL;
-    pd.transform = (tr == MLBA_TR_DFT) ? TR_DFT : (tr == MLBA_TR_DCT ? TR_DCT : (sym ? TR_DCT : TR_DFT));
+    // AUTO: periodic A is its own BCCB matrix (DFT); otherwise the reflective
+    // (DCT) matrix for a quadrantally symmetric PSF, the periodic one if not
+    const int autotr = (in.bc == MLBA_BC_PERIODIC) ? TR_DFT : (sym ? TR_DCT : TR_DFT);
+    pd.transform = (tr == MLBA_TR_DFT) ? TR_DFT : (tr == MLBA_TR_DCT ? TR_DCT : autotr);
     h.psf_pre = h.psf;
   }
   if (pd.transform != TR_NONE) {
