@@ -211,6 +211,35 @@ int mlba_batch_profile(mlba_batch* b, int stage, int reps, float* ms_per_rep);
 int mlba_batch_graph_kernels(mlba_batch* b, int* n_kernels);
 void mlba_batch_destroy(mlba_batch* b);
 
+/* ---- entry point that allocates no device memory ------------------------
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc (a host framework that owns all device memory, a fixed
+ * memory budget, or a loop where the implicit synchronisation of
+ * cudaMalloc/cudaFree is not acceptable).
+ *
+ * r = g - A f and *norm2 = ||r||^2 (FP64 accumulation, fixed summation
+ * order), the residual stencil of one iteration, in FP32.  All pointers are
+ * device memory on the current device: f (N_f x N_f, N_f = n + p - 1 for
+ * MLBA_RECT else n), g and r (n x n), psf (p x p row-major floats, centred),
+ * norm2 (one double).  bc is an enum mlba_bc value; work is queued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream).
+ *
+ * Scratch: a fixed array in device memory of the library, 8 bytes per
+ * 32 x 32 tile for n up to MLBA_NOALLOC_MAX_N (about 128 KiB), which every
+ * GPU that loads the library holds until the process exits.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call shares the
+ * array: calls whose kernels overlap on the GPU (other streams, concurrent
+ * graph replays) race and must be serialised by the caller.  Nothing is
+ * allocated or freed.
+ * Errors: MLBA_E_INVAL (null pointer, even p, n < p, bad bc),
+ * MLBA_E_UNSUPPORTED (n > MLBA_NOALLOC_MAX_N or p > MLBA_NOALLOC_MAX_P),
+ * MLBA_E_CUDA (launch or symbol lookup failed). */
+#define MLBA_NOALLOC_MAX_N 4096
+#define MLBA_NOALLOC_MAX_P 41
+int mlba_residual_noalloc(const float* f, const float* g, const float* psf, int p, int n, int bc,
+                          float* r, double* norm2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

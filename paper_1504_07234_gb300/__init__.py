@@ -91,6 +91,7 @@ SIGNATURES = {
     "mlba_batch_profile": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_float)]),
     "mlba_batch_graph_kernels": (_I, [_P, ctypes.POINTER(_I)]),
     "mlba_batch_destroy": (None, [_P]),
+    "mlba_residual_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
 }
 
 _lib = None

@@ -19,7 +19,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libmlba.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["k_stencil.cu", "k_fft.cu", "k_frame.cu", "mlba_api.cu"]
+SOURCES = ["k_stencil.cu", "k_fft.cu", "k_frame.cu", "mlba_api.cu", "mlba_noalloc.cu"]
 HEADERS = ["mlba_internal.cuh", "mlba_launch.h"]
 
 
