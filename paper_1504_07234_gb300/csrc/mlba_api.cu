@@ -199,7 +199,7 @@ void enqueue_step(mlba_batch* B, cudaStream_t s) {
   launch_stencil<T>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
   // a1: z += W u, x = S_mu(z), f = W^T x
   launch_frame<T, TZ>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0,
-                      B->smem_frame, s);
+                      B->smem_frame, B->levels, s);
 }
 
 void enqueue_dispatch(mlba_batch* B, cudaStream_t s) {
@@ -753,7 +753,7 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
         launch_rows_inv<double>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
       }
       if (stage == 3) launch_stencil<double>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
-      if (stage == 4) launch_frame<double, double>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, s);
+      if (stage == 4) launch_frame<double, double>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, s);
     } else {
       if (stage == 1) launch_stencil<float>(ST_FWD_RESID, P, S, B->blur.dev, B->blur.count, SL_F, SL_R, SL_G, 0, B->smem_stencil, s);
       if (stage == 2) {
@@ -766,9 +766,9 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
       if (stage == 3) launch_stencil<float>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
       if (stage == 4) {
         if (B->z_store == MLBA_BF16)
-          launch_frame<float, __nv_bfloat16>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, s);
+          launch_frame<float, __nv_bfloat16>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, s);
         else
-          launch_frame<float, float>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, s);
+          launch_frame<float, float>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, s);
       }
     }
   }
@@ -962,11 +962,11 @@ int mlba_op_frame(mlba_ctx* c, const void* z_in, const void* u, void* z_out, voi
   if (rc != MLBA_OK) return rc;
   if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
   if (B->dtype == MLBA_F64)
-    launch_frame<double, double>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->stream);
+    launch_frame<double, double>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->levels, B->stream);
   else if (B->z_store == MLBA_BF16)
-    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->stream);
+    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->levels, B->stream);
   else
-    launch_frame<float, float>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->stream);
+    launch_frame<float, float>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->levels, B->stream);
   CK(cudaGetLastError());
   rc = copy_out(B, f, pd.buf[SL_AUX1], fbytes, on_device);
   if (rc != MLBA_OK) return rc;

@@ -64,7 +64,7 @@ void launch_spectrum_setup(const Prob* probs, int pi, int transform, int n, int 
                            void* lam, int is_double, cudaStream_t s);
 template <typename T, typename TZ>
 void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, int u_slot,
-                  int f_slot, const void* zin, void* zout, double op_mu, size_t smem,
+                  int f_slot, const void* zin, void* zout, double op_mu, size_t smem, int levels,
                   cudaStream_t s);
 template <typename T, typename TZ>
 size_t frame_smem_bytes(int levels);
