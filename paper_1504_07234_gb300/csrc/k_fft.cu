@@ -233,14 +233,26 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
   const int pair0 = item.y * G;
   const bool dct = (pd.transform == TR_DCT);
   const T* src = static_cast<const T*>(pd.buf[src_slot]);
-  for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
-    const int g = e / N, x = e - g * N;
-    const int ra = 2 * (pair0 + g), rb = ra + 1;
-    const int xs = dct ? dct_src(x, N) : x;
-    T2 v;
-    v.x = (ra < N) ? src[(size_t)ra * N + xs] : T(0);
-    v.y = (rb < N) ? src[(size_t)rb * N + xs] : T(0);
-    sm[e] = v;
+  {
+    // all loads of this thread first (up to MAXV in flight), then the stores
+    constexpr int MAXV = (sizeof(T) == 8) ? TR_MAXV_F64 : TR_MAXV;
+    T2 tmp[MAXV];
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int e = threadIdx.x + q * TR_THREADS;
+      if (e < G * N) {
+        const int g = e / N, x = e - g * N;
+        const int ra = 2 * (pair0 + g), rb = ra + 1;
+        const int xs = dct ? dct_src(x, N) : x;
+        tmp[q].x = (ra < N) ? src[(size_t)ra * N + xs] : T(0);
+        tmp[q].y = (rb < N) ? src[(size_t)rb * N + xs] : T(0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int e = threadIdx.x + q * TR_THREADS;
+      if (e < G * N) sm[e] = tmp[q];
+    }
   }
   __syncthreads();
   fft_smem<T2, false>(sm, G, pd);
@@ -271,38 +283,23 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
   }
 }
 
-// spectral weight at (k1, col); alpha and kind as given
+// spectral weight at (k1, col); alpha and kind as given.  |lambda|^2 + alpha
+// is formed in T: alpha > 0 keeps it away from zero (no cancellation), so
+// FP32 holds it to 6e-8 relative; 1/n^2 of the unnormalised pair is folded in.
 template <typename T, typename T2>
-__device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, double alpha, int kind) {
-  const double d = pd.sigma[idx] + alpha;                 // FP64 denominator
-  const double scale = 1.0 / ((double)pd.n * (double)pd.n);
+__device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
+  const T inv = scale / (static_cast<const T*>(pd.w)[idx] + alpha);
   T2 w;
-  if (sizeof(T) == 8) {
-    const double inv = scale / d;
-    if (kind == W_TIKH) {
-      const T2 l = static_cast<const T2*>(pd.lam)[idx];
-      w.x = T(l.x * inv); w.y = T(-l.y * inv);
-    } else { w.x = T(inv); w.y = T(0); }
-  } else {
-    const T inv = T(1) / T(d * ((double)pd.n * (double)pd.n));
-    if (kind == W_TIKH) {
-      const T2 l = static_cast<const T2*>(pd.lam)[idx];
-      w.x = l.x * inv; w.y = -l.y * inv;
-    } else { w.x = inv; w.y = T(0); }
-  }
+  if (kind == W_TIKH) {
+    const T2 l = static_cast<const T2*>(pd.lam)[idx];
+    w.x = l.x * inv; w.y = -l.y * inv;
+  } else { w.x = inv; w.y = T(0); }
   return w;
 }
 template <typename T>
-__device__ __forceinline__ T weight_dct(const Prob& pd, size_t idx, double alpha, int kind) {
-  const double d = pd.sigma[idx] + alpha;
-  const double nn = (double)pd.n * (double)pd.n;
-  if (sizeof(T) == 8) {
-    const double inv = 1.0 / (d * nn);
-    return kind == W_TIKH ? T(static_cast<const T*>(pd.lam)[idx] * inv) : T(inv);
-  } else {
-    const T inv = T(1) / T(d * nn);
-    return kind == W_TIKH ? static_cast<const T*>(pd.lam)[idx] * inv : inv;
-  }
+__device__ __forceinline__ T weight_dct(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
+  const T inv = scale / (static_cast<const T*>(pd.w)[idx] + alpha);
+  return kind == W_TIKH ? static_cast<const T*>(pd.lam)[idx] * inv : inv;
 }
 
 // Pass 2: columns.  DFT: G complex columns of S (n x half).  DCT: G pairs of
@@ -327,17 +324,30 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   if (mode == COL_NS_INV) alpha = st.alpha_n;
   if (mode == COL_OP) { alpha = op_alpha; kind = op_kind; }
   if (pd.precond == P_KRYLOV) kind = W_INV;
+  const T Ta = T(alpha);
+  const T Tsc = T(1.0 / ((double)pd.n * (double)pd.n));
 
   if (!dct) {
     const int H = pd.half;
     const int k0 = item.y * G;
     T2* S = static_cast<T2*>(pd.buf[SL_S]);
-    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
-      const int y = e / G, g = e - y * G;
-      const int col = k0 + g;
-      T2 v; v.x = T(0); v.y = T(0);
-      if (col < H) v = S[(size_t)y * H + col];
-      sm[g * N + y] = v;
+    {
+      constexpr int MAXV = (sizeof(T) == 8) ? TR_MAXV_F64 : TR_MAXV;
+      T2 tmp[MAXV];
+#pragma unroll
+      for (int q = 0; q < MAXV; ++q) {
+        const int e = threadIdx.x + q * TR_THREADS;
+        tmp[q].x = T(0); tmp[q].y = T(0);
+        if (e < G * N) {
+          const int y = e / G, g = e - y * G;
+          if (k0 + g < H) tmp[q] = S[(size_t)y * H + k0 + g];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < MAXV; ++q) {
+        const int e = threadIdx.x + q * TR_THREADS;
+        if (e < G * N) { const int y = e / G, g = e - y * G; sm[g * N + y] = tmp[q]; }
+      }
     }
     __syncthreads();
     if (mode != COL_NS_INV) fft_smem<T2, false>(sm, G, pd);
@@ -352,7 +362,7 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
     for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
       const int g = e / N, k1 = e - g * N;
       const int col = k0 + g;
-      if (col < H) sm[e] = cmul(sm[e], weight_dft<T, T2>(pd, (size_t)k1 * H + col, alpha, kind));
+      if (col < H) sm[e] = cmul(sm[e], weight_dft<T, T2>(pd, (size_t)k1 * H + col, Ta, Tsc, kind));
     }
     __syncthreads();
     fft_smem<T2, true>(sm, G, pd);
@@ -365,13 +375,27 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
     const int k0 = item.y * 2 * G;          // first real column
     T* S = static_cast<T*>(pd.buf[SL_S]);
     T* smr = reinterpret_cast<T*>(sm);
-    for (int e = threadIdx.x; e < 2 * G * N; e += TR_THREADS) {
-      const int y = e / (2 * G), cc = e - y * (2 * G);
-      const int col = k0 + cc;
-      const T v = (col < N) ? S[(size_t)y * N + col] : T(0);
-      const int g = cc >> 1;
-      const int pos = (mode == COL_NS_INV) ? y : dct_pos(y, N);
-      smr[2 * (g * N + pos) + (cc & 1)] = v;
+    {
+      constexpr int MAXV = 2 * ((sizeof(T) == 8) ? TR_MAXV_F64 : TR_MAXV);
+      T tmp[MAXV];
+#pragma unroll
+      for (int q = 0; q < MAXV; ++q) {
+        const int e = threadIdx.x + q * TR_THREADS;
+        tmp[q] = T(0);
+        if (e < 2 * G * N) {
+          const int y = e / (2 * G), cc = e - y * (2 * G);
+          if (k0 + cc < N) tmp[q] = S[(size_t)y * N + k0 + cc];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < MAXV; ++q) {
+        const int e = threadIdx.x + q * TR_THREADS;
+        if (e < 2 * G * N) {
+          const int y = e / (2 * G), cc = e - y * (2 * G);
+          const int pos = (mode == COL_NS_INV) ? y : dct_pos(y, N);
+          smr[2 * ((cc >> 1) * N + pos) + (cc & 1)] = tmp[q];
+        }
+      }
     }
     __syncthreads();
     const T2* dtw = static_cast<const T2*>(pd.dtw);
@@ -391,8 +415,8 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
       const int g = e / N, k1 = e - g * N;
       const int ca = k0 + 2 * g, cb = ca + 1;
       T2 v = sm[e];
-      v.x *= (ca < N) ? weight_dct<T>(pd, (size_t)k1 * N + ca, alpha, kind) : T(0);
-      v.y *= (cb < N) ? weight_dct<T>(pd, (size_t)k1 * N + cb, alpha, kind) : T(0);
+      v.x *= (ca < N) ? weight_dct<T>(pd, (size_t)k1 * N + ca, Ta, Tsc, kind) : T(0);
+      v.y *= (cb < N) ? weight_dct<T>(pd, (size_t)k1 * N + cb, Ta, Tsc, kind) : T(0);
       sm[e] = v;
     }
     __syncthreads();
@@ -436,21 +460,31 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
     const int H = pd.half;
     const T2* S = static_cast<const T2*>(pd.buf[SL_S]);
     const bool even = (N & 1) == 0;
-    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
-      const int g = e / N, k = e - g * N;
-      const int ra = 2 * (pair0 + g), rb = ra + 1;
-      T2 xa, xb;
-      xa.x = xa.y = xb.x = xb.y = T(0);
-      if (k < H) {
-        if (ra < N) xa = S[(size_t)ra * H + k];
-        if (rb < N) xb = S[(size_t)rb * H + k];
-      } else {
-        if (ra < N) xa = cconj(S[(size_t)ra * H + (N - k)]);
-        if (rb < N) xb = cconj(S[(size_t)rb * H + (N - k)]);
+    constexpr int MAXV = (sizeof(T) == 8) ? TR_MAXV_F64 : TR_MAXV;
+    T2 ta[MAXV], tb[MAXV];
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int e = threadIdx.x + q * TR_THREADS;
+      ta[q].x = ta[q].y = tb[q].x = tb[q].y = T(0);
+      if (e < G * N) {
+        const int g = e / N, k = e - g * N;
+        const int ra = 2 * (pair0 + g), rb = ra + 1;
+        const int kk = (k < H) ? k : N - k;
+        if (ra < N) ta[q] = S[(size_t)ra * H + kk];
+        if (rb < N) tb[q] = S[(size_t)rb * H + kk];
       }
-      if (k == 0 || (even && k == N / 2)) { xa.y = T(0); xb.y = T(0); }
-      T2 z; z.x = xa.x - xb.y; z.y = xa.y + xb.x;   // Xa + i Xb
-      sm[e] = z;
+    }
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int e = threadIdx.x + q * TR_THREADS;
+      if (e < G * N) {
+        const int k = e % N;
+        T2 xa = ta[q], xb = tb[q];
+        if (k >= H) { xa = cconj(xa); xb = cconj(xb); }
+        if (k == 0 || (even && k == N / 2)) { xa.y = T(0); xb.y = T(0); }
+        T2 z; z.x = xa.x - xb.y; z.y = xa.y + xb.x;   // Xa + i Xb
+        sm[e] = z;
+      }
     }
     __syncthreads();
   }
@@ -476,105 +510,135 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
 // Newton steps inside the bracket until |step| <= tol.  Each block sums its
 // share in T precision (FP64 accumulation across blocks); the last block
 // updates the scalar state.
-constexpr int NS_CAND = 32;
-constexpr double NS_CAND_STEP = 0.8;
+constexpr int NS_CAND = 16;
+constexpr double NS_CAND_STEP = 1.0;
 
+// element e (< SPEC_THREADS * SPEC_PER_THREAD) of block `blk`: weighted power
+// and |lambda|^2 in T precision; false past the end of the spectrum
 template <typename T>
-__global__ void __launch_bounds__(SPEC_THREADS)
-k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items) {
+__device__ __forceinline__ bool spec_elem(const Prob& pd, int blk, int e, T& pw, T& sg) {
   using T2 = typename Vec2<T>::type;
-  __shared__ double red[32];
-  const int2 item = items[blockIdx.x];
-  const Prob& pd = probs[item.x];
-  State& st = states[item.x];
-  if (st.stopped || !pd.ns || !st.ns_active || st.nconv) return;
   const int N = pd.n;
   const bool dct = (pd.transform == TR_DCT);
   const int W = dct ? N : pd.half;
-  const size_t tot = (size_t)N * W;
-  const size_t chunk = (size_t)SPEC_THREADS * SPEC_PER_THREAD;
-  const size_t beg = (size_t)item.y * chunk;
-  const size_t end = beg + chunk < tot ? beg + chunk : tot;
-  const bool cand = (st.nphase == 0);
+  // whole rows per block, never more elements than the block's threads cover
+  const int rows_per = max(1, (SPEC_THREADS * SPEC_PER_THREAD) / W);
+  const int k1 = blk * rows_per + e / W;
+  const int k2 = e - (e / W) * W;
+  if (k1 >= N || e >= rows_per * W) return false;
+  const size_t idx = (size_t)k1 * W + k2;
+  if (dct) {
+    // unnormalised DCT-II: |orthonormal coefficient|^2 = v^2 s_k1^2 s_k2^2
+    // with s_0^2 = 1/N and s_k^2 = 2/N; the common 1/N^2 cancels
+    const T v = static_cast<const T*>(pd.buf[SL_S])[idx];
+    pw = T((k1 == 0 ? 1 : 2) * (k2 == 0 ? 1 : 2)) * v * v;
+  } else {
+    const T2 v = static_cast<const T2*>(pd.buf[SL_S])[idx];
+    const T m = (k2 == 0 || ((N & 1) == 0 && k2 == N / 2)) ? T(1) : T(2);
+    pw = m * (v.x * v.x + v.y * v.y);
+  }
+  sg = static_cast<const T*>(pd.w)[idx];
+  return true;
+}
+
+__device__ __forceinline__ void ns_set_alpha(const Prob& pd, State& st, double nb) {
+  if (nb < -32.2) nb = -32.2;                          // alpha floor 1e-14
+  st.nb = nb;
+  double a = exp(nb);
+  if (pd.bc == BC_RECT && a < pd.alpha) a = pd.alpha;  // rectangular hybrid floor
+  st.alpha_n = a;
+  const int it = st.iter - 1;
+  if (it >= 0 && it < pd.max_iter + 2) pd.hist_alpha[it] = a;
+}
+
+// Bracketing pass (nphase 0): h at NS_CAND candidates around the previous root.
+template <typename T>
+__global__ void __launch_bounds__(SPEC_THREADS)
+k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items) {
+  __shared__ double red[(NS_CAND + 1) * (SPEC_THREADS / 32)];
+  __shared__ float s_ca[NS_CAND];
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  State& st = states[item.x];
+  if (st.stopped || !pd.ns || !st.ns_active || st.nconv || st.nphase != 0) return;
   const double b0 = st.nb;
-  const double alpha = exp(b0);
-  // per-thread partial sums
-  T sP = T(0), sF = T(0), sG = T(0);
+  if (threadIdx.x < NS_CAND)
+    s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
+  T pw[SPEC_PER_THREAD], sg[SPEC_PER_THREAD];
+  bool ok[SPEC_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < SPEC_PER_THREAD; ++q)
+    ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + q * SPEC_THREADS, pw[q], sg[q]);
+  __syncthreads();
   float cF[NS_CAND];
 #pragma unroll
   for (int j = 0; j < NS_CAND; ++j) cF[j] = 0.f;
-  __shared__ float s_ca[NS_CAND];
-  float ca[NS_CAND];
-  if (cand) {
-    // candidate alphas once per block (FP64 exp is scarce on this part)
-    if (threadIdx.x < NS_CAND)
-      s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
-    __syncthreads();
+  T sP = T(0);
 #pragma unroll
-    for (int j = 0; j < NS_CAND; ++j) ca[j] = s_ca[j];
-  }
-  for (size_t i = beg + threadIdx.x; i < end; i += SPEC_THREADS) {
-    T pw;
-    if (dct) {
-      // unnormalised DCT-II: |orthonormal coefficient|^2 = v^2 s_k1^2 s_k2^2
-      // with s_0^2 = 1/N and s_k^2 = 2/N; the common 1/N^2 cancels
-      const T v = static_cast<const T*>(pd.buf[SL_S])[i];
-      const int k1 = (int)(i / W), k2 = (int)(i - (size_t)k1 * W);
-      const T m = T((k1 == 0 ? 1 : 2) * (k2 == 0 ? 1 : 2));
-      pw = m * v * v;
-    } else {
-      const T2 v = static_cast<const T2*>(pd.buf[SL_S])[i];
-      const int k2 = (int)(i % W);
-      const T m = (k2 == 0 || ((N & 1) == 0 && k2 == N / 2)) ? T(1) : T(2);
-      pw = m * (v.x * v.x + v.y * v.y);
-    }
-    const double sg = pd.sigma[i];
-    sP += pw;
-    if (cand) {
-      const float pf = (float)pw, sf = (float)sg;
+  for (int q = 0; q < SPEC_PER_THREAD; ++q) {
+    if (!ok[q]) continue;
+    sP += pw[q];
+    const float pf = (float)pw[q], sf = (float)sg[q];
 #pragma unroll
-      for (int j = 0; j < NS_CAND; ++j) {
-        const float x = __fdividef(ca[j], sf + ca[j]);
-        cF[j] += pf * x * x;
-      }
-    } else {
-      const double d = sg + alpha;                 // FP64 denominator
-      const T x = (sizeof(T) == 8) ? T(alpha / d) : T(alpha) / T(d);
-      const T x2 = x * x;
-      sF += pw * x2;
-      sG += T(2) * pw * x2 * (T(1) - x);
+    for (int j = 0; j < NS_CAND; ++j) {
+      const float x = __fdividef(s_ca[j], sf + s_ca[j]);
+      cF[j] += pf * x * x;
     }
   }
-  if (cand) {
-    double v[NS_CAND + 1], t[NS_CAND + 1];
-    v[0] = block_sum<SPEC_THREADS>((double)sP, red);
-#pragma unroll 1
-    for (int j = 0; j < NS_CAND; ++j) v[j + 1] = block_sum<SPEC_THREADS>((double)cF[j], red);
-    if (last_block_reduce<SPEC_THREADS, NS_CAND + 1>(pd, st, item.y, pd.nblk_spec, v, t, red) &&
-        threadIdx.x == 0) {
-      const double P = t[0], target = st.qn * st.qn;
-      int j = 0;
-      while (j < NS_CAND && !(P > 0.0 && t[j + 1] / P - target >= 0.0)) ++j;
-      const double bj = b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP;
-      double nb;
-      if (j == 0) { st.nb_lo = -INFINITY; st.nb_hi = bj; nb = bj - NS_CAND_STEP; }
-      else if (j == NS_CAND) { st.nb_lo = bj - NS_CAND_STEP; st.nb_hi = INFINITY; nb = bj; }
-      else {
-        const double hl = t[j] / P - target, hh = t[j + 1] / P - target;
-        st.nb_lo = bj - NS_CAND_STEP; st.nb_hi = bj;
-        nb = st.nb_lo + (hh > hl ? (-hl) / (hh - hl) : 0.5) * NS_CAND_STEP;
-      }
-      if (nb < -32.2) nb = -32.2;
-      st.nb = nb;
-      st.nphase = 1;
-      st.npass += 1;
-      double a = exp(nb);
-      if (pd.bc == BC_RECT && a < pd.alpha) a = pd.alpha;   // rectangular hybrid floor
-      st.alpha_n = a;
-      const int it = st.iter - 1;
-      if (it >= 0 && it < pd.max_iter + 2) pd.hist_alpha[it] = a;
+  double v0[NS_CAND + 1], v[NS_CAND + 1], t[NS_CAND + 1];
+  v0[0] = (double)sP;
+#pragma unroll
+  for (int j = 0; j < NS_CAND; ++j) v0[j + 1] = (double)cF[j];
+  block_sum_k<SPEC_THREADS, NS_CAND + 1>(v0, v, red);
+  if (last_block_reduce<SPEC_THREADS, NS_CAND + 1>(pd, st, item.y, pd.nblk_spec, v, t, red) &&
+      threadIdx.x == 0) {
+    const double P = t[0], target = st.qn * st.qn;
+    int j = 0;
+    while (j < NS_CAND && !(P > 0.0 && t[j + 1] / P - target >= 0.0)) ++j;
+    const double bj = b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP;
+    double nb;
+    if (j == 0) { st.nb_lo = -INFINITY; st.nb_hi = bj; nb = bj - NS_CAND_STEP; }
+    else if (j == NS_CAND) { st.nb_lo = bj - NS_CAND_STEP; st.nb_hi = INFINITY; nb = bj; }
+    else {
+      const double hl = t[j] / P - target, hh = t[j + 1] / P - target;
+      st.nb_lo = bj - NS_CAND_STEP; st.nb_hi = bj;
+      nb = st.nb_lo + (hh > hl ? (-hl) / (hh - hl) : 0.5) * NS_CAND_STEP;
     }
-    return;
+    st.nphase = 1;
+    st.npass += 1;
+    ns_set_alpha(pd, st, nb);
+  }
+}
+
+// Newton pass (nphase 1): h and dh/dlog(alpha) at the current estimate, then a
+// safeguarded step inside the bracket.
+template <typename T>
+__global__ void __launch_bounds__(SPEC_THREADS)
+k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items) {
+  __shared__ double red[32];
+  __shared__ T s_alpha;
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  State& st = states[item.x];
+  if (st.stopped || !pd.ns || !st.ns_active || st.nconv || st.nphase != 1) return;
+  const double b0 = st.nb;
+  if (threadIdx.x == 0) s_alpha = T(exp(b0));
+  T pw[SPEC_PER_THREAD], sg[SPEC_PER_THREAD];
+  bool ok[SPEC_PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < SPEC_PER_THREAD; ++q)
+    ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + q * SPEC_THREADS, pw[q], sg[q]);
+  __syncthreads();
+  const T alpha = s_alpha;
+  T sP = T(0), sF = T(0), sG = T(0);
+#pragma unroll
+  for (int q = 0; q < SPEC_PER_THREAD; ++q) {
+    if (!ok[q]) continue;
+    const T x = alpha / (sg[q] + alpha);
+    const T x2 = x * x;
+    sP += pw[q];
+    sF += pw[q] * x2;
+    sG += T(2) * pw[q] * x2 * (T(1) - x);
   }
   double v3[3];
   v3[0] = block_sum<SPEC_THREADS>((double)sP, red);
@@ -610,13 +674,7 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
     }
     st.npass += 1;
     if (conv || st.npass >= 40) st.nconv = 1;
-    if (nn < -32.2) nn = -32.2;                   // alpha floor 1e-14
-    st.nb = nn;
-    double a = exp(nn);
-    if (pd.bc == BC_RECT && a < pd.alpha) a = pd.alpha;   // rectangular hybrid floor
-    st.alpha_n = a;
-    const int it = st.iter - 1;
-    if (it >= 0 && it < pd.max_iter + 2) pd.hist_alpha[it] = a;
+    ns_set_alpha(pd, st, nn);
   }
 }
 
@@ -628,7 +686,7 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
 // e^{-2 pi i m/n} (DFT, m < n) or cos(pi m/n) (DCT, m < 2n).
 __global__ void k_spectrum(int transform, int n, int p, int half, const double* __restrict__ q,
                            const double* __restrict__ tab, double* __restrict__ sigma,
-                           void* lam, int is_double) {
+                           void* lam, void* sigT, int is_double) {
   const int c = (p - 1) / 2;
   const int W = (transform == TR_DCT) ? n : half;
   const size_t tot = (size_t)n * W;
@@ -642,7 +700,8 @@ __global__ void k_spectrum(int transform, int n, int p, int half, const double* 
         s += tab[m] * q[(size_t)a * n + k2];
       }
       sigma[i] = s * s;
-      if (is_double) static_cast<double*>(lam)[i] = s; else static_cast<float*>(lam)[i] = (float)s;
+      if (is_double) { static_cast<double*>(lam)[i] = s; static_cast<double*>(sigT)[i] = s * s; }
+      else { static_cast<float*>(lam)[i] = (float)s; static_cast<float*>(sigT)[i] = (float)(s * s); }
     } else {
       double re = 0.0, im = 0.0;
       for (int a = 0; a < p; ++a) {
@@ -653,8 +712,13 @@ __global__ void k_spectrum(int transform, int n, int p, int half, const double* 
         im += er * qi + ei * qr;
       }
       sigma[i] = re * re + im * im;
-      if (is_double) { static_cast<double2*>(lam)[i] = make_double2(re, im); }
-      else { static_cast<float2*>(lam)[i] = make_float2((float)re, (float)im); }
+      if (is_double) {
+        static_cast<double2*>(lam)[i] = make_double2(re, im);
+        static_cast<double*>(sigT)[i] = re * re + im * im;
+      } else {
+        static_cast<float2*>(lam)[i] = make_float2((float)re, (float)im);
+        static_cast<float*>(sigT)[i] = (float)(re * re + im * im);
+      }
     }
   }
 }
@@ -677,16 +741,19 @@ void launch_rows_inv(const Prob* probs, State* states, const int2* items, int ni
   if (nitems > 0) k_rows_inv<T><<<nitems, TR_THREADS, smem, s>>>(probs, states, items, dst, pcg);
 }
 template <typename T>
-void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, cudaStream_t s) {
-  if (nitems > 0) k_spec<T><<<nitems, SPEC_THREADS, 0, s>>>(probs, states, items);
+void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, int cand,
+                 cudaStream_t s) {
+  if (nitems <= 0) return;
+  if (cand) k_spec_cand<T><<<nitems, SPEC_THREADS, 0, s>>>(probs, states, items);
+  else k_spec<T><<<nitems, SPEC_THREADS, 0, s>>>(probs, states, items);
 }
 void launch_spectrum_setup(const Prob*, int, int transform, int n, int p, int half,
                            const double* q_dev, const double* tab_dev, double* sigma,
-                           void* lam, int is_double, cudaStream_t s) {
+                           void* lam, void* sigT, int is_double, cudaStream_t s) {
   const size_t tot = (size_t)n * (transform == TR_DCT ? n : half);
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_spectrum<<<blocks, 256, 0, s>>>(transform, n, p, half, q_dev, tab_dev, sigma, lam, is_double);
+  k_spectrum<<<blocks, 256, 0, s>>>(transform, n, p, half, q_dev, tab_dev, sigma, lam, sigT, is_double);
 }
 template <typename T>
 cudaError_t fft_set_smem(size_t bytes) {
@@ -701,7 +768,7 @@ cudaError_t fft_set_smem(size_t bytes) {
   template void launch_rows_fwd<T>(const Prob*, State*, const int2*, int, int, int, size_t, cudaStream_t); \
   template void launch_cols<T>(const Prob*, State*, const int2*, int, int, int, double, int, size_t, cudaStream_t); \
   template void launch_rows_inv<T>(const Prob*, State*, const int2*, int, int, int, size_t, cudaStream_t); \
-  template void launch_spec<T>(const Prob*, State*, const int2*, int, cudaStream_t);              \
+  template void launch_spec<T>(const Prob*, State*, const int2*, int, int, cudaStream_t);         \
   template cudaError_t fft_set_smem<T>(size_t);
 INST(float)
 INST(double)

@@ -295,10 +295,10 @@ template <typename TZ> struct ZQueue;
 template <typename TZ>
 struct ZQueue {
   TZ* ring;   // [F2_STAGES][4][F2_THREADS]
-  __device__ __forceinline__ void issue(int slot, const TZ* zp, const int (&zr)[2], const int (&zc)[2], int nf) {
+  __device__ __forceinline__ void issue(int slot, const TZ* zp, const int (&zo)[4]) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const TZ* g = zp + (size_t)zr[e >> 1] * nf + zc[e & 1];
+      const TZ* g = zp + zo[e];
       TZ* d = ring + ((size_t)(slot * 4 + e) * F2_THREADS + threadIdx.x);
       if (sizeof(TZ) == 8) cp_async_8(d, g); else cp_async_4(d, g);
     }
@@ -312,10 +312,9 @@ template <>
 struct ZQueue<__nv_bfloat16> {
   __nv_bfloat16 v[F2_STAGES][4];
   __nv_bfloat16* ring;
-  __device__ __forceinline__ void issue(int slot, const __nv_bfloat16* zp, const int (&zr)[2],
-                                        const int (&zc)[2], int nf) {
+  __device__ __forceinline__ void issue(int slot, const __nv_bfloat16* zp, const int (&zo)[4]) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) v[slot][e] = zp[(size_t)zr[e >> 1] * nf + zc[e & 1]];
+    for (int e = 0; e < 4; ++e) v[slot][e] = zp[zo[e]];
   }
   __device__ __forceinline__ __nv_bfloat16 get(int slot, int e) const { return v[slot][e]; }
 };
@@ -339,13 +338,24 @@ template <typename T> __device__ __forceinline__ T f2_mask(int k, int t) {
                           : (t == 1 ? T(0.5) : T(-0.25)));
 }
 
+template <typename T> struct V2T;
+template <> struct V2T<float> { using type = float2; };
+template <> struct V2T<double> { using type = double2; };
+
+// S_mu(z) = z - clamp(z, -mu, mu): the same value as sgn(z) max(|z| - mu, 0)
+template <typename T> __device__ __forceinline__ T soft_clamp(T z, T mu) {
+  return z - fmin(fmax(z, -mu), mu);
+}
+
 // one level's bands for every micro-tile of the band region; sp is the
-// synthesis accumulator padded by 2D on each side (row pitch SP)
-template <typename T, typename TZ, int LEV, int L, int SP>
+// synthesis accumulator padded by 2D on each side (row pitch SP).  INTERIOR:
+// the band region lies inside the image, so no reflection or sign is needed.
+template <typename T, typename TZ, int LEV, int L, int SP, bool INTERIOR>
 __device__ __forceinline__ void f2_level(const Prob& pd, const T* __restrict__ cur, int rc,
                                          T* __restrict__ sp, const TZ* __restrict__ zin,
                                          TZ* __restrict__ zout, int by0, int bx0, T mu,
                                          ZQueue<TZ>& q) {
+  using T2 = typename V2T<T>::type;
   constexpr int TS = FRAME_TILE;
   constexpr int D = 1 << (LEV - 1);
   constexpr int X = (1 << LEV) - 1;
@@ -361,41 +371,58 @@ __device__ __forceinline__ void f2_level(const Prob& pd, const T* __restrict__ c
   for (int mt = threadIdx.x; mt < MW * MW; mt += F2_THREADS) {
     const int my = mt / MW, mx = mt - my * MW;
     const int qy = 2 * my, qx = 2 * mx;
-    int zr[2], zc[2], pr[2], pc[2];
+    // element offsets of the four positions inside a z plane (planes hold
+    // at most 4126^2 < 2^31 elements), reflected outside the image
+    int zof[4];
+    bool pry[2], prx[2];
     bool inr[2], inc[2];
+    {
+      int zr[2], zc[2];
 #pragma unroll
-    for (int o = 0; o < 2; ++o) {
-      const int gy = by0 - X + qy + o, gx = bx0 - X + qx + o;
-      zr[o] = refl_half(gy, nf, &pr[o]);
-      zc[o] = refl_half(gx, nf, &pc[o]);
-      inr[o] = (qy + o >= X) && (qy + o < X + TS) && (gy < nf);
-      inc[o] = (qx + o >= X) && (qx + o < X + TS) && (gx < nf);
+      for (int o = 0; o < 2; ++o) {
+        const int gy = by0 - X + qy + o, gx = bx0 - X + qx + o;
+        if (INTERIOR) {
+          zr[o] = gy; zc[o] = gx; pry[o] = false; prx[o] = false;
+        } else {
+          int py, px;
+          zr[o] = refl_half(gy, nf, &py);
+          zc[o] = refl_half(gx, nf, &px);
+          pry[o] = py != 0; prx[o] = px != 0;
+        }
+        inr[o] = (qy + o >= X) && (qy + o < X + TS) && (INTERIOR || gy < nf);
+        inc[o] = (qx + o >= X) && (qx + o < X + TS) && (INTERIOR || gx < nf);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) zof[e] = zr[e >> 1] * nf + zc[e & 1];
     }
+    const int zst = (by0 - X + qy) * nf + (bx0 - X + qx);   // z store offset of (0,0)
     // prologue: queue the first bands (k = 3 j + i order)
 #pragma unroll
     for (int p = 0; p < F2_STAGES; ++p) {
       if (p < NB) {
         const int k = K0 + p;
-        q.issue(p, zin + (size_t)f2_band(LEV, L, k % 3, k / 3) * plane, zr, zc, nf);
+        q.issue(p, zin + (size_t)f2_band(LEV, L, k % 3, k / 3) * plane, zof);
       }
       cp_commit();
     }
-    const T* cbase = cur + (size_t)(qy - D + off) * wc + (qx - D + off);
+    const T* cbase = cur + (size_t)(qy - D + off) * wc + (qx - D + off);   // even column: T2 aligned
     T* sbase = sp + (size_t)qy * SP + qx;
-#pragma unroll
+#pragma unroll 1
     for (int jj = 0; jj < 3; ++jj) {
+      // column mask b_j (runtime j keeps one j's state live at a time)
+      const T bj0 = (jj == 0) ? T(0.25) : (jj == 1 ? T(0.35355339059327376220) : T(-0.25));
+      const T bj1 = (jj == 1) ? T(0) : T(0.5);
+      const T bj2 = (jj == 0) ? T(0.25) : (jj == 1 ? T(-0.35355339059327376220) : T(-0.25));
       // h_j on NR rows x 2 output columns
       T h[NR][2];
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
-        const T* row = cbase + k * wc;
+        const T2* row = reinterpret_cast<const T2*>(cbase + k * wc);
         T cv[NR];
 #pragma unroll
-        for (int m = 0; m < NR; ++m) cv[m] = row[m];
+        for (int m = 0; m < NR / 2; ++m) { const T2 v = row[m]; cv[2 * m] = v.x; cv[2 * m + 1] = v.y; }
 #pragma unroll
-        for (int ox = 0; ox < 2; ++ox)
-          h[k][ox] = f2_mask<T>(jj, 0) * cv[ox] + f2_mask<T>(jj, 1) * cv[ox + D] +
-                     f2_mask<T>(jj, 2) * cv[ox + 2 * D];
+        for (int ox = 0; ox < 2; ++ox) h[k][ox] = bj0 * cv[ox] + bj1 * cv[ox + D] + bj2 * cv[ox + 2 * D];
       }
       T P[NR][2];
 #pragma unroll
@@ -405,24 +432,26 @@ __device__ __forceinline__ void f2_level(const Prob& pd, const T* __restrict__ c
         const int k = 3 * jj + ii;
         if (k < K0) continue;
         const int seq = k - K0;
-        const int slot = seq % F2_STAGES;
+        const int slot = seq & (F2_STAGES - 1);
         cp_wait<F2_STAGES - 1>();
         const int band = f2_band(LEV, L, ii, jj);
-        TZ* zo = zout + (size_t)band * plane;
+        TZ* zo = zout + (size_t)band * plane + zst;
         T xv[2][2];
 #pragma unroll
         for (int oy = 0; oy < 2; ++oy) {
 #pragma unroll
           for (int ox = 0; ox < 2; ++ox) {
-            const T a = f2_mask<T>(ii, 0) * h[oy][ox] + f2_mask<T>(ii, 1) * h[oy + D][ox] +
-                        f2_mask<T>(ii, 2) * h[oy + 2 * D][ox];
+            T a = f2_mask<T>(ii, 0) * h[oy][ox] + f2_mask<T>(ii, 2) * h[oy + 2 * D][ox];
+            if (f2_mask<T>(ii, 1) != T(0)) a += f2_mask<T>(ii, 1) * h[oy + D][ox];
             T zv = T(q.get(slot, oy * 2 + ox));
-            const bool neg = ((ii == 1) && pr[oy]) != ((jj == 1) && pc[ox]);
-            if (neg) zv = -zv;
+            if (!INTERIOR) {
+              // antisymmetric bands change sign under an odd number of mirrorings
+              const bool neg = ((ii == 1) && pry[oy]) != ((jj == 1) && prx[ox]);
+              if (neg) zv = -zv;
+            }
             const T znew = zv + a;
-            if (inr[oy] && inc[ox])
-              st_z(zo + (size_t)(by0 - X + qy + oy) * nf + (bx0 - X + qx + ox), znew);
-            xv[oy][ox] = soft_thr<T>(znew, mu);
+            if (inr[oy] && inc[ox]) st_z(zo + oy * nf + ox, znew);
+            xv[oy][ox] = soft_clamp<T>(znew, mu);
           }
         }
         // refill this slot with the band F2_STAGES ahead
@@ -430,7 +459,7 @@ __device__ __forceinline__ void f2_level(const Prob& pd, const T* __restrict__ c
           const int sn = seq + F2_STAGES;
           if (sn < NB) {
             const int kn = K0 + sn;
-            q.issue(slot, zin + (size_t)f2_band(LEV, L, kn % 3, kn / 3) * plane, zr, zc, nf);
+            q.issue(slot, zin + (size_t)f2_band(LEV, L, kn % 3, kn / 3) * plane, zof);
           }
           cp_commit();
         }
@@ -439,9 +468,9 @@ __device__ __forceinline__ void f2_level(const Prob& pd, const T* __restrict__ c
         for (int oy = 0; oy < 2; ++oy)
 #pragma unroll
           for (int ox = 0; ox < 2; ++ox) {
-            if (f2_mask<T>(ii, 0) != T(0)) P[oy][ox] += f2_mask<T>(ii, 0) * xv[oy][ox];
+            P[oy][ox] += f2_mask<T>(ii, 0) * xv[oy][ox];
             if (f2_mask<T>(ii, 1) != T(0)) P[oy + D][ox] += f2_mask<T>(ii, 1) * xv[oy][ox];
-            if (f2_mask<T>(ii, 2) != T(0)) P[oy + 2 * D][ox] += f2_mask<T>(ii, 2) * xv[oy][ox];
+            P[oy + 2 * D][ox] += f2_mask<T>(ii, 2) * xv[oy][ox];
           }
       }
       // horizontal scatter of the patch by b_j and add into the accumulator:
@@ -451,23 +480,35 @@ __device__ __forceinline__ void f2_level(const Prob& pd, const T* __restrict__ c
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
           T v = T(0);
-          bool any = false;
 #pragma unroll
           for (int ox = 0; ox < 2; ++ox) {
             const int t = c - ox;
-            if (t == 0 && f2_mask<T>(jj, 0) != T(0)) { v += f2_mask<T>(jj, 0) * P[r][ox]; any = true; }
-            if (t == D && f2_mask<T>(jj, 1) != T(0)) { v += f2_mask<T>(jj, 1) * P[r][ox]; any = true; }
-            if (t == 2 * D && f2_mask<T>(jj, 2) != T(0)) { v += f2_mask<T>(jj, 2) * P[r][ox]; any = true; }
+            if (t == 0) v += bj0 * P[r][ox];
+            if (t == D) v += bj1 * P[r][ox];
+            if (t == 2 * D) v += bj2 * P[r][ox];
           }
-          if (any) red_shared(sbase + r * SP + c, v);
+          red_shared(sbase + r * SP + c, v);
         }
       }
     }
   }
 }
 
+// dispatch a level on whether the tile's band region lies inside the image
+template <typename T, typename TZ, int LEV, int L, int SP>
+__device__ __forceinline__ void f2_level_any(const Prob& pd, const T* cur, int rc, T* sp,
+                                             const TZ* zin, TZ* zout, int by0, int bx0, T mu,
+                                             ZQueue<TZ>& q) {
+  constexpr int X = (1 << LEV) - 1;
+  const int nf = pd.nf;
+  const bool interior = by0 - X >= 0 && bx0 - X >= 0 && by0 + FRAME_TILE + X <= nf &&
+                        bx0 + FRAME_TILE + X <= nf;
+  if (interior) f2_level<T, TZ, LEV, L, SP, true>(pd, cur, rc, sp, zin, zout, by0, bx0, mu, q);
+  else f2_level<T, TZ, LEV, L, SP, false>(pd, cur, rc, sp, zin, zout, by0, bx0, mu, q);
+}
+
 template <typename T, typename TZ, int L>
-__global__ void __launch_bounds__(F2_THREADS, 2)
+__global__ void __launch_bounds__(F2_THREADS, sizeof(T) == 8 ? 1 : 2)
 k_frame2(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
          int u_slot, int f_slot, const void* zin_op, void* zout_op, double op_mu) {
   using Gm = F2<L>;
@@ -547,10 +588,10 @@ k_frame2(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
     }
   }
   // level 1 reads u only, so it runs before the barrier that publishes c_1
-  f2_level<T, TZ, 1, L, Gm::S0P>(pd, cA, Gm::C0, s0, zin, zout, by0, bx0, mu, q);
+  f2_level_any<T, TZ, 1, L, Gm::S0P>(pd, cA, Gm::C0, s0, zin, zout, by0, bx0, mu, q);
   if (L == 2) {
     __syncthreads();
-    f2_level<T, TZ, 2, L, Gm::S1P>(pd, cB, Gm::C1, s1, zin, zout, by0, bx0, mu, q);
+    f2_level_any<T, TZ, 2, L, Gm::S1P>(pd, cB, Gm::C1, s1, zin, zout, by0, bx0, mu, q);
   }
   __syncthreads();
   if (L == 2) {

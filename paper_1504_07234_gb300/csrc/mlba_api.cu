@@ -167,7 +167,8 @@ void enqueue_step(mlba_batch* B, cudaStream_t s) {
     launch_cols<T>(P, S, B->cols_stat.dev, B->cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
     if (B->any_ns) {
       launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
-      for (int k = 0; k < NEWTON_PASSES; ++k) launch_spec<T>(P, S, B->spec.dev, B->spec.count, s);
+      launch_spec<T>(P, S, B->spec.dev, B->spec.count, 1, s);
+      for (int k = 1; k < NEWTON_PASSES; ++k) launch_spec<T>(P, S, B->spec.dev, B->spec.count, 0, s);
       launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
     }
     launch_rows_inv<T>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
@@ -319,8 +320,11 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
     pd.col_g = std::max(1, std::min(cap, pd.half));
     pd.nblk_cols = (pd.half + pd.col_g - 1) / pd.col_g;
   }
-  const size_t specn = (size_t)n * (pd.transform == TR_DCT ? n : pd.half);
-  pd.nblk_spec = (int)((specn + SPEC_THREADS * SPEC_PER_THREAD - 1) / (SPEC_THREADS * SPEC_PER_THREAD));
+  {
+    const int Wsp = (pd.transform == TR_DCT) ? n : pd.half;
+    const int rows_per = std::max(1, (SPEC_THREADS * SPEC_PER_THREAD) / Wsp);
+    pd.nblk_spec = (n + rows_per - 1) / rows_per;
+  }
   pd.nblk_vec = (int)(((size_t)n * n + VEC_THREADS * VEC_PER_THREAD - 1) / (VEC_THREADS * VEC_PER_THREAD));
   return MLBA_OK;
 }
@@ -368,7 +372,7 @@ int build_spectrum(mlba_batch* B, HostProb& h) {
   CK(cudaMalloc(&dtab, tab.size() * sizeof(double)));
   CK(cudaMemcpyAsync(dq, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, B->stream));
   CK(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, B->stream));
-  launch_spectrum_setup(nullptr, 0, pd.transform, n, p, half, dq, dtab, pd.sigma, pd.lam,
+  launch_spectrum_setup(nullptr, 0, pd.transform, n, p, half, dq, dtab, pd.sigma, pd.lam, pd.w,
                         B->dtype == MLBA_F64 ? 1 : 0, B->stream);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(B->stream));
@@ -428,11 +432,12 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         (size_t)pd.nbands * nf2 * zs,          // z1
         spec ? nspec * 8 : 8,                  // sigma
         spec ? nspec * ts * (pd.transform == TR_DCT ? 1 : 2) : ts,   // lam
+        spec ? nspec * ts : ts,                // sigma in T precision
         spec ? (size_t)pd.n * 2 * ts : ts,     // tw
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
         (size_t)pd.ntaps * 4, (size_t)pd.ntaps * 4, (size_t)pd.ntaps * ts,   // taps
         (size_t)pd.p * ts, (size_t)pd.p * ts,  // hy, hx
-        std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, 33 * (size_t)pd.nblk_spec, (size_t)1}) * 8,  // partial
+        std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, 17 * (size_t)pd.nblk_spec, (size_t)1}) * 8,  // partial
         (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 4};
     offs[i].resize(sz.size());
     for (size_t k = 0; k < sz.size(); ++k) { offs[i][k] = total; total += al(sz[k]); }
@@ -452,6 +457,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     pd.z[1] = base + of[k++];
     pd.sigma = reinterpret_cast<double*>(base + of[k++]);
     pd.lam = base + of[k++];
+    pd.w = base + of[k++];
     pd.tw = base + of[k++];
     pd.dtw = base + of[k++];
     pd.tap_dy = reinterpret_cast<int*>(base + of[k++]);
@@ -463,7 +469,6 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     pd.hist_res = reinterpret_cast<double*>(base + of[k++]);
     pd.hist_alpha = reinterpret_cast<double*>(base + of[k++]);
     pd.hist_beta = reinterpret_cast<int*>(base + of[k++]);
-    pd.w = nullptr;
     // tables
     CK(cudaMemcpy(pd.tap_dy, h.dy.data(), h.dy.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(pd.tap_dx, h.dx.data(), h.dx.size() * 4, cudaMemcpyHostToDevice));
@@ -1004,11 +1009,13 @@ int mlba_op_ns_alpha(mlba_ctx* c, const void* r, double qn, double* alpha_out, i
   if (B->dtype == MLBA_F64) {
     launch_rows_fwd<double>(dtmp, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX0, 0, B->smem_fft, B->stream);
     launch_cols<double>(dtmp, B->d_opstates, B->cols_all.dev, B->cols_all.count, COL_FWD, 0, 0.0, 0, B->smem_fft, B->stream);
-    for (int k = 0; k < 60; ++k) launch_spec<double>(dtmp, B->d_opstates, B->spec_all.dev, B->spec_all.count, B->stream);
+    launch_spec<double>(dtmp, B->d_opstates, B->spec_all.dev, B->spec_all.count, 1, B->stream);
+    for (int k = 1; k < 60; ++k) launch_spec<double>(dtmp, B->d_opstates, B->spec_all.dev, B->spec_all.count, 0, B->stream);
   } else {
     launch_rows_fwd<float>(dtmp, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX0, 0, B->smem_fft, B->stream);
     launch_cols<float>(dtmp, B->d_opstates, B->cols_all.dev, B->cols_all.count, COL_FWD, 0, 0.0, 0, B->smem_fft, B->stream);
-    for (int k = 0; k < 60; ++k) launch_spec<float>(dtmp, B->d_opstates, B->spec_all.dev, B->spec_all.count, B->stream);
+    launch_spec<float>(dtmp, B->d_opstates, B->spec_all.dev, B->spec_all.count, 1, B->stream);
+    for (int k = 1; k < 60; ++k) launch_spec<float>(dtmp, B->d_opstates, B->spec_all.dev, B->spec_all.count, 0, B->stream);
   }
   CK(cudaGetLastError());
   State s1;

@@ -52,7 +52,7 @@ struct Prob {
   double mu, alpha, gamma, delta, q, rho, tau, pcg_tol;
   void* buf[NSLOT];
   void* z[2];        // ping-pong Bregman variable
-  void* w;           // stationary spectral weight (includes 1/n^2)
+  void* w;           // |lambda|^2 in T precision (per-element weights and alpha_n terms)
   void* lam;         // spectrum of C (real for DCT, complex half for DFT), T precision
   double* sigma;     // |lambda|^2 in FP64
   void* tw;          // exp(-2 pi i k/n), k < n   (T2)
@@ -141,6 +141,32 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
   }
   return r;  // valid in thread 0
+}
+
+// block-wide sums of K doubles with one barrier: warp shuffles, then one
+// thread per value sums the warp partials in warp order (results in thread 0's
+// out[] after the call; every thread must call)
+template <int NT, int K>
+__device__ __forceinline__ void block_sum_k(double (&v)[K], double (&out)[K], double* sh) {
+  constexpr int NW = NT / 32;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * NW + w] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < NW; ++i) s += sh[k * NW + i];
+      out[k] = s;
+    }
+  }
 }
 
 // Last-block reduction: every block of problem `pi` calls this with its K

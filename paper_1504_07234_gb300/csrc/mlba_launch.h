@@ -58,10 +58,11 @@ template <typename T>
 void launch_rows_inv(const Prob* probs, State* states, const int2* items, int nitems, int dst,
                      int pcg, size_t smem, cudaStream_t s);
 template <typename T>
-void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, cudaStream_t s);
+void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, int cand,
+                 cudaStream_t s);
 void launch_spectrum_setup(const Prob* probs, int pi, int transform, int n, int p, int half,
                            const double* q_dev, const double* tab_dev, double* sigma,
-                           void* lam, int is_double, cudaStream_t s);
+                           void* lam, void* sigT, int is_double, cudaStream_t s);
 template <typename T, typename TZ>
 void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, int u_slot,
                   int f_slot, const void* zin, void* zout, double op_mu, size_t smem, int levels,

@@ -115,8 +115,11 @@ def test_frame_tight_frame_on_gpu(M):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("transform,psf,n", [("dct", "disk2", 64), ("dft", "motion7", 96),
-                                             ("dct", "gauss9", 60)])
+                                             ("dct", "gauss9", 60), ("dft", "motion7", 300),
+                                             ("dct", "disk2", 200)])
 def test_ns_alpha(M, dtype, transform, psf, n):
+    """Also at sizes whose spectrum rows do not tile the per-block element
+    count (300: 151 half-spectrum columns; 200: 200 DCT columns)."""
     h = PSFS[psf]
     ctx = M.Context(h, n, "reflective" if transform == "dct" else "periodic", "tikh_ns",
                     dtype=dtype, transform=transform)
