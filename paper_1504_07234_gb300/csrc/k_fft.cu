@@ -12,11 +12,19 @@
 // (for 4-NS the forward spectrum is kept for the alpha_n solve and the weight
 // and inverse run after it).  Pass 3 (rows): inverse.  The unnormalised
 // forward / inverse pair gives n^2 times the result; 1/n^2 is folded into the
-// weight.  Weights are formed with an FP64 denominator sigma + alpha.
+// weight.  Weights are formed in T from |lambda|^2 rounded once to T.
 //
-// The 1-D FFT is a Stockham autosort FFT in shared memory with radix 2, 3,
-// 4 and 5 stages; each stage loads all butterfly inputs of a thread into
-// registers, synchronises, and stores in place.
+// The spectrum (S, lambda, |lambda|^2) is stored column-blocked: columns are
+// grouped in blocks of cb, each block n rows x cb contiguous elements, so a
+// column-pass CTA reads and writes one contiguous block and the row passes
+// write / read contiguous runs of cb.
+//
+// The 1-D FFT is a Stockham autosort FFT in shared memory with radix 16, 8,
+// 4, 2, 3 and 5 passes (16 and 8 as 4 x 4 and 4 x 2 register butterflies with
+// constant inner twiddles); each pass loads all butterfly inputs of a thread
+// into registers, synchronises, and stores in place.  Shared memory holds
+// element i of a transform at i + i/16 so that radix-R strides do not hit the
+// same bank.
 #include "mlba_internal.cuh"
 #include "mlba_launch.h"
 
@@ -79,33 +87,109 @@ __device__ __forceinline__ void dft5(T2* v) {
     v[2] = csub(m2, in2); v[3] = cadd(m2, in2);
   }
 }
+// cos and sin of 2 pi m / 16 for the inner twiddles of the radix-16 and
+// radix-8 butterflies (m < 16)
+__host__ __device__ constexpr double cos16(int m) {
+  return m == 0 ? 1.0 : m == 1 ? 0.92387953251128675613 : m == 2 ? 0.70710678118654752440
+       : m == 3 ? 0.38268343236508977173 : m == 4 ? 0.0 : m == 5 ? -0.38268343236508977173
+       : m == 6 ? -0.70710678118654752440 : m == 7 ? -0.92387953251128675613 : m == 8 ? -1.0
+       : -cos16(m - 8);
+}
+__host__ __device__ constexpr double sin16(int m) { return cos16((m + 12) % 16); }
+// multiply by exp(-/+ 2 pi i m / 16) for a compile-time m
+template <typename T2, int M, bool INV>
+__device__ __forceinline__ T2 tw16(T2 a) {
+  using T = decltype(a.x);
+  if (M % 16 == 0) return a;
+  const T cr = T(cos16(M % 16)), si = INV ? T(sin16(M % 16)) : T(-sin16(M % 16));
+  T2 r; r.x = a.x * cr - a.y * si; r.y = a.x * si + a.y * cr;
+  return r;
+}
+// 16-point DFT as 4 x 4: X[k1 + 4 k2] = sum_r1 w4^(r1 k2) [w16^(r1 k1) DFT4_r2(v[r1 + 4 r2])](k1)
+template <typename T2, bool INV>
+__device__ __forceinline__ void dft16(T2* v) {
+  T2 y[4][4];
+#pragma unroll
+  for (int r1 = 0; r1 < 4; ++r1) {
+    T2 a[4] = {v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]};
+    dft4<T2, INV>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[r1][k1] = a[k1];
+  }
+  y[1][1] = tw16<T2, 1, INV>(y[1][1]); y[1][2] = tw16<T2, 2, INV>(y[1][2]); y[1][3] = tw16<T2, 3, INV>(y[1][3]);
+  y[2][1] = tw16<T2, 2, INV>(y[2][1]); y[2][2] = tw16<T2, 4, INV>(y[2][2]); y[2][3] = tw16<T2, 6, INV>(y[2][3]);
+  y[3][1] = tw16<T2, 3, INV>(y[3][1]); y[3][2] = tw16<T2, 6, INV>(y[3][2]); y[3][3] = tw16<T2, 9, INV>(y[3][3]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    T2 b[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+    dft4<T2, INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+  }
+}
+// 8-point DFT as 4 x 2: X[k1 + 4 k2] = sum_r1 w2^(r1 k2) [w8^(r1 k1) DFT4_r2(v[r1 + 2 r2])](k1)
+template <typename T2, bool INV>
+__device__ __forceinline__ void dft8(T2* v) {
+  T2 y[2][4];
+#pragma unroll
+  for (int r1 = 0; r1 < 2; ++r1) {
+    T2 a[4] = {v[r1], v[r1 + 2], v[r1 + 4], v[r1 + 6]};
+    dft4<T2, INV>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[r1][k1] = a[k1];
+  }
+  y[1][1] = tw16<T2, 2, INV>(y[1][1]); y[1][2] = tw16<T2, 4, INV>(y[1][2]); y[1][3] = tw16<T2, 6, INV>(y[1][3]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    T2 b[2] = {y[0][k1], y[1][k1]};
+    dft2<T2, INV>(b);
+    v[k1] = b[0];
+    v[k1 + 4] = b[1];
+  }
+}
 
 template <typename T2, int R, bool INV>
 __device__ __forceinline__ void dft_small(T2* v) {
   if (R == 2) dft2<T2, INV>(v);
   else if (R == 3) dft3<T2, INV>(v);
   else if (R == 4) dft4<T2, INV>(v);
-  else dft5<T2, INV>(v);
+  else if (R == 5) dft5<T2, INV>(v);
+  else if (R == 8) dft8<T2, INV>(v);
+  else dft16<T2, INV>(v);
 }
 
-// one Stockham stage over G transforms of length N stored back to back
+// threads of a transform CTA and the minimum CTAs per SM (register budget):
+// FP32 256 threads, at least 3 CTAs (85 registers); FP64 512 threads, so that
+// each thread holds half as many values
+__host__ __device__ constexpr int tr_nt(int elem_bytes) { return elem_bytes == 8 ? 512 : 256; }
+__host__ __device__ constexpr int tr_minb(int elem_bytes) { return elem_bytes == 8 ? 1 : 3; }
+
+// shared-memory layout of a transform: element i at fpad(i) (one spare slot
+// every 16 breaks power-of-two strides), transforms TSg = fpad(N) + 1 apart
+__host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+
+// One Stockham pass of radix R over G transforms of length N.  Each thread
+// loads all inputs of its butterflies, the block synchronises, then stores:
+// the pass runs in place.
 template <typename T2, int R, bool INV>
-__device__ __forceinline__ void fft_stage(T2* sm, int G, int N, int Ns, const T2* __restrict__ tw) {
-  constexpr int MAXV = (sizeof(T2) == 16) ? TR_MAXV_F64 : TR_MAXV;
-  constexpr int MAXB = (MAXV + R - 1) / R;
+__device__ __forceinline__ void fft_pass(int G, int N, int TSg, int Ns, const T2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  constexpr int NT = tr_nt(sizeof(T2) / 2);
+  constexpr int MAXB = (TR_CAP + R * NT - 1) / (R * NT);
   const int per = N / R;
   const int nbf = G * per;
   const int step = N / (Ns * R);
   T2 v[MAXB][R];
 #pragma unroll
   for (int q = 0; q < MAXB; ++q) {
-    const int b = threadIdx.x + q * TR_THREADS;
+    const int b = threadIdx.x + q * NT;
     if (b < nbf) {
       const int g = b / per, j = b - g * per;
       const int k = j % Ns;
-      const T2* base = sm + g * N;
+      const T2* base = sm + g * TSg;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = base[j + r * per];
+      for (int r = 0; r < R; ++r) v[q][r] = base[fpad(j + r * per)];
       if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -120,31 +204,37 @@ __device__ __forceinline__ void fft_stage(T2* sm, int G, int N, int Ns, const T2
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < MAXB; ++q) {
-    const int b = threadIdx.x + q * TR_THREADS;
+    const int b = threadIdx.x + q * NT;
     if (b < nbf) {
       const int g = b / per, j = b - g * per;
       const int k = j % Ns;
-      T2* base = sm + g * N + (j / Ns) * Ns * R + k;
+      T2* base = sm + g * TSg;
+      const int o = (j / Ns) * Ns * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) base[r * Ns] = v[q][r];
+      for (int r = 0; r < R; ++r) base[fpad(o + r * Ns)] = v[q][r];
     }
   }
   __syncthreads();
 }
 
+// G transforms of length n held in the dynamic shared memory of the block
+// (transform g at g * (fpad(n) + 1)); all threads of the block call this
+// The passes run grouped by radix (16s, one 8/4/2, 3s, 5s) in straight-line
+// regions rather than as one loop over a radix switch: the compiler then
+// keeps each region's butterflies in registers (the switch form spilled).
 template <typename T2, bool INV>
-__device__ __forceinline__ void fft_smem(T2* sm, int G, const Prob& pd) {
+__device__ __forceinline__ void fft_smem(int G, const Prob& pd) {
   const int N = pd.n;
+  const int TSg = fpad(N) + 1;
   const T2* tw = static_cast<const T2*>(pd.tw);
+  const int n16 = pd.nr16, r2 = pd.r2, n3 = pd.nr3, n5 = pd.nr5;
   int Ns = 1;
-  for (int s = 0; s < pd.nstage; ++s) {
-    const int R = pd.radix[s];
-    if (R == 4) fft_stage<T2, 4, INV>(sm, G, N, Ns, tw);
-    else if (R == 2) fft_stage<T2, 2, INV>(sm, G, N, Ns, tw);
-    else if (R == 3) fft_stage<T2, 3, INV>(sm, G, N, Ns, tw);
-    else fft_stage<T2, 5, INV>(sm, G, N, Ns, tw);
-    Ns *= R;
-  }
+  for (int s = 0; s < n16; ++s) { fft_pass<T2, 16, INV>(G, N, TSg, Ns, tw); Ns *= 16; }
+  if (r2 == 8) { fft_pass<T2, 8, INV>(G, N, TSg, Ns, tw); Ns *= 8; }
+  if (r2 == 4) { fft_pass<T2, 4, INV>(G, N, TSg, Ns, tw); Ns *= 4; }
+  if (r2 == 2) { fft_pass<T2, 2, INV>(G, N, TSg, Ns, tw); Ns *= 2; }
+  for (int s = 0; s < n3; ++s) { fft_pass<T2, 3, INV>(G, N, TSg, Ns, tw); Ns *= 3; }
+  for (int s = 0; s < n5; ++s) { fft_pass<T2, 5, INV>(G, N, TSg, Ns, tw); Ns *= 5; }
 }
 
 // position of input sample y in the DCT reordering v[j] = x[2j], v[N-1-j] = x[2j+1]
@@ -171,16 +261,17 @@ __device__ __forceinline__ T2 split_one(T2 Z, T2 Zr, T2 d) {
   return o;
 }
 template <typename T, typename T2>
-__device__ __forceinline__ void dct_split(T2* sm, int G, int N, const T2* __restrict__ dtw) {
+__device__ __forceinline__ void dct_split(T2* sm, int G, int N, int TSg, const T2* __restrict__ dtw) {
+  constexpr int NT = tr_nt(sizeof(T));
   const int np = N / 2 + 1;
-  for (int e = threadIdx.x; e < G * np; e += TR_THREADS) {
+  for (int e = threadIdx.x; e < G * np; e += NT) {
     const int g = e / np, k = e - g * np;
     const int kr = (k == 0) ? 0 : N - k;
-    T2* b = sm + g * N;
-    const T2 Z = b[k], Zr = b[kr];
+    T2* b = sm + g * TSg;
+    const T2 Z = b[fpad(k)], Zr = b[fpad(kr)];
     const T2 ok = split_one<T, T2>(Z, Zr, __ldg(&dtw[k]));
-    if (kr != k) b[kr] = split_one<T, T2>(Zr, Z, __ldg(&dtw[kr]));
-    b[k] = ok;
+    if (kr != k) b[fpad(kr)] = split_one<T, T2>(Zr, Z, __ldg(&dtw[kr]));
+    b[fpad(k)] = ok;
   }
   __syncthreads();
 }
@@ -198,17 +289,18 @@ __device__ __forceinline__ T2 merge_one(T2 X, T2 Xr, T2 d) {
   return o;
 }
 template <typename T, typename T2>
-__device__ __forceinline__ void dct_merge(T2* sm, int G, int N, const T2* __restrict__ dtw) {
+__device__ __forceinline__ void dct_merge(T2* sm, int G, int N, int TSg, const T2* __restrict__ dtw) {
+  constexpr int NT = tr_nt(sizeof(T));
   const int np = N / 2 + 1;
-  for (int e = threadIdx.x; e < G * np; e += TR_THREADS) {
+  for (int e = threadIdx.x; e < G * np; e += NT) {
     const int g = e / np, k = e - g * np;
-    T2* b = sm + g * N;
-    const T2 X = b[k];
+    T2* b = sm + g * TSg;
+    const T2 X = b[fpad(k)];
     T2 Xr;
-    if (k == 0) { Xr.x = T(0); Xr.y = T(0); } else Xr = b[N - k];
+    if (k == 0) { Xr.x = T(0); Xr.y = T(0); } else Xr = b[fpad(N - k)];
     const T2 ok = merge_one<T, T2>(X, Xr, __ldg(&dtw[k]));
-    if (k != 0 && N - k != k) b[N - k] = merge_one<T, T2>(Xr, X, __ldg(&dtw[N - k]));
-    b[k] = ok;
+    if (k != 0 && N - k != k) b[fpad(N - k)] = merge_one<T, T2>(Xr, X, __ldg(&dtw[N - k]));
+    b[fpad(k)] = ok;
   }
   __syncthreads();
 }
@@ -220,29 +312,30 @@ __device__ __forceinline__ bool tr_skip(const State& st, int pcg) {
 // ---------------------------------------------------------------------------
 // Pass 1: forward transform of row pairs: src (n x n real) -> S
 template <typename T>
-__global__ void __launch_bounds__(TR_THREADS, 1)
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
 k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
            int src_slot, int pcg) {
   using T2 = typename Vec2<T>::type;
+  constexpr int NT = tr_nt(sizeof(T)), MAXV = TR_CAP / NT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
   if (tr_skip(states[item.x], pcg)) return;
-  const int N = pd.n, G = pd.row_g;
+  const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
   const int pair0 = item.y * G;
+  const int row0 = 2 * pair0;
   const bool dct = (pd.transform == TR_DCT);
   const T* src = static_cast<const T*>(pd.buf[src_slot]);
   {
     // all loads of this thread first (up to MAXV in flight), then the stores
-    constexpr int MAXV = (sizeof(T) == 8) ? TR_MAXV_F64 : TR_MAXV;
     T2 tmp[MAXV];
 #pragma unroll
     for (int q = 0; q < MAXV; ++q) {
-      const int e = threadIdx.x + q * TR_THREADS;
+      const int e = threadIdx.x + q * NT;
       if (e < G * N) {
         const int g = e / N, x = e - g * N;
-        const int ra = 2 * (pair0 + g), rb = ra + 1;
+        const int ra = row0 + 2 * g, rb = ra + 1;
         const int xs = dct ? dct_src(x, N) : x;
         tmp[q].x = (ra < N) ? src[(size_t)ra * N + xs] : T(0);
         tmp[q].y = (rb < N) ? src[(size_t)rb * N + xs] : T(0);
@@ -250,42 +343,42 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
     }
 #pragma unroll
     for (int q = 0; q < MAXV; ++q) {
-      const int e = threadIdx.x + q * TR_THREADS;
-      if (e < G * N) sm[e] = tmp[q];
+      const int e = threadIdx.x + q * NT;
+      if (e < G * N) { const int g = e / N, x = e - g * N; sm[g * TSg + fpad(x)] = tmp[q]; }
     }
   }
   __syncthreads();
-  fft_smem<T2, false>(sm, G, pd);
-  if (dct) {
-    dct_split<T, T2>(sm, G, N, static_cast<const T2*>(pd.dtw));
-    T* S = static_cast<T*>(pd.buf[SL_S]);
-    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
-      const int g = e / N, k = e - g * N;
-      const int ra = 2 * (pair0 + g), rb = ra + 1;
-      const T2 X = sm[e];
-      if (ra < N) S[(size_t)ra * N + k] = X.x;
-      if (rb < N) S[(size_t)rb * N + k] = X.y;
-    }
-  } else {
-    const int H = pd.half;
-    T2* S = static_cast<T2*>(pd.buf[SL_S]);
-    for (int e = threadIdx.x; e < G * H; e += TR_THREADS) {
-      const int g = e / H, k = e - g * H;
-      const int ra = 2 * (pair0 + g), rb = ra + 1;
-      const T2 Z = sm[g * N + k];
-      const T2 Zr = sm[g * N + (k == 0 ? 0 : N - k)];
-      T2 xa, xb;
-      xa.x = T(0.5) * (Z.x + Zr.x); xa.y = T(0.5) * (Z.y - Zr.y);
-      xb.x = T(0.5) * (Z.y + Zr.y); xb.y = T(-0.5) * (Z.x - Zr.x);
-      if (ra < N) S[(size_t)ra * H + k] = xa;
-      if (rb < N) S[(size_t)rb * H + k] = xb;
+  fft_smem<T2, false>(G, pd);
+  if (dct) dct_split<T, T2>(sm, G, N, TSg, static_cast<const T2*>(pd.dtw));
+  // write the rows of this CTA into every column block (contiguous runs)
+  const int W = dct ? N : pd.half;
+  const int cb = pd.cb;
+  const int R2 = 2 * G;
+  const int nb = (W + cb - 1) / cb;
+  for (int e = threadIdx.x; e < nb * R2 * cb; e += NT) {
+    const int b = e / (R2 * cb), rem = e - b * (R2 * cb);
+    const int rl = rem / cb, c = rem - rl * cb;
+    const int k = b * cb + c, row = row0 + rl;
+    if (k >= W || row >= N) continue;
+    const T2* tb = sm + (rl >> 1) * TSg;
+    const size_t o = (size_t)b * N * cb + (size_t)row * cb + c;
+    if (dct) {
+      const T2 X = tb[fpad(k)];
+      static_cast<T*>(pd.buf[SL_S])[o] = (rl & 1) ? X.y : X.x;
+    } else {
+      const T2 Z = tb[fpad(k)];
+      const T2 Zr = tb[fpad(k == 0 ? 0 : N - k)];
+      T2 X;
+      if (rl & 1) { X.x = T(0.5) * (Z.y + Zr.y); X.y = T(-0.5) * (Z.x - Zr.x); }   // (Z - conj Zr)/(2i)
+      else { X.x = T(0.5) * (Z.x + Zr.x); X.y = T(0.5) * (Z.y - Zr.y); }           // (Z + conj Zr)/2
+      static_cast<T2*>(pd.buf[SL_S])[o] = X;
     }
   }
 }
 
-// spectral weight at (k1, col); alpha and kind as given.  |lambda|^2 + alpha
-// is formed in T: alpha > 0 keeps it away from zero (no cancellation), so
-// FP32 holds it to 6e-8 relative; 1/n^2 of the unnormalised pair is folded in.
+// spectral weight at blocked index idx; alpha and kind as given.  |lambda|^2 +
+// alpha is formed in T: alpha > 0 keeps it away from zero (no cancellation),
+// so FP32 holds it to 6e-8 relative; 1/n^2 of the unnormalised pair is folded in.
 template <typename T, typename T2>
 __device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
   const T inv = scale / (static_cast<const T*>(pd.w)[idx] + alpha);
@@ -302,13 +395,14 @@ __device__ __forceinline__ T weight_dct(const Prob& pd, size_t idx, T alpha, T s
   return kind == W_TIKH ? static_cast<const T*>(pd.lam)[idx] * inv : inv;
 }
 
-// Pass 2: columns.  DFT: G complex columns of S (n x half).  DCT: G pairs of
-// real columns of S (n x n).
+// Pass 2: one column block per CTA.  DFT: cb complex columns; DCT: cb real
+// columns = cb/2 packed pairs.
 template <typename T>
-__global__ void __launch_bounds__(TR_THREADS, 1)
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
 k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
        int mode, int pcg, double op_alpha, int op_kind) {
   using T2 = typename Vec2<T>::type;
+  constexpr int NT = tr_nt(sizeof(T)), MAXV = TR_CAP / NT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int2 item = items[blockIdx.x];
@@ -316,7 +410,7 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   const State& st = states[item.x];
   if (tr_skip(st, pcg)) return;
   if (mode == COL_NS_INV && !pd.ns) return;
-  const int N = pd.n, G = pd.col_g;
+  const int N = pd.n, cb = pd.cb, TSg = fpad(N) + 1;
   const bool dct = (pd.transform == TR_DCT);
   // weight parameters
   double alpha = pd.alpha;
@@ -326,174 +420,195 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   if (pd.precond == P_KRYLOV) kind = W_INV;
   const T Ta = T(alpha);
   const T Tsc = T(1.0 / ((double)pd.n * (double)pd.n));
-
+  const size_t base = (size_t)item.y * N * cb;       // this CTA's contiguous block
+  const int W = dct ? N : pd.half;
+  const int kb = item.y * cb;                         // first column of the block
   if (!dct) {
-    const int H = pd.half;
-    const int k0 = item.y * G;
-    T2* S = static_cast<T2*>(pd.buf[SL_S]);
+    const int G = cb;
+    T2* S = static_cast<T2*>(pd.buf[SL_S]) + base;
     {
-      constexpr int MAXV = (sizeof(T) == 8) ? TR_MAXV_F64 : TR_MAXV;
       T2 tmp[MAXV];
 #pragma unroll
       for (int q = 0; q < MAXV; ++q) {
-        const int e = threadIdx.x + q * TR_THREADS;
+        const int e = threadIdx.x + q * NT;
         tmp[q].x = T(0); tmp[q].y = T(0);
-        if (e < G * N) {
-          const int y = e / G, g = e - y * G;
-          if (k0 + g < H) tmp[q] = S[(size_t)y * H + k0 + g];
-        }
+        if (e < N * G && kb + e % G < W) tmp[q] = S[e];
       }
 #pragma unroll
       for (int q = 0; q < MAXV; ++q) {
-        const int e = threadIdx.x + q * TR_THREADS;
-        if (e < G * N) { const int y = e / G, g = e - y * G; sm[g * N + y] = tmp[q]; }
+        const int e = threadIdx.x + q * NT;
+        if (e < N * G) { const int k1 = e / G, c = e - k1 * G; sm[c * TSg + fpad(k1)] = tmp[q]; }
       }
     }
     __syncthreads();
-    if (mode != COL_NS_INV) fft_smem<T2, false>(sm, G, pd);
+    if (mode != COL_NS_INV) fft_smem<T2, false>(G, pd);
     if (mode == COL_FWD) {
-      for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
-        const int y = e / G, g = e - y * G;
-        const int col = k0 + g;
-        if (col < H) S[(size_t)y * H + col] = sm[g * N + y];
+      for (int e = threadIdx.x; e < N * G; e += NT) {
+        const int k1 = e / G, c = e - k1 * G;
+        if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
       }
       return;
     }
-    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
-      const int g = e / N, k1 = e - g * N;
-      const int col = k0 + g;
-      if (col < H) sm[e] = cmul(sm[e], weight_dft<T, T2>(pd, (size_t)k1 * H + col, Ta, Tsc, kind));
+    for (int e = threadIdx.x; e < N * G; e += NT) {
+      const int k1 = e / G, c = e - k1 * G;
+      if (kb + c < W) {
+        T2& v = sm[c * TSg + fpad(k1)];
+        v = cmul(v, weight_dft<T, T2>(pd, base + e, Ta, Tsc, kind));
+      }
     }
     __syncthreads();
-    fft_smem<T2, true>(sm, G, pd);
-    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
-      const int y = e / G, g = e - y * G;
-      const int col = k0 + g;
-      if (col < H) S[(size_t)y * H + col] = sm[g * N + y];
+    fft_smem<T2, true>(G, pd);
+    for (int e = threadIdx.x; e < N * G; e += NT) {
+      const int k1 = e / G, c = e - k1 * G;
+      if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
     }
   } else {
-    const int k0 = item.y * 2 * G;          // first real column
-    T* S = static_cast<T*>(pd.buf[SL_S]);
+    const int G = cb / 2;
+    T* S = static_cast<T*>(pd.buf[SL_S]) + base;
     T* smr = reinterpret_cast<T*>(sm);
     {
-      constexpr int MAXV = 2 * ((sizeof(T) == 8) ? TR_MAXV_F64 : TR_MAXV);
-      T tmp[MAXV];
+      T tmp[2 * MAXV];
 #pragma unroll
-      for (int q = 0; q < MAXV; ++q) {
-        const int e = threadIdx.x + q * TR_THREADS;
+      for (int q = 0; q < 2 * MAXV; ++q) {
+        const int e = threadIdx.x + q * NT;
         tmp[q] = T(0);
-        if (e < 2 * G * N) {
-          const int y = e / (2 * G), cc = e - y * (2 * G);
-          if (k0 + cc < N) tmp[q] = S[(size_t)y * N + k0 + cc];
-        }
+        if (e < N * cb) { const int c = e % cb; if (kb + c < W) tmp[q] = S[e]; }
       }
 #pragma unroll
-      for (int q = 0; q < MAXV; ++q) {
-        const int e = threadIdx.x + q * TR_THREADS;
-        if (e < 2 * G * N) {
-          const int y = e / (2 * G), cc = e - y * (2 * G);
-          const int pos = (mode == COL_NS_INV) ? y : dct_pos(y, N);
-          smr[2 * ((cc >> 1) * N + pos) + (cc & 1)] = tmp[q];
+      for (int q = 0; q < 2 * MAXV; ++q) {
+        const int e = threadIdx.x + q * NT;
+        if (e < N * cb) {
+          const int k1 = e / cb, c = e - k1 * cb;
+          const int pos = (mode == COL_NS_INV) ? k1 : dct_pos(k1, N);
+          smr[2 * ((c >> 1) * TSg + fpad(pos)) + (c & 1)] = tmp[q];
         }
       }
     }
     __syncthreads();
     const T2* dtw = static_cast<const T2*>(pd.dtw);
     if (mode != COL_NS_INV) {
-      fft_smem<T2, false>(sm, G, pd);
-      dct_split<T, T2>(sm, G, N, dtw);
+      fft_smem<T2, false>(G, pd);
+      dct_split<T, T2>(sm, G, N, TSg, dtw);
     }
     if (mode == COL_FWD) {
-      for (int e = threadIdx.x; e < 2 * G * N; e += TR_THREADS) {
-        const int y = e / (2 * G), cc = e - y * (2 * G);
-        const int col = k0 + cc;
-        if (col < N) S[(size_t)y * N + col] = smr[2 * ((cc >> 1) * N + y) + (cc & 1)];
+      for (int e = threadIdx.x; e < N * cb; e += NT) {
+        const int k1 = e / cb, c = e - k1 * cb;
+        if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
       }
       return;
     }
-    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
-      const int g = e / N, k1 = e - g * N;
-      const int ca = k0 + 2 * g, cb = ca + 1;
-      T2 v = sm[e];
-      v.x *= (ca < N) ? weight_dct<T>(pd, (size_t)k1 * N + ca, Ta, Tsc, kind) : T(0);
-      v.y *= (cb < N) ? weight_dct<T>(pd, (size_t)k1 * N + cb, Ta, Tsc, kind) : T(0);
-      sm[e] = v;
+    for (int e = threadIdx.x; e < N * cb; e += NT) {
+      const int k1 = e / cb, c = e - k1 * cb;
+      T& v = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
+      v *= (kb + c < W) ? weight_dct<T>(pd, base + e, Ta, Tsc, kind) : T(0);
     }
     __syncthreads();
-    dct_merge<T, T2>(sm, G, N, dtw);
-    fft_smem<T2, true>(sm, G, pd);
-    for (int e = threadIdx.x; e < 2 * G * N; e += TR_THREADS) {
-      const int y = e / (2 * G), cc = e - y * (2 * G);
-      const int col = k0 + cc;
-      if (col < N) S[(size_t)y * N + col] = smr[2 * ((cc >> 1) * N + dct_pos(y, N)) + (cc & 1)];
+    dct_merge<T, T2>(sm, G, N, TSg, dtw);
+    fft_smem<T2, true>(G, pd);
+    for (int e = threadIdx.x; e < N * cb; e += NT) {
+      const int k1 = e / cb, c = e - k1 * cb;
+      if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(dct_pos(k1, N))) + (c & 1)];
     }
   }
 }
 
 // Pass 3: inverse transform of row pairs: S -> dst (n x n real)
 template <typename T>
-__global__ void __launch_bounds__(TR_THREADS, 1)
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
 k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
            int dst_slot, int pcg) {
   using T2 = typename Vec2<T>::type;
+  constexpr int NT = tr_nt(sizeof(T));
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
   if (tr_skip(states[item.x], pcg)) return;
-  const int N = pd.n, G = pd.row_g;
-  const int pair0 = item.y * G;
+  const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
+  const int row0 = 2 * item.y * G;
   const bool dct = (pd.transform == TR_DCT);
+  // Loads walk the column blocks: within block b the 2G rows of this CTA are
+  // one contiguous run of 2G cb elements; thread e takes column c of pair g.
+  const int cb = pd.cb;
+  const int W = dct ? N : pd.half;
+  const int nb = (W + cb - 1) / cb;
+  const int tot = nb * G * cb;
+  constexpr int BATCH = 4;
   if (dct) {
     const T* S = static_cast<const T*>(pd.buf[SL_S]);
-    for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
-      const int g = e / N, k = e - g * N;
-      const int ra = 2 * (pair0 + g), rb = ra + 1;
-      T2 v;
-      v.x = (ra < N) ? S[(size_t)ra * N + k] : T(0);
-      v.y = (rb < N) ? S[(size_t)rb * N + k] : T(0);
-      sm[e] = v;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += BATCH * NT) {
+      T2 v[BATCH];
+      int k[BATCH];
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = e0 + u * NT;
+        k[u] = -1;
+        if (e < tot) {
+          const int b = e / (G * cb), rem = e - b * (G * cb);
+          const int g = rem / cb, c = rem - g * cb;
+          const int ra = row0 + 2 * g;
+          const size_t o = (size_t)b * N * cb + (size_t)ra * cb + c;
+          k[u] = b * cb + c;
+          v[u].x = (ra < N && k[u] < W) ? S[o] : T(0);
+          v[u].y = (ra + 1 < N && k[u] < W) ? S[o + cb] : T(0);
+          k[u] = (k[u] < W) ? (g << 16) | k[u] : -1;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u)
+        if (k[u] >= 0) sm[(k[u] >> 16) * TSg + fpad(k[u] & 0xffff)] = v[u];
     }
     __syncthreads();
-    dct_merge<T, T2>(sm, G, N, static_cast<const T2*>(pd.dtw));
+    dct_merge<T, T2>(sm, G, N, TSg, static_cast<const T2*>(pd.dtw));
   } else {
-    const int H = pd.half;
-    const T2* S = static_cast<const T2*>(pd.buf[SL_S]);
+    // Z[k] = Xa[k] + i Xb[k]; the missing half from Hermitian symmetry
     const bool even = (N & 1) == 0;
-    constexpr int MAXV = (sizeof(T) == 8) ? TR_MAXV_F64 : TR_MAXV;
-    T2 ta[MAXV], tb[MAXV];
+    const T2* S = static_cast<const T2*>(pd.buf[SL_S]);
+    for (int e0 = threadIdx.x; e0 < tot; e0 += BATCH * NT) {
+      T2 xa[BATCH], xb[BATCH];
+      int k[BATCH];
 #pragma unroll
-    for (int q = 0; q < MAXV; ++q) {
-      const int e = threadIdx.x + q * TR_THREADS;
-      ta[q].x = ta[q].y = tb[q].x = tb[q].y = T(0);
-      if (e < G * N) {
-        const int g = e / N, k = e - g * N;
-        const int ra = 2 * (pair0 + g), rb = ra + 1;
-        const int kk = (k < H) ? k : N - k;
-        if (ra < N) ta[q] = S[(size_t)ra * H + kk];
-        if (rb < N) tb[q] = S[(size_t)rb * H + kk];
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = e0 + u * NT;
+        k[u] = -1;
+        xa[u].x = xa[u].y = xb[u].x = xb[u].y = T(0);
+        if (e < tot) {
+          const int b = e / (G * cb), rem = e - b * (G * cb);
+          const int g = rem / cb, c = rem - g * cb;
+          const int ra = row0 + 2 * g;
+          const int kk = b * cb + c;
+          if (kk < W) {
+            const size_t o = (size_t)b * N * cb + (size_t)ra * cb + c;
+            if (ra < N) xa[u] = S[o];
+            if (ra + 1 < N) xb[u] = S[o + cb];
+            k[u] = (g << 16) | kk;
+          }
+        }
       }
-    }
 #pragma unroll
-    for (int q = 0; q < MAXV; ++q) {
-      const int e = threadIdx.x + q * TR_THREADS;
-      if (e < G * N) {
-        const int k = e % N;
-        T2 xa = ta[q], xb = tb[q];
-        if (k >= H) { xa = cconj(xa); xb = cconj(xb); }
-        if (k == 0 || (even && k == N / 2)) { xa.y = T(0); xb.y = T(0); }
-        T2 z; z.x = xa.x - xb.y; z.y = xa.y + xb.x;   // Xa + i Xb
-        sm[e] = z;
+      for (int u = 0; u < BATCH; ++u) {
+        if (k[u] < 0) continue;
+        const int kk = k[u] & 0xffff;
+        T2* tb = sm + (k[u] >> 16) * TSg;
+        if (kk == 0 || (even && kk == N / 2)) {
+          T2 z; z.x = xa[u].x; z.y = xb[u].x;        // imaginary parts of DC / Nyquist are rounding
+          tb[fpad(kk)] = z;
+        } else {
+          T2 z; z.x = xa[u].x - xb[u].y; z.y = xa[u].y + xb[u].x;     // Xa + i Xb
+          tb[fpad(kk)] = z;
+          T2 zr; zr.x = xa[u].x + xb[u].y; zr.y = xb[u].x - xa[u].y;  // conj(Xa) + i conj(Xb)
+          tb[fpad(N - kk)] = zr;
+        }
       }
     }
     __syncthreads();
   }
-  fft_smem<T2, true>(sm, G, pd);
+  fft_smem<T2, true>(G, pd);
   T* dst = static_cast<T*>(pd.buf[dst_slot]);
-  for (int e = threadIdx.x; e < G * N; e += TR_THREADS) {
+  for (int e = threadIdx.x; e < G * N; e += NT) {
     const int g = e / N, x = e - g * N;
-    const int ra = 2 * (pair0 + g), rb = ra + 1;
-    const T2 v = dct ? sm[g * N + dct_pos(x, N)] : sm[e];
+    const int ra = row0 + 2 * g, rb = ra + 1;
+    const T2 v = sm[g * TSg + fpad(dct ? dct_pos(x, N) : x)];
     if (ra < N) dst[(size_t)ra * N + x] = v.x;
     if (rb < N) dst[(size_t)rb * N + x] = v.y;
   }
@@ -513,31 +628,33 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
 constexpr int NS_CAND = 16;
 constexpr double NS_CAND_STEP = 1.0;
 
-// element e (< SPEC_THREADS * SPEC_PER_THREAD) of block `blk`: weighted power
-// and |lambda|^2 in T precision; false past the end of the spectrum
+// element e (< SPEC_THREADS * SPEC_PER_THREAD) of spectrum block `blk`,
+// enumerated along the column-blocked layout (contiguous reads): weighted
+// power and |lambda|^2 in T precision; false past the end or on padding
 template <typename T>
 __device__ __forceinline__ bool spec_elem(const Prob& pd, int blk, int e, T& pw, T& sg) {
   using T2 = typename Vec2<T>::type;
-  const int N = pd.n;
+  const int N = pd.n, cb = pd.cb;
   const bool dct = (pd.transform == TR_DCT);
   const int W = dct ? N : pd.half;
-  // whole rows per block, never more elements than the block's threads cover
-  const int rows_per = max(1, (SPEC_THREADS * SPEC_PER_THREAD) / W);
-  const int k1 = blk * rows_per + e / W;
-  const int k2 = e - (e / W) * W;
-  if (k1 >= N || e >= rows_per * W) return false;
-  const size_t idx = (size_t)k1 * W + k2;
+  const size_t L = (size_t)blk * (SPEC_THREADS * SPEC_PER_THREAD) + e;
+  const size_t blksz = (size_t)N * cb;
+  const int b = (int)(L / blksz);
+  const int rem = (int)(L - (size_t)b * blksz);
+  const int k1 = rem / cb, c = rem - k1 * cb;
+  const int k2 = b * cb + c;
+  if (k2 >= W) return false;
   if (dct) {
     // unnormalised DCT-II: |orthonormal coefficient|^2 = v^2 s_k1^2 s_k2^2
     // with s_0^2 = 1/N and s_k^2 = 2/N; the common 1/N^2 cancels
-    const T v = static_cast<const T*>(pd.buf[SL_S])[idx];
+    const T v = static_cast<const T*>(pd.buf[SL_S])[L];
     pw = T((k1 == 0 ? 1 : 2) * (k2 == 0 ? 1 : 2)) * v * v;
   } else {
-    const T2 v = static_cast<const T2*>(pd.buf[SL_S])[idx];
+    const T2 v = static_cast<const T2*>(pd.buf[SL_S])[L];
     const T m = (k2 == 0 || ((N & 1) == 0 && k2 == N / 2)) ? T(1) : T(2);
     pw = m * (v.x * v.x + v.y * v.y);
   }
-  sg = static_cast<const T*>(pd.w)[idx];
+  sg = static_cast<const T*>(pd.w)[L];
   return true;
 }
 
@@ -683,43 +800,48 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
 // e^{-2 pi i k2 dx/n} (DFT) or sum_dx h cos(pi k2 dx/n) (DCT) comes from
 // the host; here lambda(k1,k2) = sum_dy e^{-2 pi i k1 dy / n} Q(dy, k2) or
 // sum_dy cos(pi k1 dy/n) Q(dy,k2), with tab the exact table of
-// e^{-2 pi i m/n} (DFT, m < n) or cos(pi m/n) (DCT, m < 2n).
-__global__ void k_spectrum(int transform, int n, int p, int half, const double* __restrict__ q,
-                           const double* __restrict__ tab, double* __restrict__ sigma,
+// e^{-2 pi i m/n} (DFT, m < n) or cos(pi m/n) (DCT, m < 2n).  lambda and
+// |lambda|^2 are rounded once to T and stored column-blocked; padding
+// columns of the last block get lambda = 0, |lambda|^2 = 1.
+__global__ void k_spectrum(int transform, int n, int p, int half, int cb,
+                           const double* __restrict__ q, const double* __restrict__ tab,
                            void* lam, void* sigT, int is_double) {
   const int c = (p - 1) / 2;
   const int W = (transform == TR_DCT) ? n : half;
-  const size_t tot = (size_t)n * W;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int k1 = (int)(i / W), k2 = (int)(i - (size_t)k1 * W);
-    if (transform == TR_DCT) {
-      double s = 0.0;
-      for (int a = 0; a < p; ++a) {
-        int m = (k1 * (a - c)) % (2 * n); if (m < 0) m += 2 * n;
-        s += tab[m] * q[(size_t)a * n + k2];
-      }
-      sigma[i] = s * s;
-      if (is_double) { static_cast<double*>(lam)[i] = s; static_cast<double*>(sigT)[i] = s * s; }
-      else { static_cast<float*>(lam)[i] = (float)s; static_cast<float*>(sigT)[i] = (float)(s * s); }
-    } else {
-      double re = 0.0, im = 0.0;
-      for (int a = 0; a < p; ++a) {
-        int m = (k1 * (a - c)) % n; if (m < 0) m += n;
-        const double er = tab[2 * m], ei = tab[2 * m + 1];
-        const double qr = q[2 * ((size_t)a * half + k2)], qi = q[2 * ((size_t)a * half + k2) + 1];
-        re += er * qr - ei * qi;
-        im += er * qi + ei * qr;
-      }
-      sigma[i] = re * re + im * im;
-      if (is_double) {
-        static_cast<double2*>(lam)[i] = make_double2(re, im);
-        static_cast<double*>(sigT)[i] = re * re + im * im;
+  const int nb = (W + cb - 1) / cb;
+  const size_t tot = (size_t)nb * n * cb;
+  for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < tot;
+       L += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(L / ((size_t)n * cb));
+    const int rem = (int)(L - (size_t)b * n * cb);
+    const int k1 = rem / cb, k2 = b * cb + (rem - k1 * cb);
+    double re = 0.0, im = 0.0;
+    if (k2 < W) {
+      if (transform == TR_DCT) {
+        for (int a = 0; a < p; ++a) {
+          int m = (k1 * (a - c)) % (2 * n); if (m < 0) m += 2 * n;
+          re += tab[m] * q[(size_t)a * n + k2];
+        }
       } else {
-        static_cast<float2*>(lam)[i] = make_float2((float)re, (float)im);
-        static_cast<float*>(sigT)[i] = (float)(re * re + im * im);
+        for (int a = 0; a < p; ++a) {
+          int m = (k1 * (a - c)) % n; if (m < 0) m += n;
+          const double er = tab[2 * m], ei = tab[2 * m + 1];
+          const double qr = q[2 * ((size_t)a * half + k2)], qi = q[2 * ((size_t)a * half + k2) + 1];
+          re += er * qr - ei * qi;
+          im += er * qi + ei * qr;
+        }
       }
     }
+    const double s2 = (k2 < W) ? re * re + im * im : 1.0;
+    if (transform == TR_DCT) {
+      if (is_double) static_cast<double*>(lam)[L] = re;
+      else static_cast<float*>(lam)[L] = (float)re;
+    } else {
+      if (is_double) static_cast<double2*>(lam)[L] = make_double2(re, im);
+      else static_cast<float2*>(lam)[L] = make_float2((float)re, (float)im);
+    }
+    if (is_double) static_cast<double*>(sigT)[L] = s2;
+    else static_cast<float*>(sigT)[L] = (float)s2;
   }
 }
 
@@ -727,18 +849,18 @@ __global__ void k_spectrum(int transform, int n, int p, int half, const double* 
 template <typename T>
 void launch_rows_fwd(const Prob* probs, State* states, const int2* items, int nitems, int src,
                      int pcg, size_t smem, cudaStream_t s) {
-  if (nitems > 0) k_rows_fwd<T><<<nitems, TR_THREADS, smem, s>>>(probs, states, items, src, pcg);
+  if (nitems > 0) k_rows_fwd<T><<<nitems, tr_nt(sizeof(T)), smem, s>>>(probs, states, items, src, pcg);
 }
 template <typename T>
 void launch_cols(const Prob* probs, State* states, const int2* items, int nitems, int mode,
                  int pcg, double op_alpha, int op_kind, size_t smem, cudaStream_t s) {
   if (nitems > 0)
-    k_cols<T><<<nitems, TR_THREADS, smem, s>>>(probs, states, items, mode, pcg, op_alpha, op_kind);
+    k_cols<T><<<nitems, tr_nt(sizeof(T)), smem, s>>>(probs, states, items, mode, pcg, op_alpha, op_kind);
 }
 template <typename T>
 void launch_rows_inv(const Prob* probs, State* states, const int2* items, int nitems, int dst,
                      int pcg, size_t smem, cudaStream_t s) {
-  if (nitems > 0) k_rows_inv<T><<<nitems, TR_THREADS, smem, s>>>(probs, states, items, dst, pcg);
+  if (nitems > 0) k_rows_inv<T><<<nitems, tr_nt(sizeof(T)), smem, s>>>(probs, states, items, dst, pcg);
 }
 template <typename T>
 void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, int cand,
@@ -747,13 +869,14 @@ void launch_spec(const Prob* probs, State* states, const int2* items, int nitems
   if (cand) k_spec_cand<T><<<nitems, SPEC_THREADS, 0, s>>>(probs, states, items);
   else k_spec<T><<<nitems, SPEC_THREADS, 0, s>>>(probs, states, items);
 }
-void launch_spectrum_setup(const Prob*, int, int transform, int n, int p, int half,
-                           const double* q_dev, const double* tab_dev, double* sigma,
-                           void* lam, void* sigT, int is_double, cudaStream_t s) {
-  const size_t tot = (size_t)n * (transform == TR_DCT ? n : half);
+void launch_spectrum_setup(int transform, int n, int p, int half, int cb, const double* q_dev,
+                           const double* tab_dev, void* lam, void* sigT, int is_double,
+                           cudaStream_t s) {
+  const int W = transform == TR_DCT ? n : half;
+  const size_t tot = (size_t)((W + cb - 1) / cb) * n * cb;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_spectrum<<<blocks, 256, 0, s>>>(transform, n, p, half, q_dev, tab_dev, sigma, lam, sigT, is_double);
+  k_spectrum<<<blocks, 256, 0, s>>>(transform, n, p, half, cb, q_dev, tab_dev, lam, sigT, is_double);
 }
 template <typename T>
 cudaError_t fft_set_smem(size_t bytes) {

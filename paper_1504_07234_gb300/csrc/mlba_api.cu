@@ -79,13 +79,21 @@ size_t tsize(int dtype) { return dtype == MLBA_F64 ? 8 : 4; }
 size_t zsize(int zs) { return zs == MLBA_F64 ? 8 : (zs == MLBA_BF16 ? 2 : 4); }
 size_t al(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
-bool fft_plan(int n, int* radix, int* nstage) {
-  int m = n, s = 0;
-  while (m % 4 == 0 && s < MAX_STAGES) { radix[s++] = 4; m /= 4; }
-  while (m % 2 == 0 && s < MAX_STAGES) { radix[s++] = 2; m /= 2; }
-  while (m % 3 == 0 && s < MAX_STAGES) { radix[s++] = 3; m /= 3; }
-  while (m % 5 == 0 && s < MAX_STAGES) { radix[s++] = 5; m /= 5; }
-  *nstage = s;
+// elements of the column-blocked spectrum (padding of the last block included)
+int fft_pad(int i) { return i + (i >> 4); }   // shared-memory slot of element i (k_fft.cu)
+size_t spec_elems(const Prob& pd) { return (size_t)pd.nblk_cols * pd.n * pd.cb; }
+
+// Radix passes of the length-n FFT: as many radix-16 passes as divide n, then
+// at most one of 8, 4 or 2 for the rest of the power of two, then 3s and 5s.
+bool fft_plan(Prob& pd) {
+  int m = pd.n, s = 0;
+  pd.nr16 = pd.r2 = pd.nr3 = pd.nr5 = 0;
+  while (m % 16 == 0 && s < MAX_STAGES) { pd.radix[s++] = 16; m /= 16; ++pd.nr16; }
+  for (int r : {8, 4, 2})
+    if (m % r == 0 && s < MAX_STAGES) { pd.radix[s++] = r; m /= r; pd.r2 = r; break; }
+  while (m % 3 == 0 && s < MAX_STAGES) { pd.radix[s++] = 3; m /= 3; ++pd.nr3; }
+  while (m % 5 == 0 && s < MAX_STAGES) { pd.radix[s++] = 5; m /= 5; ++pd.nr5; }
+  pd.nstage = s;
   return m == 1;
 }
 
@@ -291,9 +299,9 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
     h.psf_pre = h.psf;
   }
   if (pd.transform != TR_NONE) {
-    if (!fft_plan(n, pd.radix, &pd.nstage)) return MLBA_E_UNSUPPORTED;
+    if (!fft_plan(pd)) return MLBA_E_UNSUPPORTED;
     // one transform must fit the per-CTA value budget of the smem FFT
-    if (n > (o.dtype == MLBA_F64 ? TR_MAXV_F64 : TR_MAXV) * TR_THREADS) return MLBA_E_UNSUPPORTED;
+    if (n > TR_CAP) return MLBA_E_UNSUPPORTED;
   }
   // taps
   for (int a = 0; a < p; ++a)
@@ -309,22 +317,24 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   pd.nblk_blur = ((n + 31) / 32) * ((n + 31) / 32);
   pd.nblk_corr = ((pd.ne + 31) / 32) * ((pd.ne + 31) / 32);
   pd.nblk_frame = ((pd.nf + TS - 1) / TS) * ((pd.nf + TS - 1) / TS);
-  const int cap = (o.dtype == MLBA_F64 ? TR_MAXV_F64 : TR_MAXV) * TR_THREADS / n;   // transforms per CTA
+  const int cap = TR_CAP / n;                          // transforms per CTA
   const int pairs = (n + 1) / 2;
-  pd.row_g = std::max(1, std::min(cap, pairs));
-  pd.nblk_rows = (pairs + pd.row_g - 1) / pd.row_g;
-  if (pd.transform == TR_DCT) {
-    pd.col_g = std::max(1, std::min(cap, pairs));
-    pd.nblk_cols = (n + 2 * pd.col_g - 1) / (2 * pd.col_g);
-  } else {
-    pd.col_g = std::max(1, std::min(cap, pd.half));
-    pd.nblk_cols = (pd.half + pd.col_g - 1) / pd.col_g;
+  {
+    const int nb = (pairs + cap - 1) / cap;            // row CTAs, then pairs spread evenly
+    pd.row_g = std::max(1, (pairs + nb - 1) / nb);
+    pd.nblk_rows = (pairs + pd.row_g - 1) / pd.row_g;
   }
   {
-    const int Wsp = (pd.transform == TR_DCT) ? n : pd.half;
-    const int rows_per = std::max(1, (SPEC_THREADS * SPEC_PER_THREAD) / Wsp);
-    pd.nblk_spec = (n + rows_per - 1) / rows_per;
+    // column blocks: as few as the cap allows, then as even as possible
+    const bool dct = pd.transform == TR_DCT;
+    const int units = dct ? pairs : pd.half;           // complex columns to transform
+    const int nb = (units + cap - 1) / cap;
+    pd.col_g = std::max(1, (units + nb - 1) / nb);
+    pd.cb = dct ? 2 * pd.col_g : pd.col_g;
+    pd.nblk_cols = ((dct ? n : pd.half) + pd.cb - 1) / pd.cb;
   }
+  pd.nblk_spec = (int)((spec_elems(pd) + SPEC_THREADS * SPEC_PER_THREAD - 1) /
+                       (SPEC_THREADS * SPEC_PER_THREAD));
   pd.nblk_vec = (int)(((size_t)n * n + VEC_THREADS * VEC_PER_THREAD - 1) / (VEC_THREADS * VEC_PER_THREAD));
   return MLBA_OK;
 }
@@ -372,7 +382,7 @@ int build_spectrum(mlba_batch* B, HostProb& h) {
   CK(cudaMalloc(&dtab, tab.size() * sizeof(double)));
   CK(cudaMemcpyAsync(dq, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, B->stream));
   CK(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, B->stream));
-  launch_spectrum_setup(nullptr, 0, pd.transform, n, p, half, dq, dtab, pd.sigma, pd.lam, pd.w,
+  launch_spectrum_setup(pd.transform, n, p, half, pd.cb, dq, dtab, pd.lam, pd.w,
                         B->dtype == MLBA_F64 ? 1 : 0, B->stream);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(B->stream));
@@ -414,8 +424,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     const size_t n2 = (size_t)pd.n * pd.n, nf2 = (size_t)pd.nf * pd.nf, ne2 = (size_t)pd.ne * pd.ne;
     const bool spec = pd.transform != TR_NONE;
     const bool kry = pd.precond == P_KRYLOV;
-    const size_t W = pd.transform == TR_DCT ? pd.n : pd.half;
-    const size_t nspec = (size_t)pd.n * W;
+    const size_t nspec = spec ? spec_elems(pd) : 1;
     const size_t aux = std::max(nf2, ne2);
     std::vector<size_t> sz = {
         n2 * ts,                               // G
@@ -424,15 +433,14 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         n2 * ts,                               // T
         ne2 * ts,                              // V
         n2 * ts,                               // U
-        spec ? (size_t)pd.n * (pd.n + 2) * ts : ts,   // S
+        nspec * ts * (pd.transform == TR_DCT ? 1 : 2),   // S
         kry ? n2 * ts : ts, kry ? n2 * ts : ts, kry ? n2 * ts : ts, kry ? n2 * ts : ts,
         kry ? n2 * ts : ts,                    // PCG vectors
         aux * ts, aux * ts,                    // AUX0, AUX1
         (size_t)pd.nbands * nf2 * zs,          // z0
         (size_t)pd.nbands * nf2 * zs,          // z1
-        spec ? nspec * 8 : 8,                  // sigma
-        spec ? nspec * ts * (pd.transform == TR_DCT ? 1 : 2) : ts,   // lam
-        spec ? nspec * ts : ts,                // sigma in T precision
+        nspec * ts * (pd.transform == TR_DCT ? 1 : 2),   // lam
+        nspec * ts,                            // |lambda|^2 in T precision
         spec ? (size_t)pd.n * 2 * ts : ts,     // tw
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
         (size_t)pd.ntaps * 4, (size_t)pd.ntaps * 4, (size_t)pd.ntaps * ts,   // taps
@@ -455,7 +463,6 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     int k = NSLOT;
     pd.z[0] = base + of[k++];
     pd.z[1] = base + of[k++];
-    pd.sigma = reinterpret_cast<double*>(base + of[k++]);
     pd.lam = base + of[k++];
     pd.w = base + of[k++];
     pd.tw = base + of[k++];
@@ -541,7 +548,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     const size_t st_b = (((nw + 1) & ~(size_t)1) + R * R + (pd.sep ? R * 32 : 0)) * ts + (pd.sep ? 0 : pd.ntaps * 4);
     smem_st = std::max(smem_st, st_b);
     if (specp) {
-      const size_t fb = (size_t)std::max(pd.row_g, pd.col_g) * pd.n * 2 * ts;
+      const size_t fb = (size_t)std::max(pd.row_g, pd.col_g) * (fft_pad(pd.n) + 1) * 2 * ts;
       smem_fft = std::max(smem_fft, fb);
     }
   }
@@ -1033,12 +1040,20 @@ int mlba_op_spectrum(mlba_ctx* c, double* out, int* rows, int* cols, int* is_com
   if (pd.transform == TR_NONE) return MLBA_E_INVAL;
   const bool dct = pd.transform == TR_DCT;
   const size_t W = dct ? pd.n : pd.half;
-  const size_t cnt = (size_t)pd.n * W * (dct ? 1 : 2);
+  const int comps = dct ? 1 : 2;
+  const size_t cnt = spec_elems(pd) * comps;
   std::vector<unsigned char> tmp(cnt * tsize(B->dtype));
   CK(cudaMemcpy(tmp.data(), pd.lam, tmp.size(), cudaMemcpyDeviceToHost));
-  for (size_t i = 0; i < cnt; ++i)
-    out[i] = B->dtype == MLBA_F64 ? reinterpret_cast<double*>(tmp.data())[i]
-                                  : (double)reinterpret_cast<float*>(tmp.data())[i];
+  // undo the column blocking: (k1, k2) lives at (k2 / cb) n cb + k1 cb + k2 % cb
+  const size_t cb = pd.cb;
+  for (size_t k1 = 0; k1 < (size_t)pd.n; ++k1)
+    for (size_t k2 = 0; k2 < W; ++k2)
+      for (int q = 0; q < comps; ++q) {
+        const size_t src = ((k2 / cb) * pd.n * cb + k1 * cb + k2 % cb) * comps + q;
+        out[(k1 * W + k2) * comps + q] = B->dtype == MLBA_F64
+            ? reinterpret_cast<double*>(tmp.data())[src]
+            : (double)reinterpret_cast<float*>(tmp.data())[src];
+      }
   if (rows) *rows = pd.n;
   if (cols) *cols = (int)W;
   if (is_complex) *is_complex = dct ? 0 : 1;

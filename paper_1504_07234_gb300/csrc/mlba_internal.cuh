@@ -26,7 +26,7 @@ enum Slot {
   SL_T,       // preconditioned residual t (n x n)
   SL_V,       // full correlation of t on the extended (n+p-1)^2 domain
   SL_U,       // BC-folded A^T t (n x n); PCG work
-  SL_S,       // transform work array (n x (n+2) reals)
+  SL_S,       // transform work array (column-blocked spectrum, see Prob::cb)
   SL_PX, SL_PRES, SL_PP, SL_PQ, SL_PZ,  // PCG vectors (n x n)
   SL_AUX0, SL_AUX1,                     // operator entry-point scratch (Nf x Nf)
   NSLOT
@@ -46,15 +46,19 @@ struct Prob {
   int max_iter, stop, pcg_max;
   int nstage;        // FFT plan of length n
   int radix[MAX_STAGES];
+  int nr16, r2, nr3, nr5;   // the same plan: radix-16 passes, one 8/4/2 pass, 3s, 5s
   // per-list block counts (reductions need them)
   int nblk_blur, nblk_corr, nblk_frame, nblk_rows, nblk_cols, nblk_spec, nblk_vec;
   int row_g, col_g;  // transforms per CTA in the row / column passes
+  int cb;            // spectrum column block: col_g complex columns (DFT) or
+                     // 2 col_g real columns (DCT); block j holds columns
+                     // [j cb, (j+1) cb) as n rows of cb contiguous elements;
+                     // there are nblk_cols blocks, the last one may be padded
   double mu, alpha, gamma, delta, q, rho, tau, pcg_tol;
   void* buf[NSLOT];
   void* z[2];        // ping-pong Bregman variable
-  void* w;           // |lambda|^2 in T precision (per-element weights and alpha_n terms)
-  void* lam;         // spectrum of C (real for DCT, complex half for DFT), T precision
-  double* sigma;     // |lambda|^2 in FP64
+  void* w;           // |lambda|^2 in T precision, column-blocked like S
+  void* lam;         // spectrum of C (real for DCT, complex half for DFT), T, blocked
   void* tw;          // exp(-2 pi i k/n), k < n   (T2)
   void* dtw;         // exp(-i pi k/(2n)), k < n  (T2)
   int* tap_dy; int* tap_dx; void* tap_w;   // nonzero taps (offsets from centre)

@@ -34,9 +34,7 @@ enum { W_INV = 0, W_TIKH = 1 };
 constexpr int STENCIL_THREADS = 256;
 constexpr int VEC_THREADS = 256;
 constexpr int VEC_PER_THREAD = 8;
-constexpr int TR_THREADS = 512;
-constexpr int TR_MAXV = 16;           // complex values per thread in the smem FFT (FP32)
-constexpr int TR_MAXV_F64 = 8;        // the same for FP64
+constexpr int TR_CAP = 4096;          // complex values held by one transform CTA
 constexpr int FRAME_THREADS = 256;
 constexpr int FRAME_TILE = 32;
 constexpr int SPEC_THREADS = 512;
@@ -60,9 +58,9 @@ void launch_rows_inv(const Prob* probs, State* states, const int2* items, int ni
 template <typename T>
 void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, int cand,
                  cudaStream_t s);
-void launch_spectrum_setup(const Prob* probs, int pi, int transform, int n, int p, int half,
-                           const double* q_dev, const double* tab_dev, double* sigma,
-                           void* lam, void* sigT, int is_double, cudaStream_t s);
+void launch_spectrum_setup(int transform, int n, int p, int half, int cb, const double* q_dev,
+                           const double* tab_dev, void* lam, void* sigT, int is_double,
+                           cudaStream_t s);
 template <typename T, typename TZ>
 void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, int u_slot,
                   int f_slot, const void* zin, void* zout, double op_mu, size_t smem, int levels,
