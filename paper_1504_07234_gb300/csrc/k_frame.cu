@@ -626,16 +626,292 @@ k_frame2(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp row-sweep variant for L <= 2 (the measured workloads).
+//
+// A CTA owns an F3_TX x (32 F3_NWR) tile of f and of every z band; warp w
+// owns the 32-row segment w of it.  In each level a lane owns one column of
+// the band region (coefficients at columns tx0 - X .. tx0 - X + 31) and the
+// warp sweeps down the rows:
+//   analysis   h_j(y, x) = sum_t b_j[t] c(y, x + (t-1)D)     (shared memory)
+//              a_ij(y, x) = sum_s b_i[s] h_j(y + (s-1)D, x)  (register ring)
+//   update     z' = z + a, x_ij = S_mu(z')                   (z in registers,
+//              loaded PF rows ahead straight from global memory)
+//   synthesis  P_j(y + (s-1)D) += b_i[s] x_ij                (register ring)
+//              out(y, x) = A(x + D) + B(x) + C(x - D)         (warp shuffles)
+//              with A, B, C = sum_j b_j[0], b_j[1], b_j[2] P_j
+// Every lane computes a coefficient column, but only lanes whose +-D
+// neighbours are in the warp produce output: level 2 (D = 2) lanes 2..29,
+// level 1 lanes 1..26.  Neighbouring warps and tiles recompute the
+// overlapping coefficients (from the same z_in) and only the owner writes
+// z_out.  Shared memory carries only the inputs (u, c_1 = (b0 x b0) u) and
+// the level-2 part of f, so there are no shared-memory atomics; the only
+// CTA-wide barriers are the two after the u and c_1 tiles.
+constexpr int F3_TX = 26;      // tile columns: level-2 output lanes 3..28 after the +-1 low-pass
+constexpr int F3_SEG = 32;     // rows per warp
+constexpr int F3_NWR = 2;      // warps (row segments) per CTA
+constexpr int F3_TY = F3_SEG * F3_NWR;
+constexpr int F3_PF = 2;       // z prefetch distance (rows)
+
+template <int L>
+struct F3 {
+  static constexpr int C0 = (L == 2) ? 6 : 2;         // radius of the u tile
+  static constexpr int UW = F3_TX + 2 * C0, UH = F3_TY + 2 * C0;
+  static constexpr int C1W = F3_TX + 10, C1H = F3_TY + 10;   // c_1 radius 5 (L = 2)
+  static constexpr size_t elems = (size_t)UW * UH + (L == 2 ? (size_t)C1W * C1H + (size_t)F3_TX * F3_TY : 0);
+};
+template <typename T, int L>
+__host__ __device__ constexpr size_t frame3_smem_bytes() { return F3<L>::elems * sizeof(T); }
+
+// z offset inside a band plane of the (reflected) row; sets *par to the
+// row's mirroring parity
+template <bool INTERIOR>
+__device__ __forceinline__ int f3_zrow(int y, int nf, bool* par) {
+  if (INTERIOR) { *par = false; return y * nf; }
+  int o;
+  const int r = refl_half(y, nf, &o);
+  *par = o != 0;
+  return r * nf;
+}
+
+template <typename T, typename TZ, int LEV, int L, bool INTERIOR>
+__device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ cin, int cpitch,
+                                         int cy0, int cx0, const TZ* __restrict__ zin,
+                                         TZ* __restrict__ zout, int ty0, int tx0, int seg_lo,
+                                         int seg_hi, T mu, T* __restrict__ f2s,
+                                         T* __restrict__ fout) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int D = 1 << (LEV - 1);
+  constexpr bool TOP = (LEV == L);
+  constexpr int XO = (LEV == 2) ? 3 : 1;                 // first coefficient column tx0 - XO
+  constexpr int NL = (LEV == 2) ? 32 : F3_TX + 2;        // lanes with a coefficient column
+  constexpr int K0 = TOP ? 0 : 1;                        // band k = 3 j + i; (0,0) only at level L
+  constexpr int NB = 9 - K0;
+  const T s2q = T(0.35355339059327376220);               // sqrt(2) / 4
+  const int lane = threadIdx.x & 31;
+  const int x = tx0 - XO + lane;
+  const bool act = lane < NL;
+  const int nf = pd.nf;
+  const size_t plane = (size_t)nf * nf;
+  // rows: outputs [yo0, yo1), coefficients [yc0, yc1)
+  const int yo0 = (LEV == 2) ? seg_lo - 1 : seg_lo;
+  const int yo1 = (LEV == 2) ? seg_hi + 1 : seg_hi;
+  const int yc0 = yo0 - D, yc1 = yo1 + D;
+  // column part of the z offsets and its mirroring parity
+  int zc = x;
+  bool pcx = false;
+  if (!INTERIOR) { int o; zc = refl_half(x, nf, &o); pcx = o != 0; }
+  const bool own_c = act && x >= tx0 && x < tx0 + F3_TX && x < nf;
+  const T* ccol = cin + (act ? x - cx0 : D);   // idle lanes read a valid column
+  // band planes in k order
+  size_t boff[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int k = K0 + b;
+    boff[b] = (size_t)f2_band(LEV, L, k % 3, k / 3) * plane;
+  }
+  // h ring: rows y - D .. y + D of the current coefficient row y
+  T hr[2 * D + 1][3];
+  auto hrow = [&](int y, T (&h)[3]) {
+    const T* r = ccol + (size_t)(y - cy0) * cpitch;
+    const T cm = r[-D], c0 = r[0], cp = r[D];
+    const T sp = cm + cp;
+    h[0] = T(0.25) * sp + T(0.5) * c0;
+    h[1] = s2q * (cm - cp);
+    h[2] = T(0.5) * c0 - T(0.25) * sp;
+  };
+#pragma unroll
+  for (int k = 0; k < 2 * D; ++k) hrow(yc0 - D + k, hr[k]);
+  // z queue: rows y .. y + PF - 1
+  TZ zq[F3_PF][NB];
+  auto zload = [&](int y, TZ (&q)[NB]) {
+    bool par;
+    const int ro = f3_zrow<INTERIOR>(y, nf, &par);
+    const TZ* zp = zin + (ro + zc);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) q[b] = act ? zp[boff[b]] : TZ(0.0f);
+  };
+#pragma unroll
+  for (int k = 0; k < F3_PF; ++k) zload(yc0 + k, zq[k]);
+  // synthesis ring: rows y - D .. y + D
+  T pr[2 * D + 1][3];
+#pragma unroll
+  for (int k = 0; k <= 2 * D; ++k) pr[k][0] = pr[k][1] = pr[k][2] = T(0);
+  // level-2 low-pass ring of the horizontally filtered s_1 rows r-2, r-1, r
+  T gq[3] = {T(0), T(0), T(0)};
+#pragma unroll 1
+  for (int y = yc0; y < yc1; ++y) {
+    hrow(y + D, hr[2 * D]);
+    bool pry;
+    const int zro = f3_zrow<INTERIOR>(y, nf, &pry);
+    const bool own = own_c && y >= seg_lo && y < seg_hi && y < nf;
+    TZ* zw = zout + (zro + zc);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int k = K0 + b, i = k % 3, j = k / 3;
+      const T bi0 = (i == 0) ? T(0.25) : (i == 1 ? s2q : T(-0.25));
+      const T bi1 = (i == 1) ? T(0) : T(0.5);
+      const T bi2 = (i == 0) ? T(0.25) : (i == 1 ? -s2q : T(-0.25));
+      T a = bi0 * hr[0][j] + bi2 * hr[2 * D][j];
+      if (i != 1) a += bi1 * hr[D][j];
+      T zv = T(ld_z(&zq[0][b]));
+      if (!INTERIOR) {
+        // antisymmetric (b1) bands change sign under an odd number of mirrorings
+        if (((i == 1) && pry) != ((j == 1) && pcx)) zv = -zv;
+      }
+      const T zn = zv + a;
+      if (own) st_z(zw + boff[b], zn);
+      const T xv = zn - fmin(fmax(zn, -mu), mu);     // S_mu
+      pr[0][j] += bi0 * xv;
+      if (i != 1) pr[D][j] += bi1 * xv;
+      pr[2 * D][j] += bi2 * xv;
+    }
+    // advance the z queue
+#pragma unroll
+    for (int k = 0; k + 1 < F3_PF; ++k)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) zq[k][b] = zq[k + 1][b];
+    if (y + F3_PF < yc1) zload(y + F3_PF, zq[F3_PF - 1]);
+    // row y - D has all its contributions: horizontal synthesis
+    const int r = y - D;
+    if (r >= yo0) {
+      const T A = T(0.25) * pr[0][0] + s2q * pr[0][1] - T(0.25) * pr[0][2];
+      const T B = T(0.5) * (pr[0][0] + pr[0][2]);
+      const T C = T(0.25) * pr[0][0] - s2q * pr[0][1] - T(0.25) * pr[0][2];
+      const T out = B + __shfl_down_sync(FULL, A, D) + __shfl_up_sync(FULL, C, D);
+      if (LEV == 2 && L == 2) {
+        // s_1 row r (lanes 2..29) -> (b0 x b0)^T s_1 row r - 1 (lanes 3..28)
+        const T g = T(0.5) * out +
+                    T(0.25) * (__shfl_up_sync(FULL, out, 1) + __shfl_down_sync(FULL, out, 1));
+        gq[0] = gq[1]; gq[1] = gq[2]; gq[2] = g;
+        if (r - 1 >= seg_lo && lane >= 3 && lane < 3 + F3_TX)
+          f2s[(r - 1 - ty0) * F3_TX + (lane - 3)] = T(0.25) * (gq[0] + gq[2]) + T(0.5) * gq[1];
+      } else {
+        // level 1: f row r (lanes 1..26) = out + level-2 part
+        if (lane >= 1 && lane < 1 + F3_TX) {
+          T fv = out;
+          if (L == 2) fv += f2s[(r - ty0) * F3_TX + (lane - 1)];
+          if (r < nf && x < nf) fout[(size_t)r * nf + x] = fv;
+        }
+      }
+    }
+    // shift the rings
+#pragma unroll
+    for (int k = 0; k < 2 * D; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) { hr[k][j] = hr[k + 1][j]; pr[k][j] = pr[k + 1][j]; }
+    pr[2 * D][0] = pr[2 * D][1] = pr[2 * D][2] = T(0);
+  }
+}
+
+template <typename T, typename TZ, int L>
+__global__ void __launch_bounds__(32 * F3_NWR)
+k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+         int u_slot, int f_slot, const void* zin_op, void* zout_op, double op_mu) {
+  using Gm = F3<L>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  const State& st = states[item.x];
+  if (st.stopped) return;
+  const int nf = pd.nf;
+  const int tilesX = (nf + F3_TX - 1) / F3_TX;
+  const int ty0 = (item.y / tilesX) * F3_TY, tx0 = (item.y % tilesX) * F3_TX;
+  const T mu = T(zin_op ? op_mu : pd.mu);
+  const TZ* zin;
+  TZ* zout;
+  if (zin_op) {
+    zin = static_cast<const TZ*>(zin_op);
+    zout = static_cast<TZ*>(zout_op);
+  } else {
+    zin = static_cast<const TZ*>(pd.z[(st.iter - 1) & 1]);
+    zout = static_cast<TZ*>(pd.z[st.iter & 1]);
+  }
+  T* su = reinterpret_cast<T*>(smraw);            // u on rows ty0 - C0.., cols tx0 - C0..
+  T* sc1 = su + Gm::UW * Gm::UH;                  // c_1 on rows ty0 - 5.., cols tx0 - 5..
+  T* sf2 = sc1 + (L == 2 ? Gm::C1W * Gm::C1H : 0);   // level-2 part of f on the tile
+  constexpr int C0 = Gm::C0;
+  {
+    int mode;
+    const T* src;
+    if (u_slot >= 0) { src = static_cast<const T*>(pd.buf[u_slot]); mode = 1; }
+    else if (!pd.use_adj) { src = static_cast<const T*>(pd.buf[SL_T]); mode = 1; }
+    else if (pd.bc == BC_RECT) { src = static_cast<const T*>(pd.buf[SL_V]); mode = 1; }
+    else { src = static_cast<const T*>(pd.buf[SL_V]); mode = 0; }
+    const bool interior = ty0 - C0 >= 0 && tx0 - C0 >= 0 && ty0 + F3_TY + C0 <= nf &&
+                          tx0 + F3_TX + C0 <= nf;
+    for (int idx = threadIdx.x; idx < Gm::UW * Gm::UH; idx += 32 * F3_NWR) {
+      const int ry = idx / Gm::UW, rx = idx - ry * Gm::UW;
+      const int gy = ty0 - C0 + ry, gx = tx0 - C0 + rx;
+      int o;
+      const int ay = interior ? gy : refl_half(gy, nf, &o);
+      const int ax = interior ? gx : refl_half(gx, nf, &o);
+      su[idx] = mode ? src[(size_t)ay * nf + ax] : fold_fetch<T>(pd, src, ay, ax);
+    }
+  }
+  __syncthreads();
+  if (L == 2) {
+    // c_1 = (b0 x b0) u, 2 x 2 outputs per thread
+    constexpr int MW = Gm::C1W / 2, MH = Gm::C1H / 2;
+    constexpr int OFF = C0 - 5;        // = 1
+    for (int mt = threadIdx.x; mt < MW * MH; mt += 32 * F3_NWR) {
+      const int my = mt / MW, mx = mt - my * MW;
+      const int qy = 2 * my, qx = 2 * mx;
+      T hrw[4][2];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const T* row = su + (qy - 1 + k + OFF) * Gm::UW + (qx - 1 + OFF);
+        const T a = row[0], b = row[1], c = row[2], d = row[3];
+        hrw[k][0] = T(0.25) * (a + c) + T(0.5) * b;
+        hrw[k][1] = T(0.25) * (b + d) + T(0.5) * c;
+      }
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox)
+          sc1[(qy + oy) * Gm::C1W + qx + ox] =
+              T(0.25) * (hrw[oy][ox] + hrw[oy + 2][ox]) + T(0.5) * hrw[oy + 1][ox];
+    }
+    __syncthreads();
+  }
+  const int w = threadIdx.x >> 5;
+  const int seg_lo = ty0 + w * F3_SEG, seg_hi = seg_lo + F3_SEG;
+  if (seg_lo >= nf) return;        // no barrier follows
+  T* f = static_cast<T*>(pd.buf[f_slot]);
+  // z rows [seg_lo - 3, seg_hi + 3) and columns [tx0 - 3, tx0 + 29) inside the image
+  const bool interior = seg_lo - 3 >= 0 && tx0 - 3 >= 0 && seg_hi + 3 <= nf && tx0 + 29 <= nf;
+  if (L == 2) {
+    if (interior)
+      f3_level<T, TZ, 2, L, true>(pd, sc1, Gm::C1W, ty0 - 5, tx0 - 5, zin, zout, ty0, tx0, seg_lo,
+                                  seg_hi, mu, sf2, f);
+    else
+      f3_level<T, TZ, 2, L, false>(pd, sc1, Gm::C1W, ty0 - 5, tx0 - 5, zin, zout, ty0, tx0, seg_lo,
+                                   seg_hi, mu, sf2, f);
+    __syncwarp();
+  }
+  if (interior)
+    f3_level<T, TZ, 1, L, true>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0, seg_lo,
+                                seg_hi, mu, sf2, f);
+  else
+    f3_level<T, TZ, 1, L, false>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0, seg_lo,
+                                 seg_hi, mu, sf2, f);
+}
+
+int frame_tiles(int nf, int levels) {
+  if (levels <= 2) return ((nf + F3_TX - 1) / F3_TX) * ((nf + F3_TY - 1) / F3_TY);
+  return ((nf + FRAME_TILE - 1) / FRAME_TILE) * ((nf + FRAME_TILE - 1) / FRAME_TILE);
+}
+
 template <typename T, typename TZ>
 void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, int u_slot,
                   int f_slot, const void* zin, void* zout, double op_mu, size_t smem, int levels,
                   cudaStream_t s) {
   if (nitems <= 0) return;
   if (levels == 1)
-    k_frame2<T, TZ, 1><<<nitems, F2_THREADS, frame2_smem_bytes<T, TZ, 1>(), s>>>(
+    k_frame3<T, TZ, 1><<<nitems, 32 * F3_NWR, frame3_smem_bytes<T, 1>(), s>>>(
         probs, states, items, u_slot, f_slot, zin, zout, op_mu);
   else if (levels == 2)
-    k_frame2<T, TZ, 2><<<nitems, F2_THREADS, frame2_smem_bytes<T, TZ, 2>(), s>>>(
+    k_frame3<T, TZ, 2><<<nitems, 32 * F3_NWR, frame3_smem_bytes<T, 2>(), s>>>(
         probs, states, items, u_slot, f_slot, zin, zout, op_mu);
   else
     k_frame<T, TZ><<<nitems, FRAME_THREADS, smem, s>>>(probs, states, items, u_slot, f_slot, zin,
@@ -643,11 +919,11 @@ void launch_frame(const Prob* probs, State* states, const int2* items, int nitem
 }
 template <typename T, typename TZ>
 cudaError_t frame_set_smem(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_frame2<T, TZ, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)frame2_smem_bytes<T, TZ, 1>());
+  cudaError_t e = cudaFuncSetAttribute(k_frame3<T, TZ, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)frame3_smem_bytes<T, 1>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_frame2<T, TZ, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)frame2_smem_bytes<T, TZ, 2>());
+  e = cudaFuncSetAttribute(k_frame3<T, TZ, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)frame3_smem_bytes<T, 2>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_frame<T, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)bytes);

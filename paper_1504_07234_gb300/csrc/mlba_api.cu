@@ -313,10 +313,9 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   pd.ntaps = (int)h.w.size();
   pd.sep = rank_one(h.psf, p, h.hy, h.hx) && p > 1 ? 1 : 0;
   // launch geometry
-  const int TS = FRAME_TILE;
   pd.nblk_blur = ((n + 31) / 32) * ((n + 31) / 32);
   pd.nblk_corr = ((pd.ne + 31) / 32) * ((pd.ne + 31) / 32);
-  pd.nblk_frame = ((pd.nf + TS - 1) / TS) * ((pd.nf + TS - 1) / TS);
+  pd.nblk_frame = frame_tiles(pd.nf, o.levels);
   const int cap = TR_CAP / n;                          // transforms per CTA
   const int pairs = (n + 1) / 2;
   {
