@@ -644,9 +644,9 @@ k_frame2(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
 // neighbours are in the warp produce output: level 2 (D = 2) lanes 2..29,
 // level 1 lanes 1..26.  Neighbouring warps and tiles recompute the
 // overlapping coefficients (from the same z_in) and only the owner writes
-// z_out.  Shared memory carries only the inputs (u, c_1 = (b0 x b0) u) and
-// the level-2 part of f, so there are no shared-memory atomics; the only
-// CTA-wide barriers are the two after the u and c_1 tiles.
+// z_out.  Shared memory carries only the input u (c_1 = (b0 x b0) u is formed
+// on the fly by the level-2 sweep) and the level-2 part of f, so there are no
+// shared-memory atomics; the only CTA-wide barrier follows the u tile.
 constexpr int F3_TX = 26;      // tile columns: level-2 output lanes 3..28 after the +-1 low-pass
 constexpr int F3_SEG = 32;     // rows per warp
 constexpr int F3_NWR = 2;      // warps (row segments) per CTA
@@ -657,24 +657,24 @@ template <int L>
 struct F3 {
   static constexpr int C0 = (L == 2) ? 6 : 2;         // radius of the u tile
   static constexpr int UW = F3_TX + 2 * C0, UH = F3_TY + 2 * C0;
-  static constexpr int C1W = F3_TX + 10, C1H = F3_TY + 10;   // c_1 radius 5 (L = 2)
-  static constexpr size_t elems = (size_t)UW * UH + (L == 2 ? (size_t)C1W * C1H + (size_t)F3_TX * F3_TY : 0);
+  static constexpr size_t elems = (size_t)UW * UH + (L == 2 ? (size_t)F3_TX * F3_TY : 0);
 };
 template <typename T, int L>
 __host__ __device__ constexpr size_t frame3_smem_bytes() { return F3<L>::elems * sizeof(T); }
 
-// z offset inside a band plane of the (reflected) row; sets *par to the
-// row's mirroring parity
-template <bool INTERIOR>
-__device__ __forceinline__ int f3_zrow(int y, int nf, bool* par) {
-  if (INTERIOR) { *par = false; return y * nf; }
+// half-sample reflection of an index with the parity of the mirroring; the
+// common cases (inside, or one mirror away) avoid the division
+__device__ __forceinline__ int f3_refl(int e, int n, bool* par) {
+  if (e >= 0 && e < n) { *par = false; return e; }
+  if (e < 0 && e >= -n) { *par = true; return -1 - e; }
+  if (e >= n && e < 2 * n) { *par = true; return 2 * n - 1 - e; }
   int o;
-  const int r = refl_half(y, nf, &o);
+  const int r = refl_half(e, n, &o);
   *par = o != 0;
-  return r * nf;
+  return r;
 }
 
-template <typename T, typename TZ, int LEV, int L, bool INTERIOR>
+template <typename T, typename TZ, int LEV, int L>
 __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ cin, int cpitch,
                                          int cy0, int cx0, const TZ* __restrict__ zin,
                                          TZ* __restrict__ zout, int ty0, int tx0, int seg_lo,
@@ -692,41 +692,67 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   const int x = tx0 - XO + lane;
   const bool act = lane < NL;
   const int nf = pd.nf;
-  const size_t plane = (size_t)nf * nf;
+  const int plane = nf * nf;     // nbands nf^2 < 2^31 is checked at set-up
   // rows: outputs [yo0, yo1), coefficients [yc0, yc1)
   const int yo0 = (LEV == 2) ? seg_lo - 1 : seg_lo;
   const int yo1 = (LEV == 2) ? seg_hi + 1 : seg_hi;
   const int yc0 = yo0 - D, yc1 = yo1 + D;
   // column part of the z offsets and its mirroring parity
-  int zc = x;
-  bool pcx = false;
-  if (!INTERIOR) { int o; zc = refl_half(x, nf, &o); pcx = o != 0; }
+  bool pcx;
+  const int zc = f3_refl(x, nf, &pcx);
+  const T scol = pcx ? T(-1) : T(1);
   const bool own_c = act && x >= tx0 && x < tx0 + F3_TX && x < nf;
   const T* ccol = cin + (act ? x - cx0 : D);   // idle lanes read a valid column
+  // level 2 reads c_1 = (b0 x b0) u, formed here from the u tile: lane l keeps
+  // c_1 at columns x - 2 and x + 2 (a sliding ring of the horizontally
+  // filtered u rows, g), and gets c_1 at x from lane l - 2 (or l + 2)
+  const T* ua = cin + (x - 2 - cx0);
+  T gr[3][2];
+  auto grow = [&](int y, T (&g)[2]) {
+    const T* r = ua + (y - cy0) * cpitch;
+    g[0] = T(0.25) * (r[-1] + r[1]) + T(0.5) * r[0];
+    g[1] = T(0.25) * (r[3] + r[5]) + T(0.5) * r[4];
+  };
   // band planes in k order
-  size_t boff[NB];
+  int boff[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int k = K0 + b;
-    boff[b] = (size_t)f2_band(LEV, L, k % 3, k / 3) * plane;
+    boff[b] = f2_band(LEV, L, k % 3, k / 3) * plane;
   }
   // h ring: rows y - D .. y + D of the current coefficient row y
   T hr[2 * D + 1][3];
   auto hrow = [&](int y, T (&h)[3]) {
-    const T* r = ccol + (size_t)(y - cy0) * cpitch;
-    const T cm = r[-D], c0 = r[0], cp = r[D];
+    T cm, c0, cp;
+    if constexpr (LEV == 2) {
+      // rows are requested in order: g holds rows y - 1, y and gets y + 1
+      grow(y + 1, gr[2]);
+      cm = T(0.25) * (gr[0][0] + gr[2][0]) + T(0.5) * gr[1][0];
+      cp = T(0.25) * (gr[0][1] + gr[2][1]) + T(0.5) * gr[1][1];
+      const T up = __shfl_up_sync(FULL, cp, 2), dn = __shfl_down_sync(FULL, cm, 2);
+      c0 = lane >= 2 ? up : dn;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) { gr[0][q] = gr[1][q]; gr[1][q] = gr[2][q]; }
+    } else {
+      const T* r = ccol + (y - cy0) * cpitch;
+      cm = r[-D]; c0 = r[0]; cp = r[D];
+    }
     const T sp = cm + cp;
     h[0] = T(0.25) * sp + T(0.5) * c0;
     h[1] = s2q * (cm - cp);
     h[2] = T(0.5) * c0 - T(0.25) * sp;
   };
+  if constexpr (LEV == 2) {
+    grow(yc0 - D - 1, gr[0]);
+    grow(yc0 - D, gr[1]);
+  }
 #pragma unroll
   for (int k = 0; k < 2 * D; ++k) hrow(yc0 - D + k, hr[k]);
   // z queue: rows y .. y + PF - 1
   TZ zq[F3_PF][NB];
   auto zload = [&](int y, TZ (&q)[NB]) {
     bool par;
-    const int ro = f3_zrow<INTERIOR>(y, nf, &par);
+    const int ro = f3_refl(y, nf, &par) * nf;
     const TZ* zp = zin + (ro + zc);
 #pragma unroll
     for (int b = 0; b < NB; ++b) q[b] = act ? zp[boff[b]] : TZ(0.0f);
@@ -739,11 +765,17 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   for (int k = 0; k <= 2 * D; ++k) pr[k][0] = pr[k][1] = pr[k][2] = T(0);
   // level-2 low-pass ring of the horizontally filtered s_1 rows r-2, r-1, r
   T gq[3] = {T(0), T(0), T(0)};
-#pragma unroll 1
-  for (int y = yc0; y < yc1; ++y) {
+  // one coefficient row; q holds its z and is refilled with row y + PF.  The
+  // queue is indexed statically (the sweep is unrolled by PF) so that no
+  // register receiving an outstanding load is copied before it is used.
+  auto step = [&](int y, TZ (&q)[NB]) {
     hrow(y + D, hr[2 * D]);
     bool pry;
-    const int zro = f3_zrow<INTERIOR>(y, nf, &pry);
+    const int zro = f3_refl(y, nf, &pry) * nf;
+    // z outside the image is its mirror image; antisymmetric (b1) bands
+    // change sign under an odd number of mirrorings
+    const T srow = pry ? T(-1) : T(1);
+    const T s11 = srow * scol;
     const bool own = own_c && y >= seg_lo && y < seg_hi && y < nf;
     TZ* zw = zout + (zro + zc);
 #pragma unroll
@@ -754,24 +786,16 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
       const T bi2 = (i == 0) ? T(0.25) : (i == 1 ? -s2q : T(-0.25));
       T a = bi0 * hr[0][j] + bi2 * hr[2 * D][j];
       if (i != 1) a += bi1 * hr[D][j];
-      T zv = T(ld_z(&zq[0][b]));
-      if (!INTERIOR) {
-        // antisymmetric (b1) bands change sign under an odd number of mirrorings
-        if (((i == 1) && pry) != ((j == 1) && pcx)) zv = -zv;
-      }
-      const T zn = zv + a;
+      const T zv = T(ld_z(&q[b]));
+      const T zn = (i == 1 && j == 1) ? fma(zv, s11, a)
+                 : (i == 1) ? fma(zv, srow, a) : (j == 1) ? fma(zv, scol, a) : zv + a;
       if (own) st_z(zw + boff[b], zn);
       const T xv = zn - fmin(fmax(zn, -mu), mu);     // S_mu
       pr[0][j] += bi0 * xv;
       if (i != 1) pr[D][j] += bi1 * xv;
       pr[2 * D][j] += bi2 * xv;
     }
-    // advance the z queue
-#pragma unroll
-    for (int k = 0; k + 1 < F3_PF; ++k)
-#pragma unroll
-      for (int b = 0; b < NB; ++b) zq[k][b] = zq[k + 1][b];
-    if (y + F3_PF < yc1) zload(y + F3_PF, zq[F3_PF - 1]);
+    if (y + F3_PF < yc1) zload(y + F3_PF, q);
     // row y - D has all its contributions: horizontal synthesis
     const int r = y - D;
     if (r >= yo0) {
@@ -801,6 +825,12 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
 #pragma unroll
       for (int j = 0; j < 3; ++j) { hr[k][j] = hr[k + 1][j]; pr[k][j] = pr[k + 1][j]; }
     pr[2 * D][0] = pr[2 * D][1] = pr[2 * D][2] = T(0);
+  };
+#pragma unroll 1
+  for (int y = yc0; y < yc1; y += F3_PF) {
+#pragma unroll
+    for (int k = 0; k < F3_PF; ++k)
+      if (y + k < yc1) step(y + k, zq[k]);
   }
 }
 
@@ -828,8 +858,7 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
     zout = static_cast<TZ*>(pd.z[st.iter & 1]);
   }
   T* su = reinterpret_cast<T*>(smraw);            // u on rows ty0 - C0.., cols tx0 - C0..
-  T* sc1 = su + Gm::UW * Gm::UH;                  // c_1 on rows ty0 - 5.., cols tx0 - 5..
-  T* sf2 = sc1 + (L == 2 ? Gm::C1W * Gm::C1H : 0);   // level-2 part of f on the tile
+  T* sf2 = su + Gm::UW * Gm::UH;                  // level-2 part of f on the tile (L = 2)
   constexpr int C0 = Gm::C0;
   {
     int mode;
@@ -840,61 +869,40 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
     else { src = static_cast<const T*>(pd.buf[SL_V]); mode = 0; }
     const bool interior = ty0 - C0 >= 0 && tx0 - C0 >= 0 && ty0 + F3_TY + C0 <= nf &&
                           tx0 + F3_TX + C0 <= nf;
-    for (int idx = threadIdx.x; idx < Gm::UW * Gm::UH; idx += 32 * F3_NWR) {
-      const int ry = idx / Gm::UW, rx = idx - ry * Gm::UW;
-      const int gy = ty0 - C0 + ry, gx = tx0 - C0 + rx;
-      int o;
-      const int ay = interior ? gy : refl_half(gy, nf, &o);
-      const int ax = interior ? gx : refl_half(gx, nf, &o);
-      su[idx] = mode ? src[(size_t)ay * nf + ax] : fold_fetch<T>(pd, src, ay, ax);
+    constexpr int NT = 32 * F3_NWR, UB = 1;     // UB loads of a thread in flight
+    constexpr int UN = Gm::UW * Gm::UH;
+    for (int i0 = threadIdx.x; i0 < UN; i0 += UB * NT) {
+      T v[UB];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int idx = i0 + u * NT;
+        v[u] = T(0);
+        if (idx < UN) {
+          const int ry = idx / Gm::UW, rx = idx - ry * Gm::UW;
+          const int gy = ty0 - C0 + ry, gx = tx0 - C0 + rx;
+          int o;
+          const int ay = interior ? gy : refl_half(gy, nf, &o);
+          const int ax = interior ? gx : refl_half(gx, nf, &o);
+          v[u] = mode ? src[(size_t)ay * nf + ax] : fold_fetch<T>(pd, src, ay, ax);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UB; ++u)
+        if (i0 + u * NT < UN) su[i0 + u * NT] = v[u];
     }
   }
   __syncthreads();
-  if (L == 2) {
-    // c_1 = (b0 x b0) u, 2 x 2 outputs per thread
-    constexpr int MW = Gm::C1W / 2, MH = Gm::C1H / 2;
-    constexpr int OFF = C0 - 5;        // = 1
-    for (int mt = threadIdx.x; mt < MW * MH; mt += 32 * F3_NWR) {
-      const int my = mt / MW, mx = mt - my * MW;
-      const int qy = 2 * my, qx = 2 * mx;
-      T hrw[4][2];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const T* row = su + (qy - 1 + k + OFF) * Gm::UW + (qx - 1 + OFF);
-        const T a = row[0], b = row[1], c = row[2], d = row[3];
-        hrw[k][0] = T(0.25) * (a + c) + T(0.5) * b;
-        hrw[k][1] = T(0.25) * (b + d) + T(0.5) * c;
-      }
-#pragma unroll
-      for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-        for (int ox = 0; ox < 2; ++ox)
-          sc1[(qy + oy) * Gm::C1W + qx + ox] =
-              T(0.25) * (hrw[oy][ox] + hrw[oy + 2][ox]) + T(0.5) * hrw[oy + 1][ox];
-    }
-    __syncthreads();
-  }
   const int w = threadIdx.x >> 5;
   const int seg_lo = ty0 + w * F3_SEG, seg_hi = seg_lo + F3_SEG;
   if (seg_lo >= nf) return;        // no barrier follows
   T* f = static_cast<T*>(pd.buf[f_slot]);
-  // z rows [seg_lo - 3, seg_hi + 3) and columns [tx0 - 3, tx0 + 29) inside the image
-  const bool interior = seg_lo - 3 >= 0 && tx0 - 3 >= 0 && seg_hi + 3 <= nf && tx0 + 29 <= nf;
   if (L == 2) {
-    if (interior)
-      f3_level<T, TZ, 2, L, true>(pd, sc1, Gm::C1W, ty0 - 5, tx0 - 5, zin, zout, ty0, tx0, seg_lo,
-                                  seg_hi, mu, sf2, f);
-    else
-      f3_level<T, TZ, 2, L, false>(pd, sc1, Gm::C1W, ty0 - 5, tx0 - 5, zin, zout, ty0, tx0, seg_lo,
-                                   seg_hi, mu, sf2, f);
+    f3_level<T, TZ, 2, L>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0, seg_lo, seg_hi,
+                          mu, sf2, f);
     __syncwarp();
   }
-  if (interior)
-    f3_level<T, TZ, 1, L, true>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0, seg_lo,
-                                seg_hi, mu, sf2, f);
-  else
-    f3_level<T, TZ, 1, L, false>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0, seg_lo,
-                                 seg_hi, mu, sf2, f);
+  f3_level<T, TZ, 1, L>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0, seg_lo, seg_hi,
+                        mu, sf2, f);
 }
 
 int frame_tiles(int nf, int levels) {

@@ -316,6 +316,8 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   pd.nblk_blur = ((n + 31) / 32) * ((n + 31) / 32);
   pd.nblk_corr = ((pd.ne + 31) / 32) * ((pd.ne + 31) / 32);
   pd.nblk_frame = frame_tiles(pd.nf, o.levels);
+  // the frame kernel indexes a z array (all bands) with 32-bit offsets
+  if ((double)pd.nbands * pd.nf * pd.nf >= 2147483647.0) return MLBA_E_UNSUPPORTED;
   const int cap = TR_CAP / n;                          // transforms per CTA
   const int pairs = (n + 1) / 2;
   {
