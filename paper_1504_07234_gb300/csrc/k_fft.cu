@@ -617,30 +617,41 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
 // ---------------------------------------------------------------------------
 // Algorithm 4-NS: alpha_n of Eq. Alg4_rev_7.  With a unitary transform the
 // equation reads h(b) = F(a)/P - q_n^2 = 0, a = exp(b), P = sum |r^|^2,
-// F(a) = sum |r^|^2 x^2, x = a/(s+a); h increases with b (unique root), and
-// dh/db = sum 2 |r^|^2 x^2 (1-x) / P.  The spectrum in S is the unnormalised
-// one; every coefficient carries its orthonormal weight, so the ratio is
-// exact.  Pass 1 evaluates h at NS_CAND points b_prev + (j - 15.5) * 0.8 and
-// brackets the root within a factor e^0.8; later passes take safeguarded
-// Newton steps inside the bracket until |step| <= tol.  Each block sums its
-// share in T precision (FP64 accumulation across blocks); the last block
-// updates the scalar state.
+// F(a) = sum |r^|^2 x^2, x = a/(s+a).  h increases with b (unique root);
+// with dx/db = x(1-x) its derivatives are
+//   h'  = 2 sum |r^|^2 x^2 (1-x) / P,
+//   h'' = 2 sum |r^|^2 x^2 (1-x)(2-3x) / P.
+// The spectrum in S is the unnormalised one; every coefficient carries its
+// orthonormal weight, so the ratio is exact.  Pass 1 evaluates h and h' at
+// NS_CAND points b_prev + (j - 7.5) NS_CAND_STEP, brackets the root and
+// takes the root of the cubic Hermite interpolant on the bracket.  Later
+// passes take safeguarded Halley steps inside the bracket; a step below
+// tol, or below ns_tol3 (the next error is of the order of its cube), ends
+// the solve.  Each block sums its share in T precision (FP64 across
+// blocks); the last block updates the scalar state.
 constexpr int NS_CAND = 16;
 constexpr double NS_CAND_STEP = 1.0;
+constexpr int NS_NT = SPEC_THREADS, NS_PT = SPEC_PER_THREAD;
+static_assert(SPEC_SUMS == 2 * NS_CAND + 1, "partial buffer sized for the bracketing pass");
 
-// element e (< SPEC_THREADS * SPEC_PER_THREAD) of spectrum block `blk`,
-// enumerated along the column-blocked layout (contiguous reads): weighted
-// power and |lambda|^2 in T precision; false past the end or on padding
+__host__ __device__ constexpr double ns_tol(int elem_bytes) { return elem_bytes == 8 ? 1e-10 : 1e-5; }
+// FP32: cbrt(tol) / 8, where the error after a Halley step (of the order of
+// the step's cube) is far below tol; FP64 takes only steps below tol
+__host__ __device__ constexpr double ns_tol3(int elem_bytes) { return elem_bytes == 8 ? 1e-10 : 2.7e-3; }
+
+// element e (< NS_NT * NS_PT) of spectrum block `blk`, enumerated along the
+// column-blocked layout (contiguous reads): weighted power and |lambda|^2 in
+// T precision; false past the end or on padding
 template <typename T>
 __device__ __forceinline__ bool spec_elem(const Prob& pd, int blk, int e, T& pw, T& sg) {
   using T2 = typename Vec2<T>::type;
   const int N = pd.n, cb = pd.cb;
   const bool dct = (pd.transform == TR_DCT);
   const int W = dct ? N : pd.half;
-  const size_t L = (size_t)blk * (SPEC_THREADS * SPEC_PER_THREAD) + e;
-  const size_t blksz = (size_t)N * cb;
-  const int b = (int)(L / blksz);
-  const int rem = (int)(L - (size_t)b * blksz);
+  const int L = blk * (NS_NT * NS_PT) + e;      // < 2^31: one spectrum holds < 2^25 elements
+  const int blksz = N * cb;
+  const int b = L / blksz;
+  const int rem = L - b * blksz;
   const int k1 = rem / cb, c = rem - k1 * cb;
   const int k2 = b * cb + c;
   if (k2 >= W) return false;
@@ -668,11 +679,83 @@ __device__ __forceinline__ void ns_set_alpha(const Prob& pd, State& st, double n
   if (it >= 0 && it < pd.max_iter + 2) pd.hist_alpha[it] = a;
 }
 
-// Bracketing pass (nphase 0): h at NS_CAND candidates around the previous root.
+// Block totals of K values of type A (the warp sums stay in A: FP32 for the
+// FP32 path, where FP64 arithmetic is scarce), then the cross-warp and
+// cross-block totals in FP64 in the block that arrives last (true there;
+// tot[] valid in thread 0).  Every sum runs in a fixed order, so the result
+// is deterministic.
+template <int NT, int K, typename A>
+__device__ bool ns_reduce(const Prob& pd, State& st, int blk, int nblk, A (&v)[K],
+                          double* sh, double* tot) {
+  constexpr int NW = NT / 32;
+  __shared__ int is_last;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (l == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * NW + w] = (double)v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int i = 0; i < NW; ++i) t += sh[threadIdx.x * NW + i];
+    pd.partial[(size_t)threadIdx.x * nblk + blk] = t;
+    __threadfence();                 // each writer publishes its partial
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int prev = atomicAdd(&st.counter, 1u);
+    is_last = (prev == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  for (int k = w; k < K; k += NW) {
+    double s = 0.0;
+    for (int i = l; i < nblk; i += 32) s += __ldcg(&pd.partial[(size_t)k * nblk + i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) tot[k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st.counter = 0u;
+  return true;
+}
+
+// root in [0, 1] of the cubic Hermite interpolant with p(0) = h0 < 0 <= p(1)
+// = h1 and slopes m0, m1 (per unit t): bisection-safeguarded Newton
+__device__ double hermite_root(double h0, double h1, double m0, double m1) {
+  auto p = [&](double t, double* dp) {
+    const double t2 = t * t, t3 = t2 * t;
+    const double H00 = 2 * t3 - 3 * t2 + 1, H10 = t3 - 2 * t2 + t;
+    const double H01 = -2 * t3 + 3 * t2, H11 = t3 - t2;
+    *dp = h0 * (6 * t2 - 6 * t) + m0 * (3 * t2 - 4 * t + 1) + h1 * (-6 * t2 + 6 * t) +
+          m1 * (3 * t2 - 2 * t);
+    return h0 * H00 + m0 * H10 + h1 * H01 + m1 * H11;
+  };
+  double lo = 0.0, hi = 1.0;
+  double t = (h1 > h0) ? -h0 / (h1 - h0) : 0.5;
+  for (int it = 0; it < 40; ++it) {
+    double dp;
+    const double v = p(t, &dp);
+    if (v < 0.0) lo = t; else hi = t;
+    double tn = (dp > 0.0) ? t - v / dp : 0.5 * (lo + hi);
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (fabs(tn - t) < 1e-14) { t = tn; break; }
+    t = tn;
+  }
+  return t;
+}
+
+// Bracketing pass (nphase 0): h and h' at NS_CAND candidates around the
+// previous root.
 template <typename T>
-__global__ void __launch_bounds__(SPEC_THREADS)
+__global__ void __launch_bounds__(NS_NT, 2)
 k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items) {
-  __shared__ double red[(NS_CAND + 1) * (SPEC_THREADS / 32)];
+  constexpr int K = 2 * NS_CAND + 1;
+  __shared__ double red[K * (NS_NT / 32)];
+  __shared__ double tot[K];
   __shared__ float s_ca[NS_CAND];
   const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
@@ -681,45 +764,57 @@ k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const in
   const double b0 = st.nb;
   if (threadIdx.x < NS_CAND)
     s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
-  T pw[SPEC_PER_THREAD], sg[SPEC_PER_THREAD];
-  bool ok[SPEC_PER_THREAD];
+  T pw[NS_PT], sg[NS_PT];
+  bool ok[NS_PT];
 #pragma unroll
-  for (int q = 0; q < SPEC_PER_THREAD; ++q)
-    ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + q * SPEC_THREADS, pw[q], sg[q]);
+  for (int q = 0; q < NS_PT; ++q)
+    ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + q * NS_NT, pw[q], sg[q]);
   __syncthreads();
-  float cF[NS_CAND];
+  float ca[NS_CAND], cF[NS_CAND], cG[NS_CAND];
 #pragma unroll
-  for (int j = 0; j < NS_CAND; ++j) cF[j] = 0.f;
+  for (int j = 0; j < NS_CAND; ++j) { ca[j] = s_ca[j]; cF[j] = 0.f; cG[j] = 0.f; }
   T sP = T(0);
 #pragma unroll
-  for (int q = 0; q < SPEC_PER_THREAD; ++q) {
+  for (int q = 0; q < NS_PT; ++q) {
     if (!ok[q]) continue;
     sP += pw[q];
     const float pf = (float)pw[q], sf = (float)sg[q];
 #pragma unroll
     for (int j = 0; j < NS_CAND; ++j) {
-      const float x = __fdividef(s_ca[j], sf + s_ca[j]);
-      cF[j] += pf * x * x;
+      const float x = __fdividef(ca[j], sf + ca[j]);
+      const float px2 = pf * x * x;
+      cF[j] += px2;
+      cG[j] = fmaf(-px2, x, cG[j] + px2);        // + pw x^2 (1 - x)
     }
   }
-  double v0[NS_CAND + 1], v[NS_CAND + 1], t[NS_CAND + 1];
-  v0[0] = (double)sP;
+  T v[K];
+  v[0] = sP;
 #pragma unroll
-  for (int j = 0; j < NS_CAND; ++j) v0[j + 1] = (double)cF[j];
-  block_sum_k<SPEC_THREADS, NS_CAND + 1>(v0, v, red);
-  if (last_block_reduce<SPEC_THREADS, NS_CAND + 1>(pd, st, item.y, pd.nblk_spec, v, t, red) &&
-      threadIdx.x == 0) {
-    const double P = t[0], target = st.qn * st.qn;
+  for (int j = 0; j < NS_CAND; ++j) { v[1 + j] = T(cF[j]); v[1 + NS_CAND + j] = T(cG[j]); }
+  if (ns_reduce<NS_NT, K, T>(pd, st, item.y, pd.nblk_spec, v, red, tot) && threadIdx.x == 0) {
+    const double P = tot[0], target = st.qn * st.qn;
+    auto hv = [&](int j) { return P > 0.0 ? tot[1 + j] / P - target : 0.0; };
+    auto dv = [&](int j) { return P > 0.0 ? 2.0 * tot[1 + NS_CAND + j] / P : 0.0; };
+    auto bv = [&](int j) { return b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP; };
     int j = 0;
-    while (j < NS_CAND && !(P > 0.0 && t[j + 1] / P - target >= 0.0)) ++j;
-    const double bj = b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP;
+    while (j < NS_CAND && !(hv(j) >= 0.0)) ++j;
     double nb;
-    if (j == 0) { st.nb_lo = -INFINITY; st.nb_hi = bj; nb = bj - NS_CAND_STEP; }
-    else if (j == NS_CAND) { st.nb_lo = bj - NS_CAND_STEP; st.nb_hi = INFINITY; nb = bj; }
-    else {
-      const double hl = t[j] / P - target, hh = t[j + 1] / P - target;
-      st.nb_lo = bj - NS_CAND_STEP; st.nb_hi = bj;
-      nb = st.nb_lo + (hh > hl ? (-hl) / (hh - hl) : 0.5) * NS_CAND_STEP;
+    if (j == 0) {
+      // root below the window: Newton from the lowest candidate, at most 4 down
+      st.nb_lo = -INFINITY; st.nb_hi = bv(0);
+      const double d = dv(0);
+      nb = (d > 0.0 && isfinite(hv(0) / d)) ? bv(0) - hv(0) / d : bv(0) - 4.0;
+      nb = fmax(nb, bv(0) - 4.0);
+    } else if (j == NS_CAND) {
+      st.nb_lo = bv(NS_CAND - 1); st.nb_hi = INFINITY;
+      const double d = dv(NS_CAND - 1);
+      nb = (d > 0.0 && isfinite(hv(NS_CAND - 1) / d)) ? bv(NS_CAND - 1) - hv(NS_CAND - 1) / d
+                                                      : bv(NS_CAND - 1) + 4.0;
+      nb = fmin(nb, bv(NS_CAND - 1) + 4.0);
+    } else {
+      st.nb_lo = bv(j - 1); st.nb_hi = bv(j);
+      const double t = hermite_root(hv(j - 1), hv(j), dv(j - 1) * NS_CAND_STEP, dv(j) * NS_CAND_STEP);
+      nb = st.nb_lo + t * NS_CAND_STEP;
     }
     st.nphase = 1;
     st.npass += 1;
@@ -727,63 +822,59 @@ k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const in
   }
 }
 
-// Newton pass (nphase 1): h and dh/dlog(alpha) at the current estimate, then a
-// safeguarded step inside the bracket.
+// Refinement pass (nphase 1): a safeguarded Halley step at the current b.
 template <typename T>
-__global__ void __launch_bounds__(SPEC_THREADS)
+__global__ void __launch_bounds__(NS_NT)
 k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items) {
-  __shared__ double red[32];
-  __shared__ T s_alpha;
+  __shared__ double red[4 * (NS_NT / 32)];
+  __shared__ double tot[4];
   const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
   State& st = states[item.x];
   if (st.stopped || !pd.ns || !st.ns_active || st.nconv || st.nphase != 1) return;
   const double b0 = st.nb;
-  if (threadIdx.x == 0) s_alpha = T(exp(b0));
-  T pw[SPEC_PER_THREAD], sg[SPEC_PER_THREAD];
-  bool ok[SPEC_PER_THREAD];
+  const T alpha = T(exp(b0));
+  T pw[NS_PT], sg[NS_PT];
+  bool ok[NS_PT];
 #pragma unroll
-  for (int q = 0; q < SPEC_PER_THREAD; ++q)
-    ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + q * SPEC_THREADS, pw[q], sg[q]);
-  __syncthreads();
-  const T alpha = s_alpha;
-  T sP = T(0), sF = T(0), sG = T(0);
+  for (int q = 0; q < NS_PT; ++q)
+    ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + q * NS_NT, pw[q], sg[q]);
+  T sP = T(0), sF = T(0), sG1 = T(0), sG2 = T(0);
 #pragma unroll
-  for (int q = 0; q < SPEC_PER_THREAD; ++q) {
+  for (int q = 0; q < NS_PT; ++q) {
     if (!ok[q]) continue;
     const T x = alpha / (sg[q] + alpha);
-    const T x2 = x * x;
+    const T px2 = pw[q] * x * x;
+    const T g1 = px2 * (T(1) - x);
     sP += pw[q];
-    sF += pw[q] * x2;
-    sG += T(2) * pw[q] * x2 * (T(1) - x);
+    sF += px2;
+    sG1 += g1;
+    sG2 += g1 * (T(2) - T(3) * x);
   }
-  double v3[3];
-  v3[0] = block_sum<SPEC_THREADS>((double)sP, red);
-  v3[1] = block_sum<SPEC_THREADS>((double)sF, red);
-  v3[2] = block_sum<SPEC_THREADS>((double)sG, red);
-  double t3[3];
-  if (last_block_reduce<SPEC_THREADS, 3>(pd, st, item.y, pd.nblk_spec, v3, t3, red) &&
-      threadIdx.x == 0) {
-    const double P = t3[0];
+  T v[4] = {sP, sF, sG1, sG2};
+  if (ns_reduce<NS_NT, 4, T>(pd, st, item.y, pd.nblk_spec, v, red, tot) && threadIdx.x == 0) {
+    const double P = tot[0];
     const double target = st.qn * st.qn;
-    const double h = (P > 0.0) ? t3[1] / P - target : 0.0;
-    const double hp = (P > 0.0) ? t3[2] / P : 0.0;
-    const double tol = (sizeof(T) == 8) ? 1e-10 : 1e-5;
+    const double h = (P > 0.0) ? tot[1] / P - target : 0.0;
+    const double h1 = (P > 0.0) ? 2.0 * tot[2] / P : 0.0;
+    const double h2 = (P > 0.0) ? 2.0 * tot[3] / P : 0.0;
     const double nb = b0;
     if (h < 0.0) st.nb_lo = fmax(st.nb_lo, nb);
     else if (h > 0.0) st.nb_hi = fmin(st.nb_hi, nb);
-    double nn;
-    bool conv = false;
-    if (hp > 0.0 && isfinite(h / hp)) {
-      const double step = h / hp;
-      nn = nb - step;
-      conv = fabs(step) <= tol;        // quadratic convergence: nn is accurate
-    } else {
-      nn = (h < 0.0) ? nb + 2.0 : nb - 2.0;
+    double step = 0.0;
+    bool have = false;
+    if (h1 > 0.0) {
+      const double den = 2.0 * h1 * h1 - h * h2;
+      step = (den > 0.0) ? 2.0 * h * h1 / den : h / h1;     // Halley, else Newton
+      have = isfinite(step);
     }
+    double nn = have ? nb - step : ((h < 0.0) ? nb + 2.0 : nb - 2.0);
+    const bool inside = nn >= st.nb_lo && nn <= st.nb_hi;
+    bool conv = have && inside &&
+                (fabs(step) <= ns_tol(sizeof(T)) || fabs(step) <= ns_tol3(sizeof(T)));
     if (!conv) {
       if (isfinite(st.nb_lo) && isfinite(st.nb_hi)) {
-        if (!(nn >= st.nb_lo && nn <= st.nb_hi)) nn = 0.5 * (st.nb_lo + st.nb_hi);
+        if (!inside) nn = 0.5 * (st.nb_lo + st.nb_hi);
       } else {
         if (nn > nb + 4.0) nn = nb + 4.0;
         if (nn < nb - 4.0) nn = nb - 4.0;
@@ -866,8 +957,8 @@ template <typename T>
 void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, int cand,
                  cudaStream_t s) {
   if (nitems <= 0) return;
-  if (cand) k_spec_cand<T><<<nitems, SPEC_THREADS, 0, s>>>(probs, states, items);
-  else k_spec<T><<<nitems, SPEC_THREADS, 0, s>>>(probs, states, items);
+  if (cand) k_spec_cand<T><<<nitems, NS_NT, 0, s>>>(probs, states, items);
+  else k_spec<T><<<nitems, NS_NT, 0, s>>>(probs, states, items);
 }
 void launch_spectrum_setup(int transform, int n, int p, int half, int cb, const double* q_dev,
                            const double* tab_dev, void* lam, void* sigT, int is_double,

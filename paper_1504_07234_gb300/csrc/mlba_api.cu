@@ -22,7 +22,9 @@ using namespace mlba;
 
 namespace {
 
-constexpr int NEWTON_PASSES = 8;    // graph nodes per iteration for the alpha_n solve (1 bracketing + Newton)
+// graph nodes per iteration for the alpha_n solve: 1 bracketing pass and
+// Halley passes (FP64 accepts only steps below its tighter tolerance)
+template <typename T> constexpr int ns_passes() { return sizeof(T) == 8 ? 6 : 4; }
 constexpr size_t ALIGN = 256;
 
 #define CK(call)                                   \
@@ -176,7 +178,7 @@ void enqueue_step(mlba_batch* B, cudaStream_t s) {
     if (B->any_ns) {
       launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
       launch_spec<T>(P, S, B->spec.dev, B->spec.count, 1, s);
-      for (int k = 1; k < NEWTON_PASSES; ++k) launch_spec<T>(P, S, B->spec.dev, B->spec.count, 0, s);
+      for (int k = 1; k < ns_passes<T>(); ++k) launch_spec<T>(P, S, B->spec.dev, B->spec.count, 0, s);
       launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
     }
     launch_rows_inv<T>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
@@ -446,7 +448,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
         (size_t)pd.ntaps * 4, (size_t)pd.ntaps * 4, (size_t)pd.ntaps * ts,   // taps
         (size_t)pd.p * ts, (size_t)pd.p * ts,  // hy, hx
-        std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, 17 * (size_t)pd.nblk_spec, (size_t)1}) * 8,  // partial
+        std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, (size_t)SPEC_SUMS * pd.nblk_spec, (size_t)1}) * 8,  // partial
         (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 4};
     offs[i].resize(sz.size());
     for (size_t k = 0; k < sz.size(); ++k) { offs[i][k] = total; total += al(sz[k]); }
