@@ -164,6 +164,19 @@ __device__ __forceinline__ void dft_small(T2* v) {
 __host__ __device__ constexpr int tr_nt(int elem_bytes) { return elem_bytes == 8 ? 512 : 256; }
 __host__ __device__ constexpr int tr_minb(int elem_bytes) { return elem_bytes == 8 ? 1 : 3; }
 
+// n / d by a multiply-high: m = floor((2^32 - 1) / d) + 1 gives the exact
+// quotient whenever 0 <= n and n d < 2^32 (every index here is below 2^17
+// and every divisor at most 8192); d = 1 passes n through
+struct FastDiv {
+  unsigned m;
+  int d;
+  __device__ __forceinline__ explicit FastDiv(int dd)
+      : m(dd > 1 ? 0xFFFFFFFFu / (unsigned)dd + 1u : 0u), d(dd) {}
+  __device__ __forceinline__ int div(int n) const {
+    return d == 1 ? n : (int)__umulhi((unsigned)n, m);
+  }
+};
+
 // shared-memory layout of a transform: element i at fpad(i) (one spare slot
 // every 16 breaks power-of-two strides), transforms TSg = fpad(N) + 1 apart
 __host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
@@ -180,13 +193,14 @@ __device__ __forceinline__ void fft_pass(int G, int N, int TSg, int Ns, const T2
   const int per = N / R;
   const int nbf = G * per;
   const int step = N / (Ns * R);
+  const FastDiv fper(per), fns(Ns);
   T2 v[MAXB][R];
 #pragma unroll
   for (int q = 0; q < MAXB; ++q) {
     const int b = threadIdx.x + q * NT;
     if (b < nbf) {
-      const int g = b / per, j = b - g * per;
-      const int k = j % Ns;
+      const int g = fper.div(b), j = b - g * per;
+      const int k = j - fns.div(j) * Ns;
       const T2* base = sm + g * TSg;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q][r] = base[fpad(j + r * per)];
@@ -206,10 +220,11 @@ __device__ __forceinline__ void fft_pass(int G, int N, int TSg, int Ns, const T2
   for (int q = 0; q < MAXB; ++q) {
     const int b = threadIdx.x + q * NT;
     if (b < nbf) {
-      const int g = b / per, j = b - g * per;
-      const int k = j % Ns;
+      const int g = fper.div(b), j = b - g * per;
+      const int jd = fns.div(j);
+      const int k = j - jd * Ns;
       T2* base = sm + g * TSg;
-      const int o = (j / Ns) * Ns * R + k;
+      const int o = jd * Ns * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) base[fpad(o + r * Ns)] = v[q][r];
     }
@@ -223,7 +238,7 @@ __device__ __forceinline__ void fft_pass(int G, int N, int TSg, int Ns, const T2
 // regions rather than as one loop over a radix switch: the compiler then
 // keeps each region's butterflies in registers (the switch form spilled).
 template <typename T2, bool INV>
-__device__ __forceinline__ void fft_smem(int G, const Prob& pd) {
+__device__ __noinline__ void fft_smem(int G, const Prob& pd) {
   const int N = pd.n;
   const int TSg = fpad(N) + 1;
   const T2* tw = static_cast<const T2*>(pd.tw);
@@ -264,8 +279,9 @@ template <typename T, typename T2>
 __device__ __forceinline__ void dct_split(T2* sm, int G, int N, int TSg, const T2* __restrict__ dtw) {
   constexpr int NT = tr_nt(sizeof(T));
   const int np = N / 2 + 1;
+  const FastDiv fnp(np);
   for (int e = threadIdx.x; e < G * np; e += NT) {
-    const int g = e / np, k = e - g * np;
+    const int g = fnp.div(e), k = e - g * np;
     const int kr = (k == 0) ? 0 : N - k;
     T2* b = sm + g * TSg;
     const T2 Z = b[fpad(k)], Zr = b[fpad(kr)];
@@ -292,8 +308,9 @@ template <typename T, typename T2>
 __device__ __forceinline__ void dct_merge(T2* sm, int G, int N, int TSg, const T2* __restrict__ dtw) {
   constexpr int NT = tr_nt(sizeof(T));
   const int np = N / 2 + 1;
+  const FastDiv fnp(np);
   for (int e = threadIdx.x; e < G * np; e += NT) {
-    const int g = e / np, k = e - g * np;
+    const int g = fnp.div(e), k = e - g * np;
     T2* b = sm + g * TSg;
     const T2 X = b[fpad(k)];
     T2 Xr;
@@ -327,6 +344,7 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
   const int row0 = 2 * pair0;
   const bool dct = (pd.transform == TR_DCT);
   const T* src = static_cast<const T*>(pd.buf[src_slot]);
+  const FastDiv fN(N);
   {
     // all loads of this thread first (up to MAXV in flight), then the stores
     T2 tmp[MAXV];
@@ -334,7 +352,7 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
     for (int q = 0; q < MAXV; ++q) {
       const int e = threadIdx.x + q * NT;
       if (e < G * N) {
-        const int g = e / N, x = e - g * N;
+        const int g = fN.div(e), x = e - g * N;
         const int ra = row0 + 2 * g, rb = ra + 1;
         const int xs = dct ? dct_src(x, N) : x;
         tmp[q].x = (ra < N) ? src[(size_t)ra * N + xs] : T(0);
@@ -344,7 +362,7 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
 #pragma unroll
     for (int q = 0; q < MAXV; ++q) {
       const int e = threadIdx.x + q * NT;
-      if (e < G * N) { const int g = e / N, x = e - g * N; sm[g * TSg + fpad(x)] = tmp[q]; }
+      if (e < G * N) { const int g = fN.div(e), x = e - g * N; sm[g * TSg + fpad(x)] = tmp[q]; }
     }
   }
   __syncthreads();
@@ -355,9 +373,10 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
   const int cb = pd.cb;
   const int R2 = 2 * G;
   const int nb = (W + cb - 1) / cb;
+  const FastDiv frc(R2 * cb), fcb(cb);
   for (int e = threadIdx.x; e < nb * R2 * cb; e += NT) {
-    const int b = e / (R2 * cb), rem = e - b * (R2 * cb);
-    const int rl = rem / cb, c = rem - rl * cb;
+    const int b = frc.div(e), rem = e - b * (R2 * cb);
+    const int rl = fcb.div(rem), c = rem - rl * cb;
     const int k = b * cb + c, row = row0 + rl;
     if (k >= W || row >= N) continue;
     const T2* tb = sm + (rl >> 1) * TSg;
@@ -379,9 +398,14 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
 // spectral weight at blocked index idx; alpha and kind as given.  |lambda|^2 +
 // alpha is formed in T: alpha > 0 keeps it away from zero (no cancellation),
 // so FP32 holds it to 6e-8 relative; 1/n^2 of the unnormalised pair is folded in.
+// scale / (|lambda|^2 + alpha): the fast reciprocal-based quotient in FP32
+// (within 2 ulp), the exact one in FP64
+__device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
+
 template <typename T, typename T2>
 __device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
-  const T inv = scale / (static_cast<const T*>(pd.w)[idx] + alpha);
+  const T inv = wdiv(scale, static_cast<const T*>(pd.w)[idx] + alpha);
   T2 w;
   if (kind == W_TIKH) {
     const T2 l = static_cast<const T2*>(pd.lam)[idx];
@@ -391,7 +415,7 @@ __device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, T alpha, T 
 }
 template <typename T>
 __device__ __forceinline__ T weight_dct(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
-  const T inv = scale / (static_cast<const T*>(pd.w)[idx] + alpha);
+  const T inv = wdiv(scale, static_cast<const T*>(pd.w)[idx] + alpha);
   return kind == W_TIKH ? static_cast<const T*>(pd.lam)[idx] * inv : inv;
 }
 
@@ -425,6 +449,7 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   const int kb = item.y * cb;                         // first column of the block
   if (!dct) {
     const int G = cb;
+    const FastDiv fG(G);
     T2* S = static_cast<T2*>(pd.buf[SL_S]) + base;
     {
       T2 tmp[MAXV];
@@ -432,25 +457,25 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
       for (int q = 0; q < MAXV; ++q) {
         const int e = threadIdx.x + q * NT;
         tmp[q].x = T(0); tmp[q].y = T(0);
-        if (e < N * G && kb + e % G < W) tmp[q] = S[e];
+        if (e < N * G && kb + (e - fG.div(e) * G) < W) tmp[q] = S[e];
       }
 #pragma unroll
       for (int q = 0; q < MAXV; ++q) {
         const int e = threadIdx.x + q * NT;
-        if (e < N * G) { const int k1 = e / G, c = e - k1 * G; sm[c * TSg + fpad(k1)] = tmp[q]; }
+        if (e < N * G) { const int k1 = fG.div(e), c = e - k1 * G; sm[c * TSg + fpad(k1)] = tmp[q]; }
       }
     }
     __syncthreads();
     if (mode != COL_NS_INV) fft_smem<T2, false>(G, pd);
     if (mode == COL_FWD) {
       for (int e = threadIdx.x; e < N * G; e += NT) {
-        const int k1 = e / G, c = e - k1 * G;
+        const int k1 = fG.div(e), c = e - k1 * G;
         if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
       }
       return;
     }
     for (int e = threadIdx.x; e < N * G; e += NT) {
-      const int k1 = e / G, c = e - k1 * G;
+      const int k1 = fG.div(e), c = e - k1 * G;
       if (kb + c < W) {
         T2& v = sm[c * TSg + fpad(k1)];
         v = cmul(v, weight_dft<T, T2>(pd, base + e, Ta, Tsc, kind));
@@ -459,11 +484,12 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
     __syncthreads();
     fft_smem<T2, true>(G, pd);
     for (int e = threadIdx.x; e < N * G; e += NT) {
-      const int k1 = e / G, c = e - k1 * G;
+      const int k1 = fG.div(e), c = e - k1 * G;
       if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
     }
   } else {
     const int G = cb / 2;
+    const FastDiv fcb(cb);
     T* S = static_cast<T*>(pd.buf[SL_S]) + base;
     T* smr = reinterpret_cast<T*>(sm);
     {
@@ -472,13 +498,13 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
       for (int q = 0; q < 2 * MAXV; ++q) {
         const int e = threadIdx.x + q * NT;
         tmp[q] = T(0);
-        if (e < N * cb) { const int c = e % cb; if (kb + c < W) tmp[q] = S[e]; }
+        if (e < N * cb) { const int c = e - fcb.div(e) * cb; if (kb + c < W) tmp[q] = S[e]; }
       }
 #pragma unroll
       for (int q = 0; q < 2 * MAXV; ++q) {
         const int e = threadIdx.x + q * NT;
         if (e < N * cb) {
-          const int k1 = e / cb, c = e - k1 * cb;
+          const int k1 = fcb.div(e), c = e - k1 * cb;
           const int pos = (mode == COL_NS_INV) ? k1 : dct_pos(k1, N);
           smr[2 * ((c >> 1) * TSg + fpad(pos)) + (c & 1)] = tmp[q];
         }
@@ -492,13 +518,13 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
     }
     if (mode == COL_FWD) {
       for (int e = threadIdx.x; e < N * cb; e += NT) {
-        const int k1 = e / cb, c = e - k1 * cb;
+        const int k1 = fcb.div(e), c = e - k1 * cb;
         if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
       }
       return;
     }
     for (int e = threadIdx.x; e < N * cb; e += NT) {
-      const int k1 = e / cb, c = e - k1 * cb;
+      const int k1 = fcb.div(e), c = e - k1 * cb;
       T& v = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
       v *= (kb + c < W) ? weight_dct<T>(pd, base + e, Ta, Tsc, kind) : T(0);
     }
@@ -506,7 +532,7 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
     dct_merge<T, T2>(sm, G, N, TSg, dtw);
     fft_smem<T2, true>(G, pd);
     for (int e = threadIdx.x; e < N * cb; e += NT) {
-      const int k1 = e / cb, c = e - k1 * cb;
+      const int k1 = fcb.div(e), c = e - k1 * cb;
       if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(dct_pos(k1, N))) + (c & 1)];
     }
   }
@@ -533,6 +559,7 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
   const int W = dct ? N : pd.half;
   const int nb = (W + cb - 1) / cb;
   const int tot = nb * G * cb;
+  const FastDiv fgc(G * cb), fcb(cb), fN(N);
   constexpr int BATCH = 4;
   if (dct) {
     const T* S = static_cast<const T*>(pd.buf[SL_S]);
@@ -544,8 +571,8 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
         const int e = e0 + u * NT;
         k[u] = -1;
         if (e < tot) {
-          const int b = e / (G * cb), rem = e - b * (G * cb);
-          const int g = rem / cb, c = rem - g * cb;
+          const int b = fgc.div(e), rem = e - b * (G * cb);
+          const int g = fcb.div(rem), c = rem - g * cb;
           const int ra = row0 + 2 * g;
           const size_t o = (size_t)b * N * cb + (size_t)ra * cb + c;
           k[u] = b * cb + c;
@@ -573,8 +600,8 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
         k[u] = -1;
         xa[u].x = xa[u].y = xb[u].x = xb[u].y = T(0);
         if (e < tot) {
-          const int b = e / (G * cb), rem = e - b * (G * cb);
-          const int g = rem / cb, c = rem - g * cb;
+          const int b = fgc.div(e), rem = e - b * (G * cb);
+          const int g = fcb.div(rem), c = rem - g * cb;
           const int ra = row0 + 2 * g;
           const int kk = b * cb + c;
           if (kk < W) {
@@ -606,7 +633,7 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
   fft_smem<T2, true>(G, pd);
   T* dst = static_cast<T*>(pd.buf[dst_slot]);
   for (int e = threadIdx.x; e < G * N; e += NT) {
-    const int g = e / N, x = e - g * N;
+    const int g = fN.div(e), x = e - g * N;
     const int ra = row0 + 2 * g, rb = ra + 1;
     const T2 v = sm[g * TSg + fpad(dct ? dct_pos(x, N) : x)];
     if (ra < N) dst[(size_t)ra * N + x] = v.x;
