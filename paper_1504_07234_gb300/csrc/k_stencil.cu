@@ -50,6 +50,58 @@ __device__ __forceinline__ bool skip(const State& st, int pcg) {
   return st.stopped || (pcg && st.pdone);
 }
 
+// acc[j] += sum_t w[t] v[t + j] over a run of len taps, v[i] = base[i * stride]:
+// an 8-value window of v kept as a ring (slot (i & 7) holds v[i]), unrolled by
+// 8 so that every register index is static
+template <typename T>
+__device__ __forceinline__ void window_run(T (&acc)[8], const T* __restrict__ base, int stride,
+                                           const T* __restrict__ w, int len) {
+  T win[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) win[j] = base[j * stride];
+  for (int t0 = 0; t0 < len; t0 += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (t0 + u < len) {
+        const T wt = w[t0 + u];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += wt * win[(j + u) & 7];
+        // slot u held v[t0 + u], needed by no later tap: refill with v[t0 + u + 8]
+        if (t0 + u + 1 < len) win[u] = base[(t0 + u + 8) * stride];
+      }
+    }
+  }
+}
+
+// Table 1 map for an extended index within one period of the image (the
+// common case), else the general map
+__device__ __forceinline__ int bc_map_near(int e, int n, int bc) {
+  if (e >= 0 && e < n) return e;
+  if (e >= -n && e < 2 * n) {
+    if (bc == BC_ZERO) return -1;
+    if (bc == BC_PERIODIC) return e < 0 ? e + n : e - n;
+    return e < 0 ? -1 - e : 2 * n - 1 - e;
+  }
+  return bc_map(e, n, bc);
+}
+
+// Stencil tile geometry: 32 x 32 outputs per CTA of 128 threads, 8 outputs
+// per thread held in registers.  The input tile (32 + p - 1)^2 lives in
+// shared memory with a row pitch of 1 mod 32 words.
+__host__ __device__ constexpr int st_pitch(int R) { return R + ((33 - R % 32) % 32); }
+
+// Blur A (Eq. 2 with the Table 1 boundary conditions, or the valid part for
+// rectangular A) and the full correlation that A^T is built from, as
+// register-window stencils:
+//  - general PSF: the taps are grouped by PSF column b into dense runs
+//    [lo_b, hi_b] of rows; a thread owns 8 consecutive outputs of one column
+//    and slides an 8-value window of the input column down the run, so each
+//    tap costs one shared load of the input, one (broadcast) weight and 8 FMAs;
+//  - rank-one PSF (h = hy hx^T): a horizontal pass with an 8-value window along
+//    the rows into shared memory, then a vertical pass with a window along the
+//    columns.
+// Forward (A f)(y, x) = sum_{a,b} H[a][b] f_ext(y + c - a, x + c - b); the
+// correlation (ne x ne) is sum_{a,b} H[a][b] t(y - 2c + a, x - 2c + b).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(STENCIL_THREADS)
 k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
@@ -62,41 +114,50 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   if (skip(st, pcg)) return;
 
   constexpr bool CORR = (MODE == ST_CORR);
+  constexpr int NT = STENCIL_THREADS;
   const int n = pd.n, p = pd.p, c = pd.c;
   const int outN = CORR ? pd.ne : n;
   const int tilesX = (outN + 31) >> 5;
   const int ty0 = (item.y / tilesX) * 32, tx0 = (item.y % tilesX) * 32;
   const int R = 32 + p - 1;
-  const int ntaps = pd.sep ? 0 : pd.ntaps;
+  const int RP = st_pitch(R);
+  const bool sep = pd.sep != 0;
 
-  T* s_w = reinterpret_cast<T*>(smraw);          // ntaps weights (or 2p separable)
-  const int nw = pd.sep ? 2 * p : ntaps;
-  T* s_in = s_w + ((nw + 1) & ~1);               // R x R input region
-  T* s_tmp = s_in + R * R;                        // R x 32 (separable)
-  int* s_off = reinterpret_cast<int*>(s_tmp + (pd.sep ? R * 32 : 0));
+  // shared memory: weights, column runs (general PSF), input tile, row-pass
+  // tile (rank-one PSF, pitch 33)
+  const int nw = sep ? 2 * p : pd.nrw;
+  T* s_w = reinterpret_cast<T*>(smraw);
+  int4* s_runs = reinterpret_cast<int4*>(s_w + ((nw + 3) & ~3));
+  T* s_in = reinterpret_cast<T*>(s_runs + (sep ? 0 : pd.nruns));
+  T* s_tmp = s_in + R * RP;
 
   // src_slot < 0: the per-problem default operand (t, or r for P = I, in the
   // correlation; A^T p for the PCG product: V for rectangular A, U otherwise)
   if (src_slot < 0)
     src_slot = CORR ? (pd.precond == P_NONE ? SL_R : SL_T) : (pd.bc == BC_RECT ? SL_V : SL_U);
   const T* src = static_cast<const T*>(pd.buf[src_slot]);
-  // taps
-  if (pd.sep) {
+  // weights in the order the windows consume them: the forward stencil runs
+  // over the reversed PSF
+  if (sep) {
     const T* hy = static_cast<const T*>(pd.hy);
     const T* hx = static_cast<const T*>(pd.hx);
-    for (int k = threadIdx.x; k < p; k += blockDim.x) { s_w[k] = hy[k]; s_w[p + k] = hx[k]; }
+    for (int k = threadIdx.x; k < p; k += NT) {
+      s_w[k] = CORR ? hx[k] : hx[p - 1 - k];
+      s_w[p + k] = CORR ? hy[k] : hy[p - 1 - k];
+    }
   } else {
     const T* tw = static_cast<const T*>(pd.tap_w);
-    for (int k = threadIdx.x; k < ntaps; k += blockDim.x) {
-      s_w[k] = tw[k];
-      const int dy = pd.tap_dy[k], dx = pd.tap_dx[k];
-      s_off[k] = CORR ? (c + dy) * R + (c + dx) : (c - dy) * R + (c - dx);
+    for (int k = threadIdx.x; k < pd.nruns; k += NT) s_runs[k] = pd.tap_runs[k];
+    for (int k = threadIdx.x; k < pd.nruns; k += NT) {
+      const int4 rn = pd.tap_runs[k];
+      const int len = rn.z - rn.y + 1;
+      for (int t = 0; t < len; ++t) s_w[rn.w + t] = CORR ? tw[rn.w + t] : tw[rn.w + len - 1 - t];
     }
   }
   // input region
   const int oy0 = CORR ? ty0 - 2 * c : ty0 - c;
   const int ox0 = CORR ? tx0 - 2 * c : tx0 - c;
-  for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < R * R; idx += NT) {
     const int ry = idx / R, rx = idx - ry * R;
     const int ey = oy0 + ry, ex = ox0 + rx;
     T v = T(0);
@@ -106,65 +167,76 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
       const int my = ey + c, mx = ex + c;
       if (my >= 0 && my < pd.nf && mx >= 0 && mx < pd.nf) v = src[(size_t)my * pd.nf + mx];
     } else {
-      const int iy = bc_map(ey, n, pd.bc), ix = bc_map(ex, n, pd.bc);
+      const int iy = bc_map_near(ey, n, pd.bc), ix = bc_map_near(ex, n, pd.bc);
       if (iy >= 0 && ix >= 0) v = src[(size_t)iy * n + ix];
     }
-    s_in[idx] = v;
+    s_in[ry * RP + rx] = v;
   }
   __syncthreads();
-  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;   // 32 x 8 threads
-  if (pd.sep) {
-    // horizontal pass over all R rows, then vertical
-    for (int ry = ly; ry < R; ry += 8) {
-      T acc = T(0);
-      for (int k = 0; k < p; ++k) {
-        const int dx = k - c;
-        acc += s_w[p + k] * s_in[ry * R + lx + (CORR ? c + dx : c - dx)];
-      }
-      s_tmp[ry * 32 + lx] = acc;
+  // this thread's outputs: column x, rows y8 .. y8 + 7 of the tile
+  const int x = threadIdx.x & 31, y8 = (threadIdx.x >> 5) * 8;
+  T acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = T(0);
+  if (sep) {
+    // row pass over all R rows: tmp(ry, xx) = sum_t wx[t] in(ry, xx + t)
+    for (int idx = threadIdx.x; idx < 4 * R; idx += NT) {
+      const int ry = idx >> 2, x8 = (idx & 3) * 8;
+      T h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = T(0);
+      window_run<T>(h, s_in + ry * RP + x8, 1, s_w, p);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s_tmp[ry * 33 + x8 + j] = h[j];
     }
     __syncthreads();
+    // column pass: out(y, x) = sum_t wy[t] tmp(y + t, x)
+    window_run<T>(acc, s_tmp + y8 * 33 + x, 33, s_w + p, p);
+  } else {
+    // runs of PSF column b over rows lo..hi: input column x + (CORR ? b : 2c - b),
+    // window rows from y8 + (CORR ? lo : 2c - hi)
+    for (int k = 0; k < pd.nruns; ++k) {
+      const int4 rn = s_runs[k];
+      const int len = rn.z - rn.y + 1;
+      const int col = CORR ? x + rn.x : x + 2 * c - rn.x;
+      const int r0 = CORR ? y8 + rn.y : y8 + 2 * c - rn.z;
+      window_run<T>(acc, s_in + r0 * RP + col, RP, s_w + rn.w, len);
+    }
   }
-  double local = 0.0;
   T* dst = static_cast<T*>(pd.buf[dst_slot]);
   const T* aux = static_cast<const T*>(pd.buf[aux_slot]);
   T lacc = T(0);
+  const int gx = tx0 + x;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int oy = ly + 8 * q;
-    T acc = T(0);
-    if (pd.sep) {
-      for (int k = 0; k < p; ++k) {
-        const int dy = k - c;
-        acc += s_w[k] * s_tmp[(oy + (CORR ? c + dy : c - dy)) * 32 + lx];
-      }
-    } else {
-      const T* base = s_in + oy * R + lx;
-      for (int k = 0; k < ntaps; ++k) acc += s_w[k] * base[s_off[k]];
-    }
-    const int gy = ty0 + oy, gx = tx0 + lx;
+  for (int j = 0; j < 8; ++j) {
+    const int gy = ty0 + y8 + j;
     if (gy < outN && gx < outN) {
       const size_t o = (size_t)gy * outN + gx;
       if (MODE == ST_FWD_RESID) {
-        const T r = aux[o] - acc;
+        const T r = aux[o] - acc[j];
         dst[o] = r;
         lacc += r * r;
       } else if (MODE == ST_FWD_PCGQ) {
         const T pv = aux[o];
-        const T qv = acc + T(pd.alpha) * pv;
+        const T qv = acc[j] + T(pd.alpha) * pv;
         dst[o] = qv;
         lacc += pv * qv;
       } else {
-        dst[o] = acc;
+        dst[o] = acc[j];
       }
     }
   }
   if (MODE == ST_FWD_RESID || MODE == ST_FWD_PCGQ) {
-    local = (double)lacc;
-    const double bs = block_sum<STENCIL_THREADS>(local, red);
+    // warp sums in T, then FP64 across warps and blocks
+    for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)lacc;
+    __syncthreads();
+    double vals[1] = {0.0};
+    if (threadIdx.x == 0)
+      for (int w = 0; w < NT / 32; ++w) vals[0] += red[w];
+    __syncthreads();
     double tot[1];
-    const double vals[1] = {bs};
-    if (last_block_reduce<STENCIL_THREADS, 1>(pd, st, item.y, pd.nblk_blur, vals, tot, red)) {
+    if (last_block_reduce<NT, 1>(pd, st, item.y, pd.nblk_blur, vals, tot, red)) {
       if (threadIdx.x == 0) {
         if (MODE == ST_FWD_RESID) {
           finalize_residual(pd, st, tot[0]);

@@ -37,8 +37,8 @@ struct HostProb {
   Prob pd;                       // host copy with device pointers filled in
   std::vector<double> psf;       // p x p, the PSF used by A
   std::vector<double> psf_pre;   // PSF of the preconditioner (H or H~)
-  std::vector<int> dy, dx;
-  std::vector<double> w;
+  std::vector<int> runs;         // (b, lo, hi, offset) per nonzero PSF column
+  std::vector<double> rw;        // packed run weights H[lo..hi][b]
   std::vector<double> hy, hx;
   size_t off[NSLOT + 16];
 };
@@ -305,14 +305,20 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
     // one transform must fit the per-CTA value budget of the smem FFT
     if (n > TR_CAP) return MLBA_E_UNSUPPORTED;
   }
-  // taps
-  for (int a = 0; a < p; ++a)
-    for (int b = 0; b < p; ++b)
-      if (h.psf[a * p + b] != 0.0) {
-        h.dy.push_back(a - pd.c); h.dx.push_back(b - pd.c); h.w.push_back(h.psf[a * p + b]);
-      }
-  if (h.w.empty()) return MLBA_E_INVAL;
-  pd.ntaps = (int)h.w.size();
+  // taps: per PSF column the dense run of rows between its first and last
+  // nonzero entry
+  pd.ntaps = 0;
+  for (int b = 0; b < p; ++b) {
+    int lo = -1, hi = -1;
+    for (int a = 0; a < p; ++a)
+      if (h.psf[a * p + b] != 0.0) { if (lo < 0) lo = a; hi = a; ++pd.ntaps; }
+    if (lo < 0) continue;
+    h.runs.insert(h.runs.end(), {b, lo, hi, (int)h.rw.size()});
+    for (int a = lo; a <= hi; ++a) h.rw.push_back(h.psf[a * p + b]);
+  }
+  if (pd.ntaps == 0) return MLBA_E_INVAL;
+  pd.nruns = (int)h.runs.size() / 4;
+  pd.nrw = (int)h.rw.size();
   pd.sep = rank_one(h.psf, p, h.hy, h.hx) && p > 1 ? 1 : 0;
   // launch geometry
   pd.nblk_blur = ((n + 31) / 32) * ((n + 31) / 32);
@@ -446,7 +452,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         nspec * ts,                            // |lambda|^2 in T precision
         spec ? (size_t)pd.n * 2 * ts : ts,     // tw
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
-        (size_t)pd.ntaps * 4, (size_t)pd.ntaps * 4, (size_t)pd.ntaps * ts,   // taps
+        (size_t)pd.nruns * 16, (size_t)pd.nrw * ts,   // tap runs and weights
         (size_t)pd.p * ts, (size_t)pd.p * ts,  // hy, hx
         std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, (size_t)SPEC_SUMS * pd.nblk_spec, (size_t)1}) * 8,  // partial
         (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 4};
@@ -470,8 +476,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     pd.w = base + of[k++];
     pd.tw = base + of[k++];
     pd.dtw = base + of[k++];
-    pd.tap_dy = reinterpret_cast<int*>(base + of[k++]);
-    pd.tap_dx = reinterpret_cast<int*>(base + of[k++]);
+    pd.tap_runs = reinterpret_cast<int4*>(base + of[k++]);
     pd.tap_w = base + of[k++];
     pd.hy = base + of[k++];
     pd.hx = base + of[k++];
@@ -480,8 +485,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     pd.hist_alpha = reinterpret_cast<double*>(base + of[k++]);
     pd.hist_beta = reinterpret_cast<int*>(base + of[k++]);
     // tables
-    CK(cudaMemcpy(pd.tap_dy, h.dy.data(), h.dy.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(pd.tap_dx, h.dx.data(), h.dx.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pd.tap_runs, h.runs.data(), h.runs.size() * 4, cudaMemcpyHostToDevice));
     std::vector<unsigned char> tmp;
     auto upload = [&](void* dst, const std::vector<double>& v) -> int {
       tmp.assign(v.size() * ts, 0);
@@ -489,7 +493,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
       if (!v.empty()) CK(cudaMemcpy(dst, tmp.data(), tmp.size(), cudaMemcpyHostToDevice));
       return MLBA_OK;
     };
-    if (upload(pd.tap_w, h.w) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
+    if (upload(pd.tap_w, h.rw) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
     if (pd.sep) {
       if (upload(pd.hy, h.hy) != MLBA_OK || upload(pd.hx, h.hx) != MLBA_OK) {
         destroy_batch(B); return MLBA_E_CUDA;
@@ -546,9 +550,12 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
       if (pd.ns) { add(cols_ns, pd.nblk_cols); add(spec, pd.nblk_spec); B->any_ns = 1; }
       else { add(cols_stat, pd.nblk_cols); B->any_stat = 1; }
     }
+    // stencil: weights (padded to 16 bytes), runs, input tile, row-pass tile
     const size_t R = 32 + pd.p - 1;
-    const size_t nw = pd.sep ? 2 * pd.p : pd.ntaps;
-    const size_t st_b = (((nw + 1) & ~(size_t)1) + R * R + (pd.sep ? R * 32 : 0)) * ts + (pd.sep ? 0 : pd.ntaps * 4);
+    const size_t RP = R + (33 - R % 32) % 32;
+    const size_t nw = pd.sep ? 2 * pd.p : pd.nrw;
+    const size_t st_b = (((nw + 3) & ~(size_t)3) + R * RP + (pd.sep ? R * 33 : 0)) * ts +
+                        (pd.sep ? 0 : (size_t)pd.nruns * 16);
     smem_st = std::max(smem_st, st_b);
     if (specp) {
       const size_t fb = (size_t)std::max(pd.row_g, pd.col_g) * (fft_pad(pd.n) + 1) * 2 * ts;

@@ -43,6 +43,7 @@ struct Prob {
   int use_adj;       // 1: u = A^T t ; 0: u = t (Algorithm 4 forms)
   int sep;           // rank-one PSF: separable stencils
   int ntaps;         // nonzero taps of the PSF
+  int nruns, nrw;    // PSF column runs and their packed weights (general PSF)
   int max_iter, stop, pcg_max;
   int nstage;        // FFT plan of length n
   int radix[MAX_STAGES];
@@ -61,7 +62,8 @@ struct Prob {
   void* lam;         // spectrum of C (real for DCT, complex half for DFT), T, blocked
   void* tw;          // exp(-2 pi i k/n), k < n   (T2)
   void* dtw;         // exp(-i pi k/(2n)), k < n  (T2)
-  int* tap_dy; int* tap_dx; void* tap_w;   // nonzero taps (offsets from centre)
+  int4* tap_runs;     // per nonzero PSF column b: (b, lo, hi, offset of H[lo..hi][b] in tap_w)
+  void* tap_w;        // packed run weights, T precision
   void* hy; void* hx;                      // separable factors (length p)
   double* partial;   // reduction partials (capacity per problem)
   double* hist_res; double* hist_alpha; int* hist_beta;  // history, max_iter+2

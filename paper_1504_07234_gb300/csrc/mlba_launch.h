@@ -31,7 +31,7 @@ enum {
 };
 enum { W_INV = 0, W_TIKH = 1 };
 
-constexpr int STENCIL_THREADS = 256;
+constexpr int STENCIL_THREADS = 128;
 constexpr int VEC_THREADS = 256;
 constexpr int VEC_PER_THREAD = 8;
 constexpr int TR_CAP = 4096;          // complex values held by one transform CTA
