@@ -288,7 +288,7 @@ def main():
     achieved = fb / (stage_ms["frame"] / 1e3) / 1e9
     khash = src_hash("k_frame.cu")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": ncu_traffic(khash), "kernel": "k_frame2<float,float,2>",
+                "frac": achieved / hbm, "traffic": ncu_traffic(khash), "kernel": "k_frame3<float,float,2>",
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": fb}
     bmin = step_min_bytes(probs)
     step_frac = bmin / (ms_step / 1e3) / 1e9 / hbm
