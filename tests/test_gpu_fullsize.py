@@ -1,0 +1,168 @@
+"""GPU parity at the full sizes of the measured workloads, in the launch
+configuration the benchmark times (FP32, L = 2, one graph launch per step).
+
+- The 64-problem batch (sizes up to 1024^2): the whole batch advances
+  together; sampled problems of every kind (periodic / reflective 4-NS,
+  rectangular Algorithm 1, Algorithm 3, smallest and largest sizes) are
+  compared with the FP64 oracle run on its own for the same iterations.
+- 1024^2 rectangular motion blur (Rect1 / Rect2 / Rect3, FP32 and BF16 z):
+  a few iterations against the oracle.
+- 4096^2 rectangular Gaussian with the nonstationary alpha_n (hybrid): the
+  oracle's full loop is far too slow at this size, so the first iterate is
+  checked on sampled windows the oracle computes one by one.  Everything in
+  f^1 = W^T S_mu(W A^T (CC^T + alpha_0 I)^{-1} g) is local except the
+  preconditioner and alpha_0, which the oracle computes on the whole image
+  with library transforms; A^T and the framelets run on windows with a
+  margin wider than their reach (A^T: 2c, one framelet step: 6 pixels).
+  The forward blur is checked the same way on a random image.
+"""
+import numpy as np
+import pytest
+
+import mlba_inputs as I
+from oracle import mlba_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1504_07234_gb300.build import build
+    build()
+    import paper_1504_07234_gb300 as mod
+    return mod
+
+
+def oracle_run(pr, iters):
+    return O.mlba(pr.g, pr.psf, pr.delta, pr.bc, pr.precond, pr.mu, pr.alpha, pr.levels, iters,
+                  stop=False, gamma=pr.gamma, q=pr.q, rho=pr.rho, transform=pr.transform,
+                  rect_ns_hybrid=pr.rect_ns_hybrid)
+
+
+def test_batch64_full_size_sampled(M):
+    import bench
+    probs = bench.problems_for_rank(0)
+    iters = 3
+    b = M.Batch(bench.descs(probs), dtype="f32", levels=2, stop=False, max_iter=iters,
+                rect_ns_hybrid=True)
+    b.iterate(iters + 1)
+    # one problem of each kind, the smallest and the largest sizes
+    kinds = {}
+    for i, p in enumerate(probs):
+        kinds.setdefault((p.bc, p.precond), []).append(i)
+    sample = {max(ix, key=lambda i: probs[i].n) for ix in kinds.values()}
+    sample.add(min(range(len(probs)), key=lambda i: probs[i].n))
+    for i in sorted(sample):
+        p = probs[i]
+        ref = oracle_run(p, iters)
+        st = b.stats(i)
+        assert st["iter"] == iters, (i, st)
+        f = b.result(i).astype(np.float64)
+        scale = np.abs(ref["f"]).max()
+        assert np.abs(f - ref["f"]).max() <= 1e-4 * scale, (i, p.n, p.bc, p.precond)
+        np.testing.assert_allclose(st["resnorm"], ref["resnorms"][-1], rtol=1e-5)
+        if p.precond == "tikh_ns":
+            np.testing.assert_allclose(st["alpha_n"], ref["alphas"][-1], rtol=1e-4)
+    b.close()
+
+
+@pytest.mark.parametrize("variant,z_store", [("rect1", None), ("rect2", None), ("rect3", None),
+                                             ("rect1", "bf16")])
+def test_config3_full_size(M, variant, z_store):
+    """1024^2 rectangular, 21x21 motion blur, L = 2: FP32 (and BF16 z) against
+    the FP64 oracle after a few iterations."""
+    pr = I.config(3, variant=variant)
+    iters = 2 if variant == "rect2" else 3
+    ctx = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype="f32", z_store=z_store, mu=pr.mu,
+                    alpha=pr.alpha, levels=pr.levels, max_iter=iters, stop=False, gamma=pr.gamma,
+                    q=pr.q, rho=pr.rho, transform=pr.transform)
+    ctx.set_data(pr.g, pr.delta)
+    ctx.run(iters)
+    f = ctx.result().astype(np.float64)
+    res, al, be = ctx.history()
+    ctx.close()
+    ref = oracle_run(pr, iters)
+    scale = np.abs(ref["f"]).max()
+    # BF16 z keeps 8 significant bits per coefficient: unit roundoff 2^-8
+    tol = 1e-4 if z_store is None else 1e-2
+    assert np.abs(f - ref["f"]).max() <= tol * scale
+    np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-5 if z_store is None else 2.0 ** -8)
+    if variant == "rect2":
+        assert list(be) == ref["betas"]
+
+
+def _spectrum_dct_windowed(h, n):
+    """The oracle's DCT eigenvalues, dct2(A e1) ./ dct2(e1), with A e1 formed on
+    a 2p x 2p corner: e1 and its reflective extension are supported within
+    the PSF radius of the corner, so the far edges do not enter (n >= 2p)."""
+    from scipy import fft as sfft
+    p = h.shape[0]
+    m = 2 * p
+    e = np.zeros((m, m))
+    e[0, 0] = 1.0
+    corner = O.blur(e, h, "reflective")[:p, :p]
+    a_e1 = np.zeros((n, n))
+    a_e1[:p, :p] = corner
+    e1 = np.zeros((n, n))
+    e1[0, 0] = 1.0
+    return sfft.dctn(a_e1, type=2, norm="ortho") / sfft.dctn(e1, type=2, norm="ortho")
+
+
+def test_config5_first_iterate_windows(M):
+    """4096^2 rectangular, 31x31 Gaussian, NS alpha (hybrid), L = 2, FP32."""
+    pr = I.config(5)
+    n, h = pr.n, pr.psf
+    p = h.shape[0]
+    c = (p - 1) // 2
+    nf = n + p - 1
+    ctx = M.Context(h, n, "rect", "tikh_ns", dtype="f32", mu=pr.mu, alpha=pr.alpha, levels=2,
+                    max_iter=1, stop=False, gamma=pr.gamma, q=pr.q, rho=pr.rho, transform="dct",
+                    rect_ns_hybrid=True)
+    ctx.set_data(pr.g, pr.delta)
+    ctx.run(1)
+    f1 = ctx.result().astype(np.float64)
+    res, al, _ = ctx.history()
+    # forward blur of a random image on the same context
+    rng = np.random.default_rng(55)
+    fr = rng.random((nf, nf)).astype(np.float32)
+    af = ctx.blur(fr).astype(np.float64)
+    ctx.close()
+
+    # whole-image pieces: ||r^0|| = ||g||, alpha_0, t = (CC^T + alpha_0 I)^{-1} g
+    g = pr.g.astype(np.float64)
+    rn = float(np.linalg.norm(g))
+    np.testing.assert_allclose(res[0], rn, rtol=1e-5)
+    lam = _spectrum_dct_windowed(h, n)
+    sigma = lam ** 2
+    from scipy import fft as sfft
+    ghat = sfft.dctn(g, type=2, norm="ortho")
+    qn = O.ns_qn(rn, pr.delta, pr.q, pr.rho)
+    a0 = max(O.ns_alpha(ghat ** 2, sigma, qn), pr.alpha)
+    np.testing.assert_allclose(al[0], a0, rtol=1e-4)
+    t = sfft.idctn(ghat / (sigma + a0), type=2, norm="ortho")
+
+    w, mg = 64, 8
+    for (y0, x0) in [(0, 0), (1900, 2300), (nf - w, nf - w)]:
+        # u = A^T t on [u0, u1)^2 needs t on [u0 - 2c, u1) (zero outside the image)
+        u0y, u1y = max(0, y0 - mg), min(nf, y0 + w + mg)
+        u0x, u1x = max(0, x0 - mg), min(nf, x0 + w + mg)
+        assert u1y - u0y == u1x - u0x            # square windows for the framelets
+        t0y, t1y = max(0, u0y - 2 * c), min(n, u1y)
+        t0x, t1x = max(0, u0x - 2 * c), min(n, u1x)
+        tc = np.zeros((u1y - u0y + 2 * c, u1x - u0x + 2 * c))
+        tc[t0y - (u0y - 2 * c):t1y - (u0y - 2 * c), t0x - (u0x - 2 * c):t1x - (u0x - 2 * c)] = \
+            t[t0y:t1y, t0x:t1x]
+        # the full correlation of the padded crop; its entries 2c.. are the
+        # global u on [u0, u1)
+        uc = O.blur_adjoint(tc, h, "rect")[2 * c:2 * c + (u1y - u0y), 2 * c:2 * c + (u1x - u0x)]
+        # framelet step on the window: exact where the window edge is the image
+        # edge (same half-sample reflection), and at least 6 pixels inside elsewhere
+        fw = O.framelet_synthesis(O.soft(O.framelet_analysis(uc, 2), pr.mu), 2)
+        sy, sx = y0 - u0y, x0 - u0x
+        ref = fw[sy:sy + w, sx:sx + w]
+        got = f1[y0:y0 + w, x0:x0 + w]
+        assert np.abs(got - ref).max() <= 1e-4 * max(np.abs(ref).max(), 1e-30), (y0, x0)
+        # forward blur: valid convolution of the (w + p - 1)^2 crop of f
+        if y0 + w <= n and x0 + w <= n:
+            ref_a = O.blur(fr[y0:y0 + w + p - 1, x0:x0 + w + p - 1].astype(np.float64), h, "rect")
+            assert np.abs(af[y0:y0 + w, x0:x0 + w] - ref_a).max() <= 1e-5 * np.abs(ref_a).max()
