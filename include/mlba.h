@@ -118,8 +118,13 @@ typedef struct mlba_stats {
 /* ---- single problem --------------------------------------------------- */
 typedef struct mlba_ctx mlba_ctx;
 
+/* Largest PSF side accepted by mlba_create / mlba_batch_create (the stencil
+ * tile holds 32 + p - 1 < 96 columns). */
+#define MLBA_MAX_P 65
+
 /* Create a context for one problem.  psf: host, p*p doubles, row-major,
- * nonnegative; the library copies it.  n: observed size (n >= p).
+ * nonnegative; the library copies it.  n: observed size (n >= p); p odd and
+ * at most MLBA_MAX_P (else MLBA_E_UNSUPPORTED).
  * Validates the combination (Algorithm 4 needs a square A, Section 5), builds
  * the PSF tap list and its rank-one test, the FFT plans for length n and the
  * spectrum of C / Q in FP64 on the device (Section 4.1, 4.3), allocates all

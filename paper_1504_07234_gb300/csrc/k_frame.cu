@@ -750,12 +750,13 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   for (int k = 0; k < 2 * D; ++k) hrow(yc0 - D + k, hr[k]);
   // z queue: rows y .. y + PF - 1
   TZ zq[F3_PF][NB];
+  // (idle lanes load a valid mirrored column too; their values are unused.
+  // Offsets stay in 32 bits: nbands nf^2 < 2^31.)
   auto zload = [&](int y, TZ (&q)[NB]) {
     bool par;
-    const int ro = f3_refl(y, nf, &par) * nf;
-    const TZ* zp = zin + (ro + zc);
+    const int ro = f3_refl(y, nf, &par) * nf + zc;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) q[b] = act ? zp[boff[b]] : TZ(0.0f);
+    for (int b = 0; b < NB; ++b) q[b] = zin[ro + boff[b]];
   };
 #pragma unroll
   for (int k = 0; k < F3_PF; ++k) zload(yc0 + k, zq[k]);
@@ -777,7 +778,7 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
     const T srow = pry ? T(-1) : T(1);
     const T s11 = srow * scol;
     const bool own = own_c && y >= seg_lo && y < seg_hi && y < nf;
-    TZ* zw = zout + (zro + zc);
+    const int zwo = zro + zc;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int k = K0 + b, i = k % 3, j = k / 3;
@@ -789,7 +790,7 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
       const T zv = T(ld_z(&q[b]));
       const T zn = (i == 1 && j == 1) ? fma(zv, s11, a)
                  : (i == 1) ? fma(zv, srow, a) : (j == 1) ? fma(zv, scol, a) : zv + a;
-      if (own) st_z(zw + boff[b], zn);
+      if (own) st_z(zout + (zwo + boff[b]), zn);
       const T xv = zn - fmin(fmax(zn, -mu), mu);     // S_mu
       pr[0][j] += bi0 * xv;
       if (i != 1) pr[D][j] += bi1 * xv;

@@ -51,26 +51,51 @@ __device__ __forceinline__ bool skip(const State& st, int pcg) {
 }
 
 // acc[j] += sum_t w[t] v[t + j] over a run of len taps, v[i] = base[i * stride]:
-// an 8-value window of v kept as a ring (slot (i & 7) holds v[i]), unrolled by
-// 8 so that every register index is static
+// an 8-value window of v.  Whole groups of 8 taps keep the window as a ring
+// (slot (i & 7) holds v[i]) so every register index is static and no value
+// moves; after them the ring is aligned again (slot j holds v[t + j]) and the
+// last len % 8 taps shift the window instead, so that short runs (thin PSFs)
+// issue no predicated-off work.
 template <typename T>
 __device__ __forceinline__ void window_run(T (&acc)[8], const T* __restrict__ base, int stride,
                                            const T* __restrict__ w, int len) {
   T win[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) win[j] = base[j * stride];
-  for (int t0 = 0; t0 < len; t0 += 8) {
+  int t = 0;
+  for (; t + 8 <= len; t += 8) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      if (t0 + u < len) {
-        const T wt = w[t0 + u];
+      const T wt = w[t + u];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] += wt * win[(j + u) & 7];
-        // slot u held v[t0 + u], needed by no later tap: refill with v[t0 + u + 8]
-        if (t0 + u + 1 < len) win[u] = base[(t0 + u + 8) * stride];
-      }
+      for (int j = 0; j < 8; ++j) acc[j] += wt * win[(j + u) & 7];
+      // slot u held v[t + u], needed by no later tap: refill with v[t + u + 8]
+      if (t + u + 1 < len) win[u] = base[(t + u + 8) * stride];
     }
   }
+  for (; t < len; ++t) {
+    const T wt = w[t];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] += wt * win[j];
+    if (t + 1 < len) {
+#pragma unroll
+      for (int j = 0; j < 7; ++j) win[j] = win[j + 1];
+      win[7] = base[(t + 8) * stride];
+    }
+  }
+}
+
+// asynchronous global -> shared copy of one 4- or 8-byte element; !valid
+// writes zeros (0 source bytes)
+template <int B>
+__device__ __forceinline__ void cp_async_zfill(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int src_bytes = valid ? B : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"(B),
+               "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // Table 1 map for an extended index within one period of the image (the
@@ -157,20 +182,36 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   // input region
   const int oy0 = CORR ? ty0 - 2 * c : ty0 - c;
   const int ox0 = CORR ? tx0 - 2 * c : tx0 - c;
-  for (int idx = threadIdx.x; idx < R * R; idx += NT) {
-    const int ry = idx / R, rx = idx - ry * R;
-    const int ey = oy0 + ry, ex = ox0 + rx;
-    T v = T(0);
-    if (CORR) {
-      if (ey >= 0 && ey < n && ex >= 0 && ex < n) v = src[(size_t)ey * n + ex];
-    } else if (pd.bc == BC_RECT) {
-      const int my = ey + c, mx = ex + c;
-      if (my >= 0 && my < pd.nf && mx >= 0 && mx < pd.nf) v = src[(size_t)my * pd.nf + mx];
-    } else {
-      const int iy = bc_map_near(ey, n, pd.bc), ix = bc_map_near(ex, n, pd.bc);
-      if (iy >= 0 && ix >= 0) v = src[(size_t)iy * n + ix];
+  // asynchronous copies straight into shared memory (no registers held, all
+  // of a thread's copies in flight together); positions outside the source
+  // are zero-filled by a copy of 0 source bytes.  One warp per row, lanes
+  // along the row (R <= 32 + MLBA_MAX_P - 1 < 96: three column passes at
+  // most); the row's source index is mapped once.
+  {
+    const int lane = threadIdx.x & 31;
+    const int pitch = (!CORR && pd.bc == BC_RECT) ? pd.nf : n;
+    for (int ry = threadIdx.x >> 5; ry < R; ry += NT / 32) {
+      const int ey = oy0 + ry;
+      int sy;
+      if (CORR) sy = (ey >= 0 && ey < n) ? ey : -1;
+      else if (pd.bc == BC_RECT) sy = (ey + c >= 0 && ey + c < pd.nf) ? ey + c : -1;
+      else sy = bc_map_near(ey, n, pd.bc);
+      const T* row = src + (size_t)(sy < 0 ? 0 : sy) * pitch;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int rx = lane + 32 * k;
+        if (rx < R) {
+          const int ex = ox0 + rx;
+          int sx;
+          if (CORR) sx = (ex >= 0 && ex < n) ? ex : -1;
+          else if (pd.bc == BC_RECT) sx = (ex + c >= 0 && ex + c < pd.nf) ? ex + c : -1;
+          else sx = bc_map_near(ex, n, pd.bc);
+          const bool ok = sy >= 0 && sx >= 0;
+          cp_async_zfill<sizeof(T)>(s_in + ry * RP + rx, row + (ok ? sx : 0), ok);
+        }
+      }
     }
-    s_in[ry * RP + rx] = v;
+    cp_async_wait_all();
   }
   __syncthreads();
   // this thread's outputs: column x, rows y8 .. y8 + 7 of the tile

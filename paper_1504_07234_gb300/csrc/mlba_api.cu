@@ -256,6 +256,7 @@ void destroy_batch(mlba_batch* B) {
 int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   const int p = in.p, n = in.n;
   if (!in.psf || p < 1 || (p % 2) == 0 || n < p || n < 2) return MLBA_E_INVAL;
+  if (p > MLBA_MAX_P) return MLBA_E_UNSUPPORTED;
   if (in.bc < 0 || in.bc > 3 || in.precond < 0 || in.precond > 5) return MLBA_E_INVAL;
   if (o.levels < 1 || o.levels > 4) return MLBA_E_INVAL;
   if (!(in.delta >= 0.0) || !(in.mu >= 0.0)) return MLBA_E_INVAL;

@@ -66,3 +66,6 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert lib.mlba_create(psf.ctypes.data_as(ctypes.c_void_p), 5, 4, 1, 1, ctypes.byref(o), ctypes.byref(h)) == -1
     assert lib.mlba_create(psf.ctypes.data_as(ctypes.c_void_p), 5, 16, 3, 4, ctypes.byref(o), ctypes.byref(h)) == -1
     assert lib.mlba_create(psf.ctypes.data_as(ctypes.c_void_p), 5, 16, 3, 5, ctypes.byref(o), ctypes.byref(h)) == -1
+    # a PSF wider than the stencil tile supports is refused, also before any device work
+    big = np.full((67, 67), 1 / 67.0 ** 2)
+    assert lib.mlba_create(big.ctypes.data_as(ctypes.c_void_p), 67, 128, 1, 1, ctypes.byref(o), ctypes.byref(h)) == -7
