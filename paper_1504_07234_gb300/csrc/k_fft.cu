@@ -715,14 +715,32 @@ template <int NT, int K, typename A>
 __device__ bool ns_reduce(const Prob& pd, State& st, int blk, int nblk, A (&v)[K],
                           double* sh, double* tot) {
   constexpr int NW = NT / 32;
+  constexpr unsigned FULL = 0xffffffffu;
   __shared__ int is_last;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if constexpr (K >= 32) {
+    // values 0..31: reduce-scatter across the warp (31 exchanges instead of
+    // 160): at each halving a lane keeps the half of its values selected by
+    // its lane bit and adds its partner's copy; lane l ends with value l
 #pragma unroll
-  for (int k = 0; k < K; ++k)
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    for (int o = 16; o > 0; o >>= 1) {
+      const bool hi = (l & o) != 0;
+#pragma unroll
+      for (int i = 0; i < o; ++i) {
+        const A send = hi ? v[i] : v[i + o];
+        const A keep = hi ? v[i + o] : v[i];
+        v[i] = keep + __shfl_xor_sync(FULL, send, o);
+      }
+    }
+    sh[l * NW + w] = (double)v[0];
+  }
+  constexpr int K0 = (K >= 32) ? 32 : 0;
+#pragma unroll
+  for (int k = K0; k < K; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
   if (l == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) sh[k * NW + w] = (double)v[k];
+    for (int k = K0; k < K; ++k) sh[k * NW + w] = (double)v[k];
   }
   __syncthreads();
   if (threadIdx.x < K) {
@@ -815,13 +833,13 @@ k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const in
     }
   }
   T v[K];
-  v[0] = sP;
 #pragma unroll
-  for (int j = 0; j < NS_CAND; ++j) { v[1 + j] = T(cF[j]); v[1 + NS_CAND + j] = T(cG[j]); }
+  for (int j = 0; j < NS_CAND; ++j) { v[j] = T(cF[j]); v[NS_CAND + j] = T(cG[j]); }
+  v[2 * NS_CAND] = sP;
   if (ns_reduce<NS_NT, K, T>(pd, st, item.y, pd.nblk_spec, v, red, tot) && threadIdx.x == 0) {
-    const double P = tot[0], target = st.qn * st.qn;
-    auto hv = [&](int j) { return P > 0.0 ? tot[1 + j] / P - target : 0.0; };
-    auto dv = [&](int j) { return P > 0.0 ? 2.0 * tot[1 + NS_CAND + j] / P : 0.0; };
+    const double P = tot[2 * NS_CAND], target = st.qn * st.qn;
+    auto hv = [&](int j) { return P > 0.0 ? tot[j] / P - target : 0.0; };
+    auto dv = [&](int j) { return P > 0.0 ? 2.0 * tot[NS_CAND + j] / P : 0.0; };
     auto bv = [&](int j) { return b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP; };
     int j = 0;
     while (j < NS_CAND && !(hv(j) >= 0.0)) ++j;
