@@ -327,321 +327,6 @@ __device__ __forceinline__ bool tr_skip(const State& st, int pcg) {
 }
 
 // ---------------------------------------------------------------------------
-// Pass 1: forward transform of row pairs: src (n x n real) -> S
-template <typename T>
-__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
-k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-           int src_slot, int pcg) {
-  using T2 = typename Vec2<T>::type;
-  constexpr int NT = tr_nt(sizeof(T)), MAXV = TR_CAP / NT;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T2* sm = reinterpret_cast<T2*>(smraw);
-  const int2 item = items[blockIdx.x];
-  const Prob& pd = probs[item.x];
-  if (tr_skip(states[item.x], pcg)) return;
-  const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
-  const int pair0 = item.y * G;
-  const int row0 = 2 * pair0;
-  const bool dct = (pd.transform == TR_DCT);
-  const T* src = static_cast<const T*>(pd.buf[src_slot]);
-  const FastDiv fN(N);
-  {
-    // all loads of this thread first (up to MAXV in flight), then the stores
-    T2 tmp[MAXV];
-#pragma unroll
-    for (int q = 0; q < MAXV; ++q) {
-      const int e = threadIdx.x + q * NT;
-      if (e < G * N) {
-        const int g = fN.div(e), x = e - g * N;
-        const int ra = row0 + 2 * g, rb = ra + 1;
-        const int xs = dct ? dct_src(x, N) : x;
-        tmp[q].x = (ra < N) ? src[(size_t)ra * N + xs] : T(0);
-        tmp[q].y = (rb < N) ? src[(size_t)rb * N + xs] : T(0);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < MAXV; ++q) {
-      const int e = threadIdx.x + q * NT;
-      if (e < G * N) { const int g = fN.div(e), x = e - g * N; sm[g * TSg + fpad(x)] = tmp[q]; }
-    }
-  }
-  __syncthreads();
-  fft_smem<T2, false>(G, pd);
-  if (dct) dct_split<T, T2>(sm, G, N, TSg, static_cast<const T2*>(pd.dtw));
-  // write the rows of this CTA into every column block (contiguous runs)
-  const int W = dct ? N : pd.half;
-  const int cb = pd.cb;
-  const int R2 = 2 * G;
-  const int nb = (W + cb - 1) / cb;
-  const FastDiv frc(R2 * cb), fcb(cb);
-  for (int e = threadIdx.x; e < nb * R2 * cb; e += NT) {
-    const int b = frc.div(e), rem = e - b * (R2 * cb);
-    const int rl = fcb.div(rem), c = rem - rl * cb;
-    const int k = b * cb + c, row = row0 + rl;
-    if (k >= W || row >= N) continue;
-    const T2* tb = sm + (rl >> 1) * TSg;
-    const size_t o = (size_t)b * N * cb + (size_t)row * cb + c;
-    if (dct) {
-      const T2 X = tb[fpad(k)];
-      static_cast<T*>(pd.buf[SL_S])[o] = (rl & 1) ? X.y : X.x;
-    } else {
-      const T2 Z = tb[fpad(k)];
-      const T2 Zr = tb[fpad(k == 0 ? 0 : N - k)];
-      T2 X;
-      if (rl & 1) { X.x = T(0.5) * (Z.y + Zr.y); X.y = T(-0.5) * (Z.x - Zr.x); }   // (Z - conj Zr)/(2i)
-      else { X.x = T(0.5) * (Z.x + Zr.x); X.y = T(0.5) * (Z.y - Zr.y); }           // (Z + conj Zr)/2
-      static_cast<T2*>(pd.buf[SL_S])[o] = X;
-    }
-  }
-}
-
-// spectral weight at blocked index idx; alpha and kind as given.  |lambda|^2 +
-// alpha is formed in T: alpha > 0 keeps it away from zero (no cancellation),
-// so FP32 holds it to 6e-8 relative; 1/n^2 of the unnormalised pair is folded in.
-// scale / (|lambda|^2 + alpha): the fast reciprocal-based quotient in FP32
-// (within 2 ulp), the exact one in FP64
-__device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
-
-template <typename T, typename T2>
-__device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
-  const T inv = wdiv(scale, static_cast<const T*>(pd.w)[idx] + alpha);
-  T2 w;
-  if (kind == W_TIKH) {
-    const T2 l = static_cast<const T2*>(pd.lam)[idx];
-    w.x = l.x * inv; w.y = -l.y * inv;
-  } else { w.x = inv; w.y = T(0); }
-  return w;
-}
-template <typename T>
-__device__ __forceinline__ T weight_dct(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
-  const T inv = wdiv(scale, static_cast<const T*>(pd.w)[idx] + alpha);
-  return kind == W_TIKH ? static_cast<const T*>(pd.lam)[idx] * inv : inv;
-}
-
-// Pass 2: one column block per CTA.  DFT: cb complex columns; DCT: cb real
-// columns = cb/2 packed pairs.
-template <typename T>
-__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
-k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-       int mode, int pcg, double op_alpha, int op_kind) {
-  using T2 = typename Vec2<T>::type;
-  constexpr int NT = tr_nt(sizeof(T)), MAXV = TR_CAP / NT;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T2* sm = reinterpret_cast<T2*>(smraw);
-  const int2 item = items[blockIdx.x];
-  const Prob& pd = probs[item.x];
-  const State& st = states[item.x];
-  if (tr_skip(st, pcg)) return;
-  if (mode == COL_NS_INV && !pd.ns) return;
-  const int N = pd.n, cb = pd.cb, TSg = fpad(N) + 1;
-  const bool dct = (pd.transform == TR_DCT);
-  // weight parameters
-  double alpha = pd.alpha;
-  int kind = (pd.precond == P_TIKH || pd.precond == P_TIKH_NS) && pd.bc != BC_RECT ? W_TIKH : W_INV;
-  if (mode == COL_NS_INV) alpha = st.alpha_n;
-  if (mode == COL_OP) { alpha = op_alpha; kind = op_kind; }
-  if (pd.precond == P_KRYLOV) kind = W_INV;
-  const T Ta = T(alpha);
-  const T Tsc = T(1.0 / ((double)pd.n * (double)pd.n));
-  const size_t base = (size_t)item.y * N * cb;       // this CTA's contiguous block
-  const int W = dct ? N : pd.half;
-  const int kb = item.y * cb;                         // first column of the block
-  if (!dct) {
-    const int G = cb;
-    const FastDiv fG(G);
-    T2* S = static_cast<T2*>(pd.buf[SL_S]) + base;
-    {
-      T2 tmp[MAXV];
-#pragma unroll
-      for (int q = 0; q < MAXV; ++q) {
-        const int e = threadIdx.x + q * NT;
-        tmp[q].x = T(0); tmp[q].y = T(0);
-        if (e < N * G && kb + (e - fG.div(e) * G) < W) tmp[q] = S[e];
-      }
-#pragma unroll
-      for (int q = 0; q < MAXV; ++q) {
-        const int e = threadIdx.x + q * NT;
-        if (e < N * G) { const int k1 = fG.div(e), c = e - k1 * G; sm[c * TSg + fpad(k1)] = tmp[q]; }
-      }
-    }
-    __syncthreads();
-    if (mode != COL_NS_INV) fft_smem<T2, false>(G, pd);
-    if (mode == COL_FWD) {
-      for (int e = threadIdx.x; e < N * G; e += NT) {
-        const int k1 = fG.div(e), c = e - k1 * G;
-        if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
-      }
-      return;
-    }
-    for (int e = threadIdx.x; e < N * G; e += NT) {
-      const int k1 = fG.div(e), c = e - k1 * G;
-      if (kb + c < W) {
-        T2& v = sm[c * TSg + fpad(k1)];
-        v = cmul(v, weight_dft<T, T2>(pd, base + e, Ta, Tsc, kind));
-      }
-    }
-    __syncthreads();
-    fft_smem<T2, true>(G, pd);
-    for (int e = threadIdx.x; e < N * G; e += NT) {
-      const int k1 = fG.div(e), c = e - k1 * G;
-      if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
-    }
-  } else {
-    const int G = cb / 2;
-    const FastDiv fcb(cb);
-    T* S = static_cast<T*>(pd.buf[SL_S]) + base;
-    T* smr = reinterpret_cast<T*>(sm);
-    {
-      T tmp[2 * MAXV];
-#pragma unroll
-      for (int q = 0; q < 2 * MAXV; ++q) {
-        const int e = threadIdx.x + q * NT;
-        tmp[q] = T(0);
-        if (e < N * cb) { const int c = e - fcb.div(e) * cb; if (kb + c < W) tmp[q] = S[e]; }
-      }
-#pragma unroll
-      for (int q = 0; q < 2 * MAXV; ++q) {
-        const int e = threadIdx.x + q * NT;
-        if (e < N * cb) {
-          const int k1 = fcb.div(e), c = e - k1 * cb;
-          const int pos = (mode == COL_NS_INV) ? k1 : dct_pos(k1, N);
-          smr[2 * ((c >> 1) * TSg + fpad(pos)) + (c & 1)] = tmp[q];
-        }
-      }
-    }
-    __syncthreads();
-    const T2* dtw = static_cast<const T2*>(pd.dtw);
-    if (mode != COL_NS_INV) {
-      fft_smem<T2, false>(G, pd);
-      dct_split<T, T2>(sm, G, N, TSg, dtw);
-    }
-    if (mode == COL_FWD) {
-      for (int e = threadIdx.x; e < N * cb; e += NT) {
-        const int k1 = fcb.div(e), c = e - k1 * cb;
-        if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
-      }
-      return;
-    }
-    for (int e = threadIdx.x; e < N * cb; e += NT) {
-      const int k1 = fcb.div(e), c = e - k1 * cb;
-      T& v = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
-      v *= (kb + c < W) ? weight_dct<T>(pd, base + e, Ta, Tsc, kind) : T(0);
-    }
-    __syncthreads();
-    dct_merge<T, T2>(sm, G, N, TSg, dtw);
-    fft_smem<T2, true>(G, pd);
-    for (int e = threadIdx.x; e < N * cb; e += NT) {
-      const int k1 = fcb.div(e), c = e - k1 * cb;
-      if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(dct_pos(k1, N))) + (c & 1)];
-    }
-  }
-}
-
-// Pass 3: inverse transform of row pairs: S -> dst (n x n real)
-template <typename T>
-__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
-k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-           int dst_slot, int pcg) {
-  using T2 = typename Vec2<T>::type;
-  constexpr int NT = tr_nt(sizeof(T));
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T2* sm = reinterpret_cast<T2*>(smraw);
-  const int2 item = items[blockIdx.x];
-  const Prob& pd = probs[item.x];
-  if (tr_skip(states[item.x], pcg)) return;
-  const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
-  const int row0 = 2 * item.y * G;
-  const bool dct = (pd.transform == TR_DCT);
-  // Loads walk the column blocks: within block b the 2G rows of this CTA are
-  // one contiguous run of 2G cb elements; thread e takes column c of pair g.
-  const int cb = pd.cb;
-  const int W = dct ? N : pd.half;
-  const int nb = (W + cb - 1) / cb;
-  const int tot = nb * G * cb;
-  const FastDiv fgc(G * cb), fcb(cb), fN(N);
-  constexpr int BATCH = 4;
-  if (dct) {
-    const T* S = static_cast<const T*>(pd.buf[SL_S]);
-    for (int e0 = threadIdx.x; e0 < tot; e0 += BATCH * NT) {
-      T2 v[BATCH];
-      int k[BATCH];
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        const int e = e0 + u * NT;
-        k[u] = -1;
-        if (e < tot) {
-          const int b = fgc.div(e), rem = e - b * (G * cb);
-          const int g = fcb.div(rem), c = rem - g * cb;
-          const int ra = row0 + 2 * g;
-          const size_t o = (size_t)b * N * cb + (size_t)ra * cb + c;
-          k[u] = b * cb + c;
-          v[u].x = (ra < N && k[u] < W) ? S[o] : T(0);
-          v[u].y = (ra + 1 < N && k[u] < W) ? S[o + cb] : T(0);
-          k[u] = (k[u] < W) ? (g << 16) | k[u] : -1;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u)
-        if (k[u] >= 0) sm[(k[u] >> 16) * TSg + fpad(k[u] & 0xffff)] = v[u];
-    }
-    __syncthreads();
-    dct_merge<T, T2>(sm, G, N, TSg, static_cast<const T2*>(pd.dtw));
-  } else {
-    // Z[k] = Xa[k] + i Xb[k]; the missing half from Hermitian symmetry
-    const bool even = (N & 1) == 0;
-    const T2* S = static_cast<const T2*>(pd.buf[SL_S]);
-    for (int e0 = threadIdx.x; e0 < tot; e0 += BATCH * NT) {
-      T2 xa[BATCH], xb[BATCH];
-      int k[BATCH];
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        const int e = e0 + u * NT;
-        k[u] = -1;
-        xa[u].x = xa[u].y = xb[u].x = xb[u].y = T(0);
-        if (e < tot) {
-          const int b = fgc.div(e), rem = e - b * (G * cb);
-          const int g = fcb.div(rem), c = rem - g * cb;
-          const int ra = row0 + 2 * g;
-          const int kk = b * cb + c;
-          if (kk < W) {
-            const size_t o = (size_t)b * N * cb + (size_t)ra * cb + c;
-            if (ra < N) xa[u] = S[o];
-            if (ra + 1 < N) xb[u] = S[o + cb];
-            k[u] = (g << 16) | kk;
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        if (k[u] < 0) continue;
-        const int kk = k[u] & 0xffff;
-        T2* tb = sm + (k[u] >> 16) * TSg;
-        if (kk == 0 || (even && kk == N / 2)) {
-          T2 z; z.x = xa[u].x; z.y = xb[u].x;        // imaginary parts of DC / Nyquist are rounding
-          tb[fpad(kk)] = z;
-        } else {
-          T2 z; z.x = xa[u].x - xb[u].y; z.y = xa[u].y + xb[u].x;     // Xa + i Xb
-          tb[fpad(kk)] = z;
-          T2 zr; zr.x = xa[u].x + xb[u].y; zr.y = xb[u].x - xa[u].y;  // conj(Xa) + i conj(Xb)
-          tb[fpad(N - kk)] = zr;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  fft_smem<T2, true>(G, pd);
-  T* dst = static_cast<T*>(pd.buf[dst_slot]);
-  for (int e = threadIdx.x; e < G * N; e += NT) {
-    const int g = fN.div(e), x = e - g * N;
-    const int ra = row0 + 2 * g, rb = ra + 1;
-    const T2 v = sm[g * TSg + fpad(dct ? dct_pos(x, N) : x)];
-    if (ra < N) dst[(size_t)ra * N + x] = v.x;
-    if (rb < N) dst[(size_t)rb * N + x] = v.y;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Algorithm 4-NS: alpha_n of Eq. Alg4_rev_7.  With a unitary transform the
 // equation reads h(b) = F(a)/P - q_n^2 = 0, a = exp(b), P = sum |r^|^2,
 // F(a) = sum |r^|^2 x^2, x = a/(s+a).  h increases with b (unique root);
@@ -793,6 +478,421 @@ __device__ double hermite_root(double h0, double h1, double m0, double m1) {
   return t;
 }
 
+// Thread 0 of the last block of a bracketing pass: from the totals (h and h'
+// sums at the candidates, P last) bracket the root and take the Hermite root.
+__device__ void ns_bracket_finish(const Prob& pd, State& st, const double* tot, double b0) {
+  const double P = tot[2 * NS_CAND], target = st.qn * st.qn;
+  auto hv = [&](int j) { return P > 0.0 ? tot[j] / P - target : 0.0; };
+  auto dv = [&](int j) { return P > 0.0 ? 2.0 * tot[NS_CAND + j] / P : 0.0; };
+  auto bv = [&](int j) { return b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP; };
+  int j = 0;
+  while (j < NS_CAND && !(hv(j) >= 0.0)) ++j;
+  double nb;
+  if (j == 0) {
+    // root below the window: Newton from the lowest candidate, at most 4 down
+    st.nb_lo = -INFINITY; st.nb_hi = bv(0);
+    const double d = dv(0);
+    nb = (d > 0.0 && isfinite(hv(0) / d)) ? bv(0) - hv(0) / d : bv(0) - 4.0;
+    nb = fmax(nb, bv(0) - 4.0);
+  } else if (j == NS_CAND) {
+    st.nb_lo = bv(NS_CAND - 1); st.nb_hi = INFINITY;
+    const double d = dv(NS_CAND - 1);
+    nb = (d > 0.0 && isfinite(hv(NS_CAND - 1) / d)) ? bv(NS_CAND - 1) - hv(NS_CAND - 1) / d
+                                                    : bv(NS_CAND - 1) + 4.0;
+    nb = fmin(nb, bv(NS_CAND - 1) + 4.0);
+  } else {
+    st.nb_lo = bv(j - 1); st.nb_hi = bv(j);
+    const double t = hermite_root(hv(j - 1), hv(j), dv(j - 1) * NS_CAND_STEP, dv(j) * NS_CAND_STEP);
+    nb = st.nb_lo + t * NS_CAND_STEP;
+  }
+  st.nphase = 1;
+  st.npass += 1;
+  ns_set_alpha(pd, st, nb);
+}
+
+// accumulate one spectral coefficient (weighted power pf, sigma sf) into the
+// candidate sums
+__device__ __forceinline__ void ns_cand_acc(float pf, float sf, const float (&ca)[NS_CAND],
+                                            float (&cF)[NS_CAND], float (&cG)[NS_CAND]) {
+#pragma unroll
+  for (int j = 0; j < NS_CAND; ++j) {
+    const float x = __fdividef(ca[j], sf + ca[j]);
+    const float px2 = pf * x * x;
+    cF[j] += px2;
+    cG[j] = fmaf(-px2, x, cG[j] + px2);        // + pw x^2 (1 - x)
+  }
+}
+
+// The bracketing pass fused into the forward column pass: the column-pass
+// CTA holds its block of the spectrum in shared memory (real view smr:
+// transform g's element k at 2 (g TSg + fpad(k)) + {0, 1}), so the candidate
+// sums need no second read of S.  DFT: complex column c of the block is
+// transform c; DCT: real column c is part (c & 1) of transform c / 2.
+template <typename T>
+__device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, const T* smr,
+                                           int TSg, size_t base) {
+  constexpr int NT = tr_nt(sizeof(T));
+  constexpr int K = 2 * NS_CAND + 1;
+  __shared__ double red[K * (NT / 32)];
+  __shared__ double tot[K];
+  __shared__ float s_ca[NS_CAND];
+  const int N = pd.n, cb = pd.cb;
+  const bool dct = pd.transform == TR_DCT;
+  const int W = dct ? N : pd.half;
+  const int kb = blk * cb;
+  const double b0 = st.nb;
+  if (threadIdx.x < NS_CAND)
+    s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
+  __syncthreads();
+  float ca[NS_CAND], cF[NS_CAND], cG[NS_CAND];
+#pragma unroll
+  for (int j = 0; j < NS_CAND; ++j) { ca[j] = s_ca[j]; cF[j] = 0.f; cG[j] = 0.f; }
+  const T* w = static_cast<const T*>(pd.w) + base;
+  const FastDiv fcb(cb);
+  T sP = T(0);
+  for (int e = threadIdx.x; e < N * cb; e += NT) {
+    const int k1 = fcb.div(e), c = e - k1 * cb;
+    const int k2 = kb + c;
+    if (k2 >= W) continue;
+    T pw;
+    if (dct) {
+      const T v = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
+      pw = T((k1 == 0 ? 1 : 2) * (k2 == 0 ? 1 : 2)) * v * v;
+    } else {
+      const T vr = smr[2 * (c * TSg + fpad(k1))], vi = smr[2 * (c * TSg + fpad(k1)) + 1];
+      const T m = (k2 == 0 || ((N & 1) == 0 && k2 == N / 2)) ? T(1) : T(2);
+      pw = m * (vr * vr + vi * vi);
+    }
+    sP += pw;
+    ns_cand_acc((float)pw, (float)w[e], ca, cF, cG);
+  }
+  T v[K];
+#pragma unroll
+  for (int j = 0; j < NS_CAND; ++j) { v[j] = T(cF[j]); v[NS_CAND + j] = T(cG[j]); }
+  v[2 * NS_CAND] = sP;
+  if (ns_reduce<NT, K, T>(pd, st, blk, pd.nblk_cols, v, red, tot) && threadIdx.x == 0)
+    ns_bracket_finish(pd, st, tot, b0);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: forward transform of row pairs: src (n x n real) -> S
+template <typename T>
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
+k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+           int src_slot, int pcg) {
+  using T2 = typename Vec2<T>::type;
+  constexpr int NT = tr_nt(sizeof(T)), MAXV = TR_CAP / NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  if (tr_skip(states[item.x], pcg)) return;
+  const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
+  const int pair0 = item.y * G;
+  const int row0 = 2 * pair0;
+  const bool dct = (pd.transform == TR_DCT);
+  const T* src = static_cast<const T*>(pd.buf[src_slot]);
+  const FastDiv fN(N);
+  {
+    // all loads of this thread first (up to MAXV in flight), then the stores
+    T2 tmp[MAXV];
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (e < G * N) {
+        const int g = fN.div(e), x = e - g * N;
+        const int ra = row0 + 2 * g, rb = ra + 1;
+        const int xs = dct ? dct_src(x, N) : x;
+        tmp[q].x = (ra < N) ? src[(size_t)ra * N + xs] : T(0);
+        tmp[q].y = (rb < N) ? src[(size_t)rb * N + xs] : T(0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXV; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (e < G * N) { const int g = fN.div(e), x = e - g * N; sm[g * TSg + fpad(x)] = tmp[q]; }
+    }
+  }
+  __syncthreads();
+  fft_smem<T2, false>(G, pd);
+  if (dct) dct_split<T, T2>(sm, G, N, TSg, static_cast<const T2*>(pd.dtw));
+  // write the rows of this CTA into every column block (contiguous runs)
+  const int W = dct ? N : pd.half;
+  const int cb = pd.cb;
+  const int R2 = 2 * G;
+  const int nb = (W + cb - 1) / cb;
+  const FastDiv frc(R2 * cb), fcb(cb);
+  for (int e = threadIdx.x; e < nb * R2 * cb; e += NT) {
+    const int b = frc.div(e), rem = e - b * (R2 * cb);
+    const int rl = fcb.div(rem), c = rem - rl * cb;
+    const int k = b * cb + c, row = row0 + rl;
+    if (k >= W || row >= N) continue;
+    const T2* tb = sm + (rl >> 1) * TSg;
+    const size_t o = (size_t)b * N * cb + (size_t)row * cb + c;
+    if (dct) {
+      const T2 X = tb[fpad(k)];
+      static_cast<T*>(pd.buf[SL_S])[o] = (rl & 1) ? X.y : X.x;
+    } else {
+      const T2 Z = tb[fpad(k)];
+      const T2 Zr = tb[fpad(k == 0 ? 0 : N - k)];
+      T2 X;
+      if (rl & 1) { X.x = T(0.5) * (Z.y + Zr.y); X.y = T(-0.5) * (Z.x - Zr.x); }   // (Z - conj Zr)/(2i)
+      else { X.x = T(0.5) * (Z.x + Zr.x); X.y = T(0.5) * (Z.y - Zr.y); }           // (Z + conj Zr)/2
+      static_cast<T2*>(pd.buf[SL_S])[o] = X;
+    }
+  }
+}
+
+// spectral weight at blocked index idx; alpha and kind as given.  |lambda|^2 +
+// alpha is formed in T: alpha > 0 keeps it away from zero (no cancellation),
+// so FP32 holds it to 6e-8 relative; 1/n^2 of the unnormalised pair is folded in.
+// scale / (|lambda|^2 + alpha): the fast reciprocal-based quotient in FP32
+// (within 2 ulp), the exact one in FP64
+__device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
+
+template <typename T, typename T2>
+__device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
+  const T inv = wdiv(scale, static_cast<const T*>(pd.w)[idx] + alpha);
+  T2 w;
+  if (kind == W_TIKH) {
+    const T2 l = static_cast<const T2*>(pd.lam)[idx];
+    w.x = l.x * inv; w.y = -l.y * inv;
+  } else { w.x = inv; w.y = T(0); }
+  return w;
+}
+template <typename T>
+__device__ __forceinline__ T weight_dct(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
+  const T inv = wdiv(scale, static_cast<const T*>(pd.w)[idx] + alpha);
+  return kind == W_TIKH ? static_cast<const T*>(pd.lam)[idx] * inv : inv;
+}
+
+// Pass 2: one column block per CTA.  DFT: cb complex columns; DCT: cb real
+// columns = cb/2 packed pairs.
+template <typename T>
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
+k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+       int mode, int pcg, double op_alpha, int op_kind) {
+  using T2 = typename Vec2<T>::type;
+  constexpr int NT = tr_nt(sizeof(T)), MAXV = TR_CAP / NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  State& st = states[item.x];
+  if (tr_skip(st, pcg)) return;
+  if (mode == COL_NS_INV && !pd.ns) return;
+  // Algorithm 4-NS: the forward pass also runs the bracketing pass of alpha_n
+  const bool cand = mode == COL_FWD && !pcg && pd.ns && st.ns_active && !st.nconv && st.nphase == 0;
+  const int N = pd.n, cb = pd.cb, TSg = fpad(N) + 1;
+  const bool dct = (pd.transform == TR_DCT);
+  // weight parameters
+  double alpha = pd.alpha;
+  int kind = (pd.precond == P_TIKH || pd.precond == P_TIKH_NS) && pd.bc != BC_RECT ? W_TIKH : W_INV;
+  if (mode == COL_NS_INV) alpha = st.alpha_n;
+  if (mode == COL_OP) { alpha = op_alpha; kind = op_kind; }
+  if (pd.precond == P_KRYLOV) kind = W_INV;
+  const T Ta = T(alpha);
+  const T Tsc = T(1.0 / ((double)pd.n * (double)pd.n));
+  const size_t base = (size_t)item.y * N * cb;       // this CTA's contiguous block
+  const int W = dct ? N : pd.half;
+  const int kb = item.y * cb;                         // first column of the block
+  if (!dct) {
+    const int G = cb;
+    const FastDiv fG(G);
+    T2* S = static_cast<T2*>(pd.buf[SL_S]) + base;
+    {
+      T2 tmp[MAXV];
+#pragma unroll
+      for (int q = 0; q < MAXV; ++q) {
+        const int e = threadIdx.x + q * NT;
+        tmp[q].x = T(0); tmp[q].y = T(0);
+        if (e < N * G && kb + (e - fG.div(e) * G) < W) tmp[q] = S[e];
+      }
+#pragma unroll
+      for (int q = 0; q < MAXV; ++q) {
+        const int e = threadIdx.x + q * NT;
+        if (e < N * G) { const int k1 = fG.div(e), c = e - k1 * G; sm[c * TSg + fpad(k1)] = tmp[q]; }
+      }
+    }
+    __syncthreads();
+    if (mode != COL_NS_INV) fft_smem<T2, false>(G, pd);
+    if (mode == COL_FWD) {
+      for (int e = threadIdx.x; e < N * G; e += NT) {
+        const int k1 = fG.div(e), c = e - k1 * G;
+        if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
+      }
+      if (cand) ns_cand_block<T>(pd, st, item.y, reinterpret_cast<const T*>(sm), TSg, base);
+      return;
+    }
+    for (int e = threadIdx.x; e < N * G; e += NT) {
+      const int k1 = fG.div(e), c = e - k1 * G;
+      if (kb + c < W) {
+        T2& v = sm[c * TSg + fpad(k1)];
+        v = cmul(v, weight_dft<T, T2>(pd, base + e, Ta, Tsc, kind));
+      }
+    }
+    __syncthreads();
+    fft_smem<T2, true>(G, pd);
+    for (int e = threadIdx.x; e < N * G; e += NT) {
+      const int k1 = fG.div(e), c = e - k1 * G;
+      if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
+    }
+  } else {
+    const int G = cb / 2;
+    const FastDiv fcb(cb);
+    T* S = static_cast<T*>(pd.buf[SL_S]) + base;
+    T* smr = reinterpret_cast<T*>(sm);
+    {
+      T tmp[2 * MAXV];
+#pragma unroll
+      for (int q = 0; q < 2 * MAXV; ++q) {
+        const int e = threadIdx.x + q * NT;
+        tmp[q] = T(0);
+        if (e < N * cb) { const int c = e - fcb.div(e) * cb; if (kb + c < W) tmp[q] = S[e]; }
+      }
+#pragma unroll
+      for (int q = 0; q < 2 * MAXV; ++q) {
+        const int e = threadIdx.x + q * NT;
+        if (e < N * cb) {
+          const int k1 = fcb.div(e), c = e - k1 * cb;
+          const int pos = (mode == COL_NS_INV) ? k1 : dct_pos(k1, N);
+          smr[2 * ((c >> 1) * TSg + fpad(pos)) + (c & 1)] = tmp[q];
+        }
+      }
+    }
+    __syncthreads();
+    const T2* dtw = static_cast<const T2*>(pd.dtw);
+    if (mode != COL_NS_INV) {
+      fft_smem<T2, false>(G, pd);
+      dct_split<T, T2>(sm, G, N, TSg, dtw);
+    }
+    if (mode == COL_FWD) {
+      for (int e = threadIdx.x; e < N * cb; e += NT) {
+        const int k1 = fcb.div(e), c = e - k1 * cb;
+        if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
+      }
+      if (cand) ns_cand_block<T>(pd, st, item.y, smr, TSg, base);
+      return;
+    }
+    for (int e = threadIdx.x; e < N * cb; e += NT) {
+      const int k1 = fcb.div(e), c = e - k1 * cb;
+      T& v = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
+      v *= (kb + c < W) ? weight_dct<T>(pd, base + e, Ta, Tsc, kind) : T(0);
+    }
+    __syncthreads();
+    dct_merge<T, T2>(sm, G, N, TSg, dtw);
+    fft_smem<T2, true>(G, pd);
+    for (int e = threadIdx.x; e < N * cb; e += NT) {
+      const int k1 = fcb.div(e), c = e - k1 * cb;
+      if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(dct_pos(k1, N))) + (c & 1)];
+    }
+  }
+}
+
+// Pass 3: inverse transform of row pairs: S -> dst (n x n real)
+template <typename T>
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
+k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+           int dst_slot, int pcg) {
+  using T2 = typename Vec2<T>::type;
+  constexpr int NT = tr_nt(sizeof(T));
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  if (tr_skip(states[item.x], pcg)) return;
+  const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
+  const int row0 = 2 * item.y * G;
+  const bool dct = (pd.transform == TR_DCT);
+  // Loads walk the column blocks: within block b the 2G rows of this CTA are
+  // one contiguous run of 2G cb elements; thread e takes column c of pair g.
+  const int cb = pd.cb;
+  const int W = dct ? N : pd.half;
+  const int nb = (W + cb - 1) / cb;
+  const int tot = nb * G * cb;
+  const FastDiv fgc(G * cb), fcb(cb), fN(N);
+  constexpr int BATCH = 4;
+  if (dct) {
+    const T* S = static_cast<const T*>(pd.buf[SL_S]);
+    for (int e0 = threadIdx.x; e0 < tot; e0 += BATCH * NT) {
+      T2 v[BATCH];
+      int k[BATCH];
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = e0 + u * NT;
+        k[u] = -1;
+        if (e < tot) {
+          const int b = fgc.div(e), rem = e - b * (G * cb);
+          const int g = fcb.div(rem), c = rem - g * cb;
+          const int ra = row0 + 2 * g;
+          const size_t o = (size_t)b * N * cb + (size_t)ra * cb + c;
+          k[u] = b * cb + c;
+          v[u].x = (ra < N && k[u] < W) ? S[o] : T(0);
+          v[u].y = (ra + 1 < N && k[u] < W) ? S[o + cb] : T(0);
+          k[u] = (k[u] < W) ? (g << 16) | k[u] : -1;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u)
+        if (k[u] >= 0) sm[(k[u] >> 16) * TSg + fpad(k[u] & 0xffff)] = v[u];
+    }
+    __syncthreads();
+    dct_merge<T, T2>(sm, G, N, TSg, static_cast<const T2*>(pd.dtw));
+  } else {
+    // Z[k] = Xa[k] + i Xb[k]; the missing half from Hermitian symmetry
+    const bool even = (N & 1) == 0;
+    const T2* S = static_cast<const T2*>(pd.buf[SL_S]);
+    for (int e0 = threadIdx.x; e0 < tot; e0 += BATCH * NT) {
+      T2 xa[BATCH], xb[BATCH];
+      int k[BATCH];
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = e0 + u * NT;
+        k[u] = -1;
+        xa[u].x = xa[u].y = xb[u].x = xb[u].y = T(0);
+        if (e < tot) {
+          const int b = fgc.div(e), rem = e - b * (G * cb);
+          const int g = fcb.div(rem), c = rem - g * cb;
+          const int ra = row0 + 2 * g;
+          const int kk = b * cb + c;
+          if (kk < W) {
+            const size_t o = (size_t)b * N * cb + (size_t)ra * cb + c;
+            if (ra < N) xa[u] = S[o];
+            if (ra + 1 < N) xb[u] = S[o + cb];
+            k[u] = (g << 16) | kk;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        if (k[u] < 0) continue;
+        const int kk = k[u] & 0xffff;
+        T2* tb = sm + (k[u] >> 16) * TSg;
+        if (kk == 0 || (even && kk == N / 2)) {
+          T2 z; z.x = xa[u].x; z.y = xb[u].x;        // imaginary parts of DC / Nyquist are rounding
+          tb[fpad(kk)] = z;
+        } else {
+          T2 z; z.x = xa[u].x - xb[u].y; z.y = xa[u].y + xb[u].x;     // Xa + i Xb
+          tb[fpad(kk)] = z;
+          T2 zr; zr.x = xa[u].x + xb[u].y; zr.y = xb[u].x - xa[u].y;  // conj(Xa) + i conj(Xb)
+          tb[fpad(N - kk)] = zr;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  fft_smem<T2, true>(G, pd);
+  T* dst = static_cast<T*>(pd.buf[dst_slot]);
+  for (int e = threadIdx.x; e < G * N; e += NT) {
+    const int g = fN.div(e), x = e - g * N;
+    const int ra = row0 + 2 * g, rb = ra + 1;
+    const T2 v = sm[g * TSg + fpad(dct ? dct_pos(x, N) : x)];
+    if (ra < N) dst[(size_t)ra * N + x] = v.x;
+    if (rb < N) dst[(size_t)rb * N + x] = v.y;
+  }
+}
+
 // Bracketing pass (nphase 0): h and h' at NS_CAND candidates around the
 // previous root.
 template <typename T>
@@ -823,48 +923,14 @@ k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const in
   for (int q = 0; q < NS_PT; ++q) {
     if (!ok[q]) continue;
     sP += pw[q];
-    const float pf = (float)pw[q], sf = (float)sg[q];
-#pragma unroll
-    for (int j = 0; j < NS_CAND; ++j) {
-      const float x = __fdividef(ca[j], sf + ca[j]);
-      const float px2 = pf * x * x;
-      cF[j] += px2;
-      cG[j] = fmaf(-px2, x, cG[j] + px2);        // + pw x^2 (1 - x)
-    }
+    ns_cand_acc((float)pw[q], (float)sg[q], ca, cF, cG);
   }
   T v[K];
 #pragma unroll
   for (int j = 0; j < NS_CAND; ++j) { v[j] = T(cF[j]); v[NS_CAND + j] = T(cG[j]); }
   v[2 * NS_CAND] = sP;
-  if (ns_reduce<NS_NT, K, T>(pd, st, item.y, pd.nblk_spec, v, red, tot) && threadIdx.x == 0) {
-    const double P = tot[2 * NS_CAND], target = st.qn * st.qn;
-    auto hv = [&](int j) { return P > 0.0 ? tot[j] / P - target : 0.0; };
-    auto dv = [&](int j) { return P > 0.0 ? 2.0 * tot[NS_CAND + j] / P : 0.0; };
-    auto bv = [&](int j) { return b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP; };
-    int j = 0;
-    while (j < NS_CAND && !(hv(j) >= 0.0)) ++j;
-    double nb;
-    if (j == 0) {
-      // root below the window: Newton from the lowest candidate, at most 4 down
-      st.nb_lo = -INFINITY; st.nb_hi = bv(0);
-      const double d = dv(0);
-      nb = (d > 0.0 && isfinite(hv(0) / d)) ? bv(0) - hv(0) / d : bv(0) - 4.0;
-      nb = fmax(nb, bv(0) - 4.0);
-    } else if (j == NS_CAND) {
-      st.nb_lo = bv(NS_CAND - 1); st.nb_hi = INFINITY;
-      const double d = dv(NS_CAND - 1);
-      nb = (d > 0.0 && isfinite(hv(NS_CAND - 1) / d)) ? bv(NS_CAND - 1) - hv(NS_CAND - 1) / d
-                                                      : bv(NS_CAND - 1) + 4.0;
-      nb = fmin(nb, bv(NS_CAND - 1) + 4.0);
-    } else {
-      st.nb_lo = bv(j - 1); st.nb_hi = bv(j);
-      const double t = hermite_root(hv(j - 1), hv(j), dv(j - 1) * NS_CAND_STEP, dv(j) * NS_CAND_STEP);
-      nb = st.nb_lo + t * NS_CAND_STEP;
-    }
-    st.nphase = 1;
-    st.npass += 1;
-    ns_set_alpha(pd, st, nb);
-  }
+  if (ns_reduce<NS_NT, K, T>(pd, st, item.y, pd.nblk_spec, v, red, tot) && threadIdx.x == 0)
+    ns_bracket_finish(pd, st, tot, b0);
 }
 
 // Refinement pass (nphase 1): a safeguarded Halley step at the current b.

@@ -177,7 +177,7 @@ void enqueue_step(mlba_batch* B, cudaStream_t s) {
     launch_cols<T>(P, S, B->cols_stat.dev, B->cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
     if (B->any_ns) {
       launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
-      launch_spec<T>(P, S, B->spec.dev, B->spec.count, 1, s);
+      // (the bracketing pass runs inside the forward column pass)
       for (int k = 1; k < ns_passes<T>(); ++k) launch_spec<T>(P, S, B->spec.dev, B->spec.count, 0, s);
       launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
     }
@@ -455,7 +455,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
         (size_t)pd.nruns * 16, (size_t)pd.nrw * ts,   // tap runs and weights
         (size_t)pd.p * ts, (size_t)pd.p * ts,  // hy, hx
-        std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, (size_t)SPEC_SUMS * pd.nblk_spec, (size_t)1}) * 8,  // partial
+        std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, (size_t)SPEC_SUMS * std::max(pd.nblk_spec, pd.nblk_cols), (size_t)1}) * 8,  // partial
         (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 4};
     offs[i].resize(sz.size());
     for (size_t k = 0; k < sz.size(); ++k) { offs[i][k] = total; total += al(sz[k]); }
