@@ -119,7 +119,7 @@ typedef struct mlba_stats {
 typedef struct mlba_ctx mlba_ctx;
 
 /* Largest PSF side accepted by mlba_create / mlba_batch_create (the stencil
- * tile holds 32 + p - 1 < 96 columns). */
+ * tile holds 64 + p - 1 <= 128 columns). */
 #define MLBA_MAX_P 65
 
 /* Create a context for one problem.  psf: host, p*p doubles, row-major,

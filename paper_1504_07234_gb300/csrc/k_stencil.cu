@@ -110,27 +110,87 @@ __device__ __forceinline__ int bc_map_near(int e, int n, int bc) {
   return bc_map(e, n, bc);
 }
 
-// Stencil tile geometry: 32 x 32 outputs per CTA of 128 threads, 8 outputs
-// per thread held in registers.  The input tile (32 + p - 1)^2 lives in
-// shared memory with a row pitch of 1 mod 32 words.
-__host__ __device__ constexpr int st_pitch(int R) { return R + ((33 - R % 32) % 32); }
+// Pairs of FP32 values: the paired FP32 instructions of sm_100+ do two
+// multiply-adds in one; FP64 falls back to two scalar ones.
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+  using type = float2;
+  static __device__ __forceinline__ float2 fma(float2 a, float w, float2 acc) {
+    return __ffma2_rn(a, make_float2(w, w), acc);
+  }
+};
+template <> struct Pair<double> {
+  using type = double2;
+  static __device__ __forceinline__ double2 fma(double2 a, double w, double2 acc) {
+    return make_double2(::fma(a.x, w, acc.x), ::fma(a.y, w, acc.y));
+  }
+};
+
+// acc[j] += sum_t w[t] v[t + j] over a run of len taps for pairs of
+// neighbouring columns, v[i] = (base[i stride], base[i stride + 1]) (one
+// 8-byte or 16-byte load when `aligned`, else two): the same ring / shifting
+// window as window_run, on pairs.
+template <typename T>
+__device__ __forceinline__ void window_run2(typename Pair<T>::type (&acc)[8], const T* __restrict__ base,
+                                            int stride, const T* __restrict__ w, int len,
+                                            bool aligned) {
+  using T2 = typename Pair<T>::type;
+  auto ld = [&](int i) -> T2 {
+    const T* q = base + i * stride;
+    if (aligned) return *reinterpret_cast<const T2*>(q);
+    T2 v; v.x = q[0]; v.y = q[1]; return v;
+  };
+  T2 win[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) win[j] = ld(j);
+  int t = 0;
+  for (; t + 8 <= len; t += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T wt = w[t + u];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = Pair<T>::fma(win[(j + u) & 7], wt, acc[j]);
+      if (t + u + 1 < len) win[u] = ld(t + u + 8);
+    }
+  }
+  for (; t < len; ++t) {
+    const T wt = w[t];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = Pair<T>::fma(win[j], wt, acc[j]);
+    if (t + 1 < len) {
+#pragma unroll
+      for (int j = 0; j < 7; ++j) win[j] = win[j + 1];
+      win[7] = ld(t + 8);
+    }
+  }
+}
+
+// Stencil tile geometry: 64 x 32 outputs per CTA of 128 threads; a thread
+// owns two neighbouring columns over 8 rows (16 outputs in registers).  The
+// input tile (32 + p - 1) x (64 + p - 1) lives in shared memory with an even
+// row pitch (pairs of columns are one 8-byte word when the column is even).
+constexpr int ST_TX = 64, ST_TY = 32;
+__host__ __device__ constexpr int st_pitch(int RX) { return (RX + 1) & ~1; }
+constexpr int ST_TP = ST_TX + 2;      // row-pass tile pitch (rank-one PSF)
+
+int stencil_tiles(int outN) { return ((outN + ST_TX - 1) / ST_TX) * ((outN + ST_TY - 1) / ST_TY); }
 
 // Blur A (Eq. 2 with the Table 1 boundary conditions, or the valid part for
 // rectangular A) and the full correlation that A^T is built from, as
 // register-window stencils:
 //  - general PSF: the taps are grouped by PSF column b into dense runs
-//    [lo_b, hi_b] of rows; a thread owns 8 consecutive outputs of one column
-//    and slides an 8-value window of the input column down the run, so each
-//    tap costs one shared load of the input, one (broadcast) weight and 8 FMAs;
+//    [lo_b, hi_b] of rows; a thread slides an 8-row window of two input
+//    columns down the run, so each tap costs one (or two) shared loads, one
+//    broadcast weight and 8 paired FMAs for 16 outputs;
 //  - rank-one PSF (h = hy hx^T): a horizontal pass with an 8-value window along
-//    the rows into shared memory, then a vertical pass with a window along the
-//    columns.
+//    the rows into shared memory, then a vertical pass with paired windows.
 // Forward (A f)(y, x) = sum_{a,b} H[a][b] f_ext(y + c - a, x + c - b); the
 // correlation (ne x ne) is sum_{a,b} H[a][b] t(y - 2c + a, x - 2c + b).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(STENCIL_THREADS)
 k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
           int src_slot, int dst_slot, int aux_slot, int pcg) {
+  using T2 = typename Pair<T>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
   const int2 item = items[blockIdx.x];
@@ -142,19 +202,19 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   constexpr int NT = STENCIL_THREADS;
   const int n = pd.n, p = pd.p, c = pd.c;
   const int outN = CORR ? pd.ne : n;
-  const int tilesX = (outN + 31) >> 5;
-  const int ty0 = (item.y / tilesX) * 32, tx0 = (item.y % tilesX) * 32;
-  const int R = 32 + p - 1;
-  const int RP = st_pitch(R);
+  const int tilesX = (outN + ST_TX - 1) / ST_TX;
+  const int ty0 = (item.y / tilesX) * ST_TY, tx0 = (item.y % tilesX) * ST_TX;
+  const int RY = ST_TY + p - 1, RX = ST_TX + p - 1;
+  const int RP = st_pitch(RX);
   const bool sep = pd.sep != 0;
 
   // shared memory: weights, column runs (general PSF), input tile, row-pass
-  // tile (rank-one PSF, pitch 33)
+  // tile (rank-one PSF)
   const int nw = sep ? 2 * p : pd.nrw;
   T* s_w = reinterpret_cast<T*>(smraw);
   int4* s_runs = reinterpret_cast<int4*>(s_w + ((nw + 3) & ~3));
   T* s_in = reinterpret_cast<T*>(s_runs + (sep ? 0 : pd.nruns));
-  T* s_tmp = s_in + R * RP;
+  T* s_tmp = s_in + RY * RP;
 
   // src_slot < 0: the per-problem default operand (t, or r for P = I, in the
   // correlation; A^T p for the PCG product: V for rectangular A, U otherwise)
@@ -185,12 +245,12 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   // asynchronous copies straight into shared memory (no registers held, all
   // of a thread's copies in flight together); positions outside the source
   // are zero-filled by a copy of 0 source bytes.  One warp per row, lanes
-  // along the row (R <= 32 + MLBA_MAX_P - 1 < 96: three column passes at
+  // along the row (RX <= 64 + MLBA_MAX_P - 1 = 128: four column passes at
   // most); the row's source index is mapped once.
   {
     const int lane = threadIdx.x & 31;
     const int pitch = (!CORR && pd.bc == BC_RECT) ? pd.nf : n;
-    for (int ry = threadIdx.x >> 5; ry < R; ry += NT / 32) {
+    for (int ry = threadIdx.x >> 5; ry < RY; ry += NT / 32) {
       const int ey = oy0 + ry;
       int sy;
       if (CORR) sy = (ey >= 0 && ey < n) ? ey : -1;
@@ -198,9 +258,9 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
       else sy = bc_map_near(ey, n, pd.bc);
       const T* row = src + (size_t)(sy < 0 ? 0 : sy) * pitch;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < 4; ++k) {
         const int rx = lane + 32 * k;
-        if (rx < R) {
+        if (rx < RX) {
           const int ex = ox0 + rx;
           int sx;
           if (CORR) sx = (ex >= 0 && ex < n) ? ex : -1;
@@ -214,57 +274,61 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
     cp_async_wait_all();
   }
   __syncthreads();
-  // this thread's outputs: column x, rows y8 .. y8 + 7 of the tile
-  const int x = threadIdx.x & 31, y8 = (threadIdx.x >> 5) * 8;
-  T acc[8];
+  // this thread's outputs: columns x2, x2 + 1, rows y8 .. y8 + 7 of the tile
+  const int x2 = 2 * (threadIdx.x & 31), y8 = (threadIdx.x >> 5) * 8;
+  T2 acc[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc[j] = T(0);
+  for (int j = 0; j < 8; ++j) { acc[j].x = T(0); acc[j].y = T(0); }
   if (sep) {
-    // row pass over all R rows: tmp(ry, xx) = sum_t wx[t] in(ry, xx + t)
-    for (int idx = threadIdx.x; idx < 4 * R; idx += NT) {
-      const int ry = idx >> 2, x8 = (idx & 3) * 8;
+    // row pass over all RY rows: tmp(ry, xx) = sum_t wx[t] in(ry, xx + t)
+    for (int idx = threadIdx.x; idx < 8 * RY; idx += NT) {
+      const int ry = idx >> 3, x8 = (idx & 7) * 8;
       T h[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) h[j] = T(0);
       window_run<T>(h, s_in + ry * RP + x8, 1, s_w, p);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) s_tmp[ry * 33 + x8 + j] = h[j];
+      for (int j = 0; j < 8; ++j) s_tmp[ry * ST_TP + x8 + j] = h[j];
     }
     __syncthreads();
     // column pass: out(y, x) = sum_t wy[t] tmp(y + t, x)
-    window_run<T>(acc, s_tmp + y8 * 33 + x, 33, s_w + p, p);
+    window_run2<T>(acc, s_tmp + y8 * ST_TP + x2, ST_TP, s_w + p, p, true);
   } else {
-    // runs of PSF column b over rows lo..hi: input column x + (CORR ? b : 2c - b),
+    // runs of PSF column b over rows lo..hi: input columns x + (CORR ? b : 2c - b),
     // window rows from y8 + (CORR ? lo : 2c - hi)
     for (int k = 0; k < pd.nruns; ++k) {
       const int4 rn = s_runs[k];
       const int len = rn.z - rn.y + 1;
-      const int col = CORR ? x + rn.x : x + 2 * c - rn.x;
+      const int col = CORR ? x2 + rn.x : x2 + 2 * c - rn.x;
       const int r0 = CORR ? y8 + rn.y : y8 + 2 * c - rn.z;
-      window_run<T>(acc, s_in + r0 * RP + col, RP, s_w + rn.w, len);
+      window_run2<T>(acc, s_in + r0 * RP + col, RP, s_w + rn.w, len, (col & 1) == 0);
     }
   }
   T* dst = static_cast<T*>(pd.buf[dst_slot]);
   const T* aux = static_cast<const T*>(pd.buf[aux_slot]);
   T lacc = T(0);
-  const int gx = tx0 + x;
+  const int gx = tx0 + x2;
+  auto emit = [&](size_t o, T a) {
+    if (MODE == ST_FWD_RESID) {
+      const T r = aux[o] - a;
+      dst[o] = r;
+      lacc += r * r;
+    } else if (MODE == ST_FWD_PCGQ) {
+      const T pv = aux[o];
+      const T qv = a + T(pd.alpha) * pv;
+      dst[o] = qv;
+      lacc += pv * qv;
+    } else {
+      dst[o] = a;
+    }
+  };
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int gy = ty0 + y8 + j;
-    if (gy < outN && gx < outN) {
+    if (gy < outN) {
       const size_t o = (size_t)gy * outN + gx;
-      if (MODE == ST_FWD_RESID) {
-        const T r = aux[o] - acc[j];
-        dst[o] = r;
-        lacc += r * r;
-      } else if (MODE == ST_FWD_PCGQ) {
-        const T pv = aux[o];
-        const T qv = acc[j] + T(pd.alpha) * pv;
-        dst[o] = qv;
-        lacc += pv * qv;
-      } else {
-        dst[o] = acc[j];
-      }
+      if (gx < outN) emit(o, acc[j].x);
+      if (gx + 1 < outN) emit(o + 1, acc[j].y);
     }
   }
   if (MODE == ST_FWD_RESID || MODE == ST_FWD_PCGQ) {

@@ -322,8 +322,8 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   pd.nrw = (int)h.rw.size();
   pd.sep = rank_one(h.psf, p, h.hy, h.hx) && p > 1 ? 1 : 0;
   // launch geometry
-  pd.nblk_blur = ((n + 31) / 32) * ((n + 31) / 32);
-  pd.nblk_corr = ((pd.ne + 31) / 32) * ((pd.ne + 31) / 32);
+  pd.nblk_blur = stencil_tiles(n);
+  pd.nblk_corr = stencil_tiles(pd.ne);
   pd.nblk_frame = frame_tiles(pd.nf, o.levels);
   // the frame kernel indexes a z array (all bands) with 32-bit offsets
   if ((double)pd.nbands * pd.nf * pd.nf >= 2147483647.0) return MLBA_E_UNSUPPORTED;
@@ -552,10 +552,10 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
       else { add(cols_stat, pd.nblk_cols); B->any_stat = 1; }
     }
     // stencil: weights (padded to 16 bytes), runs, input tile, row-pass tile
-    const size_t R = 32 + pd.p - 1;
-    const size_t RP = R + (33 - R % 32) % 32;
+    const size_t RY = 32 + pd.p - 1, RX = 64 + pd.p - 1;
+    const size_t RP = (RX + 1) & ~(size_t)1;
     const size_t nw = pd.sep ? 2 * pd.p : pd.nrw;
-    const size_t st_b = (((nw + 3) & ~(size_t)3) + R * RP + (pd.sep ? R * 33 : 0)) * ts +
+    const size_t st_b = (((nw + 3) & ~(size_t)3) + RY * RP + (pd.sep ? RY * 66 : 0)) * ts +
                         (pd.sep ? 0 : (size_t)pd.nruns * 16);
     smem_st = std::max(smem_st, st_b);
     if (specp) {

@@ -69,6 +69,7 @@ void launch_frame(const Prob* probs, State* states, const int2* items, int nitem
 template <typename T, typename TZ>
 size_t frame_smem_bytes(int levels);
 int frame_tiles(int nf, int levels);     // CTAs of the frame kernel for one problem
+int stencil_tiles(int outN);             // CTAs of the stencil for an outN x outN output
 template <typename T, typename TZ>
 cudaError_t frame_set_smem(size_t bytes);
 template <typename T>
