@@ -674,6 +674,19 @@ __device__ __forceinline__ int f3_refl(int e, int n, bool* par) {
   return r;
 }
 
+// Grouped z layout (L <= 2): the 8 high-pass bands of level l of pixel q are
+// contiguous, at (l - 1) 8 nf^2 + 8 q + (3 i + j - 1); the final low-pass band
+// keeps its plane at 8 L nf^2 + q.  A lane then moves one pixel's bands of a
+// level with one to four 16-byte accesses and one address.
+template <typename TZ>
+union ZGroup {
+  uint4 v[8 * sizeof(TZ) / 16];
+  TZ e[8];
+};
+__device__ __forceinline__ float to_z(float v, float*) { return v; }
+__device__ __forceinline__ double to_z(double v, double*) { return v; }
+__device__ __forceinline__ __nv_bfloat16 to_z(float v, __nv_bfloat16*) { return __float2bfloat16_rn(v); }
+
 template <typename T, typename TZ, int LEV, int L>
 __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ cin, int cpitch,
                                          int cy0, int cx0, const TZ* __restrict__ zin,
@@ -713,13 +726,9 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
     g[0] = T(0.25) * (r[-1] + r[1]) + T(0.5) * r[0];
     g[1] = T(0.25) * (r[3] + r[5]) + T(0.5) * r[4];
   };
-  // band planes in k order
-  int boff[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int k = K0 + b;
-    boff[b] = f2_band(LEV, L, k % 3, k / 3) * plane;
-  }
+  // this level's band group and (top level) the low-pass plane
+  constexpr int NV = 8 * (int)sizeof(TZ) / 16;
+  const int gbase = (LEV - 1) * 8 * plane, lbase = 8 * L * plane;
   // h ring: rows y - D .. y + D of the current coefficient row y
   T hr[2 * D + 1][3];
   auto hrow = [&](int y, T (&h)[3]) {
@@ -748,28 +757,31 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   }
 #pragma unroll
   for (int k = 0; k < 2 * D; ++k) hrow(yc0 - D + k, hr[k]);
-  // z queue: rows y .. y + PF - 1
-  TZ zq[F3_PF][NB];
+  // z queue: rows y .. y + PF - 1 (group and low-pass value per row)
+  ZGroup<TZ> zq[F3_PF];
+  TZ zl[F3_PF];
   // (idle lanes load a valid mirrored column too; their values are unused.
   // Offsets stay in 32 bits: nbands nf^2 < 2^31.)
-  auto zload = [&](int y, TZ (&q)[NB]) {
+  auto zload = [&](int y, int k) {
     bool par;
-    const int ro = f3_refl(y, nf, &par) * nf + zc;
+    const int q = f3_refl(y, nf, &par) * nf + zc;
+    const uint4* src = reinterpret_cast<const uint4*>(zin + (gbase + 8 * q));
 #pragma unroll
-    for (int b = 0; b < NB; ++b) q[b] = zin[ro + boff[b]];
+    for (int v = 0; v < NV; ++v) zq[k].v[v] = src[v];
+    if (TOP) zl[k] = zin[lbase + q];
   };
 #pragma unroll
-  for (int k = 0; k < F3_PF; ++k) zload(yc0 + k, zq[k]);
+  for (int k = 0; k < F3_PF; ++k) zload(yc0 + k, k);
   // synthesis ring: rows y - D .. y + D
   T pr[2 * D + 1][3];
 #pragma unroll
   for (int k = 0; k <= 2 * D; ++k) pr[k][0] = pr[k][1] = pr[k][2] = T(0);
   // level-2 low-pass ring of the horizontally filtered s_1 rows r-2, r-1, r
   T gq[3] = {T(0), T(0), T(0)};
-  // one coefficient row; q holds its z and is refilled with row y + PF.  The
-  // queue is indexed statically (the sweep is unrolled by PF) so that no
-  // register receiving an outstanding load is copied before it is used.
-  auto step = [&](int y, TZ (&q)[NB]) {
+  // one coefficient row; queue slot kq holds its z and is refilled with row
+  // y + PF.  The queue is indexed statically (the sweep is unrolled by PF) so
+  // that no register receiving an outstanding load is copied before it is used.
+  auto step = [&](int y, int kq) {
     hrow(y + D, hr[2 * D]);
     bool pry;
     const int zro = f3_refl(y, nf, &pry) * nf;
@@ -779,6 +791,8 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
     const T s11 = srow * scol;
     const bool own = own_c && y >= seg_lo && y < seg_hi && y < nf;
     const int zwo = zro + zc;
+    ZGroup<TZ> zo;
+    TZ zlo = TZ(0.0f);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int k = K0 + b, i = k % 3, j = k / 3;
@@ -787,16 +801,24 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
       const T bi2 = (i == 0) ? T(0.25) : (i == 1 ? -s2q : T(-0.25));
       T a = bi0 * hr[0][j] + bi2 * hr[2 * D][j];
       if (i != 1) a += bi1 * hr[D][j];
-      const T zv = T(ld_z(&q[b]));
+      const int pos = 3 * i + j - 1;              // place in the group ((0,0): low-pass)
+      const T zv = (i == 0 && j == 0) ? T(ld_z(&zl[kq])) : T(ld_z(&zq[kq].e[pos]));
       const T zn = (i == 1 && j == 1) ? fma(zv, s11, a)
                  : (i == 1) ? fma(zv, srow, a) : (j == 1) ? fma(zv, scol, a) : zv + a;
-      if (own) st_z(zout + (zwo + boff[b]), zn);
+      if (i == 0 && j == 0) zlo = to_z(zn, (TZ*)nullptr);
+      else zo.e[pos] = to_z(zn, (TZ*)nullptr);
       const T xv = zn - fmin(fmax(zn, -mu), mu);     // S_mu
       pr[0][j] += bi0 * xv;
       if (i != 1) pr[D][j] += bi1 * xv;
       pr[2 * D][j] += bi2 * xv;
     }
-    if (y + F3_PF < yc1) zload(y + F3_PF, q);
+    if (own) {
+      uint4* dstz = reinterpret_cast<uint4*>(zout + (gbase + 8 * zwo));
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dstz[v] = zo.v[v];
+      if (TOP) zout[lbase + zwo] = zlo;
+    }
+    if (y + F3_PF < yc1) zload(y + F3_PF, kq);
     // row y - D has all its contributions: horizontal synthesis
     const int r = y - D;
     if (r >= yo0) {
@@ -831,7 +853,7 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   for (int y = yc0; y < yc1; y += F3_PF) {
 #pragma unroll
     for (int k = 0; k < F3_PF; ++k)
-      if (y + k < yc1) step(y + k, zq[k]);
+      if (y + k < yc1) step(y + k, k);
   }
 }
 
@@ -909,6 +931,42 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
 int frame_tiles(int nf, int levels) {
   if (levels <= 2) return ((nf + F3_TX - 1) / F3_TX) * ((nf + F3_TY - 1) / F3_TY);
   return ((nf + FRAME_TILE - 1) / FRAME_TILE) * ((nf + FRAME_TILE - 1) / FRAME_TILE);
+}
+
+// Planar (band-major) <-> grouped z layout (L <= 2), element size E bytes.
+template <typename E>
+__global__ void k_zlayout(E* __restrict__ dst, const E* __restrict__ src, int nbands, int plane,
+                          int to_grouped) {
+  const size_t tot = (size_t)nbands * plane;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / plane), q = (int)(i - (size_t)b * plane);
+    const size_t g = (b < nbands - 1) ? (size_t)(b / 8) * 8 * plane + (size_t)8 * q + (b % 8) : i;
+    if (to_grouped) dst[g] = src[i]; else dst[i] = src[g];
+  }
+}
+
+bool z_grouped(int levels) { return levels <= 2; }
+
+size_t z_grouped_index(int b, size_t q, int nbands, size_t plane) {
+  return (b < nbands - 1) ? (size_t)(b / 8) * 8 * plane + 8 * q + (b % 8) : (size_t)b * plane + q;
+}
+
+void launch_z_layout(void* dst, const void* src, int levels, int nf, int elem_bytes,
+                     int to_grouped, cudaStream_t s) {
+  const int nbands = 8 * levels + 1, plane = nf * nf;
+  const size_t tot = (size_t)nbands * plane;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (elem_bytes == 8)
+    k_zlayout<unsigned long long><<<blocks, 256, 0, s>>>(static_cast<unsigned long long*>(dst),
+        static_cast<const unsigned long long*>(src), nbands, plane, to_grouped);
+  else if (elem_bytes == 4)
+    k_zlayout<unsigned int><<<blocks, 256, 0, s>>>(static_cast<unsigned int*>(dst),
+        static_cast<const unsigned int*>(src), nbands, plane, to_grouped);
+  else
+    k_zlayout<unsigned short><<<blocks, 256, 0, s>>>(static_cast<unsigned short*>(dst),
+        static_cast<const unsigned short*>(src), nbands, plane, to_grouped);
 }
 
 template <typename T, typename TZ>

@@ -892,9 +892,27 @@ int mlba_get_z(mlba_ctx* c, void* z_out, int on_device) {
   mlba_stats s;
   int rc = stats_of(c->b, 0, &s);
   if (rc != MLBA_OK) return rc;
-  const Prob& pd = c->b->hp[0].pd;
-  return copy_out(c->b, z_out, pd.z[s.iter & 1],
-                  (size_t)pd.nbands * pd.nf * pd.nf * zsize(c->b->z_store), on_device);
+  mlba_batch* B = c->b;
+  const Prob& pd = B->hp[0].pd;
+  const size_t es = zsize(B->z_store), plane = (size_t)pd.nf * pd.nf;
+  const size_t zbytes = (size_t)pd.nbands * plane * es;
+  if (!z_grouped(pd.levels)) return copy_out(B, z_out, pd.z[s.iter & 1], zbytes, on_device);
+  if (!z_out) return MLBA_E_INVAL;
+  // the library keeps z grouped; the caller gets band-major planes
+  if (on_device) {
+    launch_z_layout(z_out, pd.z[s.iter & 1], pd.levels, pd.nf, (int)es, 0, B->stream);
+    CK(cudaGetLastError());
+    return MLBA_OK;
+  }
+  std::vector<unsigned char> raw(zbytes);
+  CK(cudaMemcpyAsync(raw.data(), pd.z[s.iter & 1], zbytes, cudaMemcpyDeviceToHost, B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  unsigned char* out = static_cast<unsigned char*>(z_out);
+  for (int b = 0; b < pd.nbands; ++b)
+    for (size_t q = 0; q < plane; ++q)
+      std::memcpy(out + ((size_t)b * plane + q) * es,
+                  raw.data() + z_grouped_index(b, q, pd.nbands, plane) * es, es);
+  return MLBA_OK;
 }
 
 void mlba_destroy(mlba_ctx* c) {
@@ -981,16 +999,35 @@ int mlba_op_frame(mlba_ctx* c, const void* z_in, const void* u, void* z_out, voi
     CK(cudaMalloc(&dzo, zbytes));
     CK(cudaMemcpyAsync(dzi, z_in, zbytes, cudaMemcpyHostToDevice, B->stream));
   }
+  // the kernel works on grouped z (L <= 2): convert the caller's band-major
+  // planes into scratch copies and back
+  const bool grouped = z_grouped(pd.levels);
+  const int es = (int)zsize(B->z_store);
+  void *gzi = nullptr, *gzo = nullptr;
+  if (grouped) {
+    CK(cudaMalloc(&gzi, zbytes));
+    CK(cudaMalloc(&gzo, zbytes));
+    launch_z_layout(gzi, dzi, pd.levels, pd.nf, es, 1, B->stream);
+  }
+  void* kzi = grouped ? gzi : dzi;
+  void* kzo = grouped ? gzo : dzo;
   int rc = copy_in(B, pd.buf[SL_AUX0], u, fbytes, on_device);
   if (rc != MLBA_OK) return rc;
   if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
   if (B->dtype == MLBA_F64)
-    launch_frame<double, double>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->levels, B->stream);
+    launch_frame<double, double>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->stream);
   else if (B->z_store == MLBA_BF16)
-    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->levels, B->stream);
+    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->stream);
   else
-    launch_frame<float, float>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, dzi, dzo, mu, B->smem_frame, B->levels, B->stream);
+    launch_frame<float, float>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->stream);
   CK(cudaGetLastError());
+  if (grouped) {
+    launch_z_layout(dzo, gzo, pd.levels, pd.nf, es, 0, B->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(B->stream));
+    cudaFree(gzi);
+    cudaFree(gzo);
+  }
   rc = copy_out(B, f, pd.buf[SL_AUX1], fbytes, on_device);
   if (rc != MLBA_OK) return rc;
   if (!on_device) {

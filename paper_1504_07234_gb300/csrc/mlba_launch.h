@@ -70,6 +70,12 @@ template <typename T, typename TZ>
 size_t frame_smem_bytes(int levels);
 int frame_tiles(int nf, int levels);     // CTAs of the frame kernel for one problem
 int stencil_tiles(int outN);             // CTAs of the stencil for an outN x outN output
+// z layout: grouped (the 8 high bands of a level contiguous per pixel) for
+// L <= 2, band-major planes otherwise; conversion to / from band-major
+bool z_grouped(int levels);
+size_t z_grouped_index(int b, size_t q, int nbands, size_t plane);
+void launch_z_layout(void* dst, const void* src, int levels, int nf, int elem_bytes,
+                     int to_grouped, cudaStream_t s);
 template <typename T, typename TZ>
 cudaError_t frame_set_smem(size_t bytes);
 template <typename T>
