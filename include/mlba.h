@@ -155,6 +155,25 @@ int mlba_history(mlba_ctx* ctx, double* resnorm, double* alpha, int* beta, int c
 /* Copy the Bregman variable z out / in ((8L+1) x N_f x N_f, z_store type). */
 int mlba_get_z(mlba_ctx* ctx, void* z_out, int on_device);
 
+/* Checkpoint / resume.  The iteration of Eq. MLBA2 is fully determined by
+ * z^n (f^n = W^T S_mu(z^n) is kept with it so that no synthesis has to be
+ * re-run), the counters, the stop record, ||r^{n-1}||, alpha_{n-1} and the
+ * log-alpha warm start of Algorithm 4-NS; the state also carries the
+ * histories.  The state is a host blob of mlba_state_size() bytes: a header
+ * (sizes, dtype, z storage, max_iter), the scalars, the histories
+ * (max_iter + 2 entries each), f (N_f x N_f, dtype) and z (band-major planes,
+ * z_store type).  mlba_get_state synchronises the stream and copies it out;
+ * mlba_set_state loads it into a context created with the same PSF size, n,
+ * boundary treatment, levels, dtype, z storage and max_iter (else
+ * MLBA_E_INVAL).  Call mlba_set_data first (it resets the state): the
+ * observation g and delta are not part of the state.  The next mlba_iterate
+ * continues from the saved iteration exactly as the original context would
+ * have.  bytes: the caller's buffer size (>= mlba_state_size, else
+ * MLBA_E_INVAL).  No counterpart in the paper. */
+int mlba_state_size(mlba_ctx* ctx, size_t* bytes);
+int mlba_get_state(mlba_ctx* ctx, void* blob, size_t bytes);
+int mlba_set_state(mlba_ctx* ctx, const void* blob, size_t bytes);
+
 void mlba_destroy(mlba_ctx* ctx);
 const char* mlba_strerror(int status);
 

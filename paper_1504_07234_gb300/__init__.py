@@ -73,6 +73,9 @@ SIGNATURES = {
     "mlba_stats_get": (_I, [_P, ctypes.POINTER(Stats)]),
     "mlba_history": (_I, [_P, _P, _P, _P, _I]),
     "mlba_get_z": (_I, [_P, _P, _I]),
+    "mlba_state_size": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "mlba_get_state": (_I, [_P, _P, ctypes.c_size_t]),
+    "mlba_set_state": (_I, [_P, _P, ctypes.c_size_t]),
     "mlba_destroy": (None, [_P]),
     "mlba_strerror": (ctypes.c_char_p, [_I]),
     "mlba_op_blur": (_I, [_P, _P, _P, _I]),
@@ -268,6 +271,23 @@ class Context(_Base):
         _check(self.lib.mlba_get_z(self.h, ctypes.c_void_p(out.data_ptr()), 1), "mlba_get_z")
         self._leave()
         return out
+
+    def get_state(self):
+        """Checkpoint: the state blob (bytes) from which set_state resumes."""
+        n = ctypes.c_size_t()
+        _check(self.lib.mlba_state_size(self.h, ctypes.byref(n)), "mlba_state_size")
+        buf = (ctypes.c_ubyte * n.value)()
+        self._enter()
+        _check(self.lib.mlba_get_state(self.h, ctypes.cast(buf, ctypes.c_void_p), n.value),
+               "mlba_get_state")
+        return bytes(buf)
+
+    def set_state(self, blob):
+        """Resume from a blob of get_state (call set_data first)."""
+        buf = (ctypes.c_ubyte * len(blob)).from_buffer_copy(blob)
+        self._enter()
+        _check(self.lib.mlba_set_state(self.h, ctypes.cast(buf, ctypes.c_void_p), len(blob)),
+               "mlba_set_state")
 
     # -- operators -------------------------------------------------------------
     def _op_out(self, shape, device):

@@ -915,6 +915,116 @@ int mlba_get_z(mlba_ctx* c, void* z_out, int on_device) {
   return MLBA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// layout of the state blob of mlba_get_state / mlba_set_state
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t n, nf, p, bc, nbands, dtype, z_store, max_iter;
+  int32_t iter, stopped, stop_iter, status, nres, beta_last;
+  double resnorm, alpha_n, nb, qn;
+};
+constexpr uint32_t STATE_MAGIC = 0x4d4c4253u;   // "MLBS"
+constexpr uint32_t STATE_VERSION = 1;
+
+struct StateLayout {
+  size_t hist, f, z, total;
+};
+StateLayout state_layout(const mlba_batch* B) {
+  const Prob& pd = B->hp[0].pd;
+  const size_t cap = (size_t)pd.max_iter + 2;
+  const size_t plane = (size_t)pd.nf * pd.nf;
+  StateLayout L;
+  L.hist = sizeof(StateHeader);
+  L.f = al(L.hist + cap * (8 + 8 + 4));
+  L.z = al(L.f + plane * tsize(B->dtype));
+  L.total = L.z + (size_t)pd.nbands * plane * zsize(B->z_store);
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlba_state_size(mlba_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return MLBA_E_INVAL;
+  *bytes = state_layout(c->b).total;
+  return MLBA_OK;
+}
+
+int mlba_get_state(mlba_ctx* c, void* blob, size_t bytes) {
+  if (!c || !blob) return MLBA_E_INVAL;
+  mlba_batch* B = c->b;
+  const StateLayout L = state_layout(B);
+  if (bytes < L.total) return MLBA_E_INVAL;
+  const Prob& pd = B->hp[0].pd;
+  State st;
+  CK(cudaMemcpyAsync(&st, &B->d_states[0], sizeof(State), cudaMemcpyDeviceToHost, B->stream));
+  CK(cudaStreamSynchronize(B->stream));
+  unsigned char* out = static_cast<unsigned char*>(blob);
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = STATE_MAGIC; h.version = STATE_VERSION;
+  h.n = pd.n; h.nf = pd.nf; h.p = pd.p; h.bc = pd.bc; h.nbands = pd.nbands;
+  h.dtype = B->dtype; h.z_store = B->z_store; h.max_iter = pd.max_iter;
+  h.iter = st.iter; h.stopped = st.stopped; h.stop_iter = st.stop_iter; h.status = st.status;
+  h.nres = st.nres; h.beta_last = st.beta_last;
+  h.resnorm = st.resnorm; h.alpha_n = st.alpha_n; h.nb = st.nb; h.qn = st.qn;
+  std::memcpy(out, &h, sizeof(h));
+  const size_t cap = (size_t)pd.max_iter + 2;
+  CK(cudaMemcpy(out + L.hist, pd.hist_res, cap * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(out + L.hist + cap * 8, pd.hist_alpha, cap * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(out + L.hist + cap * 16, pd.hist_beta, cap * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(out + L.f, pd.buf[SL_F], (size_t)pd.nf * pd.nf * tsize(B->dtype),
+                cudaMemcpyDeviceToHost));
+  return mlba_get_z(c, out + L.z, 0);
+}
+
+int mlba_set_state(mlba_ctx* c, const void* blob, size_t bytes) {
+  if (!c || !blob) return MLBA_E_INVAL;
+  mlba_batch* B = c->b;
+  const StateLayout L = state_layout(B);
+  if (bytes < L.total) return MLBA_E_INVAL;
+  const Prob& pd = B->hp[0].pd;
+  const unsigned char* in = static_cast<const unsigned char*>(blob);
+  StateHeader h;
+  std::memcpy(&h, in, sizeof(h));
+  if (h.magic != STATE_MAGIC || h.version != STATE_VERSION || h.n != pd.n || h.nf != pd.nf ||
+      h.p != pd.p || h.bc != pd.bc || h.nbands != pd.nbands || h.dtype != B->dtype ||
+      h.z_store != B->z_store || h.max_iter != pd.max_iter || h.iter < 0 || h.iter > pd.max_iter ||
+      h.nres < 0 || h.nres > pd.max_iter + 2)
+    return MLBA_E_INVAL;
+  CK(cudaStreamSynchronize(B->stream));
+  const size_t cap = (size_t)pd.max_iter + 2;
+  CK(cudaMemcpy(pd.hist_res, in + L.hist, cap * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pd.hist_alpha, in + L.hist + cap * 8, cap * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(pd.hist_beta, in + L.hist + cap * 16, cap * 4, cudaMemcpyHostToDevice));
+  const size_t plane = (size_t)pd.nf * pd.nf;
+  CK(cudaMemcpy(pd.buf[SL_F], in + L.f, plane * tsize(B->dtype), cudaMemcpyHostToDevice));
+  // z^iter lives in the ping-pong buffer the next frame step reads
+  const size_t es = zsize(B->z_store);
+  const size_t zbytes = (size_t)pd.nbands * plane * es;
+  void* zdst = pd.z[h.iter & 1];
+  if (!z_grouped(pd.levels)) {
+    CK(cudaMemcpy(zdst, in + L.z, zbytes, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<unsigned char> g(zbytes);
+    for (int b = 0; b < pd.nbands; ++b)
+      for (size_t q = 0; q < plane; ++q)
+        std::memcpy(g.data() + z_grouped_index(b, q, pd.nbands, plane) * es,
+                    in + L.z + ((size_t)b * plane + q) * es, es);
+    CK(cudaMemcpy(zdst, g.data(), zbytes, cudaMemcpyHostToDevice));
+  }
+  State st = initial_state(pd);
+  st.iter = h.iter; st.stopped = h.stopped; st.stop_iter = h.stop_iter; st.status = h.status;
+  st.nres = h.nres; st.beta_last = h.beta_last;
+  st.resnorm = h.resnorm; st.alpha_n = h.alpha_n; st.nb = h.nb; st.qn = h.qn;
+  CK(cudaMemcpy(&B->d_states[0], &st, sizeof(State), cudaMemcpyHostToDevice));
+  return MLBA_OK;
+}
+
 void mlba_destroy(mlba_ctx* c) {
   if (!c) return;
   destroy_batch(c->b);

@@ -194,3 +194,55 @@ def test_batch_own_stop_rules(M):
             assert abs(st["stop_iter"] - ref["stop_iter"]) <= 1, (i, st, ref["stop_iter"])
         restoration_bars(b.result(i), ref, p)
     b.close()
+
+
+@pytest.mark.parametrize("bc,precond,transform,psf,alpha", [
+    ("periodic", "tikh_ns", "dft", I.psf_motion(7, 0.9), 0.05),
+    ("zero", "krylov", "dft", I.psf_motion(7, 0.9), 0.05),
+    ("rect", "bccb", "dft", I.psf_motion(7, 0.9), 0.3)])
+def test_checkpoint_resume_matches_uninterrupted(M, bc, precond, transform, psf, alpha):
+    """mlba_get_state after 5 iterations, mlba_set_state into a fresh context,
+    5 more iterations: the same f, residual history and alpha_n / beta_n as 10
+    uninterrupted iterations (the same kernels run on the same data)."""
+    n = 48 if bc != "rect" else 40
+    pr = small(bc, precond, n=n, psf=psf, alpha=alpha, transform=transform, iters=10)
+    kw = dict(mu=pr.mu, alpha=pr.alpha, levels=pr.levels, max_iter=10, stop=False, gamma=pr.gamma,
+              q=pr.q, rho=pr.rho, transform=pr.transform)
+    full = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype="f64", **kw)
+    full.set_data(pr.g, pr.delta)
+    full.iterate(11)
+    f_ref = full.result()
+    res_ref, al_ref, be_ref = full.history()
+    full.close()
+    a = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype="f64", **kw)
+    a.set_data(pr.g, pr.delta)
+    a.iterate(5)
+    blob = a.get_state()
+    a.close()
+    b = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype="f64", **kw)
+    b.set_data(pr.g, pr.delta)
+    b.set_state(blob)
+    assert b.stats()["iter"] == 5
+    b.iterate(6)
+    f = b.result()
+    res, al, be = b.history()
+    b.close()
+    assert np.abs(f - f_ref).max() <= 1e-12 * np.abs(f_ref).max()
+    np.testing.assert_allclose(res, res_ref, rtol=1e-12)
+    np.testing.assert_allclose(al, al_ref, rtol=1e-12)
+    assert list(be) == list(be_ref)
+
+
+def test_set_state_rejects_a_foreign_blob(M):
+    pr = small("periodic", "bccb", n=48, transform="dft", alpha=0.05)
+    a = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype="f64", mu=pr.mu, alpha=pr.alpha,
+                  levels=2, max_iter=10, stop=False)
+    a.set_data(pr.g, pr.delta)
+    blob = a.get_state()
+    b = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype="f64", mu=pr.mu, alpha=pr.alpha,
+                  levels=1, max_iter=10, stop=False)
+    b.set_data(pr.g, pr.delta)
+    with pytest.raises(M.MlbaError):
+        b.set_state(blob)
+    a.close()
+    b.close()
