@@ -892,26 +892,31 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
     else { src = static_cast<const T*>(pd.buf[SL_V]); mode = 0; }
     const bool interior = ty0 - C0 >= 0 && tx0 - C0 >= 0 && ty0 + F3_TY + C0 <= nf &&
                           tx0 + F3_TX + C0 <= nf;
-    constexpr int NT = 32 * F3_NWR, UB = 1;     // UB loads of a thread in flight
+    constexpr int NT = 32 * F3_NWR;
     constexpr int UN = Gm::UW * Gm::UH;
-    for (int i0 = threadIdx.x; i0 < UN; i0 += UB * NT) {
-      T v[UB];
-#pragma unroll
-      for (int u = 0; u < UB; ++u) {
-        const int idx = i0 + u * NT;
-        v[u] = T(0);
-        if (idx < UN) {
-          const int ry = idx / Gm::UW, rx = idx - ry * Gm::UW;
-          const int gy = ty0 - C0 + ry, gx = tx0 - C0 + rx;
-          int o;
-          const int ay = interior ? gy : refl_half(gy, nf, &o);
-          const int ax = interior ? gx : refl_half(gx, nf, &o);
-          v[u] = mode ? src[(size_t)ay * nf + ax] : fold_fetch<T>(pd, src, ay, ax);
-        }
+    if (mode) {
+      // plain copies of the (reflected) source: asynchronous, all of a
+      // thread's copies in flight together, no registers held
+      for (int idx = threadIdx.x; idx < UN; idx += NT) {
+        const int ry = idx / Gm::UW, rx = idx - ry * Gm::UW;
+        bool par;
+        const int ay = interior ? ty0 - C0 + ry : f3_refl(ty0 - C0 + ry, nf, &par);
+        const int ax = interior ? tx0 - C0 + rx : f3_refl(tx0 - C0 + rx, nf, &par);
+        const T* g = src + ((size_t)ay * nf + ax);
+        if (sizeof(T) == 8) cp_async_8(su + idx, g); else cp_async_4(su + idx, g);
       }
-#pragma unroll
-      for (int u = 0; u < UB; ++u)
-        if (i0 + u * NT < UN) su[i0 + u * NT] = v[u];
+      cp_commit();
+      cp_wait<0>();
+    } else {
+      // the BC fold of V sums up to four entries per element
+      for (int idx = threadIdx.x; idx < UN; idx += NT) {
+        const int ry = idx / Gm::UW, rx = idx - ry * Gm::UW;
+        const int gy = ty0 - C0 + ry, gx = tx0 - C0 + rx;
+        int o;
+        const int ay = interior ? gy : refl_half(gy, nf, &o);
+        const int ax = interior ? gx : refl_half(gx, nf, &o);
+        su[idx] = fold_fetch<T>(pd, src, ay, ax);
+      }
     }
   }
   __syncthreads();
