@@ -812,7 +812,7 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
   const int nb = (W + cb - 1) / cb;
   const int tot = nb * G * cb;
   const FastDiv fgc(G * cb), fcb(cb), fN(N);
-  constexpr int BATCH = 4;
+  constexpr int BATCH = 8;
   if (dct) {
     const T* S = static_cast<const T*>(pd.buf[SL_S]);
     for (int e0 = threadIdx.x; e0 < tot; e0 += BATCH * NT) {

@@ -894,15 +894,22 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
                           tx0 + F3_TX + C0 <= nf;
     constexpr int NT = 32 * F3_NWR;
     constexpr int UN = Gm::UW * Gm::UH;
-    if (mode) {
+    // the BC fold of V has a single term wherever the tile keeps c pixels
+    // from the image edges (or for zero BCs): u(a, b) = V(a + c, b + c)
+    const int cc = pd.c;
+    const bool single = mode == 0 && interior &&
+                        (pd.bc == BC_ZERO || (ty0 - C0 >= cc && tx0 - C0 >= cc &&
+                                              ty0 + F3_TY + C0 <= nf - cc && tx0 + F3_TX + C0 <= nf - cc));
+    if (mode || single) {
       // plain copies of the (reflected) source: asynchronous, all of a
       // thread's copies in flight together, no registers held
+      const int pitch = mode ? nf : pd.ne, off = mode ? 0 : cc;
       for (int idx = threadIdx.x; idx < UN; idx += NT) {
         const int ry = idx / Gm::UW, rx = idx - ry * Gm::UW;
         bool par;
         const int ay = interior ? ty0 - C0 + ry : f3_refl(ty0 - C0 + ry, nf, &par);
         const int ax = interior ? tx0 - C0 + rx : f3_refl(tx0 - C0 + rx, nf, &par);
-        const T* g = src + ((size_t)ay * nf + ax);
+        const T* g = src + ((size_t)(ay + off) * pitch + (ax + off));
         if (sizeof(T) == 8) cp_async_8(su + idx, g); else cp_async_4(su + idx, g);
       }
       cp_commit();
