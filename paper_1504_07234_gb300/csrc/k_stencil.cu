@@ -308,13 +308,13 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   const T* aux = static_cast<const T*>(pd.buf[aux_slot]);
   T lacc = T(0);
   const int gx = tx0 + x2;
-  auto emit = [&](size_t o, T a) {
+  auto emit = [&](size_t o, T a, T xv) {
     if (MODE == ST_FWD_RESID) {
-      const T r = aux[o] - a;
+      const T r = xv - a;
       dst[o] = r;
       lacc += r * r;
     } else if (MODE == ST_FWD_PCGQ) {
-      const T pv = aux[o];
+      const T pv = xv;
       const T qv = a + T(pd.alpha) * pv;
       dst[o] = qv;
       lacc += pv * qv;
@@ -322,13 +322,24 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
       dst[o] = a;
     }
   };
+  // the second operand (g or p) for all 16 outputs first, then the stores
+  T2 av[8];
+  if (MODE == ST_FWD_RESID || MODE == ST_FWD_PCGQ) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gy = ty0 + y8 + j;
+      const size_t o = (size_t)gy * outN + gx;
+      av[j].x = (gy < outN && gx < outN) ? aux[o] : T(0);
+      av[j].y = (gy < outN && gx + 1 < outN) ? aux[o + 1] : T(0);
+    }
+  }
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int gy = ty0 + y8 + j;
     if (gy < outN) {
       const size_t o = (size_t)gy * outN + gx;
-      if (gx < outN) emit(o, acc[j].x);
-      if (gx + 1 < outN) emit(o + 1, acc[j].y);
+      if (gx < outN) emit(o, acc[j].x, av[j].x);
+      if (gx + 1 < outN) emit(o + 1, acc[j].y, av[j].y);
     }
   }
   if (MODE == ST_FWD_RESID || MODE == ST_FWD_PCGQ) {
