@@ -364,7 +364,9 @@ __device__ __forceinline__ bool spec_elem(const Prob& pd, int blk, int e, T& pw,
   const int blksz = N * cb;
   const int b = L / blksz;
   const int rem = L - b * blksz;
-  const int k1 = rem / cb, c = rem - k1 * cb;
+  // rem < 2 TR_CAP and cb <= 2 TR_CAP: rem * cb < 2^32, the multiply-high
+  // quotient is exact
+  const int k1 = FastDiv(cb).div(rem), c = rem - k1 * cb;
   const int k2 = b * cb + c;
   if (k2 >= W) return false;
   if (dct) {
@@ -541,16 +543,31 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
   const int W = dct ? N : pd.half;
   const int kb = blk * cb;
   const double b0 = st.nb;
+  const T* w = static_cast<const T*>(pd.w) + base;
   if (threadIdx.x < NS_CAND)
     s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
   __syncthreads();
   float ca[NS_CAND], cF[NS_CAND], cG[NS_CAND];
 #pragma unroll
   for (int j = 0; j < NS_CAND; ++j) { ca[j] = s_ca[j]; cF[j] = 0.f; cG[j] = 0.f; }
-  const T* w = static_cast<const T*>(pd.w) + base;
   const FastDiv fcb(cb);
   T sP = T(0);
-  for (int e = threadIdx.x; e < N * cb; e += NT) {
+  // chunks of MV elements per thread: the chunk's sigma loads first (all in
+  // flight together), then its sums (a DFT block holds <= TR_CAP complex
+  // values, a DCT block <= 2 TR_CAP reals)
+  constexpr int MV = TR_CAP / NT;
+#pragma unroll 1
+  for (int e0 = 0; e0 < N * cb; e0 += MV * NT) {
+  float wv[MV];
+#pragma unroll
+  for (int qq = 0; qq < MV; ++qq) {
+    const int e = e0 + threadIdx.x + qq * NT;
+    wv[qq] = (e < N * cb) ? (float)w[e] : 1.f;
+  }
+#pragma unroll
+  for (int qq = 0; qq < MV; ++qq) {
+    const int e = e0 + threadIdx.x + qq * NT;
+    if (e >= N * cb) break;
     const int k1 = fcb.div(e), c = e - k1 * cb;
     const int k2 = kb + c;
     if (k2 >= W) continue;
@@ -564,7 +581,8 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
       pw = m * (vr * vr + vi * vi);
     }
     sP += pw;
-    ns_cand_acc((float)pw, (float)w[e], ca, cF, cG);
+    ns_cand_acc((float)pw, wv[qq], ca, cF, cG);
+  }
   }
   T v[K];
 #pragma unroll
