@@ -223,6 +223,8 @@ def main():
     ap.add_argument("--impl", default="mlba", choices=["mlba", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
+    ap.add_argument("--one-group", action="store_true",
+                    help="advance the whole batch launch by launch (no two-group schedule)")
     ap.add_argument("--problems", type=int, default=64,
                     help="first K problems of the batch (small cases for profiling)")
     args = ap.parse_args()
@@ -251,7 +253,7 @@ def main():
     reps_prof = 20
     max_iter = W + K + 2 * reps_prof + 20
     batch = M.Batch(descs(probs), dtype="f32", levels=2, stop=False, max_iter=max_iter,
-                    rect_ns_hybrid=True)
+                    rect_ns_hybrid=True, two_group=not args.one_group)
     stream = batch.stream
     # warm-up
     batch.iterate(W)
@@ -331,7 +333,9 @@ def main():
                 "config": {"workload": WORKLOAD if len(probs) == 64 else f"first {len(probs)} problems of: " + WORKLOAD,
                            "problems": len(probs), "mpix_per_step_per_gpu": mpix,
                            "l2": "inputs larger than L2 (Bregman variable ~2.7 GB)",
-                           "parallelism": f"replicas x{ws}, problems sharded"},
+                           "parallelism": f"replicas x{ws}, problems sharded",
+                           "schedule": "one group" if args.one_group else
+                           "two groups half a step apart on two streams"},
                 "clocks": ck, "e2e": e2e, "gpu_launches": kernels * K, "roofline": roofline,
                 "step_roofline": {"min_bytes": bmin, "frac": step_frac, "peak": hbm},
                 "stage_ms": stage_ms, "cpu_baseline": cpu}

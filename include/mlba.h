@@ -95,12 +95,16 @@ typedef struct mlba_opts {
   int stop;           /* 1: stop on the discrepancy principle; 0: run max_iter iterations */
   int rect_ns_hybrid; /* 1: allow MLBA_P_TIKH_NS with MLBA_RECT (A^T (CC^T + alpha_n I)^{-1}) */
   void* stream;       /* cudaStream_t */
+  int two_group;      /* batches of >= 2 problems: 1 (default) runs two groups of about equal
+                         work half a step apart on two streams, so that one group's framelet
+                         update overlaps the other's residual and preconditioner; 0 advances
+                         the whole batch launch by launch.  The iterates are the same. */
 } mlba_opts;
 
 /* Fill defaults: mu = 10/255, alpha = 0.05, gamma = 1 + 1e-15, q = 0.5,
  * rho = 1e-4, pcg_tol = 1e-3, levels = 1, max_iter = 200, pcg_max = 5,
  * dtype = F32, z_store = F32, transform = AUTO, stop = 1, hybrid = 0,
- * stream = NULL. */
+ * stream = NULL, two_group = 1. */
 void mlba_opts_default(mlba_opts* o);
 
 /* ---- statistics ------------------------------------------------------- */
@@ -213,6 +217,8 @@ typedef struct mlba_batch mlba_batch;
  * stream; each has its own size, PSF, BC, preconditioner, mu, alpha, delta
  * and budget.  Each problem stops on its own rule. */
 int mlba_batch_create(const mlba_problem* probs, int count, const mlba_opts* opts, mlba_batch** out);
+/* Enqueue k steps on the batch stream (asynchronous).  Every live problem
+ * advances by k iterations, whatever opts.two_group says. */
 int mlba_batch_iterate(mlba_batch* b, int k);
 /* Number of problems not yet stopped (synchronises). */
 int mlba_batch_active(mlba_batch* b, int* n_active);
@@ -231,7 +237,9 @@ int mlba_batch_set_data(mlba_batch* b, int i, const void* g, int g_on_device, do
  * launch in milliseconds.  Stages 1-4 run outside the graph and advance the
  * per-problem state arbitrarily: call mlba_batch_reset before using results. */
 int mlba_batch_profile(mlba_batch* b, int stage, int reps, float* ms_per_rep);
-/* Number of kernel nodes in the captured step graph. */
+/* Kernel launches per step: the kernel nodes of the captured step graph (with
+ * the two-group schedule, of the body graph, which holds one step of each
+ * group). */
 int mlba_batch_graph_kernels(mlba_batch* b, int* n_kernels);
 void mlba_batch_destroy(mlba_batch* b);
 

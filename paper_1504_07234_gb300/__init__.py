@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
                 ("levels", ctypes.c_int), ("max_iter", ctypes.c_int), ("pcg_max", ctypes.c_int),
                 ("dtype", ctypes.c_int), ("z_store", ctypes.c_int), ("transform", ctypes.c_int),
                 ("stop", ctypes.c_int), ("rect_ns_hybrid", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("two_group", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -132,7 +132,7 @@ def _torch():
 
 def make_opts(dtype="f32", z_store=None, mu=10.0 / 255.0, alpha=0.05, levels=1, max_iter=200,
               stop=True, gamma=1.0 + 1e-15, q=0.5, rho=1e-4, transform="auto", pcg_tol=1e-3,
-              pcg_max=5, rect_ns_hybrid=False, stream=None) -> Opts:
+              pcg_max=5, rect_ns_hybrid=False, stream=None, two_group=True) -> Opts:
     lib = load_library()
     o = Opts()
     lib.mlba_opts_default(ctypes.byref(o))
@@ -144,6 +144,7 @@ def make_opts(dtype="f32", z_store=None, mu=10.0 / 255.0, alpha=0.05, levels=1, 
     o.stop = 1 if stop else 0
     o.rect_ns_hybrid = 1 if rect_ns_hybrid else 0
     o.stream = stream
+    o.two_group = 1 if two_group else 0
     return o
 
 

@@ -1008,6 +1008,18 @@ cudaError_t frame_set_smem(size_t bytes) {
                               (int)bytes);
 }
 
+bool is_frame_kernel(const void* func) {
+  const void* k[] = {
+      (const void*)k_frame3<float, float, 1>, (const void*)k_frame3<float, float, 2>,
+      (const void*)k_frame3<float, __nv_bfloat16, 1>, (const void*)k_frame3<float, __nv_bfloat16, 2>,
+      (const void*)k_frame3<double, double, 1>, (const void*)k_frame3<double, double, 2>,
+      (const void*)k_frame<float, float>, (const void*)k_frame<float, __nv_bfloat16>,
+      (const void*)k_frame<double, double>};
+  for (const void* f : k)
+    if (f == func) return true;
+  return false;
+}
+
 #define INST(T, TZ)                                                                          \
   template size_t frame_smem_bytes<T, TZ>(int);                                              \
   template void launch_frame<T, TZ>(const Prob*, State*, const int2*, int, int, int,          \

@@ -48,6 +48,22 @@ struct ItemList {
   int count = 0;
 };
 
+// The launches of one step over a set of problems.
+struct StepLists {
+  ItemList blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry, cols_kry,
+      vec_kry, vec_kry_bc, frame;
+  int any_krylov = 0, any_spec = 0, any_ns = 0, pcg_max = 5;
+};
+struct StepItems {
+  std::vector<int2> blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
+      cols_kry, vec_kry, vec_kry_bc, frame;
+  int any_krylov = 0, any_spec = 0, any_ns = 0, pcg_max = 5;
+};
+
+// parts of a step: a = residual and stop rule, then the preconditioner;
+// b = A^T and the framelet update
+enum { PART_A = 1, PART_B = 2, PART_ALL = 3 };
+
 }  // namespace
 
 struct mlba_batch {
@@ -69,6 +85,18 @@ struct mlba_batch {
   cudaGraphExec_t exec = nullptr;
   bool has_data = false;
   int any_krylov = 0, any_spec = 0, any_ns = 0, any_stat = 0;
+  // Two-group schedule (batches of two or more problems): group 1 runs half a
+  // step behind group 0 on a second stream, so that one group's framelet
+  // sweep (HBM-bound) overlaps the other group's residual and preconditioner
+  // (latency-bound).  iterate(k) replays: head (group 0: part a), body k - 1
+  // times (group 0: part b, part a | group 1: part a, part b), tail (group 0:
+  // part b | group 1: part a, part b); every problem then has done k steps.
+  bool split = false;
+  StepLists grp[2];
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraph_t g_head = nullptr, g_body = nullptr, g_tail = nullptr;
+  cudaGraphExec_t x_head = nullptr, x_body = nullptr, x_tail = nullptr;
 };
 
 struct mlba_ctx {
@@ -165,58 +193,187 @@ State initial_state(const Prob& pd) {
 }
 
 template <typename T, typename TZ>
-void enqueue_step(mlba_batch* B, cudaStream_t s) {
+void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
   const Prob* P = B->d_probs;
   State* S = B->d_states;
-  // a2: r = g - A f with ||r||^2 and the stop rule
-  launch_stencil<T>(ST_FWD_RESID, P, S, B->blur.dev, B->blur.count, SL_F, SL_R, SL_G, 0,
-                    B->smem_stencil, s);
-  // a4: spectral preconditioners (Algorithms 1, 3, 4, 4-NS)
-  if (B->any_spec) {
-    launch_rows_fwd<T>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_R, 0, B->smem_fft, s);
-    launch_cols<T>(P, S, B->cols_stat.dev, B->cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
-    if (B->any_ns) {
-      launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
-      // (the bracketing pass runs inside the forward column pass)
-      for (int k = 1; k < ns_passes<T>(); ++k) launch_spec<T>(P, S, B->spec.dev, B->spec.count, 0, s);
-      launch_cols<T>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
+  if (part & PART_A) {
+    // a2: r = g - A f with ||r||^2 and the stop rule
+    launch_stencil<T>(ST_FWD_RESID, P, S, L.blur.dev, L.blur.count, SL_F, SL_R, SL_G, 0,
+                      B->smem_stencil, s);
+    // a4: spectral preconditioners (Algorithms 1, 3, 4, 4-NS)
+    if (L.any_spec) {
+      launch_rows_fwd<T>(P, S, L.rows_spec.dev, L.rows_spec.count, SL_R, 0, B->smem_fft, s);
+      launch_cols<T>(P, S, L.cols_stat.dev, L.cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
+      if (L.any_ns) {
+        launch_cols<T>(P, S, L.cols_ns.dev, L.cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
+        // (the bracketing pass runs inside the forward column pass)
+        for (int k = 1; k < ns_passes<T>(); ++k) launch_spec<T>(P, S, L.spec.dev, L.spec.count, 0, s);
+        launch_cols<T>(P, S, L.cols_ns.dev, L.cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
+      }
+      launch_rows_inv<T>(P, S, L.rows_spec.dev, L.rows_spec.count, SL_T, 0, B->smem_fft, s);
     }
-    launch_rows_inv<T>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
-  }
-  // a4': Algorithm 2, PCG on (A A^T + alpha I) t = r preconditioned by (CC^T + alpha I)^{-1}
-  if (B->any_krylov) {
-    const int maxs = B->hp.empty() ? 5 : B->hp[0].pd.pcg_max;
-    launch_vec<T>(VEC_PCG_INIT, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
-    launch_rows_fwd<T>(P, S, B->rows_kry.dev, B->rows_kry.count, SL_PRES, 1, B->smem_fft, s);
-    launch_cols<T>(P, S, B->cols_kry.dev, B->cols_kry.count, COL_FUSED, 1, 0.0, 0, B->smem_fft, s);
-    launch_rows_inv<T>(P, S, B->rows_kry.dev, B->rows_kry.count, SL_PZ, 1, B->smem_fft, s);
-    launch_vec<T>(VEC_PCG_RHO0, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
-    for (int k = 0; k < maxs; ++k) {
-      launch_stencil<T>(ST_CORR, P, S, B->corr_kry.dev, B->corr_kry.count, SL_PP, SL_V, SL_V, 1,
-                        B->smem_stencil, s);
-      launch_vec<T>(VEC_FOLD, P, S, B->vec_kry_bc.dev, B->vec_kry_bc.count, 1, s);
-      launch_stencil<T>(ST_FWD_PCGQ, P, S, B->blur_kry.dev, B->blur_kry.count, -1, SL_PQ, SL_PP, 1,
-                        B->smem_stencil, s);
-      launch_vec<T>(VEC_PCG_AXPY, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
-      launch_rows_fwd<T>(P, S, B->rows_kry.dev, B->rows_kry.count, SL_PRES, 1, B->smem_fft, s);
-      launch_cols<T>(P, S, B->cols_kry.dev, B->cols_kry.count, COL_FUSED, 1, 0.0, 0, B->smem_fft, s);
-      launch_rows_inv<T>(P, S, B->rows_kry.dev, B->rows_kry.count, SL_PZ, 1, B->smem_fft, s);
-      launch_vec<T>(VEC_PCG_RHO, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
-      launch_vec<T>(VEC_PCG_PUPD, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
+    // a4': Algorithm 2, PCG on (A A^T + alpha I) t = r preconditioned by (CC^T + alpha I)^{-1}
+    if (L.any_krylov) {
+      const int maxs = L.pcg_max;
+      launch_vec<T>(VEC_PCG_INIT, P, S, L.vec_kry.dev, L.vec_kry.count, 1, s);
+      launch_rows_fwd<T>(P, S, L.rows_kry.dev, L.rows_kry.count, SL_PRES, 1, B->smem_fft, s);
+      launch_cols<T>(P, S, L.cols_kry.dev, L.cols_kry.count, COL_FUSED, 1, 0.0, 0, B->smem_fft, s);
+      launch_rows_inv<T>(P, S, L.rows_kry.dev, L.rows_kry.count, SL_PZ, 1, B->smem_fft, s);
+      launch_vec<T>(VEC_PCG_RHO0, P, S, L.vec_kry.dev, L.vec_kry.count, 1, s);
+      for (int k = 0; k < maxs; ++k) {
+        launch_stencil<T>(ST_CORR, P, S, L.corr_kry.dev, L.corr_kry.count, SL_PP, SL_V, SL_V, 1,
+                          B->smem_stencil, s);
+        launch_vec<T>(VEC_FOLD, P, S, L.vec_kry_bc.dev, L.vec_kry_bc.count, 1, s);
+        launch_stencil<T>(ST_FWD_PCGQ, P, S, L.blur_kry.dev, L.blur_kry.count, -1, SL_PQ, SL_PP, 1,
+                          B->smem_stencil, s);
+        launch_vec<T>(VEC_PCG_AXPY, P, S, L.vec_kry.dev, L.vec_kry.count, 1, s);
+        launch_rows_fwd<T>(P, S, L.rows_kry.dev, L.rows_kry.count, SL_PRES, 1, B->smem_fft, s);
+        launch_cols<T>(P, S, L.cols_kry.dev, L.cols_kry.count, COL_FUSED, 1, 0.0, 0, B->smem_fft, s);
+        launch_rows_inv<T>(P, S, L.rows_kry.dev, L.rows_kry.count, SL_PZ, 1, B->smem_fft, s);
+        launch_vec<T>(VEC_PCG_RHO, P, S, L.vec_kry.dev, L.vec_kry.count, 1, s);
+        launch_vec<T>(VEC_PCG_PUPD, P, S, L.vec_kry.dev, L.vec_kry.count, 1, s);
+      }
+      launch_vec<T>(VEC_PCG_FINISH, P, S, L.vec_kry.dev, L.vec_kry.count, 1, s);
     }
-    launch_vec<T>(VEC_PCG_FINISH, P, S, B->vec_kry.dev, B->vec_kry.count, 1, s);
   }
-  // a6: full correlation of t (A^T up to the BC fold)
-  launch_stencil<T>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
-  // a1: z += W u, x = S_mu(z), f = W^T x
-  launch_frame<T, TZ>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0,
-                      B->smem_frame, B->levels, s);
+  if (part & PART_B) {
+    // a6: full correlation of t (A^T up to the BC fold)
+    launch_stencil<T>(ST_CORR, P, S, L.corr.dev, L.corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
+    // a1: z += W u, x = S_mu(z), f = W^T x
+    launch_frame<T, TZ>(P, S, L.frame.dev, L.frame.count, -1, SL_F, nullptr, nullptr, 0.0,
+                        B->smem_frame, B->levels, s);
+  }
 }
 
-void enqueue_dispatch(mlba_batch* B, cudaStream_t s) {
-  if (B->dtype == MLBA_F64) enqueue_step<double, double>(B, s);
-  else if (B->z_store == MLBA_BF16) enqueue_step<float, __nv_bfloat16>(B, s);
-  else enqueue_step<float, float>(B, s);
+void enqueue_dispatch(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
+  if (B->dtype == MLBA_F64) enqueue_step<double, double>(B, L, part, s);
+  else if (B->z_store == MLBA_BF16) enqueue_step<float, __nv_bfloat16>(B, L, part, s);
+  else enqueue_step<float, float>(B, L, part, s);
+}
+
+StepLists all_lists(const mlba_batch* B) {
+  StepLists L;
+  L.blur = B->blur; L.corr = B->corr; L.corr_kry = B->corr_kry; L.blur_kry = B->blur_kry;
+  L.rows_spec = B->rows_spec; L.cols_stat = B->cols_stat; L.cols_ns = B->cols_ns; L.spec = B->spec;
+  L.rows_kry = B->rows_kry; L.cols_kry = B->cols_kry; L.vec_kry = B->vec_kry;
+  L.vec_kry_bc = B->vec_kry_bc; L.frame = B->frame;
+  L.any_krylov = B->any_krylov; L.any_spec = B->any_spec; L.any_ns = B->any_ns;
+  L.pcg_max = B->hp.empty() ? 5 : B->hp[0].pd.pcg_max;
+  return L;
+}
+
+// the launches of one step of problem i (kinds as in the whole-batch lists)
+void collect_step(const Prob& pd, int i, StepItems& V) {
+  auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
+  add(V.blur, pd.nblk_blur);
+  add(V.frame, pd.nblk_frame);
+  if (pd.use_adj) add(V.corr, pd.nblk_corr);
+  const bool specp = pd.transform != TR_NONE;
+  if (pd.precond == P_KRYLOV) {
+    add(V.corr_kry, pd.nblk_corr); add(V.blur_kry, pd.nblk_blur); add(V.rows_kry, pd.nblk_rows);
+    add(V.cols_kry, pd.nblk_cols); add(V.vec_kry, pd.nblk_vec);
+    if (pd.bc != BC_RECT) add(V.vec_kry_bc, pd.nblk_vec);
+    V.any_krylov = 1;
+  } else if (specp) {
+    add(V.rows_spec, pd.nblk_rows);
+    V.any_spec = 1;
+    if (pd.ns) { add(V.cols_ns, pd.nblk_cols); add(V.spec, pd.nblk_spec); V.any_ns = 1; }
+    else add(V.cols_stat, pd.nblk_cols);
+  }
+  V.pcg_max = pd.pcg_max;
+}
+
+// Low priority for the framelet launches of the two-group graphs: the
+// latency-bound launches of the other group take SM resources first and the
+// framelet sweep fills the rest.
+int set_node_priorities(cudaGraph_t g, int lo, int hi) {
+  size_t cnt = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &cnt));
+  std::vector<cudaGraphNode_t> nodes(cnt);
+  CK(cudaGraphGetNodes(g, nodes.data(), &cnt));
+  for (size_t i = 0; i < cnt; ++i) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nodes[i], &t));
+    if (t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    CK(cudaGraphKernelNodeGetParams(nodes[i], &kp));
+    cudaKernelNodeAttrValue v;
+    std::memset(&v, 0, sizeof(v));
+    v.priority = is_frame_kernel(kp.func) ? lo : hi;
+    CK(cudaGraphKernelNodeSetAttribute(nodes[i], cudaKernelNodeAttributePriority, &v));
+  }
+  return MLBA_OK;
+}
+
+// capture parts pa of group 0 and pb of group 1 (0: none) as one graph; the
+// group-0 parts run in order a, b (head) or b, a (body) on the batch stream,
+// the group-1 parts (a then b) on the side stream
+int capture_split(mlba_batch* B, int pa, bool b_first, int pb, cudaGraph_t* g, cudaGraphExec_t* x) {
+  cudaStream_t s = B->stream;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MLBA_E_CUDA;
+  if (pb) {
+    cudaEventRecord(B->ev_fork, s);
+    cudaStreamWaitEvent(B->side, B->ev_fork, 0);
+    if (pb & PART_A) enqueue_dispatch(B, B->grp[1], PART_A, B->side);
+    if (pb & PART_B) enqueue_dispatch(B, B->grp[1], PART_B, B->side);
+  }
+  if (b_first) {
+    if (pa & PART_B) enqueue_dispatch(B, B->grp[0], PART_B, s);
+    if (pa & PART_A) enqueue_dispatch(B, B->grp[0], PART_A, s);
+  } else {
+    if (pa & PART_A) enqueue_dispatch(B, B->grp[0], PART_A, s);
+    if (pa & PART_B) enqueue_dispatch(B, B->grp[0], PART_B, s);
+  }
+  if (pb) {
+    cudaEventRecord(B->ev_join, B->side);
+    cudaStreamWaitEvent(s, B->ev_join, 0);
+  }
+  if (cudaStreamEndCapture(s, g) != cudaSuccess) return MLBA_E_CUDA;
+  int lo = 0, hi = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  if (set_node_priorities(*g, lo, hi) != MLBA_OK) return MLBA_E_CUDA;
+  CK(cudaGraphInstantiate(x, *g, 0));
+  return MLBA_OK;
+}
+
+// Split the problems into two groups of about equal work (largest first, each
+// to the lighter group) and capture the head, body and tail graphs.
+int build_split(mlba_batch* B) {
+  const int count = (int)B->hp.size();
+  if (count < 2) return MLBA_OK;
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  auto work = [&](int i) { const Prob& pd = B->hp[i].pd; return (double)pd.nf * pd.nf; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+  std::vector<int> grp(count, 0);
+  double w[2] = {0.0, 0.0};
+  for (int i : order) { const int g = w[1] < w[0] ? 1 : 0; grp[i] = g; w[g] += work(i); }
+  StepItems V[2];
+  for (int i = 0; i < count; ++i) collect_step(B->hp[i].pd, i, V[grp[i]]);
+  int rc = MLBA_OK;
+  for (int g = 0; g < 2; ++g) {
+    StepLists& L = B->grp[g];
+    const StepItems& v = V[g];
+    rc |= build_list(B, L.blur, v.blur); rc |= build_list(B, L.corr, v.corr);
+    rc |= build_list(B, L.corr_kry, v.corr_kry); rc |= build_list(B, L.blur_kry, v.blur_kry);
+    rc |= build_list(B, L.rows_spec, v.rows_spec); rc |= build_list(B, L.cols_stat, v.cols_stat);
+    rc |= build_list(B, L.cols_ns, v.cols_ns); rc |= build_list(B, L.spec, v.spec);
+    rc |= build_list(B, L.rows_kry, v.rows_kry); rc |= build_list(B, L.cols_kry, v.cols_kry);
+    rc |= build_list(B, L.vec_kry, v.vec_kry); rc |= build_list(B, L.vec_kry_bc, v.vec_kry_bc);
+    rc |= build_list(B, L.frame, v.frame);
+    L.any_krylov = v.any_krylov; L.any_spec = v.any_spec; L.any_ns = v.any_ns;
+    L.pcg_max = B->hp[0].pd.pcg_max;
+  }
+  if (rc != MLBA_OK) return MLBA_E_CUDA;
+  CK(cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming));
+  if (capture_split(B, PART_A, false, 0, &B->g_head, &B->x_head) != MLBA_OK ||
+      capture_split(B, PART_ALL, true, PART_ALL, &B->g_body, &B->x_body) != MLBA_OK ||
+      capture_split(B, PART_B, false, PART_ALL, &B->g_tail, &B->x_tail) != MLBA_OK)
+    return MLBA_E_CUDA;
+  B->split = true;
+  return MLBA_OK;
 }
 
 int set_smem_attrs(mlba_batch* B) {
@@ -243,6 +400,11 @@ void destroy_batch(mlba_batch* B) {
   if (!B) return;
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
+  for (cudaGraphExec_t x : {B->x_head, B->x_body, B->x_tail}) if (x) cudaGraphExecDestroy(x);
+  for (cudaGraph_t g : {B->g_head, B->g_body, B->g_tail}) if (g) cudaGraphDestroy(g);
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+  if (B->ev_join) cudaEventDestroy(B->ev_join);
+  if (B->side) cudaStreamDestroy(B->side);
   for (int2* p : B->allocs) cudaFree(p);
   if (B->arena) cudaFree(B->arena);
   if (B->d_probs) cudaFree(B->d_probs);
@@ -582,11 +744,12 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     destroy_batch(B); return MLBA_E_CUDA;
   }
-  enqueue_dispatch(B, B->stream);
+  enqueue_dispatch(B, all_lists(B), PART_ALL, B->stream);
   if (cudaStreamEndCapture(B->stream, &B->graph) != cudaSuccess ||
       cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess) {
     destroy_batch(B); return MLBA_E_CUDA;
   }
+  if (o.two_group && build_split(B) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
   *out = B;
   return MLBA_OK;
 }
@@ -671,6 +834,7 @@ void mlba_opts_default(mlba_opts* o) {
   o->levels = 1;
   o->max_iter = 200;
   o->pcg_max = 5;
+  o->two_group = 1;
   o->dtype = MLBA_F32;
   o->z_store = MLBA_F32;
   o->transform = MLBA_TR_AUTO;
@@ -716,6 +880,13 @@ int mlba_batch_create(const mlba_problem* probs, int count, const mlba_opts* opt
 int mlba_batch_iterate(mlba_batch* B, int k) {
   if (!B || k < 0) return MLBA_E_INVAL;
   if (!B->has_data) return MLBA_E_STATE;
+  if (k == 0) return MLBA_OK;
+  if (B->split) {
+    CK(cudaGraphLaunch(B->x_head, B->stream));
+    for (int i = 1; i < k; ++i) CK(cudaGraphLaunch(B->x_body, B->stream));
+    CK(cudaGraphLaunch(B->x_tail, B->stream));
+    return MLBA_OK;
+  }
   for (int i = 0; i < k; ++i) CK(cudaGraphLaunch(B->exec, B->stream));
   return MLBA_OK;
 }
@@ -808,10 +979,13 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
 
 int mlba_batch_graph_kernels(mlba_batch* B, int* n) {
   if (!B || !n || !B->graph) return MLBA_E_INVAL;
+  // kernels of one step: the body graph of the two-group schedule holds one
+  // step of each group
+  cudaGraph_t g = B->split ? B->g_body : B->graph;
   size_t cnt = 0;
-  CK(cudaGraphGetNodes(B->graph, nullptr, &cnt));
+  CK(cudaGraphGetNodes(g, nullptr, &cnt));
   std::vector<cudaGraphNode_t> nodes(cnt);
-  CK(cudaGraphGetNodes(B->graph, nodes.data(), &cnt));
+  CK(cudaGraphGetNodes(g, nodes.data(), &cnt));
   int k = 0;
   for (size_t i = 0; i < cnt; ++i) {
     cudaGraphNodeType t;

@@ -69,6 +69,7 @@ void launch_frame(const Prob* probs, State* states, const int2* items, int nitem
 template <typename T, typename TZ>
 size_t frame_smem_bytes(int levels);
 int frame_tiles(int nf, int levels);     // CTAs of the frame kernel for one problem
+bool is_frame_kernel(const void* func);  // func is one of the framelet-update kernels
 int stencil_tiles(int outN);             // CTAs of the stencil for an outN x outN output
 // z layout: grouped (the 8 high bands of a level contiguous per pixel) for
 // L <= 2, band-major planes otherwise; conversion to / from band-major

@@ -179,6 +179,37 @@ def test_batch_matches_single(M):
     b.close()
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_two_group_schedule_equals_one_group(M, dtype):
+    """The two-group schedule (two groups half a step apart on two streams)
+    runs the same kernels on the same data as the one-group schedule: the
+    iterates, stop iterations and statistics are bit-identical, also when the
+    steps come in several iterate() calls and some problems stop early."""
+    probs = [small("rect", "bccb", n=40, transform="dft", iters=9),
+             small("reflective", "tikh_ns", n=48, psf=I.psf_disk(3), transform="dct", iters=9, seed=3),
+             small("periodic", "tikh_ns", n=36, psf=I.psf_motion(5, 0.2), iters=9, seed=4),
+             small("zero", "krylov", n=48, iters=9, alpha=0.05, seed=6),
+             small("rect", "none", n=32, iters=9, seed=7),
+             small("rect", "bccb", n=60, psf=I.psf_gaussian(1.2, 7), transform="dct", iters=9, seed=5)]
+    descs = [dict(psf=p.psf, g=p.g, delta=p.delta, bc=p.bc, precond=p.precond, mu=p.mu,
+                  alpha=p.alpha, transform=p.transform,
+                  max_iter=3 if i == 1 else p.max_iter) for i, p in enumerate(probs)]
+    out = []
+    for two in (False, True):
+        b = M.Batch(descs, dtype=dtype, levels=2, stop=True, max_iter=9, rect_ns_hybrid=True,
+                    two_group=two)
+        for k in (1, 3, 2, 4):
+            b.iterate(k)
+        out.append(([b.result(i) for i in range(len(probs))],
+                    [b.stats(i) for i in range(len(probs))]))
+        b.close()
+    (f1, s1), (f2, s2) = out
+    for i in range(len(probs)):
+        assert np.array_equal(f1[i], f2[i]), i
+        assert s1[i] == s2[i], (i, s1[i], s2[i])
+    assert s2[1]["iter"] == 3 and s2[1]["stopped"] == 1
+
+
 def test_batch_own_stop_rules(M):
     """Each problem of a batch stops on its own discrepancy rule."""
     probs = I.batch_problems(count=6, sizes=(64, 96, 128), max_iter=300)
