@@ -159,10 +159,11 @@ __device__ __forceinline__ void dft_small(T2* v) {
 }
 
 // threads of a transform CTA and the minimum CTAs per SM (register budget):
-// FP32 256 threads, at least 3 CTAs (85 registers); FP64 512 threads, so that
-// each thread holds half as many values
+// FP32 256 threads, at least 4 CTAs (64 registers: a few spilled values cost
+// less than the lost overlap of the barrier-separated phases at 3 CTAs per
+// SM); FP64 512 threads, so that each thread holds half as many values
 __host__ __device__ constexpr int tr_nt(int elem_bytes) { return elem_bytes == 8 ? 512 : 256; }
-__host__ __device__ constexpr int tr_minb(int elem_bytes) { return elem_bytes == 8 ? 1 : 3; }
+__host__ __device__ constexpr int tr_minb(int elem_bytes) { return elem_bytes == 8 ? 1 : 4; }
 
 // n / d by a multiply-high: m = floor((2^32 - 1) / d) + 1 gives the exact
 // quotient whenever 0 <= n and n d < 2^32 (every index here is below 2^17
@@ -592,6 +593,24 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
     ns_bracket_finish(pd, st, tot, b0);
 }
 
+// four consecutive reals of a row (16-byte aligned for FP32: the row length is
+// a multiple of 4 and the buffers are 256-byte aligned)
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+  const double2 u = reinterpret_cast<const double2*>(p)[0], v = reinterpret_cast<const double2*>(p)[1];
+  o[0] = u.x; o[1] = u.y; o[2] = v.x; o[3] = v.y;
+}
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
 // ---------------------------------------------------------------------------
 // Pass 1: forward transform of row pairs: src (n x n real) -> S
 template <typename T>
@@ -611,7 +630,40 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
   const bool dct = (pd.transform == TR_DCT);
   const T* src = static_cast<const T*>(pd.buf[src_slot]);
   const FastDiv fN(N);
-  {
+  if ((N & 3) == 0) {
+    // rows in groups of 4 reals, one vector load per group and row; sample
+    // y = 4 xq + i goes to position y (DFT) or to its DCT position (even y to
+    // y / 2, odd y to N - 1 - (y - 1) / 2).  All loads first, then the stores.
+    constexpr int MQ = MAXV / 4;
+    const int NQ = N >> 2;
+    const FastDiv fq(NQ);
+    T a[MQ][4], b[MQ][4];
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (e < G * NQ) {
+        const int g = fq.div(e), xq = e - g * NQ;
+        const int ra = row0 + 2 * g;
+        const T* r = src + (size_t)ra * N + 4 * xq;
+        if (ra < N) ld4(r, a[q]); else a[q][0] = a[q][1] = a[q][2] = a[q][3] = T(0);
+        if (ra + 1 < N) ld4(r + N, b[q]); else b[q][0] = b[q][1] = b[q][2] = b[q][3] = T(0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+      const int e = threadIdx.x + q * NT;
+      if (e < G * NQ) {
+        const int g = fq.div(e), xq = e - g * NQ;
+        T2* tb = sm + g * TSg;
+        const int p0 = dct ? 2 * xq : 4 * xq, p1 = dct ? N - 1 - 2 * xq : 4 * xq + 1;
+        const int p2 = dct ? 2 * xq + 1 : 4 * xq + 2, p3 = dct ? N - 2 - 2 * xq : 4 * xq + 3;
+        tb[fpad(p0)] = mk2<T2>(a[q][0], b[q][0]);
+        tb[fpad(p1)] = mk2<T2>(a[q][1], b[q][1]);
+        tb[fpad(p2)] = mk2<T2>(a[q][2], b[q][2]);
+        tb[fpad(p3)] = mk2<T2>(a[q][3], b[q][3]);
+      }
+    }
+  } else {
     // all loads of this thread first (up to MAXV in flight), then the stores
     T2 tmp[MAXV];
 #pragma unroll
@@ -902,6 +954,23 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
   }
   fft_smem<T2, true>(G, pd);
   T* dst = static_cast<T*>(pd.buf[dst_slot]);
+  if ((N & 3) == 0) {
+    // groups of 4 reals per row, one vector store per group and row
+    const int NQ = N >> 2;
+    const FastDiv fq(NQ);
+    for (int e = threadIdx.x; e < G * NQ; e += NT) {
+      const int g = fq.div(e), xq = e - g * NQ;
+      const int ra = row0 + 2 * g;
+      const T2* tb = sm + g * TSg;
+      const int p0 = dct ? 2 * xq : 4 * xq, p1 = dct ? N - 1 - 2 * xq : 4 * xq + 1;
+      const int p2 = dct ? 2 * xq + 1 : 4 * xq + 2, p3 = dct ? N - 2 - 2 * xq : 4 * xq + 3;
+      const T2 v0 = tb[fpad(p0)], v1 = tb[fpad(p1)], v2 = tb[fpad(p2)], v3 = tb[fpad(p3)];
+      T* r = dst + (size_t)ra * N + 4 * xq;
+      if (ra < N) st4(r, v0.x, v1.x, v2.x, v3.x);
+      if (ra + 1 < N) st4(r + N, v0.y, v1.y, v2.y, v3.y);
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < G * N; e += NT) {
     const int g = fN.div(e), x = e - g * N;
     const int ra = row0 + 2 * g, rb = ra + 1;
