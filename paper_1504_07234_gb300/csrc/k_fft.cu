@@ -345,6 +345,8 @@ __device__ __forceinline__ bool tr_skip(const State& st, int pcg) {
 constexpr int NS_CAND = 16;
 constexpr double NS_CAND_STEP = 1.0;
 constexpr int NS_NT = SPEC_THREADS, NS_PT = SPEC_PER_THREAD;
+constexpr int NS_B = 8;                    // elements per thread with loads in flight together
+static_assert(NS_PT % NS_B == 0, "spectrum pass batches");
 static_assert(SPEC_SUMS == 2 * NS_CAND + 1, "partial buffer sized for the bracketing pass");
 
 __host__ __device__ constexpr double ns_tol(int elem_bytes) { return elem_bytes == 8 ? 1e-10 : 1e-5; }
@@ -383,6 +385,25 @@ __device__ __forceinline__ bool spec_elem(const Prob& pd, int blk, int e, T& pw,
   sg = static_cast<const T*>(pd.w)[L];
   return true;
 }
+
+// Position in the column-blocked spectrum (block b, frequency k1 of the
+// block's rows, column c of the block) advanced by a fixed step below N cb
+// with adds and compares only (two divisions at the start).
+struct SpecWalk {
+  int b, k1, c, N, cb, dk1, dc;
+  __device__ __forceinline__ SpecWalk(int n, int cbk, int L, int step) : N(n), cb(cbk) {
+    const int blksz = n * cbk;
+    b = L / blksz;
+    const int rem = L - b * blksz;
+    k1 = rem / cbk; c = rem - k1 * cbk;
+    dk1 = step / cbk; dc = step - dk1 * cbk;
+  }
+  __device__ __forceinline__ void next() {
+    c += dc; k1 += dk1;
+    if (c >= cb) { c -= cb; ++k1; }
+    if (k1 >= N) { k1 -= N; ++b; }
+  }
+};
 
 __device__ __forceinline__ void ns_set_alpha(const Prob& pd, State& st, double nb) {
   if (nb < -32.2) nb = -32.2;                          // alpha floor 1e-14
@@ -515,14 +536,22 @@ __device__ void ns_bracket_finish(const Prob& pd, State& st, const double* tot, 
 
 // accumulate one spectral coefficient (weighted power pf, sigma sf) into the
 // candidate sums
+// (candidates in pairs: two-wide FP32 instructions, one reciprocal each)
 __device__ __forceinline__ void ns_cand_acc(float pf, float sf, const float (&ca)[NS_CAND],
                                             float (&cF)[NS_CAND], float (&cG)[NS_CAND]) {
+  const float2 s2 = make_float2(sf, sf), p2 = make_float2(pf, pf);
 #pragma unroll
-  for (int j = 0; j < NS_CAND; ++j) {
-    const float x = __fdividef(ca[j], sf + ca[j]);
-    const float px2 = pf * x * x;
-    cF[j] += px2;
-    cG[j] = fmaf(-px2, x, cG[j] + px2);        // + pw x^2 (1 - x)
+  for (int j = 0; j < NS_CAND; j += 2) {
+    const float2 a = make_float2(ca[j], ca[j + 1]);
+    const float2 d = __fadd2_rn(s2, a);
+    const float2 x = __fmul2_rn(a, make_float2(__fdividef(1.f, d.x), __fdividef(1.f, d.y)));
+    const float2 px2 = __fmul2_rn(__fmul2_rn(p2, x), x);
+    const float2 f = __fadd2_rn(make_float2(cF[j], cF[j + 1]), px2);
+    // + pw x^2 (1 - x)
+    const float2 g = __ffma2_rn(make_float2(-px2.x, -px2.y), x,
+                                __fadd2_rn(make_float2(cG[j], cG[j + 1]), px2));
+    cF[j] = f.x; cF[j + 1] = f.y;
+    cG[j] = g.x; cG[j + 1] = g.y;
   }
 }
 
@@ -996,21 +1025,24 @@ k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const in
   const double b0 = st.nb;
   if (threadIdx.x < NS_CAND)
     s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
-  T pw[NS_PT], sg[NS_PT];
-  bool ok[NS_PT];
-#pragma unroll
-  for (int q = 0; q < NS_PT; ++q)
-    ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + q * NS_NT, pw[q], sg[q]);
   __syncthreads();
   float ca[NS_CAND], cF[NS_CAND], cG[NS_CAND];
 #pragma unroll
   for (int j = 0; j < NS_CAND; ++j) { ca[j] = s_ca[j]; cF[j] = 0.f; cG[j] = 0.f; }
   T sP = T(0);
+#pragma unroll 1
+  for (int q0 = 0; q0 < NS_PT; q0 += NS_B) {
+    T pw[NS_B], sg[NS_B];
+    bool ok[NS_B];
 #pragma unroll
-  for (int q = 0; q < NS_PT; ++q) {
-    if (!ok[q]) continue;
-    sP += pw[q];
-    ns_cand_acc((float)pw[q], (float)sg[q], ca, cF, cG);
+    for (int q = 0; q < NS_B; ++q)
+      ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + (q0 + q) * NS_NT, pw[q], sg[q]);
+#pragma unroll
+    for (int q = 0; q < NS_B; ++q) {
+      if (!ok[q]) continue;
+      sP += pw[q];
+      ns_cand_acc((float)pw[q], (float)sg[q], ca, cF, cG);
+    }
   }
   T v[K];
 #pragma unroll
@@ -1032,22 +1064,50 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   if (st.stopped || !pd.ns || !st.ns_active || st.nconv || st.nphase != 1) return;
   const double b0 = st.nb;
   const T alpha = T(exp(b0));
-  T pw[NS_PT], sg[NS_PT];
-  bool ok[NS_PT];
-#pragma unroll
-  for (int q = 0; q < NS_PT; ++q)
-    ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + q * NS_NT, pw[q], sg[q]);
+  using T2 = typename Vec2<T>::type;
+  const int N = pd.n, cb = pd.cb;
+  const bool dct = (pd.transform == TR_DCT);
+  const int W = dct ? N : pd.half;
+  const int nel = pd.nblk_cols * N * cb;
+  int L = item.y * (NS_NT * NS_PT) + threadIdx.x;
+  SpecWalk wk(N, cb, L, NS_NT);
   T sP = T(0), sF = T(0), sG1 = T(0), sG2 = T(0);
+#pragma unroll 1
+  for (int q0 = 0; q0 < NS_PT; q0 += NS_B) {
+  T pw[NS_B], sg[NS_B];
+  bool ok[NS_B];
 #pragma unroll
-  for (int q = 0; q < NS_PT; ++q) {
+  for (int q = 0; q < NS_B; ++q) {
+    const int k2 = wk.b * cb + wk.c;
+    ok[q] = L < nel && k2 < W;
+    pw[q] = T(0); sg[q] = T(1);
+    if (ok[q]) {
+      sg[q] = static_cast<const T*>(pd.w)[L];
+      if (dct) {
+        // unnormalised DCT-II: |orthonormal coefficient|^2 = v^2 s_k1^2 s_k2^2
+        // with s_0^2 = 1/N and s_k^2 = 2/N; the common 1/N^2 cancels
+        const T v = static_cast<const T*>(pd.buf[SL_S])[L];
+        pw[q] = T((wk.k1 == 0 ? 1 : 2) * (k2 == 0 ? 1 : 2)) * v * v;
+      } else {
+        const T2 v = static_cast<const T2*>(pd.buf[SL_S])[L];
+        const T m = (k2 == 0 || ((N & 1) == 0 && k2 == N / 2)) ? T(1) : T(2);
+        pw[q] = m * (v.x * v.x + v.y * v.y);
+      }
+    }
+    L += NS_NT;
+    wk.next();
+  }
+#pragma unroll
+  for (int q = 0; q < NS_B; ++q) {
     if (!ok[q]) continue;
-    const T x = alpha / (sg[q] + alpha);
+    const T x = wdiv(alpha, sg[q] + alpha);
     const T px2 = pw[q] * x * x;
     const T g1 = px2 * (T(1) - x);
     sP += pw[q];
     sF += px2;
     sG1 += g1;
     sG2 += g1 * (T(2) - T(3) * x);
+  }
   }
   T v[4] = {sP, sF, sG1, sG2};
   if (ns_reduce<NS_NT, 4, T>(pd, st, item.y, pd.nblk_spec, v, red, tot) && threadIdx.x == 0) {

@@ -38,7 +38,7 @@ constexpr int TR_CAP = 4096;          // complex values held by one transform CT
 constexpr int FRAME_THREADS = 256;
 constexpr int FRAME_TILE = 32;
 constexpr int SPEC_THREADS = 256;    // alpha_n solve (k_fft.cu)
-constexpr int SPEC_PER_THREAD = 8;
+constexpr int SPEC_PER_THREAD = 32;
 constexpr int SPEC_SUMS = 33;        // block sums of the bracketing pass (2 x 16 candidates + 1)
 
 template <typename T>
