@@ -765,6 +765,19 @@ __device__ __forceinline__ T weight_dct(const Prob& pd, size_t idx, T alpha, T s
   const T inv = wdiv(scale, static_cast<const T*>(pd.w)[idx] + alpha);
   return kind == W_TIKH ? static_cast<const T*>(pd.lam)[idx] * inv : inv;
 }
+// the weights of real columns idx and idx + 1 (idx even: one aligned pair load)
+template <typename T, typename T2>
+__device__ __forceinline__ T2 weight_dct2(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
+  const T2 s = *reinterpret_cast<const T2*>(static_cast<const T*>(pd.w) + idx);
+  T2 r;
+  r.x = wdiv(scale, s.x + alpha);
+  r.y = wdiv(scale, s.y + alpha);
+  if (kind == W_TIKH) {
+    const T2 l = *reinterpret_cast<const T2*>(static_cast<const T*>(pd.lam) + idx);
+    r.x *= l.x; r.y *= l.y;
+  }
+  return r;
+}
 
 // Pass 2: one column block per CTA.  DFT: cb complex columns; DCT: cb real
 // columns = cb/2 packed pairs.
@@ -838,25 +851,35 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
       if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
     }
   } else {
+    // real columns 2g and 2g + 1 of the block are transform g (real and
+    // imaginary part): the block moves as N G pairs, pair (k1, g) at 2 (k1 G + g)
     const int G = cb / 2;
-    const FastDiv fcb(cb);
+    const FastDiv fG(G);
     T* S = static_cast<T*>(pd.buf[SL_S]) + base;
+    T2* S2 = reinterpret_cast<T2*>(S);          // cb even, base even: aligned pairs
     T* smr = reinterpret_cast<T*>(sm);
+    const int NP = N * G;
+    // valid real columns of this block (the last block may be padded)
+    const int nvc = W - kb < cb ? W - kb : cb;
     {
-      T tmp[2 * MAXV];
+      T2 tmp[MAXV];
 #pragma unroll
-      for (int q = 0; q < 2 * MAXV; ++q) {
+      for (int q = 0; q < MAXV; ++q) {
         const int e = threadIdx.x + q * NT;
-        tmp[q] = T(0);
-        if (e < N * cb) { const int c = e - fcb.div(e) * cb; if (kb + c < W) tmp[q] = S[e]; }
+        tmp[q].x = T(0); tmp[q].y = T(0);
+        if (e < NP) {
+          const int c = 2 * (e - fG.div(e) * G);
+          if (c + 1 < nvc) tmp[q] = S2[e];
+          else if (c < nvc) tmp[q].x = S[2 * e];
+        }
       }
 #pragma unroll
-      for (int q = 0; q < 2 * MAXV; ++q) {
+      for (int q = 0; q < MAXV; ++q) {
         const int e = threadIdx.x + q * NT;
-        if (e < N * cb) {
-          const int k1 = fcb.div(e), c = e - k1 * cb;
+        if (e < NP) {
+          const int k1 = fG.div(e), g = e - k1 * G;
           const int pos = (mode == COL_NS_INV) ? k1 : dct_pos(k1, N);
-          smr[2 * ((c >> 1) * TSg + fpad(pos)) + (c & 1)] = tmp[q];
+          sm[g * TSg + fpad(pos)] = tmp[q];
         }
       }
     }
@@ -866,25 +889,39 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
       fft_smem<T2, false>(G, pd);
       dct_split<T, T2>(sm, G, N, TSg, dtw);
     }
+    // store pair e from shared-memory position pos of its transform
+    auto put = [&](int e, int g, int pos) {
+      const int c = 2 * g;
+      const T2 v = sm[g * TSg + fpad(pos)];
+      if (c + 1 < nvc) S2[e] = v;
+      else if (c < nvc) S[2 * e] = v.x;
+    };
     if (mode == COL_FWD) {
-      for (int e = threadIdx.x; e < N * cb; e += NT) {
-        const int k1 = fcb.div(e), c = e - k1 * cb;
-        if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
+      for (int e = threadIdx.x; e < NP; e += NT) {
+        const int k1 = fG.div(e), g = e - k1 * G;
+        put(e, g, k1);
       }
       if (cand) ns_cand_block<T>(pd, st, item.y, smr, TSg, base);
       return;
     }
-    for (int e = threadIdx.x; e < N * cb; e += NT) {
-      const int k1 = fcb.div(e), c = e - k1 * cb;
-      T& v = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
-      v *= (kb + c < W) ? weight_dct<T>(pd, base + e, Ta, Tsc, kind) : T(0);
+    for (int e = threadIdx.x; e < NP; e += NT) {
+      const int k1 = fG.div(e), g = e - k1 * G;
+      const int c = 2 * g;
+      T2& v = sm[g * TSg + fpad(k1)];
+      if (c + 1 < nvc) {
+        const T2 w = weight_dct2<T, T2>(pd, base + 2 * (size_t)e, Ta, Tsc, kind);
+        v.x *= w.x; v.y *= w.y;
+      } else {
+        v.x *= (c < nvc) ? weight_dct<T>(pd, base + 2 * (size_t)e, Ta, Tsc, kind) : T(0);
+        v.y = T(0);
+      }
     }
     __syncthreads();
     dct_merge<T, T2>(sm, G, N, TSg, dtw);
     fft_smem<T2, true>(G, pd);
-    for (int e = threadIdx.x; e < N * cb; e += NT) {
-      const int k1 = fcb.div(e), c = e - k1 * cb;
-      if (kb + c < W) S[e] = smr[2 * ((c >> 1) * TSg + fpad(dct_pos(k1, N))) + (c & 1)];
+    for (int e = threadIdx.x; e < NP; e += NT) {
+      const int k1 = fG.div(e), g = e - k1 * G;
+      put(e, g, dct_pos(k1, N));
     }
   }
 }
