@@ -750,6 +750,17 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
 __device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
 
+// two consecutive complex values (one 16-byte access for FP32; p 16-byte aligned)
+__device__ __forceinline__ void ldc2(const float2* p, float2& a, float2& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = make_float2(v.x, v.y); b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ldc2(const double2* p, double2& a, double2& b) { a = p[0]; b = p[1]; }
+__device__ __forceinline__ void stc2(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void stc2(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
+
 template <typename T, typename T2>
 __device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
   const T inv = wdiv(scale, static_cast<const T*>(pd.w)[idx] + alpha);
@@ -809,7 +820,69 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   const size_t base = (size_t)item.y * N * cb;       // this CTA's contiguous block
   const int W = dct ? N : pd.half;
   const int kb = item.y * cb;                         // first column of the block
-  if (!dct) {
+  if (!dct && (cb & 1) == 0) {
+    // an even number of complex columns: columns 2h and 2h + 1 (transforms
+    // 2h, 2h + 1) move together, quad (k1, h) at 2 (k1 cb / 2 + h)
+    const int G = cb, H = cb / 2;
+    const FastDiv fH(H);
+    T2* S = static_cast<T2*>(pd.buf[SL_S]) + base;
+    const int NQ = N * H;
+    const int nvc = W - kb < cb ? W - kb : cb;      // valid columns of the block
+    {
+      T2 ta[MAXV / 2], tb[MAXV / 2];
+#pragma unroll
+      for (int q = 0; q < MAXV / 2; ++q) {
+        const int e = threadIdx.x + q * NT;
+        ta[q].x = ta[q].y = tb[q].x = tb[q].y = T(0);
+        if (e < NQ) {
+          const int c = 2 * (e - fH.div(e) * H);
+          if (c + 1 < nvc) ldc2(S + 2 * e, ta[q], tb[q]);
+          else if (c < nvc) ta[q] = S[2 * e];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < MAXV / 2; ++q) {
+        const int e = threadIdx.x + q * NT;
+        if (e < NQ) {
+          const int k1 = fH.div(e), c = 2 * (e - k1 * H);
+          sm[c * TSg + fpad(k1)] = ta[q];
+          sm[(c + 1) * TSg + fpad(k1)] = tb[q];
+        }
+      }
+    }
+    __syncthreads();
+    auto put = [&](int e, int k1, int c) {
+      const T2 a = sm[c * TSg + fpad(k1)], b = sm[(c + 1) * TSg + fpad(k1)];
+      if (c + 1 < nvc) stc2(S + 2 * e, a, b);
+      else if (c < nvc) S[2 * e] = a;
+    };
+    if (mode != COL_NS_INV) fft_smem<T2, false>(G, pd);
+    if (mode == COL_FWD) {
+      for (int e = threadIdx.x; e < NQ; e += NT) {
+        const int k1 = fH.div(e), c = 2 * (e - k1 * H);
+        put(e, k1, c);
+      }
+      if (cand) ns_cand_block<T>(pd, st, item.y, reinterpret_cast<const T*>(sm), TSg, base);
+      return;
+    }
+    for (int e = threadIdx.x; e < NQ; e += NT) {
+      const int k1 = fH.div(e), c = 2 * (e - k1 * H);
+      if (c < nvc) {
+        T2& v = sm[c * TSg + fpad(k1)];
+        v = cmul(v, weight_dft<T, T2>(pd, base + 2 * (size_t)e, Ta, Tsc, kind));
+      }
+      if (c + 1 < nvc) {
+        T2& v = sm[(c + 1) * TSg + fpad(k1)];
+        v = cmul(v, weight_dft<T, T2>(pd, base + 2 * (size_t)e + 1, Ta, Tsc, kind));
+      }
+    }
+    __syncthreads();
+    fft_smem<T2, true>(G, pd);
+    for (int e = threadIdx.x; e < NQ; e += NT) {
+      const int k1 = fH.div(e), c = 2 * (e - k1 * H);
+      put(e, k1, c);
+    }
+  } else if (!dct) {
     const int G = cb;
     const FastDiv fG(G);
     T2* S = static_cast<T2*>(pd.buf[SL_S]) + base;
@@ -1100,7 +1173,11 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   State& st = states[item.x];
   if (st.stopped || !pd.ns || !st.ns_active || st.nconv || st.nphase != 1) return;
   const double b0 = st.nb;
-  const T alpha = T(exp(b0));
+  // exp in FP64 once per CTA (FP64 throughput is scarce), shared with the block
+  __shared__ T s_alpha;
+  if (threadIdx.x == 0) s_alpha = T(exp(b0));
+  __syncthreads();
+  const T alpha = s_alpha;
   using T2 = typename Vec2<T>::type;
   const int N = pd.n, cb = pd.cb;
   const bool dct = (pd.transform == TR_DCT);
