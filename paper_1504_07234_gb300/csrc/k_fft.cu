@@ -582,10 +582,10 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
   for (int j = 0; j < NS_CAND; ++j) { ca[j] = s_ca[j]; cF[j] = 0.f; cG[j] = 0.f; }
   const FastDiv fcb(cb);
   T sP = T(0);
-  // chunks of MV elements per thread: the chunk's sigma loads first (all in
-  // flight together), then its sums (a DFT block holds <= TR_CAP complex
-  // values, a DCT block <= 2 TR_CAP reals)
-  constexpr int MV = TR_CAP / NT;
+  // chunks of MV elements per thread: the chunk's sigma loads first (in
+  // flight together), then its sums; a short chunk keeps the unrolled body
+  // (MV x NS_CAND candidate updates) small enough for the instruction cache
+  constexpr int MV = 4;
 #pragma unroll 1
   for (int e0 = 0; e0 < N * cb; e0 += MV * NT) {
   float wv[MV];
