@@ -792,10 +792,11 @@ __device__ __forceinline__ T2 weight_dct2(const Prob& pd, size_t idx, T alpha, T
 
 // Pass 2: one column block per CTA.  DFT: cb complex columns; DCT: cb real
 // columns = cb/2 packed pairs.
-template <typename T>
+// (the mode is a template parameter: each launch runs only its own code)
+template <typename T, int mode>
 __global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
 k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-       int mode, int pcg, double op_alpha, int op_kind) {
+       int pcg, double op_alpha, int op_kind) {
   using T2 = typename Vec2<T>::type;
   constexpr int NT = tr_nt(sizeof(T)), MAXV = TR_CAP / NT;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1317,8 +1318,16 @@ void launch_rows_fwd(const Prob* probs, State* states, const int2* items, int ni
 template <typename T>
 void launch_cols(const Prob* probs, State* states, const int2* items, int nitems, int mode,
                  int pcg, double op_alpha, int op_kind, size_t smem, cudaStream_t s) {
-  if (nitems > 0)
-    k_cols<T><<<nitems, tr_nt(sizeof(T)), smem, s>>>(probs, states, items, mode, pcg, op_alpha, op_kind);
+  if (nitems <= 0) return;
+  const int nt = tr_nt(sizeof(T));
+  if (mode == COL_FUSED)
+    k_cols<T, COL_FUSED><<<nitems, nt, smem, s>>>(probs, states, items, pcg, op_alpha, op_kind);
+  else if (mode == COL_FWD)
+    k_cols<T, COL_FWD><<<nitems, nt, smem, s>>>(probs, states, items, pcg, op_alpha, op_kind);
+  else if (mode == COL_NS_INV)
+    k_cols<T, COL_NS_INV><<<nitems, nt, smem, s>>>(probs, states, items, pcg, op_alpha, op_kind);
+  else
+    k_cols<T, COL_OP><<<nitems, nt, smem, s>>>(probs, states, items, pcg, op_alpha, op_kind);
 }
 template <typename T>
 void launch_rows_inv(const Prob* probs, State* states, const int2* items, int nitems, int dst,
@@ -1345,8 +1354,11 @@ template <typename T>
 cudaError_t fft_set_smem(size_t bytes) {
   cudaError_t e = cudaFuncSetAttribute(k_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
+  for (const void* f : {(const void*)k_cols<T, COL_FUSED>, (const void*)k_cols<T, COL_FWD>,
+                        (const void*)k_cols<T, COL_NS_INV>, (const void*)k_cols<T, COL_OP>}) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
