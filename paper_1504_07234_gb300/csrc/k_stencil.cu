@@ -50,12 +50,45 @@ __device__ __forceinline__ bool skip(const State& st, int pcg) {
   return st.stopped || (pcg && st.pdone);
 }
 
+// The last R (1..7) taps t .. t + R - 1 of a run from the aligned window
+// (slot j holds v[t + j]): v[t + 8 .. t + R + 6] go to R - 1 more registers and
+// every index is static, so no value moves and no work is predicated off.
+template <int R, typename V, typename W, typename LD, typename FMA>
+__device__ __forceinline__ void window_tail(V (&acc)[8], const V (&win)[8], const W* __restrict__ w,
+                                            int t, LD ld, FMA fma2) {
+  V ext[R > 1 ? R - 1 : 1];
+#pragma unroll
+  for (int i = 0; i < R - 1; ++i) ext[i] = ld(t + 8 + i);
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const W wt = w[t + u];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int sidx = j + u;
+      acc[j] = fma2(sidx < 8 ? win[sidx] : ext[sidx - 8 < R - 1 ? sidx - 8 : 0], wt, acc[j]);
+    }
+  }
+}
+template <typename V, typename W, typename LD, typename FMA>
+__device__ __forceinline__ void window_tails(V (&acc)[8], const V (&win)[8], const W* __restrict__ w,
+                                             int t, int r, LD ld, FMA fma2) {
+  switch (r) {
+    case 1: window_tail<1>(acc, win, w, t, ld, fma2); break;
+    case 2: window_tail<2>(acc, win, w, t, ld, fma2); break;
+    case 3: window_tail<3>(acc, win, w, t, ld, fma2); break;
+    case 4: window_tail<4>(acc, win, w, t, ld, fma2); break;
+    case 5: window_tail<5>(acc, win, w, t, ld, fma2); break;
+    case 6: window_tail<6>(acc, win, w, t, ld, fma2); break;
+    case 7: window_tail<7>(acc, win, w, t, ld, fma2); break;
+    default: break;
+  }
+}
+
 // acc[j] += sum_t w[t] v[t + j] over a run of len taps, v[i] = base[i * stride]:
 // an 8-value window of v.  Whole groups of 8 taps keep the window as a ring
 // (slot (i & 7) holds v[i]) so every register index is static and no value
 // moves; after them the ring is aligned again (slot j holds v[t + j]) and the
-// last len % 8 taps shift the window instead, so that short runs (thin PSFs)
-// issue no predicated-off work.
+// last len % 8 taps go through window_tail.
 template <typename T>
 __device__ __forceinline__ void window_run(T (&acc)[8], const T* __restrict__ base, int stride,
                                            const T* __restrict__ w, int len) {
@@ -73,16 +106,8 @@ __device__ __forceinline__ void window_run(T (&acc)[8], const T* __restrict__ ba
       if (t + u + 1 < len) win[u] = base[(t + u + 8) * stride];
     }
   }
-  for (; t < len; ++t) {
-    const T wt = w[t];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] += wt * win[j];
-    if (t + 1 < len) {
-#pragma unroll
-      for (int j = 0; j < 7; ++j) win[j] = win[j + 1];
-      win[7] = base[(t + 8) * stride];
-    }
-  }
+  window_tails(acc, win, w, t, len - t, [&](int i) { return base[i * stride]; },
+               [](T v, T wt, T a) { return a + wt * v; });
 }
 
 // asynchronous global -> shared copy of one 4- or 8-byte element; !valid
@@ -153,16 +178,7 @@ __device__ __forceinline__ void window_run2(typename Pair<T>::type (&acc)[8], co
       if (t + u + 1 < len) win[u] = ld(t + u + 8);
     }
   }
-  for (; t < len; ++t) {
-    const T wt = w[t];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = Pair<T>::fma(win[j], wt, acc[j]);
-    if (t + 1 < len) {
-#pragma unroll
-      for (int j = 0; j < 7; ++j) win[j] = win[j + 1];
-      win[7] = ld(t + 8);
-    }
-  }
+  window_tails(acc, win, w, t, len - t, ld, [](T2 v, T wt, T2 a) { return Pair<T>::fma(v, wt, a); });
 }
 
 // Stencil tile geometry: 64 x 32 outputs per CTA of 128 threads; a thread
