@@ -640,6 +640,17 @@ __device__ __forceinline__ void st4(double* p, double a, double b, double c, dou
   reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
 }
 
+// two consecutive complex values (one 16-byte access for FP32; p 16-byte aligned)
+__device__ __forceinline__ void ldc2(const float2* p, float2& a, float2& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = make_float2(v.x, v.y); b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ldc2(const double2* p, double2& a, double2& b) { a = p[0]; b = p[1]; }
+__device__ __forceinline__ void stc2(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void stc2(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
+
 // ---------------------------------------------------------------------------
 // Pass 1: forward transform of row pairs: src (n x n real) -> S
 template <typename T>
@@ -720,6 +731,44 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
   const int cb = pd.cb;
   const int R2 = 2 * G;
   const int nb = (W + cb - 1) / cb;
+  // spectral value k of local row rl
+  auto spec_val = [&](const T2* tb, int rl, int k) -> T2 {
+    if (dct) {
+      const T2 X = tb[fpad(k)];
+      T2 r; r.x = (rl & 1) ? X.y : X.x; r.y = T(0); return r;
+    }
+    const T2 Z = tb[fpad(k)];
+    const T2 Zr = tb[fpad(k == 0 ? 0 : N - k)];
+    T2 X;
+    if (rl & 1) { X.x = T(0.5) * (Z.y + Zr.y); X.y = T(-0.5) * (Z.x - Zr.x); }   // (Z - conj Zr)/(2i)
+    else { X.x = T(0.5) * (Z.x + Zr.x); X.y = T(0.5) * (Z.y - Zr.y); }           // (Z + conj Zr)/2
+    return X;
+  };
+  if ((cb & 1) == 0) {
+    // columns in pairs (c, c + 1): one 8-byte (DCT) or 16-byte (DFT) store
+    const int H = cb / 2;
+    const FastDiv frh(R2 * H), fh(H);
+    for (int e = threadIdx.x; e < nb * R2 * H; e += NT) {
+      const int b = frh.div(e), rem = e - b * (R2 * H);
+      const int rl = fh.div(rem), c = 2 * (rem - rl * H);
+      const int k = b * cb + c, row = row0 + rl;
+      if (k >= W || row >= N) continue;
+      const T2* tb = sm + (rl >> 1) * TSg;
+      const size_t o = (size_t)b * N * cb + (size_t)row * cb + c;
+      const bool two = k + 1 < W;
+      const T2 x0 = spec_val(tb, rl, k);
+      if (dct) {
+        T* S = static_cast<T*>(pd.buf[SL_S]);
+        if (two) *reinterpret_cast<T2*>(S + o) = mk2<T2>(x0.x, spec_val(tb, rl, k + 1).x);
+        else S[o] = x0.x;
+      } else {
+        T2* S = static_cast<T2*>(pd.buf[SL_S]);
+        if (two) stc2(S + o, x0, spec_val(tb, rl, k + 1));
+        else S[o] = x0;
+      }
+    }
+    return;
+  }
   const FastDiv frc(R2 * cb), fcb(cb);
   for (int e = threadIdx.x; e < nb * R2 * cb; e += NT) {
     const int b = frc.div(e), rem = e - b * (R2 * cb);
@@ -749,17 +798,6 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
 // (within 2 ulp), the exact one in FP64
 __device__ __forceinline__ float wdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double wdiv(double a, double b) { return a / b; }
-
-// two consecutive complex values (one 16-byte access for FP32; p 16-byte aligned)
-__device__ __forceinline__ void ldc2(const float2* p, float2& a, float2& b) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  a = make_float2(v.x, v.y); b = make_float2(v.z, v.w);
-}
-__device__ __forceinline__ void ldc2(const double2* p, double2& a, double2& b) { a = p[0]; b = p[1]; }
-__device__ __forceinline__ void stc2(float2* p, float2 a, float2 b) {
-  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
-}
-__device__ __forceinline__ void stc2(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
 
 template <typename T, typename T2>
 __device__ __forceinline__ T2 weight_dft(const Prob& pd, size_t idx, T alpha, T scale, int kind) {
@@ -1023,7 +1061,74 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
   const int tot = nb * G * cb;
   const FastDiv fgc(G * cb), fcb(cb), fN(N);
   constexpr int BATCH = 8;
-  if (dct) {
+  const bool even = (N & 1) == 0;
+  // Z[k] = Xa[k] + i Xb[k] of the DFT rows (the missing half from Hermitian
+  // symmetry), or the packed pair (Xa, Xb) of the DCT rows, into transform g
+  auto put_dft = [&](T2* tb, int kk, T2 xa, T2 xb) {
+    if (kk == 0 || (even && kk == N / 2)) {
+      T2 z; z.x = xa.x; z.y = xb.x;        // imaginary parts of DC / Nyquist are rounding
+      tb[fpad(kk)] = z;
+    } else {
+      T2 z; z.x = xa.x - xb.y; z.y = xa.y + xb.x;     // Xa + i Xb
+      tb[fpad(kk)] = z;
+      T2 zr; zr.x = xa.x + xb.y; zr.y = xb.x - xa.y;  // conj(Xa) + i conj(Xb)
+      tb[fpad(N - kk)] = zr;
+    }
+  };
+  if ((cb & 1) == 0) {
+    // columns in pairs (c, c + 1): one 8-byte (DCT) or 16-byte (DFT) load per
+    // row of the pair
+    constexpr int BATCH2 = 4;          // 4 pairs of 2 rows x 2 columns in flight
+    const int H = cb / 2;
+    const int tot2 = nb * G * H;
+    const FastDiv fgh(G * H), fh(H);
+    for (int e0 = threadIdx.x; e0 < tot2; e0 += BATCH2 * NT) {
+      T2 a0[BATCH2], a1[BATCH2], b0[BATCH2], b1[BATCH2];
+      int kq[BATCH2];
+#pragma unroll
+      for (int u = 0; u < BATCH2; ++u) {
+        const int e = e0 + u * NT;
+        kq[u] = -1;
+        a0[u].x = a0[u].y = a1[u].x = a1[u].y = T(0);
+        b0[u] = a0[u]; b1[u] = a0[u];
+        if (e < tot2) {
+          const int b = fgh.div(e), rem = e - b * (G * H);
+          const int g = fh.div(rem), c = 2 * (rem - g * H);
+          const int ra = row0 + 2 * g;
+          const int k = b * cb + c;
+          if (k < W) {
+            const size_t o = (size_t)b * N * cb + (size_t)ra * cb + c;
+            if (dct) {
+              const T* S = static_cast<const T*>(pd.buf[SL_S]);
+              if (ra < N) a0[u] = *reinterpret_cast<const T2*>(S + o);        // row ra, columns c, c + 1
+              if (ra + 1 < N) b0[u] = *reinterpret_cast<const T2*>(S + o + cb);
+            } else {
+              const T2* S = static_cast<const T2*>(pd.buf[SL_S]);
+              if (ra < N) ldc2(S + o, a0[u], a1[u]);
+              if (ra + 1 < N) ldc2(S + o + cb, b0[u], b1[u]);
+            }
+            kq[u] = (g << 16) | k;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH2; ++u) {
+        if (kq[u] < 0) continue;
+        const int k = kq[u] & 0xffff;
+        T2* tb = sm + (kq[u] >> 16) * TSg;
+        const bool two = k + 1 < W;
+        if (dct) {
+          tb[fpad(k)] = mk2<T2>(a0[u].x, b0[u].x);
+          if (two) tb[fpad(k + 1)] = mk2<T2>(a0[u].y, b0[u].y);
+        } else {
+          put_dft(tb, k, a0[u], b0[u]);
+          if (two) put_dft(tb, k + 1, a1[u], b1[u]);
+        }
+      }
+    }
+    __syncthreads();
+    if (dct) dct_merge<T, T2>(sm, G, N, TSg, static_cast<const T2*>(pd.dtw));
+  } else if (dct) {
     const T* S = static_cast<const T*>(pd.buf[SL_S]);
     for (int e0 = threadIdx.x; e0 < tot; e0 += BATCH * NT) {
       T2 v[BATCH];
