@@ -247,13 +247,10 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
       s_w[p + k] = CORR ? hy[k] : hy[p - 1 - k];
     }
   } else {
-    const T* tw = static_cast<const T*>(pd.tap_w);
+    // the weights are stored in both orders: one flat, coalesced copy
+    const T* tw = static_cast<const T*>(pd.tap_w) + (CORR ? 0 : pd.nrw);
     for (int k = threadIdx.x; k < pd.nruns; k += NT) s_runs[k] = pd.tap_runs[k];
-    for (int k = threadIdx.x; k < pd.nruns; k += NT) {
-      const int4 rn = pd.tap_runs[k];
-      const int len = rn.z - rn.y + 1;
-      for (int t = 0; t < len; ++t) s_w[rn.w + t] = CORR ? tw[rn.w + t] : tw[rn.w + len - 1 - t];
-    }
+    for (int k = threadIdx.x; k < pd.nrw; k += NT) s_w[k] = tw[k];
   }
   // input region
   const int oy0 = CORR ? ty0 - 2 * c : ty0 - c;

@@ -38,7 +38,7 @@ struct HostProb {
   std::vector<double> psf;       // p x p, the PSF used by A
   std::vector<double> psf_pre;   // PSF of the preconditioner (H or H~)
   std::vector<int> runs;         // (b, lo, hi, offset) per nonzero PSF column
-  std::vector<double> rw;        // packed run weights H[lo..hi][b]
+  std::vector<double> rw;        // packed run weights H[lo..hi][b], then the same runs reversed
   std::vector<double> hy, hx;
   size_t off[NSLOT + 16];
 };
@@ -482,6 +482,15 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   if (pd.ntaps == 0) return MLBA_E_INVAL;
   pd.nruns = (int)h.runs.size() / 4;
   pd.nrw = (int)h.rw.size();
+  // second copy with every run reversed (the order the forward stencil
+  // consumes), so that a CTA copies its weights with one flat loop
+  for (int r = 0; r < pd.nruns; ++r) {
+    const int lo = h.runs[4 * r + 1], hi = h.runs[4 * r + 2], off = h.runs[4 * r + 3];
+    for (int t = 0; t <= hi - lo; ++t) {
+      const double v = h.rw[off + (hi - lo) - t];
+      h.rw.push_back(v);
+    }
+  }
   pd.sep = rank_one(h.psf, p, h.hy, h.hx) && p > 1 ? 1 : 0;
   // launch geometry
   pd.nblk_blur = stencil_tiles(n);
@@ -615,7 +624,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         nspec * ts,                            // |lambda|^2 in T precision
         spec ? (size_t)pd.n * 2 * ts : ts,     // tw
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
-        (size_t)pd.nruns * 16, (size_t)pd.nrw * ts,   // tap runs and weights
+        (size_t)pd.nruns * 16, 2 * (size_t)pd.nrw * ts,   // tap runs and weights (both orders)
         (size_t)pd.p * ts, (size_t)pd.p * ts,  // hy, hx
         std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, (size_t)SPEC_SUMS * std::max(pd.nblk_spec, pd.nblk_cols), (size_t)1}) * 8,  // partial
         (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 4};

@@ -63,7 +63,8 @@ struct Prob {
   void* tw;          // exp(-2 pi i k/n), k < n   (T2)
   void* dtw;         // exp(-i pi k/(2n)), k < n  (T2)
   int4* tap_runs;     // per nonzero PSF column b: (b, lo, hi, offset of H[lo..hi][b] in tap_w)
-  void* tap_w;        // packed run weights, T precision
+  void* tap_w;        // packed run weights, T precision: nrw in PSF order, then nrw with
+                      // every run reversed
   void* hy; void* hx;                      // separable factors (length p)
   double* partial;   // reduction partials (capacity per problem)
   double* hist_res; double* hist_alpha; int* hist_beta;  // history, max_iter+2
