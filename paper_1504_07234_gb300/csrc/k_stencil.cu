@@ -110,6 +110,18 @@ __device__ __forceinline__ void window_run(T (&acc)[8], const T* __restrict__ ba
                [](T v, T wt, T a) { return a + wt * v; });
 }
 
+// asynchronous global -> shared copy of a B-byte chunk (B = 8 or 16, both
+// addresses B-aligned) of which the first nbytes come from global memory and
+// the rest are zero-filled
+template <int B>
+__device__ __forceinline__ void cp_async_bytes(void* smem, const void* gmem, int nbytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+}
+
 // asynchronous global -> shared copy of one 4- or 8-byte element; !valid
 // writes zeros (0 source bytes)
 template <int B>
@@ -186,7 +198,11 @@ __device__ __forceinline__ void window_run2(typename Pair<T>::type (&acc)[8], co
 // input tile (32 + p - 1) x (64 + p - 1) lives in shared memory with an even
 // row pitch (pairs of columns are one 8-byte word when the column is even).
 constexpr int ST_TX = 64, ST_TY = 32;
-__host__ __device__ constexpr int st_pitch(int RX) { return (RX + 1) & ~1; }
+// row pitch of the input tile: a multiple of 16 bytes with room for the
+// shift (< 16 bytes) that aligns a row's source to 16 bytes
+__host__ __device__ constexpr int st_pitch(int RX, int elem) {
+  return (RX + 16 / elem - 1 + 16 / elem - 1) / (16 / elem) * (16 / elem);
+}
 constexpr int ST_TP = ST_TX + 2;      // row-pass tile pitch (rank-one PSF)
 
 int stencil_tiles(int outN) { return ((outN + ST_TX - 1) / ST_TX) * ((outN + ST_TY - 1) / ST_TY); }
@@ -221,7 +237,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   const int tilesX = (outN + ST_TX - 1) / ST_TX;
   const int ty0 = (item.y / tilesX) * ST_TY, tx0 = (item.y % tilesX) * ST_TX;
   const int RY = ST_TY + p - 1, RX = ST_TX + p - 1;
-  const int RP = st_pitch(RX);
+  const int RP = st_pitch(RX, (int)sizeof(T));
   const bool sep = pd.sep != 0;
 
   // shared memory: weights, column runs (general PSF), input tile, row-pass
@@ -260,27 +276,68 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   // are zero-filled by a copy of 0 source bytes.  One warp per row, lanes
   // along the row (RX <= 64 + MLBA_MAX_P - 1 = 128: four column passes at
   // most); the row's source index is mapped once.
+  // When the tile's columns lie inside the source, every tile row is one
+  // contiguous source run: it is copied in 16-byte (or 8-byte) chunks from a
+  // chunk-aligned start, the tile sitting xs elements into its shared-memory
+  // row (xs = the start's offset from the chunk boundary; the same for every
+  // row when the source pitch is a multiple of the chunk); bytes past the
+  // source row are zero-filled.  Other tiles map every element.
+  int xs = 0;
   {
     const int lane = threadIdx.x & 31;
     const int pitch = (!CORR && pd.bc == BC_RECT) ? pd.nf : n;
-    for (int ry = threadIdx.x >> 5; ry < RY; ry += NT / 32) {
-      const int ey = oy0 + ry;
-      int sy;
-      if (CORR) sy = (ey >= 0 && ey < n) ? ey : -1;
-      else if (pd.bc == BC_RECT) sy = (ey + c >= 0 && ey + c < pd.nf) ? ey + c : -1;
-      else sy = bc_map_near(ey, n, pd.bc);
-      const T* row = src + (size_t)(sy < 0 ? 0 : sy) * pitch;
+    const int sx0 = (!CORR && pd.bc == BC_RECT) ? ox0 + c : ox0;
+    const bool colin = sx0 >= 0 && sx0 + RX <= pitch;
+    // chunk in elements: 16 bytes when the pitch keeps the rows aligned alike,
+    // 8 bytes (FP32) for an even pitch, 0: element by element
+    const int c16 = 16 / (int)sizeof(T);
+    const int ce = !colin ? 0 : (pitch % c16 == 0 ? c16 : (sizeof(T) == 4 && pitch % 2 == 0 ? 2 : 0));
+    if (ce > 0) {
+      xs = sx0 % ce;
+      const int gs = sx0 - xs;
+      const int nch = (xs + RX + ce - 1) / ce;      // <= 65 (8-byte chunks of <= 129 values): three passes
+      for (int ry = threadIdx.x >> 5; ry < RY; ry += NT / 32) {
+        const int ey = oy0 + ry;
+        int sy;
+        if (CORR) sy = (ey >= 0 && ey < n) ? ey : -1;
+        else if (pd.bc == BC_RECT) sy = (ey + c >= 0 && ey + c < pd.nf) ? ey + c : -1;
+        else sy = bc_map_near(ey, n, pd.bc);
+        const T* row = src + (size_t)(sy < 0 ? 0 : sy) * pitch;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int rx = lane + 32 * k;
-        if (rx < RX) {
-          const int ex = ox0 + rx;
-          int sx;
-          if (CORR) sx = (ex >= 0 && ex < n) ? ex : -1;
-          else if (pd.bc == BC_RECT) sx = (ex + c >= 0 && ex + c < pd.nf) ? ex + c : -1;
-          else sx = bc_map_near(ex, n, pd.bc);
-          const bool ok = sy >= 0 && sx >= 0;
-          cp_async_zfill<sizeof(T)>(s_in + ry * RP + rx, row + (ok ? sx : 0), ok);
+        for (int k = 0; k < 3; ++k) {
+          const int ch = lane + 32 * k;
+          if (ch < nch) {
+            const int g0 = gs + ch * ce;
+            int nv = pitch - g0;
+            nv = nv < 0 ? 0 : (nv > ce ? ce : nv);
+            if (sy < 0) nv = 0;
+            T* d = s_in + ry * RP + ch * ce;
+            const T* g = row + (nv > 0 ? g0 : 0);
+            if (ce * (int)sizeof(T) == 16) cp_async_bytes<16>(d, g, nv * (int)sizeof(T));
+            else cp_async_bytes<8>(d, g, nv * (int)sizeof(T));
+          }
+        }
+      }
+    } else {
+      for (int ry = threadIdx.x >> 5; ry < RY; ry += NT / 32) {
+        const int ey = oy0 + ry;
+        int sy;
+        if (CORR) sy = (ey >= 0 && ey < n) ? ey : -1;
+        else if (pd.bc == BC_RECT) sy = (ey + c >= 0 && ey + c < pd.nf) ? ey + c : -1;
+        else sy = bc_map_near(ey, n, pd.bc);
+        const T* row = src + (size_t)(sy < 0 ? 0 : sy) * pitch;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int rx = lane + 32 * k;
+          if (rx < RX) {
+            const int ex = ox0 + rx;
+            int sx;
+            if (CORR) sx = (ex >= 0 && ex < n) ? ex : -1;
+            else if (pd.bc == BC_RECT) sx = (ex + c >= 0 && ex + c < pd.nf) ? ex + c : -1;
+            else sx = bc_map_near(ex, n, pd.bc);
+            const bool ok = sy >= 0 && sx >= 0;
+            cp_async_zfill<sizeof(T)>(s_in + ry * RP + rx, row + (ok ? sx : 0), ok);
+          }
         }
       }
     }
@@ -299,7 +356,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
       T h[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) h[j] = T(0);
-      window_run<T>(h, s_in + ry * RP + x8, 1, s_w, p);
+      window_run<T>(h, s_in + ry * RP + xs + x8, 1, s_w, p);
 #pragma unroll
       for (int j = 0; j < 8; ++j) s_tmp[ry * ST_TP + x8 + j] = h[j];
     }
@@ -314,7 +371,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
       const int len = rn.z - rn.y + 1;
       const int col = CORR ? x2 + rn.x : x2 + 2 * c - rn.x;
       const int r0 = CORR ? y8 + rn.y : y8 + 2 * c - rn.z;
-      window_run2<T>(acc, s_in + r0 * RP + col, RP, s_w + rn.w, len, (col & 1) == 0);
+      window_run2<T>(acc, s_in + r0 * RP + xs + col, RP, s_w + rn.w, len, ((xs + col) & 1) == 0);
     }
   }
   T* dst = static_cast<T*>(pd.buf[dst_slot]);

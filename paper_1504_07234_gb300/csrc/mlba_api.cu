@@ -724,7 +724,8 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     }
     // stencil: weights (padded to 16 bytes), runs, input tile, row-pass tile
     const size_t RY = 32 + pd.p - 1, RX = 64 + pd.p - 1;
-    const size_t RP = (RX + 1) & ~(size_t)1;
+    const size_t ce = 16 / ts;                  // input-tile pitch as in k_stencil.cu (st_pitch)
+    const size_t RP = (RX + 2 * (ce - 1)) / ce * ce;
     const size_t nw = pd.sep ? 2 * pd.p : pd.nrw;
     const size_t st_b = (((nw + 3) & ~(size_t)3) + RY * RP + (pd.sep ? RY * 66 : 0)) * ts +
                         (pd.sep ? 0 : (size_t)pd.nruns * 16);
