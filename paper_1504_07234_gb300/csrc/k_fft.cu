@@ -386,25 +386,6 @@ __device__ __forceinline__ bool spec_elem(const Prob& pd, int blk, int e, T& pw,
   return true;
 }
 
-// Position in the column-blocked spectrum (block b, frequency k1 of the
-// block's rows, column c of the block) advanced by a fixed step below N cb
-// with adds and compares only (two divisions at the start).
-struct SpecWalk {
-  int b, k1, c, N, cb, dk1, dc;
-  __device__ __forceinline__ SpecWalk(int n, int cbk, int L, int step) : N(n), cb(cbk) {
-    const int blksz = n * cbk;
-    b = L / blksz;
-    const int rem = L - b * blksz;
-    k1 = rem / cbk; c = rem - k1 * cbk;
-    dk1 = step / cbk; dc = step - dk1 * cbk;
-  }
-  __device__ __forceinline__ void next() {
-    c += dc; k1 += dk1;
-    if (c >= cb) { c -= cb; ++k1; }
-    if (k1 >= N) { k1 -= N; ++b; }
-  }
-};
-
 __device__ __forceinline__ void ns_set_alpha(const Prob& pd, State& st, double nb) {
   if (nb < -32.2) nb = -32.2;                          // alpha floor 1e-14
   st.nb = nb;
@@ -574,6 +555,7 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
   const int kb = blk * cb;
   const double b0 = st.nb;
   const T* w = static_cast<const T*>(pd.w) + base;
+  T* pwo = static_cast<T*>(pd.pw) + base;   // weighted powers for the Halley passes
   if (threadIdx.x < NS_CAND)
     s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
   __syncthreads();
@@ -600,7 +582,7 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
     if (e >= N * cb) break;
     const int k1 = fcb.div(e), c = e - k1 * cb;
     const int k2 = kb + c;
-    if (k2 >= W) continue;
+    if (k2 >= W) { pwo[e] = T(0); continue; }
     T pw;
     if (dct) {
       const T v = smr[2 * ((c >> 1) * TSg + fpad(k1)) + (c & 1)];
@@ -610,6 +592,7 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
       const T m = (k2 == 0 || ((N & 1) == 0 && k2 == N / 2)) ? T(1) : T(2);
       pw = m * (vr * vr + vi * vi);
     }
+    pwo[e] = pw;
     sP += pw;
     ns_cand_acc((float)pw, wv[qq], ca, cF, cG);
   }
@@ -1255,6 +1238,8 @@ k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const in
       ok[q] = spec_elem<T>(pd, item.y, threadIdx.x + (q0 + q) * NS_NT, pw[q], sg[q]);
 #pragma unroll
     for (int q = 0; q < NS_B; ++q) {
+      const int L = item.y * (NS_NT * NS_PT) + threadIdx.x + (q0 + q) * NS_NT;
+      if (L < pd.nblk_cols * pd.n * pd.cb) static_cast<T*>(pd.pw)[L] = ok[q] ? pw[q] : T(0);
       if (!ok[q]) continue;
       sP += pw[q];
       ns_cand_acc((float)pw[q], (float)sg[q], ca, cF, cG);
@@ -1284,50 +1269,32 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   if (threadIdx.x == 0) s_alpha = T(exp(b0));
   __syncthreads();
   const T alpha = s_alpha;
-  using T2 = typename Vec2<T>::type;
-  const int N = pd.n, cb = pd.cb;
-  const bool dct = (pd.transform == TR_DCT);
-  const int W = dct ? N : pd.half;
-  const int nel = pd.nblk_cols * N * cb;
+  // the weighted powers (0 on padding) and sigma, both blocked like S
+  const int nel = pd.nblk_cols * pd.n * pd.cb;
+  const T* P = static_cast<const T*>(pd.pw);
+  const T* Sg = static_cast<const T*>(pd.w);
   int L = item.y * (NS_NT * NS_PT) + threadIdx.x;
-  SpecWalk wk(N, cb, L, NS_NT);
   T sP = T(0), sF = T(0), sG1 = T(0), sG2 = T(0);
 #pragma unroll 1
   for (int q0 = 0; q0 < NS_PT; q0 += NS_B) {
-  T pw[NS_B], sg[NS_B];
-  bool ok[NS_B];
+    T pw[NS_B], sg[NS_B];
 #pragma unroll
-  for (int q = 0; q < NS_B; ++q) {
-    const int k2 = wk.b * cb + wk.c;
-    ok[q] = L < nel && k2 < W;
-    pw[q] = T(0); sg[q] = T(1);
-    if (ok[q]) {
-      sg[q] = static_cast<const T*>(pd.w)[L];
-      if (dct) {
-        // unnormalised DCT-II: |orthonormal coefficient|^2 = v^2 s_k1^2 s_k2^2
-        // with s_0^2 = 1/N and s_k^2 = 2/N; the common 1/N^2 cancels
-        const T v = static_cast<const T*>(pd.buf[SL_S])[L];
-        pw[q] = T((wk.k1 == 0 ? 1 : 2) * (k2 == 0 ? 1 : 2)) * v * v;
-      } else {
-        const T2 v = static_cast<const T2*>(pd.buf[SL_S])[L];
-        const T m = (k2 == 0 || ((N & 1) == 0 && k2 == N / 2)) ? T(1) : T(2);
-        pw[q] = m * (v.x * v.x + v.y * v.y);
-      }
+    for (int q = 0; q < NS_B; ++q) {
+      const int e = L + q * NS_NT;
+      pw[q] = T(0); sg[q] = T(1);
+      if (e < nel) { pw[q] = P[e]; sg[q] = Sg[e]; }
     }
-    L += NS_NT;
-    wk.next();
-  }
 #pragma unroll
-  for (int q = 0; q < NS_B; ++q) {
-    if (!ok[q]) continue;
-    const T x = wdiv(alpha, sg[q] + alpha);
-    const T px2 = pw[q] * x * x;
-    const T g1 = px2 * (T(1) - x);
-    sP += pw[q];
-    sF += px2;
-    sG1 += g1;
-    sG2 += g1 * (T(2) - T(3) * x);
-  }
+    for (int q = 0; q < NS_B; ++q) {
+      const T x = wdiv(alpha, sg[q] + alpha);
+      const T px2 = pw[q] * x * x;
+      const T g1 = px2 * (T(1) - x);
+      sP += pw[q];
+      sF += px2;
+      sG1 += g1;
+      sG2 += g1 * (T(2) - T(3) * x);
+    }
+    L += NS_B * NS_NT;
   }
   T v[4] = {sP, sF, sG1, sG2};
   if (ns_reduce<NS_NT, 4, T>(pd, st, item.y, pd.nblk_spec, v, red, tot) && threadIdx.x == 0) {

@@ -622,6 +622,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         (size_t)pd.nbands * nf2 * zs,          // z1
         nspec * ts * (pd.transform == TR_DCT ? 1 : 2),   // lam
         nspec * ts,                            // |lambda|^2 in T precision
+        (pd.ns ? nspec : 1) * ts,              // 4-NS weighted power
         spec ? (size_t)pd.n * 2 * ts : ts,     // tw
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
         (size_t)pd.nruns * 16, 2 * (size_t)pd.nrw * ts,   // tap runs and weights (both orders)
@@ -646,6 +647,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     pd.z[1] = base + of[k++];
     pd.lam = base + of[k++];
     pd.w = base + of[k++];
+    pd.pw = base + of[k++];
     pd.tw = base + of[k++];
     pd.dtw = base + of[k++];
     pd.tap_runs = reinterpret_cast<int4*>(base + of[k++]);

@@ -59,6 +59,9 @@ struct Prob {
   void* buf[NSLOT];
   void* z[2];        // ping-pong Bregman variable
   void* w;           // |lambda|^2 in T precision, column-blocked like S
+  void* pw;          // 4-NS: weighted power |orthonormal coefficient of r|^2 per
+                     // spectral value, T, blocked like S (0 on padding); written by
+                     // the bracketing pass, read by the Halley passes
   void* lam;         // spectrum of C (real for DCT, complex half for DFT), T, blocked
   void* tw;          // exp(-2 pi i k/n), k < n   (T2)
   void* dtw;         // exp(-i pi k/(2n)), k < n  (T2)
