@@ -203,7 +203,8 @@ constexpr int ST_TX = 64, ST_TY = 32;
 __host__ __device__ constexpr int st_pitch(int RX, int elem) {
   return (RX + 16 / elem - 1 + 16 / elem - 1) / (16 / elem) * (16 / elem);
 }
-constexpr int ST_TP = ST_TX + 2;      // row-pass tile pitch (rank-one PSF)
+constexpr int ST_TP = ST_TX + 2;      // row-pass tile pitch (rank-one PSF, p > 33)
+constexpr int ST_ROW_ITEMS = 4;       // row-pass items a thread holds in registers (8 RY <= 4 x 128)
 
 int stencil_tiles(int outN) { return ((outN + ST_TX - 1) / ST_TX) * ((outN + ST_TY - 1) / ST_TY); }
 
@@ -218,8 +219,10 @@ int stencil_tiles(int outN) { return ((outN + ST_TX - 1) / ST_TX) * ((outN + ST_
 //    the rows into shared memory, then a vertical pass with paired windows.
 // Forward (A f)(y, x) = sum_{a,b} H[a][b] f_ext(y + c - a, x + c - b); the
 // correlation (ne x ne) is sum_{a,b} H[a][b] t(y - 2c + a, x - 2c + b).
+// (FP32: 8 CTAs per SM, 64 registers; the tile of the largest PSF of a batch
+// decides how many fit in shared memory)
 template <typename T, int MODE>
-__global__ void __launch_bounds__(STENCIL_THREADS)
+__global__ void __launch_bounds__(STENCIL_THREADS, sizeof(T) == 4 ? 8 : 4)
 k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
           int src_slot, int dst_slot, int aux_slot, int pcg) {
   using T2 = typename Pair<T>::type;
@@ -349,8 +352,33 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   T2 acc[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) { acc[j].x = T(0); acc[j].y = T(0); }
-  if (sep) {
-    // row pass over all RY rows: tmp(ry, xx) = sum_t wx[t] in(ry, xx + t)
+  if (sep && 8 * RY <= ST_ROW_ITEMS * NT) {
+    // row pass over all RY rows, tmp(ry, xx) = sum_t wx[t] in(ry, xx + t): every
+    // thread first holds all of its (row, 8 columns) items in registers, then,
+    // after a barrier, writes them over the input tile (row ry of tmp at the
+    // start of input row ry), so no second tile is needed
+    T h[ST_ROW_ITEMS][8];
+#pragma unroll
+    for (int i = 0; i < ST_ROW_ITEMS; ++i) {
+      const int idx = threadIdx.x + i * NT;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[i][j] = T(0);
+      if (idx < 8 * RY) window_run<T>(h[i], s_in + (idx >> 3) * RP + xs + (idx & 7) * 8, 1, s_w, p);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ST_ROW_ITEMS; ++i) {
+      const int idx = threadIdx.x + i * NT;
+      if (idx < 8 * RY) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s_in[(idx >> 3) * RP + (idx & 7) * 8 + j] = h[i][j];
+      }
+    }
+    __syncthreads();
+    // column pass: out(y, x) = sum_t wy[t] tmp(y + t, x)
+    window_run2<T>(acc, s_in + y8 * RP + x2, RP, s_w + p, p, true);
+  } else if (sep) {
+    // (taller tiles, p > 33) the row pass into a second tile
     for (int idx = threadIdx.x; idx < 8 * RY; idx += NT) {
       const int ry = idx >> 3, x8 = (idx & 7) * 8;
       T h[8];

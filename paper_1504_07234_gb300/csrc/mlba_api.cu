@@ -729,7 +729,8 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     const size_t ce = 16 / ts;                  // input-tile pitch as in k_stencil.cu (st_pitch)
     const size_t RP = (RX + 2 * (ce - 1)) / ce * ce;
     const size_t nw = pd.sep ? 2 * pd.p : pd.nrw;
-    const size_t st_b = (((nw + 3) & ~(size_t)3) + RY * RP + (pd.sep ? RY * 66 : 0)) * ts +
+    // (a second row-pass tile only for rank-one PSFs with 8 RY > 4 x 128, see k_stencil.cu)
+    const size_t st_b = (((nw + 3) & ~(size_t)3) + RY * RP + (pd.sep && 8 * RY > 4 * 128 ? RY * 66 : 0)) * ts +
                         (pd.sep ? 0 : (size_t)pd.nruns * 16);
     smem_st = std::max(smem_st, st_b);
     if (specp) {
