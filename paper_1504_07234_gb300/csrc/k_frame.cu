@@ -237,47 +237,7 @@ k_frame(const Prob* __restrict__ probs, State* __restrict__ states, const int2* 
 }
 
 // ---------------------------------------------------------------------------
-// Register micro-tile variant for L <= 2 (the measured workloads).
-//
-// Each thread owns 2 x 2 positions of a band region.  For each column mask
-// b_j it forms the row-filtered neighbourhood h_j = b_j (x) c of the level
-// input c (shared memory, dilation D), then for the three bands (i, j):
-// a = b_i (y) h_j, z_out = z_in + a, x = S_mu(z_out), and scatters b_i (y) x
-// into a register patch; after the three bands the patch is spread by b_j (x)
-// and added into the synthesis accumulator (shared memory, padded by 2D so no
-// add needs a bounds test).  z is streamed through a per-thread queue of
-// asynchronous copies (cp.async) four bands ahead, so every thread keeps
-// 16 loads in flight without holding them in registers.  The order of the
-// shared-memory adds is not fixed: the synthesis is reproducible to
-// rounding, not bit for bit.
-constexpr int F2_THREADS = 384;
-constexpr int F2_STAGES = 4;
-
-template <int L>
-struct F2 {
-  static constexpr int TS = FRAME_TILE;
-  static constexpr int XL = (1 << L) - 1;
-  static constexpr int C0 = 2 * XL;                       // radius of u
-  static constexpr int C1 = (L == 2) ? XL + 2 : 0;        // radius of c_1
-  static constexpr int W0 = TS + 2 * C0;
-  static constexpr int W1 = TS + 2 * C1;
-  static constexpr int S0P = TS + 4;                      // s_0 padded by 2D = 2
-  static constexpr int S1P = TS + 2 + 8;                  // s_1 (radius 1) padded by 2D = 4
-};
-
-// bytes before the z queue, and total dynamic shared memory
-template <typename T, int L>
-__host__ __device__ constexpr size_t frame2_head_bytes() {
-  return ((((size_t)F2<L>::W0 * F2<L>::W0 + (size_t)F2<L>::S0P * F2<L>::S0P +
-            (L == 2 ? (size_t)F2<L>::W1 * F2<L>::W1 + (size_t)F2<L>::S1P * F2<L>::S1P : 0)) *
-           sizeof(T)) + 15) & ~(size_t)15;
-}
-template <typename T, typename TZ, int L>
-__host__ __device__ constexpr size_t frame2_smem_bytes() {
-  return frame2_head_bytes<T, L>() +
-         (sizeof(TZ) >= 4 ? (size_t)F2_STAGES * 4 * F2_THREADS * sizeof(TZ) : 0);
-}
-
+// asynchronous global -> shared copies (one thread, 4 or 8 bytes) and their groups
 __device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -289,342 +249,6 @@ __device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-template <typename TZ> struct ZQueue;
-// 4- and 8-byte z: asynchronous per-thread queue in shared memory
-template <typename TZ>
-struct ZQueue {
-  TZ* ring;   // [F2_STAGES][4][F2_THREADS]
-  __device__ __forceinline__ void issue(int slot, const TZ* zp, const int (&zo)[4]) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const TZ* g = zp + zo[e];
-      TZ* d = ring + ((size_t)(slot * 4 + e) * F2_THREADS + threadIdx.x);
-      if (sizeof(TZ) == 8) cp_async_8(d, g); else cp_async_4(d, g);
-    }
-  }
-  __device__ __forceinline__ TZ get(int slot, int e) const {
-    return ring[(size_t)(slot * 4 + e) * F2_THREADS + threadIdx.x];
-  }
-};
-// 2-byte (bf16) z: plain loads one band ahead
-template <>
-struct ZQueue<__nv_bfloat16> {
-  __nv_bfloat16 v[F2_STAGES][4];
-  __nv_bfloat16* ring;
-  __device__ __forceinline__ void issue(int slot, const __nv_bfloat16* zp, const int (&zo)[4]) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[slot][e] = zp[zo[e]];
-  }
-  __device__ __forceinline__ __nv_bfloat16 get(int slot, int e) const { return v[slot][e]; }
-};
-
-__device__ __forceinline__ void red_shared(float* p, float v) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("red.shared.add.f32 [%0], %1;\n" ::"r"(a), "f"(v) : "memory");
-}
-__device__ __forceinline__ void red_shared(double* p, double v) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("red.shared.add.f64 [%0], %1;\n" ::"r"(a), "d"(v) : "memory");
-}
-
-__host__ __device__ constexpr int f2_band(int lev, int L, int i, int j) {
-  return (i == 0 && j == 0) ? 8 * L : (lev - 1) * 8 + 3 * i + j - 1;
-}
-template <typename T> __device__ __forceinline__ T f2_mask(int k, int t) {
-  // b0 = [1,2,1]/4, b1 = sqrt(2)/4 [1,0,-1], b2 = [-1,2,-1]/4 at taps -1, 0, +1
-  return k == 0 ? (t == 1 ? T(0.5) : T(0.25))
-                : (k == 1 ? (t == 0 ? T(0.35355339059327376220) : (t == 2 ? T(-0.35355339059327376220) : T(0)))
-                          : (t == 1 ? T(0.5) : T(-0.25)));
-}
-
-template <typename T> struct V2T;
-template <> struct V2T<float> { using type = float2; };
-template <> struct V2T<double> { using type = double2; };
-
-// S_mu(z) = z - clamp(z, -mu, mu): the same value as sgn(z) max(|z| - mu, 0)
-template <typename T> __device__ __forceinline__ T soft_clamp(T z, T mu) {
-  return z - fmin(fmax(z, -mu), mu);
-}
-
-// one level's bands for every micro-tile of the band region; sp is the
-// synthesis accumulator padded by 2D on each side (row pitch SP).  INTERIOR:
-// the band region lies inside the image, so no reflection or sign is needed.
-template <typename T, typename TZ, int LEV, int L, int SP, bool INTERIOR>
-__device__ __forceinline__ void f2_level(const Prob& pd, const T* __restrict__ cur, int rc,
-                                         T* __restrict__ sp, const TZ* __restrict__ zin,
-                                         TZ* __restrict__ zout, int by0, int bx0, T mu,
-                                         ZQueue<TZ>& q) {
-  using T2 = typename V2T<T>::type;
-  constexpr int TS = FRAME_TILE;
-  constexpr int D = 1 << (LEV - 1);
-  constexpr int X = (1 << LEV) - 1;
-  constexpr int WB = TS + 2 * X;
-  constexpr int MW = WB / 2;
-  constexpr int NR = 2 + 2 * D;      // rows / columns of the neighbourhood and the patch
-  constexpr int K0 = (LEV == L) ? 0 : 1;      // band sequence k = 3 j + i, (0,0) only at level L
-  constexpr int NB = 9 - K0;
-  const int wc = TS + 2 * rc;
-  const int off = rc - X;
-  const int nf = pd.nf;
-  const size_t plane = (size_t)nf * nf;
-  for (int mt = threadIdx.x; mt < MW * MW; mt += F2_THREADS) {
-    const int my = mt / MW, mx = mt - my * MW;
-    const int qy = 2 * my, qx = 2 * mx;
-    // element offsets of the four positions inside a z plane (planes hold
-    // at most 4126^2 < 2^31 elements), reflected outside the image
-    int zof[4];
-    bool pry[2], prx[2];
-    bool inr[2], inc[2];
-    {
-      int zr[2], zc[2];
-#pragma unroll
-      for (int o = 0; o < 2; ++o) {
-        const int gy = by0 - X + qy + o, gx = bx0 - X + qx + o;
-        if (INTERIOR) {
-          zr[o] = gy; zc[o] = gx; pry[o] = false; prx[o] = false;
-        } else {
-          int py, px;
-          zr[o] = refl_half(gy, nf, &py);
-          zc[o] = refl_half(gx, nf, &px);
-          pry[o] = py != 0; prx[o] = px != 0;
-        }
-        inr[o] = (qy + o >= X) && (qy + o < X + TS) && (INTERIOR || gy < nf);
-        inc[o] = (qx + o >= X) && (qx + o < X + TS) && (INTERIOR || gx < nf);
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) zof[e] = zr[e >> 1] * nf + zc[e & 1];
-    }
-    const int zst = (by0 - X + qy) * nf + (bx0 - X + qx);   // z store offset of (0,0)
-    // prologue: queue the first bands (k = 3 j + i order)
-#pragma unroll
-    for (int p = 0; p < F2_STAGES; ++p) {
-      if (p < NB) {
-        const int k = K0 + p;
-        q.issue(p, zin + (size_t)f2_band(LEV, L, k % 3, k / 3) * plane, zof);
-      }
-      cp_commit();
-    }
-    const T* cbase = cur + (size_t)(qy - D + off) * wc + (qx - D + off);   // even column: T2 aligned
-    T* sbase = sp + (size_t)qy * SP + qx;
-#pragma unroll 1
-    for (int jj = 0; jj < 3; ++jj) {
-      // column mask b_j (runtime j keeps one j's state live at a time)
-      const T bj0 = (jj == 0) ? T(0.25) : (jj == 1 ? T(0.35355339059327376220) : T(-0.25));
-      const T bj1 = (jj == 1) ? T(0) : T(0.5);
-      const T bj2 = (jj == 0) ? T(0.25) : (jj == 1 ? T(-0.35355339059327376220) : T(-0.25));
-      // h_j on NR rows x 2 output columns
-      T h[NR][2];
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        const T2* row = reinterpret_cast<const T2*>(cbase + k * wc);
-        T cv[NR];
-#pragma unroll
-        for (int m = 0; m < NR / 2; ++m) { const T2 v = row[m]; cv[2 * m] = v.x; cv[2 * m + 1] = v.y; }
-#pragma unroll
-        for (int ox = 0; ox < 2; ++ox) h[k][ox] = bj0 * cv[ox] + bj1 * cv[ox + D] + bj2 * cv[ox + 2 * D];
-      }
-      T P[NR][2];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) { P[r][0] = T(0); P[r][1] = T(0); }
-#pragma unroll
-      for (int ii = 0; ii < 3; ++ii) {
-        const int k = 3 * jj + ii;
-        if (k < K0) continue;
-        const int seq = k - K0;
-        const int slot = seq & (F2_STAGES - 1);
-        cp_wait<F2_STAGES - 1>();
-        const int band = f2_band(LEV, L, ii, jj);
-        TZ* zo = zout + (size_t)band * plane + zst;
-        T xv[2][2];
-#pragma unroll
-        for (int oy = 0; oy < 2; ++oy) {
-#pragma unroll
-          for (int ox = 0; ox < 2; ++ox) {
-            T a = f2_mask<T>(ii, 0) * h[oy][ox] + f2_mask<T>(ii, 2) * h[oy + 2 * D][ox];
-            if (f2_mask<T>(ii, 1) != T(0)) a += f2_mask<T>(ii, 1) * h[oy + D][ox];
-            T zv = T(q.get(slot, oy * 2 + ox));
-            if (!INTERIOR) {
-              // antisymmetric bands change sign under an odd number of mirrorings
-              const bool neg = ((ii == 1) && pry[oy]) != ((jj == 1) && prx[ox]);
-              if (neg) zv = -zv;
-            }
-            const T znew = zv + a;
-            if (inr[oy] && inc[ox]) st_z(zo + oy * nf + ox, znew);
-            xv[oy][ox] = soft_clamp<T>(znew, mu);
-          }
-        }
-        // refill this slot with the band F2_STAGES ahead
-        {
-          const int sn = seq + F2_STAGES;
-          if (sn < NB) {
-            const int kn = K0 + sn;
-            q.issue(slot, zin + (size_t)f2_band(LEV, L, kn % 3, kn / 3) * plane, zof);
-          }
-          cp_commit();
-        }
-        // vertical scatter (convolution): patch row oy + (s+1) D gets b_i[s] x
-#pragma unroll
-        for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-          for (int ox = 0; ox < 2; ++ox) {
-            P[oy][ox] += f2_mask<T>(ii, 0) * xv[oy][ox];
-            if (f2_mask<T>(ii, 1) != T(0)) P[oy + D][ox] += f2_mask<T>(ii, 1) * xv[oy][ox];
-            P[oy + 2 * D][ox] += f2_mask<T>(ii, 2) * xv[oy][ox];
-          }
-      }
-      // horizontal scatter of the patch by b_j and add into the accumulator:
-      // padded accumulator position (qy + r, qx + c), c = ox + (t+1) D
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-#pragma unroll
-        for (int c = 0; c < NR; ++c) {
-          T v = T(0);
-#pragma unroll
-          for (int ox = 0; ox < 2; ++ox) {
-            const int t = c - ox;
-            if (t == 0) v += bj0 * P[r][ox];
-            if (t == D) v += bj1 * P[r][ox];
-            if (t == 2 * D) v += bj2 * P[r][ox];
-          }
-          red_shared(sbase + r * SP + c, v);
-        }
-      }
-    }
-  }
-}
-
-// dispatch a level on whether the tile's band region lies inside the image
-template <typename T, typename TZ, int LEV, int L, int SP>
-__device__ __forceinline__ void f2_level_any(const Prob& pd, const T* cur, int rc, T* sp,
-                                             const TZ* zin, TZ* zout, int by0, int bx0, T mu,
-                                             ZQueue<TZ>& q) {
-  constexpr int X = (1 << LEV) - 1;
-  const int nf = pd.nf;
-  const bool interior = by0 - X >= 0 && bx0 - X >= 0 && by0 + FRAME_TILE + X <= nf &&
-                        bx0 + FRAME_TILE + X <= nf;
-  if (interior) f2_level<T, TZ, LEV, L, SP, true>(pd, cur, rc, sp, zin, zout, by0, bx0, mu, q);
-  else f2_level<T, TZ, LEV, L, SP, false>(pd, cur, rc, sp, zin, zout, by0, bx0, mu, q);
-}
-
-template <typename T, typename TZ, int L>
-__global__ void __launch_bounds__(F2_THREADS, sizeof(T) == 8 ? 1 : 2)
-k_frame2(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-         int u_slot, int f_slot, const void* zin_op, void* zout_op, double op_mu) {
-  using Gm = F2<L>;
-  constexpr int TS = Gm::TS;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int2 item = items[blockIdx.x];
-  const Prob& pd = probs[item.x];
-  const State& st = states[item.x];
-  if (st.stopped) return;
-  const int nf = pd.nf;
-  const int tilesX = (nf + TS - 1) / TS;
-  const int by0 = (item.y / tilesX) * TS, bx0 = (item.y % tilesX) * TS;
-  const T mu = T(zin_op ? op_mu : pd.mu);
-  const TZ* zin;
-  TZ* zout;
-  if (zin_op) {
-    zin = static_cast<const TZ*>(zin_op);
-    zout = static_cast<TZ*>(zout_op);
-  } else {
-    zin = static_cast<const TZ*>(pd.z[(st.iter - 1) & 1]);
-    zout = static_cast<TZ*>(pd.z[st.iter & 1]);
-  }
-  T* cA = reinterpret_cast<T*>(smraw);            // u, radius C0
-  T* s0 = cA + Gm::W0 * Gm::W0;                   // f accumulator, padded by 2
-  T* cB = s0 + Gm::S0P * Gm::S0P;                 // c_1, radius C1 (L = 2)
-  T* s1 = cB + (L == 2 ? Gm::W1 * Gm::W1 : 0);    // s_1, radius 1, padded by 4 (L = 2)
-  unsigned char* qraw = smraw + frame2_head_bytes<T, L>();
-  ZQueue<TZ> q;
-  q.ring = reinterpret_cast<TZ*>(qraw);
-  // u on the extended tile
-  {
-    constexpr int C0 = Gm::C0, W0 = Gm::W0;
-    int mode;
-    const T* src;
-    if (u_slot >= 0) { src = static_cast<const T*>(pd.buf[u_slot]); mode = 1; }
-    else if (!pd.use_adj) { src = static_cast<const T*>(pd.buf[SL_T]); mode = 1; }
-    else if (pd.bc == BC_RECT) { src = static_cast<const T*>(pd.buf[SL_V]); mode = 1; }
-    else { src = static_cast<const T*>(pd.buf[SL_V]); mode = 0; }
-    const bool interior = by0 - C0 >= 0 && bx0 - C0 >= 0 && by0 + TS + C0 <= nf && bx0 + TS + C0 <= nf;
-    const int ty = threadIdx.x / 32, tx = threadIdx.x % 32;
-    for (int ry = ty; ry < W0; ry += F2_THREADS / 32) {
-      const int gy = by0 - C0 + ry;
-      int o;
-      const int ay = interior ? gy : refl_half(gy, nf, &o);
-      for (int rx = tx; rx < W0; rx += 32) {
-        const int gx = bx0 - C0 + rx;
-        const int ax = interior ? gx : refl_half(gx, nf, &o);
-        cA[ry * W0 + rx] = mode ? src[(size_t)ay * nf + ax] : fold_fetch<T>(pd, src, ay, ax);
-      }
-    }
-    for (int idx = threadIdx.x; idx < Gm::S0P * Gm::S0P; idx += F2_THREADS) s0[idx] = T(0);
-    if (L == 2)
-      for (int idx = threadIdx.x; idx < Gm::S1P * Gm::S1P; idx += F2_THREADS) s1[idx] = T(0);
-  }
-  __syncthreads();
-  if (L == 2) {
-    // c_1 = (b0 x b0) u on radius C1, 2 x 2 outputs per thread
-    constexpr int C1 = Gm::C1, W1 = Gm::W1, MW = W1 / 2, W0 = Gm::W0;
-    constexpr int OFF = Gm::C0 - C1;        // = 1
-    for (int mt = threadIdx.x; mt < MW * MW; mt += F2_THREADS) {
-      const int my = mt / MW, mx = mt - my * MW;
-      const int qy = 2 * my, qx = 2 * mx;
-      T hr[4][2];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const T* row = cA + (qy - 1 + k + OFF) * W0 + (qx - 1 + OFF);
-        const T a = row[0], b = row[1], c = row[2], d = row[3];
-        hr[k][0] = T(0.25) * (a + c) + T(0.5) * b;
-        hr[k][1] = T(0.25) * (b + d) + T(0.5) * c;
-      }
-#pragma unroll
-      for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-        for (int ox = 0; ox < 2; ++ox)
-          cB[(qy + oy) * W1 + qx + ox] =
-              T(0.25) * (hr[oy][ox] + hr[oy + 2][ox]) + T(0.5) * hr[oy + 1][ox];
-    }
-  }
-  // level 1 reads u only, so it runs before the barrier that publishes c_1
-  f2_level_any<T, TZ, 1, L, Gm::S0P>(pd, cA, Gm::C0, s0, zin, zout, by0, bx0, mu, q);
-  if (L == 2) {
-    __syncthreads();
-    f2_level_any<T, TZ, 2, L, Gm::S1P>(pd, cB, Gm::C1, s1, zin, zout, by0, bx0, mu, q);
-  }
-  __syncthreads();
-  if (L == 2) {
-    // s_0 += (b0 x b0, dilation 1) * s_1 ; s_1 (radius 1) sits at offset 4 in
-    // its padded buffer, s_0 at offset 2 in its own
-    constexpr int MW = TS / 2;
-    for (int mt = threadIdx.x; mt < MW * MW; mt += F2_THREADS) {
-      const int my = mt / MW, mx = mt - my * MW;
-      const int qy = 2 * my, qx = 2 * mx;
-      T hr[4][2];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const T* row = s1 + (qy + k + 4) * Gm::S1P + qx + 4;
-        const T a = row[0], b = row[1], c = row[2], d = row[3];
-        hr[k][0] = T(0.25) * (a + c) + T(0.5) * b;
-        hr[k][1] = T(0.25) * (b + d) + T(0.5) * c;
-      }
-#pragma unroll
-      for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-        for (int ox = 0; ox < 2; ++ox)
-          s0[(qy + oy + 2) * Gm::S0P + qx + ox + 2] +=
-              T(0.25) * (hr[oy][ox] + hr[oy + 2][ox]) + T(0.5) * hr[oy + 1][ox];
-    }
-    __syncthreads();
-  }
-  T* f = static_cast<T*>(pd.buf[f_slot]);
-  for (int idx = threadIdx.x; idx < TS * TS; idx += F2_THREADS) {
-    const int qy = idx / TS, qx = idx - qy * TS;
-    const int gy = by0 + qy, gx = bx0 + qx;
-    if (gy < nf && gx < nf) f[(size_t)gy * nf + gx] = s0[(qy + 2) * Gm::S0P + qx + 2];
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Warp row-sweep variant for L <= 2 (the measured workloads).
