@@ -813,9 +813,11 @@ __device__ __forceinline__ T2 weight_dct2(const Prob& pd, size_t idx, T alpha, T
 
 // Pass 2: one column block per CTA.  DFT: cb complex columns; DCT: cb real
 // columns = cb/2 packed pairs.
-// (the mode is a template parameter: each launch runs only its own code)
+// (the mode is a template parameter: each launch runs only its own code; the
+// two 4-NS modes measured faster at 5 FP32 CTAs per SM, the others at 4)
 template <typename T, int mode>
-__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
+__global__ void __launch_bounds__(tr_nt(sizeof(T)),
+                                  tr_minb(sizeof(T)) + ((sizeof(T) == 4 && (mode == COL_FWD || mode == COL_NS_INV)) ? 1 : 0))
 k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
        int pcg, double op_alpha, int op_kind) {
   using T2 = typename Vec2<T>::type;
