@@ -869,8 +869,14 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
         const int e = threadIdx.x + q * NT;
         if (e < NQ) {
           const int k1 = fH.div(e), c = 2 * (e - k1 * H);
-          sm[c * TSg + fpad(k1)] = ta[q];
-          sm[(c + 1) * TSg + fpad(k1)] = tb[q];
+          T2 a = ta[q], b = tb[q];
+          if (mode == COL_NS_INV) {
+            // no forward transform: the weights are applied on the way in
+            if (c < nvc) a = cmul(a, weight_dft<T, T2>(pd, base + 2 * (size_t)e, Ta, Tsc, kind));
+            if (c + 1 < nvc) b = cmul(b, weight_dft<T, T2>(pd, base + 2 * (size_t)e + 1, Ta, Tsc, kind));
+          }
+          sm[c * TSg + fpad(k1)] = a;
+          sm[(c + 1) * TSg + fpad(k1)] = b;
         }
       }
     }
@@ -889,18 +895,20 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
       if (cand) ns_cand_block<T>(pd, st, item.y, reinterpret_cast<const T*>(sm), TSg, base);
       return;
     }
-    for (int e = threadIdx.x; e < NQ; e += NT) {
-      const int k1 = fH.div(e), c = 2 * (e - k1 * H);
-      if (c < nvc) {
-        T2& v = sm[c * TSg + fpad(k1)];
-        v = cmul(v, weight_dft<T, T2>(pd, base + 2 * (size_t)e, Ta, Tsc, kind));
+    if (mode != COL_NS_INV) {
+      for (int e = threadIdx.x; e < NQ; e += NT) {
+        const int k1 = fH.div(e), c = 2 * (e - k1 * H);
+        if (c < nvc) {
+          T2& v = sm[c * TSg + fpad(k1)];
+          v = cmul(v, weight_dft<T, T2>(pd, base + 2 * (size_t)e, Ta, Tsc, kind));
+        }
+        if (c + 1 < nvc) {
+          T2& v = sm[(c + 1) * TSg + fpad(k1)];
+          v = cmul(v, weight_dft<T, T2>(pd, base + 2 * (size_t)e + 1, Ta, Tsc, kind));
+        }
       }
-      if (c + 1 < nvc) {
-        T2& v = sm[(c + 1) * TSg + fpad(k1)];
-        v = cmul(v, weight_dft<T, T2>(pd, base + 2 * (size_t)e + 1, Ta, Tsc, kind));
-      }
+      __syncthreads();
     }
-    __syncthreads();
     fft_smem<T2, true>(G, pd);
     for (int e = threadIdx.x; e < NQ; e += NT) {
       const int k1 = fH.div(e), c = 2 * (e - k1 * H);
@@ -976,7 +984,18 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
         if (e < NP) {
           const int k1 = fG.div(e), g = e - k1 * G;
           const int pos = (mode == COL_NS_INV) ? k1 : dct_pos(k1, N);
-          sm[g * TSg + fpad(pos)] = tmp[q];
+          T2 v = tmp[q];
+          if (mode == COL_NS_INV) {
+            // no forward transform: the weights are applied on the way in
+            const int c = 2 * g;
+            if (c + 1 < nvc) {
+              const T2 w = weight_dct2<T, T2>(pd, base + 2 * (size_t)e, Ta, Tsc, kind);
+              v.x *= w.x; v.y *= w.y;
+            } else if (c < nvc) {
+              v.x *= weight_dct<T>(pd, base + 2 * (size_t)e, Ta, Tsc, kind);
+            }
+          }
+          sm[g * TSg + fpad(pos)] = v;
         }
       }
     }
@@ -1001,19 +1020,21 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
       if (cand) ns_cand_block<T>(pd, st, item.y, smr, TSg, base);
       return;
     }
-    for (int e = threadIdx.x; e < NP; e += NT) {
-      const int k1 = fG.div(e), g = e - k1 * G;
-      const int c = 2 * g;
-      T2& v = sm[g * TSg + fpad(k1)];
-      if (c + 1 < nvc) {
-        const T2 w = weight_dct2<T, T2>(pd, base + 2 * (size_t)e, Ta, Tsc, kind);
-        v.x *= w.x; v.y *= w.y;
-      } else {
-        v.x *= (c < nvc) ? weight_dct<T>(pd, base + 2 * (size_t)e, Ta, Tsc, kind) : T(0);
-        v.y = T(0);
+    if (mode != COL_NS_INV) {
+      for (int e = threadIdx.x; e < NP; e += NT) {
+        const int k1 = fG.div(e), g = e - k1 * G;
+        const int c = 2 * g;
+        T2& v = sm[g * TSg + fpad(k1)];
+        if (c + 1 < nvc) {
+          const T2 w = weight_dct2<T, T2>(pd, base + 2 * (size_t)e, Ta, Tsc, kind);
+          v.x *= w.x; v.y *= w.y;
+        } else {
+          v.x *= (c < nvc) ? weight_dct<T>(pd, base + 2 * (size_t)e, Ta, Tsc, kind) : T(0);
+          v.y = T(0);
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
     dct_merge<T, T2>(sm, G, N, TSg, dtw);
     fft_smem<T2, true>(G, pd);
     for (int e = threadIdx.x; e < NP; e += NT) {
