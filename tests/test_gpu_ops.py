@@ -38,13 +38,15 @@ PSFS = {
     "motion7": I.psf_motion(7, 0.7),                # sparse, nonsymmetric
     "asym3": np.array([[0.0, 0.1, 0.05], [0.2, 0.3, 0.0], [0.15, 0.1, 0.1]]),
     "gauss31": I.psf_gaussian(5.0, 31),
+    "gauss41": I.psf_gaussian(7.0, 41),             # separable, p > 33: row pass into a second tile
+    "disk17": I.psf_disk(17),                       # 37 x 37 dense runs: full groups of 8 taps + remainders
 }
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc", ["zero", "periodic", "reflective", "rect"])
 @pytest.mark.parametrize("psf,n", [("gauss9", 70), ("disk2", 33), ("motion7", 45), ("asym3", 17),
-                                   ("gauss31", 64)])
+                                   ("gauss31", 64), ("gauss41", 80), ("disk17", 72)])
 def test_blur_and_adjoint(M, dtype, bc, psf, n):
     h = PSFS[psf]
     ctx = M.Context(h, n, bc, "none", dtype=dtype)
