@@ -69,3 +69,38 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     # a PSF wider than the stencil tile supports is refused, also before any device work
     big = np.full((67, 67), 1 / 67.0 ** 2)
     assert lib.mlba_create(big.ctypes.data_as(ctypes.c_void_p), 67, 128, 1, 1, ctypes.byref(o), ctypes.byref(h)) == -7
+
+
+def test_binding_structs_match_header_layout(tmp_path):
+    """The ctypes mirrors of mlba_opts, mlba_stats and mlba_problem have the
+    C layout of include/mlba.h: every field offset and the struct sizes, as a
+    host C compiler lays the header out (no GPU)."""
+    import ctypes
+    import shutil
+    import subprocess
+    import paper_1504_07234_gb300 as M
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    mirrors = {"mlba_opts": M.Opts, "mlba_stats": M.Stats, "mlba_problem": M.ProblemDesc}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mlba.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append(f'  printf("{cname} . %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {}
+    for line in out:
+        if line.strip():
+            cname, fname, v = line.split()
+            c_layout[(cname, fname)] = int(v)
+    for cname, cls in mirrors.items():
+        assert c_layout[(cname, ".")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert c_layout[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
