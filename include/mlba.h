@@ -164,13 +164,17 @@ int mlba_get_z(mlba_ctx* ctx, void* z_out, int on_device);
  * re-run), the counters, the stop record, ||r^{n-1}||, alpha_{n-1} and the
  * log-alpha warm start of Algorithm 4-NS; the state also carries the
  * histories.  The state is a host blob of mlba_state_size() bytes: a header
- * (sizes, dtype, z storage, max_iter), the scalars, the histories
- * (max_iter + 2 entries each), f (N_f x N_f, dtype) and z (band-major planes,
- * z_store type).  mlba_get_state synchronises the stream and copies it out;
- * mlba_set_state loads it into a context created with the same PSF size, n,
- * boundary treatment, levels, dtype, z storage and max_iter (else
- * MLBA_E_INVAL).  Call mlba_set_data first (it resets the state): the
- * observation g and delta are not part of the state.  The next mlba_iterate
+ * (sizes, dtype, z storage, max_iter, preconditioner, transform, stop flag,
+ * PCG cap, and mu, alpha, gamma, delta, q, rho, pcg_tol), the scalars, the
+ * histories (max_iter + 2 entries each), f (N_f x N_f, dtype) and z
+ * (band-major planes, z_store type).  mlba_get_state synchronises the stream
+ * and copies it out; mlba_set_state loads it into a context created with the
+ * same PSF size, n, boundary treatment, levels, dtype, z storage, max_iter,
+ * preconditioner, transform and parameters, whose mlba_set_data gave the same
+ * delta (else MLBA_E_INVAL: a state taken under another preconditioner or
+ * parameter set would silently continue a different iteration).  Call
+ * mlba_set_data first (it resets the state): the observation g is not part of
+ * the state.  The next mlba_iterate
  * continues from the saved iteration exactly as the original context would
  * have.  bytes: the caller's buffer size (>= mlba_state_size, else
  * MLBA_E_INVAL).  No counterpart in the paper. */

@@ -441,9 +441,11 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
     }
   }
   if (MODE == ST_FWD_RESID || MODE == ST_FWD_PCGQ) {
-    // warp sums in T, then FP64 across warps and blocks
-    for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)lacc;
+    // each thread's 16 terms in T; from the warp sum on, FP64 (an FP32
+    // partial of 16 squares is within 16 u = 1e-6 of its exact value)
+    double dl = (double)lacc;
+    for (int o = 16; o > 0; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dl;
     __syncthreads();
     double vals[1] = {0.0};
     if (threadIdx.x == 0)

@@ -1110,11 +1110,25 @@ namespace {
 struct StateHeader {
   uint32_t magic, version;
   int32_t n, nf, p, bc, nbands, dtype, z_store, max_iter;
+  int32_t precond, transform, stop, pcg_max;
   int32_t iter, stopped, stop_iter, status, nres, beta_last;
+  double mu, alpha, gamma, delta, q, rho, pcg_tol;   // the iteration's parameters
   double resnorm, alpha_n, nb, qn;
 };
 constexpr uint32_t STATE_MAGIC = 0x4d4c4253u;   // "MLBS"
-constexpr uint32_t STATE_VERSION = 1;
+constexpr uint32_t STATE_VERSION = 2;
+
+// the parameters that decide how the iteration continues, as the header keeps them
+void header_params(const Prob& pd, StateHeader& h) {
+  h.precond = pd.precond; h.transform = pd.transform; h.stop = pd.stop; h.pcg_max = pd.pcg_max;
+  h.mu = pd.mu; h.alpha = pd.alpha; h.gamma = pd.gamma; h.delta = pd.delta;
+  h.q = pd.q; h.rho = pd.rho; h.pcg_tol = pd.pcg_tol;
+}
+bool same_params(const StateHeader& a, const StateHeader& b) {
+  return a.precond == b.precond && a.transform == b.transform && a.stop == b.stop &&
+         a.pcg_max == b.pcg_max && a.mu == b.mu && a.alpha == b.alpha && a.gamma == b.gamma &&
+         a.delta == b.delta && a.q == b.q && a.rho == b.rho && a.pcg_tol == b.pcg_tol;
+}
 
 struct StateLayout {
   size_t hist, f, z, total;
@@ -1156,6 +1170,7 @@ int mlba_get_state(mlba_ctx* c, void* blob, size_t bytes) {
   h.magic = STATE_MAGIC; h.version = STATE_VERSION;
   h.n = pd.n; h.nf = pd.nf; h.p = pd.p; h.bc = pd.bc; h.nbands = pd.nbands;
   h.dtype = B->dtype; h.z_store = B->z_store; h.max_iter = pd.max_iter;
+  header_params(pd, h);
   h.iter = st.iter; h.stopped = st.stopped; h.stop_iter = st.stop_iter; h.status = st.status;
   h.nres = st.nres; h.beta_last = st.beta_last;
   h.resnorm = st.resnorm; h.alpha_n = st.alpha_n; h.nb = st.nb; h.qn = st.qn;
@@ -1176,8 +1191,11 @@ int mlba_set_state(mlba_ctx* c, const void* blob, size_t bytes) {
   if (bytes < L.total) return MLBA_E_INVAL;
   const Prob& pd = B->hp[0].pd;
   const unsigned char* in = static_cast<const unsigned char*>(blob);
-  StateHeader h;
+  StateHeader h, mine;
   std::memcpy(&h, in, sizeof(h));
+  std::memset(&mine, 0, sizeof(mine));
+  header_params(pd, mine);
+  if (!same_params(h, mine)) return MLBA_E_INVAL;
   if (h.magic != STATE_MAGIC || h.version != STATE_VERSION || h.n != pd.n || h.nf != pd.nf ||
       h.p != pd.p || h.bc != pd.bc || h.nbands != pd.nbands || h.dtype != B->dtype ||
       h.z_store != B->z_store || h.max_iter != pd.max_iter || h.iter < 0 || h.iter > pd.max_iter ||

@@ -80,7 +80,7 @@ k_residual_noalloc(const float* __restrict__ f, const float* __restrict__ g,
   }
   __syncthreads();
   const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-  float lacc = 0.f;
+  double lacc = 0.0;   // every square and sum in FP64
   for (int q = 0; q < 4; ++q) {
     const int oy = ly + 8 * q;
     const int gy = ty0 + oy, gx = tx0 + lx;
@@ -94,10 +94,10 @@ k_residual_noalloc(const float* __restrict__ f, const float* __restrict__ g,
       const size_t o = (size_t)gy * n + gx;
       const float rv = g[o] - acc;
       r[o] = rv;
-      lacc += rv * rv;
+      lacc += (double)rv * rv;
     }
   }
-  const double bs = mlba::block_sum<NA_THREADS>((double)lacc, red);
+  const double bs = mlba::block_sum<NA_THREADS>(lacc, red);
   unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + NA_MAX_TILES);
   if (threadIdx.x == 0) {
     scratch[blockIdx.x] = bs;

@@ -275,5 +275,34 @@ def test_set_state_rejects_a_foreign_blob(M):
     b.set_data(pr.g, pr.delta)
     with pytest.raises(M.MlbaError):
         b.set_state(blob)
-    a.close()
     b.close()
+    # same shape, another preconditioner or threshold: the blob would continue
+    # a different iteration, so it is refused too
+    for kw in (dict(precond="tikh"), dict(mu=2 * pr.mu), dict(alpha=2 * pr.alpha)):
+        o = dict(precond=pr.precond, mu=pr.mu, alpha=pr.alpha)
+        o.update(kw)
+        c = M.Context(pr.psf, pr.n, pr.bc, o["precond"], dtype="f64", mu=o["mu"],
+                      alpha=o["alpha"], levels=2, max_iter=10, stop=False, transform="dft")
+        c.set_data(pr.g, pr.delta)
+        with pytest.raises(M.MlbaError):
+            c.set_state(blob)
+        c.close()
+    a.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_nonfinite_data_reports_divergence(M, dtype):
+    """Host-side fault injection: a NaN planted in g makes ||r^0|| NaN; the
+    device stop rule records MLBA_E_DIVERGED and stops the problem, and later
+    steps do nothing."""
+    pr = small("reflective", "tikh_ns", n=48, psf=I.psf_disk(3), transform="dct", alpha=0.05)
+    g = pr.g.copy()
+    g[17, 5] = np.nan
+    ctx = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype=dtype, mu=pr.mu, alpha=pr.alpha,
+                    levels=2, max_iter=10, stop=True, transform="dct")
+    ctx.set_data(g, pr.delta)
+    ctx.iterate(5)
+    st = ctx.stats()
+    assert st["status"] == -5 and st["stopped"] == 1 and st["iter"] == 0
+    assert st["nres"] == 1
+    ctx.close()

@@ -49,3 +49,34 @@ def test_wrong_dilation_is_caught(monkeypatch):
     TF.test_tight_frame_dense(8, 2)          # still a tight frame ...
     with pytest.raises(AssertionError):      # ... but not the a-trous cascade
         TF.test_level2_a_trous_impulse_response()
+
+
+def test_unpreconditioned_pcg_stop_rule_is_caught(monkeypatch):
+    """Reading c12 fixes the relative residual of the preconditioned system
+    (psys); a stop on ||r_k|| / ||r_0|| must fail the pin."""
+    import test_oracle_precond as TP
+
+    def pcg_plain(r, apply_aat, apply_m, alpha, tol=1e-3, max_steps=5):
+        x = np.zeros_like(r)
+        res = r.copy()
+        zz = apply_m(res)
+        rho = float(np.vdot(res, zz))
+        p = zz.copy()
+        n0 = float(np.linalg.norm(r))
+        steps = 0
+        for k in range(1, max_steps + 1):
+            q = apply_aat(p) + alpha * p
+            a = rho / float(np.vdot(p, q))
+            x = x + a * p
+            res = res - a * q
+            steps = k
+            zz = apply_m(res)
+            rho_new = float(np.vdot(res, zz))
+            if float(np.linalg.norm(res)) / n0 <= tol:
+                break
+            p = zz + (rho_new / rho) * p
+            rho = rho_new
+        return x, steps
+    monkeypatch.setattr(O, "pcg", pcg_plain)
+    with pytest.raises(AssertionError):
+        TP.test_pcg_stops_on_preconditioned_relative_residual()

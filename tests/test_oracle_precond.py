@@ -195,3 +195,64 @@ def test_convergence_condition_batch_workload():
             lam = np.linalg.norm(w) / np.linalg.norm(v)
             v = w / np.linalg.norm(w)
         assert lam < 0.95, (p.name, lam)
+
+
+def _dense_precond(h, n, alpha):
+    """M = (CC^T + alpha I)^{-1} as a dense matrix, C the periodic-BC matrix
+    of h, built from the unitary 2-D DFT matrix and the spectrum (Section 4.1)."""
+    f1 = np.fft.fft(np.eye(n)) / math.sqrt(n)
+    f2 = np.kron(f1, f1)
+    lam = O.spectrum_dft(h, n).ravel()
+    return np.real(f2.conj().T @ np.diag(1.0 / (np.abs(lam) ** 2 + alpha)) @ f2)
+
+
+def _galerkin_pcg_iterates(a, m, alpha, r, kmax):
+    """The k-th PCG iterate without the CG recurrence: the Galerkin solution
+    of (A A^T + alpha I) x = r over the Krylov space spanned by
+    (M S)^j M r, j < k (S = A A^T + alpha I), which is the minimiser of the
+    S-norm error there.  Returns, per k, the iterate and both relative
+    residual norms: the preconditioned sqrt(r_k^T M r_k / r_0^T M r_0) and
+    the plain ||r_k|| / ||r_0||."""
+    s = a @ a.T + alpha * np.eye(a.shape[0])
+    r0 = r.ravel()
+    m0 = r0 @ m @ r0
+    basis = [m @ r0]
+    out = []
+    for _ in range(kmax):
+        v, _ = np.linalg.qr(np.stack(basis, axis=1))
+        x = v @ np.linalg.solve(v.T @ s @ v, v.T @ r0)
+        rk = r0 - s @ x
+        out.append((x, math.sqrt(rk @ m @ rk / m0), np.linalg.norm(rk) / np.linalg.norm(r0)))
+        basis.append(m @ s @ basis[-1])
+    return out
+
+
+PCG_STOP_CASE = dict(h=np.array([[0.0, 0.1, 0.05], [0.2, 0.3, 0.0], [0.15, 0.1, 0.1]]),
+                     n=16, bc="zero", alpha=0.1, tol=1e-2, seed=4)
+
+
+def test_pcg_stops_on_preconditioned_relative_residual():
+    """Section 4.2 (Eqs. psys, bet; reading c12): beta_n is the first step
+    at which sqrt(r_k^T M r_k / r_0^T M r_0) <= tol, capped at 5.  The
+    expected step and iterate come from dense matrices (Galerkin projection
+    on the Krylov space, no CG recurrence).  The case is chosen so that the
+    plain criterion ||r_k|| / ||r_0|| <= tol would stop at a later step."""
+    cs = PCG_STOP_CASE
+    h, n, bc, alpha, tol = cs["h"], cs["n"], cs["bc"], cs["alpha"], cs["tol"]
+    a = dense_blur_matrix(h, n, bc)
+    m = _dense_precond(h, n, alpha)
+    r = np.random.default_rng(cs["seed"]).standard_normal((n, n))
+    its = _galerkin_pcg_iterates(a, m, alpha, r, 5)
+    k_pre = next(k for k, (_, rel, _) in enumerate(its, 1) if rel <= tol)
+    k_plain = next((k for k, (_, _, rel) in enumerate(its, 1) if rel <= tol), 6)
+    assert 1 < k_pre < 5 and k_plain != k_pre      # the case discriminates
+    pre = O.SpectralPrecond(h, n, "dft")
+    t, steps = O.pcg(r, lambda v: O.blur(O.blur_adjoint(v, h, bc), h, bc),
+                     lambda v: pre.inv(v, alpha), alpha, tol=tol, max_steps=5)
+    assert steps == k_pre
+    np.testing.assert_allclose(t.ravel(), its[k_pre - 1][0], atol=1e-10)
+    # at the design tolerance 1e-3 the same system runs to the cap of Eq. bet
+    t5, steps5 = O.pcg(r, lambda v: O.blur(O.blur_adjoint(v, h, bc), h, bc),
+                       lambda v: pre.inv(v, alpha), alpha, tol=1e-3, max_steps=5)
+    assert all(rel > 1e-3 for _, rel, _ in its[:4]) and steps5 == 5
+    np.testing.assert_allclose(t5.ravel(), its[4][0], atol=1e-10)
