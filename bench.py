@@ -14,6 +14,13 @@ variable alone) is far larger than L2.
 
 Metric: megapixel-iterations per second (sum of observed n^2 per step).
 `python bench.py --gpus N --steps K --warmup W [--impl reference]`.
+
+`--config {1,2,3,5,l4}` measures one of the single-image workloads instead
+(64x64 FP64; 256x256 reflective 4-NS to the discrepancy stop; 1024x1024
+rectangular Rect1/2/3 with BF16 z; 4096x4096 rectangular 500 nonstationary
+iterations; the 4096x4096 image with 4 framelet levels) and prints its own
+line.  The default run also appends a compact record of those workloads
+(`per_config`) to its one line.
 """
 from __future__ import annotations
 
@@ -169,47 +176,122 @@ def ncu_traffic(kernel_hash):
     return d.get("bytes_per_launch_bench")
 
 
-def oracle_sample(probs, seconds=15.0, iters=2):
-    """Time the oracle as it stands on the first problems of the batch."""
+def cpu_model():
+    """The host CPU's model string and logical core count."""
+    name = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if not name:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return name or "unknown", os.cpu_count() or 1
+
+
+def _oracle_job(args):
+    """One worker's share of the oracle sample: run the oracle as it stands on
+    problem i for `iters` iterations; returns (i, seconds)."""
+    i, seed, count, iters = args
     from oracle import mlba_oracle as O
+    p = I.batch_problems(count=count, seed=seed)[i]
     t0 = time.perf_counter()
-    mpix_it = 0.0
-    used = []
-    for i, p in enumerate(probs):
-        O.mlba(p.g, p.psf, p.delta, p.bc, p.precond, p.mu, p.alpha, p.levels, iters, stop=False,
-               q=p.q, rho=p.rho)
-        mpix_it += p.n * p.n * iters / 1e6
-        used.append(i)
-        if time.perf_counter() - t0 > seconds:
-            break
+    O.mlba(p.g, p.psf, p.delta, p.bc, p.precond, p.mu, p.alpha, p.levels, iters, stop=False,
+           q=p.q, rho=p.rho)
+    return i, time.perf_counter() - t0
+
+
+def oracle_pool(jobs, workers):
+    """Run oracle jobs on `workers` host processes (spawned: no state of this
+    process, GPU context included, is inherited)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        return pool.map(_oracle_job, jobs, chunksize=1)
+
+
+def oracle_sample(probs, seed, count, iters=2, budget_s=20.0):
+    """Time the oracle as it stands on the host cores: one process per core,
+    each running whole problems of the batch for `iters` iterations.  The
+    sample is the whole batch when it fits the budget (estimated from the
+    first wave), else the first problems."""
+    name, ncpu = cpu_model()
+    workers = max(1, min(ncpu, 16, len(probs)))
+    t0 = time.perf_counter()
+    first = oracle_pool([(i, seed, count, iters) for i in range(workers)], workers)
     el = time.perf_counter() - t0
-    return mpix_it / el, el, used
+    per_mpix = el / max(sum(probs[i].n ** 2 for i, _ in first) / 1e6, 1e-9)
+    rest = []
+    spent = el
+    for i in range(workers, len(probs)):
+        cost = per_mpix * probs[i].n ** 2 / 1e6 / workers
+        if spent + cost > budget_s:
+            break
+        rest.append(i)
+        spent += cost
+    if rest:
+        t1 = time.perf_counter()
+        oracle_pool([(i, seed, count, iters) for i in rest], workers)
+        el += time.perf_counter() - t1
+    used = list(range(workers)) + rest
+    mpix_it = sum(probs[i].n ** 2 for i in used) * iters / 1e6
+    return {"value": mpix_it / el, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "cpu": name, "nproc": ncpu,
+            "sample": f"oracle (FP64 numpy) {iters} iterations of {len(used)} of the "
+                      f"{len(probs)} problems, one process per core, {el:.1f} s"}
 
 
 def run_reference(args):
+    """The oracle as it stands, on the same 64-problem workload, spread over
+    the host cores (one process per core, whole problems each).  Iterations
+    W .. W + K of every problem of the sample are timed as the difference of a
+    W-iteration and a (W + K)-iteration run.  The sample is the whole batch
+    when that fits about a minute, else the first problems."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle import mlba_oracle as O
+    seed, count = 4, 64
     probs = problems_for_rank(0)
-    smallest = min(range(len(probs)), key=lambda i: probs[i].n)
-    p = probs[smallest]
-    kw = dict(stop=False, q=p.q, rho=p.rho)
+    name, ncpu = cpu_model()
+    workers = max(1, min(ncpu, 16))
+    W, K = args.warmup, args.steps
+    # calibrate on one wave, then size the sample
     t0 = time.perf_counter()
-    O.mlba(p.g, p.psf, p.delta, p.bc, p.precond, p.mu, p.alpha, p.levels, args.warmup, **kw)
+    oracle_pool([(i, seed, count, 1) for i in range(workers)], workers)
+    cal = (time.perf_counter() - t0) / max(sum(probs[i].n ** 2 for i in range(workers)), 1)
+    used, cost = [], 0.0
+    for i in range(count):
+        c = cal * probs[i].n ** 2 * (2 * W + K) / workers
+        if used and cost + c > 60.0:
+            break
+        used.append(i)
+        cost += c
+    t0 = time.perf_counter()
+    oracle_pool([(i, seed, count, W) for i in used], workers)
     t1 = time.perf_counter()
-    O.mlba(p.g, p.psf, p.delta, p.bc, p.precond, p.mu, p.alpha, p.levels, args.warmup + args.steps, **kw)
+    oracle_pool([(i, seed, count, W + K) for i in used], workers)
     t2 = time.perf_counter()
-    el = (t2 - t1) - (t1 - t0)
-    el = max(el, 1e-9)
-    value = p.n * p.n * args.steps / 1e6 / el
-    sample = (f"oracle (FP64 numpy) iterations {args.warmup}..{args.warmup + args.steps} of problem "
-              f"{smallest} ({p.n}x{p.n}, {p.bc}, {p.precond}) of the 64-problem batch")
+    el = max((t2 - t1) - (t1 - t0), 1e-9)
+    mpix = sum(probs[i].n ** 2 for i in used) / 1e6
+    value = mpix * K / el
+    sample = (f"oracle (FP64 numpy) iterations {W}..{W + K} of {len(used)} of the {count} problems "
+              f"(every problem when it fits), {workers} processes")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * el / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "problems": 64},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "problems": count},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "cpu": name, "nproc": ncpu, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -227,11 +309,18 @@ def main():
                     help="advance the whole batch launch by launch (no two-group schedule)")
     ap.add_argument("--problems", type=int, default=64,
                     help="first K problems of the batch (small cases for profiling)")
+    ap.add_argument("--config", default="4", choices=["4", "1", "2", "3", "5", "l4"],
+                    help="workload: 4 = the 64-problem batch (default); 1, 2, 3, 5, l4 = the "
+                         "single-image workloads")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default run: skip the per-config record of the single-image workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.config != "4":
+        return run_single_config(args)
 
     import torch
     ws, rank, local = dist_env()
@@ -318,13 +407,13 @@ def main():
     extra = {}
     if rank == 0 and not args.no_fp64:
         extra["fp64_plain"] = fp64_plain_vs_fp32(M, probs, torch)
+    if rank == 0 and not args.no_configs and len(probs) == 64:
+        extra["per_config"] = {c: measure_config(M, torch, c, compact=True)
+                               for c in ("1", "2", "3", "5", "l4")}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, el, used = oracle_sample(probs)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle (FP64 numpy, 1 thread) 2 iterations of problems {used[0]}..{used[-1]} "
-                         f"of the batch, {el:.1f} s"}
+        cpu = oracle_sample(probs, seed=4, count=64)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
@@ -344,6 +433,252 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# single-image workloads (BASELINE configs 1, 2, 3, 5 and a 4-level variant)
+
+def frame_bytes_one(p, levels, zbytes, tbytes):
+    """Algorithmic bytes of one framelet launch for one problem: z read and
+    written, u read (the correlation for rectangular A, t otherwise), f
+    written."""
+    nb = 8 * levels + 1
+    nf2 = p.nf * p.nf
+    u = (p.n + p.p - 1) ** 2 if p.bc == "rect" else p.n * p.n
+    return 2 * nb * zbytes * nf2 + tbytes * u + tbytes * nf2
+
+
+def stage_bytes_one(p, tbytes):
+    """Algorithmic bytes of the other launches of one step for one problem:
+    residual (f, g read, r written), correlation (t read, the (n+p-1)^2
+    correlation written), spectral preconditioner (rows: r read, spectrum
+    written; columns: spectrum read and written, sigma read; rows: spectrum
+    read, t written; the half spectrum is n (n/2+1) complex for the DFT, n^2
+    real for the DCT, i.e. about n^2 values either way)."""
+    n2, ne2 = p.n * p.n, (p.n + p.p - 1) ** 2
+    return {"residual": tbytes * (p.nf * p.nf + 2 * n2),
+            "adjoint_corr": tbytes * (n2 + ne2),
+            "preconditioner": tbytes * (n2 + n2 + 3 * n2 + n2 + n2)}
+
+
+def _single_problem(c, variant=None):
+    if c == "l4":
+        pr = I.config(5)
+        pr.levels = 4
+        pr.name = "C5-L4"
+        return pr
+    return I.config(int(c), variant=variant)
+
+
+def _run_batch(M, torch, pr, dtype, iters, z_store=None, warm=0, stop=None, profile=False):
+    """One problem as a batch of one: device time of `iters` steps after
+    `warm` steps (CUDA events on the library stream), the result and stats;
+    optionally the per-stage launch times."""
+    d = dict(psf=pr.psf, g=pr.g.astype(np.float32 if dtype == "f32" else np.float64),
+             delta=pr.delta, bc=pr.bc, precond=pr.precond, mu=pr.mu, alpha=pr.alpha,
+             transform=pr.transform, max_iter=warm + iters)
+    b = M.Batch([d], dtype=dtype, z_store=z_store, levels=pr.levels,
+                stop=pr.stop if stop is None else stop, max_iter=warm + iters, gamma=pr.gamma,
+                q=pr.q, rho=pr.rho, rect_ns_hybrid=pr.rect_ns_hybrid)
+    steps = iters + 1             # the last step only evaluates the final residual
+    if stop:
+        # time exactly the steps up to the discrepancy stop (found by an
+        # untimed run), not the idle launches after it
+        b.iterate(steps)
+        steps = b.stats(0)["iter"] + 1
+        b.reset()
+    if warm:
+        b.iterate(warm)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.iterate(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = b.stats(0)
+    f = b.result(0).astype(np.float64)
+    stages = None
+    if profile:
+        stages = {}
+        for stage, name in ((4, "frame"), (3, "adjoint_corr"), (2, "preconditioner"), (1, "residual")):
+            b.reset()
+            stages[name] = b.profile(stage, 10)
+    kern = b.graph_kernels()
+    b.close()
+    return ms, st, f, stages, kern
+
+
+def _e2e(M, torch, pr, dtype, iters, z_store=None):
+    """The same run through the public API with host buffers: pinned g
+    uploaded, iterations, f downloaded, all inside the timed region."""
+    npd = np.float32 if dtype == "f32" else np.float64
+    g = torch.from_numpy(pr.g.astype(npd)).pin_memory()
+    fo = torch.empty((pr.nf, pr.nf), dtype=torch.float32 if dtype == "f32" else torch.float64).pin_memory()
+    d = dict(psf=pr.psf, g=g.numpy(), delta=pr.delta, bc=pr.bc, precond=pr.precond, mu=pr.mu,
+             alpha=pr.alpha, transform=pr.transform, max_iter=iters)
+    b = M.Batch([d], dtype=dtype, z_store=z_store, levels=pr.levels, stop=pr.stop,
+                max_iter=iters, gamma=pr.gamma, q=pr.q, rho=pr.rho, rect_ns_hybrid=pr.rect_ns_hybrid)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.set_data(0, g.numpy(), pr.delta)
+    b.reset()
+    b.iterate(iters + 1)
+    b.result(0, out=fo.numpy())
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    done = b.stats(0)["iter"]
+    b.close()
+    return {"value": pr.n * pr.n * max(done, 1) / 1e6 / el, "unit": UNIT,
+            "h2d_bytes_per_step": g.numel() * g.element_size() / max(done, 1),
+            "d2h_bytes_per_step": fo.numel() * fo.element_size() / max(done, 1)}
+
+
+def _quality(f, pr):
+    t = pr.truth_in_fov()
+    return {"rre": float(np.linalg.norm(f - t) / np.linalg.norm(t)),
+            "psnr": float(20 * np.log10(t.shape[0] / np.linalg.norm(f - t)))}
+
+
+def measure_config(M, torch, c, compact=False, iters=None, warm=5):
+    """Measure one single-image workload; returns its record (value in
+    Mpix-it/s of the observed image, roofline of the framelet launch, per
+    stage fractions, and the precision comparison the workload asks for)."""
+    hbm, peak_kind = measured_peaks()
+    out = {"workload": I.CONFIG_NAMES.get(int(c), "") if c != "l4" else
+           "rect 4096x4096, 31x31 Gaussian sigma=5, DCT + NS alpha, L=4 (the paper's level count)"}
+    if c == "1":
+        pr = _single_problem(c)
+        it = iters or pr.max_iter
+        ms, st, f, stg, kern = _run_batch(M, torch, pr, "f64", it, profile=not compact)
+        out.update(dtype="f64", iters=it, value=pr.n ** 2 * it / 1e6 / (ms / 1e3),
+                   ms_per_iter=ms / (it + 1), quality=_quality(f, pr), graph_kernels=kern,
+                   note="launch-latency bound (1.06 MB of compulsory traffic per iteration)")
+        fp32 = _run_batch(M, torch, pr, "f32", it)
+        out["fp32"] = {"value": pr.n ** 2 * it / 1e6 / (fp32[0] / 1e3),
+                       "rre_diff_vs_fp64": abs(_quality(fp32[2], pr)["rre"] - out["quality"]["rre"])}
+        main = ("f64", pr, it, None)
+    elif c == "2":
+        pr = _single_problem(c)
+        ms, st, f, stg, kern = _run_batch(M, torch, pr, "f32", pr.max_iter, stop=True, profile=not compact)
+        it = max(st["iter"], 1)
+        ms64, st64, f64, _, _ = _run_batch(M, torch, pr, "f64", pr.max_iter, stop=True)
+        q32, q64 = _quality(f, pr), _quality(f64, pr)
+        out.update(dtype="f32", iters=st["iter"], stop_iter=st["stop_iter"],
+                   value=pr.n ** 2 * it / 1e6 / (ms / 1e3), ms_per_iter=ms / (it + 1),
+                   quality=q32, graph_kernels=kern,
+                   fp64={"stop_iter": st64["stop_iter"], "quality": q64,
+                         "value": pr.n ** 2 * max(st64["iter"], 1) / 1e6 / (ms64 / 1e3)},
+                   rre_diff_vs_fp64=abs(q32["rre"] - q64["rre"]),
+                   psnr_diff_vs_fp64=abs(q32["psnr"] - q64["psnr"]))
+        main = ("f32", pr, pr.max_iter, None)
+    elif c == "3":
+        res = {}
+        it = iters or 200
+        for v in ("rect1", "rect2", "rect3"):
+            pr = _single_problem(c, v)
+            ms, st, f, stg, kern = _run_batch(M, torch, pr, "f32", it, warm=0)
+            msb, stb, fb, _, _ = _run_batch(M, torch, pr, "f32", it, z_store="bf16", warm=0)
+            ms64, _, f64, _, _ = _run_batch(M, torch, pr, "f64", it, warm=0)
+            q, qb, q64 = _quality(f, pr), _quality(fb, pr), _quality(f64, pr)
+            res[v] = {"value_fp32z": pr.n ** 2 * it / 1e6 / (ms / 1e3),
+                      "value_bf16z": pr.n ** 2 * it / 1e6 / (msb / 1e3),
+                      "value_fp64": pr.n ** 2 * it / 1e6 / (ms64 / 1e3),
+                      "quality_fp32z": q, "quality_bf16z": qb, "quality_fp64": q64,
+                      "bf16z_rel_f_err_vs_fp64": float(np.abs(fb - f64).max() / np.abs(f64).max()),
+                      "fp32z_rel_f_err_vs_fp64": float(np.abs(f - f64).max() / np.abs(f64).max())}
+        out.update(dtype="f32 (bf16 z)", iters=it, variants=res,
+                   value=res["rect1"]["value_bf16z"],
+                   note="equal budget of 200 iterations; Rect1 = BCCB (DFT), Rect2 = PCG, "
+                        "Rect3 = symmetrised PSF (DCT); the FP64 reference is the library's FP64 "
+                        "path (pinned to the oracle at smaller sizes)")
+        pr = _single_problem(c, "rect1")
+        main = ("f32", pr, it, "bf16")
+    else:   # "5", "l4"
+        pr = _single_problem(c)
+        it = iters or (pr.max_iter if c == "5" else 50)
+        ms, st, f, stg, kern = _run_batch(M, torch, pr, "f32", it, warm=0, profile=True)
+        out.update(dtype="f32", iters=it, value=pr.n ** 2 * it / 1e6 / (ms / 1e3),
+                   ms_per_iter=ms / (it + 1), quality=_quality(f, pr), stop_iter=st["stop_iter"],
+                   graph_kernels=kern)
+        if c == "5":
+            ms64, st64, f64, _, _ = _run_batch(M, torch, pr, "f64", it, warm=0)
+            q64 = _quality(f64, pr)
+            out["fp64"] = {"quality": q64, "value": pr.n ** 2 * it / 1e6 / (ms64 / 1e3)}
+            out["rre_diff_vs_fp64"] = abs(out["quality"]["rre"] - q64["rre"])
+            out["rel_f_err_vs_fp64"] = float(np.abs(f - f64).max() / np.abs(f64).max())
+        main = ("f32", pr, it, None)
+    dtype, pr, it, zst = main
+    if stg is None:
+        _, _, _, stg, _ = _run_batch(M, torch, pr, dtype, 8, z_store=zst, warm=0, profile=True)
+    tb = 8 if dtype == "f64" else 4
+    zb = 8 if dtype == "f64" else (2 if zst == "bf16" else 4)
+    fb = frame_bytes_one(pr, pr.levels, zb, tb)
+    ach = fb / (stg["frame"] / 1e3) / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "k_frame3" if pr.levels <= 2 else "k_frame",
+                       "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                       "peak_kind": peak_kind, "algorithmic_bytes_per_launch": fb}
+    sb = stage_bytes_one(pr, tb)
+    out["stage_ms"] = stg
+    out["stage_frac"] = {k: sb[k] / (stg[k] / 1e3) / 1e9 / hbm for k in sb if stg.get(k)}
+    if not compact:
+        out["e2e"] = _e2e(M, torch, pr, dtype, it, z_store=zst)
+    return out
+
+
+def run_single_config(args):
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    from paper_1504_07234_gb300.build import build
+    build()
+    import paper_1504_07234_gb300 as M
+    c = args.config
+    cpu = None
+    if not args.no_cpu:
+        cpu = oracle_config_sample(c)
+    clocks = ClockSampler(local)
+    clocks.start()
+    rec = measure_config(M, torch, c)
+    ck = clocks.stop()
+    pr = _single_problem(c, "rect1" if c == "3" else None)
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": rec["iters"], "warmup": 0,
+            "ms_per_step": rec.get("ms_per_iter"), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
+            "config": {"workload": rec["workload"], "n": pr.n, "p": pr.p, "levels": pr.levels,
+                       "l2": "inputs larger than L2" if pr.n >= 1024 else "inputs fit in L2"},
+            "clocks": ck, "e2e": rec.get("e2e"), "gpu_launches": rec.get("graph_kernels", 0) * rec["iters"],
+            "roofline": rec["roofline"], "cpu_baseline": cpu, "record": rec}
+    print(json.dumps(line))
+    return 0
+
+
+def oracle_config_sample(c):
+    """The oracle as it stands on a bounded sample of a single-image workload
+    (two iterations; the 4096 x 4096 images are sampled at 512 x 512)."""
+    from oracle import mlba_oracle as O
+    name, ncpu = cpu_model()
+    if c in ("5", "l4"):
+        pr = I.config(5, n=512)
+        if c == "l4":
+            pr.levels = 4
+    elif c == "3":
+        pr = I.config(3, variant="rect1", n=256)
+    else:
+        pr = I.config(int(c))
+    iters = 2
+    t0 = time.perf_counter()
+    O.mlba(pr.g, pr.psf, pr.delta, pr.bc, pr.precond, pr.mu, pr.alpha, pr.levels, iters,
+           stop=False, q=pr.q, rho=pr.rho, transform=pr.transform, rect_ns_hybrid=pr.rect_ns_hybrid)
+    el = time.perf_counter() - t0
+    return {"value": pr.n ** 2 * iters / 1e6 / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu": name, "nproc": ncpu,
+            "sample": f"oracle (FP64 numpy, one process) {iters} iterations of the workload at "
+                      f"{pr.n}x{pr.n}, {el:.1f} s"}
 
 
 def fp64_plain_vs_fp32(M, probs, torch, count=4, iters=40):

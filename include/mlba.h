@@ -51,7 +51,7 @@ extern "C" {
 #define MLBA_E_TIMEOUT    (-4)  /* a bounded device-side wait expired */
 #define MLBA_E_DIVERGED   (-5)  /* ||r|| became NaN or Inf */
 #define MLBA_E_STATE      (-6)  /* call out of order (e.g. iterate before set_data) */
-#define MLBA_E_UNSUPPORTED (-7) /* size not supported (a preconditioned n must be 2^a 3^b 5^c and <= 4096) */
+#define MLBA_E_UNSUPPORTED (-7) /* size not supported (a preconditioned n must be <= 4096; p <= MLBA_MAX_P) */
 
 /* ---- enumerations ---------------------------------------------------- */
 enum mlba_bc {                 /* Section 2, Table 1 */

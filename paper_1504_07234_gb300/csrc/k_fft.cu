@@ -233,6 +233,62 @@ __device__ __forceinline__ void fft_pass(int G, int N, int TSg, int Ns, const T2
   __syncthreads();
 }
 
+// One Stockham pass of any radix R (the prime factors of n above 5) over G
+// transforms of length N, as a direct sum: output s of butterfly j is
+//   sum_r x[j + r N/R] exp(-/+ 2 pi i (r k step + ((r s) mod R) N/R) / N)
+// with k = j mod Ns, step = N/(Ns R): the Stockham twiddle of input r and the
+// R-point DFT kernel folded into one index of the length-N table.  Each
+// thread computes whole outputs (R complex multiply-adds each, O(N R) per
+// pass) and holds them in registers until the block has read its inputs.
+template <typename T2, bool INV>
+__device__ __noinline__ void fft_pass_any(int G, int N, int TSg, int Ns, int R,
+                                          const T2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  constexpr int NT = tr_nt(sizeof(T2) / 2);
+  constexpr int MAXO = TR_CAP / NT;
+  const int per = N / R, step = N / (Ns * R);
+  const FastDiv fN(N), fR(R), fns(Ns);
+  T2 out[MAXO];
+#pragma unroll
+  for (int q = 0; q < MAXO; ++q) {
+    const int e = threadIdx.x + q * NT;
+    out[q].x = out[q].y = 0;
+    if (e < G * N) {
+      const int g = fN.div(e), rem = e - g * N;
+      const int j = fR.div(rem), sidx = rem - j * R;
+      const int k = j - fns.div(j) * Ns;
+      const T2* base = sm + g * TSg;
+      const int ks = k * step;
+      int rs = 0;                     // (r s) mod R, advanced by s each term
+      T2 acc = base[fpad(j)];         // r = 0: no twiddle
+      for (int r = 1; r < R; ++r) {
+        rs += sidx; if (rs >= R) rs -= R;
+        int ti = r * ks + rs * per;   // < 2N
+        if (ti >= N) ti -= N;
+        T2 w = __ldg(&tw[ti]);
+        if (INV) w.y = -w.y;
+        const T2 v = base[fpad(j + r * per)];
+        acc.x += v.x * w.x - v.y * w.y;
+        acc.y += v.x * w.y + v.y * w.x;
+      }
+      out[q] = acc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < MAXO; ++q) {
+    const int e = threadIdx.x + q * NT;
+    if (e < G * N) {
+      const int g = fN.div(e), rem = e - g * N;
+      const int j = fR.div(rem), sidx = rem - j * R;
+      const int jd = fns.div(j), k = j - jd * Ns;
+      sm[g * TSg + fpad(jd * Ns * R + k + sidx * Ns)] = out[q];
+    }
+  }
+  __syncthreads();
+}
+
 // G transforms of length n held in the dynamic shared memory of the block
 // (transform g at g * (fpad(n) + 1)); all threads of the block call this
 // The passes run grouped by radix (16s, one 8/4/2, 3s, 5s) in straight-line
@@ -251,6 +307,12 @@ __device__ __noinline__ void fft_smem(int G, const Prob& pd) {
   if (r2 == 2) { fft_pass<T2, 2, INV>(G, N, TSg, Ns, tw); Ns *= 2; }
   for (int s = 0; s < n3; ++s) { fft_pass<T2, 3, INV>(G, N, TSg, Ns, tw); Ns *= 3; }
   for (int s = 0; s < n5; ++s) { fft_pass<T2, 5, INV>(G, N, TSg, Ns, tw); Ns *= 5; }
+  // prime factors above 5 (the plan lists them after the smooth passes)
+  for (int s = pd.nstage - pd.nrany; s < pd.nstage; ++s) {
+    const int R = pd.radix[s];
+    fft_pass_any<T2, INV>(G, N, TSg, Ns, R, tw);
+    Ns *= R;
+  }
 }
 
 // position of input sample y in the DCT reordering v[j] = x[2j], v[N-1-j] = x[2j+1]

@@ -114,15 +114,22 @@ int fft_pad(int i) { return i + (i >> 4); }   // shared-memory slot of element i
 size_t spec_elems(const Prob& pd) { return (size_t)pd.nblk_cols * pd.n * pd.cb; }
 
 // Radix passes of the length-n FFT: as many radix-16 passes as divide n, then
-// at most one of 8, 4 or 2 for the rest of the power of two, then 3s and 5s.
+// at most one of 8, 4 or 2 for the rest of the power of two, then 3s and 5s,
+// then every prime factor above 5 as a direct-sum pass (any n factors within
+// MAX_STAGES passes: n <= 4096 has at most 12 prime factors).
 bool fft_plan(Prob& pd) {
   int m = pd.n, s = 0;
-  pd.nr16 = pd.r2 = pd.nr3 = pd.nr5 = 0;
+  pd.nr16 = pd.r2 = pd.nr3 = pd.nr5 = pd.nrany = 0;
   while (m % 16 == 0 && s < MAX_STAGES) { pd.radix[s++] = 16; m /= 16; ++pd.nr16; }
   for (int r : {8, 4, 2})
     if (m % r == 0 && s < MAX_STAGES) { pd.radix[s++] = r; m /= r; pd.r2 = r; break; }
   while (m % 3 == 0 && s < MAX_STAGES) { pd.radix[s++] = 3; m /= 3; ++pd.nr3; }
   while (m % 5 == 0 && s < MAX_STAGES) { pd.radix[s++] = 5; m /= 5; ++pd.nr5; }
+  for (int f = 7; m > 1 && s < MAX_STAGES;) {
+    if ((long long)f * f > m) f = m;          // the rest is prime
+    if (m % f == 0) { pd.radix[s++] = f; m /= f; ++pd.nrany; }
+    else f += 2;
+  }
   pd.nstage = s;
   return m == 1;
 }
@@ -865,7 +872,7 @@ const char* mlba_strerror(int s) {
     case MLBA_E_TIMEOUT: return "device wait timed out";
     case MLBA_E_DIVERGED: return "residual norm not finite (diverged)";
     case MLBA_E_STATE: return "call out of order";
-    case MLBA_E_UNSUPPORTED: return "unsupported size (FFT length must be 2^a 3^b 5^c)";
+    case MLBA_E_UNSUPPORTED: return "unsupported size";
     default: return "unknown status";
   }
 }

@@ -47,7 +47,8 @@ struct Prob {
   int max_iter, stop, pcg_max;
   int nstage;        // FFT plan of length n
   int radix[MAX_STAGES];
-  int nr16, r2, nr3, nr5;   // the same plan: radix-16 passes, one 8/4/2 pass, 3s, 5s
+  int nr16, r2, nr3, nr5;   // the same plan: radix-16 passes, one 8/4/2 pass, 3s, 5s,
+  int nrany;                // then the prime factors above 5 (direct-sum passes)
   // per-list block counts (reductions need them)
   int nblk_blur, nblk_corr, nblk_frame, nblk_rows, nblk_cols, nblk_spec, nblk_vec;
   int row_g, col_g;  // transforms per CTA in the row / column passes

@@ -81,7 +81,7 @@ CASES = [
 @pytest.mark.parametrize("bc,precond,transform,psf,alpha", CASES,
                          ids=[f"{c[0]}-{c[1]}-{c[2]}" for c in CASES])
 def test_fp64_loop_matches_oracle(M, bc, precond, transform, psf, alpha):
-    n = 48 if bc != "rect" else 40       # several tiles, ragged tails, FFT radix 2, 3, 4, 5
+    n = 48 if bc != "rect" else 42       # several tiles, ragged tails, FFT radix 2, 3, 16, 7
     pr = small(bc, precond, n=n, psf=psf, alpha=alpha, transform=transform)
     f, st, res, al, be = run_gpu(M, pr, "f64")
     ref = run_oracle(pr)
@@ -93,6 +93,52 @@ def test_fp64_loop_matches_oracle(M, bc, precond, transform, psf, alpha):
         np.testing.assert_allclose(al, ref["alphas"], rtol=1e-8)
     if precond == "krylov":
         assert list(be) == ref["betas"]
+
+
+ANY_N = [(196, "reflective", "tikh_ns", "dct", I.psf_disk(3), 0.05),   # 2^2 7^2 (Example 3's size)
+         (226, "zero", "bccb", "dft", I.psf_motion(7, 0.9), 0.3),         # 2 x 113 (Example 4's size)
+         (197, "periodic", "tikh", "dft", I.psf_motion(7, 0.9), 0.05),    # prime
+         (197, "rect", "sym", "auto", I.psf_motion(7, 0.9), 0.5)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n,bc,precond,transform,psf,alpha", ANY_N,
+                         ids=[f"{c[0]}-{c[1]}-{c[2]}" for c in ANY_N])
+def test_any_length_loop_matches_oracle(M, dtype, n, bc, precond, transform, psf, alpha):
+    """Transform lengths with prime factors above 5 (the field-of-view sizes
+    of Examples 3 and 4, Section 6, and a prime): FP64 to rounding, FP32 to
+    the restoration bars."""
+    pr = small(bc, precond, n=n, psf=psf, alpha=alpha, transform=transform, iters=8)
+    f, st, res, al, be = run_gpu(M, pr, dtype)
+    ref = run_oracle(pr)
+    assert st["iter"] == ref["iters"]
+    if dtype == "f64":
+        assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-9)
+        if precond == "tikh_ns":
+            np.testing.assert_allclose(al, ref["alphas"], rtol=1e-8)
+    else:
+        restoration_bars(f, ref, pr)
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc,precond,transform,n", [("reflective", "tikh_ns", "dct", 64),
+                                                    ("rect", "bccb", "dft", 50)])
+def test_four_level_loop_matches_oracle(M, dtype, bc, precond, transform, n):
+    """Four framelet levels, the paper's setting (Section 6.1)."""
+    psf = I.psf_disk(3) if transform == "dct" else I.psf_motion(7, 0.9)
+    pr = small(bc, precond, n=n, psf=psf, levels=4, alpha=0.05 if precond == "tikh_ns" else 0.3,
+               transform=transform, iters=8)
+    f, st, res, al, be = run_gpu(M, pr, dtype)
+    ref = run_oracle(pr)
+    assert st["iter"] == ref["iters"]
+    if dtype == "f64":
+        assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-9)
+    else:
+        restoration_bars(f, ref, pr)
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-3)
 
 
 def test_fp64_stop_rule_matches_oracle(M):

@@ -5,7 +5,8 @@ Tolerances: FP64 path max|err| <= 1e-11 * max|ref| (rounding-order only);
 FP32 path <= 1e-5 relative in the max norm (per-operator bar of the design)
 and 2e-2 for the bf16-stored Bregman variable (8 significant bits).
 Sizes span several 32 x 32 tiles with ragged tails, sizes below one tile, and
-FFT lengths with radix 2, 3, 4 and 5 factors.
+FFT lengths with radix 2, 3, 4 and 5 factors and with prime factors above 5
+(direct-sum passes: 196 = 2^2 7^2, 226 = 2 x 113, the prime 197, 4093).
 """
 import numpy as np
 import pytest
@@ -59,7 +60,7 @@ def test_blur_and_adjoint(M, dtype, bc, psf, n):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("n", [48, 60, 64, 100, 128, 192, 250, 256])
+@pytest.mark.parametrize("n", [48, 60, 64, 100, 128, 192, 250, 256, 42, 196, 226, 197])
 @pytest.mark.parametrize("transform,psf", [("dft", "motion7"), ("dct", "disk2"), ("dft", "gauss9"),
                                            ("dct", "gauss9")])
 def test_spectrum_and_precond(M, dtype, n, transform, psf):
@@ -83,9 +84,12 @@ def test_spectrum_and_precond(M, dtype, n, transform, psf):
 
 
 @pytest.mark.parametrize("dtype,zs", [("f64", "f64"), ("f32", "f32"), ("f32", "bf16")])
-@pytest.mark.parametrize("levels", [1, 2, 3])
-@pytest.mark.parametrize("bc,n", [("periodic", 70), ("reflective", 20), ("rect", 37), ("zero", 64)])
+@pytest.mark.parametrize("levels", [1, 2, 3, 4])
+@pytest.mark.parametrize("bc,n", [("periodic", 70), ("reflective", 20), ("rect", 37), ("zero", 64),
+                                  ("reflective", 11)])
 def test_frame_step(M, dtype, zs, levels, bc, n):
+    """L = 4 is the paper's setting (Section 6.1): dilation 8, reach 30 pixels
+    per side, wider than the 11 x 11 and 20 x 20 images (repeated mirroring)."""
     h = PSFS["asym3"]
     ctx = M.Context(h, n, bc, "none", dtype=dtype, z_store=zs, levels=levels)
     nf = ctx.nf
@@ -118,7 +122,8 @@ def test_frame_tight_frame_on_gpu(M):
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("transform,psf,n", [("dct", "disk2", 64), ("dft", "motion7", 96),
                                              ("dct", "gauss9", 60), ("dft", "motion7", 300),
-                                             ("dct", "disk2", 200)])
+                                             ("dct", "disk2", 200), ("dct", "disk2", 196),
+                                             ("dft", "motion7", 226), ("dft", "motion7", 197)])
 def test_ns_alpha(M, dtype, transform, psf, n):
     """Also at sizes whose spectrum rows do not tile the per-block element
     count (300: 151 half-spectrum columns; 200: 200 DCT columns)."""
@@ -131,4 +136,20 @@ def test_ns_alpha(M, dtype, transform, psf, n):
         ref = O.ns_alpha(np.abs(pre.forward(r)) ** 2, pre.sigma, qn)
         got = ctx.ns_alpha(r, qn)
         assert abs(got - ref) <= (1e-10 if dtype == "f64" else 2e-4) * ref, (qn, got, ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("transform,psf", [("dft", "motion7"), ("dct", "gauss9")])
+def test_precond_largest_prime_length(M, transform, psf):
+    """n = 4093, the largest prime below the 4096 limit: one direct-sum pass
+    of radix 4093 per 1-D transform (FP32).  Checked against the oracle's
+    preconditioner on the whole image."""
+    n = 4093
+    h = PSFS[psf]
+    ctx = M.Context(h, n, "periodic" if transform == "dft" else "reflective", "bccb",
+                    dtype="f32", transform=transform)
+    pre = O.SpectralPrecond(h, n, transform)
+    r = np.random.default_rng(11).standard_normal((n, n))
+    got = ctx.precond(r, 0.05, "inv")
+    assert rel_err(got, pre.inv(r, 0.05)) <= 2e-5
     ctx.close()
