@@ -99,12 +99,22 @@ typedef struct mlba_opts {
                          work half a step apart on two streams, so that one group's framelet
                          update overlaps the other's residual and preconditioner; 0 advances
                          the whole batch launch by launch.  The iterates are the same. */
+  int autotune;       /* tile shape of the framelet kernel (FP32, levels <= 2): 0 (default) the
+                         built-in shape; 1 measure every candidate shape at create on the
+                         batch's own buffers and keep the fastest, reusing an earlier
+                         measurement from the on-disk cache (MLBA_TUNE_CACHE, else
+                         $XDG_CACHE_HOME/mlba_tune.txt, else $HOME/.cache/mlba_tune.txt; an
+                         unwritable cache is skipped); 2 measure, ignoring the cache.  Every
+                         shape computes the same values; only the time differs. */
+  int frame_shape;    /* -1 (default): as autotune says; 0 .. MLBA_FRAME_SHAPES - 1: force it */
 } mlba_opts;
+
+#define MLBA_FRAME_SHAPES 8
 
 /* Fill defaults: mu = 10/255, alpha = 0.05, gamma = 1 + 1e-15, q = 0.5,
  * rho = 1e-4, pcg_tol = 1e-3, levels = 1, max_iter = 200, pcg_max = 5,
  * dtype = F32, z_store = F32, transform = AUTO, stop = 1, hybrid = 0,
- * stream = NULL, two_group = 1. */
+ * stream = NULL, two_group = 1, autotune = 0, frame_shape = -1. */
 void mlba_opts_default(mlba_opts* o);
 
 /* ---- statistics ------------------------------------------------------- */
@@ -246,6 +256,17 @@ int mlba_batch_profile(mlba_batch* b, int stage, int reps, float* ms_per_rep);
  * group). */
 int mlba_batch_graph_kernels(mlba_batch* b, int* n_kernels);
 void mlba_batch_destroy(mlba_batch* b);
+
+/* Tile shape of the framelet launch: shape index, tile columns x rows, z
+ * prefetch distance in rows, how it was chosen (0 built-in default, 1
+ * measured at create, 2 read from the tuning cache, 3 forced by
+ * opts.frame_shape) and the measured microseconds per launch (1, 2).  Shapes
+ * apply to levels <= 2; with more levels tile_x = tile_y = prefetch = 0.
+ * Any output pointer may be NULL.  No counterpart in the paper. */
+int mlba_batch_tiles(mlba_batch* b, int* frame_shape, int* tile_x, int* tile_y, int* prefetch,
+                     int* how, float* us);
+int mlba_tiles(mlba_ctx* ctx, int* frame_shape, int* tile_x, int* tile_y, int* prefetch, int* how,
+               float* us);
 
 /* ---- entry point that allocates no device memory ------------------------
  * The paper has no counterpart: this is a service for callers that cannot

@@ -42,7 +42,8 @@ class Opts(ctypes.Structure):
                 ("levels", ctypes.c_int), ("max_iter", ctypes.c_int), ("pcg_max", ctypes.c_int),
                 ("dtype", ctypes.c_int), ("z_store", ctypes.c_int), ("transform", ctypes.c_int),
                 ("stop", ctypes.c_int), ("rect_ns_hybrid", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("two_group", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("two_group", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("frame_shape", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -94,6 +95,8 @@ SIGNATURES = {
     "mlba_batch_profile": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_float)]),
     "mlba_batch_graph_kernels": (_I, [_P, ctypes.POINTER(_I)]),
     "mlba_batch_destroy": (None, [_P]),
+    "mlba_batch_tiles": (_I, [_P] + [ctypes.POINTER(_I)] * 5 + [ctypes.POINTER(ctypes.c_float)]),
+    "mlba_tiles": (_I, [_P] + [ctypes.POINTER(_I)] * 5 + [ctypes.POINTER(ctypes.c_float)]),
     "mlba_residual_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
 }
 
@@ -132,7 +135,8 @@ def _torch():
 
 def make_opts(dtype="f32", z_store=None, mu=10.0 / 255.0, alpha=0.05, levels=1, max_iter=200,
               stop=True, gamma=1.0 + 1e-15, q=0.5, rho=1e-4, transform="auto", pcg_tol=1e-3,
-              pcg_max=5, rect_ns_hybrid=False, stream=None, two_group=True) -> Opts:
+              pcg_max=5, rect_ns_hybrid=False, stream=None, two_group=True, autotune=0,
+              frame_shape=-1) -> Opts:
     lib = load_library()
     o = Opts()
     lib.mlba_opts_default(ctypes.byref(o))
@@ -145,7 +149,18 @@ def make_opts(dtype="f32", z_store=None, mu=10.0 / 255.0, alpha=0.05, levels=1, 
     o.rect_ns_hybrid = 1 if rect_ns_hybrid else 0
     o.stream = stream
     o.two_group = 1 if two_group else 0
+    o.autotune = int(autotune)
+    o.frame_shape = int(frame_shape)
     return o
+
+
+def _tiles(fn, h):
+    v = [ctypes.c_int() for _ in range(5)]
+    us = ctypes.c_float()
+    _check(fn(h, *[ctypes.byref(x) for x in v], ctypes.byref(us)), "tiles")
+    how = {0: "default", 1: "measured", 2: "cache", 3: "forced"}[v[4].value]
+    return {"frame_shape": v[0].value, "tile_x": v[1].value, "tile_y": v[2].value,
+            "prefetch": v[3].value, "how": how, "us": us.value}
 
 
 class _Base:
@@ -254,6 +269,10 @@ class Context(_Base):
         s = Stats()
         _check(self.lib.mlba_stats_get(self.h, ctypes.byref(s)), "mlba_stats_get")
         return s.as_dict()
+
+    def tiles(self):
+        """Tile shape of the framelet launch and how it was chosen."""
+        return _tiles(self.lib.mlba_tiles, self.h)
 
     def history(self):
         cap = self.opts.max_iter + 2
@@ -459,6 +478,10 @@ class Batch(_Base):
         _check(self.lib.mlba_batch_profile(self.h, int(stage), int(reps), ctypes.byref(ms)),
                "mlba_batch_profile")
         return ms.value
+
+    def tiles(self):
+        """Tile shape of the framelet launch and how it was chosen."""
+        return _tiles(self.lib.mlba_batch_tiles, self.h)
 
     def graph_kernels(self):
         k = ctypes.c_int()

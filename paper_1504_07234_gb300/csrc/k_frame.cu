@@ -249,6 +249,67 @@ __device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (cp.async.bulk, completion counted in bytes on an
+// mbarrier) for the z rows of the ring variant of the framelet sweep.  Every
+// wait on an mbarrier is bounded: after about one second (global timer) or
+// Z_SPIN_LIMIT polls it gives up and the caller reports MLBA_E_TIMEOUT
+// instead of hanging.
+constexpr unsigned Z_SPIN_LIMIT = 1u << 26;
+constexpr unsigned long long Z_WAIT_NS = 1000000000ull;
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// true once the phase with the given parity has completed; false after the
+// spin limit
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  const unsigned a = smem_u32(b);
+  unsigned long long t0 = 0;
+  for (unsigned it = 0; it < Z_SPIN_LIMIT; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it == 0) t0 = global_ns();
+    else if ((it & 255) == 0 && global_ns() - t0 > Z_WAIT_NS) return false;
+  }
+  return false;
+}
 
 // ---------------------------------------------------------------------------
 // Warp row-sweep variant for L <= 2 (the measured workloads).
@@ -273,18 +334,40 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // shared-memory atomics; the only CTA-wide barrier follows the u tile.
 constexpr int F3_TX = 26;      // tile columns: level-2 output lanes 3..28 after the +-1 low-pass
 constexpr int F3_SEG = 32;     // rows per warp
-constexpr int F3_NWR = 2;      // warps (row segments) per CTA
-constexpr int F3_TY = F3_SEG * F3_NWR;
-constexpr int F3_PF = 2;       // z prefetch distance (rows)
+// Tile shapes the autotuner chooses from: warps (32-row segments) per CTA and
+// the z prefetch distance in rows.  Every shape computes the same values in
+// the same order (a warp's sweep does not depend on its CTA), so the choice
+// changes the time only.  Shape 0 is the default; FP64 always uses it.
+// Shapes with ring > 0 stream each warp's z rows through a ring of `ring`
+// row slots in shared memory, filled by bulk asynchronous copies (one 1 KB
+// copy per row for FP32 z, 512 B for BF16) so that many rows are in flight
+// without holding registers; warps whose 32 columns cross the left or right
+// image edge (mirrored columns) fill the same ring with per-lane 16-byte
+// asynchronous copies.
+struct F3Shape { int nwr, pf, ring; };
+constexpr F3Shape F3_SHAPES[FRAME_SHAPES] = {{2, 2, 0}, {1, 2, 0}, {4, 2, 0}, {2, 3, 0}, {1, 3, 0},
+                                             {2, 2, 6}, {2, 2, 10}, {1, 2, 12}};
 
-template <int L>
+template <int L, int NWR>
 struct F3 {
+  static constexpr int TY = F3_SEG * NWR;
   static constexpr int C0 = (L == 2) ? 6 : 2;         // radius of the u tile
-  static constexpr int UW = F3_TX + 2 * C0, UH = F3_TY + 2 * C0;
-  static constexpr size_t elems = (size_t)UW * UH + (L == 2 ? (size_t)F3_TX * F3_TY : 0);
+  static constexpr int UW = F3_TX + 2 * C0, UH = TY + 2 * C0;
+  static constexpr size_t elems = (size_t)UW * UH + (L == 2 ? (size_t)F3_TX * TY : 0);
 };
-template <typename T, int L>
-__host__ __device__ constexpr size_t frame3_smem_bytes() { return F3<L>::elems * sizeof(T); }
+// bytes of one ring slot: 32 pixels' groups of 8 z values
+template <typename TZ>
+__host__ __device__ constexpr size_t f3_slot_bytes() { return 32 * 8 * sizeof(TZ); }
+// shared memory: u tile and level-2 part of f (T), then per warp `ring` slots
+// and `ring` mbarriers
+template <typename T, typename TZ, int L, int NWR, int RING>
+__host__ __device__ constexpr size_t frame3_ring_offset() {
+  return (F3<L, NWR>::elems * sizeof(T) + 15) / 16 * 16;
+}
+template <typename T, typename TZ, int L, int NWR, int RING>
+__host__ __device__ constexpr size_t frame3_smem_bytes() {
+  return frame3_ring_offset<T, TZ, L, NWR, RING>() + (size_t)NWR * RING * (f3_slot_bytes<TZ>() + 8);
+}
 
 // half-sample reflection of an index with the parity of the mirroring; the
 // common cases (inside, or one mirror away) avoid the division
@@ -311,12 +394,24 @@ __device__ __forceinline__ float to_z(float v, float*) { return v; }
 __device__ __forceinline__ double to_z(double v, double*) { return v; }
 __device__ __forceinline__ __nv_bfloat16 to_z(float v, __nv_bfloat16*) { return __float2bfloat16_rn(v); }
 
-template <typename T, typename TZ, int LEV, int L>
+// A warp's ring of z rows (RING > 0): slot k holds one row's 32 groups at
+// buf + k * 256 values and completes on bar[k]; seq counts the rows that went
+// through the bulk path (every bulk row advances one slot and, every RING rows,
+// the expected parity); bad is set when a bounded wait gave up.
+template <typename TZ>
+struct F3Ring {
+  TZ* buf;
+  unsigned long long* bar;
+  int seq;
+  bool bad;
+};
+
+template <typename T, typename TZ, int LEV, int L, int F3_PF, int RING>
 __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ cin, int cpitch,
                                          int cy0, int cx0, const TZ* __restrict__ zin,
                                          TZ* __restrict__ zout, int ty0, int tx0, int seg_lo,
                                          int seg_hi, T mu, T* __restrict__ f2s,
-                                         T* __restrict__ fout) {
+                                         T* __restrict__ fout, F3Ring<TZ>& rg) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int D = 1 << (LEV - 1);
   constexpr bool TOP = (LEV == L);
@@ -381,21 +476,65 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   }
 #pragma unroll
   for (int k = 0; k < 2 * D; ++k) hrow(yc0 - D + k, hr[k]);
-  // z queue: rows y .. y + PF - 1 (group and low-pass value per row)
-  ZGroup<TZ> zq[F3_PF];
+  // z queue: rows y .. y + PF - 1 (group and low-pass value per row; with a
+  // ring, the low-pass value only)
+  ZGroup<TZ> zq[RING > 0 ? 1 : F3_PF];
   TZ zl[F3_PF];
   // (idle lanes load a valid mirrored column too; their values are unused.
   // Offsets stay in 32 bits: nbands nf^2 < 2^31.)
   auto zload = [&](int y, int k) {
     bool par;
     const int q = f3_refl(y, nf, &par) * nf + zc;
-    const uint4* src = reinterpret_cast<const uint4*>(zin + (gbase + 8 * q));
+    if constexpr (RING == 0) {
+      const uint4* src = reinterpret_cast<const uint4*>(zin + (gbase + 8 * q));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) zq[k].v[v] = src[v];
+      for (int v = 0; v < NV; ++v) zq[k].v[v] = src[v];
+    }
     if (TOP) zl[k] = zin[lbase + q];
   };
 #pragma unroll
   for (int k = 0; k < F3_PF; ++k) zload(yc0 + k, k);
+  // ring: rows are issued RING ahead of the sweep.  Bulk path when the warp's
+  // 32 columns lie inside the image (one contiguous run of 32 groups per row),
+  // else per-lane 16-byte asynchronous copies of the mirrored columns.
+  const int x0 = tx0 - XO;
+  const bool bulk = RING > 0 && x0 >= 0 && x0 + 32 <= nf;
+  const int nrows = yc1 - yc0;
+  const int seq0 = rg.seq;
+  int n_issued = 0, first_bad = nrows;      // bulk rows issued; first row whose wait gave up
+  auto issue = [&](int i) {                 // row yc0 + i into its slot
+    if constexpr (RING > 0) {
+      bool par;
+      const int yr = f3_refl(yc0 + i, nf, &par);
+      if (bulk) {
+        const int slot = (seq0 + i) % RING;
+        ++n_issued;
+        if (lane == 0) {
+          // (the slot's previous row was only read, by this warp, before the
+          // __syncwarp that precedes this copy: no proxy fence is needed)
+          mbar_expect_tx(rg.bar + slot, (unsigned)f3_slot_bytes<TZ>());
+          bulk_g2s(rg.buf + slot * 256, zin + (gbase + 8 * (yr * nf + x0)),
+                   (unsigned)f3_slot_bytes<TZ>(), rg.bar + slot);
+        }
+      } else {
+        const int slot = i % RING;
+        const TZ* src = zin + (gbase + 8 * (yr * nf + zc));
+        TZ* dst = rg.buf + slot * 256 + 8 * lane;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) cp_async_16(dst + v * (16 / (int)sizeof(TZ)), src + v * (16 / (int)sizeof(TZ)));
+        cp_commit();
+      }
+    }
+  };
+  if constexpr (RING > 0) {
+    // the ring may hold rows an earlier level wrote with per-lane copies:
+    // order those writes before this level's bulk copies
+    if (bulk && lane == 0) fence_proxy_async();
+    for (int i = 0; i < RING; ++i) {
+      if (i < nrows) issue(i);
+      else if (!bulk) cp_commit();          // empty group: one group per row slot
+    }
+  }
   // synthesis ring: rows y - D .. y + D
   T pr[2 * D + 1][3];
 #pragma unroll
@@ -406,6 +545,28 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   // y + PF.  The queue is indexed statically (the sweep is unrolled by PF) so
   // that no register receiving an outstanding load is copied before it is used.
   auto step = [&](int y, int kq) {
+    if constexpr (RING > 0) {
+      // this row's groups from the ring, then the slot is refilled with row y + RING
+      const int i = y - yc0;
+      if (bulk) {
+        const int g = seq0 + i;
+        if (!rg.bad && !mbar_wait(rg.bar + g % RING, (unsigned)(g / RING) & 1u)) {
+          rg.bad = true;
+          first_bad = i;
+        }
+        const uint4* sv = reinterpret_cast<const uint4*>(rg.buf + (g % RING) * 256 + 8 * lane);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) zq[0].v[v] = sv[v];
+      } else {
+        cp_wait<RING - 1>();
+        const uint4* sv = reinterpret_cast<const uint4*>(rg.buf + (i % RING) * 256 + 8 * lane);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) zq[0].v[v] = sv[v];
+      }
+      __syncwarp();
+      if (i + RING < nrows && !rg.bad) issue(i + RING);
+      else if (!bulk) cp_commit();
+    }
     hrow(y + D, hr[2 * D]);
     bool pry;
     const int zro = f3_refl(y, nf, &pry) * nf;
@@ -426,7 +587,7 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
       T a = bi0 * hr[0][j] + bi2 * hr[2 * D][j];
       if (i != 1) a += bi1 * hr[D][j];
       const int pos = 3 * i + j - 1;              // place in the group ((0,0): low-pass)
-      const T zv = (i == 0 && j == 0) ? T(ld_z(&zl[kq])) : T(ld_z(&zq[kq].e[pos]));
+      const T zv = (i == 0 && j == 0) ? T(ld_z(&zl[kq])) : T(ld_z(&zq[RING > 0 ? 0 : kq].e[pos]));
       const T zn = (i == 1 && j == 1) ? fma(zv, s11, a)
                  : (i == 1) ? fma(zv, srow, a) : (j == 1) ? fma(zv, scol, a) : zv + a;
       if (i == 0 && j == 0) zlo = to_z(zn, (TZ*)nullptr);
@@ -479,13 +640,30 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
     for (int k = 0; k < F3_PF; ++k)
       if (y + k < yc1) step(y + k, k);
   }
+  if constexpr (RING > 0) {
+    if (bulk) {
+      if (rg.bad) {
+        // a wait gave up: wait (bounded) for the copies this level issued
+        // from that row on, so none lands after the CTA has gone
+        for (int i = first_bad; i < n_issued; ++i) {
+          const int g = seq0 + i;
+          mbar_wait(rg.bar + g % RING, (unsigned)(g / RING) & 1u);
+        }
+      }
+      rg.seq = seq0 + nrows;
+    } else {
+      cp_wait<0>();
+    }
+    __syncwarp();
+  }
 }
 
-template <typename T, typename TZ, int L>
+template <typename T, typename TZ, int L, int F3_NWR, int F3_PF, int RING>
 __global__ void __launch_bounds__(32 * F3_NWR)
 k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
          int u_slot, int f_slot, const void* zin_op, void* zout_op, double op_mu) {
-  using Gm = F3<L>;
+  using Gm = F3<L, F3_NWR>;
+  constexpr int F3_TY = Gm::TY;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
@@ -555,18 +733,51 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
   const int seg_lo = ty0 + w * F3_SEG, seg_hi = seg_lo + F3_SEG;
   if (seg_lo >= nf) return;        // no barrier follows
   T* f = static_cast<T*>(pd.buf[f_slot]);
-  if (L == 2) {
-    f3_level<T, TZ, 2, L>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0, seg_lo, seg_hi,
-                          mu, sf2, f);
+  // this warp's ring of z rows and its mbarriers (RING > 0)
+  F3Ring<TZ> rg;
+  rg.seq = 0;
+  rg.bad = false;
+  rg.buf = nullptr;
+  rg.bar = nullptr;
+  if constexpr (RING > 0) {
+    unsigned char* rb = smraw + frame3_ring_offset<T, TZ, L, F3_NWR, RING>();
+    rg.buf = reinterpret_cast<TZ*>(rb + (size_t)w * RING * f3_slot_bytes<TZ>());
+    rg.bar = reinterpret_cast<unsigned long long*>(rb + (size_t)F3_NWR * RING * f3_slot_bytes<TZ>()) +
+             w * RING;
+    if ((threadIdx.x & 31) == 0) {
+      for (int k = 0; k < RING; ++k) mbar_init(rg.bar + k, 1);
+      mbar_init_fence();
+    }
     __syncwarp();
   }
-  f3_level<T, TZ, 1, L>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0, seg_lo, seg_hi,
-                        mu, sf2, f);
+  if (L == 2) {
+    f3_level<T, TZ, 2, L, F3_PF, RING>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0,
+                                       seg_lo, seg_hi, mu, sf2, f, rg);
+    __syncwarp();
+  }
+  if (!rg.bad)
+    f3_level<T, TZ, 1, L, F3_PF, RING>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0,
+                                       seg_lo, seg_hi, mu, sf2, f, rg);
+  if (rg.bad && (threadIdx.x & 31) == 0) {
+    // a bounded wait gave up: the problem stops with a timeout status
+    volatile State* vs = &states[item.x];
+    vs->status = -4;
+    vs->stopped = 1;
+  }
 }
 
-int frame_tiles(int nf, int levels) {
-  if (levels <= 2) return ((nf + F3_TX - 1) / F3_TX) * ((nf + F3_TY - 1) / F3_TY);
+int frame_tiles(int nf, int levels, int shape) {
+  if (levels <= 2) {
+    const int ty = F3_SEG * F3_SHAPES[shape].nwr;
+    return ((nf + F3_TX - 1) / F3_TX) * ((nf + ty - 1) / ty);
+  }
   return ((nf + FRAME_TILE - 1) / FRAME_TILE) * ((nf + FRAME_TILE - 1) / FRAME_TILE);
+}
+
+void frame_shape(int shape, int* tile_x, int* tile_y, int* prefetch) {
+  *tile_x = F3_TX;
+  *tile_y = F3_SEG * F3_SHAPES[shape].nwr;
+  *prefetch = F3_SHAPES[shape].ring > 0 ? F3_SHAPES[shape].ring : F3_SHAPES[shape].pf;
 }
 
 // Planar (band-major) <-> grouped z layout (L <= 2), element size E bytes.
@@ -605,49 +816,105 @@ void launch_z_layout(void* dst, const void* src, int levels, int nf, int elem_by
         static_cast<const unsigned short*>(src), nbands, plane, to_grouped);
 }
 
+// the kernel of one tile shape, its shared memory and its launch (FP64 has
+// only shape 0); the cases follow F3_SHAPES
+#define F3_SHAPE_CASES(X) \
+  X(1, 1, 2, 0) X(2, 4, 2, 0) X(3, 2, 3, 0) X(4, 1, 3, 0) X(5, 2, 2, 6) X(6, 2, 2, 10) X(7, 1, 2, 12)
+
+template <typename T, typename TZ, int L>
+const void* frame3_kernel(int shape) {
+  if constexpr (sizeof(T) == 8) {
+    return (const void*)k_frame3<T, TZ, L, 2, 2, 0>;
+  } else {
+    switch (shape) {
+#define X(S, NWR, PF, RING) case S: return (const void*)k_frame3<T, TZ, L, NWR, PF, RING>;
+      F3_SHAPE_CASES(X)
+#undef X
+      default: return (const void*)k_frame3<T, TZ, L, 2, 2, 0>;
+    }
+  }
+}
+template <typename T, typename TZ, int L>
+size_t frame3_smem(int shape) {
+  if constexpr (sizeof(T) == 8) {
+    return frame3_smem_bytes<T, TZ, L, 2, 0>();
+  } else {
+    switch (shape) {
+#define X(S, NWR, PF, RING) case S: return frame3_smem_bytes<T, TZ, L, NWR, RING>();
+      F3_SHAPE_CASES(X)
+#undef X
+      default: return frame3_smem_bytes<T, TZ, L, 2, 0>();
+    }
+  }
+}
+template <typename T, typename TZ, int L>
+void launch_frame3_shape(int shape, const Prob* probs, State* states, const int2* items, int nitems,
+                         int u_slot, int f_slot, const void* zin, void* zout, double op_mu,
+                         cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    k_frame3<T, TZ, L, 2, 2, 0><<<nitems, 64, frame3_smem_bytes<T, TZ, L, 2, 0>(), s>>>(
+        probs, states, items, u_slot, f_slot, zin, zout, op_mu);
+  } else {
+    switch (shape) {
+#define X(S, NWR, PF, RING)                                                                     \
+  case S:                                                                                       \
+    k_frame3<T, TZ, L, NWR, PF, RING><<<nitems, 32 * NWR, frame3_smem_bytes<T, TZ, L, NWR, RING>(), s>>>( \
+        probs, states, items, u_slot, f_slot, zin, zout, op_mu);                               \
+    break;
+      F3_SHAPE_CASES(X)
+#undef X
+      default:
+        k_frame3<T, TZ, L, 2, 2, 0><<<nitems, 64, frame3_smem_bytes<T, TZ, L, 2, 0>(), s>>>(
+            probs, states, items, u_slot, f_slot, zin, zout, op_mu);
+    }
+  }
+}
+
 template <typename T, typename TZ>
 void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, int u_slot,
                   int f_slot, const void* zin, void* zout, double op_mu, size_t smem, int levels,
-                  cudaStream_t s) {
+                  int shape, cudaStream_t s) {
   if (nitems <= 0) return;
   if (levels == 1)
-    k_frame3<T, TZ, 1><<<nitems, 32 * F3_NWR, frame3_smem_bytes<T, 1>(), s>>>(
-        probs, states, items, u_slot, f_slot, zin, zout, op_mu);
+    launch_frame3_shape<T, TZ, 1>(shape, probs, states, items, nitems, u_slot, f_slot, zin, zout, op_mu, s);
   else if (levels == 2)
-    k_frame3<T, TZ, 2><<<nitems, 32 * F3_NWR, frame3_smem_bytes<T, 2>(), s>>>(
-        probs, states, items, u_slot, f_slot, zin, zout, op_mu);
+    launch_frame3_shape<T, TZ, 2>(shape, probs, states, items, nitems, u_slot, f_slot, zin, zout, op_mu, s);
   else
     k_frame<T, TZ><<<nitems, FRAME_THREADS, smem, s>>>(probs, states, items, u_slot, f_slot, zin,
                                                          zout, op_mu);
 }
 template <typename T, typename TZ>
 cudaError_t frame_set_smem(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_frame3<T, TZ, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)frame3_smem_bytes<T, 1>());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_frame3<T, TZ, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)frame3_smem_bytes<T, 2>());
-  if (e != cudaSuccess) return e;
+  for (int sh = 0; sh < FRAME_SHAPES; ++sh) {
+    cudaError_t e = cudaFuncSetAttribute(frame3_kernel<T, TZ, 1>(sh),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)frame3_smem<T, TZ, 1>(sh));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(frame3_kernel<T, TZ, 2>(sh), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)frame3_smem<T, TZ, 2>(sh));
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k_frame<T, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)bytes);
 }
 
 bool is_frame_kernel(const void* func) {
-  const void* k[] = {
-      (const void*)k_frame3<float, float, 1>, (const void*)k_frame3<float, float, 2>,
-      (const void*)k_frame3<float, __nv_bfloat16, 1>, (const void*)k_frame3<float, __nv_bfloat16, 2>,
-      (const void*)k_frame3<double, double, 1>, (const void*)k_frame3<double, double, 2>,
-      (const void*)k_frame<float, float>, (const void*)k_frame<float, __nv_bfloat16>,
-      (const void*)k_frame<double, double>};
-  for (const void* f : k)
-    if (f == func) return true;
-  return false;
+  for (int sh = 0; sh < FRAME_SHAPES; ++sh) {
+    const void* k[] = {frame3_kernel<float, float, 1>(sh), frame3_kernel<float, float, 2>(sh),
+                       frame3_kernel<float, __nv_bfloat16, 1>(sh), frame3_kernel<float, __nv_bfloat16, 2>(sh),
+                       frame3_kernel<double, double, 1>(sh), frame3_kernel<double, double, 2>(sh)};
+    for (const void* f : k)
+      if (f == func) return true;
+  }
+  return func == (const void*)k_frame<float, float> || func == (const void*)k_frame<float, __nv_bfloat16> ||
+         func == (const void*)k_frame<double, double>;
 }
 
 #define INST(T, TZ)                                                                          \
   template size_t frame_smem_bytes<T, TZ>(int);                                              \
   template void launch_frame<T, TZ>(const Prob*, State*, const int2*, int, int, int,          \
-                                    const void*, void*, double, size_t, int, cudaStream_t);  \
+                                    const void*, void*, double, size_t, int, int,             \
+                                    cudaStream_t);                                            \
   template cudaError_t frame_set_smem<T, TZ>(size_t);
 INST(float, float)
 INST(float, __nv_bfloat16)

@@ -13,6 +13,7 @@
 #include <vector>
 #include <algorithm>
 #include <new>
+#include <string>
 
 #include "../../include/mlba.h"
 #include "mlba_internal.cuh"
@@ -97,6 +98,10 @@ struct mlba_batch {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraph_t g_head = nullptr, g_body = nullptr, g_tail = nullptr;
   cudaGraphExec_t x_head = nullptr, x_body = nullptr, x_tail = nullptr;
+  // framelet tile shape (k_frame.cu) and how it was chosen
+  int frame_shape = 0;
+  int frame_tuned = 0;          // 0 default, 1 measured here, 2 from the cache, 3 forced
+  float frame_us = 0.f;         // measured time of one launch of the chosen shape
 };
 
 struct mlba_ctx {
@@ -248,7 +253,7 @@ void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
     launch_stencil<T>(ST_CORR, P, S, L.corr.dev, L.corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
     // a1: z += W u, x = S_mu(z), f = W^T x
     launch_frame<T, TZ>(P, S, L.frame.dev, L.frame.count, -1, SL_F, nullptr, nullptr, 0.0,
-                        B->smem_frame, B->levels, s);
+                        B->smem_frame, B->levels, B->frame_shape, s);
   }
 }
 
@@ -403,6 +408,10 @@ size_t frame_smem(int dtype, int zs, int L) {
   return frame_smem_bytes<float, float>(L);
 }
 
+void frame_shape_of(const mlba_batch* B, int* tx, int* ty, int* pf) {
+  frame_shape(B->frame_shape, tx, ty, pf);
+}
+
 void destroy_batch(mlba_batch* B) {
   if (!B) return;
   if (B->exec) cudaGraphExecDestroy(B->exec);
@@ -502,7 +511,7 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   // launch geometry
   pd.nblk_blur = stencil_tiles(n);
   pd.nblk_corr = stencil_tiles(pd.ne);
-  pd.nblk_frame = frame_tiles(pd.nf, o.levels);
+  pd.nblk_frame = frame_tiles(pd.nf, o.levels, 0);   // shape chosen at create
   // the frame kernel indexes a z array (all bands) with 32-bit offsets
   if ((double)pd.nbands * pd.nf * pd.nf >= 2147483647.0) return MLBA_E_UNSUPPORTED;
   const int cap = TR_CAP / n;                          // transforms per CTA
@@ -580,6 +589,161 @@ int build_spectrum(mlba_batch* B, HostProb& h) {
   return MLBA_OK;
 }
 
+// ---- tile-shape autotuner of the framelet kernel ----------------------------
+// The shape (warps per CTA, z prefetch distance) of the L <= 2 framelet
+// launch is chosen per batch: forced by the options, read from the on-disk
+// cache, or measured here (every candidate launched over the batch's own
+// buffers, best of a few CUDA-event-timed launches).  All shapes give the same
+// values, so the choice changes only the time.
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+  return h;
+}
+
+std::string tune_key(const mlba_batch* B) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) std::memset(&prop, 0, sizeof(prop));
+  std::string name(prop.name);
+  for (char& ch : name) if (ch == ' ' || ch == '\t') ch = '_';
+  uint64_t h = 1469598103934665603ull;
+  for (const HostProb& hp : B->hp) {
+    const int v[5] = {hp.pd.n, hp.pd.nf, hp.pd.bc, hp.pd.use_adj, hp.pd.c};
+    h = fnv1a(h, v, sizeof(v));
+  }
+  char buf[320];
+  std::snprintf(buf, sizeof(buf), "frame3 %s sm%d%d dt%d zs%d L%d count%zu h%016llx",
+                name.empty() ? "gpu" : name.c_str(), prop.major, prop.minor, B->dtype, B->z_store,
+                B->levels, B->hp.size(), (unsigned long long)h);
+  return std::string(buf);
+}
+
+std::string tune_cache_path() {
+  if (const char* e = std::getenv("MLBA_TUNE_CACHE")) return std::string(e);
+  if (const char* x = std::getenv("XDG_CACHE_HOME")) return std::string(x) + "/mlba_tune.txt";
+  if (const char* h = std::getenv("HOME")) return std::string(h) + "/.cache/mlba_tune.txt";
+  return std::string();
+}
+
+bool tune_lookup(const std::string& key, int* shape, float* us) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return false;
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    char* tab = std::strchr(line, '\t');
+    if (!tab) continue;
+    *tab = 0;
+    if (key != line) continue;
+    int sh = -1;
+    float t = 0.f;
+    if (std::sscanf(tab + 1, "%d %f", &sh, &t) == 2 && sh >= 0 && sh < FRAME_SHAPES) {
+      *shape = sh; *us = t; found = true;     // the last entry for a key wins
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void tune_store(const std::string& key, int shape, float us) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return;
+  FILE* f = std::fopen(path.c_str(), "a");
+  if (!f) return;                               // no writable cache: keep the choice in memory
+  std::fprintf(f, "%s\t%d %.3f\n", key.c_str(), shape, us);
+  std::fclose(f);
+}
+
+void launch_frame_any(mlba_batch* B, const int2* items, int count, int shape, cudaStream_t s) {
+  if (B->dtype == MLBA_F64)
+    launch_frame<double, double>(B->d_probs, B->d_states, items, count, -1, SL_F, nullptr, nullptr,
+                                 0.0, B->smem_frame, B->levels, shape, s);
+  else if (B->z_store == MLBA_BF16)
+    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_states, items, count, -1, SL_F, nullptr,
+                                       nullptr, 0.0, B->smem_frame, B->levels, shape, s);
+  else
+    launch_frame<float, float>(B->d_probs, B->d_states, items, count, -1, SL_F, nullptr, nullptr,
+                               0.0, B->smem_frame, B->levels, shape, s);
+}
+
+std::vector<int2> frame_items(const mlba_batch* B, int shape) {
+  std::vector<int2> v;
+  for (size_t i = 0; i < B->hp.size(); ++i) {
+    const int nb = frame_tiles(B->hp[i].pd.nf, B->levels, shape);
+    for (int k = 0; k < nb; ++k) v.push_back(make_int2((int)i, k));
+  }
+  return v;
+}
+
+// mean microseconds of one framelet launch of `shape` over the whole batch
+int time_frame_shape(mlba_batch* B, int shape, float* us) {
+  const std::vector<int2> items = frame_items(B, shape);
+  int2* dev = nullptr;
+  CK(cudaMalloc(&dev, items.size() * sizeof(int2)));
+  if (cudaMemcpy(dev, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(dev);
+    return MLBA_E_CUDA;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int warm = 2, reps = 6;
+  for (int r = 0; r < warm; ++r) launch_frame_any(B, dev, (int)items.size(), shape, B->stream);
+  cudaEventRecord(e0, B->stream);
+  for (int r = 0; r < reps; ++r) launch_frame_any(B, dev, (int)items.size(), shape, B->stream);
+  cudaEventRecord(e1, B->stream);
+  const cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(dev);
+  if (err != cudaSuccess || cudaGetLastError() != cudaSuccess) return MLBA_E_CUDA;
+  *us = 1e3f * ms / reps;
+  return MLBA_OK;
+}
+
+int choose_frame_shape(mlba_batch* B, const mlba_opts& o) {
+  B->frame_shape = 0;
+  B->frame_tuned = 0;
+  const bool shaped = B->levels <= 2 && B->dtype != MLBA_F64;   // FP64: one shape
+  if (!shaped) return MLBA_OK;
+  if (o.frame_shape >= 0) {
+    B->frame_shape = o.frame_shape;
+    B->frame_tuned = 3;
+    return MLBA_OK;
+  }
+  if (!o.autotune) return MLBA_OK;
+  const std::string key = tune_key(B);
+  int sh = 0;
+  float us = 0.f;
+  if (o.autotune == 1 && tune_lookup(key, &sh, &us)) {
+    B->frame_shape = sh; B->frame_tuned = 2; B->frame_us = us;
+    return MLBA_OK;
+  }
+  // the first step reads z^0 = 0 from z[0] and writes z[1]; the timed
+  // launches read z[1] and write z[0], which the reset after create clears
+  for (const HostProb& hp : B->hp)
+    CK(cudaMemsetAsync(hp.pd.z[1], 0, (size_t)hp.pd.nbands * hp.pd.nf * hp.pd.nf * zsize(B->z_store),
+                       B->stream));
+  int best = 0;
+  float tbest = 0.f;
+  for (int k = 0; k < FRAME_SHAPES; ++k) {
+    float t = 0.f;
+    const int rc = time_frame_shape(B, k, &t);
+    if (rc != MLBA_OK) return rc;
+    if (k == 0 || t < tbest) { best = k; tbest = t; }
+  }
+  B->frame_shape = best; B->frame_tuned = 1; B->frame_us = tbest;
+  tune_store(key, best, tbest);
+  return MLBA_OK;
+}
+
 int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in, mlba_batch** out) {
   if (!probs || count <= 0 || !out) return MLBA_E_INVAL;
   mlba_opts o;
@@ -588,6 +752,8 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   if (o.dtype == MLBA_F64 && o.z_store != MLBA_F64) o.z_store = MLBA_F64;
   if (o.dtype == MLBA_F32 && o.z_store != MLBA_BF16) o.z_store = MLBA_F32;
   if (o.pcg_max < 1 || o.pcg_max > 50) return MLBA_E_INVAL;
+  if (o.autotune < 0 || o.autotune > 2 || o.frame_shape < -1 || o.frame_shape >= FRAME_SHAPES)
+    return MLBA_E_INVAL;
   mlba_batch* B = new (std::nothrow) mlba_batch();
   if (!B) return MLBA_E_NOMEM;
   B->dtype = o.dtype; B->z_store = o.z_store; B->levels = o.levels;
@@ -760,6 +926,18 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   rc |= build_list(B, B->spec_all, spec_all); rc |= build_list(B, B->vec_all, vec_all);
   if (rc != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
   if (set_smem_attrs(B) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
+  // ---- framelet tile shape (the frame list above is for shape 0)
+  {
+    const int trc = choose_frame_shape(B, o);
+    if (trc != MLBA_OK) { destroy_batch(B); return trc; }
+    if (B->frame_shape != 0) {
+      const std::vector<int2> fr = frame_items(B, B->frame_shape);
+      for (HostProb& hp : B->hp) hp.pd.nblk_frame = frame_tiles(hp.pd.nf, B->levels, B->frame_shape);
+      ItemList L;
+      if (build_list(B, L, fr) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
+      B->frame = L;      // the shape-0 list stays in B->allocs and is freed at destroy
+    }
+  }
   // ---- capture one step
   if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     destroy_batch(B); return MLBA_E_CUDA;
@@ -861,6 +1039,8 @@ void mlba_opts_default(mlba_opts* o) {
   o->stop = 1;
   o->rect_ns_hybrid = 0;
   o->stream = nullptr;
+  o->autotune = 0;
+  o->frame_shape = -1;
 }
 
 const char* mlba_strerror(int s) {
@@ -967,7 +1147,7 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
         launch_rows_inv<double>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
       }
       if (stage == 3) launch_stencil<double>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
-      if (stage == 4) launch_frame<double, double>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, s);
+      if (stage == 4) launch_frame<double, double>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, B->frame_shape, s);
     } else {
       if (stage == 1) launch_stencil<float>(ST_FWD_RESID, P, S, B->blur.dev, B->blur.count, SL_F, SL_R, SL_G, 0, B->smem_stencil, s);
       if (stage == 2) {
@@ -980,9 +1160,9 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
       if (stage == 3) launch_stencil<float>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
       if (stage == 4) {
         if (B->z_store == MLBA_BF16)
-          launch_frame<float, __nv_bfloat16>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, s);
+          launch_frame<float, __nv_bfloat16>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, B->frame_shape, s);
         else
-          launch_frame<float, float>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, s);
+          launch_frame<float, float>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, B->frame_shape, s);
       }
     }
   }
@@ -996,6 +1176,9 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
   *ms = t / (float)reps;
   return MLBA_OK;
 }
+
+int mlba_batch_tiles(mlba_batch* B, int* frame_shape, int* tile_x, int* tile_y, int* prefetch,
+                     int* how, float* us);
 
 int mlba_batch_graph_kernels(mlba_batch* B, int* n) {
   if (!B || !n || !B->graph) return MLBA_E_INVAL;
@@ -1018,6 +1201,20 @@ int mlba_batch_graph_kernels(mlba_batch* B, int* n) {
 
 void mlba_batch_destroy(mlba_batch* B) { destroy_batch(B); }
 
+int mlba_batch_tiles(mlba_batch* B, int* frame_shape, int* tile_x, int* tile_y, int* prefetch,
+                     int* how, float* us) {
+  if (!B) return MLBA_E_INVAL;
+  int tx = 0, ty = 0, pf = 0;
+  if (B->levels <= 2) frame_shape_of(B, &tx, &ty, &pf);
+  if (frame_shape) *frame_shape = B->frame_shape;
+  if (tile_x) *tile_x = tx;
+  if (tile_y) *tile_y = ty;
+  if (prefetch) *prefetch = pf;
+  if (how) *how = B->frame_tuned;
+  if (us) *us = B->frame_us;
+  return MLBA_OK;
+}
+
 // ---- single problem ---------------------------------------------------------
 int mlba_create(const double* psf, int p, int n, int bc, int precond, const mlba_opts* opts,
                 mlba_ctx** out) {
@@ -1039,6 +1236,12 @@ int mlba_create(const double* psf, int p, int n, int bc, int precond, const mlba
   c->b = B;
   *out = c;
   return MLBA_OK;
+}
+
+int mlba_tiles(mlba_ctx* c, int* frame_shape, int* tile_x, int* tile_y, int* prefetch, int* how,
+               float* us) {
+  if (!c) return MLBA_E_INVAL;
+  return mlba_batch_tiles(c->b, frame_shape, tile_x, tile_y, prefetch, how, us);
 }
 
 int mlba_set_data(mlba_ctx* c, const void* g, int on_device, double delta) {
@@ -1337,11 +1540,11 @@ int mlba_op_frame(mlba_ctx* c, const void* z_in, const void* u, void* z_out, voi
   if (rc != MLBA_OK) return rc;
   if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
   if (B->dtype == MLBA_F64)
-    launch_frame<double, double>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->stream);
+    launch_frame<double, double>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->frame_shape, B->stream);
   else if (B->z_store == MLBA_BF16)
-    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->stream);
+    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->frame_shape, B->stream);
   else
-    launch_frame<float, float>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->stream);
+    launch_frame<float, float>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->frame_shape, B->stream);
   CK(cudaGetLastError());
   if (grouped) {
     launch_z_layout(dzo, gzo, pd.levels, pd.nf, es, 0, B->stream);

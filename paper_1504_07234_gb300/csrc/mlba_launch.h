@@ -36,6 +36,7 @@ constexpr int VEC_THREADS = 256;
 constexpr int VEC_PER_THREAD = 8;
 constexpr int TR_CAP = 4096;          // complex values held by one transform CTA
 constexpr int FRAME_THREADS = 256;
+constexpr int FRAME_SHAPES = 8;      // tile shapes of the L <= 2 framelet kernel (k_frame.cu)
 constexpr int FRAME_TILE = 32;
 constexpr int SPEC_THREADS = 256;    // alpha_n solve (k_fft.cu)
 constexpr int SPEC_PER_THREAD = 32;
@@ -65,10 +66,11 @@ void launch_spectrum_setup(int transform, int n, int p, int half, int cb, const 
 template <typename T, typename TZ>
 void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, int u_slot,
                   int f_slot, const void* zin, void* zout, double op_mu, size_t smem, int levels,
-                  cudaStream_t s);
+                  int shape, cudaStream_t s);
 template <typename T, typename TZ>
 size_t frame_smem_bytes(int levels);
-int frame_tiles(int nf, int levels);     // CTAs of the frame kernel for one problem
+int frame_tiles(int nf, int levels, int shape);   // CTAs of the frame kernel for one problem
+void frame_shape(int shape, int* tile_x, int* tile_y, int* prefetch);
 bool is_frame_kernel(const void* func);  // func is one of the framelet-update kernels
 int stencil_tiles(int outN);             // CTAs of the stencil for an outN x outN output
 // z layout: grouped (the 8 high bands of a level contiguous per pixel) for

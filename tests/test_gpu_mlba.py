@@ -352,3 +352,38 @@ def test_nonfinite_data_reports_divergence(M, dtype):
     assert st["status"] == -5 and st["stopped"] == 1 and st["iter"] == 0
     assert st["nres"] == 1
     ctx.close()
+
+
+@pytest.mark.parametrize("zs", ["f32", "bf16"])
+def test_tile_shapes_give_identical_iterates(M, zs, tmp_path, monkeypatch):
+    """Every tile shape the autotuner chooses from computes the same values in
+    the same order: forced shapes give bit-identical iterates and statistics,
+    and a tuned batch (measured at create, then read back from the on-disk
+    cache) equals them too."""
+    monkeypatch.setenv("MLBA_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    probs = [small("rect", "bccb", n=70, transform="dft", iters=6),
+             small("reflective", "tikh_ns", n=100, psf=I.psf_disk(3), transform="dct", iters=6, seed=3),
+             small("periodic", "tikh_ns", n=36, psf=I.psf_motion(5, 0.2), iters=6, seed=4)]
+    descs = [dict(psf=p.psf, g=p.g, delta=p.delta, bc=p.bc, precond=p.precond, mu=p.mu,
+                  alpha=p.alpha, transform=p.transform, max_iter=6) for p in probs]
+    runs = []
+    kw = dict(dtype="f32", z_store=zs, levels=2, stop=False, max_iter=6, rect_ns_hybrid=True)
+    cases = [dict(frame_shape=k) for k in range(8)] + [dict(autotune=2), dict(autotune=1)]
+    for extra in cases:
+        b = M.Batch(descs, **kw, **extra)
+        t = b.tiles()
+        if "frame_shape" in extra:
+            assert t["frame_shape"] == extra["frame_shape"] and t["how"] == "forced"
+        elif extra["autotune"] == 2:
+            assert t["how"] == "measured" and t["us"] > 0
+        else:
+            assert t["how"] == "cache"
+        b.iterate(7)
+        runs.append(([b.result(i) for i in range(len(probs))], [b.stats(i) for i in range(len(probs))]))
+        b.close()
+    f0, s0 = runs[0]
+    for fk, sk in runs[1:]:
+        for i in range(len(probs)):
+            assert np.array_equal(f0[i], fk[i]), i
+            assert s0[i] == sk[i], i
+    assert (tmp_path / "tune.txt").read_text().startswith("frame3 ")

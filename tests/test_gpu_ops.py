@@ -126,7 +126,11 @@ def test_frame_tight_frame_on_gpu(M):
                                              ("dft", "motion7", 226), ("dft", "motion7", 197)])
 def test_ns_alpha(M, dtype, transform, psf, n):
     """Also at sizes whose spectrum rows do not tile the per-block element
-    count (300: 151 half-spectrum columns; 200: 200 DCT columns)."""
+    count (300: 151 half-spectrum columns; 200: 200 DCT columns).  FP32 is
+    held to the per-operator 1e-5: the root moves by less than 5e-8 when the
+    oracle's spectrum and eigenvalues are rounded to FP32, so the FP32
+    spectrum is not the limit, and the FP32 candidate sums measured at most
+    1.2e-6 on these cases."""
     h = PSFS[psf]
     ctx = M.Context(h, n, "reflective" if transform == "dct" else "periodic", "tikh_ns",
                     dtype=dtype, transform=transform)
@@ -135,7 +139,7 @@ def test_ns_alpha(M, dtype, transform, psf, n):
     for qn in (0.5, 0.8, 0.95):
         ref = O.ns_alpha(np.abs(pre.forward(r)) ** 2, pre.sigma, qn)
         got = ctx.ns_alpha(r, qn)
-        assert abs(got - ref) <= (1e-10 if dtype == "f64" else 2e-4) * ref, (qn, got, ref)
+        assert abs(got - ref) <= (1e-10 if dtype == "f64" else 1e-5) * ref, (qn, got, ref)
     ctx.close()
 
 
@@ -153,3 +157,31 @@ def test_precond_largest_prime_length(M, transform, psf):
     got = ctx.precond(r, 0.05, "inv")
     assert rel_err(got, pre.inv(r, 0.05)) <= 2e-5
     ctx.close()
+
+
+@pytest.mark.parametrize("zs", ["f32", "bf16"])
+@pytest.mark.parametrize("shape", range(8))
+@pytest.mark.parametrize("levels", [1, 2])
+def test_frame_step_every_tile_shape(M, zs, shape, levels):
+    """Every tile shape of the fused framelet kernel (register queue or ring
+    of z rows filled by bulk asynchronous copies, with per-lane copies where
+    a warp's columns cross the image edge) against the oracle; 150 x 150 with
+    the reflective BC and 97 x 97 rectangular (103 x 103 unknown) put warps on
+    both sides of that split."""
+    for bc, n in (("reflective", 150), ("rect", 97)):
+        ctx = M.Context(PSFS["gauss9"] if bc == "rect" else PSFS["asym3"], n, bc, "none",
+                        dtype="f32", z_store=zs, levels=levels, frame_shape=shape)
+        assert ctx.tiles()["frame_shape"] == shape
+        nf = ctx.nf
+        rng = np.random.default_rng(shape * 10 + levels)
+        z_in = 0.05 * rng.standard_normal((8 * levels + 1, nf, nf))
+        if zs == "bf16":
+            import torch
+            z_in = torch.tensor(z_in, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+        u = 0.1 * rng.standard_normal((nf, nf))
+        zo, f = ctx.frame(z_in, u, 0.03)
+        z_ref = z_in + O.framelet_analysis(u, levels)
+        f_ref = O.framelet_synthesis(O.soft(z_ref, 0.03), levels)
+        assert rel_err(zo.double().cpu().numpy(), z_ref) <= (2e-6 if zs == "f32" else 1e-2)
+        assert rel_err(f.double().cpu().numpy(), f_ref) <= 1e-5
+        ctx.close()
