@@ -616,7 +616,7 @@ def measure_config(M, torch, c, compact=False, iters=None, warm=5):
     zb = 8 if dtype == "f64" else (2 if zst == "bf16" else 4)
     fb = frame_bytes_one(pr, pr.levels, zb, tb)
     ach = fb / (stg["frame"] / 1e3) / 1e9
-    out["roofline"] = {"bound": "hbm", "kernel": "k_frame3" if pr.levels <= 2 else "k_frame",
+    out["roofline"] = {"bound": "hbm", "kernel": "k_frame3" if pr.levels <= 2 else "k_lowpass + k_frame_lev (per level)",
                        "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                        "peak_kind": peak_kind, "algorithmic_bytes_per_launch": fb}
     sb = stage_bytes_one(pr, tb)

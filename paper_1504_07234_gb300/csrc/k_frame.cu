@@ -3,16 +3,18 @@
 //     z_out = z_in + W u,   x = S_mu(z_out),   f = W^T x
 //
 // W is the L-level undecimated transform of Section 6.1 (masks b0, b1, b2,
-// dilated by 2^(l-1) at level l, half-sample reflective boundary).  One CTA
-// owns a 32 x 32 tile of f and of every z band.  Everything is computed on
-// the reflectively extended domain around the tile: u is loaded with a halo
-// of 2(2^L - 1) pixels, z with the halo each band needs (2^l - 1), taking
-// z outside the image from its mirror image with the sign of the band's
-// symmetry (b1 is antisymmetric).  The extension of W u under the same
-// mirroring equals W of the extended u, and S_mu is odd, so every value on
-// the halo is exact and W^T reduces to plain (dilated) convolutions there.
-// z is read once per band from a ping-pong buffer (no in-place race between
-// neighbouring tiles) and written once for the tile interior.
+// dilated by 2^(l-1) at level l, half-sample reflective boundary).  All
+// values are computed on the reflectively extended domain around a tile: z
+// outside the image is its mirror image with the sign of the band's symmetry
+// (b1 is antisymmetric).  The extension of W u under the same mirroring
+// equals W of the extended u, and S_mu is odd, so every value on a halo is
+// exact and W^T reduces to plain (dilated) convolutions there.  z is read from
+// one ping-pong buffer and written to the other (no in-place race between
+// neighbouring tiles), once per owned coefficient.
+//
+// Two kernel families: for L <= 2 one fused row sweep per tile (k_frame3);
+// for L >= 3 a low-pass chain and one row-sweep kernel per level whose halo
+// is only that level's dilation (k_lowpass, k_frame_lev).
 //
 // u comes from (per problem): the full correlation V folded by the BC
 // transpose (A^T t for imposed boundary conditions), V itself (rectangular
@@ -21,220 +23,6 @@
 #include "mlba_launch.h"
 
 namespace mlba {
-
-__device__ __constant__ float c_mask_f[3][3] = {
-    {0.25f, 0.5f, 0.25f},
-    {0.35355339059327376220f, 0.0f, -0.35355339059327376220f},
-    {-0.25f, 0.5f, -0.25f}};
-__device__ __constant__ double c_mask_d[3][3] = {
-    {0.25, 0.5, 0.25},
-    {0.35355339059327376220, 0.0, -0.35355339059327376220},
-    {-0.25, 0.5, -0.25}};
-
-template <typename T> __device__ __forceinline__ T mask(int k, int t);
-template <> __device__ __forceinline__ float mask<float>(int k, int t) { return c_mask_f[k][t]; }
-template <> __device__ __forceinline__ double mask<double>(int k, int t) { return c_mask_d[k][t]; }
-
-template <typename T> __device__ __forceinline__ T soft_thr(T v, T mu) {
-  const T a = fabs(v) - mu;
-  return a > T(0) ? copysign(a, v) : T(0);
-}
-
-__host__ __device__ __forceinline__ int xr(int l) { return (1 << l) - 1; }   // X_l = 2^l - 1
-// radius of the level-l low-pass c_l that the tile needs: X_L + 2^L - 2^l
-__host__ __device__ __forceinline__ int cr(int l, int L) { return xr(L) + (1 << L) - (1 << l); }
-
-template <typename T, typename TZ>
-size_t frame_smem_bytes(int L) {
-  const int TS = FRAME_TILE;
-  size_t e = 0;
-  const int w0 = TS + 2 * cr(0, L), w1 = TS + 2 * cr(L > 1 ? 1 : 0, L);
-  e += (size_t)w0 * w0 + (size_t)w1 * w1;               // c ping-pong
-  e += (size_t)(TS + 2 * xr(L)) * (TS + 2 * xr(L));     // one x band
-  for (int l = 0; l < L; ++l) e += (size_t)(TS + 2 * xr(l)) * (TS + 2 * xr(l));   // s_l
-  return e * sizeof(T);
-}
-
-template <typename T, typename TZ>
-__global__ void __launch_bounds__(FRAME_THREADS)
-k_frame(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-        int u_slot, int f_slot, const void* zin_op, void* zout_op, double op_mu) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int2 item = items[blockIdx.x];
-  const Prob& pd = probs[item.x];
-  const State& st = states[item.x];
-  if (st.stopped) return;
-  const int TS = FRAME_TILE;
-  const int L = pd.levels, nf = pd.nf;
-  const int tilesX = (nf + TS - 1) / TS;
-  const int by0 = (item.y / tilesX) * TS, bx0 = (item.y % tilesX) * TS;
-  const T mu = T(zin_op ? op_mu : pd.mu);
-  const TZ* zin;
-  TZ* zout;
-  if (zin_op) {
-    zin = static_cast<const TZ*>(zin_op);
-    zout = static_cast<TZ*>(zout_op);
-  } else {
-    zin = static_cast<const TZ*>(pd.z[(st.iter - 1) & 1]);
-    zout = static_cast<TZ*>(pd.z[st.iter & 1]);
-  }
-  const size_t plane = (size_t)nf * nf;
-
-  // shared memory carve-up
-  T* cA = reinterpret_cast<T*>(smraw);
-  const int w0 = TS + 2 * cr(0, L);
-  T* cB = cA + w0 * w0;
-  const int w1 = TS + 2 * cr(L > 1 ? 1 : 0, L);
-  T* xb = cB + w1 * w1;
-  const int wx = TS + 2 * xr(L);
-  T* sbuf[MAX_LEVELS];
-  {
-    T* q = xb + wx * wx;
-    for (int l = 0; l < L; ++l) { sbuf[l] = q; q += (TS + 2 * xr(l)) * (TS + 2 * xr(l)); }
-  }
-
-  // 1. u on the extended tile (radius C_0 = 2(2^L - 1))
-  {
-    const int C0 = cr(0, L);
-    int mode;          // 0: V folded, 1: direct nf x nf array
-    const T* src;
-    if (u_slot >= 0) { src = static_cast<const T*>(pd.buf[u_slot]); mode = 1; }
-    else if (!pd.use_adj) { src = static_cast<const T*>(pd.buf[SL_T]); mode = 1; }
-    else if (pd.bc == BC_RECT) { src = static_cast<const T*>(pd.buf[SL_V]); mode = 1; }
-    else { src = static_cast<const T*>(pd.buf[SL_V]); mode = 0; }
-    for (int idx = threadIdx.x; idx < w0 * w0; idx += FRAME_THREADS) {
-      const int ry = idx / w0, rx = idx - ry * w0;
-      int o;
-      const int ay = refl_half(by0 - C0 + ry, nf, &o);
-      const int ax = refl_half(bx0 - C0 + rx, nf, &o);
-      cA[idx] = mode ? src[(size_t)ay * nf + ax] : fold_fetch<T>(pd, src, ay, ax);
-    }
-  }
-  // zero the synthesis accumulators
-  for (int l = 0; l < L; ++l) {
-    const int ws = TS + 2 * xr(l);
-    for (int idx = threadIdx.x; idx < ws * ws; idx += FRAME_THREADS) sbuf[l][idx] = T(0);
-  }
-  __syncthreads();
-
-  // 2. levels, bottom-up: analysis, update, threshold, synthesis of the bands
-  T* cur = cA;
-  T* nxt = cB;
-  int wc = w0, rc = cr(0, L);
-  for (int lev = 1; lev <= L; ++lev) {
-    const int D = 1 << (lev - 1);
-    const int X = xr(lev), wxl = TS + 2 * X;
-    const int Xs = xr(lev - 1), ws = TS + 2 * Xs;
-    T* s = sbuf[lev - 1];
-    const int nb = (lev == L) ? 9 : 8;
-    for (int b = 0; b < nb; ++b) {
-      int bi, bj;
-      if (b == 8) { bi = 0; bj = 0; } else { const int q = b + 1; bi = q / 3; bj = q % 3; }
-      const int band = (b == 8) ? 8 * L : (lev - 1) * 8 + b;
-      const TZ* zi = zin + band * plane;
-      TZ* zo = zout + band * plane;
-      const int off = rc - X;   // offset of the band region inside cur
-      // a. analysis + update + threshold on radius X
-      for (int idx = threadIdx.x; idx < wxl * wxl; idx += FRAME_THREADS) {
-        const int qy = idx / wxl, qx = idx - qy * wxl;
-        T val = T(0);
-#pragma unroll
-        for (int sy = 0; sy < 3; ++sy) {
-          const T my = mask<T>(bi, sy);
-          if (my == T(0)) continue;
-          T rowacc = T(0);
-          const T* crow = cur + (qy + off + (sy - 1) * D) * wc + qx + off;
-#pragma unroll
-          for (int sx = 0; sx < 3; ++sx) {
-            const T mx = mask<T>(bj, sx);
-            if (mx != T(0)) rowacc += mx * crow[(sx - 1) * D];
-          }
-          val += my * rowacc;
-        }
-        const int gy = by0 - X + qy, gx = bx0 - X + qx;
-        int oy, ox;
-        const int zy = refl_half(gy, nf, &oy), zx = refl_half(gx, nf, &ox);
-        const bool neg = ((bi == 1) && oy) != ((bj == 1) && ox);
-        T zo_v = T(ld_z(zi + (size_t)zy * nf + zx));
-        if (neg) zo_v = -zo_v;
-        const T zn = zo_v + val;
-        if (qy >= X && qy < X + TS && qx >= X && qx < X + TS && gy < nf && gx < nf)
-          st_z(zo + (size_t)gy * nf + gx, zn);
-        xb[idx] = soft_thr<T>(zn, mu);
-      }
-      __syncthreads();
-      // b. synthesis of this band into s_{lev-1} on radius Xs (convolution)
-      for (int idx = threadIdx.x; idx < ws * ws; idx += FRAME_THREADS) {
-        const int qy = idx / ws, qx = idx - qy * ws;
-        T acc = T(0);
-#pragma unroll
-        for (int sy = 0; sy < 3; ++sy) {
-          const T my = mask<T>(bi, sy);
-          if (my == T(0)) continue;
-          T rowacc = T(0);
-          const T* xrow = xb + (qy + D - (sy - 1) * D) * wxl + qx + D;
-#pragma unroll
-          for (int sx = 0; sx < 3; ++sx) {
-            const T mx = mask<T>(bj, sx);
-            if (mx != T(0)) rowacc += mx * xrow[-(sx - 1) * D];
-          }
-          acc += my * rowacc;
-        }
-        s[idx] += acc;
-      }
-      __syncthreads();
-    }
-    if (lev < L) {
-      // next low-pass c_lev on its radius
-      const int rn = cr(lev, L), wn = TS + 2 * rn;
-      const int off = rc - rn;
-      for (int idx = threadIdx.x; idx < wn * wn; idx += FRAME_THREADS) {
-        const int qy = idx / wn, qx = idx - qy * wn;
-        T val = T(0);
-#pragma unroll
-        for (int sy = 0; sy < 3; ++sy) {
-          T rowacc = T(0);
-          const T* crow = cur + (qy + off + (sy - 1) * D) * wc + qx + off;
-#pragma unroll
-          for (int sx = 0; sx < 3; ++sx) rowacc += mask<T>(0, sx) * crow[(sx - 1) * D];
-          val += mask<T>(0, sy) * rowacc;
-        }
-        nxt[idx] = val;
-      }
-      __syncthreads();
-      T* tmp = cur; cur = nxt; nxt = tmp;
-      wc = wn; rc = rn;
-    }
-  }
-  // 3. top-down: s_{l-1} += (b0 x b0, dilation 2^(l-1)) * s_l
-  for (int lev = L - 1; lev >= 1; --lev) {
-    const int D = 1 << (lev - 1);
-    const int wl = TS + 2 * xr(lev), ws = TS + 2 * xr(lev - 1);
-    const T* sl = sbuf[lev];
-    T* sd = sbuf[lev - 1];
-    for (int idx = threadIdx.x; idx < ws * ws; idx += FRAME_THREADS) {
-      const int qy = idx / ws, qx = idx - qy * ws;
-      T acc = T(0);
-#pragma unroll
-      for (int sy = 0; sy < 3; ++sy) {
-        T rowacc = T(0);
-        const T* row = sl + (qy + D - (sy - 1) * D) * wl + qx + D;
-#pragma unroll
-        for (int sx = 0; sx < 3; ++sx) rowacc += mask<T>(0, sx) * row[-(sx - 1) * D];
-        acc += mask<T>(0, sy) * rowacc;
-      }
-      sd[idx] += acc;
-    }
-    __syncthreads();
-  }
-  // 4. f = s_0 on the tile
-  T* f = static_cast<T*>(pd.buf[f_slot]);
-  for (int idx = threadIdx.x; idx < TS * TS; idx += FRAME_THREADS) {
-    const int qy = idx / TS, qx = idx - qy * TS;
-    const int gy = by0 + qy, gx = bx0 + qx;
-    if (gy < nf && gx < nf) f[(size_t)gy * nf + gx] = sbuf[0][idx];
-  }
-}
 
 // ---------------------------------------------------------------------------
 // asynchronous global -> shared copies (one thread, 4 or 8 bytes) and their groups
@@ -766,12 +554,301 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
   }
 }
 
-int frame_tiles(int nf, int levels, int shape) {
-  if (levels <= 2) {
-    const int ty = F3_SEG * F3_SHAPES[shape].nwr;
-    return ((nf + F3_TX - 1) / F3_TX) * ((nf + ty - 1) / ty);
+
+// ---------------------------------------------------------------------------
+// L >= 3: the step level by level (the paper's experiments use L = 4).
+//
+//   c_0 = u,  c_l = (b0 x b0)_{2^(l-1)} c_{l-1}         (k_lowpass, kept in HBM)
+//   level l = L, L-1, ..., 1 (k_frame_lev, dilation D = 2^(l-1)):
+//     z_l <- z_l + W_l c_{l-1},  x = S_mu(z_l),
+//     s_{l-1} = sum over the level's bands of B_ij^T x_ij  +  (b0 x b0)^T s_l
+//   (the top level's nine bands include the final low-pass and it has no
+//   s_L term), f = s_0.  s_1 .. s_{L-1} live in HBM too, so each kernel needs
+//   a halo of its own dilation only (the fused single-pass form needs
+//   2 (2^L - 1) = 30 pixels per side at L = 4).
+
+// u as the level-1 kernel and the first low-pass read it: the op entry
+// point's slot, t (Algorithm 4 forms), V (rectangular A) or the BC fold of V
+// materialised in U before the sweep
+template <typename T>
+__device__ __forceinline__ const T* frame_u(const Prob& pd, int u_slot) {
+  if (u_slot >= 0) return static_cast<const T*>(pd.buf[u_slot]);
+  if (!pd.use_adj) return static_cast<const T*>(pd.buf[SL_T]);
+  if (pd.bc == BC_RECT) return static_cast<const T*>(pd.buf[SL_V]);
+  return static_cast<const T*>(pd.buf[SL_U]);
+}
+
+// c_lev = (b0 x b0) with dilation 2^(lev-1) applied to c_{lev-1}, half-sample
+// mirror at the border; LP_PER outputs per thread, item.y = block of the plane
+template <typename T>
+__global__ void __launch_bounds__(LP_THREADS)
+k_lowpass(const Prob* __restrict__ probs, const State* __restrict__ states,
+          const int2* __restrict__ items, int lev, int u_slot) {
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  if (states[item.x].stopped) return;
+  const int nf = pd.nf;
+  const size_t plane = (size_t)nf * nf;
+  const int D = 1 << (lev - 1);
+  const T* in = (lev == 1) ? frame_u<T>(pd, u_slot)
+                           : static_cast<const T*>(pd.lp) + (size_t)(lev - 2) * plane;
+  T* out = static_cast<T*>(pd.lp) + (size_t)(lev - 1) * plane;
+  const size_t base = (size_t)item.y * LP_THREADS * LP_PER;
+#pragma unroll
+  for (int k = 0; k < LP_PER; ++k) {
+    const size_t e = base + threadIdx.x + (size_t)k * LP_THREADS;
+    if (e >= plane) break;
+    const int y = (int)(e / nf), x = (int)(e - (size_t)y * nf);
+    bool par;
+    const int ym = f3_refl(y - D, nf, &par), yp = f3_refl(y + D, nf, &par);
+    const int xm = f3_refl(x - D, nf, &par), xp = f3_refl(x + D, nf, &par);
+    auto row = [&](int r) {
+      const T* q = in + (size_t)r * nf;
+      return T(0.25) * (q[xm] + q[xp]) + T(0.5) * q[x];
+    };
+    out[e] = T(0.25) * (row(ym) + row(yp)) + T(0.5) * row(y);
   }
-  return ((nf + FRAME_TILE - 1) / FRAME_TILE) * ((nf + FRAME_TILE - 1) / FRAME_TILE);
+}
+
+// Level kernel geometry: a CTA of LV_NWR warps owns OUTW columns x 32 LV_NWR
+// rows of s_{l-1}; lane k of a warp owns the coefficient column tx0 - D + k
+// (every lane computes coefficients, lanes D .. 31 - D produce output).
+template <int D>
+struct LV {
+  static constexpr int OUTW = 32 - 2 * D;                  // output columns of a tile
+  static constexpr int TY = 32 * LV_NWR;
+  static constexpr int CW = 32 + 2 * D, CH = TY + 4 * D;   // c tile: cols tx0 - 2D.., rows ty0 - 2D..
+  static constexpr int SW = 32, SH = TY + 2 * D;           // s tile: cols tx0 - D.., rows ty0 - D..
+  static constexpr int PR = 2 * D + 1;                     // synthesis ring rows
+};
+template <typename T, int D>
+__host__ __device__ constexpr size_t lev_smem_bytes() {
+  return ((size_t)LV<D>::CW * LV<D>::CH + (size_t)LV<D>::SW * LV<D>::SH +
+          (size_t)LV_NWR * LV<D>::PR * 3 * 32) * sizeof(T);
+}
+
+// One level of the step.  The warp sweeps down its rows: the horizontal
+// analysis of the three rows y - D, y, y + D of c_{l-1} (shared-memory tile),
+// the vertical masks, the update of z (register queue, PF rows ahead), the
+// threshold, and the vertical synthesis scattered into a ring of 2D + 1 rows
+// (shared memory, one column per lane); row y - D then has all its
+// contributions and is combined horizontally by warp shuffles at +-D and, for
+// l < L, with (b0 x b0)^T s_l from the s tile.
+template <typename T, typename TZ, int D, bool TOP>
+__global__ void __launch_bounds__(32 * LV_NWR)
+k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
+            const int2* __restrict__ items, int lev, int u_slot, int f_slot, const void* zin_op,
+            void* zout_op, double op_mu) {
+  using G = LV<D>;
+  constexpr int PF = 2;
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int K0 = TOP ? 0 : 1;            // band k = 3 j + i; (0,0) only at the top level
+  constexpr int NB = 9 - K0;
+  constexpr int NV = 8 * (int)sizeof(TZ) / 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  const State& st = states[item.x];
+  if (st.stopped) return;
+  const int nf = pd.nf, L = pd.levels;
+  const int plane = nf * nf;                 // nbands nf^2 < 2^31 is checked at set-up
+  const int tilesX = (nf + G::OUTW - 1) / G::OUTW;
+  const int ty0 = (item.y / tilesX) * G::TY, tx0 = (item.y % tilesX) * G::OUTW;
+  const T mu = T(zin_op ? op_mu : pd.mu);
+  const TZ* zin;
+  TZ* zout;
+  if (zin_op) {
+    zin = static_cast<const TZ*>(zin_op);
+    zout = static_cast<TZ*>(zout_op);
+  } else {
+    zin = static_cast<const TZ*>(pd.z[(st.iter - 1) & 1]);
+    zout = static_cast<TZ*>(pd.z[st.iter & 1]);
+  }
+  T* sc = reinterpret_cast<T*>(smraw);       // c_{l-1} on rows ty0 - 2D.., cols tx0 - 2D..
+  T* ss = sc + G::CW * G::CH;                // s_l on rows ty0 - D.., cols tx0 - D..
+  T* sring = ss + G::SW * G::SH;             // per-warp synthesis rings
+  {
+    const T* cin = (lev == 1) ? frame_u<T>(pd, u_slot)
+                              : static_cast<const T*>(pd.lp) + (size_t)(lev - 2) * plane;
+    constexpr int NT = 32 * LV_NWR;
+    for (int idx = threadIdx.x; idx < G::CW * G::CH; idx += NT) {
+      const int ry = idx / G::CW, rx = idx - ry * G::CW;
+      bool par;
+      const int ay = f3_refl(ty0 - 2 * D + ry, nf, &par), ax = f3_refl(tx0 - 2 * D + rx, nf, &par);
+      const T* g = cin + ((size_t)ay * nf + ax);
+      if (sizeof(T) == 8) cp_async_8(sc + idx, g); else cp_async_4(sc + idx, g);
+    }
+    if (!TOP) {
+      const T* sin = static_cast<const T*>(pd.sy) + (size_t)(lev - 1) * plane;
+      for (int idx = threadIdx.x; idx < G::SW * G::SH; idx += NT) {
+        const int ry = idx / G::SW, rx = idx - ry * G::SW;
+        bool par;
+        const int ay = f3_refl(ty0 - D + ry, nf, &par), ax = f3_refl(tx0 - D + rx, nf, &par);
+        const T* g = sin + ((size_t)ay * nf + ax);
+        if (sizeof(T) == 8) cp_async_8(ss + idx, g); else cp_async_4(ss + idx, g);
+      }
+    }
+    cp_commit();
+    for (int idx = threadIdx.x; idx < LV_NWR * G::PR * 3 * 32; idx += NT) sring[idx] = T(0);
+    cp_wait<0>();
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg_lo = ty0 + 32 * w, seg_hi = seg_lo + 32;
+  if (seg_lo >= nf) return;                  // no barrier follows
+  const T s2q = T(0.35355339059327376220);   // sqrt(2) / 4
+  const int x = tx0 - D + lane;              // this lane's coefficient column
+  bool pcx;
+  const int zc = f3_refl(x, nf, &pcx);
+  const T scol = pcx ? T(-1) : T(1);
+  const bool own_c = lane >= D && lane < 32 - D && x < nf;
+  const int yc0 = seg_lo - D, yc1 = seg_hi + D;
+  T* ring = sring + w * (G::PR * 3 * 32) + lane;    // (row slot k, j) at ring[(3 k + j) 32]
+  const T* ccol = sc + (lane + D);                  // c tile column of x
+  const int crow0 = ty0 - 2 * D;
+  const int gbase = (lev - 1) * 8 * plane, lbase = 8 * L * plane;
+  T* dst = (lev == 1) ? static_cast<T*>(pd.buf[f_slot])
+                      : static_cast<T*>(pd.sy) + (size_t)(lev - 2) * plane;
+  ZGroup<TZ> zq[PF];
+  TZ zl[PF];
+  auto zload = [&](int y, int k) {
+    bool par;
+    const int q = f3_refl(y, nf, &par) * nf + zc;
+    const uint4* src = reinterpret_cast<const uint4*>(zin + (gbase + 8 * q));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) zq[k].v[v] = src[v];
+    if (TOP) zl[k] = zin[lbase + q];
+  };
+#pragma unroll
+  for (int k = 0; k < PF; ++k) zload(yc0 + k, k);
+  // ring slots of rows y - D, y, y + D (advanced by one per row)
+  int k0 = 0, k1 = D, k2 = 2 * D;
+  auto step = [&](int y, int kq) {
+    // horizontal analysis of rows y - D, y, y + D: h[s][j]
+    T h[3][3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const T* r = ccol + (y + (s - 1) * D - crow0) * G::CW;
+      const T cm = r[-D], c0 = r[0], cp = r[D];
+      const T sp = cm + cp;
+      h[s][0] = T(0.25) * sp + T(0.5) * c0;
+      h[s][1] = s2q * (cm - cp);
+      h[s][2] = T(0.5) * c0 - T(0.25) * sp;
+    }
+    bool pry;
+    const int zro = f3_refl(y, nf, &pry) * nf;
+    const T srow = pry ? T(-1) : T(1);
+    const T s11 = srow * scol;
+    const bool own = own_c && y >= seg_lo && y < seg_hi && y < nf;
+    const int zwo = zro + zc;
+    ZGroup<TZ> zo;
+    TZ zlo = TZ(0.0f);
+    T p0[3] = {T(0), T(0), T(0)}, p1[3] = {T(0), T(0), T(0)}, p2[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int k = K0 + b, i = k % 3, j = k / 3;
+      const T bi0 = (i == 0) ? T(0.25) : (i == 1 ? s2q : T(-0.25));
+      const T bi1 = (i == 1) ? T(0) : T(0.5);
+      const T bi2 = (i == 0) ? T(0.25) : (i == 1 ? -s2q : T(-0.25));
+      T a = bi0 * h[0][j] + bi2 * h[2][j];
+      if (i != 1) a += bi1 * h[1][j];
+      const int pos = 3 * i + j - 1;
+      const T zv = (i == 0 && j == 0) ? T(ld_z(&zl[kq])) : T(ld_z(&zq[kq].e[pos]));
+      const T zn = (i == 1 && j == 1) ? fma(zv, s11, a)
+                 : (i == 1) ? fma(zv, srow, a) : (j == 1) ? fma(zv, scol, a) : zv + a;
+      if (i == 0 && j == 0) zlo = to_z(zn, (TZ*)nullptr);
+      else zo.e[pos] = to_z(zn, (TZ*)nullptr);
+      const T xv = zn - fmin(fmax(zn, -mu), mu);     // S_mu
+      p0[j] += bi0 * xv;
+      if (i != 1) p1[j] += bi1 * xv;
+      p2[j] += bi2 * xv;
+    }
+    if (own) {
+      uint4* dz = reinterpret_cast<uint4*>(zout + (gbase + 8 * zwo));
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dz[v] = zo.v[v];
+      if (TOP) zout[lbase + zwo] = zlo;
+    }
+    if (y + PF < yc1) zload(y + PF, kq);
+    // scatter into rows y - D, y, y + D; row y - D is then complete
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      ring[(3 * k1 + j) * 32] += p1[j];
+      ring[(3 * k2 + j) * 32] += p2[j];
+    }
+    T P[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      P[j] = ring[(3 * k0 + j) * 32] + p0[j];
+      ring[(3 * k0 + j) * 32] = T(0);         // the slot becomes row y + D + 1
+    }
+    const int r = y - D;
+    const T A = T(0.25) * P[0] + s2q * P[1] - T(0.25) * P[2];
+    const T B = T(0.5) * (P[0] + P[2]);
+    const T C = T(0.25) * P[0] - s2q * P[1] - T(0.25) * P[2];
+    T out = B + __shfl_down_sync(FULL, A, D) + __shfl_up_sync(FULL, C, D);
+    if (r >= seg_lo && own_c && r < nf) {
+      if (!TOP) {
+        // (b0 x b0)^T s_l at (r, x): rows r - D, r, r + D, columns x - D, x, x + D
+        const T* sr = ss + (r - (ty0 - D)) * G::SW + lane;
+        auto hs = [&](const T* q) { return T(0.25) * (q[-D] + q[D]) + T(0.5) * q[0]; };
+        out += T(0.25) * (hs(sr - D * G::SW) + hs(sr + D * G::SW)) + T(0.5) * hs(sr);
+      }
+      dst[(size_t)r * nf + x] = out;
+    }
+    k0 = (k0 + 1 == G::PR) ? 0 : k0 + 1;
+    k1 = (k1 + 1 == G::PR) ? 0 : k1 + 1;
+    k2 = (k2 + 1 == G::PR) ? 0 : k2 + 1;
+  };
+#pragma unroll 1
+  for (int y = yc0; y < yc1; y += PF) {
+#pragma unroll
+    for (int k = 0; k < PF; ++k)
+      if (y + k < yc1) step(y + k, k);
+  }
+}
+
+int lev_tiles(int nf, int lev) {
+  const int D = 1 << (lev - 1);
+  const int outw = 32 - 2 * D, ty = 32 * LV_NWR;
+  return ((nf + outw - 1) / outw) * ((nf + ty - 1) / ty);
+}
+int lowpass_blocks(int nf) {
+  const size_t plane = (size_t)nf * nf;
+  return (int)((plane + LP_THREADS * LP_PER - 1) / (LP_THREADS * LP_PER));
+}
+
+template <typename T, typename TZ>
+void launch_frame_levels(const Prob* probs, State* states, const int2* items, const int* sec,
+                         int levels, int u_slot, int f_slot, const void* zin, void* zout,
+                         double op_mu, cudaStream_t s) {
+  // sec: (offset, count) of the fold, low-pass and level-L .. level-1 sections
+  if (u_slot < 0 && sec[1] > 0) launch_vec<T>(VEC_FOLD, probs, states, items + sec[0], sec[1], 0, s);
+  if (sec[3] > 0)
+    for (int l = 1; l < levels; ++l)
+      k_lowpass<T><<<sec[3], LP_THREADS, 0, s>>>(probs, states, items + sec[2], l, u_slot);
+  for (int k = 0; k < levels; ++k) {
+    const int lev = levels - k, off = sec[4 + 2 * k], cnt = sec[5 + 2 * k];
+    if (cnt <= 0) continue;
+    const int2* it = items + off;
+    const bool top = lev == levels;
+#define LEVK(DD, TT) \
+  k_frame_lev<T, TZ, DD, TT><<<cnt, 32 * LV_NWR, lev_smem_bytes<T, DD>(), s>>>( \
+      probs, states, it, lev, u_slot, f_slot, zin, zout, op_mu)
+    switch (lev) {
+      case 1: LEVK(1, false); break;
+      case 2: LEVK(2, false); break;
+      case 3: if (top) LEVK(4, true); else LEVK(4, false); break;
+      default: if (top) LEVK(8, true); else LEVK(8, false); break;
+    }
+#undef LEVK
+  }
+}
+
+int frame_tiles(int nf, int levels, int shape) {
+  const int ty = F3_SEG * F3_SHAPES[shape].nwr;
+  (void)levels;
+  return ((nf + F3_TX - 1) / F3_TX) * ((nf + ty - 1) / ty);
 }
 
 void frame_shape(int shape, int* tile_x, int* tile_y, int* prefetch) {
@@ -793,7 +870,7 @@ __global__ void k_zlayout(E* __restrict__ dst, const E* __restrict__ src, int nb
   }
 }
 
-bool z_grouped(int levels) { return levels <= 2; }
+bool z_grouped(int levels) { (void)levels; return true; }
 
 size_t z_grouped_index(int b, size_t q, int nbands, size_t plane) {
   return (b < nbands - 1) ? (size_t)(b / 8) * 8 * plane + 8 * q + (b % 8) : (size_t)b * plane + q;
@@ -871,8 +948,8 @@ void launch_frame3_shape(int shape, const Prob* probs, State* states, const int2
 }
 
 template <typename T, typename TZ>
-void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, int u_slot,
-                  int f_slot, const void* zin, void* zout, double op_mu, size_t smem, int levels,
+void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, const int* sec,
+                  int u_slot, int f_slot, const void* zin, void* zout, double op_mu, int levels,
                   int shape, cudaStream_t s) {
   if (nitems <= 0) return;
   if (levels == 1)
@@ -880,11 +957,32 @@ void launch_frame(const Prob* probs, State* states, const int2* items, int nitem
   else if (levels == 2)
     launch_frame3_shape<T, TZ, 2>(shape, probs, states, items, nitems, u_slot, f_slot, zin, zout, op_mu, s);
   else
-    k_frame<T, TZ><<<nitems, FRAME_THREADS, smem, s>>>(probs, states, items, u_slot, f_slot, zin,
-                                                         zout, op_mu);
+    launch_frame_levels<T, TZ>(probs, states, items, sec, levels, u_slot, f_slot, zin, zout, op_mu, s);
 }
+
+// the level kernels of one precision, for every (dilation, top) pair used
 template <typename T, typename TZ>
-cudaError_t frame_set_smem(size_t bytes) {
+const void* const* lev_kernels() {
+  static const void* const k[] = {
+      (const void*)k_frame_lev<T, TZ, 1, false>, (const void*)k_frame_lev<T, TZ, 2, false>,
+      (const void*)k_frame_lev<T, TZ, 4, false>, (const void*)k_frame_lev<T, TZ, 8, false>,
+      (const void*)k_frame_lev<T, TZ, 4, true>,  (const void*)k_frame_lev<T, TZ, 8, true>,
+      (const void*)k_lowpass<T>};
+  return k;
+}
+template <typename T>
+size_t lev_kernel_smem(int k) {
+  switch (k) {
+    case 0: return lev_smem_bytes<T, 1>();
+    case 1: return lev_smem_bytes<T, 2>();
+    case 2: case 4: return lev_smem_bytes<T, 4>();
+    case 3: case 5: return lev_smem_bytes<T, 8>();
+    default: return 0;
+  }
+}
+
+template <typename T, typename TZ>
+cudaError_t frame_set_smem() {
   for (int sh = 0; sh < FRAME_SHAPES; ++sh) {
     cudaError_t e = cudaFuncSetAttribute(frame3_kernel<T, TZ, 1>(sh),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -894,8 +992,13 @@ cudaError_t frame_set_smem(size_t bytes) {
                              (int)frame3_smem<T, TZ, 2>(sh));
     if (e != cudaSuccess) return e;
   }
-  return cudaFuncSetAttribute(k_frame<T, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+  for (int k = 0; k < 6; ++k) {
+    const cudaError_t e = cudaFuncSetAttribute(lev_kernels<T, TZ>()[k],
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)lev_kernel_smem<T>(k));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 bool is_frame_kernel(const void* func) {
@@ -906,16 +1009,17 @@ bool is_frame_kernel(const void* func) {
     for (const void* f : k)
       if (f == func) return true;
   }
-  return func == (const void*)k_frame<float, float> || func == (const void*)k_frame<float, __nv_bfloat16> ||
-         func == (const void*)k_frame<double, double>;
+  for (int k = 0; k < 7; ++k)
+    if (func == lev_kernels<float, float>()[k] || func == lev_kernels<float, __nv_bfloat16>()[k] ||
+        func == lev_kernels<double, double>()[k])
+      return true;
+  return false;
 }
 
 #define INST(T, TZ)                                                                          \
-  template size_t frame_smem_bytes<T, TZ>(int);                                              \
-  template void launch_frame<T, TZ>(const Prob*, State*, const int2*, int, int, int,          \
-                                    const void*, void*, double, size_t, int, int,             \
-                                    cudaStream_t);                                            \
-  template cudaError_t frame_set_smem<T, TZ>(size_t);
+  template void launch_frame<T, TZ>(const Prob*, State*, const int2*, int, const int*, int,   \
+                                    int, const void*, void*, double, int, int, cudaStream_t); \
+  template cudaError_t frame_set_smem<T, TZ>();
 INST(float, float)
 INST(float, __nv_bfloat16)
 INST(double, double)

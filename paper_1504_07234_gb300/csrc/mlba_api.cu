@@ -47,6 +47,7 @@ struct HostProb {
 struct ItemList {
   int2* dev = nullptr;
   int count = 0;
+  int sec[2 * FRAME_SECTIONS] = {0};   // framelet list at L >= 3: (offset, count) per section
 };
 
 // The launches of one step over a set of problems.
@@ -57,9 +58,23 @@ struct StepLists {
 };
 struct StepItems {
   std::vector<int2> blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
-      cols_kry, vec_kry, vec_kry_bc, frame;
+      cols_kry, vec_kry, vec_kry_bc;
+  std::vector<int2> frame[FRAME_SECTIONS];   // see add_frame_items
   int any_krylov = 0, any_spec = 0, any_ns = 0, pcg_max = 5;
 };
+
+// Framelet launches of problem i: levels <= 2, the tiles of the fused sweep
+// (section 0); levels >= 3, the BC fold of the correlation (section 0, BC
+// problems that apply A^T), the low-pass chain (section 1) and the level
+// kernels of level L .. 1 (sections 2 ..).
+void add_frame_items(const Prob& pd, int i, int levels, int shape,
+                     std::vector<int2> (&fs)[FRAME_SECTIONS]) {
+  auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
+  if (levels <= 2) { add(fs[0], frame_tiles(pd.nf, levels, shape)); return; }
+  if (pd.use_adj && pd.bc != BC_RECT) add(fs[0], pd.nblk_vec);
+  add(fs[1], lowpass_blocks(pd.nf));
+  for (int k = 0; k < levels; ++k) add(fs[2 + k], lev_tiles(pd.nf, levels - k));
+}
 
 // parts of a step: a = residual and stop rule, then the preconditioner;
 // b = A^T and the framelet update
@@ -81,7 +96,7 @@ struct mlba_batch {
   ItemList blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry, cols_kry,
       vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all;
   std::vector<int2*> allocs;
-  size_t smem_stencil = 0, smem_fft = 0, smem_frame = 0;
+  size_t smem_stencil = 0, smem_fft = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool has_data = false;
@@ -195,6 +210,20 @@ int build_list(mlba_batch* B, ItemList& L, const std::vector<int2>& items) {
   return MLBA_OK;
 }
 
+// the framelet list: one section (levels <= 2) or the sections concatenated
+int build_frame_list(mlba_batch* B, ItemList& L, const std::vector<int2> (&fs)[FRAME_SECTIONS],
+                     int levels) {
+  if (levels <= 2) return build_list(B, L, fs[0]);
+  std::vector<int2> all;
+  for (int k = 0; k < 2 + levels; ++k) {
+    L.sec[2 * k] = (int)all.size();
+    L.sec[2 * k + 1] = (int)fs[k].size();
+    all.insert(all.end(), fs[k].begin(), fs[k].end());
+  }
+  const int rc = build_list(B, L, all);
+  return rc;
+}
+
 State initial_state(const Prob& pd) {
   State s;
   std::memset(&s, 0, sizeof(s));
@@ -252,8 +281,8 @@ void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
     // a6: full correlation of t (A^T up to the BC fold)
     launch_stencil<T>(ST_CORR, P, S, L.corr.dev, L.corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
     // a1: z += W u, x = S_mu(z), f = W^T x
-    launch_frame<T, TZ>(P, S, L.frame.dev, L.frame.count, -1, SL_F, nullptr, nullptr, 0.0,
-                        B->smem_frame, B->levels, B->frame_shape, s);
+    launch_frame<T, TZ>(P, S, L.frame.dev, L.frame.count, L.frame.sec, -1, SL_F, nullptr, nullptr,
+                        0.0, B->levels, B->frame_shape, s);
   }
 }
 
@@ -275,10 +304,10 @@ StepLists all_lists(const mlba_batch* B) {
 }
 
 // the launches of one step of problem i (kinds as in the whole-batch lists)
-void collect_step(const Prob& pd, int i, StepItems& V) {
+void collect_step(const Prob& pd, int i, int levels, int shape, StepItems& V) {
   auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
   add(V.blur, pd.nblk_blur);
-  add(V.frame, pd.nblk_frame);
+  add_frame_items(pd, i, levels, shape, V.frame);
   if (pd.use_adj) add(V.corr, pd.nblk_corr);
   const bool specp = pd.transform != TR_NONE;
   if (pd.precond == P_KRYLOV) {
@@ -361,7 +390,7 @@ int build_split(mlba_batch* B) {
   double w[2] = {0.0, 0.0};
   for (int i : order) { const int g = w[1] < w[0] ? 1 : 0; grp[i] = g; w[g] += work(i); }
   StepItems V[2];
-  for (int i = 0; i < count; ++i) collect_step(B->hp[i].pd, i, V[grp[i]]);
+  for (int i = 0; i < count; ++i) collect_step(B->hp[i].pd, i, B->levels, B->frame_shape, V[grp[i]]);
   int rc = MLBA_OK;
   for (int g = 0; g < 2; ++g) {
     StepLists& L = B->grp[g];
@@ -372,7 +401,7 @@ int build_split(mlba_batch* B) {
     rc |= build_list(B, L.cols_ns, v.cols_ns); rc |= build_list(B, L.spec, v.spec);
     rc |= build_list(B, L.rows_kry, v.rows_kry); rc |= build_list(B, L.cols_kry, v.cols_kry);
     rc |= build_list(B, L.vec_kry, v.vec_kry); rc |= build_list(B, L.vec_kry_bc, v.vec_kry_bc);
-    rc |= build_list(B, L.frame, v.frame);
+    rc |= build_frame_list(B, L.frame, v.frame, B->levels);
     L.any_krylov = v.any_krylov; L.any_spec = v.any_spec; L.any_ns = v.any_ns;
     L.pcg_max = B->hp[0].pd.pcg_max;
   }
@@ -392,20 +421,14 @@ int set_smem_attrs(mlba_batch* B) {
   if (B->dtype == MLBA_F64) {
     CK(stencil_set_smem<double>(B->smem_stencil));
     CK(fft_set_smem<double>(B->smem_fft));
-    CK((frame_set_smem<double, double>(B->smem_frame)));
+    CK((frame_set_smem<double, double>()));
   } else {
     CK(stencil_set_smem<float>(B->smem_stencil));
     CK(fft_set_smem<float>(B->smem_fft));
-    if (B->z_store == MLBA_BF16) CK((frame_set_smem<float, __nv_bfloat16>(B->smem_frame)));
-    else CK((frame_set_smem<float, float>(B->smem_frame)));
+    if (B->z_store == MLBA_BF16) CK((frame_set_smem<float, __nv_bfloat16>()));
+    else CK((frame_set_smem<float, float>()));
   }
   return MLBA_OK;
-}
-
-size_t frame_smem(int dtype, int zs, int L) {
-  if (dtype == MLBA_F64) return frame_smem_bytes<double, double>(L);
-  if (zs == MLBA_BF16) return frame_smem_bytes<float, __nv_bfloat16>(L);
-  return frame_smem_bytes<float, float>(L);
 }
 
 void frame_shape_of(const mlba_batch* B, int* tx, int* ty, int* pf) {
@@ -511,7 +534,6 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   // launch geometry
   pd.nblk_blur = stencil_tiles(n);
   pd.nblk_corr = stencil_tiles(pd.ne);
-  pd.nblk_frame = frame_tiles(pd.nf, o.levels, 0);   // shape chosen at create
   // the frame kernel indexes a z array (all bands) with 32-bit offsets
   if ((double)pd.nbands * pd.nf * pd.nf >= 2147483647.0) return MLBA_E_UNSUPPORTED;
   const int cap = TR_CAP / n;                          // transforms per CTA
@@ -661,14 +683,14 @@ void tune_store(const std::string& key, int shape, float us) {
 
 void launch_frame_any(mlba_batch* B, const int2* items, int count, int shape, cudaStream_t s) {
   if (B->dtype == MLBA_F64)
-    launch_frame<double, double>(B->d_probs, B->d_states, items, count, -1, SL_F, nullptr, nullptr,
-                                 0.0, B->smem_frame, B->levels, shape, s);
+    launch_frame<double, double>(B->d_probs, B->d_states, items, count, nullptr, -1, SL_F, nullptr,
+                                 nullptr, 0.0, B->levels, shape, s);
   else if (B->z_store == MLBA_BF16)
-    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_states, items, count, -1, SL_F, nullptr,
-                                       nullptr, 0.0, B->smem_frame, B->levels, shape, s);
+    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_states, items, count, nullptr, -1, SL_F,
+                                       nullptr, nullptr, 0.0, B->levels, shape, s);
   else
-    launch_frame<float, float>(B->d_probs, B->d_states, items, count, -1, SL_F, nullptr, nullptr,
-                               0.0, B->smem_frame, B->levels, shape, s);
+    launch_frame<float, float>(B->d_probs, B->d_states, items, count, nullptr, -1, SL_F, nullptr,
+                               nullptr, 0.0, B->levels, shape, s);
 }
 
 std::vector<int2> frame_items(const mlba_batch* B, int shape) {
@@ -796,6 +818,8 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         nspec * ts * (pd.transform == TR_DCT ? 1 : 2),   // lam
         nspec * ts,                            // |lambda|^2 in T precision
         (pd.ns ? nspec : 1) * ts,              // 4-NS weighted power
+        (pd.levels >= 3 ? (size_t)(pd.levels - 1) * nf2 : 1) * ts,   // low-pass chain (L >= 3)
+        (pd.levels >= 3 ? (size_t)(pd.levels - 1) * nf2 : 1) * ts,   // synthesis partials
         spec ? (size_t)pd.n * 2 * ts : ts,     // tw
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
         (size_t)pd.nruns * 16, 2 * (size_t)pd.nrw * ts,   // tap runs and weights (both orders)
@@ -821,6 +845,8 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     pd.lam = base + of[k++];
     pd.w = base + of[k++];
     pd.pw = base + of[k++];
+    pd.lp = base + of[k++];
+    pd.sy = base + of[k++];
     pd.tw = base + of[k++];
     pd.dtw = base + of[k++];
     pd.tap_runs = reinterpret_cast<int4*>(base + of[k++]);
@@ -874,13 +900,12 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   CK(cudaMemcpy(B->d_states, st_h.data(), count * sizeof(State), cudaMemcpyHostToDevice));
   // ---- item lists
   std::vector<int2> blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
-      cols_kry, vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all;
+      cols_kry, vec_kry, vec_kry_bc, corr_all, rows_all, cols_all, spec_all, vec_all;
   size_t smem_st = 0, smem_fft = 0;
   for (int i = 0; i < count; ++i) {
     const Prob& pd = B->hp[i].pd;
     auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
     add(blur, pd.nblk_blur);
-    add(frame, pd.nblk_frame);
     add(corr_all, pd.nblk_corr);
     add(vec_all, pd.nblk_vec);
     if (pd.use_adj) add(corr, pd.nblk_corr);
@@ -913,7 +938,6 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   }
   B->smem_stencil = std::max<size_t>(smem_st, 16);
   B->smem_fft = std::max<size_t>(smem_fft, 16);
-  B->smem_frame = frame_smem(o.dtype, o.z_store, o.levels);
   int rc = MLBA_OK;
   rc |= build_list(B, B->blur, blur); rc |= build_list(B, B->corr, corr);
   rc |= build_list(B, B->corr_kry, corr_kry); rc |= build_list(B, B->blur_kry, blur_kry);
@@ -921,22 +945,18 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   rc |= build_list(B, B->cols_ns, cols_ns); rc |= build_list(B, B->spec, spec);
   rc |= build_list(B, B->rows_kry, rows_kry); rc |= build_list(B, B->cols_kry, cols_kry);
   rc |= build_list(B, B->vec_kry, vec_kry); rc |= build_list(B, B->vec_kry_bc, vec_kry_bc);
-  rc |= build_list(B, B->frame, frame); rc |= build_list(B, B->corr_all, corr_all);
+  rc |= build_list(B, B->corr_all, corr_all);
   rc |= build_list(B, B->rows_all, rows_all); rc |= build_list(B, B->cols_all, cols_all);
   rc |= build_list(B, B->spec_all, spec_all); rc |= build_list(B, B->vec_all, vec_all);
   if (rc != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
   if (set_smem_attrs(B) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
-  // ---- framelet tile shape (the frame list above is for shape 0)
+  // ---- framelet tile shape, then the framelet list in that shape
   {
     const int trc = choose_frame_shape(B, o);
     if (trc != MLBA_OK) { destroy_batch(B); return trc; }
-    if (B->frame_shape != 0) {
-      const std::vector<int2> fr = frame_items(B, B->frame_shape);
-      for (HostProb& hp : B->hp) hp.pd.nblk_frame = frame_tiles(hp.pd.nf, B->levels, B->frame_shape);
-      ItemList L;
-      if (build_list(B, L, fr) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
-      B->frame = L;      // the shape-0 list stays in B->allocs and is freed at destroy
-    }
+    std::vector<int2> fs[FRAME_SECTIONS];
+    for (int i = 0; i < count; ++i) add_frame_items(B->hp[i].pd, i, B->levels, B->frame_shape, fs);
+    if (build_frame_list(B, B->frame, fs, B->levels) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
   }
   // ---- capture one step
   if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -1147,7 +1167,7 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
         launch_rows_inv<double>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
       }
       if (stage == 3) launch_stencil<double>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
-      if (stage == 4) launch_frame<double, double>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, B->frame_shape, s);
+      if (stage == 4) launch_frame<double, double>(P, S, B->frame.dev, B->frame.count, B->frame.sec, -1, SL_F, nullptr, nullptr, 0.0, B->levels, B->frame_shape, s);
     } else {
       if (stage == 1) launch_stencil<float>(ST_FWD_RESID, P, S, B->blur.dev, B->blur.count, SL_F, SL_R, SL_G, 0, B->smem_stencil, s);
       if (stage == 2) {
@@ -1160,9 +1180,9 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
       if (stage == 3) launch_stencil<float>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
       if (stage == 4) {
         if (B->z_store == MLBA_BF16)
-          launch_frame<float, __nv_bfloat16>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, B->frame_shape, s);
+          launch_frame<float, __nv_bfloat16>(P, S, B->frame.dev, B->frame.count, B->frame.sec, -1, SL_F, nullptr, nullptr, 0.0, B->levels, B->frame_shape, s);
         else
-          launch_frame<float, float>(P, S, B->frame.dev, B->frame.count, -1, SL_F, nullptr, nullptr, 0.0, B->smem_frame, B->levels, B->frame_shape, s);
+          launch_frame<float, float>(P, S, B->frame.dev, B->frame.count, B->frame.sec, -1, SL_F, nullptr, nullptr, 0.0, B->levels, B->frame_shape, s);
       }
     }
   }
@@ -1540,11 +1560,11 @@ int mlba_op_frame(mlba_ctx* c, const void* z_in, const void* u, void* z_out, voi
   if (rc != MLBA_OK) return rc;
   if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
   if (B->dtype == MLBA_F64)
-    launch_frame<double, double>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->frame_shape, B->stream);
+    launch_frame<double, double>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, B->frame.sec, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->levels, B->frame_shape, B->stream);
   else if (B->z_store == MLBA_BF16)
-    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->frame_shape, B->stream);
+    launch_frame<float, __nv_bfloat16>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, B->frame.sec, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->levels, B->frame_shape, B->stream);
   else
-    launch_frame<float, float>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->smem_frame, B->levels, B->frame_shape, B->stream);
+    launch_frame<float, float>(B->d_probs, B->d_opstates, B->frame.dev, B->frame.count, B->frame.sec, SL_AUX0, SL_AUX1, kzi, kzo, mu, B->levels, B->frame_shape, B->stream);
   CK(cudaGetLastError());
   if (grouped) {
     launch_z_layout(dzo, gzo, pd.levels, pd.nf, es, 0, B->stream);

@@ -33,7 +33,7 @@ enum Slot {
 };
 
 constexpr int MAX_STAGES = 24;
-constexpr int MAX_LEVELS = 6;
+constexpr int MAX_LEVELS = 4;
 
 // Constant description of one problem (device copy lives in a table).
 struct Prob {
@@ -50,7 +50,7 @@ struct Prob {
   int nr16, r2, nr3, nr5;   // the same plan: radix-16 passes, one 8/4/2 pass, 3s, 5s,
   int nrany;                // then the prime factors above 5 (direct-sum passes)
   // per-list block counts (reductions need them)
-  int nblk_blur, nblk_corr, nblk_frame, nblk_rows, nblk_cols, nblk_spec, nblk_vec;
+  int nblk_blur, nblk_corr, nblk_rows, nblk_cols, nblk_spec, nblk_vec;
   int row_g, col_g;  // transforms per CTA in the row / column passes
   int cb;            // spectrum column block: col_g complex columns (DFT) or
                      // 2 col_g real columns (DCT); block j holds columns
@@ -64,6 +64,8 @@ struct Prob {
                      // spectral value, T, blocked like S (0 on padding); written by
                      // the bracketing pass, read by the Halley passes
   void* lam;         // spectrum of C (real for DCT, complex half for DFT), T, blocked
+  void* lp;          // L >= 3: low-pass chain c_1 .. c_{L-1} (nf x nf planes, T)
+  void* sy;          // L >= 3: synthesis partials s_1 .. s_{L-1} (nf x nf planes, T)
   void* tw;          // exp(-2 pi i k/n), k < n   (T2)
   void* dtw;         // exp(-i pi k/(2n)), k < n  (T2)
   int4* tap_runs;     // per nonzero PSF column b: (b, lo, hi, offset of H[lo..hi][b] in tap_w)

@@ -35,9 +35,10 @@ constexpr int STENCIL_THREADS = 128;
 constexpr int VEC_THREADS = 256;
 constexpr int VEC_PER_THREAD = 8;
 constexpr int TR_CAP = 4096;          // complex values held by one transform CTA
-constexpr int FRAME_THREADS = 256;
 constexpr int FRAME_SHAPES = 8;      // tile shapes of the L <= 2 framelet kernel (k_frame.cu)
-constexpr int FRAME_TILE = 32;
+constexpr int LV_NWR = 2;            // warps per CTA of the per-level framelet kernel (L >= 3)
+constexpr int LP_THREADS = 256, LP_PER = 4;   // low-pass chain kernel (L >= 3)
+constexpr int FRAME_SECTIONS = 2 + 4;         // fold, low-pass, up to four levels
 constexpr int SPEC_THREADS = 256;    // alpha_n solve (k_fft.cu)
 constexpr int SPEC_PER_THREAD = 32;
 constexpr int SPEC_SUMS = 33;        // block sums of the bracketing pass (2 x 16 candidates + 1)
@@ -63,13 +64,18 @@ void launch_spec(const Prob* probs, State* states, const int2* items, int nitems
 void launch_spectrum_setup(int transform, int n, int p, int half, int cb, const double* q_dev,
                            const double* tab_dev, void* lam, void* sigT, int is_double,
                            cudaStream_t s);
+// The framelet step.  levels <= 2: one launch of the fused sweep over
+// `items` in tile shape `shape`.  levels >= 3: the item list holds sections
+// whose (offset, count) pairs `sec` gives: the BC fold of the correlation
+// (VEC_FOLD items, skipped when u_slot >= 0), the low-pass chain (blocks of
+// LP_THREADS * LP_PER values), then the level kernels of level L, L-1, ..., 1.
 template <typename T, typename TZ>
-void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, int u_slot,
-                  int f_slot, const void* zin, void* zout, double op_mu, size_t smem, int levels,
+void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, const int* sec,
+                  int u_slot, int f_slot, const void* zin, void* zout, double op_mu, int levels,
                   int shape, cudaStream_t s);
-template <typename T, typename TZ>
-size_t frame_smem_bytes(int levels);
-int frame_tiles(int nf, int levels, int shape);   // CTAs of the frame kernel for one problem
+int frame_tiles(int nf, int levels, int shape);   // CTAs of the fused sweep for one problem (L <= 2)
+int lev_tiles(int nf, int lev);                   // CTAs of one level kernel (L >= 3)
+int lowpass_blocks(int nf);                       // CTAs of one low-pass launch (L >= 3)
 void frame_shape(int shape, int* tile_x, int* tile_y, int* prefetch);
 bool is_frame_kernel(const void* func);  // func is one of the framelet-update kernels
 int stencil_tiles(int outN);             // CTAs of the stencil for an outN x outN output
@@ -80,7 +86,7 @@ size_t z_grouped_index(int b, size_t q, int nbands, size_t plane);
 void launch_z_layout(void* dst, const void* src, int levels, int nf, int elem_bytes,
                      int to_grouped, cudaStream_t s);
 template <typename T, typename TZ>
-cudaError_t frame_set_smem(size_t bytes);
+cudaError_t frame_set_smem();
 template <typename T>
 cudaError_t stencil_set_smem(size_t bytes);
 template <typename T>
