@@ -29,7 +29,7 @@ import numpy as np
 import scipy.fft as sfft
 import scipy.sparse as sp
 
-BCS = ("zero", "periodic", "reflective", "rect")
+BCS = ("zero", "periodic", "reflective", "rect", "antireflective")
 PRECONDS = ("none", "bccb", "krylov", "sym", "tikh", "tikh_ns")
 
 
@@ -63,8 +63,29 @@ def bc_index(e: np.ndarray, n: int, bc: str) -> np.ndarray:
     raise ValueError(bc)
 
 
+def antireflect_1d(f: np.ndarray, c: int, axis: int) -> np.ndarray:
+    """Antireflective pad by c along one axis (Section 2.2): outside the left
+    edge F(1 - i) = 2 F(1) - F(i + 1), outside the right edge
+    F(n + i) = 2 F(n) - F(n - i), i = 1..c (1-based, as printed).  Needs
+    c <= n - 1."""
+    f = np.moveaxis(f, axis, 0)
+    n = f.shape[0]
+    if c > n - 1:
+        raise ValueError("antireflective pad wider than the image")
+    out = np.empty((n + 2 * c,) + f.shape[1:])
+    out[c:c + n] = f
+    for i in range(1, c + 1):
+        out[c - i] = 2.0 * f[0] - f[i]
+        out[c + n - 1 + i] = 2.0 * f[n - 1] - f[n - 1 - i]
+    return np.moveaxis(out, 0, axis)
+
+
 def extend(f: np.ndarray, c: int, bc: str) -> np.ndarray:
-    """Pad the n x n image by c pixels on every side as in Table 1."""
+    """Pad the n x n image by c pixels on every side as in Table 1; the
+    antireflective pad of Section 2.2 antireflects the rows first and then
+    the columns of the result, which gives the printed corner formulas."""
+    if bc == "antireflective":
+        return antireflect_1d(antireflect_1d(f, c, 0), c, 1)
     n = f.shape[0]
     idx = bc_index(np.arange(-c, n + c), n, bc)
     ok = idx >= 0
@@ -100,6 +121,13 @@ def blur(f: np.ndarray, h: np.ndarray, bc: str) -> np.ndarray:
             if h[a, b] != 0.0:
                 out += h[a, b] * fe[p - 1 - a:p - 1 - a + n, p - 1 - b:p - 1 - b + n]
     return out
+
+
+def reblur(t: np.ndarray, h: np.ndarray, bc: str) -> np.ndarray:
+    """A' t, the reblurring matrix of Section 2.2: the same boundary condition
+    imposed on the PSF rotated by 180 degrees.  With antireflective BCs it
+    replaces A^T; with zero and periodic BCs A' = A^T."""
+    return blur(t, h[::-1, ::-1], bc)
 
 
 def blur_adjoint(t: np.ndarray, h: np.ndarray, bc: str) -> np.ndarray:
@@ -398,14 +426,15 @@ def choose_transform(h: np.ndarray, precond: str, transform: str, bc: str = "rec
 
     Algorithm 3 always uses the DCT of the symmetrised PSF.  An explicit
     choice wins otherwise.  'auto': with periodic BCs the periodic C equals A
-    and the DFT is used; otherwise the DCT when the PSF is quadrantally
-    symmetric (the reflective C approximates A better, Section 4.1) and the
-    DFT when it is not."""
+    and the DFT is used; with antireflective BCs the BCCB C (DFT), as the
+    paper's Examples 3 and 4 do for Algorithms 1 and 4; otherwise the DCT when
+    the PSF is quadrantally symmetric (the reflective C approximates A better,
+    Section 4.1) and the DFT when it is not."""
     if precond == "sym":
         return "dct"
     if transform in ("dft", "dct"):
         return transform
-    if bc == "periodic":
+    if bc in ("periodic", "antireflective"):
         return "dft"
     return "dct" if quadrantally_symmetric(h) else "dft"
 
@@ -425,7 +454,11 @@ def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
                  form z += W A^T (CC^T + alpha_n I)^{-1} r with alpha_n floored
                  at ``alpha``, which must satisfy Eq. condconvalg1 (reading c14).
 
-    with x = S_mu(z), f = W^T x, z^0 = x^0 = 0 and r^n = g - A f^n.
+    with x = S_mu(z), f = W^T x, z^0 = x^0 = 0 and r^n = g - A f^n.  With
+    antireflective BCs every A^T is the reblurring matrix A' (Section 2.2);
+    Algorithm 2 (the paper finds it of no use there, Example 4) and
+    Algorithm 3 (whose Q would need the antireflective transform) are not
+    defined for them here.
     Stopping (Eq. discrpr, Eq. Alg4_rev_12): the first n > 0 with
     ||r^n|| <= gamma delta (Algorithms 1-4), or the first n >= 0 with
     ||r^n|| <= tau delta (4-NS) (readings c4, c16).  With ``stop=False``
@@ -443,6 +476,9 @@ def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
     nf = n + p - 1 if bc == "rect" else n
     if precond in ("tikh", "tikh_ns") and bc == "rect" and not (precond == "tikh_ns" and rect_ns_hybrid):
         raise ValueError("Algorithm 4 needs a square A (Section 5)")
+    if bc == "antireflective" and precond in ("krylov", "sym"):
+        raise ValueError("Algorithms 2 and 3 are not defined for antireflective BCs here")
+    adj = (lambda v: reblur(v, h, bc)) if bc == "antireflective" else (lambda v: blur_adjoint(v, h, bc))
     ns = precond == "tikh_ns"
     tr = choose_transform(h, precond, transform, bc)
     pre = None
@@ -471,14 +507,14 @@ def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
         if it >= max_iter:
             break
         if precond == "none":
-            u = blur_adjoint(r, h, bc)
+            u = adj(r)
         elif precond in ("bccb", "sym"):
-            u = blur_adjoint(pre.inv(r, alpha), h, bc)
+            u = adj(pre.inv(r, alpha))
         elif precond == "krylov":
             t, beta = pcg(r, lambda v: blur(blur_adjoint(v, h, bc), h, bc),
                           lambda v: pre.inv(v, alpha), alpha, pcg_tol, pcg_max)
             betas.append(beta)
-            u = blur_adjoint(t, h, bc)
+            u = adj(t)
         elif precond == "tikh":
             u = pre.tikh(r, alpha)
         else:  # tikh_ns
@@ -490,7 +526,7 @@ def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
                     alpha_n = max(alpha_n, alpha)
             alphas.append(alpha_n)
             if bc == "rect":
-                u = blur_adjoint(pre.inv(r, alpha_n), h, bc)
+                u = adj(pre.inv(r, alpha_n))
             else:
                 u = pre.tikh(r, alpha_n)
         z = z + framelet_analysis(u, levels)

@@ -132,3 +132,29 @@ def test_rect_rejects_alg4():
     g, h, delta = small_problem(n=10)
     with pytest.raises(ValueError):
         O.mlba(g, h, delta, "rect", "tikh", 0.01)
+
+
+def test_first_iterate_dense_antireflective():
+    """Antireflective BCs (Section 2.2): z^1 = W A' P g and the residual of
+    iterate 1 with the dense A (NumPy odd-reflection pad) and the dense
+    reblurring matrix A' (the same pad on the 180-degree rotated PSF), P the
+    BCCB preconditioner (Eq. Alg1)."""
+    h = np.array([[0.0, 0.1, 0.05], [0.2, 0.3, 0.0], [0.15, 0.1, 0.1]])
+    n = 7
+    rng = np.random.default_rng(9)
+    g = rng.random((n, n))
+    alpha, mu, levels = 0.1, 0.02, 1
+    out = O.mlba(g, h, 1.0, "antireflective", "bccb", mu=mu, alpha=alpha, levels=levels,
+                 max_iter=1, stop=False, transform="dft")
+    a = dense_blur_matrix(h, n, "antireflective")
+    a_re = dense_blur_matrix(h[::-1, ::-1], n, "antireflective")
+    cper = dense_blur_matrix(h, n, "periodic")
+    pmat = np.linalg.inv(cper @ cper.T + alpha * np.eye(n * n))
+    w = dense_w(n, levels)
+    z1 = w @ (a_re @ (pmat @ g.ravel()))
+    f1 = w.T @ O.soft(z1, mu)
+    np.testing.assert_allclose(out["z"].ravel(), z1, atol=1e-12)
+    np.testing.assert_allclose(out["f"].ravel(), f1, atol=1e-12)
+    assert abs(out["resnorms"][1] - np.linalg.norm(g.ravel() - a @ f1)) < 1e-12
+    with pytest.raises(ValueError):
+        O.mlba(g, h, 1.0, "antireflective", "krylov", mu=mu)

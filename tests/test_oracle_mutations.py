@@ -80,3 +80,16 @@ def test_unpreconditioned_pcg_stop_rule_is_caught(monkeypatch):
     monkeypatch.setattr(O, "pcg", pcg_plain)
     with pytest.raises(AssertionError):
         TP.test_pcg_stops_on_preconditioned_relative_residual()
+
+
+def test_reflective_pad_instead_of_antireflective_is_caught(monkeypatch):
+    """Planting the reflective pad in place of the antireflective one must
+    fail the linear-preservation pin."""
+    import test_oracle_blur as TB
+    good = O.extend
+
+    def wrong(f, c, bc):
+        return good(f, c, "reflective" if bc == "antireflective" else bc)
+    monkeypatch.setattr(O, "extend", wrong)
+    with pytest.raises(AssertionError):
+        TB.test_antireflective_preserves_linear_images()
