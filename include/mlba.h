@@ -58,7 +58,12 @@ enum mlba_bc {                 /* Section 2, Table 1 */
   MLBA_BC_ZERO = 0,            /* Dirichlet: zero outside the field of view */
   MLBA_BC_PERIODIC = 1,        /* A is BCCB */
   MLBA_BC_REFLECTIVE = 2,      /* fliplr / flipud mirror (Neumann) */
-  MLBA_RECT = 3                /* rectangular n^2 x m^2 valid operator, Eq. Arect */
+  MLBA_RECT = 3,               /* rectangular n^2 x m^2 valid operator, Eq. Arect */
+  MLBA_BC_ANTIREFLECTIVE = 4   /* 2 F(edge) - F(mirror) pad, corners antireflected row then
+                                  column (Section 2.2); A^T is replaced by the reblurring
+                                  matrix A' (the same BCs on the PSF rotated by 180 degrees).
+                                  Algorithms 1, 4 and 4-NS and P = I; not Algorithm 2 (the
+                                  paper finds it of no use there) nor Algorithm 3. */
 };
 
 enum mlba_precond {            /* Sections 3-5 */
@@ -199,7 +204,8 @@ const char* mlba_strerror(int status);
  * All arrays are in the context dtype; on_device as above. */
 /* out = A f   (f: N_f x N_f, out: n x n)  Section 2, Table 1, Eq. Arect. */
 int mlba_op_blur(mlba_ctx* ctx, const void* f, void* out, int on_device);
-/* out = A^T t (t: n x n, out: N_f x N_f)  exact transpose of mlba_op_blur. */
+/* out = A^T t (t: n x n, out: N_f x N_f)  exact transpose of mlba_op_blur;
+ * for antireflective BCs the reblurring matrix A' t (Section 2.2). */
 int mlba_op_blur_adjoint(mlba_ctx* ctx, const void* t, void* out, int on_device);
 /* out = (CC^T + alpha I)^{-1} r (which = 0, Eq. Alg1/Alg3) or
  * C^T (CC^T + alpha I)^{-1} r (which = 1, Eq. Alg4); r, out: n x n.

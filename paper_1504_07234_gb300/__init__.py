@@ -21,7 +21,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmlba.so")
 
-BC = {"zero": 0, "periodic": 1, "reflective": 2, "rect": 3}
+BC = {"zero": 0, "periodic": 1, "reflective": 2, "rect": 3, "antireflective": 4}
 PRECOND = {"none": 0, "bccb": 1, "krylov": 2, "sym": 3, "tikh": 4, "tikh_ns": 5}
 TRANSFORM = {"auto": 0, "dft": 1, "dct": 2}
 DTYPE = {"f32": 0, "f64": 1, "bf16": 2}

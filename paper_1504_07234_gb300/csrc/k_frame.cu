@@ -479,6 +479,7 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
     if (u_slot >= 0) { src = static_cast<const T*>(pd.buf[u_slot]); mode = 1; }
     else if (!pd.use_adj) { src = static_cast<const T*>(pd.buf[SL_T]); mode = 1; }
     else if (pd.bc == BC_RECT) { src = static_cast<const T*>(pd.buf[SL_V]); mode = 1; }
+    else if (pd.bc == BC_AR) { src = static_cast<const T*>(pd.buf[SL_U]); mode = 1; }   // A' t
     else { src = static_cast<const T*>(pd.buf[SL_V]); mode = 0; }
     const bool interior = ty0 - C0 >= 0 && tx0 - C0 >= 0 && ty0 + F3_TY + C0 <= nf &&
                           tx0 + F3_TX + C0 <= nf;
@@ -568,8 +569,8 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
 //   2 (2^L - 1) = 30 pixels per side at L = 4).
 
 // u as the level-1 kernel and the first low-pass read it: the op entry
-// point's slot, t (Algorithm 4 forms), V (rectangular A) or the BC fold of V
-// materialised in U before the sweep
+// point's slot, t (Algorithm 4 forms), V (rectangular A), or U: the BC fold
+// of V materialised before the sweep, or A' t for antireflective BCs
 template <typename T>
 __device__ __forceinline__ const T* frame_u(const Prob& pd, int u_slot) {
   if (u_slot >= 0) return static_cast<const T*>(pd.buf[u_slot]);

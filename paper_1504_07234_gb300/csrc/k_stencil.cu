@@ -10,6 +10,9 @@
 // the (n+p-1)^2 extended domain (t zero outside), which is A^T t for the
 // rectangular operator; for a boundary condition the fold of V by the
 // transpose of the padding gives A^T t (done where u is consumed).
+// Antireflective BCs (Section 2.2) pad by 2 F(edge) - F(mirror) instead of a
+// copy, and A^T is replaced by the reblurring matrix A': the correlation of
+// the antireflectively padded t on the n x n domain.
 #include "mlba_internal.cuh"
 #include "mlba_launch.h"
 
@@ -233,10 +236,14 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   State& st = states[item.x];
   if (skip(st, pcg)) return;
 
-  constexpr bool CORR = (MODE == ST_CORR);
+  // CORR: correlation weights and run offsets (the full correlation and the
+  // reblurring A' of antireflective BCs); ZPAD: the full correlation of the
+  // zero-padded t on the (n+p-1)^2 domain
+  constexpr bool CORR = (MODE == ST_CORR || MODE == ST_REBLUR);
+  constexpr bool ZPAD = (MODE == ST_CORR);
   constexpr int NT = STENCIL_THREADS;
   const int n = pd.n, p = pd.p, c = pd.c;
-  const int outN = CORR ? pd.ne : n;
+  const int outN = ZPAD ? pd.ne : n;
   const int tilesX = (outN + ST_TX - 1) / ST_TX;
   const int ty0 = (item.y / tilesX) * ST_TY, tx0 = (item.y % tilesX) * ST_TX;
   const int RY = ST_TY + p - 1, RX = ST_TX + p - 1;
@@ -255,6 +262,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   // correlation; A^T p for the PCG product: V for rectangular A, U otherwise)
   if (src_slot < 0)
     src_slot = CORR ? (pd.precond == P_NONE ? SL_R : SL_T) : (pd.bc == BC_RECT ? SL_V : SL_U);
+  if (MODE == ST_REBLUR && dst_slot < 0) dst_slot = SL_U;
   const T* src = static_cast<const T*>(pd.buf[src_slot]);
   // weights in the order the windows consume them: the forward stencil runs
   // over the reversed PSF
@@ -272,8 +280,8 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
     for (int k = threadIdx.x; k < pd.nrw; k += NT) s_w[k] = tw[k];
   }
   // input region
-  const int oy0 = CORR ? ty0 - 2 * c : ty0 - c;
-  const int ox0 = CORR ? tx0 - 2 * c : tx0 - c;
+  const int oy0 = ZPAD ? ty0 - 2 * c : ty0 - c;
+  const int ox0 = ZPAD ? tx0 - 2 * c : tx0 - c;
   // asynchronous copies straight into shared memory (no registers held, all
   // of a thread's copies in flight together); positions outside the source
   // are zero-filled by a copy of 0 source bytes.  One warp per row, lanes
@@ -288,21 +296,48 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   int xs = 0;
   {
     const int lane = threadIdx.x & 31;
-    const int pitch = (!CORR && pd.bc == BC_RECT) ? pd.nf : n;
-    const int sx0 = (!CORR && pd.bc == BC_RECT) ? ox0 + c : ox0;
+    const int pitch = (!ZPAD && pd.bc == BC_RECT) ? pd.nf : n;
+    const int sx0 = (!ZPAD && pd.bc == BC_RECT) ? ox0 + c : ox0;
     const bool colin = sx0 >= 0 && sx0 + RX <= pitch;
+    // antireflective BCs: outside the image a value is a combination of up to
+    // four pixels (Section 2.2), so tiles that reach outside take the
+    // per-element path below
+    const bool ar = !ZPAD && pd.bc == BC_AR;
+    const bool ar_out = ar && !(colin && oy0 >= 0 && oy0 + RY <= n);
     // chunk in elements: 16 bytes when the pitch keeps the rows aligned alike,
     // 8 bytes (FP32) for an even pitch, 0: element by element
     const int c16 = 16 / (int)sizeof(T);
     const int ce = !colin ? 0 : (pitch % c16 == 0 ? c16 : (sizeof(T) == 4 && pitch % 2 == 0 ? 2 : 0));
-    if (ce > 0) {
+    if (ar_out) {
+      // 1-D antireflection of an extended index: up to two (index, weight)
+      // terms; 0 terms past the reach of any output of the image
+      auto ar_terms = [&](int e, int (&ix)[2], T (&wt)[2]) -> int {
+        if (e >= 0 && e < n) { ix[0] = e; wt[0] = T(1); return 1; }
+        const int k = e < 0 ? -e : e - (n - 1);          // distance outside the edge
+        if (k > n - 1) return 0;
+        ix[0] = e < 0 ? 0 : n - 1;
+        ix[1] = e < 0 ? k : n - 1 - k;
+        wt[0] = T(2); wt[1] = T(-1);
+        return 2;
+      };
+      for (int idx = threadIdx.x; idx < RY * RX; idx += NT) {
+        const int ry = idx / RX, rx = idx - ry * RX;
+        int iy[2], ix[2];
+        T wy[2], wx[2];
+        const int ny = ar_terms(oy0 + ry, iy, wy), nx = ar_terms(ox0 + rx, ix, wx);
+        T v = T(0);
+        for (int a = 0; a < ny; ++a)
+          for (int b = 0; b < nx; ++b) v += wy[a] * wx[b] * src[(size_t)iy[a] * n + ix[b]];
+        s_in[ry * RP + rx] = v;
+      }
+    } else if (ce > 0) {
       xs = sx0 % ce;
       const int gs = sx0 - xs;
       const int nch = (xs + RX + ce - 1) / ce;      // <= 65 (8-byte chunks of <= 129 values): three passes
       for (int ry = threadIdx.x >> 5; ry < RY; ry += NT / 32) {
         const int ey = oy0 + ry;
         int sy;
-        if (CORR) sy = (ey >= 0 && ey < n) ? ey : -1;
+        if (ZPAD) sy = (ey >= 0 && ey < n) ? ey : -1;
         else if (pd.bc == BC_RECT) sy = (ey + c >= 0 && ey + c < pd.nf) ? ey + c : -1;
         else sy = bc_map_near(ey, n, pd.bc);
         const T* row = src + (size_t)(sy < 0 ? 0 : sy) * pitch;
@@ -325,7 +360,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
       for (int ry = threadIdx.x >> 5; ry < RY; ry += NT / 32) {
         const int ey = oy0 + ry;
         int sy;
-        if (CORR) sy = (ey >= 0 && ey < n) ? ey : -1;
+        if (ZPAD) sy = (ey >= 0 && ey < n) ? ey : -1;
         else if (pd.bc == BC_RECT) sy = (ey + c >= 0 && ey + c < pd.nf) ? ey + c : -1;
         else sy = bc_map_near(ey, n, pd.bc);
         const T* row = src + (size_t)(sy < 0 ? 0 : sy) * pitch;
@@ -335,7 +370,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
           if (rx < RX) {
             const int ex = ox0 + rx;
             int sx;
-            if (CORR) sx = (ex >= 0 && ex < n) ? ex : -1;
+            if (ZPAD) sx = (ex >= 0 && ex < n) ? ex : -1;
             else if (pd.bc == BC_RECT) sx = (ex + c >= 0 && ex + c < pd.nf) ? ex + c : -1;
             else sx = bc_map_near(ex, n, pd.bc);
             const bool ok = sy >= 0 && sx >= 0;
@@ -555,6 +590,7 @@ void launch_stencil(int mode, const Prob* probs, State* states, const int2* item
     case ST_FWD_RESID: k_stencil<T, ST_FWD_RESID><<<g, b, smem, s>>>(probs, states, items, src, dst, aux, pcg); break;
     case ST_FWD_STORE: k_stencil<T, ST_FWD_STORE><<<g, b, smem, s>>>(probs, states, items, src, dst, aux, pcg); break;
     case ST_FWD_PCGQ: k_stencil<T, ST_FWD_PCGQ><<<g, b, smem, s>>>(probs, states, items, src, dst, aux, pcg); break;
+    case ST_REBLUR: k_stencil<T, ST_REBLUR><<<g, b, smem, s>>>(probs, states, items, src, dst, aux, pcg); break;
     default: k_stencil<T, ST_CORR><<<g, b, smem, s>>>(probs, states, items, src, dst, aux, pcg); break;
   }
 }
@@ -567,6 +603,8 @@ cudaError_t stencil_set_smem(size_t bytes) {
   e = cudaFuncSetAttribute(k_stencil<T, ST_FWD_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_stencil<T, ST_FWD_PCGQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_stencil<T, ST_REBLUR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_stencil<T, ST_CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }

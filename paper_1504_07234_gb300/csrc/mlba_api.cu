@@ -52,13 +52,13 @@ struct ItemList {
 
 // The launches of one step over a set of problems.
 struct StepLists {
-  ItemList blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry, cols_kry,
-      vec_kry, vec_kry_bc, frame;
+  ItemList blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
+      cols_kry, vec_kry, vec_kry_bc, frame;
   int any_krylov = 0, any_spec = 0, any_ns = 0, pcg_max = 5;
 };
 struct StepItems {
-  std::vector<int2> blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
-      cols_kry, vec_kry, vec_kry_bc;
+  std::vector<int2> blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec,
+      rows_kry, cols_kry, vec_kry, vec_kry_bc;
   std::vector<int2> frame[FRAME_SECTIONS];   // see add_frame_items
   int any_krylov = 0, any_spec = 0, any_ns = 0, pcg_max = 5;
 };
@@ -71,7 +71,7 @@ void add_frame_items(const Prob& pd, int i, int levels, int shape,
                      std::vector<int2> (&fs)[FRAME_SECTIONS]) {
   auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
   if (levels <= 2) { add(fs[0], frame_tiles(pd.nf, levels, shape)); return; }
-  if (pd.use_adj && pd.bc != BC_RECT) add(fs[0], pd.nblk_vec);
+  if (pd.use_adj && pd.bc != BC_RECT && pd.bc != BC_AR) add(fs[0], pd.nblk_vec);
   add(fs[1], lowpass_blocks(pd.nf));
   for (int k = 0; k < levels; ++k) add(fs[2 + k], lev_tiles(pd.nf, levels - k));
 }
@@ -93,8 +93,8 @@ struct mlba_batch {
   unsigned char* arena = nullptr;
   size_t arena_bytes = 0;
   // item lists
-  ItemList blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry, cols_kry,
-      vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all;
+  ItemList blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
+      cols_kry, vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all;
   std::vector<int2*> allocs;
   size_t smem_stencil = 0, smem_fft = 0;
   cudaGraph_t graph = nullptr;
@@ -278,8 +278,10 @@ void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
     }
   }
   if (part & PART_B) {
-    // a6: full correlation of t (A^T up to the BC fold)
+    // a6: full correlation of t (A^T up to the BC fold); antireflective BCs:
+    // the reblurring A' t into U
     launch_stencil<T>(ST_CORR, P, S, L.corr.dev, L.corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
+    launch_stencil<T>(ST_REBLUR, P, S, L.reblur.dev, L.reblur.count, -1, -1, SL_U, 0, B->smem_stencil, s);
     // a1: z += W u, x = S_mu(z), f = W^T x
     launch_frame<T, TZ>(P, S, L.frame.dev, L.frame.count, L.frame.sec, -1, SL_F, nullptr, nullptr,
                         0.0, B->levels, B->frame_shape, s);
@@ -294,7 +296,7 @@ void enqueue_dispatch(mlba_batch* B, const StepLists& L, int part, cudaStream_t 
 
 StepLists all_lists(const mlba_batch* B) {
   StepLists L;
-  L.blur = B->blur; L.corr = B->corr; L.corr_kry = B->corr_kry; L.blur_kry = B->blur_kry;
+  L.blur = B->blur; L.corr = B->corr; L.reblur = B->reblur; L.corr_kry = B->corr_kry; L.blur_kry = B->blur_kry;
   L.rows_spec = B->rows_spec; L.cols_stat = B->cols_stat; L.cols_ns = B->cols_ns; L.spec = B->spec;
   L.rows_kry = B->rows_kry; L.cols_kry = B->cols_kry; L.vec_kry = B->vec_kry;
   L.vec_kry_bc = B->vec_kry_bc; L.frame = B->frame;
@@ -308,7 +310,10 @@ void collect_step(const Prob& pd, int i, int levels, int shape, StepItems& V) {
   auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
   add(V.blur, pd.nblk_blur);
   add_frame_items(pd, i, levels, shape, V.frame);
-  if (pd.use_adj) add(V.corr, pd.nblk_corr);
+  if (pd.use_adj) {
+    if (pd.bc == BC_AR) add(V.reblur, pd.nblk_blur);
+    else add(V.corr, pd.nblk_corr);
+  }
   const bool specp = pd.transform != TR_NONE;
   if (pd.precond == P_KRYLOV) {
     add(V.corr_kry, pd.nblk_corr); add(V.blur_kry, pd.nblk_blur); add(V.rows_kry, pd.nblk_rows);
@@ -396,6 +401,7 @@ int build_split(mlba_batch* B) {
     StepLists& L = B->grp[g];
     const StepItems& v = V[g];
     rc |= build_list(B, L.blur, v.blur); rc |= build_list(B, L.corr, v.corr);
+    rc |= build_list(B, L.reblur, v.reblur);
     rc |= build_list(B, L.corr_kry, v.corr_kry); rc |= build_list(B, L.blur_kry, v.blur_kry);
     rc |= build_list(B, L.rows_spec, v.rows_spec); rc |= build_list(B, L.cols_stat, v.cols_stat);
     rc |= build_list(B, L.cols_ns, v.cols_ns); rc |= build_list(B, L.spec, v.spec);
@@ -458,7 +464,11 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   const int p = in.p, n = in.n;
   if (!in.psf || p < 1 || (p % 2) == 0 || n < p || n < 2) return MLBA_E_INVAL;
   if (p > MLBA_MAX_P) return MLBA_E_UNSUPPORTED;
-  if (in.bc < 0 || in.bc > 3 || in.precond < 0 || in.precond > 5) return MLBA_E_INVAL;
+  if (in.bc < 0 || in.bc > 4 || in.precond < 0 || in.precond > 5) return MLBA_E_INVAL;
+  // antireflective BCs: Algorithm 2 is of no use there (Example 4) and
+  // Algorithm 3's Q needs the antireflective transform
+  if (in.bc == MLBA_BC_ANTIREFLECTIVE && (in.precond == MLBA_P_KRYLOV || in.precond == MLBA_P_SYM))
+    return MLBA_E_INVAL;
   if (o.levels < 1 || o.levels > 4) return MLBA_E_INVAL;
   if (!(in.delta >= 0.0) || !(in.mu >= 0.0)) return MLBA_E_INVAL;
   const bool ns = in.precond == MLBA_P_TIKH_NS;
@@ -498,7 +508,9 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
     if (tr == MLBA_TR_DCT && !sym) return MLBA_E_INVAL;
     // AUTO: periodic A is its own BCCB matrix (DFT); otherwise the reflective
     // (DCT) matrix for a quadrantally symmetric PSF, the periodic one if not
-    const int autotr = (in.bc == MLBA_BC_PERIODIC) ? TR_DFT : (sym ? TR_DCT : TR_DFT);
+    // (antireflective BCs: the BCCB C, as Examples 3 and 4 do for Algorithms 1 and 4)
+    const int autotr = (in.bc == MLBA_BC_PERIODIC || in.bc == MLBA_BC_ANTIREFLECTIVE)
+                           ? TR_DFT : (sym ? TR_DCT : TR_DFT);
     pd.transform = (tr == MLBA_TR_DFT) ? TR_DFT : (tr == MLBA_TR_DCT ? TR_DCT : autotr);
     h.psf_pre = h.psf;
   }
@@ -899,8 +911,8 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   CK(cudaMemcpy(B->d_probs, probs_h.data(), count * sizeof(Prob), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(B->d_states, st_h.data(), count * sizeof(State), cudaMemcpyHostToDevice));
   // ---- item lists
-  std::vector<int2> blur, corr, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
-      cols_kry, vec_kry, vec_kry_bc, corr_all, rows_all, cols_all, spec_all, vec_all;
+  std::vector<int2> blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec,
+      rows_kry, cols_kry, vec_kry, vec_kry_bc, corr_all, rows_all, cols_all, spec_all, vec_all;
   size_t smem_st = 0, smem_fft = 0;
   for (int i = 0; i < count; ++i) {
     const Prob& pd = B->hp[i].pd;
@@ -908,7 +920,10 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     add(blur, pd.nblk_blur);
     add(corr_all, pd.nblk_corr);
     add(vec_all, pd.nblk_vec);
-    if (pd.use_adj) add(corr, pd.nblk_corr);
+    if (pd.use_adj) {
+      if (pd.bc == BC_AR) add(reblur, pd.nblk_blur);
+      else add(corr, pd.nblk_corr);
+    }
     const bool specp = pd.transform != TR_NONE;
     if (specp) { add(rows_all, pd.nblk_rows); add(cols_all, pd.nblk_cols); add(spec_all, pd.nblk_spec); }
     if (pd.precond == P_KRYLOV) {
@@ -940,6 +955,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   B->smem_fft = std::max<size_t>(smem_fft, 16);
   int rc = MLBA_OK;
   rc |= build_list(B, B->blur, blur); rc |= build_list(B, B->corr, corr);
+  rc |= build_list(B, B->reblur, reblur);
   rc |= build_list(B, B->corr_kry, corr_kry); rc |= build_list(B, B->blur_kry, blur_kry);
   rc |= build_list(B, B->rows_spec, rows_spec); rc |= build_list(B, B->cols_stat, cols_stat);
   rc |= build_list(B, B->cols_ns, cols_ns); rc |= build_list(B, B->spec, spec);
@@ -1166,7 +1182,10 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
         launch_cols<double>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
         launch_rows_inv<double>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
       }
-      if (stage == 3) launch_stencil<double>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
+      if (stage == 3) {
+        launch_stencil<double>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
+        launch_stencil<double>(ST_REBLUR, P, S, B->reblur.dev, B->reblur.count, -1, -1, SL_U, 0, B->smem_stencil, s);
+      }
       if (stage == 4) launch_frame<double, double>(P, S, B->frame.dev, B->frame.count, B->frame.sec, -1, SL_F, nullptr, nullptr, 0.0, B->levels, B->frame_shape, s);
     } else {
       if (stage == 1) launch_stencil<float>(ST_FWD_RESID, P, S, B->blur.dev, B->blur.count, SL_F, SL_R, SL_G, 0, B->smem_stencil, s);
@@ -1177,7 +1196,10 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
         launch_cols<float>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
         launch_rows_inv<float>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
       }
-      if (stage == 3) launch_stencil<float>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
+      if (stage == 3) {
+        launch_stencil<float>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
+        launch_stencil<float>(ST_REBLUR, P, S, B->reblur.dev, B->reblur.count, -1, -1, SL_U, 0, B->smem_stencil, s);
+      }
       if (stage == 4) {
         if (B->z_store == MLBA_BF16)
           launch_frame<float, __nv_bfloat16>(P, S, B->frame.dev, B->frame.count, B->frame.sec, -1, SL_F, nullptr, nullptr, 0.0, B->levels, B->frame_shape, s);
@@ -1493,6 +1515,17 @@ int mlba_op_blur_adjoint(mlba_ctx* c, const void* t, void* out, int on_device) {
   int rc = copy_in(B, pd.buf[SL_AUX0], t, (size_t)pd.n * pd.n * ts, on_device);
   if (rc != MLBA_OK) return rc;
   if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
+  if (pd.bc == BC_AR) {
+    // the reblurring matrix A' (Section 2.2), n x n
+    if (B->dtype == MLBA_F64)
+      launch_stencil<double>(ST_REBLUR, B->d_probs, B->d_opstates, B->blur.dev, B->blur.count,
+                             SL_AUX0, SL_AUX1, SL_AUX1, 0, B->smem_stencil, B->stream);
+    else
+      launch_stencil<float>(ST_REBLUR, B->d_probs, B->d_opstates, B->blur.dev, B->blur.count,
+                            SL_AUX0, SL_AUX1, SL_AUX1, 0, B->smem_stencil, B->stream);
+    CK(cudaGetLastError());
+    return copy_out(B, out, pd.buf[SL_AUX1], (size_t)pd.n * pd.n * ts, on_device);
+  }
   if (B->dtype == MLBA_F64) {
     launch_stencil<double>(ST_CORR, B->d_probs, B->d_opstates, B->corr_all.dev, B->corr_all.count,
                            SL_AUX0, SL_V, SL_V, 0, B->smem_stencil, B->stream);

@@ -12,7 +12,7 @@ namespace mlba {
 
 // ----------------------------------------------------------------------------
 // enumerations mirrored from include/mlba.h
-enum { BC_ZERO = 0, BC_PERIODIC = 1, BC_REFLECTIVE = 2, BC_RECT = 3 };
+enum { BC_ZERO = 0, BC_PERIODIC = 1, BC_REFLECTIVE = 2, BC_RECT = 3, BC_AR = 4 };
 enum { P_NONE = 0, P_BCCB = 1, P_KRYLOV = 2, P_SYM = 3, P_TIKH = 4, P_TIKH_NS = 5 };
 enum { TR_NONE = 0, TR_DFT = 1, TR_DCT = 2 };
 

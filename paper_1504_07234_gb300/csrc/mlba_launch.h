@@ -10,7 +10,9 @@ enum {
   ST_FWD_RESID = 0,   // dst = g - A src ; ||dst||^2 -> iteration bookkeeping (stop rule)
   ST_FWD_STORE = 1,   // dst = A src
   ST_FWD_PCGQ = 2,    // dst = A src + alpha aux ; <aux, dst> -> PCG step length
-  ST_CORR = 3         // dst (ne x ne) = full correlation of src (n x n, zero padded)
+  ST_CORR = 3,        // dst (ne x ne) = full correlation of src (n x n, zero padded)
+  ST_REBLUR = 4       // dst (n x n) = A' src: correlation of the antireflectively padded src
+                      // (the reblurring matrix of Section 2.2; default dst U)
 };
 // vector kernels (k_stencil.cu)
 enum {

@@ -141,6 +141,65 @@ def test_four_level_loop_matches_oracle(M, dtype, bc, precond, transform, n):
         np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-3)
 
 
+ASYM3 = np.array([[0.0, 0.1, 0.05], [0.2, 0.3, 0.0], [0.15, 0.1, 0.1]])
+# (parameters at which the oracle converges: with antireflective BCs the BCCB
+# preconditioner needs the larger alpha of Algorithm 1, Section 4.1)
+AR_CASES = [("none", "auto", I.psf_motion(7, 0.9), 0.3),
+            ("bccb", "dft", I.psf_motion(7, 0.9), 1.0),
+            ("tikh", "dft", ASYM3, 0.05),
+            ("tikh_ns", "dft", ASYM3, 0.05),
+            ("bccb", "dct", I.psf_gaussian(1.5, 7), 0.1)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("precond,transform,psf,alpha", AR_CASES,
+                         ids=[f"{c[0]}-{c[1]}" for c in AR_CASES])
+def test_antireflective_loop_matches_oracle(M, dtype, precond, transform, psf, alpha):
+    """Antireflective BCs with the reblurring matrix A' in place of A^T
+    (Section 2.2; the paper's Examples 3 and 4 run Alg-BC1, BC4 and BC4-NS
+    with the BCCB preconditioner this way)."""
+    pr = small("antireflective", precond, n=58, psf=psf, alpha=alpha, transform=transform, iters=10)
+    f, st, res, al, be = run_gpu(M, pr, dtype)
+    ref = run_oracle(pr)
+    assert st["iter"] == ref["iters"]
+    if dtype == "f64":
+        assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-9)
+        if precond == "tikh_ns":
+            np.testing.assert_allclose(al, ref["alphas"], rtol=1e-8)
+    else:
+        restoration_bars(f, ref, pr)
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("levels", [2, 4])
+def test_antireflective_batch_with_other_bcs(M, levels):
+    """Antireflective problems batched with the other boundary treatments
+    (two-group schedule), FP64, against the oracle."""
+    probs = [small("antireflective", "bccb", n=44, transform="dft", iters=6, levels=levels,
+                   alpha=1.0),
+             small("reflective", "tikh_ns", n=48, psf=I.psf_disk(3), transform="dct", iters=6,
+                   seed=3, levels=levels),
+             small("antireflective", "tikh_ns", n=40, psf=ASYM3, iters=6, seed=4,
+                   alpha=0.05, levels=levels),
+             small("rect", "bccb", n=36, transform="dft", iters=6, seed=5, levels=levels)]
+    descs = [dict(psf=p.psf, g=p.g, delta=p.delta, bc=p.bc, precond=p.precond, mu=p.mu,
+                  alpha=p.alpha, transform=p.transform, max_iter=6) for p in probs]
+    b = M.Batch(descs, dtype="f64", levels=levels, stop=False, max_iter=6, rect_ns_hybrid=True)
+    b.iterate(7)
+    for i, p in enumerate(probs):
+        ref = run_oracle(p)
+        assert np.abs(b.result(i) - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max(), i
+    b.close()
+
+
+def test_antireflective_rejects_alg2_and_alg3(M):
+    h = I.psf_motion(7, 0.9)
+    for pc in ("krylov", "sym"):
+        with pytest.raises(M.MlbaError):
+            M.Context(h, 40, "antireflective", pc, dtype="f64")
+
+
 def test_fp64_stop_rule_matches_oracle(M):
     pr = I.config(2, n=64)
     pr.precond, pr.transform = "tikh", "dct"

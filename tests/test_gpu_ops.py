@@ -45,17 +45,20 @@ PSFS = {
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("bc", ["zero", "periodic", "reflective", "rect"])
+@pytest.mark.parametrize("bc", ["zero", "periodic", "reflective", "rect", "antireflective"])
 @pytest.mark.parametrize("psf,n", [("gauss9", 70), ("disk2", 33), ("motion7", 45), ("asym3", 17),
                                    ("gauss31", 64), ("gauss41", 80), ("disk17", 72)])
 def test_blur_and_adjoint(M, dtype, bc, psf, n):
+    """A and A^T; for antireflective BCs A^T is the reblurring matrix A'
+    (Section 2.2)."""
     h = PSFS[psf]
     ctx = M.Context(h, n, bc, "none", dtype=dtype)
     rng = np.random.default_rng(n)
     f = rng.standard_normal((ctx.nf, ctx.nf))
     t = rng.standard_normal((n, n))
     assert rel_err(ctx.blur(f), O.blur(f, h, bc)) <= TOL[dtype]
-    assert rel_err(ctx.blur_adjoint(t), O.blur_adjoint(t, h, bc)) <= TOL[dtype]
+    ref = O.reblur(t, h, bc) if bc == "antireflective" else O.blur_adjoint(t, h, bc)
+    assert rel_err(ctx.blur_adjoint(t), ref) <= TOL[dtype]
     ctx.close()
 
 
