@@ -277,9 +277,49 @@ def spectrum_dct(h: np.ndarray, n: int) -> np.ndarray:
     return sfft.dctn(a_e1, type=2, norm="ortho") / sfft.dctn(e1, type=2, norm="ortho")
 
 
+def ar_transform(n: int) -> np.ndarray:
+    """The antireflective transform of Section 2.2 as an n x n matrix: the
+    sine vectors sin(j pi i / (n-1)), j = 1..n-2 (zero at both ends), with a
+    uniform sampling of the linear functions 1 - i/(n-1) and i/(n-1) as the
+    first and last columns (together they span the constant and linear
+    functions).  Not orthogonal."""
+    i = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    t = np.sin(j * np.pi * i / (n - 1))
+    t[:, 0] = 1.0 - np.arange(n) / (n - 1)
+    t[:, n - 1] = np.arange(n) / (n - 1)
+    return t
+
+
+def ar_angles(n: int) -> np.ndarray:
+    """Frequency of each column of :func:`ar_transform`: j pi / (n-1) for the
+    sine vectors, 0 for the two linear ones."""
+    th = np.arange(n) * np.pi / (n - 1)
+    th[0] = th[n - 1] = 0.0
+    return th
+
+
+def spectrum_ar(h: np.ndarray, n: int) -> np.ndarray:
+    """Eigenvalues of the antireflective matrix of a quadrantally symmetric
+    PSF in the basis of :func:`ar_transform` (tensor products in 2-D):
+    Lambda(j, k) = sum h(d1, d2) cos(d1 th_j) cos(d2 th_k)."""
+    c = psf_centre(h)
+    p = h.shape[0]
+    th = ar_angles(n)
+    lam = np.zeros((n, n))
+    for a in range(p):
+        for b in range(p):
+            if h[a, b] != 0.0:
+                lam += h[a, b] * np.outer(np.cos((a - c) * th), np.cos((b - c) * th))
+    return lam
+
+
 class SpectralPrecond:
     """(CC^T + alpha I)^{-1} and C^T (CC^T + alpha I)^{-1} for a C diagonalised
-    by the DFT (periodic BC) or the DCT (reflective BC, symmetric PSF)."""
+    by the DFT (periodic BC), the DCT (reflective BC, symmetric PSF) or the
+    antireflective transform (antireflective BC, symmetric PSF; C^T is then
+    the reblurring matrix C' = C, Section 2.2).  The antireflective transform
+    is not unitary: forward is its inverse, applied by a dense solve."""
 
     def __init__(self, h: np.ndarray, n: int, transform: str):
         self.transform = transform
@@ -288,6 +328,10 @@ class SpectralPrecond:
             self.lam = spectrum_dft(h, n)
         elif transform == "dct":
             self.lam = spectrum_dct(h, n)
+        elif transform == "ar":
+            self.lam = spectrum_ar(h, n)
+            self.t = ar_transform(n)
+            self.tinv = np.linalg.inv(self.t)
         else:
             raise ValueError(transform)
         self.sigma = np.abs(self.lam) ** 2
@@ -295,11 +339,15 @@ class SpectralPrecond:
     def forward(self, r):
         if self.transform == "dft":
             return np.fft.fft2(r) / self.n       # unitary scaling
+        if self.transform == "ar":
+            return self.tinv @ r @ self.tinv.T
         return sfft.dctn(r, type=2, norm="ortho")
 
     def inverse(self, rhat):
         if self.transform == "dft":
             return np.real(np.fft.ifft2(rhat * self.n))
+        if self.transform == "ar":
+            return self.t @ rhat @ self.t.T
         return sfft.idctn(rhat, type=2, norm="ortho")
 
     def inv(self, r, alpha):
@@ -424,18 +472,24 @@ def ns_alpha(rhat2: np.ndarray, sigma: np.ndarray, qn: float) -> float:
 def choose_transform(h: np.ndarray, precond: str, transform: str, bc: str = "rect") -> str:
     """Diagonalising transform of C (Section 4.1).
 
-    Algorithm 3 always uses the DCT of the symmetrised PSF.  An explicit
-    choice wins otherwise.  'auto': with periodic BCs the periodic C equals A
-    and the DFT is used; with antireflective BCs the BCCB C (DFT), as the
-    paper's Examples 3 and 4 do for Algorithms 1 and 4; otherwise the DCT when
-    the PSF is quadrantally symmetric (the reflective C approximates A better,
-    Section 4.1) and the DFT when it is not."""
+    Algorithm 3 uses the DCT of the symmetrised PSF (the antireflective
+    transform with antireflective BCs, Section 4.3).  An explicit choice wins
+    otherwise.  'auto': with periodic BCs the periodic C equals A and the DFT
+    is used; with antireflective BCs the antireflective transform (C = A) for
+    a quadrantally symmetric PSF outside 4-NS, the BCCB C (DFT) otherwise, as
+    the paper's Examples 3 and 4 do; otherwise the DCT when the PSF is
+    quadrantally symmetric (the reflective C approximates A better, Section
+    4.1) and the DFT when it is not."""
     if precond == "sym":
-        return "dct"
-    if transform in ("dft", "dct"):
+        return "ar" if bc == "antireflective" else "dct"
+    if transform in ("dft", "dct", "ar"):
         return transform
-    if bc in ("periodic", "antireflective"):
+    if bc == "periodic":
         return "dft"
+    if bc == "antireflective":
+        # C = A through the antireflective transform for a symmetric PSF
+        # (Section 2.2); 4-NS needs a unitary transform for Eq. Alg4_rev_7
+        return "ar" if (quadrantally_symmetric(h) and precond != "tikh_ns") else "dft"
     return "dct" if quadrantally_symmetric(h) else "dft"
 
 
@@ -456,9 +510,9 @@ def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
 
     with x = S_mu(z), f = W^T x, z^0 = x^0 = 0 and r^n = g - A f^n.  With
     antireflective BCs every A^T is the reblurring matrix A' (Section 2.2);
-    Algorithm 2 (the paper finds it of no use there, Example 4) and
-    Algorithm 3 (whose Q would need the antireflective transform) are not
-    defined for them here.
+    Algorithm 2 is not defined for them here (the paper finds it of no use
+    there, Example 4), nor 4-NS with the antireflective transform, which is
+    not unitary (Eq. Alg4_rev_7 is solved in the transform domain).
     Stopping (Eq. discrpr, Eq. Alg4_rev_12): the first n > 0 with
     ||r^n|| <= gamma delta (Algorithms 1-4), or the first n >= 0 with
     ||r^n|| <= tau delta (4-NS) (readings c4, c16).  With ``stop=False``
@@ -476,16 +530,18 @@ def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
     nf = n + p - 1 if bc == "rect" else n
     if precond in ("tikh", "tikh_ns") and bc == "rect" and not (precond == "tikh_ns" and rect_ns_hybrid):
         raise ValueError("Algorithm 4 needs a square A (Section 5)")
-    if bc == "antireflective" and precond in ("krylov", "sym"):
-        raise ValueError("Algorithms 2 and 3 are not defined for antireflective BCs here")
+    if bc == "antireflective" and precond == "krylov":
+        raise ValueError("Algorithm 2 is not defined for antireflective BCs here")
     adj = (lambda v: reblur(v, h, bc)) if bc == "antireflective" else (lambda v: blur_adjoint(v, h, bc))
     ns = precond == "tikh_ns"
     tr = choose_transform(h, precond, transform, bc)
+    if tr == "ar" and (bc != "antireflective" or precond == "tikh_ns"):
+        raise ValueError("the antireflective transform serves antireflective BCs outside 4-NS")
     pre = None
     if precond in ("bccb", "krylov", "tikh", "tikh_ns"):
         pre = SpectralPrecond(h, n, tr)
     elif precond == "sym":
-        pre = SpectralPrecond(symmetrize(h), n, "dct")
+        pre = SpectralPrecond(symmetrize(h), n, tr)
     tau = ns_tau(rho)
 
     B = n_bands(levels)

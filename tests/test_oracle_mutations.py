@@ -93,3 +93,17 @@ def test_reflective_pad_instead_of_antireflective_is_caught(monkeypatch):
     monkeypatch.setattr(O, "extend", wrong)
     with pytest.raises(AssertionError):
         TB.test_antireflective_preserves_linear_images()
+
+
+def test_wrong_antireflective_angles_are_caught(monkeypatch):
+    """The sine vectors of the antireflective transform have frequencies
+    j pi / (n - 1); a DCT-like j pi / n must fail the diagonalisation pin."""
+    import test_oracle_precond as TP
+
+    def wrong(n):
+        th = np.arange(n) * np.pi / n
+        th[0] = th[n - 1] = 0.0
+        return th
+    monkeypatch.setattr(O, "ar_angles", wrong)
+    with pytest.raises(AssertionError):
+        TP.test_antireflective_transform_diagonalises_ar_matrix(I.psf_disk(2), 6)

@@ -256,3 +256,48 @@ def test_pcg_stops_on_preconditioned_relative_residual():
                        lambda v: pre.inv(v, alpha), alpha, tol=1e-3, max_steps=5)
     assert all(rel > 1e-3 for _, rel, _ in its[:4]) and steps5 == 5
     np.testing.assert_allclose(t5.ravel(), its[4][0], atol=1e-10)
+
+
+@pytest.mark.parametrize("psf", [I.psf_gaussian(1.1, 5), I.psf_disk(2)])
+@pytest.mark.parametrize("n", [6, 9])
+def test_antireflective_transform_diagonalises_ar_matrix(psf, n):
+    """Section 2.2: the antireflective matrix of a quadrantally symmetric PSF
+    (dense, NumPy odd-reflection pad; separable Gaussian and non-separable
+    disk) equals (T x T) diag(Lambda) (T x T)^{-1} with T the antireflective
+    transform and Lambda the cosine symbol at j pi / (n-1) (0 for the two
+    linear basis vectors)."""
+    a = dense_blur_matrix(psf, n, "antireflective")
+    tt = np.kron(O.ar_transform(n), O.ar_transform(n))
+    lam = O.spectrum_ar(psf, n)
+    np.testing.assert_allclose(tt @ np.diag(lam.ravel()) @ np.linalg.inv(tt), a, atol=1e-13)
+
+
+def test_antireflective_precond_against_dense():
+    """(QQ' + alpha I)^{-1} and Q'(QQ' + alpha I)^{-1} with Q the dense
+    antireflective matrix of a symmetric PSF and Q' its reblurring matrix
+    (Eq. Alg3 with antireflective BCs, Section 4.3; Eq. Alg4)."""
+    h = I.psf_disk(2)
+    n, alpha = 8, 0.03
+    q = dense_blur_matrix(h, n, "antireflective")
+    q_re = dense_blur_matrix(h[::-1, ::-1], n, "antireflective")
+    np.testing.assert_allclose(q_re, q, atol=1e-15)          # symmetric PSF: Q' = Q
+    pre = O.SpectralPrecond(h, n, "ar")
+    r = np.random.default_rng(8).standard_normal((n, n))
+    m = q @ q_re + alpha * np.eye(n * n)
+    np.testing.assert_allclose(pre.inv(r, alpha).ravel(), np.linalg.solve(m, r.ravel()), atol=1e-11)
+    np.testing.assert_allclose(pre.tikh(r, alpha).ravel(), q_re @ np.linalg.solve(m, r.ravel()),
+                               atol=1e-11)
+
+
+def test_alg3_antireflective_symmetric_psf_is_alg1_ar():
+    """Section 4.3 with antireflective BCs: for a quadrantally symmetric PSF
+    H~ = H, so Algorithm 3 equals Algorithm 1 with the antireflective C."""
+    h = I.psf_gaussian(1.2, 5)
+    n = 16
+    rng = np.random.default_rng(3)
+    g = rng.random((n, n))
+    a3 = O.mlba(g, h, 1.0, "antireflective", "sym", mu=0.02, alpha=0.2, levels=1, max_iter=4,
+                stop=False)
+    a1 = O.mlba(g, h, 1.0, "antireflective", "bccb", mu=0.02, alpha=0.2, levels=1, max_iter=4,
+                stop=False, transform="ar")
+    np.testing.assert_allclose(a3["f"], a1["f"], atol=1e-12)
