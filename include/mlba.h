@@ -62,8 +62,8 @@ enum mlba_bc {                 /* Section 2, Table 1 */
   MLBA_BC_ANTIREFLECTIVE = 4   /* 2 F(edge) - F(mirror) pad, corners antireflected row then
                                   column (Section 2.2); A^T is replaced by the reblurring
                                   matrix A' (the same BCs on the PSF rotated by 180 degrees).
-                                  Algorithms 1, 4 and 4-NS and P = I; not Algorithm 2 (the
-                                  paper finds it of no use there) nor Algorithm 3. */
+                                  Algorithms 1, 3, 4 and 4-NS and P = I; not Algorithm 2 (the
+                                  paper finds it of no use there). */
 };
 
 enum mlba_precond {            /* Sections 3-5 */
@@ -78,9 +78,16 @@ enum mlba_precond {            /* Sections 3-5 */
 enum mlba_dtype { MLBA_F32 = 0, MLBA_F64 = 1, MLBA_BF16 = 2 };
 
 enum mlba_transform {          /* diagonalising transform of C (Section 4.1) */
-  MLBA_TR_AUTO = 0,            /* DFT for periodic BC (C = A); else DCT for a quadrantally symmetric PSF, else DFT */
+  MLBA_TR_AUTO = 0,            /* DFT for periodic BC (C = A); antireflective BC: the antireflective
+                                  transform (C = A) for a quadrantally symmetric PSF outside 4-NS,
+                                  else DFT; otherwise DCT for a quadrantally symmetric PSF, else DFT */
   MLBA_TR_DFT = 1,             /* C = periodic-BC (Strang) matrix */
-  MLBA_TR_DCT = 2              /* C = reflective-BC matrix; PSF must be quadrantally symmetric */
+  MLBA_TR_DCT = 2,             /* C = reflective-BC matrix; PSF must be quadrantally symmetric */
+  MLBA_TR_AR = 3               /* C = antireflective-BC matrix (antireflective BCs only, Section 2.2):
+                                  the sine basis of length n - 2 plus the constant and linear
+                                  vectors; PSF quadrantally symmetric; not with 4-NS (the transform
+                                  is not unitary) nor Algorithm 2; n <= 2049.  Algorithm 3 with
+                                  antireflective BCs always uses it (Q from H~, Section 4.3). */
 };
 
 /* ---- options --------------------------------------------------------- */

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libmlba.so")
 
 BC = {"zero": 0, "periodic": 1, "reflective": 2, "rect": 3, "antireflective": 4}
 PRECOND = {"none": 0, "bccb": 1, "krylov": 2, "sym": 3, "tikh": 4, "tikh_ns": 5}
-TRANSFORM = {"auto": 0, "dft": 1, "dct": 2}
+TRANSFORM = {"auto": 0, "dft": 1, "dct": 2, "ar": 3}
 DTYPE = {"f32": 0, "f64": 1, "bf16": 2}
 ERRORS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtime error",
           -4: "device wait timed out", -5: "diverged", -6: "call out of order",

@@ -296,7 +296,7 @@ __device__ __noinline__ void fft_pass_any(int G, int N, int TSg, int Ns, int R,
 // keeps each region's butterflies in registers (the switch form spilled).
 template <typename T2, bool INV>
 __device__ __noinline__ void fft_smem(int G, const Prob& pd) {
-  const int N = pd.n;
+  const int N = pd.nfft;
   const int TSg = fpad(N) + 1;
   const T2* tw = static_cast<const T2*>(pd.tw);
   const int n16 = pd.nr16, r2 = pd.r2, n3 = pd.nr3, n5 = pd.nr5;
@@ -1416,6 +1416,201 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// The antireflective transform (Section 2.2), for antireflective BCs with a
+// quadrantally symmetric PSF:
+//   T = [ 1 - i/(n-1) | sin(j pi i/(n-1)), j = 1..n-2 | i/(n-1) ],
+//   T^{-1} x: c_0 = x_0, c_{n-1} = x_{n-1},
+//             c_j = (2/(n-1)) sum_i sin(j pi i/(n-1)) (x_i - x_0 (1 - t_i) - x_{n-1} t_i)
+//   T c:      x_0 = c_0, x_{n-1} = c_{n-1},
+//             x_i = sum_j sin(j pi i/(n-1)) c_j + c_0 (1 - t_i) + c_{n-1} t_i,
+// t_i = i/(n-1), i, j = 1..n-2.  The sine sums (a DST-I of length n - 2) are
+// one DFT of length M = 2(n-1) (pd.nfft) of the odd extension
+// (0, y_1 .. y_{n-2}, 0, -y_{n-2} .. -y_1): Z_k = -2i sum_i y_i sin(pi i k/(n-1)).
+// Two real sequences a, b travel as a + ib: sum_a = -Im Z_k / 2, sum_b = Re Z_k / 2.
+// The 2-D transform is T x T (rows, then columns); the spectrum is real and
+// column-blocked like the DCT spectrum.  T is not orthogonal: the weights
+// need no 1/n^2 and the 4-NS solve (spectral sums) does not apply.
+
+// odd-extension position i of a length-M transform -> (source index j in
+// 1..n-2, sign), j = 0 for the two zero positions
+__device__ __forceinline__ int ar_src(int i, int n, int M, int* neg) {
+  if (i >= 1 && i <= n - 2) { *neg = 0; return i; }
+  if (i >= n) { *neg = 1; return M - i; }
+  *neg = 0;
+  return 0;
+}
+
+// rows: INV = false applies T^{-1} to the rows of buf[slot] (n x n) into the
+// blocked spectrum S; INV = true applies T to the rows of S into buf[slot]
+template <typename T, bool INV>
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
+k_ar_rows(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+          int slot, int pcg) {
+  using T2 = typename Vec2<T>::type;
+  constexpr int NT = tr_nt(sizeof(T));
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  if (tr_skip(states[item.x], pcg)) return;
+  const int n = pd.n, M = pd.nfft, G = pd.row_g, TSg = fpad(M) + 1, cb = pd.cb;
+  const int row0 = 2 * item.y * G;
+  T* S = static_cast<T*>(pd.buf[SL_S]);
+  T* X = static_cast<T*>(pd.buf[slot]);
+  const T inv_n1 = T(1) / T(n - 1);
+  const FastDiv fcb(cb);
+  auto sidx = [&](int r, int k) -> size_t {
+    const int b = fcb.div(k);
+    return (size_t)b * n * cb + (size_t)r * cb + (k - b * cb);
+  };
+  // input row r at column k (0 past the last row)
+  auto in = [&](int r, int k) -> T {
+    if (r >= n) return T(0);
+    return INV ? S[sidx(r, k)] : X[(size_t)r * n + k];
+  };
+  const FastDiv fM(M), fn(n);
+  for (int e = threadIdx.x; e < G * M; e += NT) {
+    const int g = fM.div(e), i = e - g * M;
+    const int ra = row0 + 2 * g, rb = ra + 1;
+    int neg;
+    const int j = ar_src(i, n, M, &neg);
+    T2 z;
+    z.x = T(0); z.y = T(0);
+    if (j) {
+      if (INV) {
+        z.x = in(ra, j); z.y = in(rb, j);
+      } else {
+        const T t = T(j) * inv_n1;
+        z.x = in(ra, j) - in(ra, 0) * (T(1) - t) - in(ra, n - 1) * t;
+        z.y = in(rb, j) - in(rb, 0) * (T(1) - t) - in(rb, n - 1) * t;
+      }
+      if (neg) { z.x = -z.x; z.y = -z.y; }
+    }
+    sm[g * TSg + fpad(i)] = z;
+  }
+  __syncthreads();
+  fft_smem<T2, false>(G, pd);
+  for (int e = threadIdx.x; e < G * n; e += NT) {
+    const int g = fn.div(e), k = e - g * n;
+    const int ra = row0 + 2 * g, rb = ra + 1;
+    T va, vb;
+    if (k == 0 || k == n - 1) {
+      va = in(ra, k); vb = in(rb, k);
+    } else {
+      const T2 Z = sm[g * TSg + fpad(k)];
+      if (INV) {
+        const T t = T(k) * inv_n1;
+        va = T(-0.5) * Z.y + in(ra, 0) * (T(1) - t) + in(ra, n - 1) * t;
+        vb = T(0.5) * Z.x + in(rb, 0) * (T(1) - t) + in(rb, n - 1) * t;
+      } else {
+        va = -Z.y * inv_n1;
+        vb = Z.x * inv_n1;
+      }
+    }
+    if (INV) {
+      if (ra < n) X[(size_t)ra * n + k] = va;
+      if (rb < n) X[(size_t)rb * n + k] = vb;
+    } else {
+      if (ra < n) S[sidx(ra, k)] = va;
+      if (rb < n) S[sidx(rb, k)] = vb;
+    }
+  }
+}
+
+// columns of one spectrum block: T^{-1}, the weight w = 1/(Lambda^2 + alpha)
+// (Eq. Alg1, Alg3) or Lambda/(Lambda^2 + alpha) (Eq. Alg4), T; real columns
+// 2g and 2g + 1 of the block travel as transform g
+template <typename T, int mode>
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
+k_ar_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+          int pcg, double op_alpha, int op_kind) {
+  using T2 = typename Vec2<T>::type;
+  constexpr int NT = tr_nt(sizeof(T));
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  if (tr_skip(states[item.x], pcg)) return;
+  const int n = pd.n, M = pd.nfft, cb = pd.cb, TSg = fpad(M) + 1;
+  const int G = cb / 2;
+  T2* ends = sm + G * TSg;                     // weighted c_0 and c_{n-1} of each transform
+  double alpha = pd.alpha;
+  int kind = (pd.precond == P_TIKH) ? W_TIKH : W_INV;
+  if (mode == COL_OP) { alpha = op_alpha; kind = op_kind; }
+  const T Ta = T(alpha);
+  const size_t base = (size_t)item.y * n * cb;
+  const int kb = item.y * cb;
+  T* S = static_cast<T*>(pd.buf[SL_S]) + base;
+  const T inv_n1 = T(1) / T(n - 1);
+  auto col_ok = [&](int c) { return kb + c < n; };
+  auto in = [&](int r, int c) -> T { return col_ok(c) ? S[(size_t)r * cb + c] : T(0); };
+  const FastDiv fM(M), fn(n);
+  // 1. T^{-1} along the columns: odd extension of the detrended inner part
+  for (int e = threadIdx.x; e < G * M; e += NT) {
+    const int g = fM.div(e), i = e - g * M;
+    const int ca = 2 * g, cbb = ca + 1;
+    int neg;
+    const int j = ar_src(i, n, M, &neg);
+    T2 z;
+    z.x = T(0); z.y = T(0);
+    if (j) {
+      const T t = T(j) * inv_n1;
+      z.x = in(j, ca) - in(0, ca) * (T(1) - t) - in(n - 1, ca) * t;
+      z.y = in(j, cbb) - in(0, cbb) * (T(1) - t) - in(n - 1, cbb) * t;
+      if (neg) { z.x = -z.x; z.y = -z.y; }
+    }
+    sm[g * TSg + fpad(i)] = z;
+  }
+  __syncthreads();
+  fft_smem<T2, false>(G, pd);
+  // 2. coefficients, weighted; the odd extension of the weighted inner part
+  //    replaces the spectrum in place (position k is read only by its own
+  //    thread, and the mirror positions n .. M-1 are read by none)
+  auto w = [&](int r, int c) -> T {
+    return col_ok(c) ? weight_dct<T>(pd, base + (size_t)r * cb + c, Ta, T(1), kind) : T(0);
+  };
+  for (int e = threadIdx.x; e < G * n; e += NT) {
+    const int g = fn.div(e), k = e - g * n;
+    const int ca = 2 * g, cbb = ca + 1;
+    T2* tb = sm + g * TSg;
+    if (k == 0 || k == n - 1) {
+      T2 v;
+      v.x = in(k, ca) * w(k, ca);
+      v.y = in(k, cbb) * w(k, cbb);
+      ends[2 * g + (k == 0 ? 0 : 1)] = v;
+      tb[fpad(k)] = mk2<T2>(T(0), T(0));
+    } else {
+      const T2 Z = tb[fpad(k)];
+      T2 v;
+      v.x = -Z.y * inv_n1 * w(k, ca);
+      v.y = Z.x * inv_n1 * w(k, cbb);
+      tb[fpad(k)] = v;
+      tb[fpad(M - k)] = mk2<T2>(-v.x, -v.y);
+    }
+  }
+  __syncthreads();
+  // 3. T along the columns
+  fft_smem<T2, false>(G, pd);
+  for (int e = threadIdx.x; e < G * n; e += NT) {
+    const int g = fn.div(e), k = e - g * n;
+    const int ca = 2 * g, cbb = ca + 1;
+    const T2 e0 = ends[2 * g], e1 = ends[2 * g + 1];
+    T va, vb;
+    if (k == 0) { va = e0.x; vb = e0.y; }
+    else if (k == n - 1) { va = e1.x; vb = e1.y; }
+    else {
+      const T2 Z = sm[g * TSg + fpad(k)];
+      const T t = T(k) * inv_n1;
+      va = T(-0.5) * Z.y + e0.x * (T(1) - t) + e1.x * t;
+      vb = T(0.5) * Z.x + e0.y * (T(1) - t) + e1.y * t;
+    }
+    if (col_ok(ca)) S[(size_t)k * cb + ca] = va;
+    if (col_ok(cbb)) S[(size_t)k * cb + cbb] = vb;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Set-up: eigenvalues of C in FP64 (Section 4.1).  Q(dy, k2) = sum_dx h
 // e^{-2 pi i k2 dx/n} (DFT) or sum_dx h cos(pi k2 dx/n) (DCT) comes from
@@ -1428,7 +1623,7 @@ __global__ void k_spectrum(int transform, int n, int p, int half, int cb,
                            const double* __restrict__ q, const double* __restrict__ tab,
                            void* lam, void* sigT, int is_double) {
   const int c = (p - 1) / 2;
-  const int W = (transform == TR_DCT) ? n : half;
+  const int W = (transform == TR_DCT || transform == TR_AR) ? n : half;
   const int nb = (W + cb - 1) / cb;
   const size_t tot = (size_t)nb * n * cb;
   for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < tot;
@@ -1438,7 +1633,15 @@ __global__ void k_spectrum(int transform, int n, int p, int half, int cb,
     const int k1 = rem / cb, k2 = b * cb + (rem - k1 * cb);
     double re = 0.0, im = 0.0;
     if (k2 < W) {
-      if (transform == TR_DCT) {
+      if (transform == TR_AR) {
+        // angles k pi/(n-1), 0 for the two linear basis vectors (k = 0, n-1);
+        // tab[m] = cos(pi m/(n-1)), m < 2(n-1)
+        const int kk = (k1 == n - 1) ? 0 : k1, per = 2 * (n - 1);
+        for (int a = 0; a < p; ++a) {
+          int m = (kk * (a - c)) % per; if (m < 0) m += per;
+          re += tab[m] * q[(size_t)a * n + k2];
+        }
+      } else if (transform == TR_DCT) {
         for (int a = 0; a < p; ++a) {
           int m = (k1 * (a - c)) % (2 * n); if (m < 0) m += 2 * n;
           re += tab[m] * q[(size_t)a * n + k2];
@@ -1454,7 +1657,7 @@ __global__ void k_spectrum(int transform, int n, int p, int half, int cb,
       }
     }
     const double s2 = (k2 < W) ? re * re + im * im : 1.0;
-    if (transform == TR_DCT) {
+    if (transform == TR_DCT || transform == TR_AR) {
       if (is_double) static_cast<double*>(lam)[L] = re;
       else static_cast<float*>(lam)[L] = (float)re;
     } else {
@@ -1492,6 +1695,22 @@ void launch_rows_inv(const Prob* probs, State* states, const int2* items, int ni
   if (nitems > 0) k_rows_inv<T><<<nitems, tr_nt(sizeof(T)), smem, s>>>(probs, states, items, dst, pcg);
 }
 template <typename T>
+void launch_ar_rows(const Prob* probs, State* states, const int2* items, int nitems, int slot,
+                    int inv, int pcg, size_t smem, cudaStream_t s) {
+  if (nitems <= 0) return;
+  if (inv) k_ar_rows<T, true><<<nitems, tr_nt(sizeof(T)), smem, s>>>(probs, states, items, slot, pcg);
+  else k_ar_rows<T, false><<<nitems, tr_nt(sizeof(T)), smem, s>>>(probs, states, items, slot, pcg);
+}
+template <typename T>
+void launch_ar_cols(const Prob* probs, State* states, const int2* items, int nitems, int mode,
+                    int pcg, double op_alpha, int op_kind, size_t smem, cudaStream_t s) {
+  if (nitems <= 0) return;
+  if (mode == COL_OP)
+    k_ar_cols<T, COL_OP><<<nitems, tr_nt(sizeof(T)), smem, s>>>(probs, states, items, pcg, op_alpha, op_kind);
+  else
+    k_ar_cols<T, COL_FUSED><<<nitems, tr_nt(sizeof(T)), smem, s>>>(probs, states, items, pcg, op_alpha, op_kind);
+}
+template <typename T>
 void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, int cand,
                  cudaStream_t s) {
   if (nitems <= 0) return;
@@ -1501,7 +1720,7 @@ void launch_spec(const Prob* probs, State* states, const int2* items, int nitems
 void launch_spectrum_setup(int transform, int n, int p, int half, int cb, const double* q_dev,
                            const double* tab_dev, void* lam, void* sigT, int is_double,
                            cudaStream_t s) {
-  const int W = transform == TR_DCT ? n : half;
+  const int W = (transform == TR_DCT || transform == TR_AR) ? n : half;
   const size_t tot = (size_t)((W + cb - 1) / cb) * n * cb;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
@@ -1516,6 +1735,11 @@ cudaError_t fft_set_smem(size_t bytes) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
   }
+  for (const void* f : {(const void*)k_ar_rows<T, false>, (const void*)k_ar_rows<T, true>,
+                        (const void*)k_ar_cols<T, COL_FUSED>, (const void*)k_ar_cols<T, COL_OP>}) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -1524,6 +1748,8 @@ cudaError_t fft_set_smem(size_t bytes) {
   template void launch_cols<T>(const Prob*, State*, const int2*, int, int, int, double, int, size_t, cudaStream_t); \
   template void launch_rows_inv<T>(const Prob*, State*, const int2*, int, int, int, size_t, cudaStream_t); \
   template void launch_spec<T>(const Prob*, State*, const int2*, int, int, cudaStream_t);         \
+  template void launch_ar_rows<T>(const Prob*, State*, const int2*, int, int, int, int, size_t, cudaStream_t); \
+  template void launch_ar_cols<T>(const Prob*, State*, const int2*, int, int, int, double, int, size_t, cudaStream_t); \
   template cudaError_t fft_set_smem<T>(size_t);
 INST(float)
 INST(double)

@@ -53,14 +53,14 @@ struct ItemList {
 // The launches of one step over a set of problems.
 struct StepLists {
   ItemList blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
-      cols_kry, vec_kry, vec_kry_bc, frame;
-  int any_krylov = 0, any_spec = 0, any_ns = 0, pcg_max = 5;
+      cols_kry, vec_kry, vec_kry_bc, frame, ar_rows, ar_cols;
+  int any_krylov = 0, any_spec = 0, any_ns = 0, any_ar = 0, pcg_max = 5;
 };
 struct StepItems {
   std::vector<int2> blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec,
-      rows_kry, cols_kry, vec_kry, vec_kry_bc;
+      rows_kry, cols_kry, vec_kry, vec_kry_bc, ar_rows, ar_cols;
   std::vector<int2> frame[FRAME_SECTIONS];   // see add_frame_items
-  int any_krylov = 0, any_spec = 0, any_ns = 0, pcg_max = 5;
+  int any_krylov = 0, any_spec = 0, any_ns = 0, any_ar = 0, pcg_max = 5;
 };
 
 // Framelet launches of problem i: levels <= 2, the tiles of the fused sweep
@@ -94,13 +94,14 @@ struct mlba_batch {
   size_t arena_bytes = 0;
   // item lists
   ItemList blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
-      cols_kry, vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all;
+      cols_kry, vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all,
+      ar_rows, ar_cols;
   std::vector<int2*> allocs;
   size_t smem_stencil = 0, smem_fft = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool has_data = false;
-  int any_krylov = 0, any_spec = 0, any_ns = 0, any_stat = 0;
+  int any_krylov = 0, any_spec = 0, any_ns = 0, any_stat = 0, any_ar = 0;
   // Two-group schedule (batches of two or more problems): group 1 runs half a
   // step behind group 0 on a second stream, so that one group's framelet
   // sweep (HBM-bound) overlaps the other group's residual and preconditioner
@@ -138,7 +139,7 @@ size_t spec_elems(const Prob& pd) { return (size_t)pd.nblk_cols * pd.n * pd.cb; 
 // then every prime factor above 5 as a direct-sum pass (any n factors within
 // MAX_STAGES passes: n <= 4096 has at most 12 prime factors).
 bool fft_plan(Prob& pd) {
-  int m = pd.n, s = 0;
+  int m = pd.nfft, s = 0;
   pd.nr16 = pd.r2 = pd.nr3 = pd.nr5 = pd.nrany = 0;
   while (m % 16 == 0 && s < MAX_STAGES) { pd.radix[s++] = 16; m /= 16; ++pd.nr16; }
   for (int r : {8, 4, 2})
@@ -253,6 +254,12 @@ void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
       }
       launch_rows_inv<T>(P, S, L.rows_spec.dev, L.rows_spec.count, SL_T, 0, B->smem_fft, s);
     }
+    // a4 with the antireflective transform (Algorithms 1, 3, 4 on antireflective A)
+    if (L.any_ar) {
+      launch_ar_rows<T>(P, S, L.ar_rows.dev, L.ar_rows.count, SL_R, 0, 0, B->smem_fft, s);
+      launch_ar_cols<T>(P, S, L.ar_cols.dev, L.ar_cols.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
+      launch_ar_rows<T>(P, S, L.ar_rows.dev, L.ar_rows.count, SL_T, 1, 0, B->smem_fft, s);
+    }
     // a4': Algorithm 2, PCG on (A A^T + alpha I) t = r preconditioned by (CC^T + alpha I)^{-1}
     if (L.any_krylov) {
       const int maxs = L.pcg_max;
@@ -301,6 +308,7 @@ StepLists all_lists(const mlba_batch* B) {
   L.rows_kry = B->rows_kry; L.cols_kry = B->cols_kry; L.vec_kry = B->vec_kry;
   L.vec_kry_bc = B->vec_kry_bc; L.frame = B->frame;
   L.any_krylov = B->any_krylov; L.any_spec = B->any_spec; L.any_ns = B->any_ns;
+  L.ar_rows = B->ar_rows; L.ar_cols = B->ar_cols; L.any_ar = B->any_ar;
   L.pcg_max = B->hp.empty() ? 5 : B->hp[0].pd.pcg_max;
   return L;
 }
@@ -320,6 +328,9 @@ void collect_step(const Prob& pd, int i, int levels, int shape, StepItems& V) {
     add(V.cols_kry, pd.nblk_cols); add(V.vec_kry, pd.nblk_vec);
     if (pd.bc != BC_RECT) add(V.vec_kry_bc, pd.nblk_vec);
     V.any_krylov = 1;
+  } else if (pd.transform == TR_AR) {
+    add(V.ar_rows, pd.nblk_rows); add(V.ar_cols, pd.nblk_cols);
+    V.any_ar = 1;
   } else if (specp) {
     add(V.rows_spec, pd.nblk_rows);
     V.any_spec = 1;
@@ -408,7 +419,8 @@ int build_split(mlba_batch* B) {
     rc |= build_list(B, L.rows_kry, v.rows_kry); rc |= build_list(B, L.cols_kry, v.cols_kry);
     rc |= build_list(B, L.vec_kry, v.vec_kry); rc |= build_list(B, L.vec_kry_bc, v.vec_kry_bc);
     rc |= build_frame_list(B, L.frame, v.frame, B->levels);
-    L.any_krylov = v.any_krylov; L.any_spec = v.any_spec; L.any_ns = v.any_ns;
+    rc |= build_list(B, L.ar_rows, v.ar_rows); rc |= build_list(B, L.ar_cols, v.ar_cols);
+    L.any_krylov = v.any_krylov; L.any_spec = v.any_spec; L.any_ns = v.any_ns; L.any_ar = v.any_ar;
     L.pcg_max = B->hp[0].pd.pcg_max;
   }
   if (rc != MLBA_OK) return MLBA_E_CUDA;
@@ -465,10 +477,8 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   if (!in.psf || p < 1 || (p % 2) == 0 || n < p || n < 2) return MLBA_E_INVAL;
   if (p > MLBA_MAX_P) return MLBA_E_UNSUPPORTED;
   if (in.bc < 0 || in.bc > 4 || in.precond < 0 || in.precond > 5) return MLBA_E_INVAL;
-  // antireflective BCs: Algorithm 2 is of no use there (Example 4) and
-  // Algorithm 3's Q needs the antireflective transform
-  if (in.bc == MLBA_BC_ANTIREFLECTIVE && (in.precond == MLBA_P_KRYLOV || in.precond == MLBA_P_SYM))
-    return MLBA_E_INVAL;
+  // antireflective BCs: Algorithm 2 is of no use there (Example 4)
+  if (in.bc == MLBA_BC_ANTIREFLECTIVE && in.precond == MLBA_P_KRYLOV) return MLBA_E_INVAL;
   if (o.levels < 1 || o.levels > 4) return MLBA_E_INVAL;
   if (!(in.delta >= 0.0) || !(in.mu >= 0.0)) return MLBA_E_INVAL;
   const bool ns = in.precond == MLBA_P_TIKH_NS;
@@ -497,27 +507,40 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   pd.q = o.q; pd.rho = o.rho; pd.tau = (1.0 + 2.0 * o.rho) / (1.0 - 2.0 * o.rho);
   pd.pcg_tol = o.pcg_tol;
   // transform (Section 4.1 / 4.3)
+  const bool ar_bc = in.bc == MLBA_BC_ANTIREFLECTIVE;
+  if (in.transform < 0 || in.transform > 3) return MLBA_E_INVAL;
   if (in.precond == MLBA_P_NONE) {
     pd.transform = TR_NONE;
   } else if (in.precond == MLBA_P_SYM) {
-    pd.transform = TR_DCT;
+    // Section 4.3: Q from H~ under reflective BCs (DCT), or under
+    // antireflective BCs for an antireflective A (antireflective transform)
+    pd.transform = ar_bc ? TR_AR : TR_DCT;
     h.psf_pre = symmetrized(h.psf, p);
   } else {
     const int tr = in.transform;
     const bool sym = quad_symmetric(h.psf, p);
-    if (tr == MLBA_TR_DCT && !sym) return MLBA_E_INVAL;
-    // AUTO: periodic A is its own BCCB matrix (DFT); otherwise the reflective
-    // (DCT) matrix for a quadrantally symmetric PSF, the periodic one if not
-    // (antireflective BCs: the BCCB C, as Examples 3 and 4 do for Algorithms 1 and 4)
-    const int autotr = (in.bc == MLBA_BC_PERIODIC || in.bc == MLBA_BC_ANTIREFLECTIVE)
-                           ? TR_DFT : (sym ? TR_DCT : TR_DFT);
-    pd.transform = (tr == MLBA_TR_DFT) ? TR_DFT : (tr == MLBA_TR_DCT ? TR_DCT : autotr);
+    if ((tr == MLBA_TR_DCT || tr == MLBA_TR_AR) && !sym) return MLBA_E_INVAL;
+    // AUTO: periodic A is its own BCCB matrix (DFT); antireflective A is
+    // diagonalised by the antireflective transform for a quadrantally
+    // symmetric PSF (C = A) outside 4-NS, else the BCCB C as Examples 3 and 4
+    // do; otherwise the reflective (DCT) matrix for a quadrantally symmetric
+    // PSF, the periodic one if not
+    int autotr;
+    if (in.bc == MLBA_BC_PERIODIC) autotr = TR_DFT;
+    else if (ar_bc) autotr = (sym && !ns) ? TR_AR : TR_DFT;
+    else autotr = sym ? TR_DCT : TR_DFT;
+    pd.transform = (tr == MLBA_TR_DFT) ? TR_DFT
+                 : (tr == MLBA_TR_DCT ? TR_DCT : (tr == MLBA_TR_AR ? TR_AR : autotr));
     h.psf_pre = h.psf;
   }
+  // the antireflective transform serves antireflective A outside 4-NS (it is
+  // not unitary, Eq. Alg4_rev_7 is solved with spectral sums) and Algorithm 2
+  if (pd.transform == TR_AR && (!ar_bc || ns || in.precond == MLBA_P_KRYLOV)) return MLBA_E_INVAL;
+  pd.nfft = (pd.transform == TR_AR) ? 2 * (n - 1) : n;   // DST-I of n - 2 as a DFT of 2(n - 1)
   if (pd.transform != TR_NONE) {
     if (!fft_plan(pd)) return MLBA_E_UNSUPPORTED;
     // one transform must fit the per-CTA value budget of the smem FFT
-    if (n > TR_CAP) return MLBA_E_UNSUPPORTED;
+    if (pd.nfft > TR_CAP || (pd.transform == TR_AR && n < 3)) return MLBA_E_UNSUPPORTED;
   }
   // taps: per PSF column the dense run of rows between its first and last
   // nonzero entry
@@ -548,7 +571,7 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   pd.nblk_corr = stencil_tiles(pd.ne);
   // the frame kernel indexes a z array (all bands) with 32-bit offsets
   if ((double)pd.nbands * pd.nf * pd.nf >= 2147483647.0) return MLBA_E_UNSUPPORTED;
-  const int cap = TR_CAP / n;                          // transforms per CTA
+  const int cap = TR_CAP / std::max(pd.nfft, n);      // transforms per CTA
   const int pairs = (n + 1) / 2;
   {
     const int nb = (pairs + cap - 1) / cap;            // row CTAs, then pairs spread evenly
@@ -557,7 +580,8 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   }
   {
     // column blocks: as few as the cap allows, then as even as possible
-    const bool dct = pd.transform == TR_DCT;
+    // (real spectra, DCT and antireflective, move real columns in pairs)
+    const bool dct = pd.transform == TR_DCT || pd.transform == TR_AR;
     const int units = dct ? pairs : pd.half;           // complex columns to transform
     const int nb = (units + cap - 1) / cap;
     pd.col_g = std::max(1, (units + nb - 1) / nb);
@@ -575,10 +599,27 @@ int build_spectrum(mlba_batch* B, HostProb& h) {
   Prob& pd = h.pd;
   const int n = pd.n, p = pd.p, c = pd.c, half = pd.half;
   const bool dct = pd.transform == TR_DCT;
-  const int W = dct ? n : half;
+  const int W = (dct || pd.transform == TR_AR) ? n : half;
   const std::vector<double>& H = h.psf_pre;
   std::vector<double> q, tab;
-  if (dct) {
+  if (pd.transform == TR_AR) {
+    // cos(pi m/(n-1)), m < 2(n-1); angle index k for the sine vectors, 0 for
+    // the two linear ones (k = 0, n-1)
+    const int per = 2 * (n - 1);
+    tab.resize(per);
+    for (int m = 0; m < per; ++m) tab[m] = std::cos(M_PI * (double)m / (double)(n - 1));
+    q.assign((size_t)p * n, 0.0);
+    for (int a = 0; a < p; ++a)
+      for (int k2 = 0; k2 < n; ++k2) {
+        const int kk = (k2 == n - 1) ? 0 : k2;
+        double s = 0;
+        for (int b = 0; b < p; ++b) {
+          int m = (kk * (b - c)) % per; if (m < 0) m += per;
+          s += H[a * p + b] * tab[m];
+        }
+        q[(size_t)a * n + k2] = s;
+      }
+  } else if (dct) {
     tab.resize(2 * n);
     for (int m = 0; m < 2 * n; ++m) tab[m] = std::cos(M_PI * (double)m / (double)n);
     q.assign((size_t)p * n, 0.0);
@@ -821,18 +862,18 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         n2 * ts,                               // T
         ne2 * ts,                              // V
         n2 * ts,                               // U
-        nspec * ts * (pd.transform == TR_DCT ? 1 : 2),   // S
+        nspec * ts * (pd.transform == TR_DCT || pd.transform == TR_AR ? 1 : 2),   // S
         kry ? n2 * ts : ts, kry ? n2 * ts : ts, kry ? n2 * ts : ts, kry ? n2 * ts : ts,
         kry ? n2 * ts : ts,                    // PCG vectors
         aux * ts, aux * ts,                    // AUX0, AUX1
         (size_t)pd.nbands * nf2 * zs,          // z0
         (size_t)pd.nbands * nf2 * zs,          // z1
-        nspec * ts * (pd.transform == TR_DCT ? 1 : 2),   // lam
+        nspec * ts * (pd.transform == TR_DCT || pd.transform == TR_AR ? 1 : 2),   // lam
         nspec * ts,                            // |lambda|^2 in T precision
         (pd.ns ? nspec : 1) * ts,              // 4-NS weighted power
         (pd.levels >= 3 ? (size_t)(pd.levels - 1) * nf2 : 1) * ts,   // low-pass chain (L >= 3)
         (pd.levels >= 3 ? (size_t)(pd.levels - 1) * nf2 : 1) * ts,   // synthesis partials
-        spec ? (size_t)pd.n * 2 * ts : ts,     // tw
+        spec ? (size_t)pd.nfft * 2 * ts : ts,  // tw
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
         (size_t)pd.nruns * 16, 2 * (size_t)pd.nrw * ts,   // tap runs and weights (both orders)
         (size_t)pd.p * ts, (size_t)pd.p * ts,  // hy, hx
@@ -885,10 +926,12 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
       }
     }
     if (pd.transform != TR_NONE) {
-      std::vector<double> tw(2 * (size_t)pd.n), dtw(2 * (size_t)pd.n);
-      for (int m = 0; m < pd.n; ++m) {
-        const double a = 2.0 * M_PI * (double)m / (double)pd.n;
+      std::vector<double> tw(2 * (size_t)pd.nfft), dtw(2 * (size_t)pd.n);
+      for (int m = 0; m < pd.nfft; ++m) {
+        const double a = 2.0 * M_PI * (double)m / (double)pd.nfft;
         tw[2 * m] = std::cos(a); tw[2 * m + 1] = -std::sin(a);
+      }
+      for (int m = 0; m < pd.n; ++m) {
         const double b = M_PI * (double)m / (2.0 * (double)pd.n);
         dtw[2 * m] = std::cos(b); dtw[2 * m + 1] = -std::sin(b);
       }
@@ -912,7 +955,8 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   CK(cudaMemcpy(B->d_states, st_h.data(), count * sizeof(State), cudaMemcpyHostToDevice));
   // ---- item lists
   std::vector<int2> blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec,
-      rows_kry, cols_kry, vec_kry, vec_kry_bc, corr_all, rows_all, cols_all, spec_all, vec_all;
+      rows_kry, cols_kry, vec_kry, vec_kry_bc, corr_all, rows_all, cols_all, spec_all, vec_all,
+      ar_rows, ar_cols;
   size_t smem_st = 0, smem_fft = 0;
   for (int i = 0; i < count; ++i) {
     const Prob& pd = B->hp[i].pd;
@@ -931,6 +975,9 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
       add(cols_kry, pd.nblk_cols); add(vec_kry, pd.nblk_vec);
       if (pd.bc != BC_RECT) add(vec_kry_bc, pd.nblk_vec);
       B->any_krylov = 1;
+    } else if (pd.transform == TR_AR) {
+      add(ar_rows, pd.nblk_rows); add(ar_cols, pd.nblk_cols);
+      B->any_ar = 1;
     } else if (specp) {
       add(rows_spec, pd.nblk_rows);
       B->any_spec = 1;
@@ -947,7 +994,9 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
                         (pd.sep ? 0 : (size_t)pd.nruns * 16);
     smem_st = std::max(smem_st, st_b);
     if (specp) {
-      const size_t fb = (size_t)std::max(pd.row_g, pd.col_g) * (fft_pad(pd.n) + 1) * 2 * ts;
+      // (antireflective columns also keep two weighted end values per transform)
+      const size_t fb = (size_t)std::max(pd.row_g, pd.col_g) * (fft_pad(pd.nfft) + 1) * 2 * ts +
+                        (pd.transform == TR_AR ? (size_t)pd.col_g * 4 * ts : 0);
       smem_fft = std::max(smem_fft, fb);
     }
   }
@@ -964,6 +1013,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   rc |= build_list(B, B->corr_all, corr_all);
   rc |= build_list(B, B->rows_all, rows_all); rc |= build_list(B, B->cols_all, cols_all);
   rc |= build_list(B, B->spec_all, spec_all); rc |= build_list(B, B->vec_all, vec_all);
+  rc |= build_list(B, B->ar_rows, ar_rows); rc |= build_list(B, B->ar_cols, ar_cols);
   if (rc != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
   if (set_smem_attrs(B) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
   // ---- framelet tile shape, then the framelet list in that shape
@@ -1181,6 +1231,9 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
         launch_cols<double>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
         launch_cols<double>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
         launch_rows_inv<double>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
+        launch_ar_rows<double>(P, S, B->ar_rows.dev, B->ar_rows.count, SL_R, 0, 0, B->smem_fft, s);
+        launch_ar_cols<double>(P, S, B->ar_cols.dev, B->ar_cols.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
+        launch_ar_rows<double>(P, S, B->ar_rows.dev, B->ar_rows.count, SL_T, 1, 0, B->smem_fft, s);
       }
       if (stage == 3) {
         launch_stencil<double>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
@@ -1195,6 +1248,9 @@ int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
         launch_cols<float>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
         launch_cols<float>(P, S, B->cols_ns.dev, B->cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
         launch_rows_inv<float>(P, S, B->rows_spec.dev, B->rows_spec.count, SL_T, 0, B->smem_fft, s);
+        launch_ar_rows<float>(P, S, B->ar_rows.dev, B->ar_rows.count, SL_R, 0, 0, B->smem_fft, s);
+        launch_ar_cols<float>(P, S, B->ar_cols.dev, B->ar_cols.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
+        launch_ar_rows<float>(P, S, B->ar_rows.dev, B->ar_rows.count, SL_T, 1, 0, B->smem_fft, s);
       }
       if (stage == 3) {
         launch_stencil<float>(ST_CORR, P, S, B->corr.dev, B->corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
@@ -1549,6 +1605,19 @@ int mlba_op_precond(mlba_ctx* c, const void* r, void* out, double alpha, int whi
   int rc = copy_in(B, pd.buf[SL_AUX0], r, (size_t)pd.n * pd.n * ts, on_device);
   if (rc != MLBA_OK) return rc;
   if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
+  if (pd.transform == TR_AR) {
+    if (B->dtype == MLBA_F64) {
+      launch_ar_rows<double>(B->d_probs, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX0, 0, 0, B->smem_fft, B->stream);
+      launch_ar_cols<double>(B->d_probs, B->d_opstates, B->cols_all.dev, B->cols_all.count, COL_OP, 0, alpha, which, B->smem_fft, B->stream);
+      launch_ar_rows<double>(B->d_probs, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX1, 1, 0, B->smem_fft, B->stream);
+    } else {
+      launch_ar_rows<float>(B->d_probs, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX0, 0, 0, B->smem_fft, B->stream);
+      launch_ar_cols<float>(B->d_probs, B->d_opstates, B->cols_all.dev, B->cols_all.count, COL_OP, 0, alpha, which, B->smem_fft, B->stream);
+      launch_ar_rows<float>(B->d_probs, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX1, 1, 0, B->smem_fft, B->stream);
+    }
+    CK(cudaGetLastError());
+    return copy_out(B, out, pd.buf[SL_AUX1], (size_t)pd.n * pd.n * ts, on_device);
+  }
   if (B->dtype == MLBA_F64) {
     launch_rows_fwd<double>(B->d_probs, B->d_opstates, B->rows_all.dev, B->rows_all.count, SL_AUX0, 0, B->smem_fft, B->stream);
     launch_cols<double>(B->d_probs, B->d_opstates, B->cols_all.dev, B->cols_all.count, COL_OP, 0, alpha, which, B->smem_fft, B->stream);
@@ -1621,7 +1690,7 @@ int mlba_op_ns_alpha(mlba_ctx* c, const void* r, double qn, double* alpha_out, i
   if (!c || !alpha_out || !(qn > 0.0 && qn < 1.0)) return MLBA_E_INVAL;
   mlba_batch* B = c->b;
   const Prob& pd = B->hp[0].pd;
-  if (pd.transform == TR_NONE) return MLBA_E_INVAL;
+  if (pd.transform == TR_NONE || pd.transform == TR_AR) return MLBA_E_INVAL;
   const size_t ts = tsize(B->dtype);
   int rc = copy_in(B, pd.buf[SL_AUX0], r, (size_t)pd.n * pd.n * ts, on_device);
   if (rc != MLBA_OK) return rc;
@@ -1664,7 +1733,7 @@ int mlba_op_spectrum(mlba_ctx* c, double* out, int* rows, int* cols, int* is_com
   mlba_batch* B = c->b;
   const Prob& pd = B->hp[0].pd;
   if (pd.transform == TR_NONE) return MLBA_E_INVAL;
-  const bool dct = pd.transform == TR_DCT;
+  const bool dct = pd.transform == TR_DCT || pd.transform == TR_AR;   // real spectra
   const size_t W = dct ? pd.n : pd.half;
   const int comps = dct ? 1 : 2;
   const size_t cnt = spec_elems(pd) * comps;

@@ -14,7 +14,7 @@ namespace mlba {
 // enumerations mirrored from include/mlba.h
 enum { BC_ZERO = 0, BC_PERIODIC = 1, BC_REFLECTIVE = 2, BC_RECT = 3, BC_AR = 4 };
 enum { P_NONE = 0, P_BCCB = 1, P_KRYLOV = 2, P_SYM = 3, P_TIKH = 4, P_TIKH_NS = 5 };
-enum { TR_NONE = 0, TR_DFT = 1, TR_DCT = 2 };
+enum { TR_NONE = 0, TR_DFT = 1, TR_DCT = 2, TR_AR = 3 };
 
 // per-problem buffer slots; kernels pick their operands by slot so that the
 // same kernel serves the main loop, the PCG of Algorithm 2 and the operator
@@ -45,7 +45,8 @@ struct Prob {
   int ntaps;         // nonzero taps of the PSF
   int nruns, nrw;    // PSF column runs and their packed weights (general PSF)
   int max_iter, stop, pcg_max;
-  int nstage;        // FFT plan of length n
+  int nfft;          // FFT length: n (DFT, DCT) or 2(n - 1) (antireflective transform)
+  int nstage;        // FFT plan of length nfft
   int radix[MAX_STAGES];
   int nr16, r2, nr3, nr5;   // the same plan: radix-16 passes, one 8/4/2 pass, 3s, 5s,
   int nrany;                // then the prime factors above 5 (direct-sum passes)
@@ -66,7 +67,7 @@ struct Prob {
   void* lam;         // spectrum of C (real for DCT, complex half for DFT), T, blocked
   void* lp;          // L >= 3: low-pass chain c_1 .. c_{L-1} (nf x nf planes, T)
   void* sy;          // L >= 3: synthesis partials s_1 .. s_{L-1} (nf x nf planes, T)
-  void* tw;          // exp(-2 pi i k/n), k < n   (T2)
+  void* tw;          // exp(-2 pi i k/nfft), k < nfft   (T2)
   void* dtw;         // exp(-i pi k/(2n)), k < n  (T2)
   int4* tap_runs;     // per nonzero PSF column b: (b, lo, hi, offset of H[lo..hi][b] in tap_w)
   void* tap_w;        // packed run weights, T precision: nrw in PSF order, then nrw with

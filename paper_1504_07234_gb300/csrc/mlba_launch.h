@@ -63,6 +63,15 @@ void launch_rows_inv(const Prob* probs, State* states, const int2* items, int ni
 template <typename T>
 void launch_spec(const Prob* probs, State* states, const int2* items, int nitems, int cand,
                  cudaStream_t s);
+// antireflective transform passes (k_fft.cu): rows (inv = 0: T^{-1} of
+// buf[slot] into S; inv = 1: T of S into buf[slot]) and the column pass
+// (T^{-1}, weight, T; mode COL_FUSED or COL_OP)
+template <typename T>
+void launch_ar_rows(const Prob* probs, State* states, const int2* items, int nitems, int slot,
+                    int inv, int pcg, size_t smem, cudaStream_t s);
+template <typename T>
+void launch_ar_cols(const Prob* probs, State* states, const int2* items, int nitems, int mode,
+                    int pcg, double op_alpha, int op_kind, size_t smem, cudaStream_t s);
 void launch_spectrum_setup(int transform, int n, int p, int half, int cb, const double* q_dev,
                            const double* tab_dev, void* lam, void* sigT, int is_double,
                            cudaStream_t s);

@@ -193,11 +193,37 @@ def test_antireflective_batch_with_other_bcs(M, levels):
     b.close()
 
 
-def test_antireflective_rejects_alg2_and_alg3(M):
-    h = I.psf_motion(7, 0.9)
-    for pc in ("krylov", "sym"):
-        with pytest.raises(M.MlbaError):
-            M.Context(h, 40, "antireflective", pc, dtype="f64")
+AR_TR_CASES = [("bccb", I.psf_gaussian(1.5, 7), 0.1),     # auto: the antireflective transform, C = A
+               ("tikh", I.psf_disk(3), 0.05),
+               ("sym", I.psf_motion(7, 0.9), 0.3)]        # Q from H~ under antireflective BCs
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("precond,psf,alpha", AR_TR_CASES, ids=[c[0] for c in AR_TR_CASES])
+def test_antireflective_transform_loop_matches_oracle(M, dtype, precond, psf, alpha):
+    """Alg-BC1 / BC4 with C = A and Alg-BC3 (Q = antireflective matrix of H~,
+    Section 4.3) through the antireflective transform, as the paper runs
+    Examples 3 and 4."""
+    pr = small("antireflective", precond, n=61, psf=psf, alpha=alpha, iters=10)
+    f, st, res, al, be = run_gpu(M, pr, dtype)
+    ref = run_oracle(pr)
+    assert st["iter"] == ref["iters"]
+    if dtype == "f64":
+        assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-9)
+    else:
+        restoration_bars(f, ref, pr)
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-3)
+
+
+def test_antireflective_rejects_alg2_and_ns_transform(M):
+    h = I.psf_gaussian(1.5, 7)
+    with pytest.raises(M.MlbaError):
+        M.Context(h, 40, "antireflective", "krylov", dtype="f64")
+    with pytest.raises(M.MlbaError):
+        M.Context(h, 40, "antireflective", "tikh_ns", dtype="f64", transform="ar")
+    with pytest.raises(M.MlbaError):
+        M.Context(h, 40, "reflective", "bccb", dtype="f64", transform="ar")
 
 
 def test_fp64_stop_rule_matches_oracle(M):

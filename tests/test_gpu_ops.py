@@ -188,3 +188,25 @@ def test_frame_step_every_tile_shape(M, zs, shape, levels):
         assert rel_err(zo.double().cpu().numpy(), z_ref) <= (2e-6 if zs == "f32" else 1e-2)
         assert rel_err(f.double().cpu().numpy(), f_ref) <= 1e-5
         ctx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n", [3, 17, 48, 100, 197, 256])
+@pytest.mark.parametrize("psf", ["gauss9", "disk2"])
+def test_antireflective_transform_precond(M, dtype, n, psf):
+    """The antireflective transform (Section 2.2) for antireflective BCs and a
+    quadrantally symmetric PSF: eigenvalues and (CC' + alpha I)^{-1},
+    C'(CC' + alpha I)^{-1} against the oracle's dense transform."""
+    h = PSFS[psf]
+    if h.shape[0] > n:
+        h = I.psf_gaussian(0.6, 3)
+    ctx = M.Context(h, n, "antireflective", "bccb", dtype=dtype, transform="ar")
+    pre = O.SpectralPrecond(h, n, "ar")
+    assert float(np.abs(ctx.spectrum() - pre.lam).max()) <= (1e-13 if dtype == "f64" else 2e-7)
+    r = np.random.default_rng(n + 7).standard_normal((n, n))
+    for which in ("inv", "tikh"):
+        for alpha in (0.05, 1e-3):
+            ref = pre.inv(r, alpha) if which == "inv" else pre.tikh(r, alpha)
+            got = ctx.precond(r, alpha, which)
+            assert rel_err(got, ref) <= (1e-11 if dtype == "f64" else 2e-5), (which, alpha)
+    ctx.close()
