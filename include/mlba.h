@@ -119,6 +119,13 @@ typedef struct mlba_opts {
                          unwritable cache is skipped); 2 measure, ignoring the cache.  Every
                          shape computes the same values; only the time differs. */
   int frame_shape;    /* -1 (default): as autotune says; 0 .. MLBA_FRAME_SHAPES - 1: force it */
+  int blur_path;      /* how A and A^T (A' for antireflective BCs) are applied (Sections 2.1,
+                         2.2): 0 (default) direct stencils with the BCs in the index math;
+                         1 FFT convolution on a 2^a 3^b 5^c size M >= n + p - 1 (the input
+                         padded by the BCs, the PSF's DFT as the multiplier) for every problem
+                         where M <= 4096 and the algorithm is not 2 (its PCG keeps the
+                         stencils); 2 per problem the faster of the two, measured at create.
+                         Both compute the same operator (to rounding). */
 } mlba_opts;
 
 #define MLBA_FRAME_SHAPES 8
@@ -126,7 +133,7 @@ typedef struct mlba_opts {
 /* Fill defaults: mu = 10/255, alpha = 0.05, gamma = 1 + 1e-15, q = 0.5,
  * rho = 1e-4, pcg_tol = 1e-3, levels = 1, max_iter = 200, pcg_max = 5,
  * dtype = F32, z_store = F32, transform = AUTO, stop = 1, hybrid = 0,
- * stream = NULL, two_group = 1, autotune = 0, frame_shape = -1. */
+ * stream = NULL, two_group = 1, autotune = 0, frame_shape = -1, blur_path = 0. */
 void mlba_opts_default(mlba_opts* o);
 
 /* ---- statistics ------------------------------------------------------- */
@@ -280,6 +287,10 @@ int mlba_batch_tiles(mlba_batch* b, int* frame_shape, int* tile_x, int* tile_y, 
                      int* how, float* us);
 int mlba_tiles(mlba_ctx* ctx, int* frame_shape, int* tile_x, int* tile_y, int* prefetch, int* how,
                float* us);
+/* Whether problem i applies A and A^T by FFT convolution (opts.blur_path) and
+ * the convolution size M (0 on the direct path).  No counterpart in the paper
+ * beyond Section 2's remark that A is applied by FFTs after padding. */
+int mlba_batch_blur_fft(mlba_batch* b, int i, int* uses_fft, int* size);
 
 /* ---- entry point that allocates no device memory ------------------------
  * The paper has no counterpart: this is a service for callers that cannot

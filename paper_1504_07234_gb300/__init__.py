@@ -43,7 +43,8 @@ class Opts(ctypes.Structure):
                 ("dtype", ctypes.c_int), ("z_store", ctypes.c_int), ("transform", ctypes.c_int),
                 ("stop", ctypes.c_int), ("rect_ns_hybrid", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("two_group", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("frame_shape", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("frame_shape", ctypes.c_int),
+                ("blur_path", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -97,6 +98,7 @@ SIGNATURES = {
     "mlba_batch_destroy": (None, [_P]),
     "mlba_batch_tiles": (_I, [_P] + [ctypes.POINTER(_I)] * 5 + [ctypes.POINTER(ctypes.c_float)]),
     "mlba_tiles": (_I, [_P] + [ctypes.POINTER(_I)] * 5 + [ctypes.POINTER(ctypes.c_float)]),
+    "mlba_batch_blur_fft": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mlba_residual_noalloc": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
 }
 
@@ -136,7 +138,7 @@ def _torch():
 def make_opts(dtype="f32", z_store=None, mu=10.0 / 255.0, alpha=0.05, levels=1, max_iter=200,
               stop=True, gamma=1.0 + 1e-15, q=0.5, rho=1e-4, transform="auto", pcg_tol=1e-3,
               pcg_max=5, rect_ns_hybrid=False, stream=None, two_group=True, autotune=0,
-              frame_shape=-1) -> Opts:
+              frame_shape=-1, blur_path=0) -> Opts:
     lib = load_library()
     o = Opts()
     lib.mlba_opts_default(ctypes.byref(o))
@@ -151,6 +153,7 @@ def make_opts(dtype="f32", z_store=None, mu=10.0 / 255.0, alpha=0.05, levels=1, 
     o.two_group = 1 if two_group else 0
     o.autotune = int(autotune)
     o.frame_shape = int(frame_shape)
+    o.blur_path = {"direct": 0, "fft": 1, "auto": 2}.get(blur_path, blur_path)
     return o
 
 
@@ -482,6 +485,13 @@ class Batch(_Base):
     def tiles(self):
         """Tile shape of the framelet launch and how it was chosen."""
         return _tiles(self.lib.mlba_batch_tiles, self.h)
+
+    def blur_fft(self, i):
+        """(uses FFT convolution, convolution size) of problem i."""
+        u, m = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.mlba_batch_blur_fft(self.h, int(i), ctypes.byref(u), ctypes.byref(m)),
+               "mlba_batch_blur_fft")
+        return bool(u.value), m.value
 
     def graph_kernels(self):
         k = ctypes.c_int()

@@ -708,7 +708,7 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
-  if (tr_skip(states[item.x], pcg)) return;
+  if (tr_skip(states[pd.sidx], pcg)) return;
   const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
   const int pair0 = item.y * G;
   const int row0 = 2 * pair0;
@@ -888,7 +888,7 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
-  State& st = states[item.x];
+  State& st = states[pd.sidx];
   if (tr_skip(st, pcg)) return;
   if (mode == COL_NS_INV && !pd.ns) return;
   // Algorithm 4-NS: the forward pass also runs the bracketing pass of alpha_n
@@ -1117,7 +1117,7 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
-  if (tr_skip(states[item.x], pcg)) return;
+  if (tr_skip(states[pd.sidx], pcg)) return;
   const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
   const int row0 = 2 * item.y * G;
   const bool dct = (pd.transform == TR_DCT);

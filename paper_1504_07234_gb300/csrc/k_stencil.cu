@@ -580,6 +580,136 @@ k_vec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Blur by FFT convolution (Section 2.1 and 2.2: A and A^T applied with FFTs
+// after padding).  Each problem on this path has two convolution entries in
+// the problem table, forward and adjoint, of size M >= m = n + p - 1 (their
+// `sidx` is the problem), whose spectra are conj(H^) and H^ (H^ = DFT of the
+// PSF centred at the origin) with |lambda|^2 = 0, so that the spectral
+// column pass with alpha = 1 and the Algorithm-4 weight conj(lambda)/M^2
+// multiplies by H^/M^2 (convolution) or conj(H^)/M^2 (correlation).
+// Circular convolution of size M >= m has no wrap-around on the samples used:
+//   forward:  X = f extended by the BCs (m x m, zero beyond), Y = X (*) h,
+//             (A f)(i, j) = Y(i + c, j + c);
+//   adjoint:  X = t at offset (c, c), Y = X (x) h, V(a, b) = Y(a, b), a, b < m
+//             (antireflective BCs: X = t extended antireflectively,
+//             (A' t)(i, j) = Y(i + c, j + c)).
+
+// 1-D antireflection of an extended index into up to two (index, weight) terms
+template <typename T>
+__device__ __forceinline__ int fc_ar_terms(int e, int n, int (&ix)[2], T (&wt)[2]) {
+  if (e >= 0 && e < n) { ix[0] = e; wt[0] = T(1); return 1; }
+  const int k = e < 0 ? -e : e - (n - 1);
+  if (k > n - 1) return 0;
+  ix[0] = e < 0 ? 0 : n - 1;
+  ix[1] = e < 0 ? k : n - 1 - k;
+  wt[0] = T(2); wt[1] = T(-1);
+  return 2;
+}
+
+// X of a convolution entry (item.x) from its problem's image: src_slot < 0
+// takes f (forward) or t (r for P = I) (adjoint)
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_fc_pad(const Prob* __restrict__ probs, const State* __restrict__ states,
+         const int2* __restrict__ items, int adj, int src_slot) {
+  const int2 item = items[blockIdx.x];
+  const Prob& sh = probs[item.x];
+  const Prob& pd = probs[sh.sidx];
+  if (states[sh.sidx].stopped) return;
+  const int M = sh.n, n = pd.n, c = pd.c, m = pd.ne;
+  const size_t MM = (size_t)M * M;
+  if (src_slot < 0) src_slot = adj ? (pd.precond == P_NONE ? SL_R : SL_T) : SL_F;
+  const T* src = static_cast<const T*>(pd.buf[src_slot]);
+  T* X = static_cast<T*>(sh.buf[SL_R]);
+  const bool ext = !adj || pd.bc == BC_AR;          // BC-extended input on [0, m)^2
+  const size_t beg = (size_t)item.y * VEC_THREADS * VEC_PER_THREAD;
+  for (size_t e = beg + threadIdx.x; e < beg + VEC_THREADS * VEC_PER_THREAD && e < MM; e += VEC_THREADS) {
+    const int y = (int)(e / M), x = (int)(e - (size_t)y * M);
+    T v = T(0);
+    if (ext) {
+      if (y < m && x < m) {
+        if (pd.bc == BC_RECT) {
+          v = src[(size_t)y * m + x];
+        } else if (pd.bc == BC_AR) {
+          int iy[2], ix[2];
+          T wy[2], wx[2];
+          const int ny = fc_ar_terms<T>(y - c, n, iy, wy), nx = fc_ar_terms<T>(x - c, n, ix, wx);
+          for (int a = 0; a < ny; ++a)
+            for (int b = 0; b < nx; ++b) v += wy[a] * wx[b] * src[(size_t)iy[a] * n + ix[b]];
+        } else {
+          const int sy = bc_map(y - c, n, pd.bc), sx = bc_map(x - c, n, pd.bc);
+          if (sy >= 0 && sx >= 0) v = src[(size_t)sy * n + sx];
+        }
+      }
+    } else if (y >= c && y < c + n && x >= c && x < c + n) {
+      v = src[(size_t)(y - c) * n + (x - c)];
+    }
+    X[e] = v;
+  }
+}
+
+// from the convolution entry's Y to the problem (item.x = problem):
+//   FC_RESID: r = g - Y(i + c, j + c), ||r||^2 and the stop rule (as the
+//             residual stencil), FC_STORE: dst = Y(i + c, j + c) (n x n),
+//   FC_CORR: V = Y on [0, m)^2
+enum { FC_RESID = 0, FC_STORE = 1, FC_CORR = 2 };
+template <typename T, int MODE>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_fc_out(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+         int adj, int dst_slot) {
+  __shared__ double red[32];
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  State& st = states[item.x];
+  if (st.stopped) return;
+  const Prob& sh = probs[pd.fc_sh[adj]];
+  const int M = sh.n, n = pd.n, c = pd.c, m = pd.ne;
+  const T* Y = static_cast<const T*>(sh.buf[SL_T]);
+  const int w = (MODE == FC_CORR) ? m : n;
+  const size_t tot = (size_t)w * w;
+  const int off = (MODE == FC_CORR) ? 0 : c;
+  T* dst = static_cast<T*>(pd.buf[dst_slot]);
+  const T* g = static_cast<const T*>(pd.buf[SL_G]);
+  const size_t beg = (size_t)item.y * VEC_THREADS * VEC_PER_THREAD;
+  T lacc = T(0);
+  for (size_t e = beg + threadIdx.x; e < beg + VEC_THREADS * VEC_PER_THREAD && e < tot; e += VEC_THREADS) {
+    const int y = (int)(e / w), x = (int)(e - (size_t)y * w);
+    const T yv = Y[(size_t)(y + off) * M + (x + off)];
+    if (MODE == FC_RESID) {
+      const T r = g[e] - yv;
+      dst[e] = r;
+      lacc += r * r;
+    } else {
+      dst[e] = yv;
+    }
+  }
+  if (MODE == FC_RESID) {
+    // (each thread's terms in T, FP64 from the block sum on, fixed order)
+    const double bs = block_sum<VEC_THREADS>((double)lacc, red);
+    const double vals[1] = {bs};
+    double tot1[1];
+    if (last_block_reduce<VEC_THREADS, 1>(pd, st, item.y, pd.nblk_vec, vals, tot1, red) &&
+        threadIdx.x == 0)
+      finalize_residual(pd, st, tot1[0]);
+  }
+}
+
+template <typename T>
+void launch_fc_pad(const Prob* probs, State* states, const int2* items, int nitems, int adj,
+                   int src_slot, cudaStream_t s) {
+  if (nitems > 0) k_fc_pad<T><<<nitems, VEC_THREADS, 0, s>>>(probs, states, items, adj, src_slot);
+}
+template <typename T>
+void launch_fc_out(const Prob* probs, State* states, const int2* items, int nitems, int mode,
+                   int adj, int dst_slot, cudaStream_t s) {
+  if (nitems <= 0) return;
+  if (mode == FC_RESID) k_fc_out<T, FC_RESID><<<nitems, VEC_THREADS, 0, s>>>(probs, states, items, adj, dst_slot);
+  else if (mode == FC_STORE) k_fc_out<T, FC_STORE><<<nitems, VEC_THREADS, 0, s>>>(probs, states, items, adj, dst_slot);
+  else k_fc_out<T, FC_CORR><<<nitems, VEC_THREADS, 0, s>>>(probs, states, items, adj, dst_slot);
+}
+
 // ---------------------------------------------------------------------------
 template <typename T>
 void launch_stencil(int mode, const Prob* probs, State* states, const int2* items, int nitems,
@@ -629,6 +759,10 @@ template void launch_stencil<float>(int, const Prob*, State*, const int2*, int, 
 template void launch_stencil<double>(int, const Prob*, State*, const int2*, int, int, int, int, int, size_t, cudaStream_t);
 template cudaError_t stencil_set_smem<float>(size_t);
 template cudaError_t stencil_set_smem<double>(size_t);
+template void launch_fc_pad<float>(const Prob*, State*, const int2*, int, int, int, cudaStream_t);
+template void launch_fc_pad<double>(const Prob*, State*, const int2*, int, int, int, cudaStream_t);
+template void launch_fc_out<float>(const Prob*, State*, const int2*, int, int, int, int, cudaStream_t);
+template void launch_fc_out<double>(const Prob*, State*, const int2*, int, int, int, int, cudaStream_t);
 template void launch_vec<float>(int, const Prob*, State*, const int2*, int, int, cudaStream_t);
 template void launch_vec<double>(int, const Prob*, State*, const int2*, int, int, cudaStream_t);
 

@@ -54,11 +54,16 @@ struct ItemList {
 struct StepLists {
   ItemList blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
       cols_kry, vec_kry, vec_kry_bc, frame, ar_rows, ar_cols;
+  // FFT blur path: forward (f) and adjoint (a) convolution entries, and the
+  // epilogues on the problems (residual, correlation V, reblurring into U)
+  ItemList fc_pad_f, fc_rows_f, fc_cols_f, fc_out_r, fc_pad_a, fc_rows_a, fc_cols_a, fc_out_v, fc_out_u;
   int any_krylov = 0, any_spec = 0, any_ns = 0, any_ar = 0, pcg_max = 5;
 };
 struct StepItems {
   std::vector<int2> blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec,
       rows_kry, cols_kry, vec_kry, vec_kry_bc, ar_rows, ar_cols;
+  std::vector<int2> fc_pad_f, fc_rows_f, fc_cols_f, fc_out_r, fc_pad_a, fc_rows_a, fc_cols_a,
+      fc_out_v, fc_out_u;
   std::vector<int2> frame[FRAME_SECTIONS];   // see add_frame_items
   int any_krylov = 0, any_spec = 0, any_ns = 0, any_ar = 0, pcg_max = 5;
 };
@@ -96,6 +101,11 @@ struct mlba_batch {
   ItemList blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
       cols_kry, vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all,
       ar_rows, ar_cols;
+  // FFT blur path (see StepLists); the *_all_f / *_all_a lists hold every
+  // convolution entry and serve the operator entry points
+  ItemList fc_pad_f, fc_rows_f, fc_cols_f, fc_out_r, fc_pad_a, fc_rows_a, fc_cols_a, fc_out_v, fc_out_u;
+  std::vector<HostProb> fc;      // convolution entries, table indices count + k
+  int blur_path = 0;
   std::vector<int2*> allocs;
   size_t smem_stencil = 0, smem_fft = 0;
   cudaGraph_t graph = nullptr;
@@ -133,6 +143,9 @@ size_t al(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 // elements of the column-blocked spectrum (padding of the last block included)
 int fft_pad(int i) { return i + (i >> 4); }   // shared-memory slot of element i (k_fft.cu)
 size_t spec_elems(const Prob& pd) { return (size_t)pd.nblk_cols * pd.n * pd.cb; }
+int vec_blocks(size_t elems) {
+  return (int)((elems + VEC_THREADS * VEC_PER_THREAD - 1) / (VEC_THREADS * VEC_PER_THREAD));
+}
 
 // Radix passes of the length-n FFT: as many radix-16 passes as divide n, then
 // at most one of 8, 4 or 2 for the rest of the power of two, then 3s and 5s,
@@ -211,6 +224,16 @@ int build_list(mlba_batch* B, ItemList& L, const std::vector<int2>& items) {
   return MLBA_OK;
 }
 
+int build_fc_lists(mlba_batch* B, StepLists& L, const StepItems& v) {
+  int rc = MLBA_OK;
+  rc |= build_list(B, L.fc_pad_f, v.fc_pad_f); rc |= build_list(B, L.fc_rows_f, v.fc_rows_f);
+  rc |= build_list(B, L.fc_cols_f, v.fc_cols_f); rc |= build_list(B, L.fc_out_r, v.fc_out_r);
+  rc |= build_list(B, L.fc_pad_a, v.fc_pad_a); rc |= build_list(B, L.fc_rows_a, v.fc_rows_a);
+  rc |= build_list(B, L.fc_cols_a, v.fc_cols_a); rc |= build_list(B, L.fc_out_v, v.fc_out_v);
+  rc |= build_list(B, L.fc_out_u, v.fc_out_u);
+  return rc;
+}
+
 // the framelet list: one section (levels <= 2) or the sections concatenated
 int build_frame_list(mlba_batch* B, ItemList& L, const std::vector<int2> (&fs)[FRAME_SECTIONS],
                      int levels) {
@@ -242,6 +265,14 @@ void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
     // a2: r = g - A f with ||r||^2 and the stop rule
     launch_stencil<T>(ST_FWD_RESID, P, S, L.blur.dev, L.blur.count, SL_F, SL_R, SL_G, 0,
                       B->smem_stencil, s);
+    // (FFT blur path: f extended by the BCs, A f by convolution with the PSF)
+    if (L.fc_out_r.count) {
+      launch_fc_pad<T>(P, S, L.fc_pad_f.dev, L.fc_pad_f.count, 0, -1, s);
+      launch_rows_fwd<T>(P, S, L.fc_rows_f.dev, L.fc_rows_f.count, SL_R, 0, B->smem_fft, s);
+      launch_cols<T>(P, S, L.fc_cols_f.dev, L.fc_cols_f.count, COL_OP, 0, 1.0, W_TIKH, B->smem_fft, s);
+      launch_rows_inv<T>(P, S, L.fc_rows_f.dev, L.fc_rows_f.count, SL_T, 0, B->smem_fft, s);
+      launch_fc_out<T>(P, S, L.fc_out_r.dev, L.fc_out_r.count, FC_RESID_MODE, 0, SL_R, s);
+    }
     // a4: spectral preconditioners (Algorithms 1, 3, 4, 4-NS)
     if (L.any_spec) {
       launch_rows_fwd<T>(P, S, L.rows_spec.dev, L.rows_spec.count, SL_R, 0, B->smem_fft, s);
@@ -289,6 +320,16 @@ void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
     // the reblurring A' t into U
     launch_stencil<T>(ST_CORR, P, S, L.corr.dev, L.corr.count, -1, SL_V, SL_V, 0, B->smem_stencil, s);
     launch_stencil<T>(ST_REBLUR, P, S, L.reblur.dev, L.reblur.count, -1, -1, SL_U, 0, B->smem_stencil, s);
+    // (FFT blur path: t placed at (c, c), or extended antireflectively, and
+    // correlated with the PSF)
+    if (L.fc_pad_a.count) {
+      launch_fc_pad<T>(P, S, L.fc_pad_a.dev, L.fc_pad_a.count, 1, -1, s);
+      launch_rows_fwd<T>(P, S, L.fc_rows_a.dev, L.fc_rows_a.count, SL_R, 0, B->smem_fft, s);
+      launch_cols<T>(P, S, L.fc_cols_a.dev, L.fc_cols_a.count, COL_OP, 0, 1.0, W_TIKH, B->smem_fft, s);
+      launch_rows_inv<T>(P, S, L.fc_rows_a.dev, L.fc_rows_a.count, SL_T, 0, B->smem_fft, s);
+      launch_fc_out<T>(P, S, L.fc_out_v.dev, L.fc_out_v.count, FC_CORR_MODE, 1, SL_V, s);
+      launch_fc_out<T>(P, S, L.fc_out_u.dev, L.fc_out_u.count, FC_STORE_MODE, 1, SL_U, s);
+    }
     // a1: z += W u, x = S_mu(z), f = W^T x
     launch_frame<T, TZ>(P, S, L.frame.dev, L.frame.count, L.frame.sec, -1, SL_F, nullptr, nullptr,
                         0.0, B->levels, B->frame_shape, s);
@@ -309,16 +350,33 @@ StepLists all_lists(const mlba_batch* B) {
   L.vec_kry_bc = B->vec_kry_bc; L.frame = B->frame;
   L.any_krylov = B->any_krylov; L.any_spec = B->any_spec; L.any_ns = B->any_ns;
   L.ar_rows = B->ar_rows; L.ar_cols = B->ar_cols; L.any_ar = B->any_ar;
+  L.fc_pad_f = B->fc_pad_f; L.fc_rows_f = B->fc_rows_f; L.fc_cols_f = B->fc_cols_f;
+  L.fc_out_r = B->fc_out_r; L.fc_pad_a = B->fc_pad_a; L.fc_rows_a = B->fc_rows_a;
+  L.fc_cols_a = B->fc_cols_a; L.fc_out_v = B->fc_out_v; L.fc_out_u = B->fc_out_u;
   L.pcg_max = B->hp.empty() ? 5 : B->hp[0].pd.pcg_max;
   return L;
 }
 
 // the launches of one step of problem i (kinds as in the whole-batch lists)
+// The FFT-blur-path launches of problem i (pd.fc set): its forward and
+// adjoint convolution entries sf, sa (their own geometry), and the epilogues
+void collect_fc(const Prob& pd, int i, const Prob& sf, const Prob& sa, StepItems& V) {
+  auto addk = [&](std::vector<int2>& L, int x, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(x, k)); };
+  const int fi = pd.fc_sh[0], ai = pd.fc_sh[1];
+  addk(V.fc_pad_f, fi, sf.nblk_vec); addk(V.fc_rows_f, fi, sf.nblk_rows); addk(V.fc_cols_f, fi, sf.nblk_cols);
+  addk(V.fc_out_r, i, pd.nblk_vec);
+  if (pd.use_adj) {
+    addk(V.fc_pad_a, ai, sa.nblk_vec); addk(V.fc_rows_a, ai, sa.nblk_rows); addk(V.fc_cols_a, ai, sa.nblk_cols);
+    if (pd.bc == BC_AR) addk(V.fc_out_u, i, pd.nblk_vec);
+    else addk(V.fc_out_v, i, vec_blocks((size_t)pd.ne * pd.ne));
+  }
+}
+
 void collect_step(const Prob& pd, int i, int levels, int shape, StepItems& V) {
   auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
-  add(V.blur, pd.nblk_blur);
+  if (!pd.fc) add(V.blur, pd.nblk_blur);
   add_frame_items(pd, i, levels, shape, V.frame);
-  if (pd.use_adj) {
+  if (pd.use_adj && !pd.fc) {
     if (pd.bc == BC_AR) add(V.reblur, pd.nblk_blur);
     else add(V.corr, pd.nblk_corr);
   }
@@ -406,7 +464,12 @@ int build_split(mlba_batch* B) {
   double w[2] = {0.0, 0.0};
   for (int i : order) { const int g = w[1] < w[0] ? 1 : 0; grp[i] = g; w[g] += work(i); }
   StepItems V[2];
-  for (int i = 0; i < count; ++i) collect_step(B->hp[i].pd, i, B->levels, B->frame_shape, V[grp[i]]);
+  for (int i = 0; i < count; ++i) {
+    const Prob& pd = B->hp[i].pd;
+    collect_step(pd, i, B->levels, B->frame_shape, V[grp[i]]);
+    if (pd.fc)
+      collect_fc(pd, i, B->fc[pd.fc_sh[0] - count].pd, B->fc[pd.fc_sh[1] - count].pd, V[grp[i]]);
+  }
   int rc = MLBA_OK;
   for (int g = 0; g < 2; ++g) {
     StepLists& L = B->grp[g];
@@ -420,6 +483,7 @@ int build_split(mlba_batch* B) {
     rc |= build_list(B, L.vec_kry, v.vec_kry); rc |= build_list(B, L.vec_kry_bc, v.vec_kry_bc);
     rc |= build_frame_list(B, L.frame, v.frame, B->levels);
     rc |= build_list(B, L.ar_rows, v.ar_rows); rc |= build_list(B, L.ar_cols, v.ar_cols);
+    rc |= build_fc_lists(B, L, v);
     L.any_krylov = v.any_krylov; L.any_spec = v.any_spec; L.any_ns = v.any_ns; L.any_ar = v.any_ar;
     L.pcg_max = B->hp[0].pd.pcg_max;
   }
@@ -469,6 +533,67 @@ void destroy_batch(mlba_batch* B) {
   if (B->d_opstates) cudaFree(B->d_opstates);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
   delete B;
+}
+
+// Launch geometry of the transform passes of a length-n problem (FFT length
+// pd.nfft): transforms per CTA and the column blocking of the spectrum.
+void transform_geometry(Prob& pd) {
+  const int n = pd.n;
+  const int cap = TR_CAP / std::max(pd.nfft, n);      // transforms per CTA
+  const int pairs = (n + 1) / 2;
+  {
+    const int nb = (pairs + cap - 1) / cap;            // row CTAs, then pairs spread evenly
+    pd.row_g = std::max(1, (pairs + nb - 1) / nb);
+    pd.nblk_rows = (pairs + pd.row_g - 1) / pd.row_g;
+  }
+  {
+    // column blocks: as few as the cap allows, then as even as possible
+    // (real spectra, DCT and antireflective, move real columns in pairs)
+    const bool dct = pd.transform == TR_DCT || pd.transform == TR_AR;
+    const int units = dct ? pairs : pd.half;           // complex columns to transform
+    const int nb = (units + cap - 1) / cap;
+    pd.col_g = std::max(1, (units + nb - 1) / nb);
+    pd.cb = dct ? 2 * pd.col_g : pd.col_g;
+    pd.nblk_cols = ((dct ? n : pd.half) + pd.cb - 1) / pd.cb;
+  }
+  pd.nblk_spec = (int)((spec_elems(pd) + SPEC_THREADS * SPEC_PER_THREAD - 1) /
+                       (SPEC_THREADS * SPEC_PER_THREAD));
+}
+
+// smallest 2^a 3^b 5^c >= m (fast radix passes for the convolution size)
+int smooth_at_least(int m) {
+  for (int x = m;; ++x) {
+    int y = x;
+    for (int f : {2, 3, 5}) while (y % f == 0) y /= f;
+    if (y == 1) return x;
+  }
+}
+
+// A convolution entry of problem `owner` (FFT blur path): an M x M DFT
+// "problem" whose spectrum is the DFT of the PSF rotated by 180 degrees
+// (forward: the column pass's conj(lambda) is then H^, convolution) or of
+// the PSF itself (adjoint: conj(H^), correlation).
+bool setup_conv_entry(const HostProb& own, int owner, int adj, HostProb& h) {
+  const Prob& op = own.pd;
+  Prob& pd = h.pd;
+  std::memset(&pd, 0, sizeof(pd));
+  const int M = smooth_at_least(op.ne);
+  if (M > TR_CAP) return false;
+  pd.n = pd.nf = pd.ne = M; pd.p = op.p; pd.c = op.c; pd.half = M / 2 + 1;
+  pd.transform = TR_DFT; pd.precond = P_BCCB; pd.bc = BC_PERIODIC;
+  pd.levels = op.levels; pd.nbands = op.nbands;
+  pd.alpha = 1.0; pd.max_iter = -1; pd.sidx = owner;
+  pd.nfft = M;
+  if (!fft_plan(pd)) return false;
+  transform_geometry(pd);
+  pd.nblk_vec = vec_blocks((size_t)M * M);
+  const int p = op.p;
+  h.psf_pre.resize((size_t)p * p);
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b < p; ++b)
+      h.psf_pre[(size_t)a * p + b] = adj ? own.psf[(size_t)a * p + b]
+                                         : own.psf[(size_t)(p - 1 - a) * p + (p - 1 - b)];
+  return true;
 }
 
 // Validate one problem and fill its host description (no device work).
@@ -571,26 +696,8 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   pd.nblk_corr = stencil_tiles(pd.ne);
   // the frame kernel indexes a z array (all bands) with 32-bit offsets
   if ((double)pd.nbands * pd.nf * pd.nf >= 2147483647.0) return MLBA_E_UNSUPPORTED;
-  const int cap = TR_CAP / std::max(pd.nfft, n);      // transforms per CTA
-  const int pairs = (n + 1) / 2;
-  {
-    const int nb = (pairs + cap - 1) / cap;            // row CTAs, then pairs spread evenly
-    pd.row_g = std::max(1, (pairs + nb - 1) / nb);
-    pd.nblk_rows = (pairs + pd.row_g - 1) / pd.row_g;
-  }
-  {
-    // column blocks: as few as the cap allows, then as even as possible
-    // (real spectra, DCT and antireflective, move real columns in pairs)
-    const bool dct = pd.transform == TR_DCT || pd.transform == TR_AR;
-    const int units = dct ? pairs : pd.half;           // complex columns to transform
-    const int nb = (units + cap - 1) / cap;
-    pd.col_g = std::max(1, (units + nb - 1) / nb);
-    pd.cb = dct ? 2 * pd.col_g : pd.col_g;
-    pd.nblk_cols = ((dct ? n : pd.half) + pd.cb - 1) / pd.cb;
-  }
-  pd.nblk_spec = (int)((spec_elems(pd) + SPEC_THREADS * SPEC_PER_THREAD - 1) /
-                       (SPEC_THREADS * SPEC_PER_THREAD));
-  pd.nblk_vec = (int)(((size_t)n * n + VEC_THREADS * VEC_PER_THREAD - 1) / (VEC_THREADS * VEC_PER_THREAD));
+  transform_geometry(pd);
+  pd.nblk_vec = vec_blocks((size_t)n * n);
   return MLBA_OK;
 }
 
@@ -819,6 +926,78 @@ int choose_frame_shape(mlba_batch* B, const mlba_opts& o) {
   return MLBA_OK;
 }
 
+// ---- direct or FFT blur per problem (opts.blur_path 2) ----------------------
+// A f of problem i alone by the direct stencil and by FFT convolution (the
+// operator forms: no stop rule, states zeroed), best of a few CUDA-event-timed
+// launches each; the problem keeps the faster.  Both compute A f: the choice
+// changes the time (and the rounding), not the operator.
+template <typename T>
+int time_blur_paths(mlba_batch* B, int i, float* t_dir, float* t_fft) {
+  const int count = (int)B->hp.size();
+  const Prob& pd = B->hp[i].pd;
+  const Prob& sf = B->fc[pd.fc_sh[0] - count].pd;
+  const int fi = pd.fc_sh[0];
+  std::vector<int2> st, pad, rows, cols, out;
+  for (int k = 0; k < pd.nblk_blur; ++k) st.push_back(make_int2(i, k));
+  for (int k = 0; k < sf.nblk_vec; ++k) pad.push_back(make_int2(fi, k));
+  for (int k = 0; k < sf.nblk_rows; ++k) rows.push_back(make_int2(fi, k));
+  for (int k = 0; k < sf.nblk_cols; ++k) cols.push_back(make_int2(fi, k));
+  for (int k = 0; k < pd.nblk_vec; ++k) out.push_back(make_int2(i, k));
+  ItemList L[5];
+  const std::vector<int2>* v[5] = {&st, &pad, &rows, &cols, &out};
+  for (int q = 0; q < 5; ++q)
+    if (build_list(B, L[q], *v[q]) != MLBA_OK) return MLBA_E_CUDA;
+  const Prob* P = B->d_probs;
+  State* S = B->d_opstates;
+  cudaStream_t s = B->stream;
+  auto direct = [&] {
+    launch_stencil<T>(ST_FWD_STORE, P, S, L[0].dev, L[0].count, SL_F, SL_AUX1, SL_AUX1, 0, B->smem_stencil, s);
+  };
+  auto fft = [&] {
+    launch_fc_pad<T>(P, S, L[1].dev, L[1].count, 0, SL_F, s);
+    launch_rows_fwd<T>(P, S, L[2].dev, L[2].count, SL_R, 0, B->smem_fft, s);
+    launch_cols<T>(P, S, L[3].dev, L[3].count, COL_OP, 0, 1.0, W_TIKH, B->smem_fft, s);
+    launch_rows_inv<T>(P, S, L[2].dev, L[2].count, SL_T, 0, B->smem_fft, s);
+    launch_fc_out<T>(P, S, L[4].dev, L[4].count, FC_STORE_MODE, 0, SL_AUX1, s);
+  };
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best[2] = {1e30f, 1e30f};
+  for (int path = 0; path < 2; ++path)
+    for (int r = 0; r < 4; ++r) {
+      cudaEventRecord(e0, s);
+      if (path == 0) direct(); else fft();
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return MLBA_E_CUDA; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) best[path] = std::min(best[path], ms);   // the first launch warms up
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  *t_dir = best[0];
+  *t_fft = best[1];
+  return MLBA_OK;
+}
+
+int choose_blur_paths(mlba_batch* B) {
+  const int count = (int)B->hp.size();
+  CK(cudaMemsetAsync(B->d_opstates, 0, count * sizeof(State), B->stream));
+  for (int i = 0; i < count; ++i) {
+    Prob& pd = B->hp[i].pd;
+    if (pd.fc_sh[1] == 0) continue;               // no convolution entries
+    float td = 0.f, tf = 0.f;
+    const int rc = B->dtype == MLBA_F64 ? time_blur_paths<double>(B, i, &td, &tf)
+                                        : time_blur_paths<float>(B, i, &td, &tf);
+    if (rc != MLBA_OK) return rc;
+    pd.fc = tf < td ? 1 : 0;
+    CK(cudaMemcpy(&B->d_probs[i].fc, &pd.fc, sizeof(int), cudaMemcpyHostToDevice));
+  }
+  return MLBA_OK;
+}
+
 int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in, mlba_batch** out) {
   if (!probs || count <= 0 || !out) return MLBA_E_INVAL;
   mlba_opts o;
@@ -829,6 +1008,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   if (o.pcg_max < 1 || o.pcg_max > 50) return MLBA_E_INVAL;
   if (o.autotune < 0 || o.autotune > 2 || o.frame_shape < -1 || o.frame_shape >= FRAME_SHAPES)
     return MLBA_E_INVAL;
+  if (o.blur_path < 0 || o.blur_path > 2) return MLBA_E_INVAL;
   mlba_batch* B = new (std::nothrow) mlba_batch();
   if (!B) return MLBA_E_NOMEM;
   B->dtype = o.dtype; B->z_store = o.z_store; B->levels = o.levels;
@@ -836,6 +1016,24 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   for (int i = 0; i < count; ++i) {
     const int rc = setup_problem(probs[i], o, B->hp[i]);
     if (rc != MLBA_OK) { destroy_batch(B); return rc; }
+    B->hp[i].pd.sidx = i;
+  }
+  // ---- FFT blur path: two convolution entries (forward, adjoint) for every
+  // problem that may use it (Algorithm 2's PCG keeps the stencils; the
+  // convolution size must fit one transform CTA)
+  B->blur_path = o.blur_path;
+  if (o.blur_path) {
+    for (int i = 0; i < count; ++i) {
+      HostProb& h = B->hp[i];
+      if (h.pd.precond == P_KRYLOV) continue;
+      HostProb sf, sa;
+      if (!setup_conv_entry(h, i, 0, sf) || !setup_conv_entry(h, i, 1, sa)) continue;
+      h.pd.fc_sh[0] = count + (int)B->fc.size();
+      B->fc.push_back(sf);
+      h.pd.fc_sh[1] = count + (int)B->fc.size();
+      B->fc.push_back(sa);
+      h.pd.fc = (o.blur_path == 1) ? 1 : 0;       // 2: measured below
+    }
   }
   if (o.stream) { B->stream = (cudaStream_t)o.stream; }
   else {
@@ -881,6 +1079,19 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 4};
     offs[i].resize(sz.size());
     for (size_t k = 0; k < sz.size(); ++k) { offs[i][k] = total; total += al(sz[k]); }
+  }
+  // convolution entries: X, Y, the spectrum work array, the two spectra, a
+  // zero |lambda|^2 and the twiddles, shared by the pair of one problem (the
+  // forward pass and the adjoint pass of a step never overlap)
+  const size_t nfc = B->fc.size() / 2;
+  std::vector<std::vector<size_t>> foffs(nfc);
+  for (size_t k = 0; k < nfc; ++k) {
+    const Prob& sf = B->fc[2 * k].pd;
+    const size_t M2 = (size_t)sf.n * sf.n, nspec = spec_elems(sf);
+    std::vector<size_t> sz = {M2 * ts, M2 * ts, nspec * 2 * ts, nspec * 2 * ts, nspec * 2 * ts,
+                              nspec * ts, (size_t)sf.nfft * 2 * ts};
+    foffs[k].resize(sz.size());
+    for (size_t q = 0; q < sz.size(); ++q) { foffs[k][q] = total; total += al(sz[q]); }
   }
   B->arena_bytes = total;
   if (cudaMalloc(&B->arena, total) != cudaSuccess) { destroy_batch(B); return MLBA_E_NOMEM; }
@@ -942,29 +1153,95 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
       if (rc != MLBA_OK) { destroy_batch(B); return rc; }
     }
   }
-  // ---- device tables
-  std::vector<Prob> probs_h(count);
+  for (size_t k = 0; k < nfc; ++k) {
+    unsigned char* base = B->arena;
+    const std::vector<size_t>& of = foffs[k];
+    for (int a = 0; a < 2; ++a) {
+      Prob& pd = B->fc[2 * k + a].pd;
+      pd.buf[SL_R] = base + of[0];
+      pd.buf[SL_T] = base + of[1];
+      pd.buf[SL_S] = base + of[2];
+      pd.lam = base + of[3 + a];
+      pd.w = base + of[5];
+      pd.tw = pd.dtw = base + of[6];
+    }
+    const Prob& sf = B->fc[2 * k].pd;
+    std::vector<double> tw(2 * (size_t)sf.nfft);
+    for (int m = 0; m < sf.nfft; ++m) {
+      const double a = 2.0 * M_PI * (double)m / (double)sf.nfft;
+      tw[2 * m] = std::cos(a); tw[2 * m + 1] = -std::sin(a);
+    }
+    std::vector<unsigned char> tmp(tw.size() * ts);
+    if (ts == 8) put<double>(tmp.data(), 0, tw); else put<float>(tmp.data(), 0, tw);
+    if (cudaMemcpy(sf.tw, tmp.data(), tmp.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      destroy_batch(B); return MLBA_E_CUDA;
+    }
+    for (int a = 0; a < 2; ++a) {
+      const int rc = build_spectrum(B, B->fc[2 * k + a]);
+      if (rc != MLBA_OK) { destroy_batch(B); return rc; }
+    }
+    // |lambda|^2 = 0: the column pass's weight is then conj(lambda) / M^2
+    if (cudaMemset(sf.w, 0, spec_elems(sf) * ts) != cudaSuccess) { destroy_batch(B); return MLBA_E_CUDA; }
+  }
+  // ---- device tables (problems, then the convolution entries)
+  const int ntab = count + (int)B->fc.size();
+  std::vector<Prob> probs_h(ntab);
   std::vector<State> st_h(count);
   for (int i = 0; i < count; ++i) { probs_h[i] = B->hp[i].pd; st_h[i] = initial_state(probs_h[i]); }
-  if (cudaMalloc(&B->d_probs, count * sizeof(Prob)) != cudaSuccess ||
+  for (size_t k = 0; k < B->fc.size(); ++k) probs_h[count + k] = B->fc[k].pd;
+  if (cudaMalloc(&B->d_probs, ntab * sizeof(Prob)) != cudaSuccess ||
       cudaMalloc(&B->d_states, count * sizeof(State)) != cudaSuccess ||
       cudaMalloc(&B->d_opstates, count * sizeof(State)) != cudaSuccess) {
     destroy_batch(B); return MLBA_E_NOMEM;
   }
-  CK(cudaMemcpy(B->d_probs, probs_h.data(), count * sizeof(Prob), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(B->d_probs, probs_h.data(), ntab * sizeof(Prob), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(B->d_states, st_h.data(), count * sizeof(State), cudaMemcpyHostToDevice));
+  // ---- shared memory of the stencil and transform launches
+  {
+    size_t smem_st = 0, smem_fft = 0;
+    for (int i = 0; i < count; ++i) {
+      const Prob& pd = B->hp[i].pd;
+      // stencil: weights (padded to 16 bytes), runs, input tile, row-pass tile
+      const size_t RY = 32 + pd.p - 1, RX = 64 + pd.p - 1;
+      const size_t ce = 16 / ts;                  // input-tile pitch as in k_stencil.cu (st_pitch)
+      const size_t RP = (RX + 2 * (ce - 1)) / ce * ce;
+      const size_t nw = pd.sep ? 2 * pd.p : pd.nrw;
+      // (a second row-pass tile only for rank-one PSFs with 8 RY > 4 x 128, see k_stencil.cu)
+      const size_t st_b = (((nw + 3) & ~(size_t)3) + RY * RP + (pd.sep && 8 * RY > 4 * 128 ? RY * 66 : 0)) * ts +
+                          (pd.sep ? 0 : (size_t)pd.nruns * 16);
+      smem_st = std::max(smem_st, st_b);
+      if (pd.transform != TR_NONE) {
+        // (antireflective columns also keep two weighted end values per transform)
+        const size_t fb = (size_t)std::max(pd.row_g, pd.col_g) * (fft_pad(pd.nfft) + 1) * 2 * ts +
+                          (pd.transform == TR_AR ? (size_t)pd.col_g * 4 * ts : 0);
+        smem_fft = std::max(smem_fft, fb);
+      }
+    }
+    for (const HostProb& h : B->fc) {
+      const Prob& pd = h.pd;
+      smem_fft = std::max(smem_fft, (size_t)std::max(pd.row_g, pd.col_g) * (fft_pad(pd.nfft) + 1) * 2 * ts);
+    }
+    B->smem_stencil = std::max<size_t>(smem_st, 16);
+    B->smem_fft = std::max<size_t>(smem_fft, 16);
+  }
+  if (set_smem_attrs(B) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
+  // ---- FFT or direct blur per problem (blur_path 2: the faster, measured)
+  if (o.blur_path == 2) {
+    const int rc = choose_blur_paths(B);
+    if (rc != MLBA_OK) { destroy_batch(B); return rc; }
+  }
   // ---- item lists
   std::vector<int2> blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec,
       rows_kry, cols_kry, vec_kry, vec_kry_bc, corr_all, rows_all, cols_all, spec_all, vec_all,
       ar_rows, ar_cols;
-  size_t smem_st = 0, smem_fft = 0;
+  StepItems fcv;
   for (int i = 0; i < count; ++i) {
     const Prob& pd = B->hp[i].pd;
     auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
-    add(blur, pd.nblk_blur);
+    if (!pd.fc) add(blur, pd.nblk_blur);
     add(corr_all, pd.nblk_corr);
     add(vec_all, pd.nblk_vec);
-    if (pd.use_adj) {
+    if (pd.use_adj && !pd.fc) {
       if (pd.bc == BC_AR) add(reblur, pd.nblk_blur);
       else add(corr, pd.nblk_corr);
     }
@@ -984,25 +1261,17 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
       if (pd.ns) { add(cols_ns, pd.nblk_cols); add(spec, pd.nblk_spec); B->any_ns = 1; }
       else { add(cols_stat, pd.nblk_cols); B->any_stat = 1; }
     }
-    // stencil: weights (padded to 16 bytes), runs, input tile, row-pass tile
-    const size_t RY = 32 + pd.p - 1, RX = 64 + pd.p - 1;
-    const size_t ce = 16 / ts;                  // input-tile pitch as in k_stencil.cu (st_pitch)
-    const size_t RP = (RX + 2 * (ce - 1)) / ce * ce;
-    const size_t nw = pd.sep ? 2 * pd.p : pd.nrw;
-    // (a second row-pass tile only for rank-one PSFs with 8 RY > 4 x 128, see k_stencil.cu)
-    const size_t st_b = (((nw + 3) & ~(size_t)3) + RY * RP + (pd.sep && 8 * RY > 4 * 128 ? RY * 66 : 0)) * ts +
-                        (pd.sep ? 0 : (size_t)pd.nruns * 16);
-    smem_st = std::max(smem_st, st_b);
-    if (specp) {
-      // (antireflective columns also keep two weighted end values per transform)
-      const size_t fb = (size_t)std::max(pd.row_g, pd.col_g) * (fft_pad(pd.nfft) + 1) * 2 * ts +
-                        (pd.transform == TR_AR ? (size_t)pd.col_g * 4 * ts : 0);
-      smem_fft = std::max(smem_fft, fb);
-    }
+    if (pd.fc)
+      collect_fc(pd, i, B->fc[pd.fc_sh[0] - count].pd, B->fc[pd.fc_sh[1] - count].pd, fcv);
   }
-  B->smem_stencil = std::max<size_t>(smem_st, 16);
-  B->smem_fft = std::max<size_t>(smem_fft, 16);
   int rc = MLBA_OK;
+  {
+    StepLists fl;
+    rc |= build_fc_lists(B, fl, fcv);
+    B->fc_pad_f = fl.fc_pad_f; B->fc_rows_f = fl.fc_rows_f; B->fc_cols_f = fl.fc_cols_f;
+    B->fc_out_r = fl.fc_out_r; B->fc_pad_a = fl.fc_pad_a; B->fc_rows_a = fl.fc_rows_a;
+    B->fc_cols_a = fl.fc_cols_a; B->fc_out_v = fl.fc_out_v; B->fc_out_u = fl.fc_out_u;
+  }
   rc |= build_list(B, B->blur, blur); rc |= build_list(B, B->corr, corr);
   rc |= build_list(B, B->reblur, reblur);
   rc |= build_list(B, B->corr_kry, corr_kry); rc |= build_list(B, B->blur_kry, blur_kry);
@@ -1015,7 +1284,6 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   rc |= build_list(B, B->spec_all, spec_all); rc |= build_list(B, B->vec_all, vec_all);
   rc |= build_list(B, B->ar_rows, ar_rows); rc |= build_list(B, B->ar_cols, ar_cols);
   if (rc != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
-  if (set_smem_attrs(B) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
   // ---- framelet tile shape, then the framelet list in that shape
   {
     const int trc = choose_frame_shape(B, o);
@@ -1127,6 +1395,7 @@ void mlba_opts_default(mlba_opts* o) {
   o->stream = nullptr;
   o->autotune = 0;
   o->frame_shape = -1;
+  o->blur_path = 0;
 }
 
 const char* mlba_strerror(int s) {
@@ -1333,6 +1602,14 @@ int mlba_create(const double* psf, int p, int n, int bc, int precond, const mlba
   if (!c) { destroy_batch(B); return MLBA_E_NOMEM; }
   c->b = B;
   *out = c;
+  return MLBA_OK;
+}
+
+int mlba_batch_blur_fft(mlba_batch* B, int i, int* uses_fft, int* size) {
+  if (!B || i < 0 || i >= (int)B->hp.size()) return MLBA_E_INVAL;
+  const Prob& pd = B->hp[i].pd;
+  if (uses_fft) *uses_fft = pd.fc;
+  if (size) *size = pd.fc ? B->fc[pd.fc_sh[0] - (int)B->hp.size()].pd.n : 0;
   return MLBA_OK;
 }
 
@@ -1545,6 +1822,32 @@ void mlba_destroy(mlba_ctx* c) {
 }
 
 // ---- operator entry points ---------------------------------------------------
+}  // extern "C"
+
+namespace {
+// A f (adj = 0) or A^T t / A' t (adj = 1) of a problem on the FFT blur path,
+// input in SL_AUX0: the result lands in SL_AUX1 (n x n) or, for the full
+// correlation of a BC / rectangular problem, in SL_V
+template <typename T>
+void op_fc(mlba_batch* B, int adj) {
+  const Prob* P = B->d_probs;
+  State* S = B->d_opstates;
+  cudaStream_t s = B->stream;
+  const ItemList& pad = adj ? B->fc_pad_a : B->fc_pad_f;
+  const ItemList& rows = adj ? B->fc_rows_a : B->fc_rows_f;
+  const ItemList& cols = adj ? B->fc_cols_a : B->fc_cols_f;
+  launch_fc_pad<T>(P, S, pad.dev, pad.count, adj, SL_AUX0, s);
+  launch_rows_fwd<T>(P, S, rows.dev, rows.count, SL_R, 0, B->smem_fft, s);
+  launch_cols<T>(P, S, cols.dev, cols.count, COL_OP, 0, 1.0, W_TIKH, B->smem_fft, s);
+  launch_rows_inv<T>(P, S, rows.dev, rows.count, SL_T, 0, B->smem_fft, s);
+  if (!adj) launch_fc_out<T>(P, S, B->fc_out_r.dev, B->fc_out_r.count, FC_STORE_MODE, 0, SL_AUX1, s);
+  else if (B->fc_out_u.count) launch_fc_out<T>(P, S, B->fc_out_u.dev, B->fc_out_u.count, FC_STORE_MODE, 1, SL_AUX1, s);
+  else launch_fc_out<T>(P, S, B->fc_out_v.dev, B->fc_out_v.count, FC_CORR_MODE, 1, SL_V, s);
+}
+}  // namespace
+
+extern "C" {
+
 int mlba_op_blur(mlba_ctx* c, const void* f, void* out, int on_device) {
   if (!c) return MLBA_E_INVAL;
   mlba_batch* B = c->b;
@@ -1553,6 +1856,11 @@ int mlba_op_blur(mlba_ctx* c, const void* f, void* out, int on_device) {
   int rc = copy_in(B, pd.buf[SL_AUX0], f, (size_t)pd.nf * pd.nf * ts, on_device);
   if (rc != MLBA_OK) return rc;
   if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
+  if (pd.fc) {
+    if (B->dtype == MLBA_F64) op_fc<double>(B, 0); else op_fc<float>(B, 0);
+    CK(cudaGetLastError());
+    return copy_out(B, out, pd.buf[SL_AUX1], (size_t)pd.n * pd.n * ts, on_device);
+  }
   if (B->dtype == MLBA_F64)
     launch_stencil<double>(ST_FWD_STORE, B->d_probs, B->d_opstates, B->blur.dev, B->blur.count,
                            SL_AUX0, SL_AUX1, SL_AUX1, 0, B->smem_stencil, B->stream);
@@ -1571,6 +1879,18 @@ int mlba_op_blur_adjoint(mlba_ctx* c, const void* t, void* out, int on_device) {
   int rc = copy_in(B, pd.buf[SL_AUX0], t, (size_t)pd.n * pd.n * ts, on_device);
   if (rc != MLBA_OK) return rc;
   if (reset_opstates(B) != MLBA_OK) return MLBA_E_CUDA;
+  if (pd.fc) {
+    if (B->dtype == MLBA_F64) op_fc<double>(B, 1); else op_fc<float>(B, 1);
+    CK(cudaGetLastError());
+    if (pd.bc == BC_AR) return copy_out(B, out, pd.buf[SL_AUX1], (size_t)pd.n * pd.n * ts, on_device);
+    if (pd.bc != BC_RECT) {
+      if (B->dtype == MLBA_F64) launch_vec<double>(VEC_FOLD, B->d_probs, B->d_opstates, B->vec_all.dev, B->vec_all.count, 0, B->stream);
+      else launch_vec<float>(VEC_FOLD, B->d_probs, B->d_opstates, B->vec_all.dev, B->vec_all.count, 0, B->stream);
+      CK(cudaGetLastError());
+      return copy_out(B, out, pd.buf[SL_U], (size_t)pd.n * pd.n * ts, on_device);
+    }
+    return copy_out(B, out, pd.buf[SL_V], (size_t)pd.nf * pd.nf * ts, on_device);
+  }
   if (pd.bc == BC_AR) {
     // the reblurring matrix A' (Section 2.2), n x n
     if (B->dtype == MLBA_F64)

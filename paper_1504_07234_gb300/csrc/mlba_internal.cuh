@@ -38,6 +38,10 @@ constexpr int MAX_LEVELS = 4;
 // Constant description of one problem (device copy lives in a table).
 struct Prob {
   int n, p, c, nf, ne, half;     // half = n/2+1
+  int sidx;          // index of the State this entry answers to: its own, or for a
+                     // convolution entry (FFT blur path) the problem it serves
+  int fc;            // problem: 1 = A and A^T by FFT convolution (the entries below)
+  int fc_sh[2];      // problem: table indices of its forward / adjoint convolution entries
   int bc, precond, transform, levels, nbands;
   int ns;            // nonstationary alpha (4-NS)
   int use_adj;       // 1: u = A^T t ; 0: u = t (Algorithm 4 forms)

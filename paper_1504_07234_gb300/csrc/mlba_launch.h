@@ -14,6 +14,16 @@ enum {
   ST_REBLUR = 4       // dst (n x n) = A' src: correlation of the antireflectively padded src
                       // (the reblurring matrix of Section 2.2; default dst U)
 };
+// FFT-convolution blur path (k_stencil.cu): pad a convolution entry's input,
+// and move its output to the problem (residual with the stop rule, A f or A' t
+// stored n x n, or the (n+p-1)^2 correlation V)
+enum { FC_RESID_MODE = 0, FC_STORE_MODE = 1, FC_CORR_MODE = 2 };
+template <typename T>
+void launch_fc_pad(const Prob* probs, State* states, const int2* items, int nitems, int adj,
+                   int src_slot, cudaStream_t s);
+template <typename T>
+void launch_fc_out(const Prob* probs, State* states, const int2* items, int nitems, int mode,
+                   int adj, int dst_slot, cudaStream_t s);
 // vector kernels (k_stencil.cu)
 enum {
   VEC_FOLD = 0,       // U = BC fold of V

@@ -226,6 +226,57 @@ def test_antireflective_rejects_alg2_and_ns_transform(M):
         M.Context(h, 40, "reflective", "bccb", dtype="f64", transform="ar")
 
 
+FFT_CASES = [("rect", "bccb", "dft", I.psf_motion(7, 0.9), 0.3),
+             ("reflective", "tikh_ns", "dct", I.psf_disk(3), 0.05),
+             ("zero", "tikh", "dft", I.psf_motion(7, 0.9), 0.05),
+             ("antireflective", "bccb", "dft", I.psf_motion(7, 0.9), 1.0),
+             ("periodic", "none", "auto", I.psf_disk(17), 0.3)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc,precond,transform,psf,alpha", FFT_CASES,
+                         ids=[f"{c[0]}-{c[1]}" for c in FFT_CASES])
+def test_fft_blur_path_loop_matches_oracle(M, dtype, bc, precond, transform, psf, alpha):
+    """Loops whose A and A^T run as FFT convolutions (opts.blur_path = 1),
+    including a 37 x 37 dense disk, the case the path exists for."""
+    n = 48 if bc != "rect" else 42
+    pr = small(bc, precond, n=n, psf=psf, alpha=alpha, transform=transform, iters=8)
+    descs = [dict(psf=pr.psf, g=pr.g, delta=pr.delta, bc=pr.bc, precond=pr.precond, mu=pr.mu,
+                  alpha=pr.alpha, transform=pr.transform, max_iter=8)]
+    b = M.Batch(descs, dtype=dtype, levels=pr.levels, stop=False, max_iter=8, blur_path="fft",
+                rect_ns_hybrid=pr.rect_ns_hybrid)
+    assert b.blur_fft(0)[0] and b.blur_fft(0)[1] >= n + psf.shape[0] - 1
+    b.iterate(9)
+    f = b.result(0)
+    b.close()
+    ref = run_oracle(pr)
+    if dtype == "f64":
+        assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
+    else:
+        restoration_bars(f, ref, pr)
+
+
+def test_fft_blur_path_chosen_per_problem(M):
+    """opts.blur_path = 2: every problem gets the faster path, measured at
+    create; the results equal the all-direct batch to rounding (FP64)."""
+    probs = [small("rect", "bccb", n=40, transform="dft", iters=5),
+             small("reflective", "tikh_ns", n=64, psf=I.psf_disk(8), transform="dct", iters=5, seed=3),
+             small("periodic", "none", n=50, psf=I.psf_disk(17), iters=5, seed=4)]
+    descs = [dict(psf=p.psf, g=p.g, delta=p.delta, bc=p.bc, precond=p.precond, mu=p.mu,
+                  alpha=p.alpha, transform=p.transform, max_iter=5) for p in probs]
+    out = []
+    for path in ("direct", "auto"):
+        b = M.Batch(descs, dtype="f64", levels=2, stop=False, max_iter=5, blur_path=path)
+        b.iterate(6)
+        out.append([b.result(i) for i in range(len(probs))])
+        if path == "auto":
+            choices = [b.blur_fft(i)[0] for i in range(len(probs))]
+        b.close()
+    for i in range(len(probs)):
+        assert np.abs(out[0][i] - out[1][i]).max() <= 1e-10 * np.abs(out[0][i]).max(), i
+    assert len(choices) == 3
+
+
 def test_fp64_stop_rule_matches_oracle(M):
     pr = I.config(2, n=64)
     pr.precond, pr.transform = "tikh", "dct"

@@ -44,15 +44,17 @@ PSFS = {
 }
 
 
+@pytest.mark.parametrize("path", ["direct", "fft"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("bc", ["zero", "periodic", "reflective", "rect", "antireflective"])
 @pytest.mark.parametrize("psf,n", [("gauss9", 70), ("disk2", 33), ("motion7", 45), ("asym3", 17),
                                    ("gauss31", 64), ("gauss41", 80), ("disk17", 72)])
-def test_blur_and_adjoint(M, dtype, bc, psf, n):
-    """A and A^T; for antireflective BCs A^T is the reblurring matrix A'
-    (Section 2.2)."""
+def test_blur_and_adjoint(M, path, dtype, bc, psf, n):
+    """A and A^T by the direct stencils and by FFT convolution on a padded
+    size (Sections 2.1, 2.2); for antireflective BCs A^T is the reblurring
+    matrix A'."""
     h = PSFS[psf]
-    ctx = M.Context(h, n, bc, "none", dtype=dtype)
+    ctx = M.Context(h, n, bc, "none", dtype=dtype, blur_path=path)
     rng = np.random.default_rng(n)
     f = rng.standard_normal((ctx.nf, ctx.nf))
     t = rng.standard_normal((n, n))
