@@ -495,7 +495,7 @@ def choose_transform(h: np.ndarray, precond: str, transform: str, bc: str = "rec
 
 def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
          stop=True, gamma=1.0 + 1e-15, q=0.5, rho=1e-4, transform="auto",
-         rect_ns_hybrid=False, pcg_tol=1e-3, pcg_max=5):
+         rect_ns_hybrid=False, pcg_tol=1e-3, pcg_max=5, formulation="synthesis"):
     """Run the preconditioned MLBA of Eq. MLBA2 in the variant ``precond``.
 
     - 'none'   : P = I (linearized Bregman, Eq. iterLinBreg with lambda = 1)
@@ -520,11 +520,19 @@ def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
     have fired is recorded (reading c15); past that point 4-NS keeps alpha_n
     at its last value.
 
+    ``formulation='balanced'``: the balanced approach the paper names as the
+    other home of its preconditioners (Section 1; Conclusions), in its
+    proximal form x^{n+1} = S_mu(W (W^T x^n + u^n)) with u^n the same
+    preconditioned correction (A^T P r^n, or C^T (CC^T + alpha I)^{-1} r^n),
+    f = W^T x; z holds W (f^n + u^n).  (The analysis approach written as a
+    linearized Bregman iteration, z += u, f = W^T S_mu(W z), is Eq. MLBA2
+    after the change of variable z <- W z, so it needs no separate form.)
+
     Returns a dict: f (restoration), z, iters (updates done), stop_iter,
     resnorms (||r^0|| .. ||r^iters||), alphas, betas.
     """
-    if bc not in BCS or precond not in PRECONDS:
-        raise ValueError((bc, precond))
+    if bc not in BCS or precond not in PRECONDS or formulation not in ("synthesis", "balanced"):
+        raise ValueError((bc, precond, formulation))
     n = g.shape[0]
     p = h.shape[0]
     nf = n + p - 1 if bc == "rect" else n
@@ -585,7 +593,10 @@ def mlba(g, h, delta, bc, precond, mu, alpha=0.05, levels=1, max_iter=200,
                 u = adj(pre.inv(r, alpha_n))
             else:
                 u = pre.tikh(r, alpha_n)
-        z = z + framelet_analysis(u, levels)
+        if formulation == "balanced":
+            z = framelet_analysis(f + u, levels)
+        else:
+            z = z + framelet_analysis(u, levels)
         f = framelet_synthesis(soft(z, mu), levels)
         it += 1
     return {"f": f, "z": z, "iters": it, "stop_iter": stop_iter,

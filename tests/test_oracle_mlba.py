@@ -158,3 +158,42 @@ def test_first_iterate_dense_antireflective():
     assert abs(out["resnorms"][1] - np.linalg.norm(g.ravel() - a @ f1)) < 1e-12
     with pytest.raises(ValueError):
         O.mlba(g, h, 1.0, "antireflective", "krylov", mu=mu)
+
+
+@pytest.mark.parametrize("precond", ["bccb", "tikh"])
+def test_balanced_mu_zero_equals_synthesis(precond):
+    """With mu = 0 both the synthesis MLBA and the balanced iteration reduce
+    to the preconditioned Landweber step f += u (W^T W = I), so they agree."""
+    h = I.psf_motion(5, 0.4)
+    n = 12
+    g = np.random.default_rng(1).random((n, n))
+    kw = dict(mu=0.0, alpha=0.1, levels=2, max_iter=5, stop=False, transform="dft")
+    a = O.mlba(g, h, 1.0, "periodic", precond, **kw)
+    b = O.mlba(g, h, 1.0, "periodic", precond, formulation="balanced", **kw)
+    np.testing.assert_allclose(b["f"], a["f"], atol=1e-12)
+
+
+def test_balanced_second_iterate_dense():
+    """Balanced approach: x^1 = S(W A^T P g) (as the synthesis form), then
+    x^2 = S(W (W^T x^1 + A^T P (g - A W^T x^1))), with dense A, P, W; the
+    synthesis form's second iterate S(W A^T P g + W A^T P r^1) differs."""
+    h = I.psf_motion(3, 0.5)
+    n = 6
+    p = h.shape[0]
+    m = n + p - 1
+    rng = np.random.default_rng(5)
+    g = rng.random((n, n))
+    alpha, mu, levels = 0.1, 0.02, 1
+    out = O.mlba(g, h, 1.0, "rect", "bccb", mu=mu, alpha=alpha, levels=levels, max_iter=2,
+                 stop=False, transform="dft", formulation="balanced")
+    a = dense_blur_matrix(h, n, "rect")
+    cper = dense_blur_matrix(h, n, "periodic")
+    pmat = np.linalg.inv(cper @ cper.T + alpha * np.eye(n * n))
+    w = dense_w(m, levels)
+    x1 = O.soft(w @ (a.T @ (pmat @ g.ravel())), mu)
+    f1 = w.T @ x1
+    x2 = O.soft(w @ (f1 + a.T @ (pmat @ (g.ravel() - a @ f1))), mu)
+    np.testing.assert_allclose(out["f"].ravel(), w.T @ x2, atol=1e-12)
+    syn = O.mlba(g, h, 1.0, "rect", "bccb", mu=mu, alpha=alpha, levels=levels, max_iter=2,
+                 stop=False, transform="dft")
+    assert np.abs(syn["f"] - out["f"]).max() > 1e-6
