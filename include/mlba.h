@@ -126,6 +126,10 @@ typedef struct mlba_opts {
                          where M <= 4096 and the algorithm is not 2 (its PCG keeps the
                          stencils); 2 per problem the faster of the two, measured at create.
                          Both compute the same operator (to rounding). */
+  int formulation;    /* 0 (default) the synthesis MLBA of Eq. MLBA2; 1 the balanced approach
+                         the paper names as the other use of its preconditioners (Section 1,
+                         Conclusions), in proximal form x^{n+1} = S_mu(W (W^T x^n + u^n)) with
+                         u^n the same preconditioned correction; z then holds W (f^n + u^n). */
 } mlba_opts;
 
 #define MLBA_FRAME_SHAPES 8
@@ -133,7 +137,8 @@ typedef struct mlba_opts {
 /* Fill defaults: mu = 10/255, alpha = 0.05, gamma = 1 + 1e-15, q = 0.5,
  * rho = 1e-4, pcg_tol = 1e-3, levels = 1, max_iter = 200, pcg_max = 5,
  * dtype = F32, z_store = F32, transform = AUTO, stop = 1, hybrid = 0,
- * stream = NULL, two_group = 1, autotune = 0, frame_shape = -1, blur_path = 0. */
+ * stream = NULL, two_group = 1, autotune = 0, frame_shape = -1, blur_path = 0,
+ * formulation = 0. */
 void mlba_opts_default(mlba_opts* o);
 
 /* ---- statistics ------------------------------------------------------- */
@@ -194,7 +199,7 @@ int mlba_get_z(mlba_ctx* ctx, void* z_out, int on_device);
  * log-alpha warm start of Algorithm 4-NS; the state also carries the
  * histories.  The state is a host blob of mlba_state_size() bytes: a header
  * (sizes, dtype, z storage, max_iter, preconditioner, transform, stop flag,
- * PCG cap, and mu, alpha, gamma, delta, q, rho, pcg_tol), the scalars, the
+ * PCG cap, formulation, and mu, alpha, gamma, delta, q, rho, pcg_tol), the scalars, the
  * histories (max_iter + 2 entries each), f (N_f x N_f, dtype) and z
  * (band-major planes, z_store type).  mlba_get_state synchronises the stream
  * and copies it out; mlba_set_state loads it into a context created with the

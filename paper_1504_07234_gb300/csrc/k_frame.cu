@@ -467,7 +467,7 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
     zin = static_cast<const TZ*>(zin_op);
     zout = static_cast<TZ*>(zout_op);
   } else {
-    zin = static_cast<const TZ*>(pd.z[(st.iter - 1) & 1]);
+    zin = static_cast<const TZ*>(pd.z0 ? pd.z0 : pd.z[(st.iter - 1) & 1]);
     zout = static_cast<TZ*>(pd.z[st.iter & 1]);
   }
   T* su = reinterpret_cast<T*>(smraw);            // u on rows ty0 - C0.., cols tx0 - C0..
@@ -479,7 +479,7 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
     if (u_slot >= 0) { src = static_cast<const T*>(pd.buf[u_slot]); mode = 1; }
     else if (!pd.use_adj) { src = static_cast<const T*>(pd.buf[SL_T]); mode = 1; }
     else if (pd.bc == BC_RECT) { src = static_cast<const T*>(pd.buf[SL_V]); mode = 1; }
-    else if (pd.bc == BC_AR) { src = static_cast<const T*>(pd.buf[SL_U]); mode = 1; }   // A' t
+    else if (pd.bc == BC_AR || pd.balanced) { src = static_cast<const T*>(pd.buf[SL_U]); mode = 1; }   // A' t; f + u
     else { src = static_cast<const T*>(pd.buf[SL_V]); mode = 0; }
     const bool interior = ty0 - C0 >= 0 && tx0 - C0 >= 0 && ty0 + F3_TY + C0 <= nf &&
                           tx0 + F3_TX + C0 <= nf;
@@ -576,7 +576,7 @@ __device__ __forceinline__ const T* frame_u(const Prob& pd, int u_slot) {
   if (u_slot >= 0) return static_cast<const T*>(pd.buf[u_slot]);
   if (!pd.use_adj) return static_cast<const T*>(pd.buf[SL_T]);
   if (pd.bc == BC_RECT) return static_cast<const T*>(pd.buf[SL_V]);
-  return static_cast<const T*>(pd.buf[SL_U]);
+  return static_cast<const T*>(pd.buf[SL_U]);     // (also f + u of the balanced form)
 }
 
 // c_lev = (b0 x b0) with dilation 2^(lev-1) applied to c_{lev-1}, half-sample
@@ -662,7 +662,7 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
     zin = static_cast<const TZ*>(zin_op);
     zout = static_cast<TZ*>(zout_op);
   } else {
-    zin = static_cast<const TZ*>(pd.z[(st.iter - 1) & 1]);
+    zin = static_cast<const TZ*>(pd.z0 ? pd.z0 : pd.z[(st.iter - 1) & 1]);
     zout = static_cast<TZ*>(pd.z[st.iter & 1]);
   }
   T* sc = reinterpret_cast<T*>(smraw);       // c_{l-1} on rows ty0 - 2D.., cols tx0 - 2D..

@@ -696,6 +696,36 @@ k_fc_out(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
   }
 }
 
+// Balanced formulation: the framelet step's input becomes f + u, with u as
+// the step left it: the BC fold of V (written to U), V (rectangular A, in
+// place), U (A' t of antireflective BCs, in place) or t (Algorithm 4 forms,
+// in place).  item.y: block of the N_f^2 plane.
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_balance(const Prob* __restrict__ probs, const State* __restrict__ states,
+          const int2* __restrict__ items) {
+  const int2 item = items[blockIdx.x];
+  const Prob& pd = probs[item.x];
+  if (states[item.x].stopped) return;
+  const int nf = pd.nf;
+  const size_t tot = (size_t)nf * nf;
+  const T* F = static_cast<const T*>(pd.buf[SL_F]);
+  const bool fold = pd.use_adj && pd.bc != BC_RECT && pd.bc != BC_AR;
+  T* dst = static_cast<T*>(pd.buf[!pd.use_adj ? SL_T : (pd.bc == BC_RECT ? SL_V : SL_U)]);
+  const T* V = static_cast<const T*>(pd.buf[SL_V]);
+  const size_t beg = (size_t)item.y * VEC_THREADS * VEC_PER_THREAD;
+  for (size_t e = beg + threadIdx.x; e < beg + VEC_THREADS * VEC_PER_THREAD && e < tot; e += VEC_THREADS) {
+    const int a = (int)(e / nf), b = (int)(e - (size_t)a * nf);
+    const T u = fold ? fold_fetch<T>(pd, V, a, b) : dst[e];
+    dst[e] = F[e] + u;
+  }
+}
+
+template <typename T>
+void launch_balance(const Prob* probs, State* states, const int2* items, int nitems, cudaStream_t s) {
+  if (nitems > 0) k_balance<T><<<nitems, VEC_THREADS, 0, s>>>(probs, states, items);
+}
+
 template <typename T>
 void launch_fc_pad(const Prob* probs, State* states, const int2* items, int nitems, int adj,
                    int src_slot, cudaStream_t s) {
@@ -759,6 +789,8 @@ template void launch_stencil<float>(int, const Prob*, State*, const int2*, int, 
 template void launch_stencil<double>(int, const Prob*, State*, const int2*, int, int, int, int, int, size_t, cudaStream_t);
 template cudaError_t stencil_set_smem<float>(size_t);
 template cudaError_t stencil_set_smem<double>(size_t);
+template void launch_balance<float>(const Prob*, State*, const int2*, int, cudaStream_t);
+template void launch_balance<double>(const Prob*, State*, const int2*, int, cudaStream_t);
 template void launch_fc_pad<float>(const Prob*, State*, const int2*, int, int, int, cudaStream_t);
 template void launch_fc_pad<double>(const Prob*, State*, const int2*, int, int, int, cudaStream_t);
 template void launch_fc_out<float>(const Prob*, State*, const int2*, int, int, int, int, cudaStream_t);

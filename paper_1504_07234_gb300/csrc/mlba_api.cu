@@ -57,13 +57,14 @@ struct StepLists {
   // FFT blur path: forward (f) and adjoint (a) convolution entries, and the
   // epilogues on the problems (residual, correlation V, reblurring into U)
   ItemList fc_pad_f, fc_rows_f, fc_cols_f, fc_out_r, fc_pad_a, fc_rows_a, fc_cols_a, fc_out_v, fc_out_u;
+  ItemList balance;   // balanced formulation: u <- f + u
   int any_krylov = 0, any_spec = 0, any_ns = 0, any_ar = 0, pcg_max = 5;
 };
 struct StepItems {
   std::vector<int2> blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec,
       rows_kry, cols_kry, vec_kry, vec_kry_bc, ar_rows, ar_cols;
   std::vector<int2> fc_pad_f, fc_rows_f, fc_cols_f, fc_out_r, fc_pad_a, fc_rows_a, fc_cols_a,
-      fc_out_v, fc_out_u;
+      fc_out_v, fc_out_u, balance;
   std::vector<int2> frame[FRAME_SECTIONS];   // see add_frame_items
   int any_krylov = 0, any_spec = 0, any_ns = 0, any_ar = 0, pcg_max = 5;
 };
@@ -76,7 +77,7 @@ void add_frame_items(const Prob& pd, int i, int levels, int shape,
                      std::vector<int2> (&fs)[FRAME_SECTIONS]) {
   auto add = [&](std::vector<int2>& L, int nblk) { for (int k = 0; k < nblk; ++k) L.push_back(make_int2(i, k)); };
   if (levels <= 2) { add(fs[0], frame_tiles(pd.nf, levels, shape)); return; }
-  if (pd.use_adj && pd.bc != BC_RECT && pd.bc != BC_AR) add(fs[0], pd.nblk_vec);
+  if (pd.use_adj && pd.bc != BC_RECT && pd.bc != BC_AR && !pd.balanced) add(fs[0], pd.nblk_vec);
   add(fs[1], lowpass_blocks(pd.nf));
   for (int k = 0; k < levels; ++k) add(fs[2 + k], lev_tiles(pd.nf, levels - k));
 }
@@ -106,6 +107,8 @@ struct mlba_batch {
   ItemList fc_pad_f, fc_rows_f, fc_cols_f, fc_out_r, fc_pad_a, fc_rows_a, fc_cols_a, fc_out_v, fc_out_u;
   std::vector<HostProb> fc;      // convolution entries, table indices count + k
   int blur_path = 0;
+  ItemList balance;
+  int formulation = 0;
   std::vector<int2*> allocs;
   size_t smem_stencil = 0, smem_fft = 0;
   cudaGraph_t graph = nullptr;
@@ -330,6 +333,8 @@ void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
       launch_fc_out<T>(P, S, L.fc_out_v.dev, L.fc_out_v.count, FC_CORR_MODE, 1, SL_V, s);
       launch_fc_out<T>(P, S, L.fc_out_u.dev, L.fc_out_u.count, FC_STORE_MODE, 1, SL_U, s);
     }
+    // balanced formulation: x = S_mu(W (f + u))
+    launch_balance<T>(P, S, L.balance.dev, L.balance.count, s);
     // a1: z += W u, x = S_mu(z), f = W^T x
     launch_frame<T, TZ>(P, S, L.frame.dev, L.frame.count, L.frame.sec, -1, SL_F, nullptr, nullptr,
                         0.0, B->levels, B->frame_shape, s);
@@ -353,6 +358,7 @@ StepLists all_lists(const mlba_batch* B) {
   L.fc_pad_f = B->fc_pad_f; L.fc_rows_f = B->fc_rows_f; L.fc_cols_f = B->fc_cols_f;
   L.fc_out_r = B->fc_out_r; L.fc_pad_a = B->fc_pad_a; L.fc_rows_a = B->fc_rows_a;
   L.fc_cols_a = B->fc_cols_a; L.fc_out_v = B->fc_out_v; L.fc_out_u = B->fc_out_u;
+  L.balance = B->balance;
   L.pcg_max = B->hp.empty() ? 5 : B->hp[0].pd.pcg_max;
   return L;
 }
@@ -380,6 +386,7 @@ void collect_step(const Prob& pd, int i, int levels, int shape, StepItems& V) {
     if (pd.bc == BC_AR) add(V.reblur, pd.nblk_blur);
     else add(V.corr, pd.nblk_corr);
   }
+  if (pd.balanced) add(V.balance, vec_blocks((size_t)pd.nf * pd.nf));
   const bool specp = pd.transform != TR_NONE;
   if (pd.precond == P_KRYLOV) {
     add(V.corr_kry, pd.nblk_corr); add(V.blur_kry, pd.nblk_blur); add(V.rows_kry, pd.nblk_rows);
@@ -484,6 +491,7 @@ int build_split(mlba_batch* B) {
     rc |= build_frame_list(B, L.frame, v.frame, B->levels);
     rc |= build_list(B, L.ar_rows, v.ar_rows); rc |= build_list(B, L.ar_cols, v.ar_cols);
     rc |= build_fc_lists(B, L, v);
+    rc |= build_list(B, L.balance, v.balance);
     L.any_krylov = v.any_krylov; L.any_spec = v.any_spec; L.any_ns = v.any_ns; L.any_ar = v.any_ar;
     L.pcg_max = B->hp[0].pd.pcg_max;
   }
@@ -624,6 +632,7 @@ int setup_problem(const mlba_problem& in, const mlba_opts& o, HostProb& h) {
   pd.half = n / 2 + 1;
   pd.bc = in.bc; pd.precond = in.precond; pd.levels = o.levels; pd.nbands = 8 * o.levels + 1;
   pd.ns = ns ? 1 : 0;
+  pd.balanced = o.formulation == 1 ? 1 : 0;
   pd.use_adj = (in.precond == MLBA_P_TIKH || (ns && in.bc != MLBA_RECT)) ? 0 : 1;
   pd.max_iter = in.max_iter > 0 ? in.max_iter : o.max_iter;
   pd.stop = o.stop;
@@ -1009,6 +1018,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   if (o.autotune < 0 || o.autotune > 2 || o.frame_shape < -1 || o.frame_shape >= FRAME_SHAPES)
     return MLBA_E_INVAL;
   if (o.blur_path < 0 || o.blur_path > 2) return MLBA_E_INVAL;
+  if (o.formulation < 0 || o.formulation > 1) return MLBA_E_INVAL;
   mlba_batch* B = new (std::nothrow) mlba_batch();
   if (!B) return MLBA_E_NOMEM;
   B->dtype = o.dtype; B->z_store = o.z_store; B->levels = o.levels;
@@ -1071,6 +1081,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         (pd.ns ? nspec : 1) * ts,              // 4-NS weighted power
         (pd.levels >= 3 ? (size_t)(pd.levels - 1) * nf2 : 1) * ts,   // low-pass chain (L >= 3)
         (pd.levels >= 3 ? (size_t)(pd.levels - 1) * nf2 : 1) * ts,   // synthesis partials
+        pd.balanced ? (size_t)pd.nbands * nf2 * zs : zs,             // zeros (balanced z_in)
         spec ? (size_t)pd.nfft * 2 * ts : ts,  // tw
         spec ? (size_t)pd.n * 2 * ts : ts,     // dtw
         (size_t)pd.nruns * 16, 2 * (size_t)pd.nrw * ts,   // tap runs and weights (both orders)
@@ -1111,6 +1122,9 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     pd.pw = base + of[k++];
     pd.lp = base + of[k++];
     pd.sy = base + of[k++];
+    pd.z0 = base + of[k++];
+    if (pd.balanced) CK(cudaMemset(pd.z0, 0, (size_t)pd.nbands * pd.nf * pd.nf * zs));
+    else pd.z0 = nullptr;
     pd.tw = base + of[k++];
     pd.dtw = base + of[k++];
     pd.tap_runs = reinterpret_cast<int4*>(base + of[k++]);
@@ -1245,6 +1259,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
       if (pd.bc == BC_AR) add(reblur, pd.nblk_blur);
       else add(corr, pd.nblk_corr);
     }
+    if (pd.balanced) add(fcv.balance, vec_blocks((size_t)pd.nf * pd.nf));
     const bool specp = pd.transform != TR_NONE;
     if (specp) { add(rows_all, pd.nblk_rows); add(cols_all, pd.nblk_cols); add(spec_all, pd.nblk_spec); }
     if (pd.precond == P_KRYLOV) {
@@ -1271,6 +1286,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     B->fc_pad_f = fl.fc_pad_f; B->fc_rows_f = fl.fc_rows_f; B->fc_cols_f = fl.fc_cols_f;
     B->fc_out_r = fl.fc_out_r; B->fc_pad_a = fl.fc_pad_a; B->fc_rows_a = fl.fc_rows_a;
     B->fc_cols_a = fl.fc_cols_a; B->fc_out_v = fl.fc_out_v; B->fc_out_u = fl.fc_out_u;
+    rc |= build_list(B, B->balance, fcv.balance);
   }
   rc |= build_list(B, B->blur, blur); rc |= build_list(B, B->corr, corr);
   rc |= build_list(B, B->reblur, reblur);
@@ -1396,6 +1412,7 @@ void mlba_opts_default(mlba_opts* o) {
   o->autotune = 0;
   o->frame_shape = -1;
   o->blur_path = 0;
+  o->formulation = 0;
 }
 
 const char* mlba_strerror(int s) {
@@ -1695,22 +1712,24 @@ namespace {
 struct StateHeader {
   uint32_t magic, version;
   int32_t n, nf, p, bc, nbands, dtype, z_store, max_iter;
-  int32_t precond, transform, stop, pcg_max;
+  int32_t precond, transform, stop, pcg_max, formulation;
   int32_t iter, stopped, stop_iter, status, nres, beta_last;
   double mu, alpha, gamma, delta, q, rho, pcg_tol;   // the iteration's parameters
   double resnorm, alpha_n, nb, qn;
 };
 constexpr uint32_t STATE_MAGIC = 0x4d4c4253u;   // "MLBS"
-constexpr uint32_t STATE_VERSION = 2;
+constexpr uint32_t STATE_VERSION = 3;
 
 // the parameters that decide how the iteration continues, as the header keeps them
 void header_params(const Prob& pd, StateHeader& h) {
   h.precond = pd.precond; h.transform = pd.transform; h.stop = pd.stop; h.pcg_max = pd.pcg_max;
+  h.formulation = pd.balanced;
   h.mu = pd.mu; h.alpha = pd.alpha; h.gamma = pd.gamma; h.delta = pd.delta;
   h.q = pd.q; h.rho = pd.rho; h.pcg_tol = pd.pcg_tol;
 }
 bool same_params(const StateHeader& a, const StateHeader& b) {
   return a.precond == b.precond && a.transform == b.transform && a.stop == b.stop &&
+         a.formulation == b.formulation &&
          a.pcg_max == b.pcg_max && a.mu == b.mu && a.alpha == b.alpha && a.gamma == b.gamma &&
          a.delta == b.delta && a.q == b.q && a.rho == b.rho && a.pcg_tol == b.pcg_tol;
 }

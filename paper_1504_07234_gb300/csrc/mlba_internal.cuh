@@ -42,6 +42,8 @@ struct Prob {
                      // convolution entry (FFT blur path) the problem it serves
   int fc;            // problem: 1 = A and A^T by FFT convolution (the entries below)
   int fc_sh[2];      // problem: table indices of its forward / adjoint convolution entries
+  int balanced;      // 1: the balanced formulation, x = S_mu(W (f + u)): u is replaced by
+                     // f + u before the framelet step and z_in by zeros (z0)
   int bc, precond, transform, levels, nbands;
   int ns;            // nonstationary alpha (4-NS)
   int use_adj;       // 1: u = A^T t ; 0: u = t (Algorithm 4 forms)
@@ -64,6 +66,7 @@ struct Prob {
   double mu, alpha, gamma, delta, q, rho, tau, pcg_tol;
   void* buf[NSLOT];
   void* z[2];        // ping-pong Bregman variable
+  void* z0;          // balanced formulation: zeros read in place of z_in
   void* w;           // |lambda|^2 in T precision, column-blocked like S
   void* pw;          // 4-NS: weighted power |orthonormal coefficient of r|^2 per
                      // spectral value, T, blocked like S (0 on padding); written by

@@ -24,6 +24,9 @@ void launch_fc_pad(const Prob* probs, State* states, const int2* items, int nite
 template <typename T>
 void launch_fc_out(const Prob* probs, State* states, const int2* items, int nitems, int mode,
                    int adj, int dst_slot, cudaStream_t s);
+// balanced formulation: u <- f + u before the framelet step (k_stencil.cu)
+template <typename T>
+void launch_balance(const Prob* probs, State* states, const int2* items, int nitems, cudaStream_t s);
 // vector kernels (k_stencil.cu)
 enum {
   VEC_FOLD = 0,       // U = BC fold of V

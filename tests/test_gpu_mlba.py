@@ -277,6 +277,38 @@ def test_fft_blur_path_chosen_per_problem(M):
     assert len(choices) == 3
 
 
+BAL_CASES = [("rect", "bccb", "dft", I.psf_motion(7, 0.9), 0.3, 2),
+             ("reflective", "tikh_ns", "dct", I.psf_disk(3), 0.05, 2),
+             ("zero", "bccb", "dft", I.psf_motion(7, 0.9), 0.3, 4),
+             ("antireflective", "tikh", "auto", I.psf_gaussian(1.5, 7), 0.05, 2),
+             ("periodic", "krylov", "dft", I.psf_motion(7, 0.9), 0.05, 1)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc,precond,transform,psf,alpha,levels", BAL_CASES,
+                         ids=[f"{c[0]}-{c[1]}-L{c[5]}" for c in BAL_CASES])
+def test_balanced_formulation_matches_oracle(M, dtype, bc, precond, transform, psf, alpha, levels):
+    """The balanced formulation x = S_mu(W (f + u)) with the paper's
+    preconditioners (Section 1, Conclusions) against the oracle."""
+    n = 48 if bc != "rect" else 42
+    pr = small(bc, precond, n=n, psf=psf, alpha=alpha, transform=transform, iters=8, levels=levels)
+    ctx = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype=dtype, mu=pr.mu, alpha=pr.alpha,
+                    levels=levels, max_iter=8, stop=False, transform=pr.transform,
+                    formulation="balanced")
+    ctx.set_data(pr.g, pr.delta)
+    ctx.iterate(9)
+    f = ctx.result()
+    res, al, be = ctx.history()
+    ctx.close()
+    ref = O.mlba(pr.g, pr.psf, pr.delta, pr.bc, pr.precond, pr.mu, pr.alpha, levels, 8,
+                 stop=False, transform=pr.transform, formulation="balanced")
+    if dtype == "f64":
+        assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-9)
+    else:
+        restoration_bars(f, ref, pr)
+
+
 def test_fp64_stop_rule_matches_oracle(M):
     pr = I.config(2, n=64)
     pr.precond, pr.transform = "tikh", "dct"
