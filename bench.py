@@ -307,6 +307,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
     ap.add_argument("--one-group", action="store_true",
                     help="advance the whole batch launch by launch (no two-group schedule)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="the K steps as one persistent cooperative launch (grid barriers "
+                         "between the stages) instead of the captured graphs")
     ap.add_argument("--problems", type=int, default=64,
                     help="first K problems of the batch (small cases for profiling)")
     ap.add_argument("--config", default="4", choices=["4", "1", "2", "3", "5", "l4"],
@@ -342,7 +345,8 @@ def main():
     reps_prof = 20
     max_iter = W + K + 2 * reps_prof + 20
     batch = M.Batch(descs(probs), dtype="f32", levels=2, stop=False, max_iter=max_iter,
-                    rect_ns_hybrid=True, two_group=not args.one_group)
+                    rect_ns_hybrid=True, two_group=not args.one_group,
+                    persistent=args.persistent)
     stream = batch.stream
     # warm-up
     batch.iterate(W)
@@ -423,9 +427,11 @@ def main():
                            "problems": len(probs), "mpix_per_step_per_gpu": mpix,
                            "l2": "inputs larger than L2 (Bregman variable ~2.7 GB)",
                            "parallelism": f"replicas x{ws}, problems sharded",
-                           "schedule": "one group" if args.one_group else
+                           "schedule": "one persistent launch for the K steps" if args.persistent
+                           else "one group" if args.one_group else
                            "two groups half a step apart on two streams"},
-                "clocks": ck, "e2e": e2e, "gpu_launches": kernels * K, "roofline": roofline,
+                "clocks": ck, "e2e": e2e, "gpu_launches": 1 if args.persistent else kernels * K,
+                "roofline": roofline,
                 "step_roofline": {"min_bytes": bmin, "frac": step_frac, "peak": hbm},
                 "stage_ms": stage_ms, "cpu_baseline": cpu}
         line.update(extra)

@@ -130,6 +130,18 @@ typedef struct mlba_opts {
                          the paper names as the other use of its preconditioners (Section 1,
                          Conclusions), in proximal form x^{n+1} = S_mu(W (W^T x^n + u^n)) with
                          u^n the same preconditioned correction; z then holds W (f^n + u^n). */
+  int persistent;     /* 1: iterate(k) is ONE cooperative launch that runs the k steps of the
+                         whole batch, stage by stage, with grid barriers between the stages
+                         (CTAs resident on every SM take the items of a stage in turn); 0
+                         (default) the captured graphs of separate launches.  The iterates are
+                         the same.  Supported with dtype F32, levels <= 2, direct stencils
+                         (blur_path 0) and the DFT/DCT preconditioners or none (not Algorithm
+                         2, not the antireflective transform); otherwise create returns
+                         MLBA_E_UNSUPPORTED.  The framelet tile shape is the built-in one. */
+  double wait_s;      /* persistent: longest wait of a CTA at a grid barrier (default 1 s).  When
+                         it expires the launch ends and every problem of the batch stops with
+                         status MLBA_E_TIMEOUT (0: a CTA that is not the last to arrive gives up
+                         at once, so that the first barrier times out). */
 } mlba_opts;
 
 #define MLBA_FRAME_SHAPES 8
@@ -138,7 +150,7 @@ typedef struct mlba_opts {
  * rho = 1e-4, pcg_tol = 1e-3, levels = 1, max_iter = 200, pcg_max = 5,
  * dtype = F32, z_store = F32, transform = AUTO, stop = 1, hybrid = 0,
  * stream = NULL, two_group = 1, autotune = 0, frame_shape = -1, blur_path = 0,
- * formulation = 0. */
+ * formulation = 0, persistent = 0, wait_s = 1. */
 void mlba_opts_default(mlba_opts* o);
 
 /* ---- statistics ------------------------------------------------------- */
@@ -146,7 +158,7 @@ typedef struct mlba_stats {
   int iter;           /* z-updates done; the current f is f^iter */
   int stopped;        /* 1 once the context stopped (rule fired, budget used, or diverged) */
   int stop_iter;      /* first n at which the discrepancy rule held, -1 if never */
-  int status;         /* MLBA_OK or MLBA_E_DIVERGED */
+  int status;         /* MLBA_OK, MLBA_E_DIVERGED or MLBA_E_TIMEOUT */
   double resnorm;     /* ||r^k|| of the last residual computed */
   double alpha_n;     /* last alpha used (alpha_n for 4-NS) */
   int beta_n;         /* last PCG step count (Algorithm 2) */
@@ -257,7 +269,10 @@ typedef struct mlba_batch mlba_batch;
  * and budget.  Each problem stops on its own rule. */
 int mlba_batch_create(const mlba_problem* probs, int count, const mlba_opts* opts, mlba_batch** out);
 /* Enqueue k steps on the batch stream (asynchronous).  Every live problem
- * advances by k iterations, whatever opts.two_group says. */
+ * advances by k iterations, whatever opts.two_group says.  With
+ * opts.persistent the k steps are one launch; a grid barrier that waited
+ * longer than opts.wait_s shows as status MLBA_E_TIMEOUT in every problem's
+ * stats. */
 int mlba_batch_iterate(mlba_batch* b, int k);
 /* Number of problems not yet stopped (synchronises). */
 int mlba_batch_active(mlba_batch* b, int* n_active);

@@ -44,7 +44,8 @@ class Opts(ctypes.Structure):
                 ("stop", ctypes.c_int), ("rect_ns_hybrid", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("two_group", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("frame_shape", ctypes.c_int),
-                ("blur_path", ctypes.c_int), ("formulation", ctypes.c_int)]
+                ("blur_path", ctypes.c_int), ("formulation", ctypes.c_int),
+                ("persistent", ctypes.c_int), ("wait_s", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -138,7 +139,8 @@ def _torch():
 def make_opts(dtype="f32", z_store=None, mu=10.0 / 255.0, alpha=0.05, levels=1, max_iter=200,
               stop=True, gamma=1.0 + 1e-15, q=0.5, rho=1e-4, transform="auto", pcg_tol=1e-3,
               pcg_max=5, rect_ns_hybrid=False, stream=None, two_group=True, autotune=0,
-              frame_shape=-1, blur_path=0, formulation="synthesis") -> Opts:
+              frame_shape=-1, blur_path=0, formulation="synthesis", persistent=False,
+              wait_s=1.0) -> Opts:
     lib = load_library()
     o = Opts()
     lib.mlba_opts_default(ctypes.byref(o))
@@ -155,6 +157,8 @@ def make_opts(dtype="f32", z_store=None, mu=10.0 / 255.0, alpha=0.05, levels=1, 
     o.frame_shape = int(frame_shape)
     o.blur_path = {"direct": 0, "fft": 1, "auto": 2}.get(blur_path, blur_path)
     o.formulation = {"synthesis": 0, "balanced": 1}.get(formulation, formulation)
+    o.persistent = 1 if persistent else 0
+    o.wait_s = float(wait_s)
     return o
 
 

@@ -19,8 +19,12 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libmlba.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["k_stencil.cu", "k_fft.cu", "k_frame.cu", "mlba_api.cu", "mlba_noalloc.cu"]
-HEADERS = ["mlba_internal.cuh", "mlba_launch.h"]
+# k_persist.cuh includes the stage bodies of k_stencil.cu, k_fft.cu and
+# k_frame.cu (without their launchers), so those three are its headers too
+SOURCES = ["k_stencil.cu", "k_fft.cu", "k_frame.cu", "k_persist.cu", "k_persist_bf16.cu",
+           "mlba_api.cu", "mlba_noalloc.cu"]
+HEADERS = ["mlba_internal.cuh", "mlba_launch.h", "k_persist.cuh", "k_stencil.cu", "k_fft.cu",
+           "k_frame.cu"]
 
 
 def nvcc() -> str:

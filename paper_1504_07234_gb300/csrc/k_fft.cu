@@ -522,7 +522,7 @@ __device__ bool ns_reduce(const Prob& pd, State& st, int blk, int nblk, A (&v)[K
 
 // root in [0, 1] of the cubic Hermite interpolant with p(0) = h0 < 0 <= p(1)
 // = h1 and slopes m0, m1 (per unit t): bisection-safeguarded Newton
-__device__ double hermite_root(double h0, double h1, double m0, double m1) {
+static __device__ double hermite_root(double h0, double h1, double m0, double m1) {
   auto p = [&](double t, double* dp) {
     const double t2 = t * t, t3 = t2 * t;
     const double H00 = 2 * t3 - 3 * t2 + 1, H10 = t3 - 2 * t2 + t;
@@ -547,7 +547,7 @@ __device__ double hermite_root(double h0, double h1, double m0, double m1) {
 
 // Thread 0 of the last block of a bracketing pass: from the totals (h and h'
 // sums at the candidates, P last) bracket the root and take the Hermite root.
-__device__ void ns_bracket_finish(const Prob& pd, State& st, const double* tot, double b0) {
+static __device__ void ns_bracket_finish(const Prob& pd, State& st, const double* tot, double b0) {
   const double P = tot[2 * NS_CAND], target = st.qn * st.qn;
   auto hv = [&](int j) { return P > 0.0 ? tot[j] / P - target : 0.0; };
   auto dv = [&](int j) { return P > 0.0 ? 2.0 * tot[NS_CAND + j] / P : 0.0; };
@@ -699,14 +699,11 @@ __device__ __forceinline__ void stc2(double2* p, double2 a, double2 b) { p[0] = 
 // ---------------------------------------------------------------------------
 // Pass 1: forward transform of row pairs: src (n x n real) -> S
 template <typename T>
-__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
-k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-           int src_slot, int pcg) {
+__device__ __forceinline__ void rows_fwd_body(const int2 item, const Prob* __restrict__ probs, State* __restrict__ states, int src_slot, int pcg) {
   using T2 = typename Vec2<T>::type;
   constexpr int NT = tr_nt(sizeof(T)), MAXV = TR_CAP / NT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
-  const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
   if (tr_skip(states[pd.sidx], pcg)) return;
   const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
@@ -835,6 +832,12 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
     }
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
+k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items, int src_slot, int pcg) {
+  rows_fwd_body<T>(items[blockIdx.x], probs, states, src_slot, pcg);
+}
+
 
 // spectral weight at blocked index idx; alpha and kind as given.  |lambda|^2 +
 // alpha is formed in T: alpha > 0 keeps it away from zero (no cancellation),
@@ -878,15 +881,13 @@ __device__ __forceinline__ T2 weight_dct2(const Prob& pd, size_t idx, T alpha, T
 // (the mode is a template parameter: each launch runs only its own code; the
 // two 4-NS modes measured faster at 5 FP32 CTAs per SM, the others at 4)
 template <typename T, int mode>
-__global__ void __launch_bounds__(tr_nt(sizeof(T)),
-                                  tr_minb(sizeof(T)) + ((sizeof(T) == 4 && (mode == COL_FWD || mode == COL_NS_INV)) ? 1 : 0))
-k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-       int pcg, double op_alpha, int op_kind) {
+__device__ __forceinline__ void cols_body(const int2 item, const Prob* __restrict__ probs,
+                                          State* __restrict__ states, int pcg, double op_alpha,
+                                          int op_kind) {
   using T2 = typename Vec2<T>::type;
   constexpr int NT = tr_nt(sizeof(T)), MAXV = TR_CAP / NT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
-  const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
   State& st = states[pd.sidx];
   if (tr_skip(st, pcg)) return;
@@ -1105,17 +1106,21 @@ k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
     }
   }
 }
+template <typename T, int mode>
+__global__ void __launch_bounds__(tr_nt(sizeof(T)),
+                                  tr_minb(sizeof(T)) + ((sizeof(T) == 4 && (mode == COL_FWD || mode == COL_NS_INV)) ? 1 : 0))
+k_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+       int pcg, double op_alpha, int op_kind) {
+  cols_body<T, mode>(items[blockIdx.x], probs, states, pcg, op_alpha, op_kind);
+}
 
 // Pass 3: inverse transform of row pairs: S -> dst (n x n real)
 template <typename T>
-__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
-k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-           int dst_slot, int pcg) {
+__device__ __forceinline__ void rows_inv_body(const int2 item, const Prob* __restrict__ probs, State* __restrict__ states, int dst_slot, int pcg) {
   using T2 = typename Vec2<T>::type;
   constexpr int NT = tr_nt(sizeof(T));
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
-  const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
   if (tr_skip(states[pd.sidx], pcg)) return;
   const int N = pd.n, G = pd.row_g, TSg = fpad(N) + 1;
@@ -1292,6 +1297,12 @@ k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int
     if (rb < N) dst[(size_t)rb * N + x] = v.y;
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(tr_nt(sizeof(T)), tr_minb(sizeof(T)))
+k_rows_inv(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items, int dst_slot, int pcg) {
+  rows_inv_body<T>(items[blockIdx.x], probs, states, dst_slot, pcg);
+}
+
 
 // Bracketing pass (nphase 0): h and h' at NS_CAND candidates around the
 // previous root.
@@ -1340,11 +1351,9 @@ k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const in
 
 // Refinement pass (nphase 1): a safeguarded Halley step at the current b.
 template <typename T>
-__global__ void __launch_bounds__(NS_NT)
-k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items) {
+__device__ __forceinline__ void spec_body(const int2 item, const Prob* __restrict__ probs, State* __restrict__ states) {
   __shared__ double red[4 * (NS_NT / 32)];
   __shared__ double tot[4];
-  const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
   State& st = states[item.x];
   if (st.stopped || !pd.ns || !st.ns_active || st.nconv || st.nphase != 1) return;
@@ -1415,6 +1424,12 @@ k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* _
     ns_set_alpha(pd, st, nn);
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(NS_NT)
+k_spec(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items) {
+  spec_body<T>(items[blockIdx.x], probs, states);
+}
+
 
 
 // ---------------------------------------------------------------------------
@@ -1611,6 +1626,7 @@ k_ar_cols(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   }
 }
 
+#ifndef MLBA_BODIES_ONLY  // launchers: not in the persistent kernel's unit
 // ---------------------------------------------------------------------------
 // Set-up: eigenvalues of C in FP64 (Section 4.1).  Q(dy, k2) = sum_dx h
 // e^{-2 pi i k2 dx/n} (DFT) or sum_dx h cos(pi k2 dx/n) (DCT) comes from
@@ -1754,5 +1770,7 @@ cudaError_t fft_set_smem(size_t bytes) {
 INST(float)
 INST(double)
 #undef INST
+
+#endif  // MLBA_BODIES_ONLY
 
 }  // namespace mlba

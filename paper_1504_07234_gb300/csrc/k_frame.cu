@@ -446,14 +446,16 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   }
 }
 
-template <typename T, typename TZ, int L, int F3_NWR, int F3_PF, int RING>
-__global__ void __launch_bounds__(32 * F3_NWR)
-k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-         int u_slot, int f_slot, const void* zin_op, void* zout_op, double op_mu) {
+// One framelet tile on the thread group `blk` of 32 F3_NWR threads with its
+// shared memory at smraw.
+template <typename T, typename TZ, int L, int F3_NWR, int F3_PF, int RING, typename BLK>
+__device__ __forceinline__ void frame3_body(const int2 item, const Prob* __restrict__ probs,
+                                            State* __restrict__ states, int u_slot, int f_slot,
+                                            const void* zin_op, void* zout_op, double op_mu,
+                                            unsigned char* smraw, BLK blk) {
+  const int tid = blk.tid();
   using Gm = F3<L, F3_NWR>;
   constexpr int F3_TY = Gm::TY;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
   const State& st = states[item.x];
   if (st.stopped) return;
@@ -495,7 +497,7 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
       // plain copies of the (reflected) source: asynchronous, all of a
       // thread's copies in flight together, no registers held
       const int pitch = mode ? nf : pd.ne, off = mode ? 0 : cc;
-      for (int idx = threadIdx.x; idx < UN; idx += NT) {
+      for (int idx = tid; idx < UN; idx += NT) {
         const int ry = idx / Gm::UW, rx = idx - ry * Gm::UW;
         bool par;
         const int ay = interior ? ty0 - C0 + ry : f3_refl(ty0 - C0 + ry, nf, &par);
@@ -507,7 +509,7 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
       cp_wait<0>();
     } else {
       // the BC fold of V sums up to four entries per element
-      for (int idx = threadIdx.x; idx < UN; idx += NT) {
+      for (int idx = tid; idx < UN; idx += NT) {
         const int ry = idx / Gm::UW, rx = idx - ry * Gm::UW;
         const int gy = ty0 - C0 + ry, gx = tx0 - C0 + rx;
         int o;
@@ -517,8 +519,8 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
       }
     }
   }
-  __syncthreads();
-  const int w = threadIdx.x >> 5;
+  blk.sync();
+  const int w = tid >> 5;
   const int seg_lo = ty0 + w * F3_SEG, seg_hi = seg_lo + F3_SEG;
   if (seg_lo >= nf) return;        // no barrier follows
   T* f = static_cast<T*>(pd.buf[f_slot]);
@@ -533,7 +535,7 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
     rg.buf = reinterpret_cast<TZ*>(rb + (size_t)w * RING * f3_slot_bytes<TZ>());
     rg.bar = reinterpret_cast<unsigned long long*>(rb + (size_t)F3_NWR * RING * f3_slot_bytes<TZ>()) +
              w * RING;
-    if ((threadIdx.x & 31) == 0) {
+    if ((tid & 31) == 0) {
       for (int k = 0; k < RING; ++k) mbar_init(rg.bar + k, 1);
       mbar_init_fence();
     }
@@ -547,12 +549,20 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
   if (!rg.bad)
     f3_level<T, TZ, 1, L, F3_PF, RING>(pd, su, Gm::UW, ty0 - C0, tx0 - C0, zin, zout, ty0, tx0,
                                        seg_lo, seg_hi, mu, sf2, f, rg);
-  if (rg.bad && (threadIdx.x & 31) == 0) {
+  if (rg.bad && (tid & 31) == 0) {
     // a bounded wait gave up: the problem stops with a timeout status
     volatile State* vs = &states[item.x];
     vs->status = -4;
     vs->stopped = 1;
   }
+}
+template <typename T, typename TZ, int L, int F3_NWR, int F3_PF, int RING>
+__global__ void __launch_bounds__(32 * F3_NWR)
+k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+         int u_slot, int f_slot, const void* zin_op, void* zout_op, double op_mu) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  frame3_body<T, TZ, L, F3_NWR, F3_PF, RING>(items[blockIdx.x], probs, states, u_slot, f_slot, zin_op,
+                                             zout_op, op_mu, smraw, BlkFull{});
 }
 
 
@@ -809,6 +819,7 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
   }
 }
 
+#ifndef MLBA_BODIES_ONLY  // launchers: not in the persistent kernel's unit
 int lev_tiles(int nf, int lev) {
   const int D = 1 << (lev - 1);
   const int outw = 32 - 2 * D, ty = 32 * LV_NWR;
@@ -1025,5 +1036,7 @@ INST(float, float)
 INST(float, __nv_bfloat16)
 INST(double, double)
 #undef INST
+
+#endif  // MLBA_BODIES_ONLY
 
 }  // namespace mlba

@@ -20,7 +20,7 @@ namespace mlba {
 
 // stop rule and iteration bookkeeping after ||r^n||^2 is known
 // (Eq. discrpr; Algorithm 4-NS and Eq. Alg4_rev_12)
-__device__ void finalize_residual(const Prob& pd, State& st, double sumsq) {
+static __device__ void finalize_residual(const Prob& pd, State& st, double sumsq) {
   const int it = st.iter;
   const double rn = sqrt(sumsq);
   st.resnorm = rn;
@@ -209,7 +209,9 @@ __host__ __device__ constexpr int st_pitch(int RX, int elem) {
 constexpr int ST_TP = ST_TX + 2;      // row-pass tile pitch (rank-one PSF, p > 33)
 constexpr int ST_ROW_ITEMS = 4;       // row-pass items a thread holds in registers (8 RY <= 4 x 128)
 
+#ifndef MLBA_BODIES_ONLY
 int stencil_tiles(int outN) { return ((outN + ST_TX - 1) / ST_TX) * ((outN + ST_TY - 1) / ST_TY); }
+#endif
 
 // Blur A (Eq. 2 with the Table 1 boundary conditions, or the valid part for
 // rectangular A) and the full correlation that A^T is built from, as
@@ -224,14 +226,15 @@ int stencil_tiles(int outN) { return ((outN + ST_TX - 1) / ST_TX) * ((outN + ST_
 // correlation (ne x ne) is sum_{a,b} H[a][b] t(y - 2c + a, x - 2c + b).
 // (FP32: 8 CTAs per SM, 64 registers; the tile of the largest PSF of a batch
 // decides how many fit in shared memory)
-template <typename T, int MODE>
-__global__ void __launch_bounds__(STENCIL_THREADS, sizeof(T) == 4 ? 8 : 4)
-k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
-          int src_slot, int dst_slot, int aux_slot, int pcg) {
+// One stencil item (tile) on the thread group `blk` of STENCIL_THREADS threads,
+// with its shared memory at smraw, 32 doubles of reduction space and one int.
+template <typename T, int MODE, typename BLK>
+__device__ __forceinline__ void stencil_body(const int2 item, const Prob* __restrict__ probs,
+                                             State* __restrict__ states, int src_slot, int dst_slot,
+                                             int aux_slot, int pcg, unsigned char* smraw,
+                                             double* red, int* flag, BLK blk) {
   using T2 = typename Pair<T>::type;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ double red[32];
-  const int2 item = items[blockIdx.x];
+  const int tid = blk.tid();
   const Prob& pd = probs[item.x];
   State& st = states[item.x];
   if (skip(st, pcg)) return;
@@ -269,15 +272,15 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   if (sep) {
     const T* hy = static_cast<const T*>(pd.hy);
     const T* hx = static_cast<const T*>(pd.hx);
-    for (int k = threadIdx.x; k < p; k += NT) {
+    for (int k = tid; k < p; k += NT) {
       s_w[k] = CORR ? hx[k] : hx[p - 1 - k];
       s_w[p + k] = CORR ? hy[k] : hy[p - 1 - k];
     }
   } else {
     // the weights are stored in both orders: one flat, coalesced copy
     const T* tw = static_cast<const T*>(pd.tap_w) + (CORR ? 0 : pd.nrw);
-    for (int k = threadIdx.x; k < pd.nruns; k += NT) s_runs[k] = pd.tap_runs[k];
-    for (int k = threadIdx.x; k < pd.nrw; k += NT) s_w[k] = tw[k];
+    for (int k = tid; k < pd.nruns; k += NT) s_runs[k] = pd.tap_runs[k];
+    for (int k = tid; k < pd.nrw; k += NT) s_w[k] = tw[k];
   }
   // input region
   const int oy0 = ZPAD ? ty0 - 2 * c : ty0 - c;
@@ -295,7 +298,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
   // source row are zero-filled.  Other tiles map every element.
   int xs = 0;
   {
-    const int lane = threadIdx.x & 31;
+    const int lane = tid & 31;
     const int pitch = (!ZPAD && pd.bc == BC_RECT) ? pd.nf : n;
     const int sx0 = (!ZPAD && pd.bc == BC_RECT) ? ox0 + c : ox0;
     const bool colin = sx0 >= 0 && sx0 + RX <= pitch;
@@ -320,7 +323,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
         wt[0] = T(2); wt[1] = T(-1);
         return 2;
       };
-      for (int idx = threadIdx.x; idx < RY * RX; idx += NT) {
+      for (int idx = tid; idx < RY * RX; idx += NT) {
         const int ry = idx / RX, rx = idx - ry * RX;
         int iy[2], ix[2];
         T wy[2], wx[2];
@@ -334,7 +337,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
       xs = sx0 % ce;
       const int gs = sx0 - xs;
       const int nch = (xs + RX + ce - 1) / ce;      // <= 65 (8-byte chunks of <= 129 values): three passes
-      for (int ry = threadIdx.x >> 5; ry < RY; ry += NT / 32) {
+      for (int ry = tid >> 5; ry < RY; ry += NT / 32) {
         const int ey = oy0 + ry;
         int sy;
         if (ZPAD) sy = (ey >= 0 && ey < n) ? ey : -1;
@@ -357,7 +360,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
         }
       }
     } else {
-      for (int ry = threadIdx.x >> 5; ry < RY; ry += NT / 32) {
+      for (int ry = tid >> 5; ry < RY; ry += NT / 32) {
         const int ey = oy0 + ry;
         int sy;
         if (ZPAD) sy = (ey >= 0 && ey < n) ? ey : -1;
@@ -381,9 +384,9 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
     }
     cp_async_wait_all();
   }
-  __syncthreads();
+  blk.sync();
   // this thread's outputs: columns x2, x2 + 1, rows y8 .. y8 + 7 of the tile
-  const int x2 = 2 * (threadIdx.x & 31), y8 = (threadIdx.x >> 5) * 8;
+  const int x2 = 2 * (tid & 31), y8 = (tid >> 5) * 8;
   T2 acc[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) { acc[j].x = T(0); acc[j].y = T(0); }
@@ -395,26 +398,26 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
     T h[ST_ROW_ITEMS][8];
 #pragma unroll
     for (int i = 0; i < ST_ROW_ITEMS; ++i) {
-      const int idx = threadIdx.x + i * NT;
+      const int idx = tid + i * NT;
 #pragma unroll
       for (int j = 0; j < 8; ++j) h[i][j] = T(0);
       if (idx < 8 * RY) window_run<T>(h[i], s_in + (idx >> 3) * RP + xs + (idx & 7) * 8, 1, s_w, p);
     }
-    __syncthreads();
+    blk.sync();
 #pragma unroll
     for (int i = 0; i < ST_ROW_ITEMS; ++i) {
-      const int idx = threadIdx.x + i * NT;
+      const int idx = tid + i * NT;
       if (idx < 8 * RY) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) s_in[(idx >> 3) * RP + (idx & 7) * 8 + j] = h[i][j];
       }
     }
-    __syncthreads();
+    blk.sync();
     // column pass: out(y, x) = sum_t wy[t] tmp(y + t, x)
     window_run2<T>(acc, s_in + y8 * RP + x2, RP, s_w + p, p, true);
   } else if (sep) {
     // (taller tiles, p > 33) the row pass into a second tile
-    for (int idx = threadIdx.x; idx < 8 * RY; idx += NT) {
+    for (int idx = tid; idx < 8 * RY; idx += NT) {
       const int ry = idx >> 3, x8 = (idx & 7) * 8;
       T h[8];
 #pragma unroll
@@ -423,7 +426,7 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
 #pragma unroll
       for (int j = 0; j < 8; ++j) s_tmp[ry * ST_TP + x8 + j] = h[j];
     }
-    __syncthreads();
+    blk.sync();
     // column pass: out(y, x) = sum_t wy[t] tmp(y + t, x)
     window_run2<T>(acc, s_tmp + y8 * ST_TP + x2, ST_TP, s_w + p, p, true);
   } else {
@@ -480,15 +483,15 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
     // partial of 16 squares is within 16 u = 1e-6 of its exact value)
     double dl = (double)lacc;
     for (int o = 16; o > 0; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dl;
-    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = dl;
+    blk.sync();
     double vals[1] = {0.0};
-    if (threadIdx.x == 0)
+    if (tid == 0)
       for (int w = 0; w < NT / 32; ++w) vals[0] += red[w];
-    __syncthreads();
+    blk.sync();
     double tot[1];
-    if (last_block_reduce<NT, 1>(pd, st, item.y, pd.nblk_blur, vals, tot, red)) {
-      if (threadIdx.x == 0) {
+    if (last_block_reduce_b<NT, 1>(pd, st, item.y, pd.nblk_blur, vals, tot, red, flag, blk)) {
+      if (tid == 0) {
         if (MODE == ST_FWD_RESID) {
           finalize_residual(pd, st, tot[0]);
         } else {
@@ -497,6 +500,17 @@ k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2
       }
     }
   }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(STENCIL_THREADS, sizeof(T) == 4 ? 8 : 4)
+k_stencil(const Prob* __restrict__ probs, State* __restrict__ states, const int2* __restrict__ items,
+          int src_slot, int dst_slot, int aux_slot, int pcg) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[32];
+  __shared__ int flag;
+  stencil_body<T, MODE>(items[blockIdx.x], probs, states, src_slot, dst_slot, aux_slot, pcg, smraw,
+                        red, &flag, BlkFull{});
 }
 
 template <typename T, int MODE>
@@ -701,10 +715,8 @@ k_fc_out(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
 // place), U (A' t of antireflective BCs, in place) or t (Algorithm 4 forms,
 // in place).  item.y: block of the N_f^2 plane.
 template <typename T>
-__global__ void __launch_bounds__(VEC_THREADS)
-k_balance(const Prob* __restrict__ probs, const State* __restrict__ states,
-          const int2* __restrict__ items) {
-  const int2 item = items[blockIdx.x];
+__device__ __forceinline__ void balance_body(const int2 item, const Prob* __restrict__ probs,
+                                             const State* __restrict__ states) {
   const Prob& pd = probs[item.x];
   if (states[item.x].stopped) return;
   const int nf = pd.nf;
@@ -720,7 +732,14 @@ k_balance(const Prob* __restrict__ probs, const State* __restrict__ states,
     dst[e] = F[e] + u;
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS)
+k_balance(const Prob* __restrict__ probs, const State* __restrict__ states,
+          const int2* __restrict__ items) {
+  balance_body<T>(items[blockIdx.x], probs, states);
+}
 
+#ifndef MLBA_BODIES_ONLY  // launchers: not in the persistent kernel's unit
 template <typename T>
 void launch_balance(const Prob* probs, State* states, const int2* items, int nitems, cudaStream_t s) {
   if (nitems > 0) k_balance<T><<<nitems, VEC_THREADS, 0, s>>>(probs, states, items);
@@ -797,5 +816,7 @@ template void launch_fc_out<float>(const Prob*, State*, const int2*, int, int, i
 template void launch_fc_out<double>(const Prob*, State*, const int2*, int, int, int, int, cudaStream_t);
 template void launch_vec<float>(int, const Prob*, State*, const int2*, int, int, cudaStream_t);
 template void launch_vec<double>(int, const Prob*, State*, const int2*, int, int, cudaStream_t);
+
+#endif  // MLBA_BODIES_ONLY
 
 }  // namespace mlba

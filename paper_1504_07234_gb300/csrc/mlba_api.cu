@@ -131,6 +131,15 @@ struct mlba_batch {
   int frame_shape = 0;
   int frame_tuned = 0;          // 0 default, 1 measured here, 2 from the cache, 3 forced
   float frame_us = 0.f;         // measured time of one launch of the chosen shape
+  // Persistent schedule (opts.persistent): the stage program of one step, the
+  // barrier words, and the cooperative launch geometry (k_persist.cu)
+  bool persistent = false;
+  PersistStage* d_stages = nullptr;
+  int nstages = 0;
+  void* d_ctl = nullptr;
+  int p_grid = 0, p_stencil_slot = 0, p_frame_slot = 0;
+  size_t p_smem = 0;
+  unsigned long long p_wait_ns = 1000000000ull;
 };
 
 struct mlba_ctx {
@@ -539,6 +548,8 @@ void destroy_batch(mlba_batch* B) {
   if (B->d_probs) cudaFree(B->d_probs);
   if (B->d_states) cudaFree(B->d_states);
   if (B->d_opstates) cudaFree(B->d_opstates);
+  if (B->d_stages) cudaFree(B->d_stages);
+  if (B->d_ctl) cudaFree(B->d_ctl);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
   delete B;
 }
@@ -1007,6 +1018,65 @@ int choose_blur_paths(mlba_batch* B) {
   return MLBA_OK;
 }
 
+// ---- persistent schedule ----------------------------------------------------
+// The stages of one step in the order of enqueue_step; stages in one group
+// touch disjoint problems and share the grid barrier that ends the group.
+int build_persist(mlba_batch* B) {
+  const StepLists L = all_lists(B);
+  std::vector<std::vector<PersistStage>> groups;
+  auto st = [](int kind, const ItemList& l) {
+    PersistStage p;
+    p.kind = kind; p.count = l.count; p.items = l.dev; p.sync = 0; p.pad = 0;
+    return p;
+  };
+  groups.push_back({st(PS_RESID, L.blur)});
+  if (L.any_spec) {
+    groups.push_back({st(PS_ROWS_FWD, L.rows_spec)});
+    groups.push_back({st(PS_COLS_FUSED, L.cols_stat), st(PS_COLS_FWD, L.cols_ns)});
+    if (L.any_ns) {
+      for (int k = 1; k < ns_passes<float>(); ++k) groups.push_back({st(PS_SPEC, L.spec)});
+      groups.push_back({st(PS_COLS_NSINV, L.cols_ns)});
+    }
+    groups.push_back({st(PS_ROWS_INV, L.rows_spec)});
+  }
+  groups.push_back({st(PS_CORR, L.corr), st(PS_REBLUR, L.reblur)});
+  groups.push_back({st(PS_BALANCE, L.balance)});
+  groups.push_back({st(PS_FRAME, L.frame)});
+  std::vector<PersistStage> prog;
+  for (const auto& g : groups) {
+    const size_t first = prog.size();
+    for (const PersistStage& p : g) if (p.count > 0) prog.push_back(p);
+    if (prog.size() > first) prog.back().sync = 1;
+  }
+  B->nstages = (int)prog.size();
+  CK(cudaMalloc(&B->d_stages, prog.size() * sizeof(PersistStage)));
+  CK(cudaMemcpy(B->d_stages, prog.data(), prog.size() * sizeof(PersistStage), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&B->d_ctl, persist_ctl_bytes()));
+  CK(cudaMemset(B->d_ctl, 0, persist_ctl_bytes()));
+  // one stencil slot of the widest problem, the framelet slot, or a transform
+  const int zsb = B->z_store == MLBA_BF16 ? 2 : 4;
+  B->p_smem = persist_smem(4, zsb, B->levels, B->smem_stencil, B->smem_fft, &B->p_stencil_slot,
+                           &B->p_frame_slot);
+  const void* fn = persist_func(zsb, B->levels);
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->p_smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, persist_threads(), B->p_smem));
+  if (per_sm < 1) return MLBA_E_UNSUPPORTED;
+  // no more CTAs than the largest stage has work for (two stencil items or
+  // four framelet items per CTA): fewer arrivals at every grid barrier
+  int need = 1;
+  for (const PersistStage& p : prog) {
+    const int per = (p.kind == PS_RESID || p.kind == PS_CORR || p.kind == PS_REBLUR) ? 2
+                    : p.kind == PS_FRAME ? 4 : 1;
+    need = std::max(need, (p.count + per - 1) / per);
+  }
+  B->p_grid = std::min(per_sm * sms, need);
+  B->persistent = true;
+  return MLBA_OK;
+}
+
 int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in, mlba_batch** out) {
   if (!probs || count <= 0 || !out) return MLBA_E_INVAL;
   mlba_opts o;
@@ -1019,6 +1089,12 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     return MLBA_E_INVAL;
   if (o.blur_path < 0 || o.blur_path > 2) return MLBA_E_INVAL;
   if (o.formulation < 0 || o.formulation > 1) return MLBA_E_INVAL;
+  if (o.persistent < 0 || o.persistent > 1 || !(o.wait_s >= 0.0) || o.wait_s > 1e3) return MLBA_E_INVAL;
+  if (o.persistent) {
+    if (o.dtype != MLBA_F32 || o.levels > 2 || o.blur_path != 0) return MLBA_E_UNSUPPORTED;
+    o.frame_shape = 0;      // the persistent kernel's framelet body has the built-in shape
+    o.two_group = 0;
+  }
   mlba_batch* B = new (std::nothrow) mlba_batch();
   if (!B) return MLBA_E_NOMEM;
   B->dtype = o.dtype; B->z_store = o.z_store; B->levels = o.levels;
@@ -1027,6 +1103,10 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     const int rc = setup_problem(probs[i], o, B->hp[i]);
     if (rc != MLBA_OK) { destroy_batch(B); return rc; }
     B->hp[i].pd.sidx = i;
+    if (o.persistent && (B->hp[i].pd.precond == P_KRYLOV || B->hp[i].pd.transform == TR_AR)) {
+      destroy_batch(B);
+      return MLBA_E_UNSUPPORTED;
+    }
   }
   // ---- FFT blur path: two convolution entries (forward, adjoint) for every
   // problem that may use it (Algorithm 2's PCG keeps the stencils; the
@@ -1318,6 +1398,11 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     destroy_batch(B); return MLBA_E_CUDA;
   }
   if (o.two_group && build_split(B) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
+  if (o.persistent) {
+    B->p_wait_ns = (unsigned long long)(o.wait_s * 1e9);
+    const int prc = build_persist(B);
+    if (prc != MLBA_OK) { destroy_batch(B); return prc; }
+  }
   *out = B;
   return MLBA_OK;
 }
@@ -1413,6 +1498,8 @@ void mlba_opts_default(mlba_opts* o) {
   o->frame_shape = -1;
   o->blur_path = 0;
   o->formulation = 0;
+  o->persistent = 0;
+  o->wait_s = 1.0;
 }
 
 const char* mlba_strerror(int s) {
@@ -1453,6 +1540,12 @@ int mlba_batch_iterate(mlba_batch* B, int k) {
   if (!B || k < 0) return MLBA_E_INVAL;
   if (!B->has_data) return MLBA_E_STATE;
   if (k == 0) return MLBA_OK;
+  if (B->persistent) {
+    CK(launch_persist(B->z_store == MLBA_BF16 ? 2 : 4, B->levels, B->p_grid, B->p_smem, B->d_probs,
+                      B->d_states, (int)B->hp.size(), B->d_stages, B->nstages, k, B->d_ctl,
+                      B->p_wait_ns, B->p_stencil_slot, B->p_frame_slot, B->stream));
+    return MLBA_OK;
+  }
   if (B->split) {
     CK(cudaGraphLaunch(B->x_head, B->stream));
     for (int i = 1; i < k; ++i) CK(cudaGraphLaunch(B->x_body, B->stream));

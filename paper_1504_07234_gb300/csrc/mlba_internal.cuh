@@ -148,20 +148,43 @@ __device__ __forceinline__ int refl_half(int e, int n, int* odd) {
   *odd = 1; return m2 - 1 - q;
 }
 
-// block-wide sum of a double (deterministic order); all threads must call
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* sh) {
+// Thread groups a body of work runs on: the whole CTA, or a sub-block of NTS
+// threads (whole warps) of a larger CTA with its own hardware barrier `id`
+// (1..15; barrier 0 is __syncthreads).  The bodies of the persistent step
+// kernel run several stencil or framelet items side by side this way.
+struct BlkFull {
+  __device__ __forceinline__ int tid() const { return threadIdx.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+template <int NTS>
+struct BlkSub {
+  int id;
+  __device__ __forceinline__ int tid() const { return threadIdx.x % NTS; }
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NTS) : "memory");
+  }
+};
+
+// block-wide sum of a double (deterministic order) over the NT threads of
+// group b; all of them must call
+template <int NT, typename BLK>
+__device__ __forceinline__ double block_sum_b(double v, double* sh, BLK b) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
+  const int t = b.tid();
+  int w = t >> 5, l = t & 31;
+  b.sync();
   if (l == 0) sh[w] = v;
-  __syncthreads();
+  b.sync();
   double r = 0.0;
-  if (threadIdx.x < 32) {
-    r = (threadIdx.x < NT / 32) ? sh[threadIdx.x] : 0.0;
+  if (t < 32) {
+    r = (t < NT / 32) ? sh[t] : 0.0;
     for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
   }
-  return r;  // valid in thread 0
+  return r;  // valid in thread 0 of the group
+}
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  return block_sum_b<NT>(v, sh, BlkFull{});
 }
 
 // block-wide sums of K doubles with one barrier: warp shuffles, then one
@@ -193,27 +216,34 @@ __device__ __forceinline__ void block_sum_k(double (&v)[K], double (&out)[K], do
 // Last-block reduction: every block of problem `pi` calls this with its K
 // partial values (valid in thread 0); the block that arrives last returns
 // true with the K totals (summed in block order) in tot[] (valid in thread 0).
+// `flag`: one shared int of the group.
+template <int NT, int K, typename BLK>
+__device__ bool last_block_reduce_b(const Prob& pd, State& st, int blk, int nblk,
+                                    const double* vals, double* tot, double* sh, int* flag, BLK b) {
+  const int t = b.tid();
+  if (t == 0) {
+    for (int k = 0; k < K; ++k) pd.partial[(size_t)k * nblk + blk] = vals[k];
+    __threadfence();
+    unsigned int prev = atomicAdd(&st.counter, 1u);
+    *flag = (prev == (unsigned)(nblk - 1));
+  }
+  b.sync();
+  if (!*flag) return false;
+  __threadfence();
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int i = t; i < nblk; i += NT) s += __ldcg(&pd.partial[(size_t)k * nblk + i]);
+    s = block_sum_b<NT>(s, sh, b);
+    if (t == 0) tot[k] = s;
+  }
+  if (t == 0) st.counter = 0u;
+  return true;
+}
 template <int NT, int K>
 __device__ bool last_block_reduce(const Prob& pd, State& st, int blk, int nblk,
                                   const double* vals, double* tot, double* sh) {
   __shared__ int is_last;
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < K; ++k) pd.partial[(size_t)k * nblk + blk] = vals[k];
-    __threadfence();
-    unsigned int prev = atomicAdd(&st.counter, 1u);
-    is_last = (prev == (unsigned)(nblk - 1));
-  }
-  __syncthreads();
-  if (!is_last) return false;
-  __threadfence();
-  for (int k = 0; k < K; ++k) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += NT) s += __ldcg(&pd.partial[(size_t)k * nblk + i]);
-    s = block_sum<NT>(s, sh);
-    if (threadIdx.x == 0) tot[k] = s;
-  }
-  if (threadIdx.x == 0) st.counter = 0u;
-  return true;
+  return last_block_reduce_b<NT, K>(pd, st, blk, nblk, vals, tot, sh, &is_last, BlkFull{});
 }
 
 // BC fold of the extended correlation: u(a,b) = sum over the padded positions

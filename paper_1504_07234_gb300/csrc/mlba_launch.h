@@ -111,6 +111,25 @@ void launch_z_layout(void* dst, const void* src, int levels, int nf, int elem_by
                      int to_grouped, cudaStream_t s);
 template <typename T, typename TZ>
 cudaError_t frame_set_smem();
+
+// Persistent step kernel (k_persist.cu): a stage of the step and its items
+enum { PS_RESID = 0, PS_CORR, PS_REBLUR, PS_ROWS_FWD, PS_COLS_FUSED, PS_COLS_FWD, PS_SPEC,
+       PS_COLS_NSINV, PS_ROWS_INV, PS_BALANCE, PS_FRAME };
+struct PersistStage {
+  int kind, count;
+  const int2* items;
+  int sync;            // 1: a grid barrier follows (the next stage reads what this one wrote)
+  int pad;
+};
+size_t persist_smem(int dtype_bytes, int zs_bytes, int levels, size_t smem_stencil, size_t smem_fft,
+                    int* stencil_slot, int* frame_slot);
+const void* persist_func(int zs_bytes, int levels);
+cudaError_t launch_persist(int zs_bytes, int levels, int grid, size_t smem, const Prob* probs,
+                           State* states, int nprob, const PersistStage* stages, int nst,
+                           int ksteps, void* ctl, unsigned long long spin_ns, int stencil_slot,
+                           int frame_slot, cudaStream_t s);
+size_t persist_ctl_bytes();
+int persist_threads();
 template <typename T>
 cudaError_t stencil_set_smem(size_t bytes);
 template <typename T>
