@@ -75,6 +75,12 @@ def reduce_rank_metrics(ms: float, mpix: float, dist=None, device="cpu"):
     return float(t.item()), float(m.item())
 
 
+# framelet tile shape: 2 = timed at create on the batch's own buffers (the
+# shapes compute the same values; set by --autotune)
+AUTOTUNE = 2
+LAST_TILES = {}       # framelet tiles of the last single-problem run
+
+
 def descs(probs):
     return [dict(psf=p.psf, g=p.g.astype(np.float32), delta=p.delta, bc=p.bc, precond=p.precond,
                  mu=p.mu, alpha=p.alpha) for p in probs]
@@ -164,14 +170,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_hash):
+def ncu_traffic(kernel_hash, shape=0):
     """DRAM bytes of one frame-kernel launch from the committed ncu summary,
-    scaled to the bench workload; null if the kernel changed since."""
+    scaled to the bench workload; null if the kernel changed since or the
+    launch uses another tile shape than the captured one."""
     path = os.path.join(ROOT, "profiles", "frame_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    if d.get("kernel_hash") != kernel_hash:
+    if d.get("kernel_hash") != kernel_hash or d.get("tile_shape", 0) != shape:
         return None
     return d.get("bytes_per_launch_bench")
 
@@ -310,6 +317,9 @@ def main():
     ap.add_argument("--persistent", action="store_true",
                     help="the K steps as one persistent cooperative launch (grid barriers "
                          "between the stages) instead of the captured graphs")
+    ap.add_argument("--autotune", type=int, default=2, choices=[0, 1, 2],
+                    help="framelet tile shape: 0 built-in, 1 timed at create or read from the "
+                         "on-disk cache, 2 timed at create (default)")
     ap.add_argument("--problems", type=int, default=64,
                     help="first K problems of the batch (small cases for profiling)")
     ap.add_argument("--config", default="4", choices=["4", "1", "2", "3", "5", "l4"],
@@ -320,6 +330,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    global AUTOTUNE
+    AUTOTUNE = args.autotune
     if args.impl == "reference":
         return run_reference(args)
     if args.config != "4":
@@ -346,7 +358,7 @@ def main():
     max_iter = W + K + 2 * reps_prof + 20
     batch = M.Batch(descs(probs), dtype="f32", levels=2, stop=False, max_iter=max_iter,
                     rect_ns_hybrid=True, two_group=not args.one_group,
-                    persistent=args.persistent)
+                    persistent=args.persistent, autotune=AUTOTUNE)
     stream = batch.stream
     # warm-up
     batch.iterate(W)
@@ -378,12 +390,15 @@ def main():
         stage_ms[name] = batch.profile(stage, reps_prof)
     batch.reset()
     kernels = batch.graph_kernels()
+    tiles = batch.tiles()
+    shape = tiles["frame_shape"]
     hbm, peak_kind = measured_peaks()
     fb = frame_bytes(probs)
     achieved = fb / (stage_ms["frame"] / 1e3) / 1e9
     khash = src_hash("k_frame.cu")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": ncu_traffic(khash), "kernel": "k_frame3<float,float,2>",
+                "frac": achieved / hbm, "traffic": ncu_traffic(khash, shape),
+                "kernel": f"k_frame3<float, float, 2> (tile shape {shape})",
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": fb}
     bmin = step_min_bytes(probs)
     step_frac = bmin / (ms_step / 1e3) / 1e9 / hbm
@@ -429,7 +444,8 @@ def main():
                            "parallelism": f"replicas x{ws}, problems sharded",
                            "schedule": "one persistent launch for the K steps" if args.persistent
                            else "one group" if args.one_group else
-                           "two groups half a step apart on two streams"},
+                           "two groups half a step apart on two streams",
+                           "frame_tiles": tiles},
                 "clocks": ck, "e2e": e2e, "gpu_launches": 1 if args.persistent else kernels * K,
                 "roofline": roofline,
                 "step_roofline": {"min_bytes": bmin, "frac": step_frac, "peak": hbm},
@@ -462,9 +478,13 @@ def stage_bytes_one(p, tbytes):
     read, t written; the half spectrum is n (n/2+1) complex for the DFT, n^2
     real for the DCT, i.e. about n^2 values either way)."""
     n2, ne2 = p.n * p.n, (p.n + p.p - 1) ** 2
-    return {"residual": tbytes * (p.nf * p.nf + 2 * n2),
-            "adjoint_corr": tbytes * (n2 + ne2),
-            "preconditioner": tbytes * (n2 + n2 + 3 * n2 + n2 + n2)}
+    out = {"residual": tbytes * (p.nf * p.nf + 2 * n2)}
+    # Algorithm 4 / 4-NS with a BC apply C^T inside the preconditioner: no A^T
+    if p.bc == "rect" or p.precond not in ("tikh", "tikh_ns"):
+        out["adjoint_corr"] = tbytes * (n2 + ne2)
+    if p.precond != "none":
+        out["preconditioner"] = tbytes * (n2 + n2 + 3 * n2 + n2 + n2)
+    return out
 
 
 def _single_problem(c, variant=None):
@@ -485,7 +505,7 @@ def _run_batch(M, torch, pr, dtype, iters, z_store=None, warm=0, stop=None, prof
              transform=pr.transform, max_iter=warm + iters)
     b = M.Batch([d], dtype=dtype, z_store=z_store, levels=pr.levels,
                 stop=pr.stop if stop is None else stop, max_iter=warm + iters, gamma=pr.gamma,
-                q=pr.q, rho=pr.rho, rect_ns_hybrid=pr.rect_ns_hybrid)
+                q=pr.q, rho=pr.rho, rect_ns_hybrid=pr.rect_ns_hybrid, autotune=AUTOTUNE)
     steps = iters + 1             # the last step only evaluates the final residual
     if stop:
         # time exactly the steps up to the discrepancy stop (found by an
@@ -512,6 +532,8 @@ def _run_batch(M, torch, pr, dtype, iters, z_store=None, warm=0, stop=None, prof
             b.reset()
             stages[name] = b.profile(stage, 10)
     kern = b.graph_kernels()
+    LAST_TILES.clear()
+    LAST_TILES.update(b.tiles())
     b.close()
     return ms, st, f, stages, kern
 
@@ -525,7 +547,8 @@ def _e2e(M, torch, pr, dtype, iters, z_store=None):
     d = dict(psf=pr.psf, g=g.numpy(), delta=pr.delta, bc=pr.bc, precond=pr.precond, mu=pr.mu,
              alpha=pr.alpha, transform=pr.transform, max_iter=iters)
     b = M.Batch([d], dtype=dtype, z_store=z_store, levels=pr.levels, stop=pr.stop,
-                max_iter=iters, gamma=pr.gamma, q=pr.q, rho=pr.rho, rect_ns_hybrid=pr.rect_ns_hybrid)
+                max_iter=iters, gamma=pr.gamma, q=pr.q, rho=pr.rho, rect_ns_hybrid=pr.rect_ns_hybrid,
+                autotune=AUTOTUNE)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.set_data(0, g.numpy(), pr.delta)
@@ -558,6 +581,7 @@ def measure_config(M, torch, c, compact=False, iters=None, warm=5):
         pr = _single_problem(c)
         it = iters or pr.max_iter
         ms, st, f, stg, kern = _run_batch(M, torch, pr, "f64", it, profile=not compact)
+        out["frame_tiles"] = dict(LAST_TILES)
         out.update(dtype="f64", iters=it, value=pr.n ** 2 * it / 1e6 / (ms / 1e3),
                    ms_per_iter=ms / (it + 1), quality=_quality(f, pr), graph_kernels=kern,
                    note="launch-latency bound (1.06 MB of compulsory traffic per iteration)")
@@ -568,6 +592,7 @@ def measure_config(M, torch, c, compact=False, iters=None, warm=5):
     elif c == "2":
         pr = _single_problem(c)
         ms, st, f, stg, kern = _run_batch(M, torch, pr, "f32", pr.max_iter, stop=True, profile=not compact)
+        out["frame_tiles"] = dict(LAST_TILES)
         it = max(st["iter"], 1)
         ms64, st64, f64, _, _ = _run_batch(M, torch, pr, "f64", pr.max_iter, stop=True)
         q32, q64 = _quality(f, pr), _quality(f64, pr)
@@ -582,10 +607,14 @@ def measure_config(M, torch, c, compact=False, iters=None, warm=5):
     elif c == "3":
         res = {}
         it = iters or 200
+        main_ms = main_kern = None
         for v in ("rect1", "rect2", "rect3"):
             pr = _single_problem(c, v)
             ms, st, f, stg, kern = _run_batch(M, torch, pr, "f32", it, warm=0)
-            msb, stb, fb, _, _ = _run_batch(M, torch, pr, "f32", it, z_store="bf16", warm=0)
+            msb, stb, fb, _, kernb = _run_batch(M, torch, pr, "f32", it, z_store="bf16", warm=0)
+            if v == "rect1":
+                main_ms, main_kern = msb, kernb
+                out["frame_tiles"] = dict(LAST_TILES)
             ms64, _, f64, _, _ = _run_batch(M, torch, pr, "f64", it, warm=0)
             q, qb, q64 = _quality(f, pr), _quality(fb, pr), _quality(f64, pr)
             res[v] = {"value_fp32z": pr.n ** 2 * it / 1e6 / (ms / 1e3),
@@ -595,7 +624,8 @@ def measure_config(M, torch, c, compact=False, iters=None, warm=5):
                       "bf16z_rel_f_err_vs_fp64": float(np.abs(fb - f64).max() / np.abs(f64).max()),
                       "fp32z_rel_f_err_vs_fp64": float(np.abs(f - f64).max() / np.abs(f64).max())}
         out.update(dtype="f32 (bf16 z)", iters=it, variants=res,
-                   value=res["rect1"]["value_bf16z"],
+                   value=res["rect1"]["value_bf16z"], ms_per_iter=main_ms / (it + 1),
+                   graph_kernels=main_kern,
                    note="equal budget of 200 iterations; Rect1 = BCCB (DFT), Rect2 = PCG, "
                         "Rect3 = symmetrised PSF (DCT); the FP64 reference is the library's FP64 "
                         "path (pinned to the oracle at smaller sizes)")
@@ -605,6 +635,7 @@ def measure_config(M, torch, c, compact=False, iters=None, warm=5):
         pr = _single_problem(c)
         it = iters or (pr.max_iter if c == "5" else 50)
         ms, st, f, stg, kern = _run_batch(M, torch, pr, "f32", it, warm=0, profile=True)
+        out["frame_tiles"] = dict(LAST_TILES)
         out.update(dtype="f32", iters=it, value=pr.n ** 2 * it / 1e6 / (ms / 1e3),
                    ms_per_iter=ms / (it + 1), quality=_quality(f, pr), stop_iter=st["stop_iter"],
                    graph_kernels=kern)
@@ -626,7 +657,7 @@ def measure_config(M, torch, c, compact=False, iters=None, warm=5):
                        "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                        "peak_kind": peak_kind, "algorithmic_bytes_per_launch": fb}
     sb = stage_bytes_one(pr, tb)
-    out["stage_ms"] = stg
+    out["stage_ms"] = {k: v for k, v in stg.items() if k in sb or k == "frame"}
     out["stage_frac"] = {k: sb[k] / (stg[k] / 1e3) / 1e9 / hbm for k in sb if stg.get(k)}
     if not compact:
         out["e2e"] = _e2e(M, torch, pr, dtype, it, z_store=zst)
