@@ -891,7 +891,11 @@ __device__ __forceinline__ void cols_body(const int2 item, const Prob* __restric
   const Prob& pd = probs[item.x];
   State& st = states[pd.sidx];
   if (tr_skip(st, pcg)) return;
-  if (mode == COL_NS_INV && !pd.ns) return;
+  // Algorithm 4-NS past the discrepancy point keeps alpha_n (no solve this
+  // iteration): the forward pass then weights and inverts at once, as the
+  // stationary pass does, and the inverse pass has nothing left to do
+  const bool kept = mode == COL_FWD && !pcg && pd.ns && !st.ns_active;
+  if (mode == COL_NS_INV && (!pd.ns || !st.ns_active)) return;
   // Algorithm 4-NS: the forward pass also runs the bracketing pass of alpha_n
   const bool cand = mode == COL_FWD && !pcg && pd.ns && st.ns_active && !st.nconv && st.nphase == 0;
   const int N = pd.n, cb = pd.cb, TSg = fpad(N) + 1;
@@ -899,7 +903,7 @@ __device__ __forceinline__ void cols_body(const int2 item, const Prob* __restric
   // weight parameters
   double alpha = pd.alpha;
   int kind = (pd.precond == P_TIKH || pd.precond == P_TIKH_NS) && pd.bc != BC_RECT ? W_TIKH : W_INV;
-  if (mode == COL_NS_INV) alpha = st.alpha_n;
+  if (mode == COL_NS_INV || kept) alpha = st.alpha_n;
   if (mode == COL_OP) { alpha = op_alpha; kind = op_kind; }
   if (pd.precond == P_KRYLOV) kind = W_INV;
   const T Ta = T(alpha);
@@ -950,7 +954,7 @@ __device__ __forceinline__ void cols_body(const int2 item, const Prob* __restric
       else if (c < nvc) S[2 * e] = a;
     };
     if (mode != COL_NS_INV) fft_smem<T2, false>(G, pd);
-    if (mode == COL_FWD) {
+    if (mode == COL_FWD && !kept) {
       for (int e = threadIdx.x; e < NQ; e += NT) {
         const int k1 = fH.div(e), c = 2 * (e - k1 * H);
         put(e, k1, c);
@@ -997,7 +1001,7 @@ __device__ __forceinline__ void cols_body(const int2 item, const Prob* __restric
     }
     __syncthreads();
     if (mode != COL_NS_INV) fft_smem<T2, false>(G, pd);
-    if (mode == COL_FWD) {
+    if (mode == COL_FWD && !kept) {
       for (int e = threadIdx.x; e < N * G; e += NT) {
         const int k1 = fG.div(e), c = e - k1 * G;
         if (kb + c < W) S[e] = sm[c * TSg + fpad(k1)];
@@ -1075,7 +1079,7 @@ __device__ __forceinline__ void cols_body(const int2 item, const Prob* __restric
       if (c + 1 < nvc) S2[e] = v;
       else if (c < nvc) S[2 * e] = v.x;
     };
-    if (mode == COL_FWD) {
+    if (mode == COL_FWD && !kept) {
       for (int e = threadIdx.x; e < NP; e += NT) {
         const int k1 = fG.div(e), g = e - k1 * G;
         put(e, g, k1);

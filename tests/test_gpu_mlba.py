@@ -320,6 +320,36 @@ def test_fp64_stop_rule_matches_oracle(M):
     assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
 
 
+NS_PAST = [("periodic", "dft", I.psf_motion(7, 0.9)), ("reflective", "dct", I.psf_disk(3)),
+           ("rect", "dct", I.psf_gaussian(1.5, 7))]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("bc,transform,psf", NS_PAST, ids=[c[0] for c in NS_PAST])
+def test_ns_past_discrepancy_point_matches_oracle(M, dtype, bc, transform, psf):
+    """Algorithm 4-NS run past its discrepancy point with stop = 0 (reading
+    c15): from there on alpha_n is kept, and the forward column pass applies
+    the weight and the inverse transform itself (no separate inverse pass).
+    The iterates, residual norms and the alpha_n history follow the oracle;
+    the noise level puts the discrepancy point at iterations 11, 14 and 26."""
+    pr = small(bc, "tikh_ns", n=48, psf=psf, alpha=0.05, transform=transform, iters=30, nu=0.05)
+    f, st, res, al, be = run_gpu(M, pr, dtype)
+    ref = run_oracle(pr)
+    assert ref["stop_iter"] is not None and ref["stop_iter"] < 28
+    assert st["iter"] == ref["iters"] == 30
+    if dtype == "f64":
+        assert st["stop_iter"] == ref["stop_iter"]
+        assert np.abs(f - ref["f"]).max() <= 1e-9 * np.abs(ref["f"]).max()
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-9)
+        np.testing.assert_allclose(al, ref["alphas"], rtol=1e-8)
+    else:
+        assert abs(st["stop_iter"] - ref["stop_iter"]) <= 1
+        restoration_bars(f, ref, pr)
+        np.testing.assert_allclose(res, ref["resnorms"], rtol=1e-3)
+        if st["stop_iter"] == ref["stop_iter"]:
+            np.testing.assert_allclose(al, ref["alphas"], rtol=1e-3)
+
+
 def test_config1_fp64_plain(M):
     """Workload 1: 64x64 rectangular FP64, BCCB (DFT), L = 1, 200 iterations."""
     pr = I.config(1)

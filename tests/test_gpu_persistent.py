@@ -86,6 +86,25 @@ def test_persistent_balanced_equals_graph_schedule(M):
         assert sg[i] == sp[i], i
 
 
+def test_persistent_past_the_discrepancy_point(M):
+    """4-NS problems run past their discrepancy points (stop = 0), where
+    alpha_n is kept and the forward column pass weights and inverts itself:
+    the persistent launch equals the graphs there too."""
+    probs = [small("periodic", "tikh_ns", n=48, psf=I.psf_motion(7, 0.9), alpha=0.05, iters=16,
+                   nu=0.05, seed=s, levels=2) for s in (1, 2)]
+    probs.append(small("reflective", "tikh_ns", n=48, psf=I.psf_disk(3), alpha=0.05, iters=16,
+                       nu=0.05, transform="dct", levels=2))
+    descs = [dict(psf=p.psf, g=p.g, delta=p.delta, bc=p.bc, precond=p.precond, mu=p.mu,
+                  alpha=p.alpha, transform=p.transform) for p in probs]
+    kw = dict(dtype="f32", levels=2, stop=False, max_iter=16, frame_shape=0)
+    fg, sg = run(M, descs, (5, 12), two_group=False, **kw)
+    fp, sp = run(M, descs, (5, 12), persistent=True, **kw)
+    assert all(0 <= s["stop_iter"] < 16 for s in sg), sg
+    for i in range(len(descs)):
+        assert np.array_equal(fg[i], fp[i]), i
+        assert sg[i] == sp[i], i
+
+
 def test_persistent_single_problem_matches_graph(M):
     """One problem (the Context entry points) through the persistent launch."""
     p = small("reflective", "tikh_ns", n=100, psf=I.psf_disk(3), transform="dct", iters=8,
