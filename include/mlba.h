@@ -130,7 +130,8 @@ typedef struct mlba_opts {
                          the paper names as the other use of its preconditioners (Section 1,
                          Conclusions), in proximal form x^{n+1} = S_mu(W (W^T x^n + u^n)) with
                          u^n the same preconditioned correction; z then holds W (f^n + u^n). */
-  int persistent;     /* 1: iterate(k) is ONE cooperative launch that runs the k steps of the
+  int persistent;     /* 1: iterate(k) is ONE cooperative launch (a CUDA graph of a memset of
+                         the barrier words and the kernel) that runs the k steps of the
                          whole batch, stage by stage, with grid barriers between the stages
                          (CTAs resident on every SM take the items of a stage in turn); 0
                          (default) the captured graphs of separate launches.  The iterates are

@@ -140,6 +140,10 @@ struct mlba_batch {
   int p_grid = 0, p_stencil_slot = 0, p_frame_slot = 0;
   size_t p_smem = 0;
   unsigned long long p_wait_ns = 1000000000ull;
+  cudaGraph_t p_graph = nullptr;          // memset of the barrier words -> the kernel
+  cudaGraphExec_t p_exec = nullptr;
+  cudaGraphNode_t p_knode = nullptr;
+  int p_k = 0;                            // step count the instantiated graph runs
 };
 
 struct mlba_ctx {
@@ -548,6 +552,8 @@ void destroy_batch(mlba_batch* B) {
   if (B->d_probs) cudaFree(B->d_probs);
   if (B->d_states) cudaFree(B->d_states);
   if (B->d_opstates) cudaFree(B->d_opstates);
+  if (B->p_exec) cudaGraphExecDestroy(B->p_exec);
+  if (B->p_graph) cudaGraphDestroy(B->p_graph);
   if (B->d_stages) cudaFree(B->d_stages);
   if (B->d_ctl) cudaFree(B->d_ctl);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
@@ -1073,6 +1079,12 @@ int build_persist(mlba_batch* B) {
     need = std::max(need, (p.count + per - 1) / per);
   }
   B->p_grid = std::min(per_sm * sms, need);
+  // the launch as a graph (one step; iterate(k) sets k in the instantiated copy)
+  CK(persist_graph(zsb, B->levels, B->p_grid, B->p_smem, B->d_probs, B->d_states,
+                   (int)B->hp.size(), B->d_stages, B->nstages, 1, B->d_ctl, B->p_wait_ns,
+                   B->p_stencil_slot, B->p_frame_slot, &B->p_graph, &B->p_knode));
+  CK(cudaGraphInstantiate(&B->p_exec, B->p_graph, 0));
+  B->p_k = 1;
   B->persistent = true;
   return MLBA_OK;
 }
@@ -1541,9 +1553,16 @@ int mlba_batch_iterate(mlba_batch* B, int k) {
   if (!B->has_data) return MLBA_E_STATE;
   if (k == 0) return MLBA_OK;
   if (B->persistent) {
-    CK(launch_persist(B->z_store == MLBA_BF16 ? 2 : 4, B->levels, B->p_grid, B->p_smem, B->d_probs,
-                      B->d_states, (int)B->hp.size(), B->d_stages, B->nstages, k, B->d_ctl,
-                      B->p_wait_ns, B->p_stencil_slot, B->p_frame_slot, B->stream));
+    // one graph launch: the barrier words cleared, then the k steps in one
+    // cooperative kernel
+    if (k != B->p_k) {
+      CK(persist_graph_set_k(B->p_exec, B->p_knode, B->z_store == MLBA_BF16 ? 2 : 4, B->levels,
+                             B->p_grid, B->p_smem, B->d_probs, B->d_states, (int)B->hp.size(),
+                             B->d_stages, B->nstages, k, B->d_ctl, B->p_wait_ns,
+                             B->p_stencil_slot, B->p_frame_slot));
+      B->p_k = k;
+    }
+    CK(cudaGraphLaunch(B->p_exec, B->stream));
     return MLBA_OK;
   }
   if (B->split) {

@@ -124,10 +124,14 @@ struct PersistStage {
 size_t persist_smem(int dtype_bytes, int zs_bytes, int levels, size_t smem_stencil, size_t smem_fft,
                     int* stencil_slot, int* frame_slot);
 const void* persist_func(int zs_bytes, int levels);
-cudaError_t launch_persist(int zs_bytes, int levels, int grid, size_t smem, const Prob* probs,
-                           State* states, int nprob, const PersistStage* stages, int nst,
-                           int ksteps, void* ctl, unsigned long long spin_ns, int stencil_slot,
-                           int frame_slot, cudaStream_t s);
+cudaError_t persist_graph(int zs_bytes, int levels, int grid, size_t smem, const Prob* probs,
+                          State* states, int nprob, const PersistStage* stages, int nst, int ksteps,
+                          void* ctl, unsigned long long spin_ns, int stencil_slot, int frame_slot,
+                          cudaGraph_t* g, cudaGraphNode_t* knode);
+cudaError_t persist_graph_set_k(cudaGraphExec_t x, cudaGraphNode_t knode, int zs_bytes, int levels,
+                                int grid, size_t smem, const Prob* probs, State* states, int nprob,
+                                const PersistStage* stages, int nst, int ksteps, void* ctl,
+                                unsigned long long spin_ns, int stencil_slot, int frame_slot);
 size_t persist_ctl_bytes();
 int persist_threads();
 template <typename T>
