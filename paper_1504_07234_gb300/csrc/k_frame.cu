@@ -13,8 +13,9 @@
 // neighbouring tiles), once per owned coefficient.
 //
 // Two kernel families: for L <= 2 one fused row sweep per tile (k_frame3);
-// for L >= 3 a low-pass chain and one row-sweep kernel per level whose halo
-// is only that level's dilation (k_lowpass, k_frame_lev).
+// for L >= 3 a low-pass chain and one row-sweep kernel per level, which works
+// in the polyphase order of its dilation so that its halo is one position
+// (k_lowpass, k_frame_lev).
 //
 // u comes from (per problem): the full correlation V folded by the BC
 // transpose (A^T t for imposed boundary conditions), V itself (rectangular
@@ -576,7 +577,9 @@ k_frame3(const Prob* __restrict__ probs, State* __restrict__ states, const int2*
 //   (the top level's nine bands include the final low-pass and it has no
 //   s_L term), f = s_0.  s_1 .. s_{L-1} live in HBM too, so each kernel needs
 //   a halo of its own dilation only (the fused single-pass form needs
-//   2 (2^L - 1) = 30 pixels per side at L = 4).
+//   2 (2^L - 1) = 30 pixels per side at L = 4), and in the polyphase order of
+//   that dilation (Poly) the halo is one position: c_{l-1}, s_l and the
+//   level's z are kept in the order of 2^(l-1), s_{l-1} in that of 2^(l-2).
 
 // u as the level-1 kernel and the first low-pass read it: the op entry
 // point's slot, t (Algorithm 4 forms), V (rectangular A), or U: the BC fold
@@ -589,8 +592,11 @@ __device__ __forceinline__ const T* frame_u(const Prob& pd, int u_slot) {
   return static_cast<const T*>(pd.buf[SL_U]);     // (also f + u of the balanced form)
 }
 
-// c_lev = (b0 x b0) with dilation 2^(lev-1) applied to c_{lev-1}, half-sample
-// mirror at the border; LP_PER outputs per thread, item.y = block of the plane
+// c_lev = (b0 x b0) with dilation d = 2^(lev-1) applied to c_{lev-1}, half-
+// sample mirror at the border.  c_{lev-1} is read in the polyphase order of d
+// (u, lev = 1: plain) and c_lev is written in that of 2d, the order of the
+// kernels that read it.  item.y = (output row, chunk of LP_THREADS LP_PER
+// positions of it) in the output order.
 template <typename T>
 __global__ void __launch_bounds__(LP_THREADS)
 k_lowpass(const Prob* __restrict__ probs, const State* __restrict__ states,
@@ -600,57 +606,74 @@ k_lowpass(const Prob* __restrict__ probs, const State* __restrict__ states,
   if (states[item.x].stopped) return;
   const int nf = pd.nf;
   const size_t plane = (size_t)nf * nf;
-  const int D = 1 << (lev - 1);
+  const int d = 1 << (lev - 1);
+  const Poly pin(nf, d), pout(nf, 2 * d);
   const T* in = (lev == 1) ? frame_u<T>(pd, u_slot)
                            : static_cast<const T*>(pd.lp) + (size_t)(lev - 2) * plane;
-  T* out = static_cast<T*>(pd.lp) + (size_t)(lev - 1) * plane;
-  const size_t base = (size_t)item.y * LP_THREADS * LP_PER;
+  constexpr int CH = LP_THREADS * LP_PER;
+  const int chunks = (nf + CH - 1) / CH;
+  const int py = item.y / chunks, px0 = (item.y - py * chunks) * CH;
+  T* out = static_cast<T*>(pd.lp) + (size_t)(lev - 1) * plane + (size_t)py * nf;
+  const int y = pout.inv(py);
+  bool par;
+  const T* rm = in + (size_t)pin.pos(f3_refl(y - d, nf, &par)) * nf;
+  const T* r0 = in + (size_t)pin.pos(y) * nf;
+  const T* rp = in + (size_t)pin.pos(f3_refl(y + d, nf, &par)) * nf;
 #pragma unroll
   for (int k = 0; k < LP_PER; ++k) {
-    const size_t e = base + threadIdx.x + (size_t)k * LP_THREADS;
-    if (e >= plane) break;
-    const int y = (int)(e / nf), x = (int)(e - (size_t)y * nf);
-    bool par;
-    const int ym = f3_refl(y - D, nf, &par), yp = f3_refl(y + D, nf, &par);
-    const int xm = f3_refl(x - D, nf, &par), xp = f3_refl(x + D, nf, &par);
-    auto row = [&](int r) {
-      const T* q = in + (size_t)r * nf;
-      return T(0.25) * (q[xm] + q[xp]) + T(0.5) * q[x];
-    };
-    out[e] = T(0.25) * (row(ym) + row(yp)) + T(0.5) * row(y);
+    const int px = px0 + threadIdx.x + k * LP_THREADS;
+    if (px >= nf) break;
+    const int x = pout.inv(px);
+    const int xm = pin.pos(f3_refl(x - d, nf, &par)), xc = pin.pos(x),
+              xp = pin.pos(f3_refl(x + d, nf, &par));
+    auto row = [&](const T* q) { return T(0.25) * (q[xm] + q[xp]) + T(0.5) * q[xc]; };
+    out[px] = T(0.25) * (row(rm) + row(rp)) + T(0.5) * row(r0);
   }
 }
 
-// Level kernel geometry: a CTA of LV_NWR warps owns OUTW columns x 32 LV_NWR
-// rows of s_{l-1}; lane k of a warp owns the coefficient column tx0 - D + k
-// (every lane computes coefficients, lanes D .. 31 - D produce output).
-template <int D>
+// Level kernel geometry.  A level of dilation dp works in the polyphase
+// order of dp (Poly): the taps dp apart join neighbouring positions m - 1, m,
+// m + 1 of one sub-lattice, so the kernel runs the dilation-1 sweep on each
+// of the dp^2 sub-lattices (a, b) (columns x = a + dp m, rows y = b + dp m).
+// A CTA of LV_NWR warps owns OUTW positions of a column sub-lattice x 32
+// LV_NWR positions of a row sub-lattice; lane k of a warp owns the
+// coefficient column m = tx0 - 1 + k (every lane computes coefficients, lanes
+// 1 .. 30 produce output).  The halo is one position whatever dp is.
 struct LV {
-  static constexpr int OUTW = 32 - 2 * D;                  // output columns of a tile
+  static constexpr int OUTW = 30;                 // output columns of a tile
   static constexpr int TY = 32 * LV_NWR;
-  static constexpr int CW = 32 + 2 * D, CH = TY + 4 * D;   // c tile: cols tx0 - 2D.., rows ty0 - 2D..
-  static constexpr int SW = 32, SH = TY + 2 * D;           // s tile: cols tx0 - D.., rows ty0 - D..
-  static constexpr int PR = 2 * D + 1;                     // synthesis ring rows
+  static constexpr int CW = 34, CH = TY + 4;      // c tile: positions tx0 - 2.., ty0 - 2..
+  static constexpr int SW = 32, SH = TY + 2;      // s tile: positions tx0 - 1.., ty0 - 1..
+  static constexpr int PR = 3;                    // synthesis ring rows
 };
-template <typename T, int D>
+template <typename T>
 __host__ __device__ constexpr size_t lev_smem_bytes() {
-  return ((size_t)LV<D>::CW * LV<D>::CH + (size_t)LV<D>::SW * LV<D>::SH +
-          (size_t)LV_NWR * LV<D>::PR * 3 * 32) * sizeof(T);
+  return ((size_t)LV::CW * LV::CH + (size_t)LV::SW * LV::SH + (size_t)LV_NWR * LV::PR * 3 * 32) *
+         sizeof(T);
+}
+// tiles of one sub-lattice pair and of the whole level
+__host__ __device__ inline void lev_tile_grid(int nf, int dp, int* tx, int* ty) {
+  const int m = Poly(nf, dp).count_max();
+  *tx = (m + LV::OUTW - 1) / LV::OUTW;
+  *ty = (m + LV::TY - 1) / LV::TY;
 }
 
-// One level of the step.  The warp sweeps down its rows: the horizontal
-// analysis of the three rows y - D, y, y + D of c_{l-1} (shared-memory tile),
-// the vertical masks, the update of z (register queue, PF rows ahead), the
-// threshold, and the vertical synthesis scattered into a ring of 2D + 1 rows
-// (shared memory, one column per lane); row y - D then has all its
-// contributions and is combined horizontally by warp shuffles at +-D and, for
-// l < L, with (b0 x b0)^T s_l from the s tile.
-template <typename T, typename TZ, int D, bool TOP>
+// One level of the step.  The warp sweeps down its rows (one row
+// sub-lattice): the horizontal analysis of the three rows m - 1, m, m + 1 of
+// c_{l-1} (shared-memory tile, polyphase order of dp), the vertical masks,
+// the update of z (register queue, PF rows ahead; z of the level in the same
+// order), the threshold, and the vertical synthesis scattered into a ring of
+// three rows (shared memory, one column per lane); row m - 1 then has all
+// its contributions and is combined horizontally by warp shuffles at +-1 and,
+// for l < L, with (b0 x b0)^T s_l from the s tile.  s_{l-1} is written in the
+// polyphase order of dp / 2 (f, and s_1, plainly).  Coefficients outside the
+// image are mirrored with the sign of the band's symmetry, as in k_frame3.
+template <typename T, typename TZ, bool TOP>
 __global__ void __launch_bounds__(32 * LV_NWR)
 k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
             const int2* __restrict__ items, int lev, int u_slot, int f_slot, const void* zin_op,
             void* zout_op, double op_mu) {
-  using G = LV<D>;
+  using G = LV;
   constexpr int PF = 2;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int K0 = TOP ? 0 : 1;            // band k = 3 j + i; (0,0) only at the top level
@@ -663,8 +686,19 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
   if (st.stopped) return;
   const int nf = pd.nf, L = pd.levels;
   const int plane = nf * nf;                 // nbands nf^2 < 2^31 is checked at set-up
-  const int tilesX = (nf + G::OUTW - 1) / G::OUTW;
-  const int ty0 = (item.y / tilesX) * G::TY, tx0 = (item.y % tilesX) * G::OUTW;
+  const int dp = 1 << (lev - 1);
+  const Poly P(nf, dp), PO(nf, dp > 1 ? dp / 2 : 1);
+  int tX, tY;
+  lev_tile_grid(nf, dp, &tX, &tY);
+  int t = item.y;
+  const int tx = t % tX;
+  t /= tX;
+  const int ty = t % tY;
+  t /= tY;
+  const int sa = t % dp, sb = t / dp;        // column and row sub-lattices
+  const int Ma = P.count(sa), Mb = P.count(sb);
+  const int tx0 = tx * G::OUTW, ty0 = ty * G::TY;
+  if (tx0 >= Ma || ty0 >= Mb) return;        // an empty tile (uniform over the CTA)
   const T mu = T(zin_op ? op_mu : pd.mu);
   const TZ* zin;
   TZ* zout;
@@ -675,8 +709,11 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
     zin = static_cast<const TZ*>(pd.z0 ? pd.z0 : pd.z[(st.iter - 1) & 1]);
     zout = static_cast<TZ*>(pd.z[st.iter & 1]);
   }
-  T* sc = reinterpret_cast<T*>(smraw);       // c_{l-1} on rows ty0 - 2D.., cols tx0 - 2D..
-  T* ss = sc + G::CW * G::CH;                // s_l on rows ty0 - D.., cols tx0 - D..
+  // position of the local coordinate m of a sub-lattice in the level's order
+  // (mirrored into the image first)
+  auto cpos = [&](int m, int off, bool* par) { return P.pos(f3_refl(off + dp * m, nf, par)); };
+  T* sc = reinterpret_cast<T*>(smraw);       // c_{l-1} on rows ty0 - 2.., cols tx0 - 2..
+  T* ss = sc + G::CW * G::CH;                // s_l on rows ty0 - 1.., cols tx0 - 1..
   T* sring = ss + G::SW * G::SH;             // per-warp synthesis rings
   {
     const T* cin = (lev == 1) ? frame_u<T>(pd, u_slot)
@@ -685,7 +722,7 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
     for (int idx = threadIdx.x; idx < G::CW * G::CH; idx += NT) {
       const int ry = idx / G::CW, rx = idx - ry * G::CW;
       bool par;
-      const int ay = f3_refl(ty0 - 2 * D + ry, nf, &par), ax = f3_refl(tx0 - 2 * D + rx, nf, &par);
+      const int ay = cpos(ty0 - 2 + ry, sb, &par), ax = cpos(tx0 - 2 + rx, sa, &par);
       const T* g = cin + ((size_t)ay * nf + ax);
       if (sizeof(T) == 8) cp_async_8(sc + idx, g); else cp_async_4(sc + idx, g);
     }
@@ -694,7 +731,7 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
       for (int idx = threadIdx.x; idx < G::SW * G::SH; idx += NT) {
         const int ry = idx / G::SW, rx = idx - ry * G::SW;
         bool par;
-        const int ay = f3_refl(ty0 - D + ry, nf, &par), ax = f3_refl(tx0 - D + rx, nf, &par);
+        const int ay = cpos(ty0 - 1 + ry, sb, &par), ax = cpos(tx0 - 1 + rx, sa, &par);
         const T* g = sin + ((size_t)ay * nf + ax);
         if (sizeof(T) == 8) cp_async_8(ss + idx, g); else cp_async_4(ss + idx, g);
       }
@@ -706,25 +743,26 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg_lo = ty0 + 32 * w, seg_hi = seg_lo + 32;
-  if (seg_lo >= nf) return;                  // no barrier follows
+  if (seg_lo >= Mb) return;                  // no barrier follows
   const T s2q = T(0.35355339059327376220);   // sqrt(2) / 4
-  const int x = tx0 - D + lane;              // this lane's coefficient column
+  const int mx = tx0 - 1 + lane;             // this lane's coefficient column (local)
   bool pcx;
-  const int zc = f3_refl(x, nf, &pcx);
+  const int zc = cpos(mx, sa, &pcx);
   const T scol = pcx ? T(-1) : T(1);
-  const bool own_c = lane >= D && lane < 32 - D && x < nf;
-  const int yc0 = seg_lo - D, yc1 = seg_hi + D;
+  const bool own_c = lane >= 1 && lane < 31 && mx < Ma;
+  const int yc0 = seg_lo - 1, yc1 = seg_hi + 1;
   T* ring = sring + w * (G::PR * 3 * 32) + lane;    // (row slot k, j) at ring[(3 k + j) 32]
-  const T* ccol = sc + (lane + D);                  // c tile column of x
-  const int crow0 = ty0 - 2 * D;
+  const T* ccol = sc + (lane + 1);                  // c tile column of mx
+  const int crow0 = ty0 - 2;
   const int gbase = (lev - 1) * 8 * plane, lbase = 8 * L * plane;
   T* dst = (lev == 1) ? static_cast<T*>(pd.buf[f_slot])
                       : static_cast<T*>(pd.sy) + (size_t)(lev - 2) * plane;
+  const int dcol = (own_c) ? PO.pos(sa + dp * mx) : 0;   // output column in dst's order
   ZGroup<TZ> zq[PF];
   TZ zl[PF];
   auto zload = [&](int y, int k) {
     bool par;
-    const int q = f3_refl(y, nf, &par) * nf + zc;
+    const int q = cpos(y, sb, &par) * nf + zc;
     const uint4* src = reinterpret_cast<const uint4*>(zin + (gbase + 8 * q));
 #pragma unroll
     for (int v = 0; v < NV; ++v) zq[k].v[v] = src[v];
@@ -732,25 +770,25 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
   };
 #pragma unroll
   for (int k = 0; k < PF; ++k) zload(yc0 + k, k);
-  // ring slots of rows y - D, y, y + D (advanced by one per row)
-  int k0 = 0, k1 = D, k2 = 2 * D;
+  // ring slots of rows m - 1, m, m + 1 (advanced by one per row)
+  int k0 = 0, k1 = 1, k2 = 2;
   auto step = [&](int y, int kq) {
-    // horizontal analysis of rows y - D, y, y + D: h[s][j]
+    // horizontal analysis of rows y - 1, y, y + 1: h[s][j]
     T h[3][3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      const T* r = ccol + (y + (s - 1) * D - crow0) * G::CW;
-      const T cm = r[-D], c0 = r[0], cp = r[D];
+      const T* r = ccol + (y + (s - 1) - crow0) * G::CW;
+      const T cm = r[-1], c0 = r[0], cp = r[1];
       const T sp = cm + cp;
       h[s][0] = T(0.25) * sp + T(0.5) * c0;
       h[s][1] = s2q * (cm - cp);
       h[s][2] = T(0.5) * c0 - T(0.25) * sp;
     }
     bool pry;
-    const int zro = f3_refl(y, nf, &pry) * nf;
+    const int zro = cpos(y, sb, &pry) * nf;
     const T srow = pry ? T(-1) : T(1);
     const T s11 = srow * scol;
-    const bool own = own_c && y >= seg_lo && y < seg_hi && y < nf;
+    const bool own = own_c && y >= seg_lo && y < seg_hi && y < Mb;
     const int zwo = zro + zc;
     ZGroup<TZ> zo;
     TZ zlo = TZ(0.0f);
@@ -781,31 +819,31 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
       if (TOP) zout[lbase + zwo] = zlo;
     }
     if (y + PF < yc1) zload(y + PF, kq);
-    // scatter into rows y - D, y, y + D; row y - D is then complete
+    // scatter into rows y - 1, y, y + 1; row y - 1 is then complete
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       ring[(3 * k1 + j) * 32] += p1[j];
       ring[(3 * k2 + j) * 32] += p2[j];
     }
-    T P[3];
+    T Pj[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      P[j] = ring[(3 * k0 + j) * 32] + p0[j];
-      ring[(3 * k0 + j) * 32] = T(0);         // the slot becomes row y + D + 1
+      Pj[j] = ring[(3 * k0 + j) * 32] + p0[j];
+      ring[(3 * k0 + j) * 32] = T(0);         // the slot becomes row y + 2
     }
-    const int r = y - D;
-    const T A = T(0.25) * P[0] + s2q * P[1] - T(0.25) * P[2];
-    const T B = T(0.5) * (P[0] + P[2]);
-    const T C = T(0.25) * P[0] - s2q * P[1] - T(0.25) * P[2];
-    T out = B + __shfl_down_sync(FULL, A, D) + __shfl_up_sync(FULL, C, D);
-    if (r >= seg_lo && own_c && r < nf) {
+    const int r = y - 1;
+    const T A = T(0.25) * Pj[0] + s2q * Pj[1] - T(0.25) * Pj[2];
+    const T B = T(0.5) * (Pj[0] + Pj[2]);
+    const T C = T(0.25) * Pj[0] - s2q * Pj[1] - T(0.25) * Pj[2];
+    T out = B + __shfl_down_sync(FULL, A, 1) + __shfl_up_sync(FULL, C, 1);
+    if (r >= seg_lo && own_c && r < Mb) {
       if (!TOP) {
-        // (b0 x b0)^T s_l at (r, x): rows r - D, r, r + D, columns x - D, x, x + D
-        const T* sr = ss + (r - (ty0 - D)) * G::SW + lane;
-        auto hs = [&](const T* q) { return T(0.25) * (q[-D] + q[D]) + T(0.5) * q[0]; };
-        out += T(0.25) * (hs(sr - D * G::SW) + hs(sr + D * G::SW)) + T(0.5) * hs(sr);
+        // (b0 x b0)^T s_l at (r, mx): positions r - 1, r, r + 1 and mx - 1, mx, mx + 1
+        const T* sr = ss + (r - (ty0 - 1)) * G::SW + lane;
+        auto hs = [&](const T* q) { return T(0.25) * (q[-1] + q[1]) + T(0.5) * q[0]; };
+        out += T(0.25) * (hs(sr - G::SW) + hs(sr + G::SW)) + T(0.5) * hs(sr);
       }
-      dst[(size_t)r * nf + x] = out;
+      dst[(size_t)PO.pos(sb + dp * r) * nf + dcol] = out;
     }
     k0 = (k0 + 1 == G::PR) ? 0 : k0 + 1;
     k1 = (k1 + 1 == G::PR) ? 0 : k1 + 1;
@@ -821,13 +859,13 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
 
 #ifndef MLBA_BODIES_ONLY  // launchers: not in the persistent kernel's unit
 int lev_tiles(int nf, int lev) {
-  const int D = 1 << (lev - 1);
-  const int outw = 32 - 2 * D, ty = 32 * LV_NWR;
-  return ((nf + outw - 1) / outw) * ((nf + ty - 1) / ty);
+  const int dp = 1 << (lev - 1);
+  int tx, ty;
+  lev_tile_grid(nf, dp, &tx, &ty);
+  return dp * dp * tx * ty;
 }
 int lowpass_blocks(int nf) {
-  const size_t plane = (size_t)nf * nf;
-  return (int)((plane + LP_THREADS * LP_PER - 1) / (LP_THREADS * LP_PER));
+  return nf * ((nf + LP_THREADS * LP_PER - 1) / (LP_THREADS * LP_PER));
 }
 
 template <typename T, typename TZ>
@@ -843,17 +881,12 @@ void launch_frame_levels(const Prob* probs, State* states, const int2* items, co
     const int lev = levels - k, off = sec[4 + 2 * k], cnt = sec[5 + 2 * k];
     if (cnt <= 0) continue;
     const int2* it = items + off;
-    const bool top = lev == levels;
-#define LEVK(DD, TT) \
-  k_frame_lev<T, TZ, DD, TT><<<cnt, 32 * LV_NWR, lev_smem_bytes<T, DD>(), s>>>( \
-      probs, states, it, lev, u_slot, f_slot, zin, zout, op_mu)
-    switch (lev) {
-      case 1: LEVK(1, false); break;
-      case 2: LEVK(2, false); break;
-      case 3: if (top) LEVK(4, true); else LEVK(4, false); break;
-      default: if (top) LEVK(8, true); else LEVK(8, false); break;
-    }
-#undef LEVK
+    if (lev == levels)
+      k_frame_lev<T, TZ, true><<<cnt, 32 * LV_NWR, lev_smem_bytes<T>(), s>>>(
+          probs, states, it, lev, u_slot, f_slot, zin, zout, op_mu);
+    else
+      k_frame_lev<T, TZ, false><<<cnt, 32 * LV_NWR, lev_smem_bytes<T>(), s>>>(
+          probs, states, it, lev, u_slot, f_slot, zin, zout, op_mu);
   }
 }
 
@@ -869,40 +902,39 @@ void frame_shape(int shape, int* tile_x, int* tile_y, int* prefetch) {
   *prefetch = F3_SHAPES[shape].ring > 0 ? F3_SHAPES[shape].ring : F3_SHAPES[shape].pf;
 }
 
-// Planar (band-major) <-> grouped z layout (L <= 2), element size E bytes.
+// Planar (band-major) <-> internal z layout (z_index), element size E bytes.
 template <typename E>
-__global__ void k_zlayout(E* __restrict__ dst, const E* __restrict__ src, int nbands, int plane,
-                          int to_grouped) {
-  const size_t tot = (size_t)nbands * plane;
+__global__ void k_zlayout(E* __restrict__ dst, const E* __restrict__ src, int levels, int nf,
+                          int to_internal) {
+  const size_t plane = (size_t)nf * nf;
+  const size_t tot = (size_t)(8 * levels + 1) * plane;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot;
        i += (size_t)gridDim.x * blockDim.x) {
-    const int b = (int)(i / plane), q = (int)(i - (size_t)b * plane);
-    const size_t g = (b < nbands - 1) ? (size_t)(b / 8) * 8 * plane + (size_t)8 * q + (b % 8) : i;
-    if (to_grouped) dst[g] = src[i]; else dst[i] = src[g];
+    const int b = (int)(i / plane);
+    const int q = (int)(i - (size_t)b * plane);
+    const int y = q / nf, x = q - y * nf;
+    const size_t g = z_index(b, y, x, levels, nf);
+    if (to_internal) dst[g] = src[i]; else dst[i] = src[g];
   }
 }
 
 bool z_grouped(int levels) { (void)levels; return true; }
 
-size_t z_grouped_index(int b, size_t q, int nbands, size_t plane) {
-  return (b < nbands - 1) ? (size_t)(b / 8) * 8 * plane + 8 * q + (b % 8) : (size_t)b * plane + q;
-}
-
 void launch_z_layout(void* dst, const void* src, int levels, int nf, int elem_bytes,
                      int to_grouped, cudaStream_t s) {
-  const int nbands = 8 * levels + 1, plane = nf * nf;
-  const size_t tot = (size_t)nbands * plane;
+  const int nbands = 8 * levels + 1;
+  const size_t tot = (size_t)nbands * nf * nf;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (elem_bytes == 8)
     k_zlayout<unsigned long long><<<blocks, 256, 0, s>>>(static_cast<unsigned long long*>(dst),
-        static_cast<const unsigned long long*>(src), nbands, plane, to_grouped);
+        static_cast<const unsigned long long*>(src), levels, nf, to_grouped);
   else if (elem_bytes == 4)
     k_zlayout<unsigned int><<<blocks, 256, 0, s>>>(static_cast<unsigned int*>(dst),
-        static_cast<const unsigned int*>(src), nbands, plane, to_grouped);
+        static_cast<const unsigned int*>(src), levels, nf, to_grouped);
   else
     k_zlayout<unsigned short><<<blocks, 256, 0, s>>>(static_cast<unsigned short*>(dst),
-        static_cast<const unsigned short*>(src), nbands, plane, to_grouped);
+        static_cast<const unsigned short*>(src), levels, nf, to_grouped);
 }
 
 // the kernel of one tile shape, its shared memory and its launch (FP64 has
@@ -972,25 +1004,13 @@ void launch_frame(const Prob* probs, State* states, const int2* items, int nitem
     launch_frame_levels<T, TZ>(probs, states, items, sec, levels, u_slot, f_slot, zin, zout, op_mu, s);
 }
 
-// the level kernels of one precision, for every (dilation, top) pair used
+// the level kernels of one precision (below the top level, the top level)
+// and the low-pass chain kernel
 template <typename T, typename TZ>
 const void* const* lev_kernels() {
-  static const void* const k[] = {
-      (const void*)k_frame_lev<T, TZ, 1, false>, (const void*)k_frame_lev<T, TZ, 2, false>,
-      (const void*)k_frame_lev<T, TZ, 4, false>, (const void*)k_frame_lev<T, TZ, 8, false>,
-      (const void*)k_frame_lev<T, TZ, 4, true>,  (const void*)k_frame_lev<T, TZ, 8, true>,
-      (const void*)k_lowpass<T>};
+  static const void* const k[] = {(const void*)k_frame_lev<T, TZ, false>,
+                                  (const void*)k_frame_lev<T, TZ, true>, (const void*)k_lowpass<T>};
   return k;
-}
-template <typename T>
-size_t lev_kernel_smem(int k) {
-  switch (k) {
-    case 0: return lev_smem_bytes<T, 1>();
-    case 1: return lev_smem_bytes<T, 2>();
-    case 2: case 4: return lev_smem_bytes<T, 4>();
-    case 3: case 5: return lev_smem_bytes<T, 8>();
-    default: return 0;
-  }
 }
 
 template <typename T, typename TZ>
@@ -1004,10 +1024,10 @@ cudaError_t frame_set_smem() {
                              (int)frame3_smem<T, TZ, 2>(sh));
     if (e != cudaSuccess) return e;
   }
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 2; ++k) {
     const cudaError_t e = cudaFuncSetAttribute(lev_kernels<T, TZ>()[k],
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)lev_kernel_smem<T>(k));
+                                               (int)lev_smem_bytes<T>());
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1021,7 +1041,7 @@ bool is_frame_kernel(const void* func) {
     for (const void* f : k)
       if (f == func) return true;
   }
-  for (int k = 0; k < 7; ++k)
+  for (int k = 0; k < 3; ++k)
     if (func == lev_kernels<float, float>()[k] || func == lev_kernels<float, __nv_bfloat16>()[k] ||
         func == lev_kernels<double, double>()[k])
       return true;

@@ -1799,7 +1799,7 @@ int mlba_get_z(mlba_ctx* c, void* z_out, int on_device) {
   const size_t zbytes = (size_t)pd.nbands * plane * es;
   if (!z_grouped(pd.levels)) return copy_out(B, z_out, pd.z[s.iter & 1], zbytes, on_device);
   if (!z_out) return MLBA_E_INVAL;
-  // the library keeps z grouped; the caller gets band-major planes
+  // the library keeps z in its internal order (z_index); the caller gets band-major planes
   if (on_device) {
     launch_z_layout(z_out, pd.z[s.iter & 1], pd.levels, pd.nf, (int)es, 0, B->stream);
     CK(cudaGetLastError());
@@ -1812,7 +1812,8 @@ int mlba_get_z(mlba_ctx* c, void* z_out, int on_device) {
   for (int b = 0; b < pd.nbands; ++b)
     for (size_t q = 0; q < plane; ++q)
       std::memcpy(out + ((size_t)b * plane + q) * es,
-                  raw.data() + z_grouped_index(b, q, pd.nbands, plane) * es, es);
+                  raw.data() + z_index(b, (int)(q / pd.nf), (int)(q % pd.nf), pd.levels, pd.nf) * es,
+                  es);
   return MLBA_OK;
 }
 
@@ -1934,7 +1935,7 @@ int mlba_set_state(mlba_ctx* c, const void* blob, size_t bytes) {
     std::vector<unsigned char> g(zbytes);
     for (int b = 0; b < pd.nbands; ++b)
       for (size_t q = 0; q < plane; ++q)
-        std::memcpy(g.data() + z_grouped_index(b, q, pd.nbands, plane) * es,
+        std::memcpy(g.data() + z_index(b, (int)(q / pd.nf), (int)(q % pd.nf), pd.levels, pd.nf) * es,
                     in + L.z + ((size_t)b * plane + q) * es, es);
     CK(cudaMemcpy(zdst, g.data(), zbytes, cudaMemcpyHostToDevice));
   }

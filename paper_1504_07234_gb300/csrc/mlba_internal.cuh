@@ -148,6 +148,49 @@ __device__ __forceinline__ int refl_half(int e, int n, int* odd) {
   *odd = 1; return m2 - 1 - q;
 }
 
+// Polyphase order of one image axis for a dilation D (a power of two): the
+// position x = a + D m (a = x mod D) is stored at S_a + m with S_a =
+// a Q + min(a, R), nf = D Q + R, so the D sub-lattices of the axis follow one
+// another, each in increasing order (sub-lattice a holds M_a = Q + [a < R]
+// positions).  A plane in this order has its rows and its columns permuted
+// so; D = 1 is the identity.  A filter with taps D apart then reaches
+// neighbouring positions of one sub-lattice.
+struct Poly {
+  int D, sh, Q, R;
+  __host__ __device__ Poly(int nf, int d) : D(d), sh(0), Q(0), R(0) {
+    while ((1 << sh) < d) ++sh;
+    Q = nf >> sh;
+    R = nf - (Q << sh);
+  }
+  __host__ __device__ int count(int a) const { return Q + (a < R ? 1 : 0); }
+  __host__ __device__ int count_max() const { return Q + (R > 0 ? 1 : 0); }
+  __host__ __device__ int start(int a) const { return a * Q + (a < R ? a : R); }
+  __host__ __device__ int pos(int x) const { return start(x & (D - 1)) + (x >> sh); }
+  // x from its position p
+  __host__ __device__ int inv(int p) const {
+    const int big = R * (Q + 1);
+    int a, m;
+    if (p < big) { a = p / (Q + 1); m = p - a * (Q + 1); }
+    else { const int r = p - big; a = R + r / Q; m = r - (a - R) * Q; }
+    return a + (m << sh);
+  }
+};
+
+// Internal position of z band b at pixel (y, x): the 8 high-pass bands of
+// level l of a position are contiguous at (l - 1) 8 nf^2 + 8 q + (b mod 8),
+// the final low-pass band has the plane 8 L nf^2 + q.  q = y nf + x for
+// L <= 2; for L >= 3 the planes of level l are in the polyphase order of its
+// dilation 2^(l-1) (the low-pass band in that of level L), the order in which
+// the per-level kernels sweep them.
+__host__ __device__ inline size_t z_index(int b, int y, int x, int levels, int nf) {
+  const size_t plane = (size_t)nf * nf;
+  const int nb = 8 * levels + 1;
+  const int lev = b < nb - 1 ? b / 8 + 1 : levels;
+  const Poly P(nf, levels >= 3 ? 1 << (lev - 1) : 1);
+  const size_t q = (size_t)P.pos(y) * nf + P.pos(x);
+  return b < nb - 1 ? (size_t)(b / 8) * 8 * plane + 8 * q + (b % 8) : (size_t)b * plane + q;
+}
+
 // Thread groups a body of work runs on: the whole CTA, or a sub-block of NTS
 // threads (whole warps) of a larger CTA with its own hardware barrier `id`
 // (1..15; barrier 0 is __syncthreads).  The bodies of the persistent step

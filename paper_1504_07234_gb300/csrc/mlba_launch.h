@@ -103,10 +103,10 @@ int lowpass_blocks(int nf);                       // CTAs of one low-pass launch
 void frame_shape(int shape, int* tile_x, int* tile_y, int* prefetch);
 bool is_frame_kernel(const void* func);  // func is one of the framelet-update kernels
 int stencil_tiles(int outN);             // CTAs of the stencil for an outN x outN output
-// z layout: grouped (the 8 high bands of a level contiguous per pixel) for
-// L <= 2, band-major planes otherwise; conversion to / from band-major
+// z layout: the 8 high-pass bands of a level contiguous per position, in
+// the polyphase order of the level's dilation for L >= 3 (z_index);
+// conversion to / from band-major planes
 bool z_grouped(int levels);
-size_t z_grouped_index(int b, size_t q, int nbands, size_t plane);
 void launch_z_layout(void* dst, const void* src, int levels, int nf, int elem_bytes,
                      int to_grouped, cudaStream_t s);
 template <typename T, typename TZ>
