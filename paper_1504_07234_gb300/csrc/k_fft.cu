@@ -165,19 +165,6 @@ __device__ __forceinline__ void dft_small(T2* v) {
 __host__ __device__ constexpr int tr_nt(int elem_bytes) { return elem_bytes == 8 ? 512 : 256; }
 __host__ __device__ constexpr int tr_minb(int elem_bytes) { return elem_bytes == 8 ? 1 : 4; }
 
-// n / d by a multiply-high: m = floor((2^32 - 1) / d) + 1 gives the exact
-// quotient whenever 0 <= n and n d < 2^32 (every index here is below 2^17
-// and every divisor at most 8192); d = 1 passes n through
-struct FastDiv {
-  unsigned m;
-  int d;
-  __device__ __forceinline__ explicit FastDiv(int dd)
-      : m(dd > 1 ? 0xFFFFFFFFu / (unsigned)dd + 1u : 0u), d(dd) {}
-  __device__ __forceinline__ int div(int n) const {
-    return d == 1 ? n : (int)__umulhi((unsigned)n, m);
-  }
-};
-
 // shared-memory layout of a transform: element i at fpad(i) (one spare slot
 // every 16 breaks power-of-two strides), transforms TSg = fpad(N) + 1 apart
 __host__ __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }

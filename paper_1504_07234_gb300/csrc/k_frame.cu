@@ -595,8 +595,8 @@ __device__ __forceinline__ const T* frame_u(const Prob& pd, int u_slot) {
 // c_lev = (b0 x b0) with dilation d = 2^(lev-1) applied to c_{lev-1}, half-
 // sample mirror at the border.  c_{lev-1} is read in the polyphase order of d
 // (u, lev = 1: plain) and c_lev is written in that of 2d, the order of the
-// kernels that read it.  item.y = (output row, chunk of LP_THREADS LP_PER
-// positions of it) in the output order.
+// kernels that read it.  item.y = output row (in the output order); the
+// threads stride along it, LP_PER positions in flight each.
 template <typename T>
 __global__ void __launch_bounds__(LP_THREADS)
 k_lowpass(const Prob* __restrict__ probs, const State* __restrict__ states,
@@ -607,27 +607,29 @@ k_lowpass(const Prob* __restrict__ probs, const State* __restrict__ states,
   const int nf = pd.nf;
   const size_t plane = (size_t)nf * nf;
   const int d = 1 << (lev - 1);
-  const Poly pin(nf, d), pout(nf, 2 * d);
+  const Poly pin(nf, d);
+  const PolyInv pout(nf, 2 * d);
   const T* in = (lev == 1) ? frame_u<T>(pd, u_slot)
                            : static_cast<const T*>(pd.lp) + (size_t)(lev - 2) * plane;
-  constexpr int CH = LP_THREADS * LP_PER;
-  const int chunks = (nf + CH - 1) / CH;
-  const int py = item.y / chunks, px0 = (item.y - py * chunks) * CH;
+  const int py = item.y;
   T* out = static_cast<T*>(pd.lp) + (size_t)(lev - 1) * plane + (size_t)py * nf;
   const int y = pout.inv(py);
   bool par;
   const T* rm = in + (size_t)pin.pos(f3_refl(y - d, nf, &par)) * nf;
   const T* r0 = in + (size_t)pin.pos(y) * nf;
   const T* rp = in + (size_t)pin.pos(f3_refl(y + d, nf, &par)) * nf;
+#pragma unroll 1
+  for (int p0 = 0; p0 < nf; p0 += LP_THREADS * LP_PER) {
 #pragma unroll
-  for (int k = 0; k < LP_PER; ++k) {
-    const int px = px0 + threadIdx.x + k * LP_THREADS;
-    if (px >= nf) break;
-    const int x = pout.inv(px);
-    const int xm = pin.pos(f3_refl(x - d, nf, &par)), xc = pin.pos(x),
-              xp = pin.pos(f3_refl(x + d, nf, &par));
-    auto row = [&](const T* q) { return T(0.25) * (q[xm] + q[xp]) + T(0.5) * q[xc]; };
-    out[px] = T(0.25) * (row(rm) + row(rp)) + T(0.5) * row(r0);
+    for (int k = 0; k < LP_PER; ++k) {
+      const int px = p0 + threadIdx.x + k * LP_THREADS;
+      if (px >= nf) break;
+      const int x = pout.inv(px);
+      const int xm = pin.pos(f3_refl(x - d, nf, &par)), xc = pin.pos(x),
+                xp = pin.pos(f3_refl(x + d, nf, &par));
+      auto row = [&](const T* q) { return T(0.25) * (q[xm] + q[xp]) + T(0.5) * q[xc]; };
+      out[px] = T(0.25) * (row(rm) + row(rp)) + T(0.5) * row(r0);
+    }
   }
 }
 
@@ -864,9 +866,7 @@ int lev_tiles(int nf, int lev) {
   lev_tile_grid(nf, dp, &tx, &ty);
   return dp * dp * tx * ty;
 }
-int lowpass_blocks(int nf) {
-  return nf * ((nf + LP_THREADS * LP_PER - 1) / (LP_THREADS * LP_PER));
-}
+int lowpass_blocks(int nf) { return nf; }
 
 template <typename T, typename TZ>
 void launch_frame_levels(const Prob* probs, State* states, const int2* items, const int* sec,

@@ -148,6 +148,19 @@ __device__ __forceinline__ int refl_half(int e, int n, int* odd) {
   *odd = 1; return m2 - 1 - q;
 }
 
+// n / d by a multiply-high: m = floor((2^32 - 1) / d) + 1 gives the exact
+// quotient whenever 0 <= n and n d < 2^32 (every index here is below 2^17
+// and every divisor at most 8192); d = 1 passes n through
+struct FastDiv {
+  unsigned m;
+  int d;
+  __device__ __forceinline__ explicit FastDiv(int dd)
+      : m(dd > 1 ? 0xFFFFFFFFu / (unsigned)dd + 1u : 0u), d(dd) {}
+  __device__ __forceinline__ int div(int n) const {
+    return d == 1 ? n : (int)__umulhi((unsigned)n, m);
+  }
+};
+
 // Polyphase order of one image axis for a dilation D (a power of two): the
 // position x = a + D m (a = x mod D) is stored at S_a + m with S_a =
 // a Q + min(a, R), nf = D Q + R, so the D sub-lattices of the axis follow one
@@ -173,6 +186,21 @@ struct Poly {
     if (p < big) { a = p / (Q + 1); m = p - a * (Q + 1); }
     else { const int r = p - big; a = R + r / Q; m = r - (a - R) * Q; }
     return a + (m << sh);
+  }
+};
+
+// Poly::inv with the two quotients by multiply-high (device code)
+struct PolyInv {
+  Poly P;
+  FastDiv q1, q0;
+  int big;
+  __device__ __forceinline__ PolyInv(int nf, int d)
+      : P(nf, d), q1(P.Q + 1), q0(P.Q > 0 ? P.Q : 1), big(P.R * (P.Q + 1)) {}
+  __device__ __forceinline__ int inv(int p) const {
+    int a, m;
+    if (p < big) { a = q1.div(p); m = p - a * (P.Q + 1); }
+    else { const int r = p - big; const int k = q0.div(r); a = P.R + k; m = r - k * P.Q; }
+    return a + (m << P.sh);
   }
 };
 

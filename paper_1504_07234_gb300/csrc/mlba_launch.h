@@ -91,8 +91,8 @@ void launch_spectrum_setup(int transform, int n, int p, int half, int cb, const 
 // The framelet step.  levels <= 2: one launch of the fused sweep over
 // `items` in tile shape `shape`.  levels >= 3: the item list holds sections
 // whose (offset, count) pairs `sec` gives: the BC fold of the correlation
-// (VEC_FOLD items, skipped when u_slot >= 0), the low-pass chain (blocks of
-// LP_THREADS * LP_PER values), then the level kernels of level L, L-1, ..., 1.
+// (VEC_FOLD items, skipped when u_slot >= 0), the low-pass chain (one block
+// per output row), then the level kernels of level L, L-1, ..., 1.
 template <typename T, typename TZ>
 void launch_frame(const Prob* probs, State* states, const int2* items, int nitems, const int* sec,
                   int u_slot, int f_slot, const void* zin, void* zout, double op_mu, int levels,
