@@ -317,6 +317,9 @@ def main():
     ap.add_argument("--persistent", action="store_true",
                     help="the K steps as one persistent cooperative launch (grid barriers "
                          "between the stages) instead of the captured graphs")
+    ap.add_argument("--blur-path", default="direct", choices=["direct", "fft", "auto"],
+                    help="how A and A^T are applied: direct stencils (default), FFT convolution, "
+                         "or per problem the faster of the two (timed at create)")
     ap.add_argument("--autotune", type=int, default=2, choices=[0, 1, 2],
                     help="framelet tile shape: 0 built-in, 1 timed at create or read from the "
                          "on-disk cache, 2 timed at create (default)")
@@ -325,13 +328,18 @@ def main():
     ap.add_argument("--config", default="4", choices=["4", "1", "2", "3", "5", "l4"],
                     help="workload: 4 = the 64-problem batch (default); 1, 2, 3, 5, l4 = the "
                          "single-image workloads")
+    ap.add_argument("--size", type=int, default=None,
+                    help="single-image workloads: run at this n instead (profiling)")
+    ap.add_argument("--iters", type=int, default=None,
+                    help="single-image workloads 1, 3, 5, l4: iteration budget (profiling)")
     ap.add_argument("--no-configs", action="store_true",
                     help="default run: skip the per-config record of the single-image workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    global AUTOTUNE
+    global AUTOTUNE, SIZE
     AUTOTUNE = args.autotune
+    SIZE = args.size
     if args.impl == "reference":
         return run_reference(args)
     if args.config != "4":
@@ -358,7 +366,7 @@ def main():
     max_iter = W + K + 2 * reps_prof + 20
     batch = M.Batch(descs(probs), dtype="f32", levels=2, stop=False, max_iter=max_iter,
                     rect_ns_hybrid=True, two_group=not args.one_group,
-                    persistent=args.persistent, autotune=AUTOTUNE)
+                    persistent=args.persistent, autotune=AUTOTUNE, blur_path=args.blur_path)
     stream = batch.stream
     # warm-up
     batch.iterate(W)
@@ -445,7 +453,7 @@ def main():
                            "schedule": "one persistent launch for the K steps" if args.persistent
                            else "one group" if args.one_group else
                            "two groups half a step apart on two streams",
-                           "frame_tiles": tiles},
+                           "frame_tiles": tiles, "blur_path": args.blur_path},
                 "clocks": ck, "e2e": e2e, "gpu_launches": 1 if args.persistent else kernels * K,
                 "roofline": roofline,
                 "step_roofline": {"min_bytes": bmin, "frac": step_frac, "peak": hbm},
@@ -487,13 +495,16 @@ def stage_bytes_one(p, tbytes):
     return out
 
 
+SIZE = None          # --size: a single-image workload at another n (profiling)
+
+
 def _single_problem(c, variant=None):
     if c == "l4":
-        pr = I.config(5)
+        pr = I.config(5, n=SIZE)
         pr.levels = 4
         pr.name = "C5-L4"
         return pr
-    return I.config(int(c), variant=variant)
+    return I.config(int(c), variant=variant, n=SIZE)
 
 
 def _run_batch(M, torch, pr, dtype, iters, z_store=None, warm=0, stop=None, profile=False):
@@ -577,6 +588,8 @@ def measure_config(M, torch, c, compact=False, iters=None, warm=5):
     hbm, peak_kind = measured_peaks()
     out = {"workload": I.CONFIG_NAMES.get(int(c), "") if c != "l4" else
            "rect 4096x4096, 31x31 Gaussian sigma=5, DCT + NS alpha, L=4 (the paper's level count)"}
+    if SIZE:
+        out["workload"] += f" (run at n = {SIZE})"
     if c == "1":
         pr = _single_problem(c)
         it = iters or pr.max_iter
@@ -679,7 +692,7 @@ def run_single_config(args):
         cpu = oracle_config_sample(c)
     clocks = ClockSampler(local)
     clocks.start()
-    rec = measure_config(M, torch, c)
+    rec = measure_config(M, torch, c, iters=args.iters)
     ck = clocks.stop()
     pr = _single_problem(c, "rect1" if c == "3" else None)
     line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1,
