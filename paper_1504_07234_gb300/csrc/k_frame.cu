@@ -595,8 +595,11 @@ __device__ __forceinline__ const T* frame_u(const Prob& pd, int u_slot) {
 // c_lev = (b0 x b0) with dilation d = 2^(lev-1) applied to c_{lev-1}, half-
 // sample mirror at the border.  c_{lev-1} is read in the polyphase order of d
 // (u, lev = 1: plain) and c_lev is written in that of 2d, the order of the
-// kernels that read it.  item.y = output row (in the output order); the
-// threads stride along it, LP_PER positions in flight each.
+// kernels that read it.  The launch walks the input order: item.y = input
+// row; for each column sub-lattice a of d the threads stride along it, its
+// taps d apart being its neighbouring positions (contiguous reads), and its
+// even and odd positions land in the output sub-lattices a and a + d (two
+// contiguous runs of writes).
 template <typename T>
 __global__ void __launch_bounds__(LP_THREADS)
 k_lowpass(const Prob* __restrict__ probs, const State* __restrict__ states,
@@ -607,28 +610,29 @@ k_lowpass(const Prob* __restrict__ probs, const State* __restrict__ states,
   const int nf = pd.nf;
   const size_t plane = (size_t)nf * nf;
   const int d = 1 << (lev - 1);
-  const Poly pin(nf, d);
-  const PolyInv pout(nf, 2 * d);
+  const Poly pin(nf, d), pout(nf, 2 * d);
   const T* in = (lev == 1) ? frame_u<T>(pd, u_slot)
                            : static_cast<const T*>(pd.lp) + (size_t)(lev - 2) * plane;
-  const int py = item.y;
-  T* out = static_cast<T*>(pd.lp) + (size_t)(lev - 1) * plane + (size_t)py * nf;
-  const int y = pout.inv(py);
+  const int iy = item.y;
+  const int y = pin.inv(iy);
   bool par;
   const T* rm = in + (size_t)pin.pos(f3_refl(y - d, nf, &par)) * nf;
-  const T* r0 = in + (size_t)pin.pos(y) * nf;
+  const T* r0 = in + (size_t)iy * nf;
   const T* rp = in + (size_t)pin.pos(f3_refl(y + d, nf, &par)) * nf;
-#pragma unroll 1
-  for (int p0 = 0; p0 < nf; p0 += LP_THREADS * LP_PER) {
-#pragma unroll
-    for (int k = 0; k < LP_PER; ++k) {
-      const int px = p0 + threadIdx.x + k * LP_THREADS;
-      if (px >= nf) break;
-      const int x = pout.inv(px);
-      const int xm = pin.pos(f3_refl(x - d, nf, &par)), xc = pin.pos(x),
-                xp = pin.pos(f3_refl(x + d, nf, &par));
-      auto row = [&](const T* q) { return T(0.25) * (q[xm] + q[xp]) + T(0.5) * q[xc]; };
-      out[px] = T(0.25) * (row(rm) + row(rp)) + T(0.5) * row(r0);
+  T* out = static_cast<T*>(pd.lp) + (size_t)(lev - 1) * plane + (size_t)pout.pos(y) * nf;
+  for (int a = 0; a < d; ++a) {
+    const int ma = pin.count(a), sa = pin.start(a);
+    // output run starts of the even and odd positions of sub-lattice a
+    const int oe = a < nf ? pout.pos(a) : 0, oo = (a + d < nf) ? pout.pos(a + d) : 0;
+#pragma unroll 4
+    for (int m = threadIdx.x; m < ma; m += LP_THREADS) {
+      const int ic = sa + m;
+      int im = ic - 1, ip = ic + 1;             // neighbours inside the sub-lattice
+      if (m == 0) im = pin.pos(f3_refl(a - d, nf, &par));
+      if (m == ma - 1) ip = pin.pos(f3_refl(a + d * (m + 1), nf, &par));
+      auto row = [&](const T* q) { return T(0.25) * (q[im] + q[ip]) + T(0.5) * q[ic]; };
+      const T v = T(0.25) * (row(rm) + row(rp)) + T(0.5) * row(r0);
+      out[(m & 1) ? oo + (m >> 1) : oe + (m >> 1)] = v;
     }
   }
 }
