@@ -471,16 +471,20 @@ def test_batch_own_stop_rules(M):
     b.close()
 
 
-@pytest.mark.parametrize("bc,precond,transform,psf,alpha", [
-    ("periodic", "tikh_ns", "dft", I.psf_motion(7, 0.9), 0.05),
-    ("zero", "krylov", "dft", I.psf_motion(7, 0.9), 0.05),
-    ("rect", "bccb", "dft", I.psf_motion(7, 0.9), 0.3)])
-def test_checkpoint_resume_matches_uninterrupted(M, bc, precond, transform, psf, alpha):
+@pytest.mark.parametrize("bc,precond,transform,psf,alpha,levels,n", [
+    ("periodic", "tikh_ns", "dft", I.psf_motion(7, 0.9), 0.05, 2, 48),
+    ("zero", "krylov", "dft", I.psf_motion(7, 0.9), 0.05, 2, 48),
+    ("rect", "bccb", "dft", I.psf_motion(7, 0.9), 0.3, 2, 40),
+    # L >= 3: z of levels 2.. kept in polyphase order, converted to band-major
+    # planes in the blob and back
+    ("rect", "bccb", "dft", I.psf_motion(7, 0.9), 0.3, 4, 37),
+    ("reflective", "tikh_ns", "dct", I.psf_disk(3), 0.05, 3, 45)])
+def test_checkpoint_resume_matches_uninterrupted(M, bc, precond, transform, psf, alpha, levels, n):
     """mlba_get_state after 5 iterations, mlba_set_state into a fresh context,
     5 more iterations: the same f, residual history and alpha_n / beta_n as 10
-    uninterrupted iterations (the same kernels run on the same data)."""
-    n = 48 if bc != "rect" else 40
-    pr = small(bc, precond, n=n, psf=psf, alpha=alpha, transform=transform, iters=10)
+    uninterrupted iterations (the same kernels run on the same data), and the
+    resumed context's z (band-major) equals the one it was saved from."""
+    pr = small(bc, precond, n=n, psf=psf, alpha=alpha, transform=transform, iters=10, levels=levels)
     kw = dict(mu=pr.mu, alpha=pr.alpha, levels=pr.levels, max_iter=10, stop=False, gamma=pr.gamma,
               q=pr.q, rho=pr.rho, transform=pr.transform)
     full = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype="f64", **kw)
@@ -493,11 +497,13 @@ def test_checkpoint_resume_matches_uninterrupted(M, bc, precond, transform, psf,
     a.set_data(pr.g, pr.delta)
     a.iterate(5)
     blob = a.get_state()
+    z_saved = a.get_z().cpu().numpy()
     a.close()
     b = M.Context(pr.psf, pr.n, pr.bc, pr.precond, dtype="f64", **kw)
     b.set_data(pr.g, pr.delta)
     b.set_state(blob)
     assert b.stats()["iter"] == 5
+    assert np.array_equal(b.get_z().cpu().numpy(), z_saved)
     b.iterate(6)
     f = b.result()
     res, al, be = b.history()
