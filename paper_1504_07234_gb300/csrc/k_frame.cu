@@ -649,13 +649,11 @@ struct LV {
   static constexpr int OUTW = 30;                 // output columns of a tile
   static constexpr int TY = 32 * LV_NWR;
   static constexpr int CW = 34, CH = TY + 4;      // c tile: positions tx0 - 2.., ty0 - 2..
-  static constexpr int SW = 32, SH = TY + 2;      // s tile: positions tx0 - 1.., ty0 - 1..
   static constexpr int PR = 3;                    // synthesis ring rows
 };
 template <typename T>
 __host__ __device__ constexpr size_t lev_smem_bytes() {
-  return ((size_t)LV::CW * LV::CH + (size_t)LV::SW * LV::SH + (size_t)LV_NWR * LV::PR * 3 * 32) *
-         sizeof(T);
+  return ((size_t)LV::CW * LV::CH + (size_t)LV_NWR * LV::PR * 3 * 32) * sizeof(T);
 }
 // tiles of one sub-lattice pair and of the whole level
 __host__ __device__ inline void lev_tile_grid(int nf, int dp, int* tx, int* ty) {
@@ -671,7 +669,9 @@ __host__ __device__ inline void lev_tile_grid(int nf, int dp, int* tx, int* ty) 
 // order), the threshold, and the vertical synthesis scattered into a ring of
 // three rows (shared memory, one column per lane); row m - 1 then has all
 // its contributions and is combined horizontally by warp shuffles at +-1 and,
-// for l < L, with (b0 x b0)^T s_l from the s tile.  s_{l-1} is written in the
+// for l < L, with (b0 x b0)^T s_l: each lane loads s_l at its own column
+// with the z rows (PF rows ahead) and keeps the horizontally filtered rows
+// m - 2 .. m in registers (shuffles at +-1).  s_{l-1} is written in the
 // polyphase order of dp / 2 (f, and s_1, plainly).  Coefficients outside the
 // image are mirrored with the sign of the band's symmetry, as in k_frame3.
 template <typename T, typename TZ, bool TOP>
@@ -719,8 +719,7 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
   // (mirrored into the image first)
   auto cpos = [&](int m, int off, bool* par) { return P.pos(f3_refl(off + dp * m, nf, par)); };
   T* sc = reinterpret_cast<T*>(smraw);       // c_{l-1} on rows ty0 - 2.., cols tx0 - 2..
-  T* ss = sc + G::CW * G::CH;                // s_l on rows ty0 - 1.., cols tx0 - 1..
-  T* sring = ss + G::SW * G::SH;             // per-warp synthesis rings
+  T* sring = sc + G::CW * G::CH;             // per-warp synthesis rings
   {
     const T* cin = (lev == 1) ? frame_u<T>(pd, u_slot)
                               : static_cast<const T*>(pd.lp) + (size_t)(lev - 2) * plane;
@@ -731,16 +730,6 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
       const int ay = cpos(ty0 - 2 + ry, sb, &par), ax = cpos(tx0 - 2 + rx, sa, &par);
       const T* g = cin + ((size_t)ay * nf + ax);
       if (sizeof(T) == 8) cp_async_8(sc + idx, g); else cp_async_4(sc + idx, g);
-    }
-    if (!TOP) {
-      const T* sin = static_cast<const T*>(pd.sy) + (size_t)(lev - 1) * plane;
-      for (int idx = threadIdx.x; idx < G::SW * G::SH; idx += NT) {
-        const int ry = idx / G::SW, rx = idx - ry * G::SW;
-        bool par;
-        const int ay = cpos(ty0 - 1 + ry, sb, &par), ax = cpos(tx0 - 1 + rx, sa, &par);
-        const T* g = sin + ((size_t)ay * nf + ax);
-        if (sizeof(T) == 8) cp_async_8(ss + idx, g); else cp_async_4(ss + idx, g);
-      }
     }
     cp_commit();
     for (int idx = threadIdx.x; idx < LV_NWR * G::PR * 3 * 32; idx += NT) sring[idx] = T(0);
@@ -764,8 +753,10 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
   T* dst = (lev == 1) ? static_cast<T*>(pd.buf[f_slot])
                       : static_cast<T*>(pd.sy) + (size_t)(lev - 2) * plane;
   const int dcol = (own_c) ? PO.pos(sa + dp * mx) : 0;   // output column in dst's order
+  const T* sin = TOP ? nullptr : static_cast<const T*>(pd.sy) + (size_t)(lev - 1) * plane;
   ZGroup<TZ> zq[PF];
   TZ zl[PF];
+  T sq[PF];
   auto zload = [&](int y, int k) {
     bool par;
     const int q = cpos(y, sb, &par) * nf + zc;
@@ -773,7 +764,10 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
 #pragma unroll
     for (int v = 0; v < NV; ++v) zq[k].v[v] = src[v];
     if (TOP) zl[k] = zin[lbase + q];
+    else sq[k] = sin[q];                     // s_l at (y, mx), mirrored like z
   };
+  // (b0 x b0)^T s_l: horizontally filtered s_l rows m - 2, m - 1 (registers)
+  T hs2 = T(0), hs1 = T(0);
 #pragma unroll
   for (int k = 0; k < PF; ++k) zload(yc0 + k, k);
   // ring slots of rows m - 1, m, m + 1 (advanced by one per row)
@@ -824,6 +818,11 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
       for (int v = 0; v < NV; ++v) dz[v] = zo.v[v];
       if (TOP) zout[lbase + zwo] = zlo;
     }
+    T hs0 = T(0);
+    if (!TOP) {
+      const T sv = sq[kq];
+      hs0 = T(0.25) * (__shfl_up_sync(FULL, sv, 1) + __shfl_down_sync(FULL, sv, 1)) + T(0.5) * sv;
+    }
     if (y + PF < yc1) zload(y + PF, kq);
     // scatter into rows y - 1, y, y + 1; row y - 1 is then complete
 #pragma unroll
@@ -843,14 +842,12 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
     const T C = T(0.25) * Pj[0] - s2q * Pj[1] - T(0.25) * Pj[2];
     T out = B + __shfl_down_sync(FULL, A, 1) + __shfl_up_sync(FULL, C, 1);
     if (r >= seg_lo && own_c && r < Mb) {
-      if (!TOP) {
-        // (b0 x b0)^T s_l at (r, mx): positions r - 1, r, r + 1 and mx - 1, mx, mx + 1
-        const T* sr = ss + (r - (ty0 - 1)) * G::SW + lane;
-        auto hs = [&](const T* q) { return T(0.25) * (q[-1] + q[1]) + T(0.5) * q[0]; };
-        out += T(0.25) * (hs(sr - G::SW) + hs(sr + G::SW)) + T(0.5) * hs(sr);
-      }
+      // (b0 x b0)^T s_l at (r, mx): rows r - 1 = y - 2, r, r + 1 = y
+      if (!TOP) out += T(0.25) * (hs2 + hs0) + T(0.5) * hs1;
       dst[(size_t)PO.pos(sb + dp * r) * nf + dcol] = out;
     }
+    hs2 = hs1;
+    hs1 = hs0;
     k0 = (k0 + 1 == G::PR) ? 0 : k0 + 1;
     k1 = (k1 + 1 == G::PR) ? 0 : k1 + 1;
     k2 = (k2 + 1 == G::PR) ? 0 : k2 + 1;
