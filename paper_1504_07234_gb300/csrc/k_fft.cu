@@ -826,6 +826,11 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
 }
 
 
+// bring the 128-byte line of p into L2 (no registers, no wait)
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // spectral weight at blocked index idx; alpha and kind as given.  |lambda|^2 +
 // alpha is formed in T: alpha > 0 keeps it away from zero (no cancellation),
 // so FP32 holds it to 6e-8 relative; 1/n^2 of the unnormalised pair is folded in.
@@ -898,6 +903,20 @@ __device__ __forceinline__ void cols_body(const int2 item, const Prob* __restric
   const size_t base = (size_t)item.y * N * cb;       // this CTA's contiguous block
   const int W = dct ? N : pd.half;
   const int kb = item.y * cb;                         // first column of the block
+  // The weights |lambda|^2 (and lambda) of this block are read only after the
+  // forward transform; ask L2 for their lines now so that the HBM latency
+  // overlaps the block load and the passes (one prefetch per 128-byte line)
+  if (mode != COL_FWD || kept) {
+    const char* ws = reinterpret_cast<const char*>(static_cast<const T*>(pd.w) + base);
+    const size_t wb = (size_t)N * cb * sizeof(T);
+    for (size_t o = (size_t)threadIdx.x * 128; o < wb; o += (size_t)NT * 128) prefetch_l2(ws + o);
+    if (kind == W_TIKH) {
+      const size_t le = dct ? sizeof(T) : 2 * sizeof(T);
+      const char* ls = static_cast<const char*>(pd.lam) + base * le;
+      for (size_t o = (size_t)threadIdx.x * 128; o < (size_t)N * cb * le; o += (size_t)NT * 128)
+        prefetch_l2(ls + o);
+    }
+  }
   if (!dct && (cb & 1) == 0) {
     // an even number of complex columns: columns 2h and 2h + 1 (transforms
     // 2h, 2h + 1) move together, quad (k1, h) at 2 (k1 cb / 2 + h)
