@@ -826,11 +826,6 @@ k_rows_fwd(const Prob* __restrict__ probs, State* __restrict__ states, const int
 }
 
 
-// bring the 128-byte line of p into L2 (no registers, no wait)
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // spectral weight at blocked index idx; alpha and kind as given.  |lambda|^2 +
 // alpha is formed in T: alpha > 0 keeps it away from zero (no cancellation),
 // so FP32 holds it to 6e-8 relative; 1/n^2 of the unnormalised pair is folded in.

@@ -148,6 +148,11 @@ __device__ __forceinline__ int refl_half(int e, int n, int* odd) {
   *odd = 1; return m2 - 1 - q;
 }
 
+// bring the 128-byte line of p into L2 (no registers, no wait)
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // n / d by a multiply-high: m = floor((2^32 - 1) / d) + 1 gives the exact
 // quotient whenever 0 <= n and n d < 2^32 (every index here is below 2^17
 // and every divisor at most 8192); d = 1 passes n through
