@@ -122,6 +122,12 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
 // on the fly by the level-2 sweep) and the level-2 part of f, so there are no
 // shared-memory atomics; the only CTA-wide barrier follows the u tile.
 constexpr int F3_TX = 26;      // tile columns: level-2 output lanes 3..28 after the +-1 low-pass
+// rows past the register queue whose z lines are prefetched into L2: the
+// queue holds PF rows in registers, the prefetch reaches further without
+// holding any (measured on the 64-problem batch and on L = 4: 0.61 -> 0.51 ms
+// per framelet launch; distances 1..10 tried)
+constexpr int Z_L2_AHEAD = 2;   // k_frame3
+constexpr int LV_L2_AHEAD = 1;  // k_frame_lev
 constexpr int F3_SEG = 32;     // rows per warp
 // Tile shapes the autotuner chooses from: warps (32-row segments) per CTA and
 // the z prefetch distance in rows.  Every shape computes the same values in
@@ -393,6 +399,17 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
       if (TOP) zout[lbase + zwo] = zlo;
     }
     if (y + F3_PF < yc1) zload(y + F3_PF, kq);
+    if constexpr (RING == 0) {
+      // the z lines of a row further ahead into L2 (no registers held): the
+      // register queue then finds them there
+      const int ya = y + F3_PF + Z_L2_AHEAD;
+      if (ya < yc1) {
+        bool par;
+        const int qa = f3_refl(ya, nf, &par) * nf + zc;
+        prefetch_l2(zin + (gbase + 8 * qa));
+        if (TOP) prefetch_l2(zin + (lbase + qa));
+      }
+    }
     // row y - D has all its contributions: horizontal synthesis
     const int r = y - D;
     if (r >= yo0) {
@@ -824,6 +841,16 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
       hs0 = T(0.25) * (__shfl_up_sync(FULL, sv, 1) + __shfl_down_sync(FULL, sv, 1)) + T(0.5) * sv;
     }
     if (y + PF < yc1) zload(y + PF, kq);
+    {
+      const int ya = y + PF + LV_L2_AHEAD;     // z (and s_l) lines further ahead into L2
+      if (ya < yc1) {
+        bool par;
+        const int qa = cpos(ya, sb, &par) * nf + zc;
+        prefetch_l2(zin + (gbase + 8 * qa));
+        if (TOP) prefetch_l2(zin + (lbase + qa));
+        else prefetch_l2(sin + qa);
+      }
+    }
     // scatter into rows y - 1, y, y + 1; row y - 1 is then complete
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
