@@ -637,6 +637,10 @@ k_lowpass(const Prob* __restrict__ probs, const State* __restrict__ states,
   const T* r0 = in + (size_t)iy * nf;
   const T* rp = in + (size_t)pin.pos(f3_refl(y + d, nf, &par)) * nf;
   T* out = static_cast<T*>(pd.lp) + (size_t)(lev - 1) * plane + (size_t)pout.pos(y) * nf;
+  // the three input rows into L2 first (the sweep below then finds them there)
+  prefetch_range(rm, (size_t)nf * sizeof(T), threadIdx.x, LP_THREADS);
+  prefetch_range(r0, (size_t)nf * sizeof(T), threadIdx.x, LP_THREADS);
+  prefetch_range(rp, (size_t)nf * sizeof(T), threadIdx.x, LP_THREADS);
   for (int a = 0; a < d; ++a) {
     const int ma = pin.count(a), sa = pin.start(a);
     // output run starts of the even and odd positions of sub-lattice a

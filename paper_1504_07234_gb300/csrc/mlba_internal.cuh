@@ -153,6 +153,15 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// L2 prefetch of every 128-byte line of [p, p + bytes) by the threads
+// tid = 0 .. nt - 1 of a group
+__device__ __forceinline__ void prefetch_range(const void* p, size_t bytes, int tid, int nt) {
+  const size_t a0 = reinterpret_cast<size_t>(p) & ~size_t(127);
+  const size_t a1 = reinterpret_cast<size_t>(p) + bytes;
+  for (size_t a = a0 + (size_t)tid * 128; a < a1; a += (size_t)nt * 128)
+    prefetch_l2(reinterpret_cast<const void*>(a));
+}
+
 // n / d by a multiply-high: m = floor((2^32 - 1) / d) + 1 gives the exact
 // quotient whenever 0 <= n and n d < 2^32 (every index here is below 2^17
 // and every divisor at most 8192); d = 1 passes n through
