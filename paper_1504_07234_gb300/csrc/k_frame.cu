@@ -744,16 +744,24 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
   {
     const T* cin = (lev == 1) ? frame_u<T>(pd, u_slot)
                               : static_cast<const T*>(pd.lp) + (size_t)(lev - 2) * plane;
-    constexpr int NT = 32 * LV_NWR;
-    for (int idx = threadIdx.x; idx < G::CW * G::CH; idx += NT) {
-      const int ry = idx / G::CW, rx = idx - ry * G::CW;
-      bool par;
-      const int ay = cpos(ty0 - 2 + ry, sb, &par), ax = cpos(tx0 - 2 + rx, sa, &par);
-      const T* g = cin + ((size_t)ay * nf + ax);
-      if (sizeof(T) == 8) cp_async_8(sc + idx, g); else cp_async_4(sc + idx, g);
+    // one warp per tile row (the row's position mapped once), lanes along the
+    // row (columns lane and lane + 32, mapped once per lane)
+    static_assert(G::CW <= 64, "two columns per lane");
+    const int wq = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    bool par;
+    const int ax0 = cpos(tx0 - 2 + ln, sa, &par);
+    const bool two = ln + 32 < G::CW;
+    const int ax1 = two ? cpos(tx0 - 2 + ln + 32, sa, &par) : 0;
+    for (int ry = wq; ry < G::CH; ry += LV_NWR) {
+      const T* row = cin + (size_t)cpos(ty0 - 2 + ry, sb, &par) * nf;
+      T* d = sc + ry * G::CW + ln;
+      if (sizeof(T) == 8) cp_async_8(d, row + ax0); else cp_async_4(d, row + ax0);
+      if (two) {
+        if (sizeof(T) == 8) cp_async_8(d + 32, row + ax1); else cp_async_4(d + 32, row + ax1);
+      }
     }
     cp_commit();
-    for (int idx = threadIdx.x; idx < LV_NWR * G::PR * 3 * 32; idx += NT) sring[idx] = T(0);
+    for (int idx = threadIdx.x; idx < LV_NWR * G::PR * 3 * 32; idx += 32 * LV_NWR) sring[idx] = T(0);
     cp_wait<0>();
   }
   __syncthreads();
