@@ -51,7 +51,7 @@ constexpr int VEC_THREADS = 256;
 constexpr int VEC_PER_THREAD = 8;
 constexpr int TR_CAP = 4096;          // complex values held by one transform CTA
 constexpr int FRAME_SHAPES = 8;      // tile shapes of the L <= 2 framelet kernel (k_frame.cu)
-constexpr int LV_NWR = 2;            // warps per CTA of the per-level framelet kernel (L >= 3)
+constexpr int LV_NWR = 1;            // warps per CTA of the per-level framelet kernel (L >= 3; 1, 2, 4 measured)
 constexpr int LP_THREADS = 256, LP_PER = 4;   // low-pass chain kernel (L >= 3)
 constexpr int FRAME_SECTIONS = 2 + 4;         // fold, low-pass, up to four levels
 constexpr int SPEC_THREADS = 256;    // alpha_n solve (k_fft.cu)
