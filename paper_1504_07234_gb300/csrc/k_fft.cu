@@ -385,14 +385,18 @@ __device__ __forceinline__ bool tr_skip(const State& st, int pcg) {
 //   h'' = 2 sum |r^|^2 x^2 (1-x)(2-3x) / P.
 // The spectrum in S is the unnormalised one; every coefficient carries its
 // orthonormal weight, so the ratio is exact.  Pass 1 evaluates h and h' at
-// NS_CAND points b_prev + (j - 7.5) NS_CAND_STEP, brackets the root and
-// takes the root of the cubic Hermite interpolant on the bracket.  Later
+// NS_CAND points b_prev + (j - (NS_CAND - 1)/2) NS_CAND_STEP (a window of
+// +-7 around the previous root), brackets the root and takes the root of the
+// cubic Hermite interpolant on the bracket.  Later
 // passes take safeguarded Halley steps inside the bracket; a step below
 // tol, or below ns_tol3 (the next error is of the order of its cube), ends
 // the solve.  Each block sums its share in T precision (FP64 across
 // blocks); the last block updates the scalar state.
-constexpr int NS_CAND = 16;
-constexpr double NS_CAND_STEP = 1.0;
+// 8 candidates 2 apart: the candidate sums are the bulk of the bracketing
+// pass, and the wider Hermite bracket costs at most one more Halley pass
+// (FP32: 2 of the 3 in the step, FP64: 3 of 5 on the workloads' spectra)
+constexpr int NS_CAND = 8;
+constexpr double NS_CAND_STEP = 2.0;
 constexpr int NS_NT = SPEC_THREADS, NS_PT = SPEC_PER_THREAD;
 constexpr int NS_B = 8;                    // elements per thread with loads in flight together
 static_assert(NS_PT % NS_B == 0, "spectrum pass batches");
@@ -439,6 +443,7 @@ __device__ __forceinline__ void ns_set_alpha(const Prob& pd, State& st, double n
   if (nb < -32.2) nb = -32.2;                          // alpha floor 1e-14
   st.nb = nb;
   double a = exp(nb);
+  st.ea = a;
   if (pd.bc == BC_RECT && a < pd.alpha) a = pd.alpha;  // rectangular hybrid floor
   st.alpha_n = a;
   const int it = st.iter - 1;
@@ -508,25 +513,29 @@ __device__ bool ns_reduce(const Prob& pd, State& st, int blk, int nblk, A (&v)[K
 }
 
 // root in [0, 1] of the cubic Hermite interpolant with p(0) = h0 < 0 <= p(1)
-// = h1 and slopes m0, m1 (per unit t): bisection-safeguarded Newton
-static __device__ double hermite_root(double h0, double h1, double m0, double m1) {
-  auto p = [&](double t, double* dp) {
-    const double t2 = t * t, t3 = t2 * t;
-    const double H00 = 2 * t3 - 3 * t2 + 1, H10 = t3 - 2 * t2 + t;
-    const double H01 = -2 * t3 + 3 * t2, H11 = t3 - t2;
-    *dp = h0 * (6 * t2 - 6 * t) + m0 * (3 * t2 - 4 * t + 1) + h1 * (-6 * t2 + 6 * t) +
-          m1 * (3 * t2 - 2 * t);
+// = h1 and slopes m0, m1 (per unit t): bisection-safeguarded Newton.  The
+// root only seeds the Halley passes (the interpolant itself is off by far
+// more than FP32 rounding), so it runs in FP32 to 1e-6 in t: one thread of
+// the launch's last block runs it, and a dependent FP64 chain there (long
+// FP64 latency on this part) was the longest path of the whole launch.
+static __device__ float hermite_root(float h0, float h1, float m0, float m1) {
+  auto p = [&](float t, float* dp) {
+    const float t2 = t * t, t3 = t2 * t;
+    const float H00 = 2.f * t3 - 3.f * t2 + 1.f, H10 = t3 - 2.f * t2 + t;
+    const float H01 = -2.f * t3 + 3.f * t2, H11 = t3 - t2;
+    *dp = h0 * (6.f * t2 - 6.f * t) + m0 * (3.f * t2 - 4.f * t + 1.f) +
+          h1 * (-6.f * t2 + 6.f * t) + m1 * (3.f * t2 - 2.f * t);
     return h0 * H00 + m0 * H10 + h1 * H01 + m1 * H11;
   };
-  double lo = 0.0, hi = 1.0;
-  double t = (h1 > h0) ? -h0 / (h1 - h0) : 0.5;
-  for (int it = 0; it < 40; ++it) {
-    double dp;
-    const double v = p(t, &dp);
-    if (v < 0.0) lo = t; else hi = t;
-    double tn = (dp > 0.0) ? t - v / dp : 0.5 * (lo + hi);
-    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-    if (fabs(tn - t) < 1e-14) { t = tn; break; }
+  float lo = 0.f, hi = 1.f;
+  float t = (h1 > h0) ? -h0 / (h1 - h0) : 0.5f;
+  for (int it = 0; it < 32; ++it) {
+    float dp;
+    const float v = p(t, &dp);
+    if (v < 0.f) lo = t; else hi = t;
+    float tn = (dp > 0.f) ? t - v / dp : 0.5f * (lo + hi);
+    if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
+    if (fabsf(tn - t) < 1e-6f || hi - lo < 1e-6f) { t = tn; break; }
     t = tn;
   }
   return t;
@@ -556,7 +565,8 @@ static __device__ void ns_bracket_finish(const Prob& pd, State& st, const double
     nb = fmin(nb, bv(NS_CAND - 1) + 4.0);
   } else {
     st.nb_lo = bv(j - 1); st.nb_hi = bv(j);
-    const double t = hermite_root(hv(j - 1), hv(j), dv(j - 1) * NS_CAND_STEP, dv(j) * NS_CAND_STEP);
+    const double t = hermite_root((float)hv(j - 1), (float)hv(j), (float)(dv(j - 1) * NS_CAND_STEP),
+                                  (float)(dv(j) * NS_CAND_STEP));
     nb = st.nb_lo + t * NS_CAND_STEP;
   }
   st.nphase = 1;
@@ -565,23 +575,23 @@ static __device__ void ns_bracket_finish(const Prob& pd, State& st, const double
 }
 
 // accumulate one spectral coefficient (weighted power pf, sigma sf) into the
-// candidate sums
-// (candidates in pairs: two-wide FP32 instructions, one reciprocal each)
-__device__ __forceinline__ void ns_cand_acc(float pf, float sf, const float (&ca)[NS_CAND],
-                                            float (&cF)[NS_CAND], float (&cG)[NS_CAND]) {
-  const float2 s2 = make_float2(sf, sf), p2 = make_float2(pf, pf);
+// candidate sums.  With ci = 1/a_j, x = a_j/(s + a_j) = 1/(1 + s ci) needs one
+// FMA and one reciprocal; F_j += pf x^2 and H_j += pf x^3, so that
+// G_j = F_j - H_j = sum pf x^2 (1 - x) (the Hermite slopes only seed the
+// Halley passes, whose sums form 1 - x directly).  Candidates in pairs:
+// two-wide FP32 instructions.
+__device__ __forceinline__ void ns_cand_acc(float pf, float sf, const float (&ci)[NS_CAND],
+                                            float (&cF)[NS_CAND], float (&cH)[NS_CAND]) {
+  const float2 s2 = make_float2(sf, sf), p2 = make_float2(pf, pf), one = make_float2(1.f, 1.f);
 #pragma unroll
   for (int j = 0; j < NS_CAND; j += 2) {
-    const float2 a = make_float2(ca[j], ca[j + 1]);
-    const float2 d = __fadd2_rn(s2, a);
-    const float2 x = __fmul2_rn(a, make_float2(__fdividef(1.f, d.x), __fdividef(1.f, d.y)));
+    const float2 d = __ffma2_rn(s2, make_float2(ci[j], ci[j + 1]), one);
+    const float2 x = make_float2(__fdividef(1.f, d.x), __fdividef(1.f, d.y));
     const float2 px2 = __fmul2_rn(__fmul2_rn(p2, x), x);
     const float2 f = __fadd2_rn(make_float2(cF[j], cF[j + 1]), px2);
-    // + pw x^2 (1 - x)
-    const float2 g = __ffma2_rn(make_float2(-px2.x, -px2.y), x,
-                                __fadd2_rn(make_float2(cG[j], cG[j + 1]), px2));
+    const float2 h = __ffma2_rn(px2, x, make_float2(cH[j], cH[j + 1]));
     cF[j] = f.x; cF[j + 1] = f.y;
-    cG[j] = g.x; cG[j + 1] = g.y;
+    cH[j] = h.x; cH[j + 1] = h.y;
   }
 }
 
@@ -597,7 +607,7 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
   constexpr int K = 2 * NS_CAND + 1;
   __shared__ double red[K * (NT / 32)];
   __shared__ double tot[K];
-  __shared__ float s_ca[NS_CAND];
+  __shared__ float s_ci[NS_CAND];
   const int N = pd.n, cb = pd.cb;
   const bool dct = pd.transform == TR_DCT;
   const int W = dct ? N : pd.half;
@@ -606,17 +616,17 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
   const T* w = static_cast<const T*>(pd.w) + base;
   T* pwo = static_cast<T*>(pd.pw) + base;   // weighted powers for the Halley passes
   if (threadIdx.x < NS_CAND)
-    s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
+    s_ci[threadIdx.x] = expf(-(float)(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP));
   __syncthreads();
-  float ca[NS_CAND], cF[NS_CAND], cG[NS_CAND];
+  float ci[NS_CAND], cF[NS_CAND], cH[NS_CAND];
 #pragma unroll
-  for (int j = 0; j < NS_CAND; ++j) { ca[j] = s_ca[j]; cF[j] = 0.f; cG[j] = 0.f; }
+  for (int j = 0; j < NS_CAND; ++j) { ci[j] = s_ci[j]; cF[j] = 0.f; cH[j] = 0.f; }
   const FastDiv fcb(cb);
   T sP = T(0);
   // chunks of MV elements per thread: the chunk's sigma loads first (in
   // flight together), then its sums; a short chunk keeps the unrolled body
-  // (MV x NS_CAND candidate updates) small enough for the instruction cache
-  constexpr int MV = 4;
+  // (MV x NS_CAND = 64 candidate updates) small enough for the instruction cache
+  constexpr int MV = 64 / NS_CAND;
 #pragma unroll 1
   for (int e0 = 0; e0 < N * cb; e0 += MV * NT) {
   float wv[MV];
@@ -643,12 +653,12 @@ __device__ __noinline__ void ns_cand_block(const Prob& pd, State& st, int blk, c
     }
     pwo[e] = pw;
     sP += pw;
-    ns_cand_acc((float)pw, wv[qq], ca, cF, cG);
+    ns_cand_acc((float)pw, wv[qq], ci, cF, cH);
   }
   }
   T v[K];
 #pragma unroll
-  for (int j = 0; j < NS_CAND; ++j) { v[j] = T(cF[j]); v[NS_CAND + j] = T(cG[j]); }
+  for (int j = 0; j < NS_CAND; ++j) { v[j] = T(cF[j]); v[NS_CAND + j] = T(cF[j]) - T(cH[j]); }
   v[2 * NS_CAND] = sP;
   if (ns_reduce<NT, K, T>(pd, st, blk, pd.nblk_cols, v, red, tot) && threadIdx.x == 0)
     ns_bracket_finish(pd, st, tot, b0);
@@ -899,13 +909,14 @@ __device__ __forceinline__ void cols_body(const int2 item, const Prob* __restric
   const int W = dct ? N : pd.half;
   const int kb = item.y * cb;                         // first column of the block
   // The weights |lambda|^2 (and lambda) of this block are read only after the
-  // forward transform; ask L2 for their lines now so that the HBM latency
-  // overlaps the block load and the passes (one prefetch per 128-byte line)
-  if (mode != COL_FWD || kept) {
+  // forward transform (|lambda|^2 also by the bracketing pass); ask L2 for
+  // their lines now so that the HBM latency overlaps the block load and the
+  // passes (one prefetch per 128-byte line)
+  if (mode != COL_FWD || kept || cand) {
     const char* ws = reinterpret_cast<const char*>(static_cast<const T*>(pd.w) + base);
     const size_t wb = (size_t)N * cb * sizeof(T);
     for (size_t o = (size_t)threadIdx.x * 128; o < wb; o += (size_t)NT * 128) prefetch_l2(ws + o);
-    if (kind == W_TIKH) {
+    if (kind == W_TIKH && !cand) {
       const size_t le = dct ? sizeof(T) : 2 * sizeof(T);
       const char* ls = static_cast<const char*>(pd.lam) + base * le;
       for (size_t o = (size_t)threadIdx.x * 128; o < (size_t)N * cb * le; o += (size_t)NT * 128)
@@ -1317,18 +1328,18 @@ k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const in
   constexpr int K = 2 * NS_CAND + 1;
   __shared__ double red[K * (NS_NT / 32)];
   __shared__ double tot[K];
-  __shared__ float s_ca[NS_CAND];
+  __shared__ float s_ci[NS_CAND];
   const int2 item = items[blockIdx.x];
   const Prob& pd = probs[item.x];
   State& st = states[item.x];
   if (st.stopped || !pd.ns || !st.ns_active || st.nconv || st.nphase != 0) return;
   const double b0 = st.nb;
   if (threadIdx.x < NS_CAND)
-    s_ca[threadIdx.x] = (float)exp(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP);
+    s_ci[threadIdx.x] = expf(-(float)(b0 + (threadIdx.x - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP));
   __syncthreads();
-  float ca[NS_CAND], cF[NS_CAND], cG[NS_CAND];
+  float ci[NS_CAND], cF[NS_CAND], cH[NS_CAND];
 #pragma unroll
-  for (int j = 0; j < NS_CAND; ++j) { ca[j] = s_ca[j]; cF[j] = 0.f; cG[j] = 0.f; }
+  for (int j = 0; j < NS_CAND; ++j) { ci[j] = s_ci[j]; cF[j] = 0.f; cH[j] = 0.f; }
   T sP = T(0);
 #pragma unroll 1
   for (int q0 = 0; q0 < NS_PT; q0 += NS_B) {
@@ -1343,12 +1354,12 @@ k_spec_cand(const Prob* __restrict__ probs, State* __restrict__ states, const in
       if (L < pd.nblk_cols * pd.n * pd.cb) static_cast<T*>(pd.pw)[L] = ok[q] ? pw[q] : T(0);
       if (!ok[q]) continue;
       sP += pw[q];
-      ns_cand_acc((float)pw[q], (float)sg[q], ca, cF, cG);
+      ns_cand_acc((float)pw[q], (float)sg[q], ci, cF, cH);
     }
   }
   T v[K];
 #pragma unroll
-  for (int j = 0; j < NS_CAND; ++j) { v[j] = T(cF[j]); v[NS_CAND + j] = T(cG[j]); }
+  for (int j = 0; j < NS_CAND; ++j) { v[j] = T(cF[j]); v[NS_CAND + j] = T(cF[j]) - T(cH[j]); }
   v[2 * NS_CAND] = sP;
   if (ns_reduce<NS_NT, K, T>(pd, st, item.y, pd.nblk_spec, v, red, tot) && threadIdx.x == 0)
     ns_bracket_finish(pd, st, tot, b0);
@@ -1363,11 +1374,9 @@ __device__ __forceinline__ void spec_body(const int2 item, const Prob* __restric
   State& st = states[item.x];
   if (st.stopped || !pd.ns || !st.ns_active || st.nconv || st.nphase != 1) return;
   const double b0 = st.nb;
-  // exp in FP64 once per CTA (FP64 throughput is scarce), shared with the block
-  __shared__ T s_alpha;
-  if (threadIdx.x == 0) s_alpha = T(exp(b0));
-  __syncthreads();
-  const T alpha = s_alpha;
+  // exp(b0), formed in FP64 where b0 was set (FP64 latency is long on this
+  // part: no exp per CTA)
+  const T alpha = T(st.ea);
   // the weighted powers (0 on padding) and sigma, both blocked like S
   const int nel = pd.nblk_cols * pd.n * pd.cb;
   const T* P = static_cast<const T*>(pd.pw);

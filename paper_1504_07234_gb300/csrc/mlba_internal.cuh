@@ -100,6 +100,7 @@ struct State {
   int beta_last;
   double resnorm, alpha_n, qn;
   double nb, nb_lo, nb_hi;     // Newton on log(alpha)
+  double ea;                   // exp(nb), set with nb (before the rectangular floor)
   double prho, prho0, pa, pbeta;
 };
 

@@ -56,7 +56,7 @@ constexpr int LP_THREADS = 256, LP_PER = 4;   // low-pass chain kernel (L >= 3)
 constexpr int FRAME_SECTIONS = 2 + 4;         // fold, low-pass, up to four levels
 constexpr int SPEC_THREADS = 256;    // alpha_n solve (k_fft.cu)
 constexpr int SPEC_PER_THREAD = 32;
-constexpr int SPEC_SUMS = 33;        // block sums of the bracketing pass (2 x 16 candidates + 1)
+constexpr int SPEC_SUMS = 17;        // block sums of the bracketing pass (2 x 8 candidates + 1)
 
 template <typename T>
 void launch_stencil(int mode, const Prob* probs, State* states, const int2* items, int nitems,
