@@ -66,6 +66,61 @@ def test_batch64_full_size_sampled(M):
     b.close()
 
 
+def test_batch64_over_the_timed_iterations(M):
+    """The 64-problem batch exactly as the benchmark runs it (FP32, two-group
+    graph schedule, autotuned framelet tile, every problem running its budget
+    with the discrepancy point recorded) for 25 steps, the span of a short
+    timed run (5 warm-up + 20 timed) during which the alpha_n solves are
+    active.  Sampled problems of every kind up to 384^2 are compared with the
+    FP64 oracle run for the same 25 iterations: f, the last residual norm and
+    alpha_n, the discrepancy point (within one iteration) and the
+    restoration bars (RRE within 1e-3, PSNR within 0.05 dB)."""
+    import bench
+    probs = bench.problems_for_rank(0)
+    iters = 25
+    b = M.Batch(bench.descs(probs), dtype="f32", levels=2, stop=False, max_iter=iters,
+                rect_ns_hybrid=True, autotune=bench.AUTOTUNE)
+    b.iterate(iters + 1)
+    kinds = {}
+    for i, p in enumerate(probs):
+        if p.n <= 384:
+            kinds.setdefault((p.bc, p.precond), []).append(i)
+    sample = set()
+    for ix in kinds.values():
+        ix = sorted(ix, key=lambda i: (probs[i].n, i))
+        sample.update(ix[:2])
+        sample.add(ix[-1])
+    for i in sorted(sample):
+        p = probs[i]
+        ref = oracle_run(p, iters)
+        st = b.stats(i)
+        assert st["iter"] == iters, (i, st)
+        f = b.result(i).astype(np.float64)
+        scale = np.abs(ref["f"]).max()
+        where = (i, p.n, p.bc, p.precond)
+        assert np.abs(f - ref["f"]).max() <= 1e-3 * scale, where
+        np.testing.assert_allclose(st["resnorm"], ref["resnorms"][-1], rtol=1e-4, err_msg=str(where))
+        if ref["stop_iter"] is None:
+            assert st["stop_iter"] < 0 or st["stop_iter"] >= iters - 1, where
+        else:
+            assert abs(st["stop_iter"] - ref["stop_iter"]) <= 1, where
+        if p.precond == "tikh_ns":
+            if ref["stop_iter"] is None:
+                np.testing.assert_allclose(st["alpha_n"], ref["alphas"][-1], rtol=1e-3,
+                                           err_msg=str(where))
+            elif st["stop_iter"] == ref["stop_iter"]:
+                # past the discrepancy point alpha_n is the one kept from the
+                # iteration before it, where tau_n -> tau and q_n -> 1: the
+                # root of Eq. Alg4_rev_7 is ill-conditioned there (a relative
+                # change of 1e-6 in ||r|| moved it by ~3e-3 in these runs)
+                np.testing.assert_allclose(st["alpha_n"], ref["alphas"][-1], rtol=2e-2,
+                                           err_msg=str(where))
+        t = p.truth_in_fov()
+        assert abs(O.rre(f, t) - O.rre(ref["f"], t)) <= 1e-3, where
+        assert abs(O.psnr(f, t) - O.psnr(ref["f"], t)) <= 0.05, where
+    b.close()
+
+
 @pytest.mark.parametrize("variant,z_store", [("rect1", None), ("rect2", None), ("rect3", None),
                                              ("rect1", "bf16")])
 def test_config3_full_size(M, variant, z_store):
@@ -166,3 +221,51 @@ def test_config5_first_iterate_windows(M):
         if y0 + w <= n and x0 + w <= n:
             ref_a = O.blur(fr[y0:y0 + w + p - 1, x0:x0 + w + p - 1].astype(np.float64), h, "rect")
             assert np.abs(af[y0:y0 + w, x0:x0 + w] - ref_a).max() <= 1e-5 * np.abs(ref_a).max()
+
+
+def test_config5_alpha_n_root_after_several_steps(M):
+    """4096^2 workload, alpha_n at a later iteration.  The oracle's loop is far
+    too slow at this size, so this checks a property that holds at any size:
+    the alpha_n the device chose at iteration k is the root of Eq. Alg4_rev_7
+    for the residual r^k = g - A f^k of its own iterate (Algorithm 4-NS):
+        alpha^2 sum w |r^|^2 / (sigma + alpha)^2 = q_k^2 sum w |r^|^2,
+    q_k = max{q, 2 rho + (1 + rho)/tau_k}, tau_k = ||r^k|| / delta, with the
+    orthonormal DCT and sigma the squared eigenvalues of the reflective
+    matrix of the symmetric PSF; the rectangular hybrid floors it at alpha.
+    r^k is formed here in FP64 from the device's f^k (valid convolution)."""
+    from scipy import fft as sfft
+    from scipy import signal
+    pr = I.config(5)
+    n, h = pr.n, pr.psf
+    k = 5
+    ctx = M.Context(h, n, "rect", "tikh_ns", dtype="f32", mu=pr.mu, alpha=pr.alpha, levels=2,
+                    max_iter=k + 1, stop=False, gamma=pr.gamma, q=pr.q, rho=pr.rho,
+                    transform="dct", rect_ns_hybrid=True)
+    ctx.set_data(pr.g, pr.delta)
+    ctx.iterate(k)
+    fk = ctx.result().astype(np.float64)
+    ctx.iterate(1)
+    res, al, _ = ctx.history()
+    ctx.close()
+    assert len(al) >= k + 1
+    r = pr.g.astype(np.float64) - signal.fftconvolve(fk, h, mode="valid")
+    rn = float(np.linalg.norm(r))
+    np.testing.assert_allclose(res[k], rn, rtol=1e-5)
+    tau = rn / pr.delta
+    qk = max(pr.q, 2 * pr.rho + (1 + pr.rho) / tau)
+    sigma = _spectrum_dct_windowed(h, n) ** 2
+    pw = sfft.dctn(r, type=2, norm="ortho") ** 2
+    P = pw.sum()
+
+    def h_and_slope(a):
+        x = a / (sigma + a)
+        return (pw * x * x).sum() / P - qk * qk, 2.0 * (pw * x * x * (1 - x)).sum() / P
+
+    a = al[k]
+    hv, d = h_and_slope(a)
+    if a > pr.alpha * (1 + 1e-6):
+        # |log alpha - log root| ~ |h| / h' (h increases with log alpha)
+        assert abs(hv) / d <= 1e-4, (a, hv, d)
+    else:
+        # floored: the root lies at or below the floor
+        assert a == pytest.approx(pr.alpha, rel=1e-6) and hv >= -1e-4 * d, (a, hv, d)
