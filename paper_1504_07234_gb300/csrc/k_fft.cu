@@ -462,23 +462,28 @@ __device__ bool ns_reduce(const Prob& pd, State& st, int blk, int nblk, A (&v)[K
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ int is_last;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if constexpr (K >= 32) {
-    // values 0..31: reduce-scatter across the warp (31 exchanges instead of
-    // 160): at each halving a lane keeps the half of its values selected by
-    // its lane bit and adds its partner's copy; lane l ends with value l
+  // values 0..KS-1 (KS the largest power of two <= min(K, 32)): reduce-scatter
+  // across the warp.  At each halving a lane keeps the half of its values
+  // selected by its lane bit and adds its partner's copy; then the lane
+  // groups' partial sums are added (xor KS .. 16), and lane l < KS ends with
+  // value l: KS - 1 + log2(32 / KS) exchanges instead of 5 KS, and one
+  // conversion to FP64 per warp instead of KS (FP64 work is slow on this part
+  // and queues on one pipe per SM when the CTAs of a launch finish together)
+  constexpr int KS = K >= 32 ? 32 : K >= 16 ? 16 : K >= 8 ? 8 : K >= 4 ? 4 : K >= 2 ? 2 : 1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const bool hi = (l & o) != 0;
+  for (int o = KS / 2; o > 0; o >>= 1) {
+    const bool hi = (l & o) != 0;
 #pragma unroll
-      for (int i = 0; i < o; ++i) {
-        const A send = hi ? v[i] : v[i + o];
-        const A keep = hi ? v[i + o] : v[i];
-        v[i] = keep + __shfl_xor_sync(FULL, send, o);
-      }
+    for (int i = 0; i < o; ++i) {
+      const A send = hi ? v[i] : v[i + o];
+      const A keep = hi ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(FULL, send, o);
     }
-    sh[l * NW + w] = (double)v[0];
   }
-  constexpr int K0 = (K >= 32) ? 32 : 0;
+#pragma unroll
+  for (int o = KS; o < 32; o <<= 1) v[0] += __shfl_xor_sync(FULL, v[0], o);
+  if (l < KS) sh[l * NW + w] = (double)v[0];
+  constexpr int K0 = KS;
 #pragma unroll
   for (int k = K0; k < K; ++k)
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
@@ -502,8 +507,19 @@ __device__ bool ns_reduce(const Prob& pd, State& st, int blk, int nblk, A (&v)[K
   if (!is_last) return false;
   __threadfence();
   for (int k = w; k < K; k += NW) {
+    // lane l adds blocks l, l + 32, ... in that order; 8 loads in flight at a
+    // time (one L2 round trip per 256 blocks rather than per 32)
+    const double* pk = pd.partial + (size_t)k * nblk;
     double s = 0.0;
-    for (int i = l; i < nblk; i += 32) s += __ldcg(&pd.partial[(size_t)k * nblk + i]);
+    int i = l;
+    for (; i + 7 * 32 < nblk; i += 8 * 32) {
+      double a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = __ldcg(pk + i + u * 32);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += a[u];
+    }
+    for (; i < nblk; i += 32) s += __ldcg(pk + i);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (l == 0) tot[k] = s;
   }
@@ -545,8 +561,9 @@ static __device__ float hermite_root(float h0, float h1, float m0, float m1) {
 // sums at the candidates, P last) bracket the root and take the Hermite root.
 static __device__ void ns_bracket_finish(const Prob& pd, State& st, const double* tot, double b0) {
   const double P = tot[2 * NS_CAND], target = st.qn * st.qn;
-  auto hv = [&](int j) { return P > 0.0 ? tot[j] / P - target : 0.0; };
-  auto dv = [&](int j) { return P > 0.0 ? 2.0 * tot[NS_CAND + j] / P : 0.0; };
+  const double iP = P > 0.0 ? 1.0 / P : 0.0;      // one FP64 division
+  auto hv = [&](int j) { return P > 0.0 ? tot[j] * iP - target : 0.0; };
+  auto dv = [&](int j) { return 2.0 * tot[NS_CAND + j] * iP; };
   auto bv = [&](int j) { return b0 + (j - 0.5 * (NS_CAND - 1)) * NS_CAND_STEP; };
   int j = 0;
   while (j < NS_CAND && !(hv(j) >= 0.0)) ++j;
@@ -904,7 +921,8 @@ __device__ __forceinline__ void cols_body(const int2 item, const Prob* __restric
   if (mode == COL_OP) { alpha = op_alpha; kind = op_kind; }
   if (pd.precond == P_KRYLOV) kind = W_INV;
   const T Ta = T(alpha);
-  const T Tsc = T(1.0 / ((double)pd.n * (double)pd.n));
+  // 1/n^2 (n^2 < 2^24 is exact in FP32; the FP64 division stays in FP64 runs)
+  const T Tsc = T(1) / T((double)pd.n * (double)pd.n);
   const size_t base = (size_t)item.y * N * cb;       // this CTA's contiguous block
   const int W = dct ? N : pd.half;
   const int kb = item.y * cb;                         // first column of the block
@@ -1408,9 +1426,10 @@ __device__ __forceinline__ void spec_body(const int2 item, const Prob* __restric
   if (ns_reduce<NS_NT, 4, T>(pd, st, item.y, pd.nblk_spec, v, red, tot) && threadIdx.x == 0) {
     const double P = tot[0];
     const double target = st.qn * st.qn;
-    const double h = (P > 0.0) ? tot[1] / P - target : 0.0;
-    const double h1 = (P > 0.0) ? 2.0 * tot[2] / P : 0.0;
-    const double h2 = (P > 0.0) ? 2.0 * tot[3] / P : 0.0;
+    const double iP = (P > 0.0) ? 1.0 / P : 0.0;  // one FP64 division
+    const double h = (P > 0.0) ? tot[1] * iP - target : 0.0;
+    const double h1 = 2.0 * tot[2] * iP;
+    const double h2 = 2.0 * tot[3] * iP;
     const double nb = b0;
     if (h < 0.0) st.nb_lo = fmax(st.nb_lo, nb);
     else if (h > 0.0) st.nb_hi = fmin(st.nb_hi, nb);

@@ -317,8 +317,16 @@ __device__ bool last_block_reduce_b(const Prob& pd, State& st, int blk, int nblk
   if (!*flag) return false;
   __threadfence();
   for (int k = 0; k < K; ++k) {
+    // thread t adds blocks t, t + NT, ... in that order, 4 loads in flight
+    const double* pk = pd.partial + (size_t)k * nblk;
     double s = 0.0;
-    for (int i = t; i < nblk; i += NT) s += __ldcg(&pd.partial[(size_t)k * nblk + i]);
+    int i = t;
+    for (; i + 3 * NT < nblk; i += 4 * NT) {
+      const double a0 = __ldcg(pk + i), a1 = __ldcg(pk + i + NT);
+      const double a2 = __ldcg(pk + i + 2 * NT), a3 = __ldcg(pk + i + 3 * NT);
+      s += a0; s += a1; s += a2; s += a3;
+    }
+    for (; i < nblk; i += NT) s += __ldcg(pk + i);
     s = block_sum_b<NT>(s, sh, b);
     if (t == 0) tot[k] = s;
   }
