@@ -275,11 +275,17 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   // ring, the low-pass value only)
   ZGroup<TZ> zq[RING > 0 ? 1 : F3_PF];
   TZ zl[F3_PF];
+  // each queued row's mirrored offset and mirroring parity, mapped once when
+  // the row is queued and used again when it is swept
+  int zqo[F3_PF];
+  bool zqp[F3_PF];
   // (idle lanes load a valid mirrored column too; their values are unused.
   // Offsets stay in 32 bits: nbands nf^2 < 2^31.)
   auto zload = [&](int y, int k) {
     bool par;
     const int q = f3_refl(y, nf, &par) * nf + zc;
+    zqo[k] = q;
+    zqp[k] = par;
     if constexpr (RING == 0) {
       const uint4* src = reinterpret_cast<const uint4*>(zin + (gbase + 8 * q));
 #pragma unroll
@@ -363,14 +369,12 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
       else if (!bulk) cp_commit();
     }
     hrow(y + D, hr[2 * D]);
-    bool pry;
-    const int zro = f3_refl(y, nf, &pry) * nf;
     // z outside the image is its mirror image; antisymmetric (b1) bands
     // change sign under an odd number of mirrorings
-    const T srow = pry ? T(-1) : T(1);
+    const T srow = zqp[kq] ? T(-1) : T(1);
     const T s11 = srow * scol;
     const bool own = own_c && y >= seg_lo && y < seg_hi && y < nf;
-    const int zwo = zro + zc;
+    const int zwo = zqo[kq];
     ZGroup<TZ> zo;
     TZ zlo = TZ(0.0f);
 #pragma unroll
@@ -786,9 +790,13 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
   ZGroup<TZ> zq[PF];
   TZ zl[PF];
   T sq[PF];
+  int zqo[PF];                               // queued rows' offsets and parities
+  bool zqp[PF];
   auto zload = [&](int y, int k) {
     bool par;
     const int q = cpos(y, sb, &par) * nf + zc;
+    zqo[k] = q;
+    zqp[k] = par;
     const uint4* src = reinterpret_cast<const uint4*>(zin + (gbase + 8 * q));
 #pragma unroll
     for (int v = 0; v < NV; ++v) zq[k].v[v] = src[v];
@@ -813,12 +821,10 @@ k_frame_lev(const Prob* __restrict__ probs, State* __restrict__ states,
       h[s][1] = s2q * (cm - cp);
       h[s][2] = T(0.5) * c0 - T(0.25) * sp;
     }
-    bool pry;
-    const int zro = cpos(y, sb, &pry) * nf;
-    const T srow = pry ? T(-1) : T(1);
+    const T srow = zqp[kq] ? T(-1) : T(1);
     const T s11 = srow * scol;
     const bool own = own_c && y >= seg_lo && y < seg_hi && y < Mb;
-    const int zwo = zro + zc;
+    const int zwo = zqo[kq];
     ZGroup<TZ> zo;
     TZ zlo = TZ(0.0f);
     T p0[3] = {T(0), T(0), T(0)}, p1[3] = {T(0), T(0), T(0)}, p2[3] = {T(0), T(0), T(0)};
