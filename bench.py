@@ -418,17 +418,16 @@ def main():
     d2h = sum(x.numel() * 4 for x in pinned_f)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i, p in enumerate(probs):
-        batch.set_data(i, pinned_g[i].numpy(), p.delta)
+    batch.set_data_all([x.numpy() for x in pinned_g], [p.delta for p in probs])
     batch.reset()
     batch.iterate(K)
-    for i in range(len(probs)):
-        batch.result(i, out=pinned_f[i].numpy())
+    batch.result_all([x.numpy() for x in pinned_f])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": mpix * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
            "d2h_bytes_per_step": d2h / K,
-           "note": f"one call sequence = upload 64 g, reset, {K} iterations, download 64 f"}
+           "note": f"one call sequence = upload of every g (one call), reset, {K} iterations, "
+                   "download of every f (one call)"}
     batch.close()
 
     extra = {}

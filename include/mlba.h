@@ -285,6 +285,22 @@ int mlba_batch_reset(mlba_batch* b);
  * iteration state is left as it is (call mlba_batch_reset to restart).
  * Host source: synchronises. */
 int mlba_batch_set_data(mlba_batch* b, int i, const void* g, int g_on_device, double delta);
+/* Every problem at once (the observation g = A f + eta and the noise level
+ * delta of the paper's problem statement, Section 2 and Eq. discrpr):
+ * g[i] is problem i's n_i x n_i observed image (batch dtype, row-major, host
+ * or device memory as g_on_device says), delta[i] its delta.  All copies are
+ * enqueued on the batch stream and the call synchronises once, at the end,
+ * so the caller may reuse the host buffers after it returns (pinned host
+ * memory gives asynchronous copies).  Arguments are checked for every
+ * problem before anything is copied (MLBA_E_INVAL, nothing changed); the
+ * iteration state is left as it is. */
+int mlba_batch_set_data_all(mlba_batch* b, const void* const* g, int g_on_device,
+                            const double* delta);
+/* f~ of every problem at once: f_out[i] receives problem i's N_f,i x N_f,i
+ * result (batch dtype, row-major; caller-owned host or device memory as
+ * on_device says), with one synchronisation at the end for host
+ * destinations (device destinations: stream-ordered, no synchronisation). */
+int mlba_batch_result_all(mlba_batch* b, void* const* f_out, int on_device);
 /* Time one stage of the step on the batch stream with CUDA events: stage 0 =
  * the whole captured step (graph launch), 1 = residual stencil, 2 =
  * spectral preconditioner passes, 3 = adjoint correlation, 4 = fused

@@ -94,6 +94,8 @@ SIGNATURES = {
     "mlba_batch_stats": (_I, [_P, _I, ctypes.POINTER(Stats)]),
     "mlba_batch_reset": (_I, [_P]),
     "mlba_batch_set_data": (_I, [_P, _I, _P, _I, _D]),
+    "mlba_batch_set_data_all": (_I, [_P, ctypes.POINTER(_P), _I, ctypes.POINTER(_D)]),
+    "mlba_batch_result_all": (_I, [_P, ctypes.POINTER(_P), _I]),
     "mlba_batch_profile": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_float)]),
     "mlba_batch_graph_kernels": (_I, [_P, ctypes.POINTER(_I)]),
     "mlba_batch_destroy": (None, [_P]),
@@ -478,6 +480,34 @@ class Batch(_Base):
         self._enter()
         _check(self.lib.mlba_batch_set_data(self.h, int(i), ptr, dev, float(delta)),
                "mlba_batch_set_data")
+
+    def set_data_all(self, gs, deltas):
+        """Every problem's g and delta, one synchronisation (all on the host or
+        all on the device)."""
+        if len(gs) != len(self.shapes) or len(deltas) != len(self.shapes):
+            raise ValueError("one g and one delta per problem")
+        args = [self._arg(g) for g in gs]
+        devs = {a[1] for a in args}
+        if len(devs) != 1:
+            raise ValueError("all g on the host or all on the device")
+        ptrs = (_P * len(args))(*[a[0] for a in args])
+        d = (_D * len(args))(*[float(x) for x in deltas])
+        self._enter()
+        _check(self.lib.mlba_batch_set_data_all(self.h, ptrs, devs.pop(), d),
+               "mlba_batch_set_data_all")
+
+    def result_all(self, outs=None):
+        """Every problem's f, one synchronisation; into caller-provided host
+        arrays (e.g. pinned) when outs is given."""
+        if outs is None:
+            outs = [np.empty((nf, nf), dtype=self._np_dtype()) for _, nf in self.shapes]
+        if len(outs) != len(self.shapes):
+            raise ValueError("one output per problem")
+        for o, (_, nf) in zip(outs, self.shapes):
+            assert o.flags.c_contiguous and o.dtype == self._np_dtype() and o.shape == (nf, nf)
+        ptrs = (_P * len(outs))(*[o.ctypes.data_as(ctypes.c_void_p) for o in outs])
+        _check(self.lib.mlba_batch_result_all(self.h, ptrs, 0), "mlba_batch_result_all")
+        return outs
 
     def profile(self, stage, reps):
         """Mean milliseconds per launch of one stage (0 = whole step)."""

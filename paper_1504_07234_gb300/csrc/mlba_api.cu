@@ -1608,6 +1608,43 @@ int mlba_batch_set_data(mlba_batch* B, int i, const void* g, int on_device, doub
   return set_g(B, i, g, on_device, delta);
 }
 
+int mlba_batch_set_data_all(mlba_batch* B, const void* const* g, int on_device, const double* delta) {
+  if (!B || !g || !delta) return MLBA_E_INVAL;
+  const int count = (int)B->hp.size();
+  for (int i = 0; i < count; ++i) {
+    if (!g[i] || !(delta[i] >= 0.0)) return MLBA_E_INVAL;
+    if (B->hp[i].pd.ns && !(delta[i] > 0.0)) return MLBA_E_INVAL;
+  }
+  for (int i = 0; i < count; ++i) {
+    HostProb& h = B->hp[i];
+    const size_t bytes = (size_t)h.pd.n * h.pd.n * tsize(B->dtype);
+    CK(cudaMemcpyAsync(h.pd.buf[SL_G], g[i], bytes,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, B->stream));
+    if (delta[i] != h.pd.delta) {
+      h.pd.delta = delta[i];
+      CK(cudaMemcpyAsync(&B->d_probs[i].delta, &h.pd.delta, sizeof(double), cudaMemcpyHostToDevice,
+                         B->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(B->stream));
+  B->has_data = true;
+  return MLBA_OK;
+}
+
+int mlba_batch_result_all(mlba_batch* B, void* const* f_out, int on_device) {
+  if (!B || !f_out) return MLBA_E_INVAL;
+  const int count = (int)B->hp.size();
+  for (int i = 0; i < count; ++i)
+    if (!f_out[i]) return MLBA_E_INVAL;
+  for (int i = 0; i < count; ++i) {
+    const Prob& pd = B->hp[i].pd;
+    CK(cudaMemcpyAsync(f_out[i], pd.buf[SL_F], (size_t)pd.nf * pd.nf * tsize(B->dtype),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, B->stream));
+  }
+  if (!on_device) CK(cudaStreamSynchronize(B->stream));
+  return MLBA_OK;
+}
+
 int mlba_batch_profile(mlba_batch* B, int stage, int reps, float* ms) {
   if (!B || !ms || reps < 1 || stage < 0 || stage > 4) return MLBA_E_INVAL;
   if (!B->has_data) return MLBA_E_STATE;

@@ -66,6 +66,9 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert lib.mlba_create(psf.ctypes.data_as(ctypes.c_void_p), 5, 4, 1, 1, ctypes.byref(o), ctypes.byref(h)) == -1
     assert lib.mlba_create(psf.ctypes.data_as(ctypes.c_void_p), 5, 16, 3, 4, ctypes.byref(o), ctypes.byref(h)) == -1
     assert lib.mlba_create(psf.ctypes.data_as(ctypes.c_void_p), 5, 16, 3, 5, ctypes.byref(o), ctypes.byref(h)) == -1
+    # batch-wide copies without a batch or without arrays
+    assert lib.mlba_batch_set_data_all(None, None, 0, None) == -1
+    assert lib.mlba_batch_result_all(None, None, 0) == -1
     # a PSF wider than the stencil tile supports is refused, also before any device work
     big = np.full((67, 67), 1 / 67.0 ** 2)
     assert lib.mlba_create(big.ctypes.data_as(ctypes.c_void_p), 67, 128, 1, 1, ctypes.byref(o), ctypes.byref(h)) == -7

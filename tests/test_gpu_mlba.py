@@ -423,6 +423,48 @@ def test_batch_matches_single(M):
     b.close()
 
 
+def test_batch_set_data_all_and_result_all(M):
+    """The batch-wide upload and download (one synchronisation each) give
+    the per-problem calls' iterates bit for bit, and reject bad arguments
+    before copying anything."""
+    import ctypes
+    probs = [small("rect", "bccb", n=40, transform="dft", iters=6),
+             small("reflective", "tikh_ns", n=48, psf=I.psf_disk(3), transform="dct", iters=6, seed=3),
+             small("periodic", "tikh_ns", n=36, psf=I.psf_motion(5, 0.2), iters=6, seed=4)]
+    descs = [dict(psf=p.psf, g=p.g, delta=p.delta, bc=p.bc, precond=p.precond, mu=p.mu,
+                  alpha=p.alpha, transform=p.transform) for p in probs]
+    # new data: the observations scaled, the noise levels with them
+    g2 = [(1.25 * p.g).astype(np.float32) for p in probs]
+    d2 = [1.25 * p.delta for p in probs]
+    out = []
+    for batched in (False, True):
+        b = M.Batch(descs, dtype="f32", levels=2, stop=False, max_iter=6)
+        if batched:
+            b.set_data_all(g2, d2)
+        else:
+            for i in range(len(probs)):
+                b.set_data(i, g2[i], d2[i])
+        b.reset()
+        b.iterate(7)
+        fs = b.result_all() if batched else [b.result(i) for i in range(len(probs))]
+        out.append((fs, [b.stats(i) for i in range(len(probs))]))
+        if batched:
+            # a missing source or a zero delta for a 4-NS problem: MLBA_E_INVAL
+            bad = (ctypes.c_void_p * 3)(None, None, None)
+            d = (ctypes.c_double * 3)(*d2)
+            assert b.lib.mlba_batch_set_data_all(b.h, bad, 0, d) == -1
+            gp = [np.ascontiguousarray(x) for x in g2]
+            ptrs = (ctypes.c_void_p * 3)(*[x.ctypes.data_as(ctypes.c_void_p) for x in gp])
+            assert b.lib.mlba_batch_set_data_all(b.h, ptrs, 0, (ctypes.c_double * 3)(d2[0], 0.0, d2[2])) == -1
+            assert b.lib.mlba_batch_result_all(b.h, bad, 0) == -1
+            # nothing was changed by the rejected calls
+            np.testing.assert_array_equal(b.result(1), fs[1])
+        b.close()
+    for i in range(len(probs)):
+        np.testing.assert_array_equal(out[0][0][i], out[1][0][i])
+        assert out[0][1][i] == out[1][1][i]
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_two_group_schedule_equals_one_group(M, dtype):
     """The two-group schedule (two groups half a step apart on two streams)
