@@ -1197,7 +1197,11 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     for (size_t q = 0; q < sz.size(); ++q) { foffs[k][q] = total; total += al(sz[q]); }
   }
   B->arena_bytes = total;
-  if (cudaMalloc(&B->arena, total) != cudaSuccess) { destroy_batch(B); return MLBA_E_NOMEM; }
+  if (cudaMalloc(&B->arena, total) != cudaSuccess) {
+    (void)cudaGetLastError();   // an allocation failure is not sticky: leave no stale error behind
+    destroy_batch(B);
+    return MLBA_E_NOMEM;
+  }
   // ---- fill pointers and constant tables
   std::vector<unsigned char> host_init;   // staged constant data
   for (int i = 0; i < count; ++i) {
@@ -1298,6 +1302,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   if (cudaMalloc(&B->d_probs, ntab * sizeof(Prob)) != cudaSuccess ||
       cudaMalloc(&B->d_states, count * sizeof(State)) != cudaSuccess ||
       cudaMalloc(&B->d_opstates, count * sizeof(State)) != cudaSuccess) {
+    (void)cudaGetLastError();
     destroy_batch(B); return MLBA_E_NOMEM;
   }
   CK(cudaMemcpy(B->d_probs, probs_h.data(), ntab * sizeof(Prob), cudaMemcpyHostToDevice));
