@@ -229,6 +229,8 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
   const int zc = f3_refl(x, nf, &pcx);
   const T scol = pcx ? T(-1) : T(1);
   const bool own_c = act && x >= tx0 && x < tx0 + F3_TX && x < nf;
+  // owned rows [seg_lo, own_hi): one unsigned compare per row
+  const unsigned own_rows = (unsigned)max(min(seg_hi, nf) - seg_lo, 0);
   const T* ccol = cin + (act ? x - cx0 : D);   // idle lanes read a valid column
   // level 2 reads c_1 = (b0 x b0) u, formed here from the u tile: lane l keeps
   // c_1 at columns x - 2 and x + 2 (a sliding ring of the horizontally
@@ -373,7 +375,7 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
     // change sign under an odd number of mirrorings
     const T srow = zqp[kq] ? T(-1) : T(1);
     const T s11 = srow * scol;
-    const bool own = own_c && y >= seg_lo && y < seg_hi && y < nf;
+    const bool own = own_c && (unsigned)(y - seg_lo) < own_rows;
     const int zwo = zqo[kq];
     ZGroup<TZ> zo;
     TZ zlo = TZ(0.0f);
@@ -408,8 +410,9 @@ __device__ __forceinline__ void f3_level(const Prob& pd, const T* __restrict__ c
       // register queue then finds them there
       const int ya = y + F3_PF + Z_L2_AHEAD;
       if (ya < yc1) {
-        bool par;
-        const int qa = f3_refl(ya, nf, &par) * nf + zc;
+        // (ya >= 0; past the bottom edge the row is clamped rather than
+        // mirrored: a prefetch of a neighbouring line only costs an L2 miss)
+        const int qa = min(ya, nf - 1) * nf + zc;
         prefetch_l2(zin + (gbase + 8 * qa));
         if (TOP) prefetch_l2(zin + (lbase + qa));
       }
