@@ -125,6 +125,10 @@ struct mlba_batch {
   StepLists grp[2];
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // a parallel branch inside one step: the stationary column pass beside the
+  // 4-NS chain (index 0 for the batch stream, 1 for the side stream)
+  cudaStream_t br[2] = {nullptr, nullptr};
+  cudaEvent_t ev_bf[2] = {nullptr, nullptr}, ev_bj[2] = {nullptr, nullptr};
   cudaGraph_t g_head = nullptr, g_body = nullptr, g_tail = nullptr;
   cudaGraphExec_t x_head = nullptr, x_body = nullptr, x_tail = nullptr;
   // framelet tile shape (k_frame.cu) and how it was chosen
@@ -292,13 +296,27 @@ void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
     // a4: spectral preconditioners (Algorithms 1, 3, 4, 4-NS)
     if (L.any_spec) {
       launch_rows_fwd<T>(P, S, L.rows_spec.dev, L.rows_spec.count, SL_R, 0, B->smem_fft, s);
-      launch_cols<T>(P, S, L.cols_stat.dev, L.cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, s);
+      // The stationary column pass and the 4-NS chain (forward pass with the
+      // bracketing sums, Halley passes, weighted inverse) work on disjoint
+      // problems: with both present the stationary pass runs as a parallel
+      // branch, so that the partial waves of the two launches overlap.
+      const int bi = (s == B->stream) ? 0 : (s == B->side ? 1 : -1);
+      const bool fork = L.any_ns && L.cols_stat.count > 0 && bi >= 0 && B->br[bi] != nullptr;
+      cudaStream_t sc = s;
+      if (fork) {
+        cudaEventRecord(B->ev_bf[bi], s);
+        cudaStreamWaitEvent(B->br[bi], B->ev_bf[bi], 0);
+        sc = B->br[bi];
+      }
+      launch_cols<T>(P, S, L.cols_stat.dev, L.cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, sc);
+      if (fork) cudaEventRecord(B->ev_bj[bi], sc);
       if (L.any_ns) {
         launch_cols<T>(P, S, L.cols_ns.dev, L.cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
         // (the bracketing pass runs inside the forward column pass)
         for (int k = 1; k < ns_passes<T>(); ++k) launch_spec<T>(P, S, L.spec.dev, L.spec.count, 0, s);
         launch_cols<T>(P, S, L.cols_ns.dev, L.cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
       }
+      if (fork) cudaStreamWaitEvent(s, B->ev_bj[bi], 0);
       launch_rows_inv<T>(P, S, L.rows_spec.dev, L.rows_spec.count, SL_T, 0, B->smem_fft, s);
     }
     // a4 with the antireflective transform (Algorithms 1, 3, 4 on antireflective A)
@@ -547,6 +565,11 @@ void destroy_batch(mlba_batch* B) {
   if (B->ev_fork) cudaEventDestroy(B->ev_fork);
   if (B->ev_join) cudaEventDestroy(B->ev_join);
   if (B->side) cudaStreamDestroy(B->side);
+  for (int q = 0; q < 2; ++q) {
+    if (B->br[q]) cudaStreamDestroy(B->br[q]);
+    if (B->ev_bf[q]) cudaEventDestroy(B->ev_bf[q]);
+    if (B->ev_bj[q]) cudaEventDestroy(B->ev_bj[q]);
+  }
   for (int2* p : B->allocs) cudaFree(p);
   if (B->arena) cudaFree(B->arena);
   if (B->d_probs) cudaFree(B->d_probs);
@@ -1405,7 +1428,14 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
     for (int i = 0; i < count; ++i) add_frame_items(B->hp[i].pd, i, B->levels, B->frame_shape, fs);
     if (build_frame_list(B, B->frame, fs, B->levels) != MLBA_OK) { destroy_batch(B); return MLBA_E_CUDA; }
   }
-  // ---- capture one step
+  // ---- capture one step (branch streams first: a capture forks into them)
+  for (int q = 0; q < 2; ++q) {
+    if (cudaStreamCreateWithFlags(&B->br[q], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_bf[q], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_bj[q], cudaEventDisableTiming) != cudaSuccess) {
+      destroy_batch(B); return MLBA_E_CUDA;
+    }
+  }
   if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     destroy_batch(B); return MLBA_E_CUDA;
   }
