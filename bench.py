@@ -465,7 +465,7 @@ def main():
 
 
 # ---------------------------------------------------------------------------
-# single-image workloads (BASELINE configs 1, 2, 3, 5 and a 4-level variant)
+# single-image workloads 1, 2, 3 and 5, and workload 5 at four levels
 
 def frame_bytes_one(p, levels, zbytes, tbytes):
     """Algorithmic bytes of one framelet launch for one problem: z read and
