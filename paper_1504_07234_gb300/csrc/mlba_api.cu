@@ -58,6 +58,9 @@ struct StepLists {
   // epilogues on the problems (residual, correlation V, reblurring into U)
   ItemList fc_pad_f, fc_rows_f, fc_cols_f, fc_out_r, fc_pad_a, fc_rows_a, fc_cols_a, fc_out_v, fc_out_u;
   ItemList balance;   // balanced formulation: u <- f + u
+  // (two-group graphs) the row passes of the stationary and of the 4-NS
+  // problems apart, so that each kind's transform chain is one graph branch
+  ItemList rows_st, rows_ns;
   int any_krylov = 0, any_spec = 0, any_ns = 0, any_ar = 0, pcg_max = 5;
 };
 struct StepItems {
@@ -66,6 +69,7 @@ struct StepItems {
   std::vector<int2> fc_pad_f, fc_rows_f, fc_cols_f, fc_out_r, fc_pad_a, fc_rows_a, fc_cols_a,
       fc_out_v, fc_out_u, balance;
   std::vector<int2> frame[FRAME_SECTIONS];   // see add_frame_items
+  std::vector<int2> rows_st, rows_ns;
   int any_krylov = 0, any_spec = 0, any_ns = 0, any_ar = 0, pcg_max = 5;
 };
 
@@ -294,7 +298,25 @@ void enqueue_step(mlba_batch* B, const StepLists& L, int part, cudaStream_t s) {
       launch_fc_out<T>(P, S, L.fc_out_r.dev, L.fc_out_r.count, FC_RESID_MODE, 0, SL_R, s);
     }
     // a4: spectral preconditioners (Algorithms 1, 3, 4, 4-NS)
-    if (L.any_spec) {
+    const int bs = (s == B->stream) ? 0 : (s == B->side ? 1 : -1);
+    if (L.any_spec && L.rows_st.count > 0 && L.rows_ns.count > 0 && bs >= 0 && B->br[bs] != nullptr) {
+      // Stationary and 4-NS problems both present (two-group graphs): each
+      // kind's transform chain is one branch of the graph; they touch
+      // disjoint problems, so their partial waves overlap throughout
+      cudaStream_t sb = B->br[bs];
+      cudaEventRecord(B->ev_bf[bs], s);
+      cudaStreamWaitEvent(sb, B->ev_bf[bs], 0);
+      launch_rows_fwd<T>(P, S, L.rows_st.dev, L.rows_st.count, SL_R, 0, B->smem_fft, sb);
+      launch_cols<T>(P, S, L.cols_stat.dev, L.cols_stat.count, COL_FUSED, 0, 0.0, 0, B->smem_fft, sb);
+      launch_rows_inv<T>(P, S, L.rows_st.dev, L.rows_st.count, SL_T, 0, B->smem_fft, sb);
+      cudaEventRecord(B->ev_bj[bs], sb);
+      launch_rows_fwd<T>(P, S, L.rows_ns.dev, L.rows_ns.count, SL_R, 0, B->smem_fft, s);
+      launch_cols<T>(P, S, L.cols_ns.dev, L.cols_ns.count, COL_FWD, 0, 0.0, 0, B->smem_fft, s);
+      for (int k = 1; k < ns_passes<T>(); ++k) launch_spec<T>(P, S, L.spec.dev, L.spec.count, 0, s);
+      launch_cols<T>(P, S, L.cols_ns.dev, L.cols_ns.count, COL_NS_INV, 0, 0.0, 0, B->smem_fft, s);
+      launch_rows_inv<T>(P, S, L.rows_ns.dev, L.rows_ns.count, SL_T, 0, B->smem_fft, s);
+      cudaStreamWaitEvent(s, B->ev_bj[bs], 0);
+    } else if (L.any_spec) {
       launch_rows_fwd<T>(P, S, L.rows_spec.dev, L.rows_spec.count, SL_R, 0, B->smem_fft, s);
       // The stationary column pass and the 4-NS chain (forward pass with the
       // bracketing sums, Halley passes, weighted inverse) work on disjoint
@@ -430,8 +452,12 @@ void collect_step(const Prob& pd, int i, int levels, int shape, StepItems& V) {
   } else if (specp) {
     add(V.rows_spec, pd.nblk_rows);
     V.any_spec = 1;
-    if (pd.ns) { add(V.cols_ns, pd.nblk_cols); add(V.spec, pd.nblk_spec); V.any_ns = 1; }
-    else add(V.cols_stat, pd.nblk_cols);
+    if (pd.ns) {
+      add(V.rows_ns, pd.nblk_rows); add(V.cols_ns, pd.nblk_cols); add(V.spec, pd.nblk_spec);
+      V.any_ns = 1;
+    } else {
+      add(V.rows_st, pd.nblk_rows); add(V.cols_stat, pd.nblk_cols);
+    }
   }
   V.pcg_max = pd.pcg_max;
 }
@@ -517,6 +543,7 @@ int build_split(mlba_batch* B) {
     rc |= build_list(B, L.corr_kry, v.corr_kry); rc |= build_list(B, L.blur_kry, v.blur_kry);
     rc |= build_list(B, L.rows_spec, v.rows_spec); rc |= build_list(B, L.cols_stat, v.cols_stat);
     rc |= build_list(B, L.cols_ns, v.cols_ns); rc |= build_list(B, L.spec, v.spec);
+    rc |= build_list(B, L.rows_st, v.rows_st); rc |= build_list(B, L.rows_ns, v.rows_ns);
     rc |= build_list(B, L.rows_kry, v.rows_kry); rc |= build_list(B, L.cols_kry, v.cols_kry);
     rc |= build_list(B, L.vec_kry, v.vec_kry); rc |= build_list(B, L.vec_kry_bc, v.vec_kry_bc);
     rc |= build_frame_list(B, L.frame, v.frame, B->levels);
