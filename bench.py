@@ -416,18 +416,27 @@ def main():
     pinned_f = [torch.empty((p.nf, p.nf), dtype=torch.float32).pin_memory() for p in probs]
     h2d = sum(x.numel() * 4 for x in pinned_g)
     d2h = sum(x.numel() * 4 for x in pinned_f)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    batch.set_data_all([x.numpy() for x in pinned_g], [p.delta for p in probs])
-    batch.reset()
-    batch.iterate(K)
-    batch.result_all([x.numpy() for x in pinned_f])
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": mpix * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+    gs, fs, deltas = [x.numpy() for x in pinned_g], [x.numpy() for x in pinned_f], [p.delta for p in probs]
+    # host-timed, so the median of three identical call sequences
+    reps = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch.set_data_all(gs, deltas)
+        batch.reset()
+        batch.iterate(K)
+        batch.result_all(fs)
+        torch.cuda.synchronize()
+        reps.append(time.perf_counter() - t0)
+    e2e_s = sorted(reps)[1]
+    # whole job: every rank's pixels over the slowest rank's time
+    e2e_ms, e2e_mpix = reduce_rank_metrics(e2e_s * 1e3, mpix, dist, device="cuda")
+    e2e_s = e2e_ms / 1e3
+    e2e = {"value": e2e_mpix * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
            "d2h_bytes_per_step": d2h / K,
-           "note": f"one call sequence = upload of every g (one call), reset, {K} iterations, "
-                   "download of every f (one call)"}
+           "note": f"median of 3 call sequences, each = upload of every g (one call), reset, "
+                   f"{K} iterations, download of every f (one call)",
+           "sequences_s": reps}
     batch.close()
 
     extra = {}
