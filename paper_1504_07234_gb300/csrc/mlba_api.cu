@@ -102,6 +102,7 @@ struct mlba_batch {
   State* d_opstates = nullptr;
   unsigned char* arena = nullptr;
   size_t arena_bytes = 0;
+  size_t zero_bytes = 0;        // [arena, arena + zero_bytes): every problem's f and z^0
   // item lists
   ItemList blur, corr, reblur, corr_kry, blur_kry, rows_spec, cols_stat, cols_ns, spec, rows_kry,
       cols_kry, vec_kry, vec_kry_bc, frame, corr_all, rows_all, cols_all, spec_all, vec_all,
@@ -1197,7 +1198,7 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
   const size_t ts = tsize(o.dtype), zs = zsize(o.z_store);
   // ---- arena layout
   size_t total = 0;
-  std::vector<std::vector<size_t>> offs(count);
+  std::vector<std::vector<size_t>> offs(count), szs(count);
   for (int i = 0; i < count; ++i) {
     Prob& pd = B->hp[i].pd;
     const size_t n2 = (size_t)pd.n * pd.n, nf2 = (size_t)pd.nf * pd.nf, ne2 = (size_t)pd.ne * pd.ne;
@@ -1230,9 +1231,21 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
         (size_t)pd.p * ts, (size_t)pd.p * ts,  // hy, hx
         std::max({3 * (size_t)pd.nblk_blur, 3 * (size_t)pd.nblk_vec, (size_t)SPEC_SUMS * std::max(pd.nblk_spec, pd.nblk_cols), (size_t)1}) * 8,  // partial
         (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 8, (size_t)(pd.max_iter + 2) * 4};
-    offs[i].resize(sz.size());
-    for (size_t k = 0; k < sz.size(); ++k) { offs[i][k] = total; total += al(sz[k]); }
+    szs[i] = sz;
   }
+  // f and z^0 of every problem come first, side by side, so that a reset
+  // clears all of them with one memset of [arena, arena + zero_bytes); the
+  // other buffers follow, problem by problem
+  const size_t kF = SL_F, kZ0 = NSLOT;
+  for (int i = 0; i < count; ++i) {
+    offs[i].assign(szs[i].size(), 0);
+    offs[i][kF] = total; total += al(szs[i][kF]);
+    offs[i][kZ0] = total; total += al(szs[i][kZ0]);
+  }
+  B->zero_bytes = total;
+  for (int i = 0; i < count; ++i)
+    for (size_t k = 0; k < szs[i].size(); ++k)
+      if (k != kF && k != kZ0) { offs[i][k] = total; total += al(szs[i][k]); }
   // convolution entries: X, Y, the spectrum work array, the two spectra, a
   // zero |lambda|^2 and the twiddles, shared by the pair of one problem (the
   // forward pass and the adjoint pass of a step never overlap)
@@ -1483,12 +1496,9 @@ int create_batch(const mlba_problem* probs, int count, const mlba_opts* opts_in,
 
 int reset_batch(mlba_batch* B) {
   std::vector<State> st_h(B->hp.size());
-  for (size_t i = 0; i < B->hp.size(); ++i) {
-    const Prob& pd = B->hp[i].pd;
-    CK(cudaMemsetAsync(pd.z[0], 0, (size_t)pd.nbands * pd.nf * pd.nf * zsize(B->z_store), B->stream));
-    CK(cudaMemsetAsync(pd.buf[SL_F], 0, (size_t)pd.nf * pd.nf * tsize(B->dtype), B->stream));
-    st_h[i] = initial_state(pd);
-  }
+  // f and z^0 of every problem: one region at the start of the arena
+  CK(cudaMemsetAsync(B->arena, 0, B->zero_bytes, B->stream));
+  for (size_t i = 0; i < B->hp.size(); ++i) st_h[i] = initial_state(B->hp[i].pd);
   CK(cudaMemcpyAsync(B->d_states, st_h.data(), st_h.size() * sizeof(State), cudaMemcpyHostToDevice,
                      B->stream));
   CK(cudaStreamSynchronize(B->stream));
